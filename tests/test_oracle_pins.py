@@ -1,0 +1,462 @@
+"""Pins of the FP64 oracle against results the paper and the mathematics fix independently.
+
+Each test checks the oracle against something other than itself: textbook closed forms (Friis,
+Fresnel in its Snell-law form, Brewster's angle), the Tang22 path-loss formula the paper says its
+model reduces to (Sec. II-A), the far-field law of a phase-aligned RIS, pattern normalisation,
+brute-force Fermat minimisation for the image method, reciprocity, and values printed in the paper.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+from oracle import oracle as O
+from paper_2402_13034_gb300 import scenarios as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ETA0 = 120 * math.pi
+
+
+def _free(freq=28e9, M_rings=3, pitch=None, tx=(0.0, -1.5, 2.0), tx_pat=S.PATTERN_ISO, tx_gain=1.0,
+          rx_pat=S.PATTERN_ISO, rx_gain=1.0, tx_orient=None, rx_orient=None, power=1.0, elem_gain=0.0,
+          layout=None, d=None):
+    lam = S.C0 / freq
+    pitch = pitch or lam / 2
+    d = d or lam / 2
+    uv = layout if layout is not None else S.hex_layout(M_rings, pitch)
+    ris = S.RIS(uv, np.zeros(3, np.float32), np.array([1, 0, 0], np.float32),
+                np.array([0, 1, 0], np.float32), d, d, elem_gain, -1)
+    txa = S.Antenna(np.asarray(tx, np.float32), tx_orient if tx_orient is not None else S.identity_orient(),
+                    power, tx_gain, tx_pat)
+    rxa = S.Antenna(np.zeros(3, np.float32), rx_orient if rx_orient is not None else S.identity_orient(),
+                    1.0, rx_gain, rx_pat)
+    return S.Workload("t", freq, S.empty_scene(), ris, txa, rxa, np.zeros((1, 3), np.float32),
+                      np.ones((1, len(uv)), np.complex64), 0, 0, False)
+
+
+def _plane_scene(z=0.0, half=50.0, eps=5.3, sigma=0.0, extra_planes=()):
+    mb = S._MeshBuilder()
+    mats = [(eps, sigma)]
+    mb.quad((-half, -half, z), (half, -half, z), (half, half, z), (-half, half, z), 0)
+    for zz in extra_planes:
+        mb.quad((-half, -half, zz), (-half, half, zz), (half, half, zz), (half, -half, zz), 0)
+    return mb.scene(mats)
+
+
+# ------------------------------------------------------------------------------------------------
+# T1: Friis (Eq. 4 + Eq. 8 with no RIS factor) - power and phase sign
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("rx", [(0.3, 0.7, 1.5), (-1.9, 1.2, 1.5), (2.0, -2.0, 1.5)])
+def test_friis_los(rx):
+    w = _free(power=0.37, tx_gain=1.0, rx_gain=1.0)
+    o = O.Oracle(w)
+    f = o.field(np.array([rx], np.float32))
+    E, P, _ = o.evaluate(f, np.zeros(w.n_elem))
+    lam = S.C0 / w.freq_hz
+    d = np.linalg.norm(np.asarray(rx, np.float32).astype(np.float64) - w.tx.pos.astype(np.float64))
+    P_friis = float(np.float32(0.37)) * (lam / (4 * math.pi * d)) ** 2
+    assert abs(P[0] / P_friis - 1) < 1e-12
+    # phase -k d (e^{+j omega t} convention, Eq. 3)
+    ph = (-2 * math.pi * d / lam) % (2 * math.pi)
+    assert abs(np.angle(E[0] * np.exp(-1j * ph))) < 1e-9
+
+
+def test_friis_with_patterns():
+    """Directive Tx (cos^(G/2-1), Sec. III-B) and monopole Rx: P = Pt Gt Ft Gr Fr (lambda/4 pi d)^2."""
+    txp = np.array([0.0, -1.5, 2.0])
+    rxp = np.array([0.4, 0.5, 1.1], np.float32)
+    w = _free(tx_pat=S.PATTERN_COS_POW, tx_gain=10 ** 1.9, rx_pat=S.PATTERN_MONOPOLE_QW,
+              tx_orient=S.orient_towards(txp, (0, 0, 0)))
+    o = O.Oracle(w)
+    E, P, _ = o.evaluate(o.field(rxp[None]), np.zeros(w.n_elem))
+    dvec = rxp.astype(np.float64) - w.tx.pos.astype(np.float64)
+    d = np.linalg.norm(dvec)
+    zt = w.tx.orient[2].astype(np.float64)
+    cos_t = dvec @ zt / d / np.linalg.norm(zt)
+    Gt = np.float32(10 ** 1.9)
+    Ft = cos_t ** (float(Gt) / 2 - 1)
+    cos_r = -dvec[2] / d
+    Fr = (math.cos(math.pi / 2 * cos_r) / math.sqrt(1 - cos_r ** 2)) ** 2
+    lam = S.C0 / w.freq_hz
+    assert abs(P[0] / (float(Gt) * Ft * Fr * (lam / (4 * math.pi * d)) ** 2) - 1) < 1e-10
+
+
+# ------------------------------------------------------------------------------------------------
+# T2: reduction to the Tang22 model (Sec. II-A, last paragraph)
+# ------------------------------------------------------------------------------------------------
+def _tang22_power(w, rx, gamma, G):
+    """Tang et al. 2022 RIS path loss, P = Pt Gt Gr G dx dy lambda^2/(64 pi^3) |sum F^1/2 Gamma e^{-jk(rt+rr)}/(rt rr)|^2."""
+    lam = S.C0 / w.freq_hz
+    k = 2 * math.pi / lam
+    ris = w.ris
+    c = ris.center.astype(np.float64)
+    t1, t2 = ris.t1.astype(np.float64), ris.t2.astype(np.float64)
+    n = np.cross(t1, t2)
+    n /= np.linalg.norm(n)
+    e = c + ris.elem_uv[:, :1].astype(np.float64) * t1 + ris.elem_uv[:, 1:].astype(np.float64) * t2
+    T = w.tx.pos.astype(np.float64)
+    R = np.asarray(rx, np.float32).astype(np.float64)
+    rt = np.linalg.norm(e - T, axis=1)
+    rr = np.linalg.norm(R - e, axis=1)
+    cos_in = ((T - e) @ n) / rt
+    cos_out = ((R - e) @ n) / rr
+    zt = w.tx.orient[2].astype(np.float64)
+    zt /= np.linalg.norm(zt)
+    cos_tx = ((e - T) @ zt) / rt
+    Gt = float(np.float32(w.tx.gain_lin))
+    Ft = np.where(cos_tx > 0, np.abs(cos_tx) ** (Gt / 2 - 1), 0) if w.tx.pattern == S.PATTERN_COS_POW else 1.0
+    zr = w.rx.orient[2].astype(np.float64)
+    cos_rx = ((e - R) @ zr) / rr
+    Fr = (np.cos(math.pi / 2 * cos_rx) / np.sqrt(1 - cos_rx ** 2)) ** 2 \
+        if w.rx.pattern == S.PATTERN_MONOPOLE_QW else 1.0
+    Fc = Ft * Fr * cos_in * cos_out
+    s = np.sum(np.sqrt(Fc) * gamma * np.exp(-1j * k * (rt + rr)) / (rt * rr))
+    Pt, Gr = float(np.float32(w.tx.power_w)), float(np.float32(w.rx.gain_lin))
+    dx, dy = float(np.float32(ris.dy)), float(np.float32(ris.dz))
+    return Pt * Gt * Gr * G * dx * dy * lam ** 2 / (64 * math.pi ** 3) * abs(s) ** 2
+
+
+@pytest.mark.parametrize("elem_gain", [0.0, 3.7])
+def test_tang22_reduction(elem_gain):
+    w = S.paper_anechoic()
+    w.ris.elem_gain = elem_gain
+    o = O.Oracle(w)
+    rng = np.random.default_rng(5)
+    gamma = 1.25 * np.exp(2j * np.pi * rng.random(w.n_elem))
+    rx = np.array([[1.33, 0.23, 0.11], [1.0, 0.8, 0.114], [1.5, 0.05, 0.2]], np.float32)
+    f = o.field(rx)
+    lam = S.C0 / w.freq_hz
+    dy = float(np.float32(w.ris.dy))
+    G = float(np.float32(elem_gain)) if elem_gain > 0 else 4 * math.pi * dy * dy / lam ** 2
+    for i in range(len(rx)):
+        E_ris = f["A"][i] @ gamma      # RIS part only (LOS is separate in E0)
+        P_ris = abs(E_ris) ** 2 / (2 * ETA0)
+        assert abs(P_ris / _tang22_power(w, rx[i], gamma, G) - 1) < 1e-11
+
+
+def test_tang22_default_gain_form():
+    """With G = 4 pi dy dz / lambda^2 the prefactor becomes Pt Gt Gr (dy dz)^2 / (16 pi^2) (Sec. II-A)."""
+    w = _free()
+    lam = S.C0 / w.freq_hz
+    d = float(np.float32(w.ris.dy))
+    G = 4 * math.pi * d * d / lam ** 2
+    assert abs(G * d * d * lam ** 2 / (64 * math.pi ** 3) / ((d * d) ** 2 / (16 * math.pi ** 2)) - 1) < 1e-14
+    o = O.Oracle(w)
+    rx = np.array([[0.5, 0.2, 1.5]], np.float32)
+    g = np.exp(1j * np.linspace(0, 3, w.n_elem))
+    P = abs(o.field(rx)["A"][0] @ g) ** 2 / (2 * ETA0)
+    assert abs(P / _tang22_power(w, rx[0], g, G) - 1) < 1e-11
+
+
+# ------------------------------------------------------------------------------------------------
+# T3/T4: coherent focusing, N^2 gain and the far-field law
+# ------------------------------------------------------------------------------------------------
+def _far_field_case(s, rings):
+    """Tx and Rx at distances s*d1, s*d2 on fixed directions; geometric phase alignment."""
+    freq = 28e9
+    lam = S.C0 / freq
+    d1, d2 = 1.0, 1.3
+    ut = np.array([0.3, -0.4, 1.0]); ut /= np.linalg.norm(ut)
+    ur = np.array([-0.5, 0.2, 1.0]); ur /= np.linalg.norm(ur)
+    tx = (s * d1 * ut).astype(np.float32)
+    rx = (s * d2 * ur).astype(np.float32)
+    w = _free(freq=freq, M_rings=rings, tx=tx)
+    o = O.Oracle(w)
+    e = o.element_positions()
+    dt = np.linalg.norm(e - tx.astype(np.float64), axis=1)
+    dr = np.linalg.norm(rx.astype(np.float64) - e, axis=1)
+    k = 2 * math.pi / lam
+    gamma = np.exp(1j * k * (dt + dr))
+    f = o.field(rx[None])
+    A = f["A"][0]
+    E_ris = A @ gamma
+    dtt = np.linalg.norm(tx.astype(np.float64))
+    drr = np.linalg.norm(rx.astype(np.float64))
+    cos_i = tx.astype(np.float64)[2] / dtt
+    cos_r = rx.astype(np.float64)[2] / drr
+    N = w.n_elem
+    d = float(np.float32(w.ris.dy))
+    P_far = N ** 2 * (d * d) ** 2 * cos_i * cos_r / (16 * math.pi ** 2)  # Pt = Gt = Gr = 1
+    return abs(E_ris) ** 2 / (2 * ETA0) * dtt ** 2 * drr ** 2, P_far, A, gamma
+
+
+def test_coherent_sum_is_incoherent_sum_when_aligned():
+    _, _, A, gamma = _far_field_case(4.0, 3)
+    assert abs(abs(A @ gamma) / np.sum(np.abs(A)) - 1) < 1e-12
+
+
+def test_far_field_law_and_n2_gain():
+    errs = []
+    for s in (1.0, 4.0, 16.0, 64.0):
+        p, pf, _, _ = _far_field_case(s, 3)
+        errs.append(abs(p / pf - 1))
+    assert errs[-1] < 1e-4
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+    # error falls at least quadratically in 1/s between s=16 and s=64
+    assert errs[-1] < errs[-2] / 8
+    p37, _, _, _ = _far_field_case(64.0, 3)
+    p127, _, _, _ = _far_field_case(64.0, 6)
+    assert abs(p127 / p37 / (127 / 37) ** 2 - 1) < 1e-3
+
+
+# ------------------------------------------------------------------------------------------------
+# T5: pattern normalisation pins "Gt linear" and the exponent Gt/2 - 1 (Sec. III-B)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("gain_db", [10.0, 19.0, 25.0])
+def test_cos_pow_directivity(gain_db):
+    G = 10 ** (gain_db / 10)
+    th = np.linspace(0, math.pi, 200001)
+    F = np.array([O.pattern(S.PATTERN_COS_POW, G, math.cos(t)) for t in th])
+    integral = 2 * math.pi * np.trapezoid(F * np.sin(th), th)
+    assert abs(4 * math.pi / integral / G - 1) < 1e-6
+
+
+def test_monopole_shape():
+    assert O.pattern(S.PATTERN_MONOPOLE_QW, 1.0, 0.0) == pytest.approx(1.0, abs=1e-15)
+    assert O.pattern(S.PATTERN_MONOPOLE_QW, 1.0, 1.0) == 0.0
+    # symmetric about the horizontal plane and small near the axis
+    for c in (0.1, 0.5, 0.9):
+        assert O.pattern(S.PATTERN_MONOPOLE_QW, 1.0, c) == pytest.approx(O.pattern(S.PATTERN_MONOPOLE_QW, 1.0, -c))
+    assert O.pattern(S.PATTERN_MONOPOLE_QW, 1.0, 0.99999) < 1e-4
+
+
+def test_element_pattern_front_hemisphere():
+    """F(theta)=cos(theta) (Sec. III-C): an Rx behind the RIS plane receives nothing through the RIS."""
+    w = _free()
+    o = O.Oracle(w)
+    f = o.field(np.array([[0.2, 0.1, -1.0]], np.float32))
+    assert np.all(f["A"] == 0)
+
+
+# ------------------------------------------------------------------------------------------------
+# T6: Fresnel and the image method on brute-force tiny scenes
+# ------------------------------------------------------------------------------------------------
+def test_fresnel_te_snell_form():
+    """TE coefficient against its Snell's-law form (n1 cos i - n2 cos t)/(n1 cos i + n2 cos t)."""
+    for eps in (2.0, 5.3, 9.0):
+        n2 = math.sqrt(eps)
+        for th in np.linspace(0, 1.5, 13):
+            tt = math.asin(math.sin(th) / n2)
+            R = (math.cos(th) - n2 * math.cos(tt)) / (math.cos(th) + n2 * math.cos(tt))
+            assert O.fresnel(math.cos(th), eps, 0.0, 28e9) == pytest.approx(R, abs=1e-13)
+
+
+def test_fresnel_limits():
+    eps = 5.3
+    assert O.fresnel(1.0, eps, 0.0, 28e9) == pytest.approx((1 - math.sqrt(eps)) / (1 + math.sqrt(eps)), abs=1e-14)
+    assert O.fresnel(1e-9, eps, 0.0, 28e9) == pytest.approx(-1.0, abs=1e-8)
+    # PEC limit: metal eps_r = 1, sigma = 1e7 S/m at 23.8 GHz (Table 1)
+    for th in (0.0, 0.5, 1.2):
+        assert abs(abs(O.fresnel(math.cos(th), 1.0, 1e7, 23.8e9)) - 1) < 1e-3
+    # TM vanishes at Brewster's angle tan(theta_B) = sqrt(eps)
+    thb = math.atan(math.sqrt(eps))
+    assert abs(O.fresnel(math.cos(thb), eps, 0.0, 28e9, tm=True)) < 1e-14
+
+
+def _one_plane_workload(tx, eps=5.3, sigma=0.0):
+    w = _free(tx=tx)
+    w.scene = _plane_scene(0.0, 50.0, eps, sigma)
+    # lift the RIS off the plane so it does not sit in the floor; the plane is face 0
+    w.ris.center = np.array([0.0, 0.0, 1.0], np.float32)
+    w.max_order_rx = 1
+    w.env_paths = True
+    return w
+
+
+@pytest.mark.parametrize("tx,rx", [((0.0, -1.5, 2.0), (1.2, 0.7, 0.6)), ((3.0, 1.0, 0.3), (-2.0, 0.5, 2.5))])
+def test_image_method_fermat_and_fresnel(tx, rx):
+    w = _one_plane_workload(tx)
+    o = O.Oracle(w)
+    T = np.asarray(tx, np.float32).astype(np.float64)
+    R = np.asarray(rx, np.float32).astype(np.float64)
+    ok, amb, pts = o.validate(T, -1, R, -1, 0)
+    assert ok and not amb
+    L_img = np.linalg.norm(pts[1] - T) + np.linalg.norm(R - pts[1])
+    # brute force Fermat: shortest T -> (x, y, 0) -> R over the plane
+    res = minimize(lambda p: np.linalg.norm(np.array([p[0], p[1], 0]) - T) + np.linalg.norm(R - np.array([p[0], p[1], 0])),
+                   x0=[0.0, 0.0], method="Nelder-Mead", options=dict(xatol=1e-12, fatol=1e-14, maxiter=20000))
+    assert abs(res.fun - L_img) < 1e-9
+    assert np.allclose(pts[1][:2], res.x, atol=1e-5)
+    # field: E0 = LOS + R_TE(theta_i) * Friis(L1 + L2) (Eq. 4 + Eq. 8 along the unfolded path)
+    f = o.field(R.astype(np.float32)[None])
+    lam = S.C0 / w.freq_hz
+    k = 2 * math.pi / lam
+    d = np.linalg.norm(R - T)
+    cos_i = abs(T[2] - pts[1][2]) / np.linalg.norm(pts[1] - T)
+    n2 = math.sqrt(float(np.float32(5.3)))   # materials travel as float32
+    sin_i = math.sqrt(1 - cos_i ** 2)
+    cos_t = math.sqrt(1 - (sin_i / n2) ** 2)
+    Rte = (cos_i - n2 * cos_t) / (cos_i + n2 * cos_t)
+    amp = lambda L: math.sqrt(2 * ETA0) * lam / (4 * math.pi * L)
+    E_exp = amp(d) * np.exp(-1j * k * d) + Rte * amp(L_img) * np.exp(-1j * k * L_img)
+    assert abs(f["E0"][0] - E_exp) < 1e-12 * abs(E_exp)
+
+
+def test_image_method_finite_wall_brute_force():
+    """A 1x1 m wall: the image-method path is valid iff the Fermat point lies inside the wall."""
+    mb = S._MeshBuilder()
+    mb.quad((0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), 0)
+    w = _free()
+    w.scene = mb.scene([(5.3, 0.0)])
+    o = O.Oracle(w)
+    rng = np.random.default_rng(1)
+    n_valid = 0
+    for _ in range(200):
+        T = np.array([rng.uniform(-1, 2), rng.uniform(-1, 2), rng.uniform(0.2, 2)], np.float32).astype(np.float64)
+        R = np.array([rng.uniform(-1, 2), rng.uniform(-1, 2), rng.uniform(0.2, 2)], np.float32).astype(np.float64)
+        ok, amb, pts = o.validate(T, -1, R, -1, 0)
+        res = minimize(lambda p: np.linalg.norm(np.array([p[0], p[1], 0]) - T) + np.linalg.norm(R - np.array([p[0], p[1], 0])),
+                       x0=[0.5, 0.5], method="Nelder-Mead", options=dict(xatol=1e-11, fatol=1e-13, maxiter=20000))
+        inside = 0 <= res.x[0] <= 1 and 0 <= res.x[1] <= 1
+        margin = min(res.x[0], 1 - res.x[0], res.x[1], 1 - res.x[1])
+        if abs(margin) > 1e-6:
+            assert ok == inside
+            n_valid += ok
+    assert n_valid > 20
+
+
+def test_two_parallel_planes_order2_lengths():
+    """Floor z=0 and ceiling z=H: second-order unfolded lengths sqrt(rho^2 + (2H +- (a - b))^2)."""
+    H = 3.0
+    w = _free()
+    w.scene = _plane_scene(0.0, 50.0, extra_planes=(H,))
+    o = O.Oracle(w)
+    T = np.array([0.2, -1.0, 1.1], np.float32).astype(np.float64)
+    R = np.array([2.5, 1.7, 2.2], np.float32).astype(np.float64)
+    a, b = T[2], R[2]
+    rho = np.linalg.norm((R - T)[:2])
+    for (f1, f2), dz in [((0, 1), 2 * H + a - b), ((1, 0), 2 * H - a + b)]:
+        ok, amb, pts = o.validate(T, -1, R, -1, o.seq_id(f1, f2))
+        assert ok and not amb
+        L = sum(np.linalg.norm(pts[i + 1] - pts[i]) for i in range(3))
+        assert abs(L - math.hypot(rho, dz)) < 1e-12
+
+
+def test_occlusion_unit_box():
+    mb = S._MeshBuilder()
+    mb.box((0, 0, 0), (1, 1, 1), 0)
+    w = _free()
+    w.scene = mb.scene([(3.0, 0.0)])
+    o = O.Oracle(w)
+    assert o.segment_blocked((-1, 0.5, 0.5), (2, 0.5, 0.5)) == (True, False)
+    assert o.segment_blocked((-1, 1.5, 0.5), (2, 1.5, 0.5)) == (False, False)
+    assert o.segment_blocked((-1, 0.3, 0.4), (2, 0.6, 0.7)) == (True, False)
+    # through two opposite corners only: both hits sit on vertices, so the decision is ambiguous
+    assert o.segment_blocked((-1, -1, -1), (2, 2, 2))[1]
+    # a segment ending exactly on a face is not blocked by that face when the face is ignored
+    assert o.segment_blocked((-1, 0.5, 0.5), (0, 0.5, 0.5), -1, 0) == (False, False)
+    # grazing an edge is ambiguous
+    blocked, amb = o.segment_blocked((-1, 1.0, 0.5), (2, 1.0, 0.5))
+    assert amb
+
+
+# ------------------------------------------------------------------------------------------------
+# T7: reciprocity
+# ------------------------------------------------------------------------------------------------
+def test_reciprocity_room():
+    w = S.room(grid=4)
+    rng = np.random.default_rng(3)
+    g = np.exp(2j * np.pi * rng.random(w.n_elem))
+    a = np.array([3.0, 0.5, 2.5], np.float32)
+    b = np.array([4.1, 2.9, 1.2], np.float32)
+    w.tx.pos = a
+    Ea, _, _ = O.Oracle.evaluate(O.Oracle(w).field(b[None]), g)
+    w.tx.pos = b
+    Eb, _, _ = O.Oracle.evaluate(O.Oracle(w).field(a[None]), g)
+    assert abs(Ea[0]) > 0
+    assert abs(Ea[0] - Eb[0]) < 1e-12 * abs(Ea[0])
+
+
+# ------------------------------------------------------------------------------------------------
+# T8: coordinate conventions and the paper's printed numbers
+# ------------------------------------------------------------------------------------------------
+def test_paper_coordinates():
+    g = json.load(open(os.path.join(GOLD, "paper_coordinates.json")))
+    u = g["ris_centre"]
+    tol = g["printed_precision_m"] / 2 + 1e-3
+    t = S.spherical_to_cartesian(u, **{k: g["tx_spherical"][k] for k in ("r",)},
+                                 phi_deg=g["tx_spherical"]["phi_deg"], theta_deg=g["tx_spherical"]["theta_deg"])
+    r = S.spherical_to_cartesian(u, g["rx_spherical"]["r"], g["rx_spherical"]["phi_deg"], g["rx_spherical"]["theta_deg"])
+    assert np.allclose(t, g["tx_cartesian_fig3"], atol=0.05)
+    assert np.allclose(r, g["rx_cartesian_fig3"], atol=tol)
+    assert abs(r[2] - g["rx_grid_height_m"]) < 1e-3
+
+
+def test_element_frame():
+    """Elements lie at c + a t1 + b t2 (hex grid in the yz plane for the paper's RIS, Fig. 1)."""
+    w = S.paper_anechoic()
+    o = O.Oracle(w)
+    e = o.element_positions()
+    assert np.allclose(e[:, 0], 0.0)
+    assert np.allclose(e.mean(0), w.ris.center, atol=1e-7)
+    assert len(e) == 127
+
+
+def test_paper_beam_level():
+    """Anechoic Table-1 set-up with an on/off configuration that switches on the elements whose
+    contribution at the intended Rx points within 90 degrees of a common phase (the best of 64
+    offsets): the Rx power must fall in the paper's simulated beam level (Sec. IV-B)."""
+    g = json.load(open(os.path.join(GOLD, "paper_levels.json")))
+    w = S.paper_anechoic()
+    o = O.Oracle(w)
+    rx = np.asarray(g["intended_rx"], np.float32)[None]
+    f = o.field(rx)
+    A = f["A"][0]
+    best = -1
+    for psi in np.linspace(0, 2 * math.pi, 64, endpoint=False):
+        on = np.cos(np.angle(A) - psi) > 0
+        gamma = np.where(on, 1.25, 0.0)
+        _, P, _ = O.Oracle.evaluate(f, gamma)
+        best = max(best, P[0])
+    dbm = 10 * math.log10(best) + 30
+    assert g["beam_dbm_low"] - g["slack_db"] <= dbm <= g["beam_dbm_high"] + g["slack_db"]
+
+
+def test_ris_legs_with_one_wall_image_closed_form():
+    """RIS at the origin facing +z, one large wall x = 1 (eps 5.3). Each element sees the Tx directly
+    and through the wall, and reaches the Rx directly and through the wall; by the image method the
+    channel coefficient is the Cartesian sum of four Tang22-type terms with mirrored endpoints and a
+    Fresnel factor (Snell form) per bounce (Sec. II-B)."""
+    mb = S._MeshBuilder()
+    h = 40.0
+    mb.quad((1.0, -h, -h), (1.0, h, -h), (1.0, h, h), (1.0, -h, h), 0)
+    w = _free()
+    w.scene = mb.scene([(5.3, 0.0)])
+    w.max_order_tx = 1
+    w.max_order_rx = 1
+    o = O.Oracle(w)
+    R = np.array([0.3, 0.2, 1.5], np.float32).astype(np.float64)
+    A = o.field(R.astype(np.float32)[None])["A"][0]
+    lam = S.C0 / w.freq_hz
+    k = 2 * math.pi / lam
+    e = o.element_positions()
+    T = w.tx.pos.astype(np.float64)
+    mir = lambda p: np.array([2.0 - p[0], p[1], p[2]])
+    n2 = math.sqrt(float(np.float32(5.3)))
+
+    def fres(cos_i):
+        sin_i = math.sqrt(max(0.0, 1 - cos_i ** 2))
+        cos_t = math.sqrt(1 - (sin_i / n2) ** 2)
+        return (cos_i - n2 * cos_t) / (cos_i + n2 * cos_t)
+
+    d = float(np.float32(w.ris.dy))
+    G = 4 * math.pi * d * d / lam ** 2
+    exp = np.zeros(len(e), complex)
+    for m in range(len(e)):
+        for Ts, tref in ((T, False), (mir(T), True)):
+            for Rs, rref in ((R, False), (mir(R), True)):
+                rt = np.linalg.norm(e[m] - Ts)
+                rr = np.linalg.norm(Rs - e[m])
+                cin = (Ts - e[m])[2] / rt
+                cout = (Rs - e[m])[2] / rr
+                amp = math.sqrt(2 * ETA0) * math.sqrt(G * cin * cout * d * d / (4 * math.pi)) / rt * lam / (4 * math.pi * rr)
+                f = 1.0
+                if tref:
+                    f *= fres(abs((e[m] - Ts)[0]) / rt)
+                if rref:
+                    f *= fres(abs((Rs - e[m])[0]) / rr)
+                exp[m] += amp * f * np.exp(-1j * k * (rt + rr))
+    assert np.max(np.abs(A - exp)) < 1e-12 * np.max(np.abs(exp))
