@@ -1,0 +1,212 @@
+/*
+ * risrt — GB300-native RIS ray-tracing field engine (C ABI).
+ *
+ * Implements the data-parallel hot path of "Ray Tracing Algorithm for Reconfigurable Intelligent
+ * Surfaces" (Sandh et al., arXiv 2402.13034): for every receiver (Rx) point, the complex field summed
+ * over every RIS element and every propagation path, with the paper's RIS path-loss model
+ * (Sec. II-A, Eqs. 4-10) and specular wall reflections on the Tx->RIS and RIS->Rx legs found by
+ * BVH ray-triangle traversal and the image method (Sec. II-B, Fig. 2).
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an int status (RISRT_OK = 0 or a RISRT_ERR_* code). No exception,
+ *    longjmp or abort crosses the boundary. risrt_last_error(ctx) returns a message for the last
+ *    failure on that context (valid until the next call on the context).
+ *  - SI units: metres, Hz, W, V/m. Gains are linear. Angles in radians.
+ *  - Pointer arguments whose name ends in _host are host memory; every other array pointer is
+ *    CUDA device memory owned by the caller. Arrays are dense, row-major, with the stated layout.
+ *    complex values are interleaved float pairs (re, im) ("float2"), 8-byte aligned.
+ *  - Work is enqueued asynchronously on the context's stream unless a function says it
+ *    synchronises. Outputs in caller memory are valid once that stream reaches the call's work.
+ *  - Library-owned objects (scene, RIS, Rx set, path set) are opaque handles holding device memory;
+ *    free them with the matching *_destroy. A handle may be used only with the context that
+ *    created it. The context itself must outlive its handles.
+ *  - Functions are not thread-safe on one context; distinct contexts are independent.
+ */
+#ifndef RISRT_H
+#define RISRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct risrt_ctx risrt_ctx;
+typedef struct risrt_scene risrt_scene;
+typedef struct risrt_ris risrt_ris;
+typedef struct risrt_rxset risrt_rxset;
+typedef struct risrt_pathset risrt_pathset;
+
+enum {
+    RISRT_OK = 0,
+    RISRT_ERR_INVALID_ARG = 1, /* a size, pointer, index or value outside its documented range */
+    RISRT_ERR_OOM = 2,         /* device allocation failed */
+    RISRT_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    RISRT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    RISRT_ERR_NOT_READY = 5,   /* an input object is missing (e.g. antenna not set) */
+    RISRT_ERR_CAPACITY = 6     /* a fixed internal capacity would be exceeded */
+};
+
+enum { RISRT_TX = 0, RISRT_RX = 1 };
+
+/* Antenna / radiation patterns F(theta), theta measured from the antenna's local z axis (Sec. II-A). */
+enum {
+    RISRT_PATTERN_ISO = 0,        /* F = 1 */
+    RISRT_PATTERN_COS_POW = 1,    /* F = max(cos theta, 0)^(G/2 - 1), G linear (Sec. III-B, horn) */
+    RISRT_PATTERN_MONOPOLE_QW = 2 /* F = ((cos(pi/2 cos theta) - cos(pi/2)) / sin theta)^2, h = lambda/4
+                                     (Sec. III-B); 0 on the axis */
+};
+
+/* trace flags */
+enum {
+    RISRT_FLAG_ENV_PATHS = 1,  /* add Tx->Rx specular paths without the RIS (order <= max_order_rx) to E0 */
+    RISRT_FLAG_FRESNEL_TM = 2  /* TM (parallel) Fresnel coefficient instead of TE (perpendicular) */
+};
+
+/* ------------------------------------------------------------------------------------------------
+ * Context
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, enqueueing work on `stream` (a cudaStream_t; NULL means
+ * the legacy default stream). Fails with RISRT_ERR_CUDA if the device cannot be used. */
+int risrt_create(risrt_ctx** out, int device, void* stream);
+
+/* Change the stream later calls enqueue on. */
+int risrt_set_stream(risrt_ctx* ctx, void* stream);
+
+/* Synchronise the context's stream and release every device resource of the context. */
+int risrt_destroy(risrt_ctx* ctx);
+
+/* Message describing the last failure on ctx (or on creation when ctx is NULL). Never NULL. */
+const char* risrt_last_error(const risrt_ctx* ctx);
+
+/* ------------------------------------------------------------------------------------------------
+ * Inputs
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Upload a triangle scene and build its bounding-volume hierarchy on the device (LBVH: Morton
+ * codes, radix sort, binary radix tree, bottom-up box refit).
+ *   verts_host   [n_verts][3] float   vertex positions
+ *   tris_host    [n_tris][3]  int32   vertex indices, each in [0, n_verts)
+ *   face_id_host [n_tris]     int32   planar face of each triangle, ids 0..F-1 all used; triangles of
+ *                                     one face must be coplanar. The image method reflects on faces.
+ *   mat_id_host  [n_tris]     int32   material index in [0, n_mat); one material per face
+ *   mats_host    [n_mat][2]   float   (eps_r, sigma [S/m]) per material (Table 1 for metal)
+ * n_tris may be 0 (free space). Synchronises the stream (the face count is validated on the host).
+ * Errors: RISRT_ERR_INVALID_ARG on out-of-range indices or n_mat < 1; RISRT_ERR_OOM. */
+int risrt_scene_upload(risrt_ctx* ctx, const float* verts_host, int64_t n_verts,
+                       const int32_t* tris_host, const int32_t* face_id_host,
+                       const int32_t* mat_id_host, int64_t n_tris,
+                       const float* mats_host, int32_t n_mat, risrt_scene** out);
+
+/* Upload a RIS (Sec. II, Fig. 1): M elements at e_m = center + a_m t1 + b_m t2 with normal
+ * n = t1 x t2 (t1, t2 orthonormal within 1e-5), effective element size dy x dz (A_m = dy dz, Eq. 5),
+ * element gain G (<= 0 selects G = 4 pi dy dz / lambda^2, the reading under which Eqs. 4-10 reduce to
+ * Tang22), element pattern F(theta) = max(cos theta, 0) about n (Sec. III-C).
+ *   elem_uv_host [M][2] float (a_m, b_m).  1 <= M <= 65536.
+ *   host_face: face of the scene the RIS is mounted on (ignored for occlusion of rays leaving or
+ *   reaching an element), or -1. */
+int risrt_ris_upload(risrt_ctx* ctx, const float* elem_uv_host, int32_t M, const float center[3],
+                     const float t1[3], const float t2[3], float dy, float dz, float elem_gain,
+                     int32_t host_face, risrt_ris** out);
+
+/* Set the Tx or Rx antenna (Eq. 4, Eq. 8). orient3x3: rows are the antenna's local x, y, z axes in
+ * global coordinates (theta from the local z axis). pos, power_w: Tx only (pos ignored for the Rx,
+ * whose positions come from the Rx set). gain_lin > 0. */
+int risrt_antenna_set(risrt_ctx* ctx, int which, const float pos[3], const float orient3x3[9],
+                      float power_w, float gain_lin, int pattern);
+
+/* Copy n_rx receiver positions [n_rx][3] float from host memory into a library-owned Rx set.
+ * 1 <= n_rx <= 2^26. */
+int risrt_rx_upload(risrt_ctx* ctx, const float* rx_xyz_host, int64_t n_rx, risrt_rxset** out);
+
+/* Wrap caller-owned device memory [n_rx][3] float as an Rx set without copying. The caller keeps
+ * the memory alive and unchanged until risrt_rxset_destroy. */
+int risrt_rx_bind(risrt_ctx* ctx, const float* rx_xyz, int64_t n_rx, risrt_rxset** out);
+
+/* ------------------------------------------------------------------------------------------------
+ * Path finding (Sec. II-B)
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Find every propagation path for every receiver and keep it resident in a path set:
+ *  - Tx leg: direct Tx->e_m per element with an occlusion ray each (Sec. IV-A), plus reflected face
+ *    sequences of length 1..max_order_tx validated once between the Tx and the RIS centre;
+ *  - Rx leg: direct e_m->Rx per (Rx, element) with an occlusion ray each, plus reflected face
+ *    sequences of length 1..max_order_rx validated once between the RIS centre and each Rx
+ *    (the per-element image method then uses each element's own unfolded geometry);
+ *  - LOS Tx->Rx, and with RISRT_FLAG_ENV_PATHS the Tx->Rx specular paths, summed into E0 (FP64
+ *    phase);
+ *  - per-element Tx-leg coefficients c_m (Eq. 4, Eq. 5, Fresnel per bounce; FP64 phase).
+ * A sequence is a list of faces; consecutive faces may not repeat or be coplanar, and a face whose
+ * plane contains the RIS centre may not be the first Rx-leg or last Tx-leg bounce. A path is valid if
+ * every reflection point lies inside its face (union of the face's triangles, inclusive), its two
+ * neighbours lie strictly on the same side of each reflecting plane, and no triangle (faces at the
+ * segment's ends excluded) is hit between 1e-4 m after a segment's start and 1e-4 m before its end.
+ * Geometric decisions are filtered in FP32 and settled in FP64 when the FP32 margin is too small.
+ * 0 <= max_order_tx, max_order_rx <= 2; order 2 needs F <= 40000 faces. freq_hz > 0.
+ * *inout: NULL to create a new path set, or an existing path set of this context whose buffers are
+ * reused (grown when needed). Synchronises the stream (path counts size the output).
+ * Errors: RISRT_ERR_NOT_READY if the Tx or Rx antenna is unset; RISRT_ERR_INVALID_ARG. */
+int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris,
+                      const risrt_rxset* rxset, double freq_hz, int32_t max_order_tx,
+                      int32_t max_order_rx, uint32_t flags, risrt_pathset** inout);
+
+/* Counts of a path set (host struct). */
+typedef struct {
+    int64_t n_rx;          /* receivers */
+    int32_t M;             /* RIS elements */
+    int32_t n_faces;       /* scene faces */
+    int64_t n_rx_paths;    /* Rx-leg path entries, including one direct entry per receiver */
+    int64_t n_env_paths;   /* Tx->Rx reflected paths (RISRT_FLAG_ENV_PATHS) */
+    int32_t n_tx_paths;    /* valid reflected Tx-leg sequences */
+    int64_t units;         /* field evaluation units: sum over receivers of M x (Rx-leg entries) */
+    int64_t fp64_refines;  /* geometric decisions settled in FP64 in the last trace */
+} risrt_pathset_stats;
+
+int risrt_pathset_stats_get(const risrt_pathset* ps, risrt_pathset_stats* out);
+
+/* Export the path set to host memory for inspection and bit-exact comparison. Sequence ids:
+ * id = f for the single face f; id = F + f1*F + f2 for (f1, f2) in propagation order (for the Rx
+ * leg f1 is the first bounce after the RIS). Any pointer may be NULL to skip it. Synchronises.
+ *   rx_count_host   [n_rx]            int32  reflected Rx-leg sequences per receiver
+ *   rx_seq_host     [n_rx_paths - n_rx] int64 their ids, receiver-major, ascending per receiver
+ *   env_count_host  [n_rx]            int32
+ *   env_seq_host    [n_env_paths]     int64  Tx->Rx reflected ids, receiver-major, ascending
+ *   los_host        [n_rx]            uint8  1 if the Tx->Rx segment is unblocked
+ *   vis_host        [n_rx][ceil(M/32)] uint32 bit m%32 of word m/32: e_m->Rx unblocked
+ *   tx_seq_host     [n_tx_paths]      int64  valid reflected Tx-leg ids, ascending
+ *   tx_vis_host     [M]               uint8  1 if Tx->e_m is unblocked */
+int risrt_pathset_export(const risrt_pathset* ps, int32_t* rx_count_host, int64_t* rx_seq_host,
+                         int32_t* env_count_host, int64_t* env_seq_host, uint8_t* los_host,
+                         uint32_t* vis_host, int64_t* tx_seq_host, uint8_t* tx_vis_host);
+
+/* ------------------------------------------------------------------------------------------------
+ * Field (Eqs. 7-10)
+ * ---------------------------------------------------------------------------------------------- */
+
+/* For n_cfg reflection-coefficient configurations gamma [n_cfg][M] (complex64), the received field
+ * E [n_cfg][n_rx] (complex64) = E0 + sum_m Gamma_m c_m sum_q b_mq (Eq. 9 over every element and
+ * Rx-leg path) and, if P_out is not NULL, P [n_cfg][n_rx] float = |E|^2 / (2 eta0) (Eq. 10).
+ * The phase of each term is 2 pi frac(frac(D0/lambda) + dL/lambda) with D0 in FP64 per (Rx, path)
+ * and the element offset dL = (|u|^2 - 2 u.w)/(L + D0) in FP32. 1 <= n_cfg. */
+int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg,
+                     float* E_out, float* P_out);
+
+/* Dense channel matrix: A [n_rx][M] complex64 with A[r][m] = c_m sum_q b_mq(r), so that
+ * E = E0 + A . Gamma (Eq. 9 is linear in Gamma), and E0 [n_rx] complex64 (may be NULL). */
+int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out);
+
+/* ------------------------------------------------------------------------------------------------
+ * Destruction (each synchronises the context stream first; NULL is accepted)
+ * ---------------------------------------------------------------------------------------------- */
+int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* scene);
+int risrt_ris_destroy(risrt_ctx* ctx, risrt_ris* ris);
+int risrt_rxset_destroy(risrt_ctx* ctx, risrt_rxset* rxset);
+int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RISRT_H */

@@ -19,8 +19,9 @@
  * Paths (Sec. II-B): the direct legs Tx->e_m and e_m->Rx are checked for occlusion per element
  * (one ray per element, Sec. IV-A); reflected legs are found by the image method over sequences
  * of planar faces of length <= 2, validated ONCE between the RIS centre and the Rx (and between
- * the Tx and the RIS centre on the Tx leg); each element then uses its own reflection points,
- * obtained here by explicit back-tracing of its own image chain, without re-validation.
+ * the Tx and the RIS centre on the Tx leg) with explicit reflection points; each element then takes
+ * each accepted sequence through the image method (its own mirrored images, the leg length being
+ * the image-to-destination distance), without re-validation.
  * Fresnel reflection (Collin) is applied at every bounce with eps_c = eps_r - j sigma/(omega eps0).
  *
  * Readings of points the paper leaves open (scalar field, e^{+j omega t} convention, element gain
@@ -387,25 +388,6 @@ static int validate_seq(const or_ctx* C, v3 src, int src_face, v3 dst, int dst_f
     return 1;
 }
 
-/* Reflection points of the image chain src -> seq -> dst without any validity test
-   (per-element geometry of an already validated sequence). */
-static void trace_points(const or_ctx* C, v3 src, v3 dst, const int* seq, int k, v3* pts)
-{
-    v3 img[3];
-    img[0] = src;
-    for (int j = 1; j <= k; ++j) img[j] = mirror(C, img[j - 1], seq[j - 1]);
-    pts[0] = src;
-    pts[k + 1] = dst;
-    v3 y = dst;
-    for (int j = k; j >= 1; --j) {
-        int f = seq[j - 1];
-        v3 d = sub(img[j], y);
-        double t = (C->fd[f] - dot(C->fn[f], y)) / dot(C->fn[f], d);
-        pts[j] = add(y, scl(d, t));
-        y = pts[j];
-    }
-}
-
 /* Sequence enumeration: id f for (f); id F + f1*F + f2 for (f1, f2). Consecutive faces must not
    share a plane. first_excl / last_excl: faces whose plane contains the RIS centre may not be the
    first (Rx leg) or last (Tx leg) bounce. */
@@ -514,19 +496,31 @@ typedef struct {
     double complex R;    /* product of Fresnel coefficients */
 } leg_t;
 
-static leg_t leg_from_points(const or_ctx* C, const v3* pts, const int* seq, int k)
+/* A leg by the image method (Sec. II-B): the source is mirrored across the faces of the sequence
+   in propagation order; the leg length is the distance from the last image to the destination, and
+   the direction of every real segment follows from the straight unfolded line by undoing the
+   mirrors one face at a time (last face first). For a sequence validated at the RIS centre this is
+   applied to every element as is, whether or not that element's own reflection points fall inside
+   the segment (the element is not re-validated). */
+static leg_t leg_by_images(const or_ctx* C, v3 src, v3 dst, const int* seq, int k)
 {
     leg_t g;
-    g.L = 0.0;
-    g.R = 1.0;
-    for (int j = 0; j <= k; ++j) g.L += norm(sub(pts[j + 1], pts[j]));
-    g.dep = unit(sub(pts[1], pts[0]));
-    g.arr_back = unit(sub(pts[k], pts[k + 1]));
-    for (int j = 1; j <= k; ++j) {
-        v3 din = unit(sub(pts[j], pts[j - 1]));
-        double cos_i = fabs(dot(din, C->fn[seq[j - 1]]));
-        g.R *= fresnel_c(C, cos_i, seq[j - 1]);
+    v3 img = src;
+    for (int j = 0; j < k; ++j) img = mirror(C, img, seq[j]);
+    v3 d = sub(dst, img);
+    g.L = norm(d);
+    d = scl(d, 1.0 / g.L);
+    v3 dir[3];                 /* dir[j]: direction of real segment j (0 = leaving the source) */
+    dir[k] = d;
+    for (int j = k; j >= 1; --j) {
+        v3 n = C->fn[seq[j - 1]];
+        dir[j - 1] = sub(dir[j], scl(n, 2.0 * dot(n, dir[j])));
     }
+    g.dep = dir[0];
+    g.arr_back = scl(dir[k], -1.0);
+    g.R = 1.0;
+    for (int j = 1; j <= k; ++j)
+        g.R *= fresnel_c(C, fabs(dot(dir[j - 1], C->fn[seq[j - 1]])), seq[j - 1]);
     return g;
 }
 
@@ -580,8 +574,7 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
         double s0 = 0.0;
         /* LOS (Friis form of Eq. 4 + Eq. 8) */
         if (!blocked_decision(C, C->tx, r, -1, -1, &amb)) {
-            v3 pts[2] = {C->tx, r};
-            leg_t g = leg_from_points(C, pts, NULL, 0);
+            leg_t g = leg_by_images(C, C->tx, r, NULL, 0);
             double complex v = direct_term(C, &g);
             e0 += v;
             s0 += cabs(v);
@@ -596,7 +589,7 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
             if (seq_allowed(C, seq, k, 1) && validate_seq(C, C->c, hf, r, -1, seq, k, &amb, pts))
                 rx_ids[n_q++] = id;
             if (C->P.env_paths && seq_allowed(C, seq, k, 2) && validate_seq(C, C->tx, -1, r, -1, seq, k, &amb, pts)) {
-                leg_t g = leg_from_points(C, pts, seq, k);
+                leg_t g = leg_by_images(C, C->tx, r, seq, k);
                 double complex v = direct_term(C, &g);
                 e0 += v;
                 s0 += cabs(v);
@@ -607,27 +600,21 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
             double sa = 0.0;
             int rx_direct = !blocked_decision(C, C->e[m], r, hf, -1, &amb);
             for (int64_t p = -1; p < n_tx; ++p) {           /* p = -1: direct Tx -> e_m */
-                v3 tp[4];
                 int tseq[2], tk = 0;
                 if (p < 0) {
                     if (!tx_vis[m]) continue;
-                    tp[0] = C->tx; tp[1] = C->e[m];
                 } else {
                     tk = decode_seq(C, tx_ids[p], tseq);
-                    trace_points(C, C->tx, C->e[m], tseq, tk, tp);
                 }
-                leg_t gt = leg_from_points(C, tp, tseq, tk);
+                leg_t gt = leg_by_images(C, C->tx, C->e[m], tseq, tk);
                 for (int q = -1; q < n_q; ++q) {           /* q = -1: direct e_m -> Rx */
-                    v3 rp[4];
                     int rseq[2], rk = 0;
                     if (q < 0) {
                         if (!rx_direct) continue;
-                        rp[0] = C->e[m]; rp[1] = r;
                     } else {
                         rk = decode_seq(C, rx_ids[q], rseq);
-                        trace_points(C, C->e[m], r, rseq, rk, rp);
                     }
-                    leg_t gr = leg_from_points(C, rp, rseq, rk);
+                    leg_t gr = leg_by_images(C, C->e[m], r, rseq, rk);
                     double complex v = ris_term(C, &gt, &gr);
                     a += v;
                     sa += cabs(v);

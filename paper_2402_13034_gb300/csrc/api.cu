@@ -1,0 +1,397 @@
+// C ABI of the risrt library: argument validation, object lifetime and dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace risrt {
+
+static thread_local std::string g_create_err;
+
+int fail(risrt_ctx* ctx, int code, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+int cuda_fail(risrt_ctx* ctx, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? RISRT_ERR_OOM : RISRT_ERR_CUDA, m);
+}
+
+}  // namespace risrt
+
+using namespace risrt;
+
+namespace {
+
+int set_device(risrt_ctx* ctx)
+{
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return RISRT_OK;
+}
+
+#define RISRT_CHECK_CTX(ctx)                                   \
+    do {                                                       \
+        if (!(ctx)) return fail(nullptr, RISRT_ERR_INVALID_ARG, "null context"); \
+        int _rc = set_device(ctx);                             \
+        if (_rc) return _rc;                                   \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int risrt_create(risrt_ctx** out, int device, void* stream)
+{
+    if (!out) return fail(nullptr, RISRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(nullptr, RISRT_ERR_INVALID_ARG, "device index out of range");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    risrt_ctx* c = new (std::nothrow) risrt_ctx();
+    if (!c) return fail(nullptr, RISRT_ERR_OOM, "host allocation failed");
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return RISRT_OK;
+}
+
+int risrt_set_stream(risrt_ctx* ctx, void* stream)
+{
+    if (!ctx) return fail(nullptr, RISRT_ERR_INVALID_ARG, "null context");
+    ctx->stream = (cudaStream_t)stream;
+    return RISRT_OK;
+}
+
+int risrt_destroy(risrt_ctx* ctx)
+{
+    if (!ctx) return RISRT_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return RISRT_OK;
+}
+
+const char* risrt_last_error(const risrt_ctx* ctx)
+{
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+int risrt_scene_upload(risrt_ctx* ctx, const float* verts_host, int64_t n_verts, const int32_t* tris_host,
+                       const int32_t* face_id_host, const int32_t* mat_id_host, int64_t n_tris,
+                       const float* mats_host, int32_t n_mat, risrt_scene** out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, RISRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_tris < 0 || n_verts < 0 || n_mat < 1 || !mats_host) return fail(ctx, RISRT_ERR_INVALID_ARG, "bad sizes");
+    if (n_tris > (int64_t)1 << 26) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_tris above 2^26");
+    if (n_tris > 0 && (!verts_host || !tris_host || !face_id_host || !mat_id_host))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL scene array");
+    int F = 0;
+    for (int64_t t = 0; t < n_tris; ++t) {
+        for (int j = 0; j < 3; ++j)
+            if (tris_host[3 * t + j] < 0 || tris_host[3 * t + j] >= n_verts)
+                return fail(ctx, RISRT_ERR_INVALID_ARG, "triangle vertex index out of range");
+        if (face_id_host[t] < 0) return fail(ctx, RISRT_ERR_INVALID_ARG, "negative face id");
+        if (mat_id_host[t] < 0 || mat_id_host[t] >= n_mat) return fail(ctx, RISRT_ERR_INVALID_ARG, "material index out of range");
+        F = std::max(F, face_id_host[t] + 1);
+    }
+    std::vector<char> used(F, 0);
+    for (int64_t t = 0; t < n_tris; ++t) used[face_id_host[t]] = 1;
+    for (int f = 0; f < F; ++f)
+        if (!used[f]) return fail(ctx, RISRT_ERR_INVALID_ARG, "face ids must be 0..F-1 without gaps");
+    for (int64_t i = 0; i < 3 * n_verts; ++i)
+        if (!std::isfinite(verts_host[i])) return fail(ctx, RISRT_ERR_INVALID_ARG, "non-finite vertex");
+    for (int i = 0; i < n_mat; ++i)
+        if (!(mats_host[2 * i] >= 1.0f) || !(mats_host[2 * i + 1] >= 0.0f))
+            return fail(ctx, RISRT_ERR_INVALID_ARG, "material needs eps_r >= 1 and sigma >= 0");
+    risrt_scene* sc = new (std::nothrow) risrt_scene();
+    if (!sc) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    sc->n_tris = n_tris;
+    sc->n_faces = F;
+    int rc = build_scene(ctx, sc, verts_host, n_verts, tris_host, face_id_host, mat_id_host, mats_host, n_mat);
+    if (rc) {
+        risrt_scene_destroy(ctx, sc);
+        return rc;
+    }
+    *out = sc;
+    return RISRT_OK;
+}
+
+int risrt_ris_upload(risrt_ctx* ctx, const float* elem_uv_host, int32_t M, const float center[3], const float t1[3],
+                     const float t2[3], float dy, float dz, float elem_gain, int32_t host_face, risrt_ris** out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, RISRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (M < 1 || M > 65536 || !elem_uv_host || !center || !t1 || !t2)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "RIS needs 1 <= M <= 65536 and non-NULL arrays");
+    if (!(dy > 0.f) || !(dz > 0.f)) return fail(ctx, RISRT_ERR_INVALID_ARG, "element size must be positive");
+    double n1 = 0, n2 = 0, d12 = 0;
+    for (int k = 0; k < 3; ++k) {
+        n1 += (double)t1[k] * t1[k];
+        n2 += (double)t2[k] * t2[k];
+        d12 += (double)t1[k] * t2[k];
+    }
+    if (std::fabs(n1 - 1) > 1e-5 || std::fabs(n2 - 1) > 1e-5 || std::fabs(d12) > 1e-5)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "t1, t2 must be orthonormal");
+    risrt_ris* r = new (std::nothrow) risrt_ris();
+    if (!r) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    r->M = M;
+    memcpy(r->center, center, sizeof(float) * 3);
+    memcpy(r->t1, t1, sizeof(float) * 3);
+    memcpy(r->t2, t2, sizeof(float) * 3);
+    r->dy = dy;
+    r->dz = dz;
+    r->elem_gain = elem_gain;
+    r->host_face = host_face;
+    r->uv_host.assign(elem_uv_host, elem_uv_host + 2 * (size_t)M);
+    std::vector<float4> e(M);
+    for (int m = 0; m < M; ++m) {
+        float a = elem_uv_host[2 * m], b = elem_uv_host[2 * m + 1];
+        if (!std::isfinite(a) || !std::isfinite(b)) {
+            delete r;
+            return fail(ctx, RISRT_ERR_INVALID_ARG, "non-finite element coordinate");
+        }
+        e[m] = make_float4(a, b, a * a + b * b, 0.f);
+    }
+    cudaError_t err = cudaMalloc(&r->elem, sizeof(float4) * M);
+    if (err != cudaSuccess) {
+        delete r;
+        return cuda_fail(ctx, err, "cudaMalloc");
+    }
+    err = cudaMemcpyAsync(r->elem, e.data(), sizeof(float4) * M, cudaMemcpyHostToDevice, ctx->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+    if (err != cudaSuccess) {
+        cudaFree(r->elem);
+        delete r;
+        return cuda_fail(ctx, err, "element upload");
+    }
+    *out = r;
+    return RISRT_OK;
+}
+
+int risrt_antenna_set(risrt_ctx* ctx, int which, const float pos[3], const float orient3x3[9], float power_w,
+                      float gain_lin, int pattern)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (which != RISRT_TX && which != RISRT_RX) return fail(ctx, RISRT_ERR_INVALID_ARG, "which must be RISRT_TX or RISRT_RX");
+    if (!orient3x3) return fail(ctx, RISRT_ERR_INVALID_ARG, "orientation is NULL");
+    if (pattern < RISRT_PATTERN_ISO || pattern > RISRT_PATTERN_MONOPOLE_QW) return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown pattern");
+    if (!(gain_lin > 0.f)) return fail(ctx, RISRT_ERR_INVALID_ARG, "gain must be positive");
+    double zn = 0;
+    for (int k = 6; k < 9; ++k) zn += (double)orient3x3[k] * orient3x3[k];
+    if (!(zn > 0)) return fail(ctx, RISRT_ERR_INVALID_ARG, "orientation z axis is zero");
+    Antenna a{};
+    if (which == RISRT_TX) {
+        if (!pos) return fail(ctx, RISRT_ERR_INVALID_ARG, "Tx position is NULL");
+        if (!(power_w >= 0.f)) return fail(ctx, RISRT_ERR_INVALID_ARG, "power must be >= 0");
+        memcpy(a.pos, pos, sizeof(float) * 3);
+    }
+    memcpy(a.orient, orient3x3, sizeof(float) * 9);
+    a.power_w = power_w;
+    a.gain_lin = gain_lin;
+    a.pattern = pattern;
+    a.set = true;
+    if (which == RISRT_TX) ctx->tx = a;
+    else ctx->rx = a;
+    return RISRT_OK;
+}
+
+int risrt_rx_upload(risrt_ctx* ctx, const float* rx_xyz_host, int64_t n_rx, risrt_rxset** out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, RISRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || !rx_xyz_host) return fail(ctx, RISRT_ERR_INVALID_ARG, "need 1 <= n_rx <= 2^26");
+    risrt_rxset* r = new (std::nothrow) risrt_rxset();
+    if (!r) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    r->n = n_rx;
+    r->owned = true;
+    cudaError_t e = cudaMalloc(&r->xyz, sizeof(float) * 3 * n_rx);
+    if (e != cudaSuccess) {
+        delete r;
+        return cuda_fail(ctx, e, "cudaMalloc");
+    }
+    e = cudaMemcpyAsync(r->xyz, rx_xyz_host, sizeof(float) * 3 * n_rx, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(r->xyz);
+        delete r;
+        return cuda_fail(ctx, e, "cudaMemcpyAsync");
+    }
+    *out = r;
+    return RISRT_OK;
+}
+
+int risrt_rx_bind(risrt_ctx* ctx, const float* rx_xyz, int64_t n_rx, risrt_rxset** out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, RISRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || !rx_xyz) return fail(ctx, RISRT_ERR_INVALID_ARG, "need 1 <= n_rx <= 2^26");
+    risrt_rxset* r = new (std::nothrow) risrt_rxset();
+    if (!r) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    r->n = n_rx;
+    r->xyz = const_cast<float*>(rx_xyz);
+    r->owned = false;
+    *out = r;
+    return RISRT_OK;
+}
+
+int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris, const risrt_rxset* rxset,
+                      double freq_hz, int32_t max_order_tx, int32_t max_order_rx, uint32_t flags, risrt_pathset** inout)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!scene || !ris || !rxset || !inout) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->tx.set || !ctx->rx.set) return fail(ctx, RISRT_ERR_NOT_READY, "Tx and Rx antennas must be set");
+    if (!(freq_hz > 0) || !std::isfinite(freq_hz)) return fail(ctx, RISRT_ERR_INVALID_ARG, "frequency must be positive");
+    if (max_order_tx < 0 || max_order_tx > 2 || max_order_rx < 0 || max_order_rx > 2)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "orders must be in [0, 2]");
+    if ((max_order_tx == 2 || max_order_rx == 2) && scene->n_faces > 40000)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "order 2 supports at most 40000 faces");
+    if (ris->host_face >= scene->n_faces) return fail(ctx, RISRT_ERR_INVALID_ARG, "host_face out of range");
+    if (flags & ~(uint32_t)(RISRT_FLAG_ENV_PATHS | RISRT_FLAG_FRESNEL_TM)) return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown flag");
+    risrt_pathset* ps = *inout;
+    bool created = false;
+    if (!ps) {
+        ps = new (std::nothrow) risrt_pathset();
+        if (!ps) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+        created = true;
+    }
+    int rc = trace_paths(ctx, scene, ris, rxset, freq_hz, max_order_tx, max_order_rx, flags, ps);
+    if (rc) {
+        if (created) risrt_pathset_destroy(ctx, ps);
+        return rc;
+    }
+    *inout = ps;
+    return RISRT_OK;
+}
+
+int risrt_pathset_stats_get(const risrt_pathset* ps, risrt_pathset_stats* out)
+{
+    if (!ps || !out) return RISRT_ERR_INVALID_ARG;
+    out->n_rx = ps->n_rx;
+    out->M = ps->M;
+    out->n_faces = ps->n_faces;
+    out->n_rx_paths = ps->n_paths;
+    out->n_env_paths = ps->n_env;
+    out->n_tx_paths = (int32_t)ps->tx_seq_host.size();
+    out->units = ps->units;
+    out->fp64_refines = ps->fp64_refines;
+    return RISRT_OK;
+}
+
+int risrt_pathset_export(const risrt_pathset* ps, int32_t* rx_count_host, int64_t* rx_seq_host, int32_t* env_count_host,
+                         int64_t* env_seq_host, uint8_t* los_host, uint32_t* vis_host, int64_t* tx_seq_host,
+                         uint8_t* tx_vis_host)
+{
+    if (!ps) return RISRT_ERR_INVALID_ARG;
+    const int64_t n = ps->n_rx;
+    std::vector<int64_t> off(n + 1), eoff(n + 1);
+    if (cudaMemcpy(off.data(), ps->rx_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+    if (cudaMemcpy(eoff.data(), ps->env_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+    if (rx_count_host)
+        for (int64_t r = 0; r < n; ++r) rx_count_host[r] = (int32_t)(off[r + 1] - off[r] - 1);
+    if (rx_seq_host && ps->n_paths > 0) {
+        std::vector<int64_t> all(ps->n_paths);
+        if (cudaMemcpy(all.data(), ps->rx_seq, sizeof(int64_t) * ps->n_paths, cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+        int64_t k = 0;
+        for (int64_t r = 0; r < n; ++r)
+            for (int64_t i = off[r] + 1; i < off[r + 1]; ++i) rx_seq_host[k++] = all[i];
+    }
+    if (env_count_host)
+        for (int64_t r = 0; r < n; ++r) env_count_host[r] = (int32_t)(eoff[r + 1] - eoff[r]);
+    if (env_seq_host && ps->n_env > 0)
+        if (cudaMemcpy(env_seq_host, ps->env_seq, sizeof(int64_t) * ps->n_env, cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+    if (los_host)
+        if (cudaMemcpy(los_host, ps->los, n, cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+    if (vis_host)
+        if (cudaMemcpy(vis_host, ps->vis, sizeof(uint32_t) * n * ps->W, cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+    if (tx_seq_host)
+        for (size_t i = 0; i < ps->tx_seq_host.size(); ++i) tx_seq_host[i] = ps->tx_seq_host[i];
+    if (tx_vis_host)
+        for (int m = 0; m < ps->M; ++m) tx_vis_host[m] = ps->tx_vis_host[m];
+    return RISRT_OK;
+}
+
+int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg, float* E_out, float* P_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!ps || !gamma || !E_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (n_cfg < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_cfg must be >= 1");
+    if (((uintptr_t)gamma | (uintptr_t)E_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    return eval_field(ctx, ps, (const float2*)gamma, n_cfg, (float2*)E_out, P_out);
+}
+
+int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!ps || !A_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (((uintptr_t)A_out | (uintptr_t)E0_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    return build_A(ctx, ps, (float2*)A_out, (float2*)E0_out);
+}
+
+int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
+{
+    if (!sc) return RISRT_OK;
+    if (ctx) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(sc->nodes); cudaFree(sc->tri_geom); cudaFree(sc->tri_verts); cudaFree(sc->tri_face);
+    cudaFree(sc->faces); cudaFree(sc->face_tris); cudaFree(sc->mats);
+    delete sc;
+    return RISRT_OK;
+}
+
+int risrt_ris_destroy(risrt_ctx* ctx, risrt_ris* r)
+{
+    if (!r) return RISRT_OK;
+    if (ctx) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(r->elem);
+    delete r;
+    return RISRT_OK;
+}
+
+int risrt_rxset_destroy(risrt_ctx* ctx, risrt_rxset* r)
+{
+    if (!r) return RISRT_OK;
+    if (ctx) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    if (r->owned) cudaFree(r->xyz);
+    delete r;
+    return RISRT_OK;
+}
+
+int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps)
+{
+    if (!ps) return RISRT_OK;
+    if (ctx) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(ps->rec); cudaFree(ps->rx_off); cudaFree(ps->vis); cudaFree(ps->E0); cudaFree(ps->cm);
+    cudaFree(ps->elem); cudaFree(ps->rx_seq); cudaFree(ps->env_seq); cudaFree(ps->env_off); cudaFree(ps->los);
+    cudaFree(ps->scratch);
+    delete ps;
+    return RISRT_OK;
+}
+
+}  // extern "C"

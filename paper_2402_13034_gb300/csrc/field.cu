@@ -1,0 +1,254 @@
+// Field accumulation (Eqs. 7-10): for every receiver, E = E0 + sum_m Gamma_m c_m sum_q b_mq with the
+// Rx-leg term of element m on path q
+//   b_mq = sqrt(F(theta_out)) R_q sqrt(Gr Fr(theta_r)) e^{-j k L} / L        (Eq. 7 F_out, Eq. 8)
+// evaluated in the RIS frame from the unfolded receiver image I_q: w = I_q - c, L = |w - u_m|,
+// cos(theta_out) = (w - u_m).n / L, per-bounce cos(theta_i) = |(w - u_m).n'_j| / L, and the phase
+// 2 pi frac(frac(D0/lambda) + dL/lambda) with D0 = |w| from FP64 and dL = (|u|^2 - 2 u.w)/(L + D0).
+#include "internal.cuh"
+
+namespace risrt {
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+struct cf { float re, im; };
+__device__ __forceinline__ cf cmulf(cf a, cf b) { return cf{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// principal complex square root in FP32
+__device__ __forceinline__ cf csqrtf_(float x, float y)
+{
+    float r = hypotf(x, y);
+    if (r == 0.f) return cf{0.f, 0.f};
+    if (x >= 0.f) {
+        float s = sqrtf(0.5f * (r + x));
+        return cf{s, y / (2.f * s)};
+    }
+    float s = copysignf(sqrtf(0.5f * (r - x)), y);
+    return cf{y / (2.f * s), s};
+}
+
+// Fresnel coefficient at incidence cos_i for permittivity (er, ei); TE or TM (Collin).
+__device__ __forceinline__ cf fresnel_f(float c, float er, float ei, bool tm)
+{
+    float s2 = fmaxf(1.f - c * c, 0.f);
+    if (!tm && ei == 0.f && er >= s2) {      // lossless dielectric: real coefficient
+        float root = sqrtf(er - s2);
+        return cf{(c - root) / (c + root), 0.f};
+    }
+    cf root = csqrtf_(er - s2, ei);
+    cf a, b;
+    if (!tm) {
+        a = cf{c - root.re, -root.im};
+        b = cf{c + root.re, root.im};
+    } else {
+        a = cf{er * c - root.re, ei * c - root.im};
+        b = cf{er * c + root.re, ei * c + root.im};
+    }
+    float inv = 1.f / (b.re * b.re + b.im * b.im);
+    return cf{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
+}
+
+template <int PAT>
+__device__ __forceinline__ float rx_pattern(float c, float gain)
+{
+    if (PAT == RISRT_PATTERN_COS_POW) return c > 0.f ? __powf(c, 0.5f * gain - 1.f) : 0.f;
+    if (PAT == RISRT_PATTERN_MONOPOLE_QW) {
+        float s2 = 1.f - c * c;
+        if (s2 <= 0.f) return 0.f;
+        float v = cospif(0.5f * c) * rsqrtf(s2);
+        return v * v;
+    }
+    return 1.f;
+}
+
+// b_mq for one (path record, element) pair; returns false if the term is zero by visibility.
+template <int PAT>
+__device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_lam, float gr, bool tm)
+{
+    const float dx = p.w.x - e.x, dy = p.w.y - e.y, dz = p.w.z;
+    const float L2 = dx * dx + dy * dy + dz * dz;
+    const float iL = rsqrtf(L2);
+    const float L = L2 * iL;
+    const float cos_out = dz * iL;
+    float amp = sqrtf(fmaxf(cos_out, 0.f)) * iL;
+    if (PAT != RISRT_PATTERN_ISO) {
+        float cr = -(dx * p.v.x + dy * p.v.y + dz * p.v.z) * iL;
+        amp *= sqrtf(gr * rx_pattern<PAT>(cr, gr));
+    } else {
+        amp *= sqrtf(gr);
+    }
+    cf R = cf{amp, 0.f};
+    const int k = __float_as_int(p.a.y);
+    if (k >= 1) {
+        float c1 = fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) * iL;
+        R = cmulf(R, fresnel_f(c1, p.a.z, p.a.w, tm));
+        if (k == 2) {
+            float c2 = fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) * iL;
+            R = cmulf(R, fresnel_f(c2, p.n1.w, p.n2.w, tm));
+        }
+    }
+    const float dL = (e.z - 2.f * (e.x * p.w.x + e.y * p.w.y)) / (L + p.w.w);
+    float x = p.a.x + dL * inv_lam;
+    x -= rintf(x);
+    float sn, cs;
+    __sincosf(6.28318530717958647f * x, &sn, &cs);
+    return cmulf(R, cf{cs, -sn});          // e^{-j 2 pi x}
+}
+
+constexpr int kEvalWarps = 8;
+constexpr int kMaxCfgPerPass = 4;
+
+// One warp per receiver; lanes walk the flattened (path, element) index space so small arrays keep
+// every lane busy. NC configurations share each b_mq.
+template <int PAT, int NC>
+__global__ void __launch_bounds__(32 * kEvalWarps)
+k_eval(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const uint32_t* __restrict__ vis, int W,
+       const float4* __restrict__ elem, const float2* __restrict__ cm, const float2* __restrict__ gamma,
+       int M, int64_t n_rx, int cfg0, int n_cfg, const float2* __restrict__ E0, float2* __restrict__ E,
+       float* __restrict__ P, float inv_lam, float gr, int tm, float inv_2eta0)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)kEvalWarps + (threadIdx.x >> 5);
+    if (r >= n_rx) return;
+    const int64_t o = off[r];
+    const int64_t total = (off[r + 1] - o) * (int64_t)M;
+    cf acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = cf{0.f, 0.f};
+    int q = lane / M, m = lane % M;
+    for (int64_t idx = lane; idx < total; idx += 32) {
+        const PathRec p = rec[o + q];
+        const int k = __float_as_int(p.a.y);
+        bool on = k > 0 || ((vis[r * W + (m >> 5)] >> (m & 31)) & 1u);
+        if (on) {
+            const float4 e = elem[m];
+            const cf b = rx_leg_term<PAT>(p, e, inv_lam, gr, tm != 0);
+            const float2 c2 = cm[m];
+            const cf cb = cmulf(b, cf{c2.x, c2.y});
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (c < n_cfg) {
+                    const float2 g = gamma[(int64_t)(cfg0 + c) * M + m];
+                    acc[c].re += g.x * cb.re - g.y * cb.im;
+                    acc[c].im += g.x * cb.im + g.y * cb.re;
+                }
+            }
+        }
+        m += 32;
+        while (m >= M) {
+            m -= M;
+            ++q;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            acc[c].re += __shfl_down_sync(0xffffffffu, acc[c].re, s);
+            acc[c].im += __shfl_down_sync(0xffffffffu, acc[c].im, s);
+        }
+    }
+    if (lane == 0) {
+        const float2 e0 = E0[r];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (c < n_cfg) {
+                float er = e0.x + acc[c].re, ei = e0.y + acc[c].im;
+                int64_t oi = (int64_t)(cfg0 + c) * n_rx + r;
+                E[oi] = make_float2(er, ei);
+                if (P) P[oi] = (er * er + ei * ei) * inv_2eta0;
+            }
+        }
+    }
+}
+
+// A[r][m] = c_m sum_q b_mq: one warp per receiver, lanes own elements, paths broadcast.
+template <int PAT>
+__global__ void __launch_bounds__(32 * kEvalWarps)
+k_build_A(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const uint32_t* __restrict__ vis, int W,
+          const float4* __restrict__ elem, const float2* __restrict__ cm, int M, int64_t n_rx,
+          float2* __restrict__ A, float inv_lam, float gr, int tm)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)kEvalWarps + (threadIdx.x >> 5);
+    if (r >= n_rx) return;
+    const int64_t o = off[r];
+    const int nq = (int)(off[r + 1] - o);
+    for (int m0 = 0; m0 < M; m0 += 32) {
+        const int m = m0 + lane;
+        const bool valid = m < M;
+        const float4 e = valid ? elem[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool direct = valid && ((vis[r * W + (m >> 5)] >> (m & 31)) & 1u);
+        cf acc = cf{0.f, 0.f};
+        for (int q = 0; q < nq; ++q) {
+            const PathRec p = rec[o + q];
+            if (!valid || (q == 0 && !direct)) continue;   // entry 0 is the direct path
+            const cf b = rx_leg_term<PAT>(p, e, inv_lam, gr, tm != 0);
+            acc.re += b.re;
+            acc.im += b.im;
+        }
+        if (valid) {
+            const float2 c2 = cm[m];
+            const cf a = cmulf(acc, cf{c2.x, c2.y});
+            A[r * (int64_t)M + m] = make_float2(a.re, a.im);
+        }
+    }
+}
+
+}  // namespace
+
+int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P)
+{
+    const float inv_lam = (float)(ps->freq / kC0);
+    const float inv_2eta0 = (float)(1.0 / (2.0 * kEta0));
+    const int tm = (ps->flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
+    const unsigned grid = nblk(ps->n_rx, kEvalWarps);
+    for (int c0 = 0; c0 < n_cfg; c0 += kMaxCfgPerPass) {
+        const int nc = std::min(kMaxCfgPerPass, n_cfg - c0);
+#define RISRT_EVAL(PAT, NCV)                                                                                  \
+    k_eval<PAT, NCV><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, \
+                                                                ps->cm, gamma, ps->M, ps->n_rx, c0, nc, ps->E0, E, P, \
+                                                                inv_lam, ps->rx_gain, tm, inv_2eta0)
+#define RISRT_EVAL_NC(PAT)           \
+    do {                             \
+        if (nc == 1) RISRT_EVAL(PAT, 1); \
+        else if (nc == 2) RISRT_EVAL(PAT, 2); \
+        else RISRT_EVAL(PAT, 4);     \
+    } while (0)
+        switch (ps->rx_pattern) {
+            case RISRT_PATTERN_COS_POW: RISRT_EVAL_NC(RISRT_PATTERN_COS_POW); break;
+            case RISRT_PATTERN_MONOPOLE_QW: RISRT_EVAL_NC(RISRT_PATTERN_MONOPOLE_QW); break;
+            default: RISRT_EVAL_NC(RISRT_PATTERN_ISO); break;
+        }
+#undef RISRT_EVAL_NC
+#undef RISRT_EVAL
+        RISRT_LAUNCH(ctx, "k_eval");
+    }
+    return RISRT_OK;
+}
+
+int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0)
+{
+    const float inv_lam = (float)(ps->freq / kC0);
+    const int tm = (ps->flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
+    const unsigned grid = nblk(ps->n_rx, kEvalWarps);
+    switch (ps->rx_pattern) {
+        case RISRT_PATTERN_COS_POW:
+            k_build_A<RISRT_PATTERN_COS_POW><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
+                ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, ps->M, ps->n_rx, A, inv_lam, ps->rx_gain, tm);
+            break;
+        case RISRT_PATTERN_MONOPOLE_QW:
+            k_build_A<RISRT_PATTERN_MONOPOLE_QW><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
+                ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, ps->M, ps->n_rx, A, inv_lam, ps->rx_gain, tm);
+            break;
+        default:
+            k_build_A<RISRT_PATTERN_ISO><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
+                ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, ps->M, ps->n_rx, A, inv_lam, ps->rx_gain, tm);
+            break;
+    }
+    RISRT_LAUNCH(ctx, "k_build_A");
+    if (E0) RISRT_CUDA(ctx, cudaMemcpyAsync(E0, ps->E0, sizeof(float2) * ps->n_rx, cudaMemcpyDeviceToDevice, ctx->stream));
+    return RISRT_OK;
+}
+
+}  // namespace risrt

@@ -1,0 +1,281 @@
+// Device geometry: segment occlusion by BVH traversal, point-in-face tests and the image-method
+// back-trace (Sec. II-B). Decisions are filtered in FP32 and settled in FP64 when the FP32 margin
+// does not decide them.
+#pragma once
+
+#include "internal.cuh"
+
+namespace risrt {
+
+struct cd { double re, im; };
+__device__ __forceinline__ cd cmul(cd a, cd b) { return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cd cadd(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cd cdiv(cd a, cd b)
+{
+    double den = b.re * b.re + b.im * b.im;
+    return cd{(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
+}
+// principal square root, numerically stable in both half planes
+__device__ __forceinline__ cd csqrt_d(cd z)
+{
+    double r = hypot(z.re, z.im);
+    if (r == 0.0) return cd{0.0, 0.0};
+    if (z.re >= 0.0) {
+        double s = sqrt(0.5 * (r + z.re));
+        return cd{s, z.im / (2.0 * s)};
+    }
+    double s = copysign(sqrt(0.5 * (r - z.re)), z.im);
+    return cd{z.im / (2.0 * s), s};
+}
+
+// Fresnel coefficient (Collin) for complex permittivity eps at incidence cos_i; TE or TM.
+__device__ __forceinline__ cd fresnel_d(double cos_i, cd eps, bool tm)
+{
+    double s2 = 1.0 - cos_i * cos_i;
+    cd root = csqrt_d(cd{eps.re - s2, eps.im});
+    if (!tm) return cdiv(cd{cos_i - root.re, -root.im}, cd{cos_i + root.re, root.im});
+    cd ec = cd{eps.re * cos_i, eps.im * cos_i};
+    return cdiv(cd{ec.re - root.re, ec.im - root.im}, cd{ec.re + root.re, ec.im + root.im});
+}
+
+// Antenna pattern F(cos theta) in FP64 (Sec. III-B): isotropic, cos^(G/2-1), quarter-wave monopole.
+__device__ __forceinline__ double pattern_d(int pat, double gain, double c)
+{
+    if (pat == RISRT_PATTERN_COS_POW) return c > 0.0 ? pow(c, 0.5 * gain - 1.0) : 0.0;
+    if (pat == RISRT_PATTERN_MONOPOLE_QW) {
+        double s2 = 1.0 - c * c;
+        if (s2 <= 0.0) return 0.0;
+        double v = (cospi(0.5 * c) - cospi(0.5)) / sqrt(s2);
+        return v * v;
+    }
+    return 1.0;
+}
+
+__device__ __forceinline__ d3 ld3(const dv4& p) { return D3(p.x, p.y, p.z); }
+__device__ __forceinline__ d3 ldv(const float4& p) { return D3((double)p.x, (double)p.y, (double)p.z); }
+
+// ------------------------------------------------------------------------------------------------
+// triangle tests
+// ------------------------------------------------------------------------------------------------
+
+// Exact-in-FP64 decision: does segment a + s*dir, s in [0,1] (|dir| = len), hit the triangle at a
+// distance in [kSegEps, len - kSegEps]? Inside is inclusive.
+__device__ __forceinline__ bool tri_hit_fp64(const TriVerts& tv, d3 a, d3 dir, double len)
+{
+    d3 v0 = ldv(tv.v0), v1 = ldv(tv.v1), v2 = ldv(tv.v2);
+    d3 nrm = cross(v1 - v0, v2 - v0);
+    double nn = norm(nrm);
+    double den = dot(nrm, dir);
+    double num = dot(nrm, v0 - a);
+    if (fabs(den) <= 1e-12 * nn * len) return false;
+    double s = num / den;
+    double dist = s * len;
+    if (!(dist >= kSegEpsD && dist <= len - kSegEpsD)) return false;
+    d3 q = a + dir * s;
+    d3 nu = nrm * (1.0 / nn);
+    d3 P[3] = {v0, v1, v2};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        d3 p = P[(i + 1) % 3], r = P[(i + 2) % 3];
+        if (dot(cross(r - p, q - p), nu) < 0.0) return false;
+    }
+    return true;
+}
+
+// FP32 filter: 1 = certainly hit, 0 = certainly not, 2 = too close to call (settle in FP64).
+__device__ __forceinline__ int tri_hit_fp32(const TriGeom& g, float3 a, float3 dir, float len, float tol_base)
+{
+    float3 n = xyz(g.plane);
+    float den = dot(n, dir);
+    float sa = dot(n, a) - g.plane.w;          // signed distance of the start
+    float adn = fabsf(den);
+    if (adn < 1e-3f * len) {                   // nearly parallel to the plane
+        float sb = sa + den;
+        float tol = tol_base;
+        if ((sa > tol && sb > tol) || (sa < -tol && sb < -tol)) return 0;
+        return 2;
+    }
+    float t = -sa / den;
+    float dist = t * len;
+    float tol = tol_base * (len / adn);
+    if (dist < kSegEps - tol || dist > len - kSegEps + tol) return 0;
+    float3 q = a + dir * t;
+    float e0 = dot(xyz(g.edge[0]), q) - g.edge[0].w;
+    float e1 = dot(xyz(g.edge[1]), q) - g.edge[1].w;
+    float e2 = dot(xyz(g.edge[2]), q) - g.edge[2].w;
+    float emin = fminf(e0, fminf(e1, e2));
+    if (emin < -tol) return 0;
+    if (emin > tol && dist > kSegEps + tol && dist < len - kSegEps - tol) return 1;
+    return 2;
+}
+
+// ------------------------------------------------------------------------------------------------
+// segment occlusion (any hit) by stack traversal of the binary BVH
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, float3 a, float3 inv)
+{
+    float tx0 = (lo.x - a.x) * inv.x, tx1 = (hi.x - a.x) * inv.x;
+    float ty0 = (lo.y - a.y) * inv.y, ty1 = (hi.y - a.y) * inv.y;
+    float tz0 = (lo.z - a.z) * inv.z, tz1 = (hi.z - a.z) * inv.z;
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), 1.f));
+    return tmin <= tmax;
+}
+
+__device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d)); }
+
+// Is segment A->B blocked (faces ign0 / ign1 skipped)? `refines` counts FP64 settlements,
+// `err` is set if the traversal stack would overflow (never expected; treated as blocked).
+__device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
+                           unsigned long long* refines, int* err)
+{
+    if (S.root == -1) return false;
+    float3 a = to_f(A), b = to_f(B);
+    float3 dir = b - a;
+    float len = sqrtf(dot(dir, dir));
+    float3 inv = f3(safe_inv(dir.x), safe_inv(dir.y), safe_inv(dir.z));
+    d3 dirD = B - A;
+    double lenD = norm(dirD);
+    float tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
+    int stack[64];
+    int sp = 0;
+    stack[sp++] = S.root;
+    while (sp > 0) {
+        int c = stack[--sp];
+        if (c < 0) {
+            int i = ~c;
+            int f = S.tri_face[i];
+            if (f == ign0 || f == ign1) continue;
+            int r = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
+            if (r == 1) return true;
+            if (r == 2) {
+                if (refines) atomicAdd(refines, 1ull);
+                if (tri_hit_fp64(S.tri_verts[i], A, dirD, lenD)) return true;
+            }
+            continue;
+        }
+        const BvhNode nd = S.nodes[c];
+        bool hl = box_overlap(nd.l_lo, nd.l_hi, a, inv);
+        bool hr = box_overlap(nd.r_lo, nd.r_hi, a, inv);
+        if (sp + 2 > 64) {
+            if (err) atomicExch(err, 1);
+            return true;
+        }
+        if (hr) stack[sp++] = __float_as_int(nd.l_hi.w);
+        if (hl) stack[sp++] = __float_as_int(nd.l_lo.w);
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------------
+// point in face (union of the face's triangles, inclusive)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool in_face_fp64(const DeviceScene& S, int f, d3 q)
+{
+    const Face fc = S.faces[f];
+    for (int j = fc.tri_begin; j < fc.tri_end; ++j) {
+        const TriVerts tv = S.tri_verts[S.face_tris[j]];
+        d3 v0 = ldv(tv.v0), v1 = ldv(tv.v1), v2 = ldv(tv.v2);
+        d3 nrm = cross(v1 - v0, v2 - v0);
+        double nn = norm(nrm);
+        if (nn == 0.0) continue;
+        d3 nu = nrm * (1.0 / nn);
+        if (dot(cross(v2 - v1, q - v1), nu) < 0.0) continue;
+        if (dot(cross(v0 - v2, q - v2), nu) < 0.0) continue;
+        if (dot(cross(v1 - v0, q - v0), nu) < 0.0) continue;
+        return true;
+    }
+    return false;
+}
+
+// FP32 classification: 1 inside, 0 outside, 2 too close to call.
+__device__ __forceinline__ int in_face_fp32(const DeviceScene& S, int f, float3 q, float tol)
+{
+    const Face& fc = S.faces[f];
+    int res = 0;
+    for (int j = fc.tri_begin; j < fc.tri_end; ++j) {
+        const TriGeom& g = S.tri_geom[S.face_tris[j]];
+        float e0 = dot(xyz(g.edge[0]), q) - g.edge[0].w;
+        float e1 = dot(xyz(g.edge[1]), q) - g.edge[1].w;
+        float e2 = dot(xyz(g.edge[2]), q) - g.edge[2].w;
+        float emin = fminf(e0, fminf(e1, e2));
+        if (emin > tol) return 1;
+        if (emin >= -tol) res = 2;
+    }
+    return res;
+}
+
+// ------------------------------------------------------------------------------------------------
+// face sequences
+// ------------------------------------------------------------------------------------------------
+struct SeqEntry {          // FP32 data for the candidate filter
+    float4 sL;             // image of the source across every face of the sequence; w = signed
+                           // distance to the last plane of the previous image (source for order 1)
+    float4 pL;             // plane (n, d) of the last face (next to the destination)
+    float4 s1;             // order 2: image across the first face only; w = signed distance of the
+                           // source to the first plane
+    float4 p1;             // order 2: plane of the first face
+    int4 info;             // (f1, f2 or -1, id, order)
+};
+struct SeqEntryD {         // FP64 images for the settled decision and path points
+    dv4 S1;            // image across the first face
+    dv4 S2;            // order 2: image across both faces
+};
+
+// Full FP64 geometric check of a face sequence between src and dst (reflection points inside
+// their faces, strictly same side at each bounce, back-trace parameter in (0,1)); pts gets
+// src, P_1..P_k, dst.
+__device__ __forceinline__ bool seq_geom_fp64(const DeviceScene& S, d3 src, d3 dst, const int4& info,
+                                              const SeqEntryD& im, d3* pts)
+{
+    const int k = info.w;
+    const int fa[2] = {info.x, info.y};
+    d3 img[3] = {src, ld3(im.S1), ld3(im.S2)};
+    pts[0] = src;
+    pts[k + 1] = dst;
+    d3 y = dst;
+    bool ok = true;
+    for (int j = k; j >= 1; --j) {
+        const dv4 pl = S.faces[fa[j - 1]].plane;
+        d3 n = ld3(pl);
+        d3 d = img[j] - y;
+        double den = dot(n, d);
+        if (den == 0.0) return false;
+        double t = (pl.w - dot(n, y)) / den;
+        d3 p = y + d * t;
+        pts[j] = p;
+        if (!(t > 0.0 && t < 1.0)) ok = false;
+        if (ok && !in_face_fp64(S, fa[j - 1], p)) ok = false;
+        y = p;
+    }
+    if (!ok) return false;
+    for (int j = 1; j <= k; ++j) {
+        const dv4 pl = S.faces[fa[j - 1]].plane;
+        d3 n = ld3(pl);
+        double s1 = dot(n, pts[j - 1]) - pl.w, s2 = dot(n, pts[j + 1]) - pl.w;
+        if (!(s1 * s2 > 0.0)) return false;
+    }
+    return true;
+}
+
+// Back-trace without checks (per-element geometry of an accepted sequence).
+__device__ __forceinline__ void seq_points_fp64(const DeviceScene& S, d3 dst, const int4& info,
+                                                const SeqEntryD& im, d3 src, d3* pts)
+{
+    const int k = info.w;
+    const int fa[2] = {info.x, info.y};
+    d3 img[3] = {src, ld3(im.S1), ld3(im.S2)};
+    pts[0] = src;
+    pts[k + 1] = dst;
+    d3 y = dst;
+    for (int j = k; j >= 1; --j) {
+        const dv4 pl = S.faces[fa[j - 1]].plane;
+        d3 n = ld3(pl);
+        d3 d = img[j] - y;
+        double t = (pl.w - dot(n, y)) / dot(n, d);
+        pts[j] = y + d * t;
+        y = pts[j];
+    }
+}
+
+}  // namespace risrt

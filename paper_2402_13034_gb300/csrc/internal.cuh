@@ -1,0 +1,232 @@
+// Internal declarations of the risrt CUDA library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "risrt.h"
+
+namespace risrt {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kC0 = 299792458.0;          // m/s
+constexpr double kEta0 = 120.0 * kPi;        // Eq. 1: free-space impedance 120 pi ohm
+constexpr double kEps0 = 8.8541878128e-12;   // F/m
+constexpr float kSegEps = 1e-4f;             // occluder hits within this of a segment end are ignored
+constexpr double kSegEpsD = 1e-4;
+
+// ------------------------------------------------------------------------------------------------
+// small vector helpers
+// ------------------------------------------------------------------------------------------------
+struct d3 { double x, y, z; };
+struct __align__(32) dv4 { double x, y, z, w; };
+__host__ __device__ __forceinline__ dv4 mk_dv4(double x, double y, double z, double w) { dv4 r = {x, y, z, w}; return r; }
+
+__host__ __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__host__ __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__host__ __device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+
+__host__ __device__ __forceinline__ d3 D3(double x, double y, double z) { d3 r = {x, y, z}; return r; }
+__host__ __device__ __forceinline__ d3 D3(float3 a) { return D3(a.x, a.y, a.z); }
+__host__ __device__ __forceinline__ d3 operator+(d3 a, d3 b) { return D3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ __forceinline__ d3 operator-(d3 a, d3 b) { return D3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ __forceinline__ d3 operator*(d3 a, double s) { return D3(a.x * s, a.y * s, a.z * s); }
+__host__ __device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ __forceinline__ d3 cross(d3 a, d3 b) {
+    return D3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double norm(d3 a) { return sqrt(dot(a, a)); }
+__host__ __device__ __forceinline__ float3 to_f(d3 a) { return f3((float)a.x, (float)a.y, (float)a.z); }
+
+// Mirror across the plane n.x = d (n unit): the image method's reflection of a point.
+__host__ __device__ __forceinline__ d3 mirror_pt(d3 p, d3 n, double d) { return p - n * (2.0 * (dot(n, p) - d)); }
+// Linear part of the mirror: reflects a direction.
+__host__ __device__ __forceinline__ d3 mirror_dir(d3 v, d3 n) { return v - n * (2.0 * dot(n, v)); }
+
+// ------------------------------------------------------------------------------------------------
+// device-side object layouts
+// ------------------------------------------------------------------------------------------------
+
+// One triangle in BVH leaf order: FP32 plane and inward edge planes for the filtered test, plus the
+// original float vertices (exact in FP64) for the FP64 decision.
+struct TriGeom {
+    float4 plane;        // unit normal n, offset d (n.x = d)
+    float4 edge[3];      // inward in-plane unit normal m_i, offset c_i: distance to edge = m_i.q - c_i
+};
+struct TriVerts {
+    float4 v0;           // xyz, w = face id (int bits)
+    float4 v1;
+    float4 v2;
+};
+
+// BVH node with both child boxes inline; child >= 0 is an internal node, child < 0 is leaf ~child.
+struct BvhNode {
+    float4 l_lo;         // xyz, w = left child (int bits)
+    float4 l_hi;         // xyz, w = right child (int bits)
+    float4 r_lo;
+    float4 r_hi;
+};
+
+struct Face {
+    dv4 plane;       // FP64 unit normal (from the face's first triangle) and offset
+    float4 plane32;
+    int tri_begin, tri_end;  // range in the face's triangle list (indices into leaf order)
+    int mat;
+    int pad;
+};
+
+struct DeviceScene {
+    int64_t n_tris;
+    int n_faces;
+    int root;                    // root child code (internal index, or ~leaf for one triangle); -1 if empty
+    const BvhNode* nodes;
+    const TriGeom* tri_geom;     // [n_tris] leaf order
+    const TriVerts* tri_verts;   // [n_tris] leaf order
+    const int* tri_face;         // [n_tris] leaf order
+    const Face* faces;           // [n_faces]
+    const int* face_tris;        // CSR: triangles (leaf order) of each face
+    const float2* mats;          // [n_mat] (eps_r, sigma)
+};
+
+}  // namespace risrt
+
+// ------------------------------------------------------------------------------------------------
+// ABI objects
+// ------------------------------------------------------------------------------------------------
+struct Antenna {
+    float pos[3];
+    float orient[9];
+    float power_w;
+    float gain_lin;
+    int pattern;
+    bool set;
+};
+
+struct risrt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    Antenna tx{}, rx{};
+};
+
+struct risrt_scene {
+    int64_t n_tris = 0;
+    int n_faces = 0;
+    int n_mat = 0;
+    int root = -1;
+    risrt::BvhNode* nodes = nullptr;
+    risrt::TriGeom* tri_geom = nullptr;
+    risrt::TriVerts* tri_verts = nullptr;
+    int* tri_face = nullptr;
+    risrt::Face* faces = nullptr;
+    int* face_tris = nullptr;
+    float2* mats = nullptr;
+    float scene_extent = 0.f;     // max |coordinate| over vertices
+    risrt::DeviceScene dev() const {
+        risrt::DeviceScene s;
+        s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.nodes = nodes; s.tri_geom = tri_geom;
+        s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.mats = mats;
+        return s;
+    }
+};
+
+struct risrt_ris {
+    int M = 0;
+    float center[3], t1[3], t2[3];
+    float dy = 0, dz = 0, elem_gain = 0;
+    int host_face = -1;
+    float4* elem = nullptr;      // [M] (a_m, b_m, a^2 + b^2, 0)
+    std::vector<float> uv_host;  // [M][2]
+};
+
+struct risrt_rxset {
+    int64_t n = 0;
+    float* xyz = nullptr;        // [n][3] device
+    bool owned = false;
+};
+
+// Rx-leg path record (structure of arrays, one entry per (rx, path)); see field.cu for use.
+struct PathRec {
+    float4 w;        // w = I - c in the RIS frame (t1, t2, n), and D0 = |w|
+    float4 a;        // frac(D0/lambda), order (int bits), eps1 (re, im)
+    float4 n1;       // bounce-1 normal in the RIS frame, eps2.re
+    float4 n2;       // bounce-2 normal (unfolded) in the RIS frame, eps2.im
+    float4 v;        // Rx pattern axis, unfolded into the RIS frame
+};
+
+struct risrt_pathset {
+    int64_t n_rx = 0;
+    int M = 0;
+    int n_faces = 0;
+    double freq = 0;
+    uint32_t flags = 0;
+    int rx_pattern = 0;
+    float rx_gain = 1.f;
+    // resident results
+    PathRec* rec = nullptr;          // [n_paths]
+    int64_t* rx_off = nullptr;       // [n_rx + 1] entry offsets per Rx (direct entry first)
+    uint32_t* vis = nullptr;         // [n_rx][W] direct e_m -> Rx visibility
+    int W = 0;
+    float2* E0 = nullptr;            // [n_rx] LOS + environment field
+    float2* cm = nullptr;            // [M] K * c_m (Tx leg, Eq. 4/5/7 factors)
+    float4* elem = nullptr;          // [M] copy of the RIS element table (a, b, |u|^2, 0)
+    int64_t n_paths = 0, cap_paths = 0;
+    // inspection data
+    int64_t* rx_seq = nullptr;       // [n_paths] sequence id per entry (-1 for direct)
+    int64_t* env_seq = nullptr;      // [n_env]
+    int64_t* env_off = nullptr;      // [n_rx + 1]
+    int64_t n_env = 0, cap_env = 0;
+    uint8_t* los = nullptr;          // [n_rx]
+    std::vector<int64_t> tx_seq_host;
+    std::vector<uint8_t> tx_vis_host;
+    int64_t units = 0;
+    int64_t fp64_refines = 0;
+    int64_t cap_rx = 0;              // capacity of the per-Rx arrays
+    // scratch (grown as needed, kept for reuse)
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int cand_cap = 0;                // per-Rx geometric candidate capacity
+};
+
+// ------------------------------------------------------------------------------------------------
+// cross-file entry points (implemented in scene.cu / trace.cu / field.cu)
+// ------------------------------------------------------------------------------------------------
+namespace risrt {
+int fail(risrt_ctx* ctx, int code, const std::string& msg);
+int cuda_fail(risrt_ctx* ctx, cudaError_t e, const char* where);
+#define RISRT_CUDA(ctx, call)                                           \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::risrt::cuda_fail(ctx, _e, #call); \
+    } while (0)
+#define RISRT_LAUNCH(ctx, what)                                          \
+    do {                                                                 \
+        cudaError_t _e = cudaGetLastError();                             \
+        if (_e != cudaSuccess) return ::risrt::cuda_fail(ctx, _e, what); \
+    } while (0)
+
+int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_t n_verts,
+                const int32_t* tris_host, const int32_t* face_host, const int32_t* mat_host,
+                const float* mats_host, int n_mat);
+int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rx,
+                double freq, int max_order_tx, int max_order_rx, uint32_t flags, risrt_pathset* ps);
+int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
+int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0);
+
+// device-wide exclusive scan (int64 in/out), n <= 2^31; temp from scan_temp_bytes
+size_t scan_temp_bytes(int64_t n);
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s);
+// stable LSD radix sort of (key, value) pairs on the low `bits` bits of key
+size_t sort_temp_bytes(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, void* temp, cudaStream_t s);
+}  // namespace risrt

@@ -1,0 +1,593 @@
+// Scene upload: face table and linear BVH (Morton codes -> stable radix sort -> binary radix tree
+// after Karras 2012 -> bottom-up box refit), plus the device-wide scan and sort they use.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace risrt {
+
+// ================================================================================================
+// Exclusive scan of int64 (three launches: block sums, scan of the sums, apply)
+// ================================================================================================
+namespace {
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* sh_warp, int64_t* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t s = lane < nw ? sh_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sh_warp[lane] = s;
+    }
+    __syncthreads();
+    int64_t base = warp > 0 ? sh_warp[warp - 1] : 0;
+    *total = sh_warp[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void k_scan_reduce(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ sums)
+{
+    __shared__ int64_t sh[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t acc = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        int64_t i = base + (int64_t)j * kScanThreads + threadIdx.x;
+        if (i < n) acc += in[i];
+    }
+    int64_t tot;
+    block_exclusive_scan(acc, sh, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int64_t* sums, int64_t nb)
+{
+    __shared__ int64_t sh[32];
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        int64_t i = b0 + threadIdx.x;
+        int64_t v = i < nb ? sums[i] : 0;
+        int64_t tot;
+        int64_t ex = block_exclusive_scan(v, sh, &tot);
+        if (i < nb) sums[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void k_scan_apply(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                             const int64_t* __restrict__ sums)
+{
+    __shared__ int64_t sh[32];
+    // blocked arrangement: thread t owns items [t*kScanItems, (t+1)*kScanItems) of the tile
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t acc = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = base + j < n ? in[base + j] : 0;
+        acc += v[j];
+    }
+    int64_t tot;
+    int64_t ex = block_exclusive_scan(acc, sh, &tot) + sums[blockIdx.x];
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n) out[base + j] = ex;
+        ex += v[j];
+    }
+}
+}  // namespace
+
+size_t scan_temp_bytes(int64_t n) { return sizeof(int64_t) * (size_t)((n + kScanTile - 1) / kScanTile + 1); }
+
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    int64_t* sums = (int64_t*)temp;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+    return cudaGetLastError();
+}
+
+// ================================================================================================
+// Stable LSD radix sort of (uint32 key, uint32 value), 8-bit digits
+// ================================================================================================
+namespace {
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 4;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+
+__global__ void k_sort_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int64_t n_tiles,
+                            int64_t* __restrict__ hist)
+{
+    __shared__ int cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int j = 0; j < kSortRounds; ++j) {
+        int64_t i = base + (int64_t)j * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];   // digit-major
+}
+
+__global__ void k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                               int shift, int64_t n_tiles, const int64_t* __restrict__ offs)
+{
+    __shared__ int wcnt[kSortThreads / 32][256];
+    __shared__ int running[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    running[threadIdx.x] = 0;
+    int64_t tile_off = offs[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+    __shared__ int64_t toff[256];
+    toff[threadIdx.x] = tile_off;
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int j = 0; j < kSortRounds; ++j) {
+        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        int64_t i = base + (int64_t)j * kSortThreads + threadIdx.x;
+        bool ok = i < n;
+        uint32_t key = ok ? kin[i] : 0u;
+        uint32_t val = ok ? vin[i] : 0u;
+        uint32_t dig = ok ? (key >> shift) & 255u : 256u;   // 256 = padding, never written
+        unsigned peers = __match_any_sync(0xffffffffu, dig);
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) wcnt[warp][dig] = __popc(peers);
+        __syncthreads();
+        {   // per digit: exclusive prefix over warps, continuing from earlier rounds
+            int d = threadIdx.x;
+            int run = running[d];
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                int c = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += c;
+            }
+            running[d] = run;
+        }
+        __syncthreads();
+        if (ok) {
+            int64_t pos = toff[dig] + wcnt[warp][dig] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+}  // namespace
+
+size_t sort_temp_bytes(int64_t n)
+{
+    int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
+    size_t hist = sizeof(int64_t) * 256 * (size_t)n_tiles;
+    return 2 * sizeof(uint32_t) * (size_t)n + 2 * hist + scan_temp_bytes(256 * n_tiles) + 256;
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, void* temp, cudaStream_t s)
+{
+    if (n <= 1) return cudaSuccess;
+    int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
+    char* p = (char*)temp;
+    uint32_t* k2 = (uint32_t*)p; p += sizeof(uint32_t) * n;
+    uint32_t* v2 = (uint32_t*)p; p += sizeof(uint32_t) * n;
+    p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    int64_t* hist = (int64_t*)p; p += sizeof(int64_t) * 256 * n_tiles;
+    int64_t* offs = (int64_t*)p; p += sizeof(int64_t) * 256 * n_tiles;
+    void* scan_tmp = p;
+    uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
+    int passes = (bits + 7) / 8;
+    for (int pass = 0; pass < passes; ++pass) {
+        int shift = 8 * pass;
+        k_sort_hist<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(ka, n, shift, n_tiles, hist);
+        cudaError_t e = exclusive_scan_i64(hist, offs, 256 * n_tiles, scan_tmp, s);
+        if (e != cudaSuccess) return e;
+        k_sort_scatter<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, n_tiles, offs);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        cudaMemcpyAsync(keys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    return cudaGetLastError();
+}
+
+// ================================================================================================
+// BVH build
+// ================================================================================================
+namespace {
+
+__device__ __forceinline__ unsigned ordered_bits(float f)
+{
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered(unsigned o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+__global__ void k_bounds(const float* __restrict__ verts, int64_t nv, unsigned* __restrict__ bb)
+{
+    // bb[0..2] = ordered min, bb[3..5] = ordered max, bb[6] = max |coord| bits
+    unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0}, ext = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < 3; ++k) {
+            float v = verts[3 * i + k];
+            unsigned o = ordered_bits(v);
+            lo[k] = min(lo[k], o);
+            hi[k] = max(hi[k], o);
+            ext = max(ext, __float_as_uint(fabsf(v)));
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        atomicMin(&bb[k], lo[k]);
+        atomicMax(&bb[3 + k], hi[k]);
+    }
+    atomicMax(&bb[6], ext);
+}
+
+__device__ __forceinline__ unsigned spread10(unsigned x)
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void k_morton(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
+                         const unsigned* __restrict__ bb, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    float lo[3], inv[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = from_ordered(bb[k]);
+        float span = from_ordered(bb[3 + k]) - lo[k];
+        inv[k] = span > 0.f ? 1.f / span : 0.f;
+    }
+    unsigned code = 0;
+    for (int k = 0; k < 3; ++k) {
+        float c = (verts[3 * tris[3 * t] + k] + verts[3 * tris[3 * t + 1] + k] + verts[3 * tris[3 * t + 2] + k]) * (1.f / 3.f);
+        float u = (c - lo[k]) * inv[k];
+        unsigned q = (unsigned)fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+        code |= spread10(q) << (2 - k);
+    }
+    keys[t] = code;
+    vals[t] = (uint32_t)t;
+}
+
+// Per leaf (sorted order): exact float vertices, FP32 plane and edge planes computed in FP64.
+__global__ void k_leaves(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                         const int32_t* __restrict__ face, const uint32_t* __restrict__ order, int64_t nt,
+                         TriVerts* __restrict__ tv, TriGeom* __restrict__ tg, int* __restrict__ tf,
+                         int* __restrict__ leaf_of_orig)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int64_t t = order[i];
+    leaf_of_orig[t] = (int)i;
+    float3 v[3];
+    for (int j = 0; j < 3; ++j) {
+        const float* p = verts + 3 * (int64_t)tris[3 * t + j];
+        v[j] = f3(p[0], p[1], p[2]);
+    }
+    int f = face[t];
+    TriVerts o;
+    o.v0 = make_float4(v[0].x, v[0].y, v[0].z, __int_as_float(f));
+    o.v1 = make_float4(v[1].x, v[1].y, v[1].z, 0.f);
+    o.v2 = make_float4(v[2].x, v[2].y, v[2].z, 0.f);
+    tv[i] = o;
+    tf[i] = f;
+    d3 a = D3(v[0]), b = D3(v[1]), c = D3(v[2]);
+    d3 n = cross(b - a, c - a);
+    double nn = norm(n);
+    TriGeom g;
+    if (nn > 0) {
+        n = n * (1.0 / nn);
+        g.plane = make_float4((float)n.x, (float)n.y, (float)n.z, (float)dot(n, a));
+        d3 P[3] = {a, b, c};
+        for (int k = 0; k < 3; ++k) {   // edge opposite vertex k runs P[k+1] -> P[k+2]
+            d3 p = P[(k + 1) % 3], q = P[(k + 2) % 3];
+            d3 e = q - p;
+            d3 m = cross(n, e);          // in-plane, points to the interior for a CCW triangle about n
+            double mn = norm(m);
+            m = m * (1.0 / mn);
+            g.edge[k] = make_float4((float)m.x, (float)m.y, (float)m.z, (float)dot(m, p));
+        }
+    } else {   // degenerate triangle: never hit
+        g.plane = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < 3; ++k) g.edge[k] = make_float4(0.f, 0.f, 0.f, 1.f);
+    }
+    tg[i] = g;
+}
+
+__device__ __forceinline__ unsigned long long ckey(const uint32_t* keys, int i) {
+    return ((unsigned long long)keys[i] << 32) | (unsigned)i;
+}
+__device__ __forceinline__ int delta(const uint32_t* keys, int n, int i, int j)
+{
+    if (j < 0 || j >= n) return -1;
+    return __clzll(ckey(keys, i) ^ ckey(keys, j));
+}
+
+// Binary radix tree over n sorted keys (Karras, "Maximizing parallelism in the construction of
+// BVHs, octrees, and k-d trees", HPG 2012): internal node i covers a key range found by an
+// exponential + binary search on the common-prefix length, split at the highest differing bit.
+__global__ void k_karras(const uint32_t* __restrict__ keys, int n, BvhNode* __restrict__ nodes,
+                         int* __restrict__ parent_int, int* __restrict__ parent_leaf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(keys, n, i, i - d);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int l = 0;
+    for (int t = lmax / 2; t >= 1; t /= 2)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(keys, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + min(d, 0);
+    int left = (min(i, j) == gamma) ? ~gamma : gamma;
+    int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    nodes[i].l_lo.w = __int_as_float(left);
+    nodes[i].l_hi.w = __int_as_float(right);
+    if (left < 0) parent_leaf[~left] = i; else parent_int[left] = i;
+    if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
+}
+
+__device__ __forceinline__ void store_slot(BvhNode* node, bool right, float3 lo, float3 hi)
+{
+    float* base = right ? &node->r_lo.x : &node->l_lo.x;
+    float* baseh = right ? &node->r_hi.x : &node->l_hi.x;
+    volatile float* vl = base;
+    volatile float* vh = baseh;
+    vl[0] = lo.x; vl[1] = lo.y; vl[2] = lo.z;
+    vh[0] = hi.x; vh[1] = hi.y; vh[2] = hi.z;
+}
+
+// Bottom-up refit: the second child to finish a node merges both boxes and moves up.
+__global__ void k_refit(const TriVerts* __restrict__ tv, int n, BvhNode* nodes,
+                        const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
+                        int* flags, float pad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    TriVerts v = tv[i];
+    float3 lo = f3(fminf(v.v0.x, fminf(v.v1.x, v.v2.x)), fminf(v.v0.y, fminf(v.v1.y, v.v2.y)),
+                   fminf(v.v0.z, fminf(v.v1.z, v.v2.z)));
+    float3 hi = f3(fmaxf(v.v0.x, fmaxf(v.v1.x, v.v2.x)), fmaxf(v.v0.y, fmaxf(v.v1.y, v.v2.y)),
+                   fmaxf(v.v0.z, fmaxf(v.v1.z, v.v2.z)));
+    lo = lo - f3(pad, pad, pad);
+    hi = hi + f3(pad, pad, pad);
+    int child = ~i;
+    int p = parent_leaf[i];
+    while (p >= 0) {
+        BvhNode* node = nodes + p;
+        bool right = __float_as_int(((volatile float*)&node->l_hi.w)[0]) == child;
+        store_slot(node, right, lo, hi);
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;
+        __threadfence();
+        volatile float* q = &node->l_lo.x;
+        float3 a_lo = f3(q[0], q[1], q[2]), a_hi = f3(q[4], q[5], q[6]);
+        float3 b_lo = f3(q[8], q[9], q[10]), b_hi = f3(q[12], q[13], q[14]);
+        lo = f3(fminf(a_lo.x, b_lo.x), fminf(a_lo.y, b_lo.y), fminf(a_lo.z, b_lo.z));
+        hi = f3(fmaxf(a_hi.x, b_hi.x), fmaxf(a_hi.y, b_hi.y), fmaxf(a_hi.z, b_hi.z));
+        child = p;
+        p = parent_int[p];
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// faces
+// ------------------------------------------------------------------------------------------------
+__global__ void k_face_first(const int32_t* __restrict__ face, int64_t nt, int* __restrict__ first,
+                             int* __restrict__ count)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    atomicMin(&first[face[t]], (int)t);
+    atomicAdd(&count[face[t]], 1);
+}
+
+__global__ void k_face_fill(const int32_t* __restrict__ face, int64_t nt, const int* __restrict__ leaf_of_orig,
+                            const int64_t* __restrict__ start, int* __restrict__ cursor, int* __restrict__ face_tris)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int f = face[t];
+    int k = atomicAdd(&cursor[f], 1);
+    face_tris[start[f] + k] = leaf_of_orig[t];
+}
+
+// Face plane in FP64 from the face's first triangle (lowest input index), as the image method's
+// mirror plane (Sec. II-B).
+__global__ void k_face_plane(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                             const int32_t* __restrict__ mat, const int* __restrict__ first,
+                             const int64_t* __restrict__ start, const int* __restrict__ count, int F,
+                             Face* __restrict__ faces)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    int t = first[f];
+    d3 v[3];
+    for (int j = 0; j < 3; ++j) {
+        const float* p = verts + 3 * (int64_t)tris[3 * (int64_t)t + j];
+        v[j] = D3((double)p[0], (double)p[1], (double)p[2]);
+    }
+    d3 n = cross(v[1] - v[0], v[2] - v[0]);
+    n = n * (1.0 / norm(n));
+    double d = dot(n, v[0]);
+    Face fc;
+    fc.plane = mk_dv4(n.x, n.y, n.z, d);
+    fc.plane32 = make_float4((float)n.x, (float)n.y, (float)n.z, (float)d);
+    fc.tri_begin = (int)start[f];
+    fc.tri_end = (int)(start[f] + count[f]);
+    fc.mat = mat[t];
+    fc.pad = 0;
+    faces[f] = fc;
+}
+
+__global__ void k_i32_to_i64(const int* __restrict__ a, int64_t* __restrict__ b, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+template <typename T>
+int dmalloc(risrt_ctx* ctx, T** p, size_t count)
+{
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, RISRT_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    return RISRT_OK;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_t n_verts,
+                const int32_t* tris_host, const int32_t* face_host, const int32_t* mat_host,
+                const float* mats_host, int n_mat)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t nt = sc->n_tris;
+    const int F = sc->n_faces;
+    sc->n_mat = n_mat;
+    int rc;
+    if ((rc = dmalloc(ctx, &sc->mats, n_mat))) return rc;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(sc->mats, mats_host, sizeof(float2) * n_mat, cudaMemcpyHostToDevice, s));
+    if (nt == 0) {
+        sc->root = -1;
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        return RISRT_OK;
+    }
+    // inputs on the device
+    float* d_verts;
+    int32_t *d_tris, *d_face, *d_mat;
+    if ((rc = dmalloc(ctx, &d_verts, 3 * n_verts))) return rc;
+    if ((rc = dmalloc(ctx, &d_tris, 3 * nt))) return rc;
+    if ((rc = dmalloc(ctx, &d_face, nt))) return rc;
+    if ((rc = dmalloc(ctx, &d_mat, nt))) return rc;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(d_verts, verts_host, sizeof(float) * 3 * n_verts, cudaMemcpyHostToDevice, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(d_tris, tris_host, sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(d_face, face_host, sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(d_mat, mat_host, sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
+
+    // scene bounds
+    unsigned* d_bb;
+    if ((rc = dmalloc(ctx, &d_bb, 8))) return rc;
+    unsigned bb_init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0, 0, 0};
+    RISRT_CUDA(ctx, cudaMemcpyAsync(d_bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
+    k_bounds<<<std::min<int64_t>(nblk(n_verts, 256), 1024), 256, 0, s>>>(d_verts, n_verts, d_bb);
+    RISRT_LAUNCH(ctx, "k_bounds");
+
+    // Morton codes and stable sort
+    uint32_t *keys, *vals;
+    void* tmp;
+    if ((rc = dmalloc(ctx, &keys, nt))) return rc;
+    if ((rc = dmalloc(ctx, &vals, nt))) return rc;
+    size_t tmp_bytes = std::max(sort_temp_bytes(nt), scan_temp_bytes(F) + 64);
+    if ((rc = dmalloc(ctx, (char**)&tmp, tmp_bytes))) return rc;
+    k_morton<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, keys, vals);
+    RISRT_LAUNCH(ctx, "k_morton");
+    RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nt, 30, tmp, s));
+
+    // leaves, hierarchy, refit
+    int* leaf_of_orig;
+    if ((rc = dmalloc(ctx, &sc->tri_verts, nt))) return rc;
+    if ((rc = dmalloc(ctx, &sc->tri_geom, nt))) return rc;
+    if ((rc = dmalloc(ctx, &sc->tri_face, nt))) return rc;
+    if ((rc = dmalloc(ctx, &leaf_of_orig, nt))) return rc;
+    k_leaves<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, d_face, vals, nt, sc->tri_verts, sc->tri_geom,
+                                           sc->tri_face, leaf_of_orig);
+    RISRT_LAUNCH(ctx, "k_leaves");
+
+    unsigned bb_host[8];
+    RISRT_CUDA(ctx, cudaMemcpyAsync(bb_host, d_bb, sizeof(bb_host), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    float ext;
+    memcpy(&ext, &bb_host[6], 4);
+    sc->scene_extent = ext;
+    const float pad = 1e-4f * (1.f + ext);
+
+    int n_int = (int)std::max<int64_t>(nt - 1, 1);
+    int *parent_int, *parent_leaf, *flags;
+    if ((rc = dmalloc(ctx, &sc->nodes, n_int))) return rc;
+    if ((rc = dmalloc(ctx, &parent_int, n_int))) return rc;
+    if ((rc = dmalloc(ctx, &parent_leaf, nt))) return rc;
+    if ((rc = dmalloc(ctx, &flags, n_int))) return rc;
+    RISRT_CUDA(ctx, cudaMemsetAsync(sc->nodes, 0, sizeof(BvhNode) * n_int, s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * n_int, s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(parent_int, 0xff, sizeof(int) * n_int, s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nt, s));
+    if (nt > 1) {
+        k_karras<<<nblk(nt - 1, 256), 256, 0, s>>>(keys, (int)nt, sc->nodes, parent_int, parent_leaf);
+        RISRT_LAUNCH(ctx, "k_karras");
+        k_refit<<<nblk(nt, 256), 256, 0, s>>>(sc->tri_verts, (int)nt, sc->nodes, parent_int, parent_leaf, flags, pad);
+        RISRT_LAUNCH(ctx, "k_refit");
+        sc->root = 0;
+    } else {
+        sc->root = ~0;
+    }
+
+    // faces: first triangle, triangle lists, FP64 planes
+    int *first, *count, *cursor;
+    int64_t *count64, *start;
+    if ((rc = dmalloc(ctx, &first, F))) return rc;
+    if ((rc = dmalloc(ctx, &count, F))) return rc;
+    if ((rc = dmalloc(ctx, &cursor, F))) return rc;
+    if ((rc = dmalloc(ctx, &count64, F))) return rc;
+    if ((rc = dmalloc(ctx, &start, F))) return rc;
+    if ((rc = dmalloc(ctx, &sc->face_tris, nt))) return rc;
+    if ((rc = dmalloc(ctx, &sc->faces, F))) return rc;
+    RISRT_CUDA(ctx, cudaMemsetAsync(first, 0x7f, sizeof(int) * F, s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int) * F, s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * F, s));
+    k_face_first<<<nblk(nt, 256), 256, 0, s>>>(d_face, nt, first, count);
+    RISRT_LAUNCH(ctx, "k_face_first");
+    k_i32_to_i64<<<nblk(F, 256), 256, 0, s>>>(count, count64, F);
+    RISRT_CUDA(ctx, exclusive_scan_i64(count64, start, F, tmp, s));
+    k_face_fill<<<nblk(nt, 256), 256, 0, s>>>(d_face, nt, leaf_of_orig, start, cursor, sc->face_tris);
+    RISRT_LAUNCH(ctx, "k_face_fill");
+    k_face_plane<<<nblk(F, 128), 128, 0, s>>>(d_verts, d_tris, d_mat, first, start, count, F, sc->faces);
+    RISRT_LAUNCH(ctx, "k_face_plane");
+
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    cudaFree(d_verts); cudaFree(d_tris); cudaFree(d_face); cudaFree(d_mat); cudaFree(d_bb);
+    cudaFree(keys); cudaFree(vals); cudaFree(tmp); cudaFree(leaf_of_orig);
+    cudaFree(parent_int); cudaFree(parent_leaf); cudaFree(flags);
+    cudaFree(first); cudaFree(count); cudaFree(cursor); cudaFree(count64); cudaFree(start);
+    return RISRT_OK;
+}
+
+}  // namespace risrt

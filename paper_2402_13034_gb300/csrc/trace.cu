@@ -1,0 +1,865 @@
+// Path finding (Sec. II-B): image trees of the Tx and the RIS centre over face sequences of length
+// <= 2, per-destination candidate search, BVH occlusion of every segment, per-element direct-leg
+// visibility (one ray per element, Sec. IV-A), and the resident path set with FP64 phase references.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "geom.cuh"
+
+namespace risrt {
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+struct Frame {             // RIS frame, FP64
+    double c[3], t1[3], t2[3], n[3];
+};
+struct AntD {
+    double pos[3];
+    double z[3];           // unit boresight (local z axis)
+    double power, gain;
+    int pattern;
+};
+
+__device__ __forceinline__ d3 fr_c(const Frame& F) { return D3(F.c[0], F.c[1], F.c[2]); }
+__device__ __forceinline__ d3 fr_t1(const Frame& F) { return D3(F.t1[0], F.t1[1], F.t1[2]); }
+__device__ __forceinline__ d3 fr_t2(const Frame& F) { return D3(F.t2[0], F.t2[1], F.t2[2]); }
+__device__ __forceinline__ d3 fr_n(const Frame& F) { return D3(F.n[0], F.n[1], F.n[2]); }
+
+__device__ __forceinline__ d3 elem_pos(const Frame& F, float4 e)
+{
+    return fr_c(F) + fr_t1(F) * (double)e.x + fr_t2(F) * (double)e.y;
+}
+
+// ------------------------------------------------------------------------------------------------
+// sequence tables
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool coplanar_d(const Face& a, const Face& b)
+{
+    d3 na = ld3(a.plane), nb = ld3(b.plane);
+    if (norm(cross(na, nb)) > 1e-9) return false;
+    double s = dot(na, nb) > 0 ? 1.0 : -1.0;
+    return fabs(a.plane.w - s * b.plane.w) < 1e-9;
+}
+__device__ __forceinline__ bool contains_point(const Face& a, d3 p) { return fabs(dot(ld3(a.plane), p) - a.plane.w) < 1e-6; }
+
+// mode 0: Tx leg (last face may not contain the RIS centre); 1: Rx leg (first face may not);
+// 2: Tx -> Rx environment paths.
+__global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, int64_t* __restrict__ flag)
+{
+    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= n_ids) return;
+    const int F = S.n_faces;
+    int f1, f2 = -1, k = 1;
+    if (id < F) f1 = (int)id;
+    else {
+        int64_t r = id - F;
+        f1 = (int)(r / F);
+        f2 = (int)(r % F);
+        k = 2;
+    }
+    bool ok = true;
+    if (k == 2 && (f1 == f2 || coplanar_d(S.faces[f1], S.faces[f2]))) ok = false;
+    d3 c = fr_c(fr);
+    if (mode == 0 && contains_point(S.faces[k == 2 ? f2 : f1], c)) ok = false;
+    if (mode == 1 && contains_point(S.faces[f1], c)) ok = false;
+    flag[id] = ok ? 1 : 0;
+}
+
+__global__ void k_seq_build(DeviceScene S, int64_t n_ids, const int64_t* __restrict__ flag,
+                            const int64_t* __restrict__ pos, d3 src, SeqEntry* __restrict__ out,
+                            SeqEntryD* __restrict__ outd)
+{
+    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= n_ids || !flag[id]) return;
+    const int F = S.n_faces;
+    int f1, f2 = -1, k = 1;
+    if (id < F) f1 = (int)id;
+    else {
+        int64_t r = id - F;
+        f1 = (int)(r / F);
+        f2 = (int)(r % F);
+        k = 2;
+    }
+    const dv4 p1 = S.faces[f1].plane;
+    d3 S1 = mirror_pt(src, ld3(p1), p1.w);
+    d3 S2 = S1;
+    dv4 pl = p1;
+    if (k == 2) {
+        pl = S.faces[f2].plane;
+        S2 = mirror_pt(S1, ld3(pl), pl.w);
+    }
+    SeqEntry e;
+    const d3 prev = k == 2 ? S1 : src;
+    e.sL = make_float4((float)S2.x, (float)S2.y, (float)S2.z, (float)(dot(ld3(pl), prev) - pl.w));
+    e.pL = make_float4((float)pl.x, (float)pl.y, (float)pl.z, (float)pl.w);
+    e.s1 = make_float4((float)S1.x, (float)S1.y, (float)S1.z, (float)(dot(ld3(p1), src) - p1.w));
+    e.p1 = make_float4((float)p1.x, (float)p1.y, (float)p1.z, (float)p1.w);
+    e.info = make_int4(f1, f2, (int)id, k);
+    int64_t o = pos[id];
+    out[o] = e;
+    SeqEntryD d;
+    d.S1 = mk_dv4(S1.x, S1.y, S1.z, 0.0);
+    d.S2 = mk_dv4(S2.x, S2.y, S2.z, 0.0);
+    outd[o] = d;
+}
+
+// ------------------------------------------------------------------------------------------------
+// candidate search: for each destination and each allowed sequence, back-trace the reflection
+// points and keep the sequence if every point lies in its face and on the correct sides.
+// ------------------------------------------------------------------------------------------------
+constexpr int kCandThreads = 128;
+constexpr int kCandChunk = 2048;
+
+// Candidate filter in FP32 with exact conditions (Sec. II-B image method):
+//  (A) the destination and the previous image lie strictly on the same side of the last plane
+//      (equivalently the back-trace parameter lies in (0,1));
+//  (B) the last reflection point lies in its face;
+//  (C) order 2: the source and the last reflection point lie on the same side of the first plane;
+//  (D) order 2: the first reflection point lies in its face.
+// Each test is decided in FP32 when its margin exceeds the FP32 error bound, otherwise the whole
+// candidate is settled by the FP64 check.
+__global__ void __launch_bounds__(kCandThreads)
+k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3 src,
+             const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int n_seq,
+             float tol_base, int* __restrict__ cand, int* __restrict__ cand_cnt, int cap,
+             int* __restrict__ overflow, unsigned long long* __restrict__ refines)
+{
+    __shared__ SeqEntry sh[kCandThreads];
+    const int64_t r = blockIdx.x * (int64_t)kCandThreads + threadIdx.x;
+    const bool active = r < n_dst;
+    const float3 R = active ? f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]) : f3(0.f, 0.f, 0.f);
+    for (int64_t chunk = blockIdx.y; chunk * kCandChunk < n_seq; chunk += gridDim.y) {
+    const int s_begin = (int)(chunk * kCandChunk);
+    const int s_end = min(n_seq, s_begin + kCandChunk);
+    for (int s0 = s_begin; s0 < s_end; s0 += kCandThreads) {
+        __syncthreads();
+        if (s0 + threadIdx.x < s_end) sh[threadIdx.x] = seqs[s0 + threadIdx.x];
+        __syncthreads();
+        const int cnt = min(kCandThreads, s_end - s0);
+        if (!active) continue;
+        for (int j = 0; j < cnt; ++j) {
+            const SeqEntry& e = sh[j];
+            // (A)
+            const float sR = dot(xyz(e.pL), R) - e.pL.w;
+            const float sp = e.sL.w;
+            const bool clearA = fabsf(sR) > tol_base && fabsf(sp) > tol_base;
+            if (clearA && sp * sR < 0.f) continue;
+            bool unsure = !clearA;
+            // (B) last reflection point P = R + t (S_L - R), t = sR / (sR + sp)
+            const float den = sR + sp;
+            const float3 d = xyz(e.sL) - R;
+            const float t = sR / den;
+            const float3 P = R + d * t;
+            const float cond = sqrtf(dot(d, d)) / fmaxf(fabsf(den), 1e-30f);
+            const float tol = tol_base * fminf(cond, 1e6f);
+            const int k = e.info.w;
+            const int cB = in_face_fp32(S, k == 2 ? e.info.y : e.info.x, P, tol);
+            if (cB == 0) continue;
+            unsure |= cB == 2;
+            if (k == 2) {
+                // (C)
+                const float s1P = dot(xyz(e.p1), P) - e.p1.w;
+                const float ssrc = e.s1.w;
+                const bool clearC = fabsf(s1P) > tol && fabsf(ssrc) > tol_base;
+                if (clearC && s1P * ssrc < 0.f) continue;
+                unsure |= !clearC;
+                // (D) P1 = P + t1 (S1 - P), t1 = s1P / (s1P + ssrc)
+                const float den1 = s1P + ssrc;
+                const float3 d1 = xyz(e.s1) - P;
+                const float3 P1 = P + d1 * (s1P / den1);
+                const float cond1 = sqrtf(dot(d1, d1)) / fmaxf(fabsf(den1), 1e-30f);
+                const float tol1 = tol * fminf(cond1, 1e6f) + tol_base;
+                const int cD = in_face_fp32(S, e.info.x, P1, tol1);
+                if (cD == 0) continue;
+                unsure |= cD == 2;
+            }
+            if (unsure) {
+                atomicAdd(refines, 1ull);
+                d3 pts[4];
+                const d3 Rd = D3((double)R.x, (double)R.y, (double)R.z);
+                if (!seq_geom_fp64(S, src, Rd, e.info, seqd[s0 + j], pts)) continue;
+            }
+            int slot = atomicAdd(&cand_cnt[r], 1);
+            if (slot < cap) cand[r * (int64_t)cap + slot] = s0 + j;
+            else atomicExch(overflow, 1);
+        }
+    }
+    }
+}
+
+// Occlusion of every segment of every candidate (thread per candidate slot); invalid -> -1.
+__global__ void k_validate(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3 src,
+                           int src_face, int dst_face, const SeqEntry* __restrict__ seqs,
+                           const SeqEntryD* __restrict__ seqd, int* __restrict__ cand,
+                           const int* __restrict__ cand_cnt, int cap, float tol_base,
+                           unsigned long long* refines, int* err)
+{
+    int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t r = gid / cap;
+    int slot = (int)(gid % cap);
+    if (r >= n_dst || slot >= min(cand_cnt[r], cap)) return;
+    int si = cand[r * (int64_t)cap + slot];
+    const int4 info = seqs[si].info;
+    const d3 R = D3((double)dst_xyz[3 * r], (double)dst_xyz[3 * r + 1], (double)dst_xyz[3 * r + 2]);
+    d3 pts[4];
+    seq_points_fp64(S, R, info, seqd[si], src, pts);
+    const int k = info.w;
+    const int fa[2] = {info.x, info.y};
+    bool ok = true;
+    for (int j = 0; j <= k && ok; ++j) {
+        int i0 = j == 0 ? src_face : fa[j - 1];
+        int i1 = j == k ? dst_face : fa[j];
+        if (seg_blocked(S, pts[j], pts[j + 1], i0, i1, tol_base, refines, err)) ok = false;
+    }
+    if (!ok) cand[r * (int64_t)cap + slot] = -1;
+}
+
+// Per destination (one warp): keep the valid candidates, sorted by sequence id (rank sort; ids are
+// unique per destination), in the first slots; count -> cnt64.
+__global__ void k_finalize(int* __restrict__ cand, const int* __restrict__ cand_cnt, int64_t n_dst, int cap,
+                           const SeqEntry* __restrict__ seqs, int64_t* __restrict__ cnt64)
+{
+    extern __shared__ int sh_list[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (r >= n_dst) return;
+    int* list = sh_list + warp * cap;
+    int* row = cand + r * (int64_t)cap;
+    int n = min(cand_cnt[r], cap);
+    int m = 0;
+    for (int b = 0; b < n; b += 32) {
+        int v = b + lane < n ? row[b + lane] : -1;
+        unsigned ball = __ballot_sync(0xffffffffu, v >= 0);
+        if (v >= 0) list[m + __popc(ball & ((1u << lane) - 1u))] = v;
+        m += __popc(ball);
+    }
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) {      // table index order is sequence-id order
+        int v = list[i];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) rank += list[j] < v;
+        row[rank] = v;
+    }
+    __syncwarp();
+    if (lane == 0) cnt64[r] = m;
+}
+
+// ------------------------------------------------------------------------------------------------
+// direct legs
+// ------------------------------------------------------------------------------------------------
+// e_m -> Rx visibility bits, one warp per (Rx, 32 elements): coherent rays from a small aperture.
+__global__ void k_direct_vis(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, const float4* __restrict__ elem,
+                             int M, int W, Frame fr, int host_face, float tol_base, uint32_t* __restrict__ vis,
+                             unsigned long long* refines, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t r = wid / W;
+    int w = (int)(wid % W);
+    if (r >= n_rx) return;
+    int m = w * 32 + lane;
+    bool blocked = true;
+    if (m < M) {
+        d3 e = elem_pos(fr, elem[m]);
+        d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+        blocked = seg_blocked(S, e, R, host_face, -1, tol_base, refines, err);
+    }
+    unsigned b = __ballot_sync(0xffffffffu, !blocked);
+    if (lane == 0) vis[r * W + w] = b;
+}
+
+__global__ void k_tx_vis(DeviceScene S, const float4* __restrict__ elem, int M, Frame fr, AntD tx, int host_face,
+                         float tol_base, uint8_t* __restrict__ vis, unsigned long long* refines, int* err)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    d3 e = elem_pos(fr, elem[m]);
+    vis[m] = !seg_blocked(S, D3(tx.pos[0], tx.pos[1], tx.pos[2]), e, -1, host_face, tol_base, refines, err);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Tx-leg element coefficients: K * c_m = K * sum_p sqrt(2 eta0 Pt Gt Ft) sqrt(F_in) R_p e^{-jkL}/L
+// (Eq. 4, Eq. 5, Eq. 7; K = sqrt(G dy dz / 4 pi) lambda / 4 pi), all in FP64.
+// ------------------------------------------------------------------------------------------------
+struct WaveD {
+    double lam, k, omega;
+    int tm;
+};
+
+__device__ __forceinline__ cd mat_eps(const DeviceScene& S, int face, const WaveD& wv)
+{
+    float2 m = S.mats[S.faces[face].mat];
+    return cd{(double)m.x, -(double)m.y / (wv.omega * kEps0)};
+}
+
+// Unfolded-leg quantities from a source image Ts to point X: length, departure direction of the
+// real first segment (mirrors applied back), Fresnel product. faces[0..k-1] in propagation order.
+__device__ __forceinline__ void unfolded_from_source(const DeviceScene& S, d3 Ts, d3 X, const int* fa, int k,
+                                                     const WaveD& wv, double* L, d3* dep, d3* arr, cd* R)
+{
+    d3 d = X - Ts;
+    *L = norm(d);
+    d = d * (1.0 / *L);
+    *arr = d;                      // the last segment is real in this unfolding
+    cd Rp = cd{1.0, 0.0};
+    // last bounce plane is real; earlier planes are mirrored across the later ones
+    if (k >= 1) {
+        d3 nl = ld3(S.faces[fa[k - 1]].plane);
+        Rp = cmul(Rp, fresnel_d(fabs(dot(d, nl)), mat_eps(S, fa[k - 1], wv), wv.tm));
+        if (k == 2) {
+            d3 n1 = mirror_dir(ld3(S.faces[fa[0]].plane), nl);
+            Rp = cmul(Rp, fresnel_d(fabs(dot(d, n1)), mat_eps(S, fa[0], wv), wv.tm));
+        }
+    }
+    d3 dd = d;                     // real first-segment direction: L_f1 L_f2 d
+    for (int j = k - 1; j >= 0; --j) dd = mirror_dir(dd, ld3(S.faces[fa[j]].plane));
+    *dep = dd;
+    *R = Rp;
+}
+
+__global__ void k_cm(DeviceScene S, const float4* __restrict__ elem, int M, Frame fr, AntD tx, WaveD wv, double K,
+                     const uint8_t* __restrict__ tx_vis, const int* __restrict__ tx_seq, int n_tx,
+                     const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, float2* __restrict__ cm)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    d3 e = elem_pos(fr, elem[m]);
+    d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
+    d3 z = D3(tx.z[0], tx.z[1], tx.z[2]);
+    d3 n = fr_n(fr);
+    cd acc = cd{0.0, 0.0};
+    for (int p = -1; p < n_tx; ++p) {
+        d3 Ts = T;
+        int fa[2] = {-1, -1};
+        int k = 0;
+        if (p < 0) {
+            if (!tx_vis[m]) continue;
+        } else {
+            int si = tx_seq[p];
+            int4 info = seqs[si].info;
+            k = info.w;
+            fa[0] = info.x;
+            fa[1] = info.y;
+            Ts = k == 2 ? ld3(seqd[si].S2) : ld3(seqd[si].S1);
+        }
+        double L;
+        d3 dep, arr;
+        cd R;
+        unfolded_from_source(S, Ts, e, fa, k, wv, &L, &dep, &arr, &R);
+        double Ft = pattern_d(tx.pattern, tx.gain, dot(dep, z));
+        double cin = -dot(arr, n);
+        double Fin = cin > 0.0 ? cin : 0.0;
+        double amp = sqrt(2.0 * kEta0 * tx.power * tx.gain * Ft) * sqrt(Fin) / L;
+        double ph = -2.0 * kPi * (L / wv.lam - floor(L / wv.lam));
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        acc = cadd(acc, cmul(R, cd{amp * cs, amp * sn}));
+    }
+    cm[m] = make_float2((float)(K * acc.re), (float)(K * acc.im));
+}
+
+// ------------------------------------------------------------------------------------------------
+// Path records (FP64 reference quantities per (Rx, path)) and E0 = LOS + environment paths.
+// ------------------------------------------------------------------------------------------------
+__global__ void k_count_total(const int64_t* __restrict__ cnt, int64_t n, int64_t* __restrict__ tot)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) tot[i] = cnt[i] + 1;    // + the direct entry
+}
+
+__device__ __forceinline__ float4 local4(const Frame& fr, d3 v, float w)
+{
+    return make_float4((float)dot(v, fr_t1(fr)), (float)dot(v, fr_t2(fr)), (float)dot(v, fr_n(fr)), w);
+}
+
+__global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, Frame fr, WaveD wv,
+                          AntD rxa, const int* __restrict__ cand, int cap, const int64_t* __restrict__ off,
+                          const SeqEntry* __restrict__ seqs, PathRec* __restrict__ rec, int64_t* __restrict__ rec_seq)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= n_rx) return;
+    const int64_t o = off[r];
+    const int n = (int)(off[r + 1] - o);
+    const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+    const d3 c = fr_c(fr);
+    const d3 zr = D3(rxa.z[0], rxa.z[1], rxa.z[2]);
+    for (int q = lane; q < n; q += 32) {
+        int k = 0;
+        int fa[2] = {-1, -1};
+        int64_t id = -1;
+        if (q > 0) {
+            int4 info = seqs[cand[r * (int64_t)cap + q - 1]].info;
+            k = info.w;
+            fa[0] = info.x;
+            fa[1] = info.y;
+            id = info.z;
+        }
+        // Rx mirrored through the bounce planes in reverse order: I = M_f1(M_f2(R))
+        d3 I = R;
+        for (int j = k - 1; j >= 0; --j) {
+            dv4 pl = S.faces[fa[j]].plane;
+            I = mirror_pt(I, ld3(pl), pl.w);
+        }
+        d3 w = I - c;
+        double D0 = norm(w);
+        double fr0 = D0 / wv.lam - floor(D0 / wv.lam);
+        // Rx pattern axis unfolded: v = L_f1 L_f2 z_r
+        d3 v = zr;
+        for (int j = k - 1; j >= 0; --j) v = mirror_dir(v, ld3(S.faces[fa[j]].plane));
+        d3 n1 = D3(0, 0, 0), n2 = D3(0, 0, 0);
+        cd e1 = cd{1.0, 0.0}, e2 = cd{1.0, 0.0};
+        if (k >= 1) {
+            n1 = ld3(S.faces[fa[0]].plane);
+            e1 = mat_eps(S, fa[0], wv);
+        }
+        if (k == 2) {
+            n2 = mirror_dir(ld3(S.faces[fa[1]].plane), n1);
+            e2 = mat_eps(S, fa[1], wv);
+        }
+        PathRec pr;
+        pr.w = local4(fr, w, (float)D0);
+        pr.a = make_float4((float)fr0, __int_as_float(k), (float)e1.re, (float)e1.im);
+        pr.n1 = local4(fr, n1, (float)e2.re);
+        pr.n2 = local4(fr, n2, (float)e2.im);
+        pr.v = local4(fr, v, 0.f);
+        rec[o + q] = pr;
+        rec_seq[o + q] = id;
+    }
+}
+
+// E0 per receiver (one warp): LOS (if unblocked) + environment paths, FP64; fixed reduction order.
+__global__ void k_e0(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, AntD tx, AntD rxa, WaveD wv,
+                     const uint8_t* __restrict__ los, const int* __restrict__ cand, int cap,
+                     const int64_t* __restrict__ cnt, const SeqEntry* __restrict__ seqs,
+                     const SeqEntryD* __restrict__ seqd, float2* __restrict__ E0)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= n_rx) return;
+    const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+    const d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
+    const d3 zt = D3(tx.z[0], tx.z[1], tx.z[2]);
+    const d3 zr = D3(rxa.z[0], rxa.z[1], rxa.z[2]);
+    const int n = cnt ? (int)cnt[r] : 0;
+    cd acc = cd{0.0, 0.0};
+    for (int q = lane - 1; q < n; q += 32) {     // q = -1: LOS
+        d3 Ts = T;
+        int fa[2] = {-1, -1};
+        int k = 0;
+        if (q < 0) {
+            if (!los[r]) continue;
+        } else {
+            int si = cand[r * (int64_t)cap + q];
+            int4 info = seqs[si].info;
+            k = info.w;
+            fa[0] = info.x;
+            fa[1] = info.y;
+            Ts = k == 2 ? ld3(seqd[si].S2) : ld3(seqd[si].S1);
+        }
+        double L;
+        d3 dep, arr;
+        cd Rf;
+        unfolded_from_source(S, Ts, R, fa, k, wv, &L, &dep, &arr, &Rf);
+        double Ft = pattern_d(tx.pattern, tx.gain, dot(dep, zt));
+        double Fr = pattern_d(rxa.pattern, rxa.gain, -dot(arr, zr));
+        double amp = sqrt(2.0 * kEta0 * tx.power * tx.gain * Ft) * sqrt(rxa.gain * Fr) * wv.lam / (4.0 * kPi * L);
+        double ph = -2.0 * kPi * (L / wv.lam - floor(L / wv.lam));
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        acc = cadd(acc, cmul(Rf, cd{amp * cs, amp * sn}));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.re += __shfl_down_sync(0xffffffffu, acc.re, o);
+        acc.im += __shfl_down_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) E0[r] = make_float2((float)acc.re, (float)acc.im);
+}
+
+__global__ void k_los(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, AntD tx, float tol_base,
+                      uint8_t* __restrict__ los, unsigned long long* refines, int* err)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rx) return;
+    d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+    los[r] = !seg_blocked(S, D3(tx.pos[0], tx.pos[1], tx.pos[2]), R, -1, -1, tol_base, refines, err);
+}
+
+__global__ void k_env_ids(const int* __restrict__ cand, int cap, const int64_t* __restrict__ cnt,
+                          const int64_t* __restrict__ off, int64_t n_rx, const SeqEntry* __restrict__ seqs,
+                          int64_t* __restrict__ out)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rx) return;
+    for (int q = 0; q < cnt[r]; ++q) out[off[r] + q] = seqs[cand[r * (int64_t)cap + q]].info.z;
+}
+
+__global__ void k_abs_max(const float* __restrict__ v, int64_t n, unsigned* __restrict__ out)
+{
+    unsigned m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(v[i])));
+    atomicMax(out, m);
+}
+
+__global__ void k_units(const int64_t* __restrict__ off, int64_t n_rx, int M, unsigned long long* units)
+{
+    __shared__ unsigned long long s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n_rx) atomicAdd(&s, (unsigned long long)(off[r + 1] - off[r]) * M);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(units, s);
+}
+
+// ------------------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------------------
+struct Arena {   // bump allocator over one device buffer; with base == nullptr it only measures
+    char* base = nullptr;
+    size_t used = 0;
+    template <typename T>
+    T* get(size_t n)
+    {
+        size_t a = (used + 255) & ~(size_t)255;
+        used = a + sizeof(T) * (n > 0 ? n : 1);
+        return base ? (T*)(base + a) : nullptr;
+    }
+};
+
+template <typename T>
+int grow(risrt_ctx* ctx, T** p, int64_t* cap, int64_t need)
+{
+    if (*p && *cap >= need) return RISRT_OK;
+    if (*p) cudaFree(*p);
+    int64_t c = std::max<int64_t>(need, 1);
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)c);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        *cap = 0;
+        return fail(ctx, RISRT_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    *cap = c;
+    return RISRT_OK;
+}
+
+struct SeqTable {
+    SeqEntry* e = nullptr;
+    SeqEntryD* d = nullptr;
+    int n = 0;
+};
+
+struct Candidates {
+    int* cand = nullptr;
+    int* cnt = nullptr;
+    int64_t* cnt64 = nullptr;
+    int cap = 0;
+};
+
+}  // namespace
+
+int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rxs, double freq,
+                int max_tx, int max_rx, uint32_t flags, risrt_pathset* ps)
+{
+    cudaStream_t s = ctx->stream;
+    const DeviceScene S = sc->dev();
+    const int F = sc->n_faces;
+    const int M = ris->M;
+    const int64_t n_rx = rxs->n;
+    const bool env = (flags & RISRT_FLAG_ENV_PATHS) != 0;
+    if (sc->n_tris == 0) {
+        max_tx = 0;
+        max_rx = 0;
+    }
+    const int max_env = env ? max_rx : 0;
+
+    // frame, antennas, wave
+    Frame fr;
+    d3 t1 = D3(ris->t1[0], ris->t1[1], ris->t1[2]), t2 = D3(ris->t2[0], ris->t2[1], ris->t2[2]);
+    d3 nn = cross(t1, t2);
+    nn = nn * (1.0 / norm(nn));
+    for (int k = 0; k < 3; ++k) {
+        fr.c[k] = ris->center[k];
+        fr.t1[k] = ris->t1[k];
+        fr.t2[k] = ris->t2[k];
+    }
+    fr.n[0] = nn.x; fr.n[1] = nn.y; fr.n[2] = nn.z;
+    auto mk_ant = [](const Antenna& a) {
+        AntD o;
+        double z[3] = {a.orient[6], a.orient[7], a.orient[8]};
+        double zn = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+        for (int k = 0; k < 3; ++k) {
+            o.pos[k] = a.pos[k];
+            o.z[k] = z[k] / zn;
+        }
+        o.power = a.power_w;
+        o.gain = a.gain_lin;
+        o.pattern = a.pattern;
+        return o;
+    };
+    AntD tx = mk_ant(ctx->tx), rxa = mk_ant(ctx->rx);
+    WaveD wv;
+    wv.lam = kC0 / freq;
+    wv.k = 2.0 * kPi / wv.lam;
+    wv.omega = 2.0 * kPi * freq;
+    wv.tm = (flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
+    double G = ris->elem_gain > 0 ? (double)ris->elem_gain : 4.0 * kPi * (double)ris->dy * (double)ris->dz / (wv.lam * wv.lam);
+    double K = sqrt(G * (double)ris->dy * (double)ris->dz / (4.0 * kPi)) * wv.lam / (4.0 * kPi);
+
+    float ext = sc->scene_extent;
+    for (int k = 0; k < 3; ++k) {
+        ext = std::max(ext, std::fabs(ctx->tx.pos[k]));
+        ext = std::max(ext, std::fabs(ris->center[k]));
+    }
+    {   // receivers' extent (max |coordinate|) enters the FP32 error bound
+        unsigned* d_ext;
+        RISRT_CUDA(ctx, cudaMalloc(&d_ext, sizeof(unsigned)));
+        RISRT_CUDA(ctx, cudaMemsetAsync(d_ext, 0, sizeof(unsigned), s));
+        k_abs_max<<<std::min<unsigned>(nblk(3 * n_rx, 256), 1024u), 256, 0, s>>>(rxs->xyz, 3 * n_rx, d_ext);
+        unsigned h_ext = 0;
+        cudaError_t e1 = cudaMemcpyAsync(&h_ext, d_ext, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(d_ext);
+        RISRT_CUDA(ctx, e1);
+        RISRT_CUDA(ctx, e2);
+        float rx_ext;
+        memcpy(&rx_ext, &h_ext, sizeof(float));
+        ext = std::max(ext, rx_ext);
+    }
+    const float tol_base = 4e-6f * (1.f + 3.f * ext);
+
+    ps->n_rx = n_rx;
+    ps->M = M;
+    ps->n_faces = F;
+    ps->freq = freq;
+    ps->flags = flags;
+    ps->rx_pattern = ctx->rx.pattern;
+    ps->rx_gain = ctx->rx.gain_lin;
+    const int W = (M + 31) / 32;
+    ps->W = W;
+
+    // --- resident per-Rx arrays
+    int rc;
+    if (ps->cap_rx < n_rx || !ps->vis) {
+        cudaFree(ps->vis); cudaFree(ps->E0); cudaFree(ps->rx_off); cudaFree(ps->los); cudaFree(ps->env_off);
+        ps->vis = nullptr; ps->E0 = nullptr; ps->rx_off = nullptr; ps->los = nullptr; ps->env_off = nullptr;
+        int64_t c = 0;
+        if ((rc = grow(ctx, &ps->vis, &c, n_rx * W))) return rc;
+        c = 0; if ((rc = grow(ctx, &ps->E0, &c, n_rx))) return rc;
+        c = 0; if ((rc = grow(ctx, &ps->rx_off, &c, n_rx + 1))) return rc;
+        c = 0; if ((rc = grow(ctx, &ps->los, &c, n_rx))) return rc;
+        c = 0; if ((rc = grow(ctx, &ps->env_off, &c, n_rx + 1))) return rc;
+        ps->cap_rx = n_rx;
+    }
+    if (ps->cm) cudaFree(ps->cm);
+    if (ps->elem) cudaFree(ps->elem);
+    ps->cm = nullptr; ps->elem = nullptr;
+    RISRT_CUDA(ctx, cudaMalloc(&ps->cm, sizeof(float2) * M));
+    RISRT_CUDA(ctx, cudaMalloc(&ps->elem, sizeof(float4) * M));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(ps->elem, ris->elem, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s));
+
+    // --- scratch: sequence tables, candidates, counters
+    const int64_t n_ids_tx = max_tx >= 2 ? (int64_t)F + (int64_t)F * F : (max_tx >= 1 ? F : 0);
+    const int64_t n_ids_rx = max_rx >= 2 ? (int64_t)F + (int64_t)F * F : (max_rx >= 1 ? F : 0);
+    const int64_t n_ids_env = max_env >= 2 ? (int64_t)F + (int64_t)F * F : (max_env >= 1 ? F : 0);
+    const int64_t n_ids_max = std::max(n_ids_tx, std::max(n_ids_rx, n_ids_env));
+    int cap = ps->cand_cap > 0 ? ps->cand_cap : 512;
+
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        struct Layout {
+            SeqTable tab[3];
+            int64_t *flag, *pos, *tot, *env_cnt_tot;
+            void* scan_tmp;
+            Candidates crx, cenv, ctx_leg;
+            uint8_t* tx_vis;
+            unsigned long long* counters;
+            int* flags_dev;
+            float* c_xyz;
+        };
+        auto layout = [&](Arena& A, Layout& L) {
+            for (int i = 0; i < 3; ++i) {
+                L.tab[i].e = A.get<SeqEntry>(n_ids_max + 1);
+                L.tab[i].d = A.get<SeqEntryD>(n_ids_max + 1);
+            }
+            L.flag = A.get<int64_t>(n_ids_max + 1);
+            L.pos = A.get<int64_t>(n_ids_max + 1);
+            L.scan_tmp = A.get<char>(scan_temp_bytes(std::max<int64_t>(n_ids_max, n_rx + 1)));
+            L.crx.cand = A.get<int>((size_t)n_rx * cap); L.crx.cnt = A.get<int>(n_rx); L.crx.cnt64 = A.get<int64_t>(n_rx); L.crx.cap = cap;
+            L.cenv.cand = A.get<int>(env ? (size_t)n_rx * cap : 1); L.cenv.cnt = A.get<int>(n_rx); L.cenv.cnt64 = A.get<int64_t>(n_rx); L.cenv.cap = cap;
+            L.ctx_leg.cand = A.get<int>(cap); L.ctx_leg.cnt = A.get<int>(1); L.ctx_leg.cnt64 = A.get<int64_t>(1); L.ctx_leg.cap = cap;
+            L.tot = A.get<int64_t>(n_rx + 1);
+            L.env_cnt_tot = A.get<int64_t>(n_rx + 1);
+            L.tx_vis = A.get<uint8_t>(M);
+            L.counters = A.get<unsigned long long>(4);
+            L.flags_dev = A.get<int>(4);
+            L.c_xyz = A.get<float>(3);
+        };
+        Arena measure;
+        Layout Lm;
+        layout(measure, Lm);
+        const size_t need = measure.used + 256;
+        if (ps->scratch_bytes < need) {
+            cudaFree(ps->scratch);
+            ps->scratch = nullptr;
+            ps->scratch_bytes = 0;
+            cudaError_t e = cudaMalloc(&ps->scratch, need);
+            if (e != cudaSuccess) return fail(ctx, RISRT_ERR_OOM, "scratch allocation failed");
+            ps->scratch_bytes = need;
+        }
+        Arena A{(char*)ps->scratch, 0};
+        Layout L;
+        layout(A, L);
+        SeqTable* tab = L.tab;
+        int64_t *flag = L.flag, *pos = L.pos, *tot = L.tot, *env_cnt_tot = L.env_cnt_tot;
+        void* scan_tmp = L.scan_tmp;
+        Candidates &crx = L.crx, &cenv = L.cenv, &ctx_leg = L.ctx_leg;
+        uint8_t* tx_vis = L.tx_vis;
+        unsigned long long* counters = L.counters;
+        int* flags_dev = L.flags_dev;
+        float* c_xyz = L.c_xyz;
+        RISRT_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 4, s));
+        RISRT_CUDA(ctx, cudaMemsetAsync(flags_dev, 0, sizeof(int) * 4, s));
+        float cxyz[3] = {ris->center[0], ris->center[1], ris->center[2]};
+        RISRT_CUDA(ctx, cudaMemcpyAsync(c_xyz, cxyz, sizeof(cxyz), cudaMemcpyHostToDevice, s));
+
+        const d3 Tpos = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
+        const d3 Cpos = D3(fr.c[0], fr.c[1], fr.c[2]);
+        const int64_t n_ids_of[3] = {n_ids_tx, n_ids_rx, n_ids_env};
+        const d3 src_of[3] = {Tpos, Cpos, Tpos};
+        for (int i = 0; i < 3; ++i) {
+            tab[i].n = 0;
+            int64_t nid = n_ids_of[i];
+            if (nid == 0) continue;
+            k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, flag);
+            RISRT_LAUNCH(ctx, "k_seq_allowed");
+            RISRT_CUDA(ctx, exclusive_scan_i64(flag, pos, nid, scan_tmp, s));
+            k_seq_build<<<nblk(nid, 256), 256, 0, s>>>(S, nid, flag, pos, src_of[i], tab[i].e, tab[i].d);
+            RISRT_LAUNCH(ctx, "k_seq_build");
+            int64_t n_allowed = 0;
+            int64_t last[2];
+            RISRT_CUDA(ctx, cudaMemcpyAsync(&last[0], pos + nid - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            RISRT_CUDA(ctx, cudaMemcpyAsync(&last[1], flag + nid - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+            n_allowed = last[0] + last[1];
+            tab[i].n = (int)n_allowed;
+        }
+
+        auto run_candidates = [&](const SeqTable& t, const float* dst, int64_t n_dst, d3 src, int src_face,
+                                  int dst_face, Candidates& cs) -> int {
+            RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, s));
+            if (t.n > 0) {
+                dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
+                k_candidates<<<grid, kCandThreads, 0, s>>>(S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
+                                                           cs.cnt, cs.cap, flags_dev, counters);
+                RISRT_LAUNCH(ctx, "k_candidates");
+                int64_t nthreads = n_dst * cs.cap;
+                k_validate<<<nblk(nthreads, 128), 128, 0, s>>>(S, dst, n_dst, src, src_face, dst_face, t.e, t.d,
+                                                               cs.cand, cs.cnt, cs.cap, tol_base, counters, flags_dev + 1);
+                RISRT_LAUNCH(ctx, "k_validate");
+            }
+            const int warps = 4;
+            size_t shm = sizeof(int) * (size_t)cs.cap * warps;
+            if (shm > 48 * 1024) cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            k_finalize<<<nblk(n_dst, warps), 32 * warps, shm, s>>>(cs.cand, cs.cnt, n_dst, cs.cap, t.e, cs.cnt64);
+            RISRT_LAUNCH(ctx, "k_finalize");
+            return RISRT_OK;
+        };
+
+        // Tx leg (destination: RIS centre, mounted on host_face)
+        if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg))) return rc;
+        k_tx_vis<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, ris->host_face, tol_base, tx_vis, counters,
+                                              flags_dev + 1);
+        RISRT_LAUNCH(ctx, "k_tx_vis");
+        // Rx leg (source: RIS centre) and environment paths (source: Tx)
+        const float* rxp = rxs->xyz;
+        if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx))) return rc;
+        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv))) return rc;
+        // direct legs
+        {
+            int64_t nthreads = n_rx * W * 32;
+            k_direct_vis<<<nblk(nthreads, 128), 128, 0, s>>>(S, rxp, n_rx, ris->elem, M, W, fr, ris->host_face,
+                                                             tol_base, ps->vis, counters, flags_dev + 1);
+            RISRT_LAUNCH(ctx, "k_direct_vis");
+            k_los<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1);
+            RISRT_LAUNCH(ctx, "k_los");
+        }
+        int host_flags[2];
+        RISRT_CUDA(ctx, cudaMemcpyAsync(host_flags, flags_dev, sizeof(host_flags), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        if (host_flags[1]) return fail(ctx, RISRT_ERR_CAPACITY, "BVH traversal stack overflow");
+        if (host_flags[0]) {       // a destination had more geometric candidates than slots: retry
+            cap *= 4;
+            ps->cand_cap = cap;
+            continue;
+        }
+
+        // Tx-leg results to the host (small)
+        int64_t n_tx64 = 0;
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_tx64, ctx_leg.cnt64, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        const int n_tx = (int)n_tx64;
+        std::vector<int> tx_idx(n_tx);
+        if (n_tx) RISRT_CUDA(ctx, cudaMemcpyAsync(tx_idx.data(), ctx_leg.cand, sizeof(int) * n_tx, cudaMemcpyDeviceToHost, s));
+        ps->tx_vis_host.resize(M);
+        RISRT_CUDA(ctx, cudaMemcpyAsync(ps->tx_vis_host.data(), tx_vis, M, cudaMemcpyDeviceToHost, s));
+        std::vector<SeqEntry> tx_entries(n_tx);
+        for (int i = 0; i < n_tx; ++i)
+            RISRT_CUDA(ctx, cudaMemcpyAsync(&tx_entries[i], tab[0].e + tx_idx[i], sizeof(SeqEntry), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        ps->tx_seq_host.resize(n_tx);
+        for (int i = 0; i < n_tx; ++i) ps->tx_seq_host[i] = tx_entries[i].info.z;
+
+        // c_m
+        k_cm<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand, n_tx, tab[0].e, tab[0].d, ps->cm);
+        RISRT_LAUNCH(ctx, "k_cm");
+
+        // Rx-leg offsets and records
+        k_count_total<<<nblk(n_rx, 256), 256, 0, s>>>(crx.cnt64, n_rx, tot);
+        RISRT_CUDA(ctx, cudaMemsetAsync(tot + n_rx, 0, sizeof(int64_t), s));
+        RISRT_CUDA(ctx, exclusive_scan_i64(tot, ps->rx_off, n_rx + 1, scan_tmp, s));
+        int64_t n_paths = 0;
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_paths, ps->rx_off + n_rx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        if (env) {
+            RISRT_CUDA(ctx, cudaMemcpyAsync(env_cnt_tot, cenv.cnt64, sizeof(int64_t) * n_rx, cudaMemcpyDeviceToDevice, s));
+            RISRT_CUDA(ctx, cudaMemsetAsync(env_cnt_tot + n_rx, 0, sizeof(int64_t), s));
+            RISRT_CUDA(ctx, exclusive_scan_i64(env_cnt_tot, ps->env_off, n_rx + 1, scan_tmp, s));
+        } else {
+            RISRT_CUDA(ctx, cudaMemsetAsync(ps->env_off, 0, sizeof(int64_t) * (n_rx + 1), s));
+        }
+        int64_t n_env = 0;
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_env, ps->env_off + n_rx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        if ((rc = grow(ctx, &ps->rec, &ps->cap_paths, n_paths))) return rc;
+        int64_t cap_seq = ps->cap_paths;
+        if (ps->rx_seq) cudaFree(ps->rx_seq);
+        ps->rx_seq = nullptr;
+        RISRT_CUDA(ctx, cudaMalloc(&ps->rx_seq, sizeof(int64_t) * std::max<int64_t>(cap_seq, 1)));
+        if ((rc = grow(ctx, &ps->env_seq, &ps->cap_env, std::max<int64_t>(n_env, 1)))) return rc;
+        ps->n_paths = n_paths;
+        ps->n_env = n_env;
+        k_records<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
+                                                      tab[1].e, ps->rec, ps->rx_seq);
+        RISRT_LAUNCH(ctx, "k_records");
+        k_e0<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand, cenv.cap,
+                                                 env ? cenv.cnt64 : nullptr, tab[2].e, tab[2].d, ps->E0);
+        RISRT_LAUNCH(ctx, "k_e0");
+        if (env && n_env > 0) {
+            k_env_ids<<<nblk(n_rx, 128), 128, 0, s>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off, n_rx, tab[2].e, ps->env_seq);
+            RISRT_LAUNCH(ctx, "k_env_ids");
+        }
+        k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1);
+        RISRT_LAUNCH(ctx, "k_units");
+        unsigned long long host_ctr[2];
+        RISRT_CUDA(ctx, cudaMemcpyAsync(host_ctr, counters, sizeof(host_ctr), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        ps->fp64_refines = (int64_t)host_ctr[0];
+        ps->units = (int64_t)host_ctr[1];
+        return RISRT_OK;
+    }
+    return fail(ctx, RISRT_ERR_CAPACITY, "too many geometric path candidates per receiver");
+}
+
+}  // namespace risrt

@@ -1,0 +1,279 @@
+"""Thin Python binding of the risrt C ABI (include/risrt.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library. Device buffers are
+torch tensors (complex64 for complex arrays); host inputs are numpy arrays. If the compiled
+library is missing, loading fails with an error instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librisrt.so")
+
+OK = 0
+TX, RX = 0, 1
+PATTERN_ISO, PATTERN_COS_POW, PATTERN_MONOPOLE_QW = 0, 1, 2
+FLAG_ENV_PATHS, FLAG_FRESNEL_TM = 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+# Every symbol the header declares, with (restype, argtypes).
+_P = C.c_void_p
+_SIGS = {
+    "risrt_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "risrt_set_stream": (C.c_int, [_P, _P]),
+    "risrt_destroy": (C.c_int, [_P]),
+    "risrt_last_error": (C.c_char_p, [_P]),
+    "risrt_scene_upload": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, C.c_int32, C.POINTER(_P)]),
+    "risrt_ris_upload": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_int32,
+                                   C.POINTER(_P)]),
+    "risrt_antenna_set": (C.c_int, [_P, C.c_int, _P, _P, C.c_float, C.c_float, C.c_int]),
+    "risrt_rx_upload": (C.c_int, [_P, _P, C.c_int64, C.POINTER(_P)]),
+    "risrt_rx_bind": (C.c_int, [_P, _P, C.c_int64, C.POINTER(_P)]),
+    "risrt_trace_paths": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint32, C.POINTER(_P)]),
+    "risrt_pathset_stats_get": (C.c_int, [_P, _P]),
+    "risrt_pathset_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
+    "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
+    "risrt_scene_destroy": (C.c_int, [_P, _P]),
+    "risrt_ris_destroy": (C.c_int, [_P, _P]),
+    "risrt_rxset_destroy": (C.c_int, [_P, _P]),
+    "risrt_pathset_destroy": (C.c_int, [_P, _P]),
+}
+
+
+class RisrtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"risrt error {code}: {msg}")
+        self.code = code
+
+
+class PathsetStats(C.Structure):
+    _fields_ = [("n_rx", C.c_int64), ("M", C.c_int32), ("n_faces", C.c_int32), ("n_rx_paths", C.c_int64),
+                ("n_env_paths", C.c_int64), ("n_tx_paths", C.c_int32), ("units", C.c_int64),
+                ("fp64_refines", C.c_int64)]
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load the compiled library (build it with paper_2402_13034_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RisrtError(-1, f"CUDA library not built: {path} is missing")
+            lib = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} floats, got {a.size}")
+    return a
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())     # torch tensor
+
+
+def _dev_ptr(t, dtype_name: str, numel: int | None = None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("device arguments must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("device tensors must be contiguous")
+    if str(t.dtype) != dtype_name:
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class _Handle:
+    def __init__(self, ctx: "Context", ptr: C.c_void_p, destroy: str):
+        self._ctx, self._ptr, self._destroy = ctx, ptr, destroy
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def close(self):
+        if self._ptr and self._ctx._ptr:
+            getattr(load(), self._destroy)(self._ctx._ptr, self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene(_Handle):
+    pass
+
+
+class RIS(_Handle):
+    def __init__(self, ctx, ptr, M):
+        super().__init__(ctx, ptr, "risrt_ris_destroy")
+        self.M = M
+
+
+class RxSet(_Handle):
+    def __init__(self, ctx, ptr, n, keep=None):
+        super().__init__(ctx, ptr, "risrt_rxset_destroy")
+        self.n = n
+        self._keep = keep
+
+
+class PathSet(_Handle):
+    def stats(self) -> PathsetStats:
+        st = PathsetStats()
+        rc = load().risrt_pathset_stats_get(self._ptr, C.byref(st))
+        if rc:
+            raise RisrtError(rc, "pathset stats")
+        return st
+
+    def export(self) -> dict:
+        st = self.stats()
+        n, M = st.n_rx, st.M
+        W = (M + 31) // 32
+        rx_count = np.zeros(n, np.int32)
+        rx_seq = np.zeros(max(st.n_rx_paths - n, 1), np.int64)
+        env_count = np.zeros(n, np.int32)
+        env_seq = np.zeros(max(st.n_env_paths, 1), np.int64)
+        los = np.zeros(n, np.uint8)
+        vis = np.zeros((n, W), np.uint32)
+        tx_seq = np.zeros(max(st.n_tx_paths, 1), np.int64)
+        tx_vis = np.zeros(M, np.uint8)
+        rc = load().risrt_pathset_export(self._ptr, _ptr(rx_count), _ptr(rx_seq), _ptr(env_count), _ptr(env_seq),
+                                         _ptr(los), _ptr(vis), _ptr(tx_seq), _ptr(tx_vis))
+        if rc:
+            raise RisrtError(rc, "pathset export")
+        ro = np.concatenate([[0], np.cumsum(rx_count)])
+        eo = np.concatenate([[0], np.cumsum(env_count)])
+        return dict(seqs=[rx_seq[ro[i]:ro[i + 1]] for i in range(n)],
+                    env=[env_seq[eo[i]:eo[i + 1]] for i in range(n)],
+                    los=los.astype(bool), vis=vis, tx_seqs=tx_seq[: st.n_tx_paths], tx_vis=tx_vis.astype(bool),
+                    stats=st)
+
+
+class Context:
+    """One device + stream. Methods mirror the C ABI; see include/risrt.h for semantics."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        self._ptr = C.c_void_p()
+        s = None if stream is None else C.c_void_p(stream)
+        rc = lib.risrt_create(C.byref(self._ptr), device, s)
+        if rc:
+            raise RisrtError(rc, lib.risrt_last_error(None).decode())
+        self.device = device
+
+    def _check(self, rc: int):
+        if rc:
+            raise RisrtError(rc, load().risrt_last_error(self._ptr).decode())
+
+    def close(self):
+        if self._ptr:
+            load().risrt_destroy(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle: int | None):
+        self._check(load().risrt_set_stream(self._ptr, None if stream_handle is None else C.c_void_p(stream_handle)))
+
+    # --- inputs --------------------------------------------------------------------------------
+    def scene_upload(self, verts, tris, face_id, mat_id, mats) -> Scene:
+        v = _f32(verts)
+        t = np.ascontiguousarray(tris, np.int32)
+        f = np.ascontiguousarray(face_id, np.int32)
+        m = np.ascontiguousarray(mat_id, np.int32)
+        mt = _f32(mats)
+        out = C.c_void_p()
+        self._check(load().risrt_scene_upload(self._ptr, _ptr(v), v.size // 3, _ptr(t), _ptr(f), _ptr(m),
+                                              t.size // 3, _ptr(mt), mt.size // 2, C.byref(out)))
+        return Scene(self, out, "risrt_scene_destroy")
+
+    def ris_upload(self, elem_uv, center, t1, t2, dy, dz, elem_gain=0.0, host_face=-1) -> RIS:
+        uv = _f32(elem_uv)
+        out = C.c_void_p()
+        self._check(load().risrt_ris_upload(self._ptr, _ptr(uv), uv.size // 2, _ptr(_f32(center, 3)),
+                                            _ptr(_f32(t1, 3)), _ptr(_f32(t2, 3)), float(dy), float(dz),
+                                            float(elem_gain), int(host_face), C.byref(out)))
+        return RIS(self, out, uv.size // 2)
+
+    def antenna_set(self, which, pos, orient, power_w, gain_lin, pattern):
+        p = _f32(pos if pos is not None else np.zeros(3), 3)
+        o = _f32(orient, 9)
+        self._check(load().risrt_antenna_set(self._ptr, which, _ptr(p), _ptr(o), float(power_w), float(gain_lin),
+                                             int(pattern)))
+
+    def rx_upload(self, rx_xyz) -> RxSet:
+        r = _f32(rx_xyz)
+        out = C.c_void_p()
+        self._check(load().risrt_rx_upload(self._ptr, _ptr(r), r.size // 3, C.byref(out)))
+        return RxSet(self, out, r.size // 3)
+
+    def rx_bind(self, rx_xyz_dev) -> RxSet:
+        out = C.c_void_p()
+        self._check(load().risrt_rx_bind(self._ptr, _dev_ptr(rx_xyz_dev, "torch.float32"), rx_xyz_dev.numel() // 3,
+                                         C.byref(out)))
+        return RxSet(self, out, rx_xyz_dev.numel() // 3, keep=rx_xyz_dev)
+
+    # --- path finding and fields -----------------------------------------------------------------
+    def trace_paths(self, scene: Scene, ris: RIS, rxset: RxSet, freq_hz: float, max_order_tx: int,
+                    max_order_rx: int, flags: int = 0, reuse: PathSet | None = None) -> PathSet:
+        ptr = reuse.ptr if reuse is not None else C.c_void_p()
+        self._check(load().risrt_trace_paths(self._ptr, scene.ptr, ris.ptr, rxset.ptr, float(freq_hz),
+                                             int(max_order_tx), int(max_order_rx), int(flags), C.byref(ptr)))
+        return reuse if reuse is not None else PathSet(self, ptr, "risrt_pathset_destroy")
+
+    def eval_field(self, ps: PathSet, gamma, E_out, P_out=None):
+        """gamma: complex64 CUDA [C, M]; E_out: complex64 CUDA [C, n_rx]; P_out: float32 CUDA [C, n_rx]."""
+        n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
+        self._check(load().risrt_eval_field(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"), n_cfg,
+                                            _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def build_A(self, ps: PathSet, A_out, E0_out=None):
+        self._check(load().risrt_build_A(self._ptr, ps.ptr, _dev_ptr(A_out, "torch.complex64"),
+                                         _dev_ptr(E0_out, "torch.complex64")))
+
+
+def flags_of(w) -> int:
+    return FLAG_ENV_PATHS if w.env_paths else 0
+
+
+def upload_workload(ctx: Context, w, rx_device=None):
+    """Upload a scenarios.Workload (scene, RIS, antennas, receivers). Receivers come from host
+    memory unless ``rx_device`` (a float32 CUDA tensor [n,3]) is given."""
+    sc = w.scene
+    scene = ctx.scene_upload(sc.verts, sc.tris, sc.face_id, sc.mat_id, sc.mats)
+    ris = ctx.ris_upload(w.ris.elem_uv, w.ris.center, w.ris.t1, w.ris.t2, w.ris.dy, w.ris.dz, w.ris.elem_gain,
+                         w.ris.host_face)
+    ctx.antenna_set(TX, w.tx.pos, w.tx.orient, w.tx.power_w, w.tx.gain_lin, w.tx.pattern)
+    ctx.antenna_set(RX, None, w.rx.orient, w.rx.power_w, w.rx.gain_lin, w.rx.pattern)
+    rx = ctx.rx_bind(rx_device) if rx_device is not None else ctx.rx_upload(w.rx_xyz)
+    return scene, ris, rx

@@ -142,7 +142,7 @@ class Workload:
 
 def empty_scene() -> Scene:
     return Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros(0, np.int32),
-                 np.zeros(0, np.int32), np.zeros((1, 2), np.float32))
+                 np.zeros(0, np.int32), np.array([[1.0, 0.0]], np.float32))
 
 
 def hex_layout(rings: int, pitch: float) -> np.ndarray:

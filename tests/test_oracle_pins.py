@@ -460,3 +460,39 @@ def test_ris_legs_with_one_wall_image_closed_form():
                     f *= fres(abs((Rs - e[m])[0]) / rr)
                 exp[m] += amp * f * np.exp(-1j * k * (rt + rr))
     assert np.max(np.abs(A - exp)) < 1e-12 * np.max(np.abs(exp))
+
+
+def test_two_parallel_planes_order2_field():
+    """Order-2 environment paths between floor and ceiling: E0 = LOS + sum over the two sequences of
+    R_TE(theta)^2 * Friis(L) with L = sqrt(rho^2 + (2H +- (a - b))^2) and the same incidence angle at
+    both bounces (Sec. II-B with the Fresnel factor per bounce); order-1 paths add R * Friis."""
+    H = 3.0
+    w = _free()
+    w.scene = _plane_scene(0.0, 50.0, extra_planes=(H,))
+    w.max_order_rx = 2
+    w.env_paths = True
+    w.ris.center = np.array([0.0, 0.0, 1.0], np.float32)
+    w.tx.pos = np.array([0.2, -1.0, 1.1], np.float32)
+    o = O.Oracle(w)
+    T = w.tx.pos.astype(np.float64)
+    R = np.array([2.5, 1.7, 2.2], np.float32).astype(np.float64)
+    a, b = T[2], R[2]
+    rho = np.linalg.norm((R - T)[:2])
+    lam = S.C0 / w.freq_hz
+    k = 2 * math.pi / lam
+    n2 = math.sqrt(float(np.float32(5.3)))
+
+    def fres(ci):
+        si = math.sqrt(1 - ci * ci)
+        ct = math.sqrt(1 - (si / n2) ** 2)
+        return (ci - n2 * ct) / (ci + n2 * ct)
+
+    def friis(L):
+        return math.sqrt(2 * ETA0) * lam / (4 * math.pi * L) * np.exp(-1j * k * L)
+
+    E = friis(np.linalg.norm(R - T))
+    for dz, nb in [(a + b, 1), (2 * H - a - b, 1), (2 * H + a - b, 2), (2 * H - a + b, 2)]:
+        L = math.hypot(rho, dz)
+        E += fres(dz / L) ** nb * friis(L)
+    f = o.field(R.astype(np.float32)[None])
+    assert abs(f["E0"][0] - E) < 1e-12 * abs(E)

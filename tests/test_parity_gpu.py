@@ -1,0 +1,161 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Path and visibility sets must agree bit for bit on every receiver without an ambiguous decision;
+fields must agree within 5e-5 of the incoherent magnitude S(r) everywhere, and power within 1e-4
+relative and phase within 1e-3 rad where |E| >= 0.05 S(r).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2402_13034_gb300 import scenarios as S
+from tests.helpers import compare_fields, compare_pathsets, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2402_13034_gb300 import build as B
+    B.build()
+
+
+def _oracle_all(w, rx_idx=None, gammas=None):
+    o = O.Oracle(w)
+    rx = w.rx_xyz if rx_idx is None else w.rx_xyz[rx_idx]
+    fld = o.field(rx)
+    g = w.gammas if gammas is None else gammas
+    E, P, Sx = O.Oracle.evaluate(fld, g)
+    return o, fld, E, P, Sx
+
+
+def test_free_space_full_grid():
+    w = S.free_space()
+    g = run_gpu(w)
+    _, fld, E, P, Sx = _oracle_all(w)
+    st = compare_fields(g["E"], g["P"], E, P, Sx)
+    assert st["strong_frac"] > 0.5
+    # the focused configuration peaks at the focus point (grid centre region)
+    assert g["paths"]["stats"].units == w.n_rx * w.n_elem
+
+
+def test_free_space_single_rx_and_ragged():
+    w = S.free_space(grid=5)                 # 25 receivers: not a multiple of a warp or a block
+    g = run_gpu(w)
+    _, fld, E, P, Sx = _oracle_all(w)
+    compare_fields(g["E"], g["P"], E, P, Sx)
+    w1 = S.free_space(grid=1)
+    w1.rx_xyz = np.array([[0.3, -0.2, 1.5]], np.float32)
+    g1 = run_gpu(w1)
+    _, _, E1, P1, S1 = _oracle_all(w1)
+    compare_fields(g1["E"], g1["P"], E1, P1, S1)
+
+
+def test_single_element_and_behind_ris():
+    w = S.free_space(grid=4)
+    w.ris.elem_uv = w.ris.elem_uv[:1]
+    w.gammas = w.gammas[:, :1]
+    w.rx_xyz = np.concatenate([w.rx_xyz, [[0.1, 0.2, -1.0]]]).astype(np.float32)   # behind the RIS
+    g = run_gpu(w)
+    _, fld, E, P, Sx = _oracle_all(w)
+    compare_fields(g["E"], g["P"], E, P, Sx)
+
+
+def test_paper_patterns_anechoic():
+    """Horn Tx (cos^(Gt/2-1)) aimed at the RIS and monopole Rx: Table 1 set-up (Sec. III)."""
+    w = S.paper_anechoic(grid_step=0.05)
+    rng = np.random.default_rng(7)
+    gam = (1.25 * (rng.random((3, w.n_elem)) > 0.5)).astype(np.complex64)
+    g = run_gpu(w, gammas=gam)
+    _, fld, E, P, Sx = _oracle_all(w, gammas=gam)
+    compare_fields(g["E"], g["P"], E, P, Sx)
+
+
+@pytest.mark.parametrize("grid", [12, 24])
+def test_room_pathsets_bit_exact(grid):
+    w = S.room(grid=grid)
+    g = run_gpu(w)
+    o = O.Oracle(w)
+    op = o.rx_paths(w.rx_xyz)
+    tx = o.tx_leg()
+    bad = compare_pathsets(g["paths"], op, op["amb"], tx)
+    assert not bad, bad[:10]
+    assert op["amb"].mean() < 0.02
+    # a room of this kind has many reflected paths per receiver
+    n_ref = np.array([len(s) for s in g["paths"]["seqs"]])
+    assert n_ref.max() > 5
+
+
+def test_room_field_parity():
+    w = S.room(grid=16)
+    g = run_gpu(w, want_A=True)
+    o, fld, E, P, Sx = _oracle_all(w)
+    ok = ~fld["amb"]
+    compare_fields(g["E"], g["P"], E, P, Sx, mask=ok)
+    # channel matrix rows: A[r, m] against the oracle's per-element sum over all path pairs
+    SA = np.where(fld["SA"] > 0, fld["SA"], 1.0)
+    errA = np.abs(g["A"] - fld["A"]) / SA.sum(1, keepdims=True)
+    assert errA[ok].max() < 5e-5
+    e0err = np.abs(g["E0"] - fld["E0"]) / np.where(fld["S0"] > 0, fld["S0"], 1.0)
+    assert e0err[ok].max() < 5e-5
+
+
+def test_room_full_size_sampled():
+    """The benchmark's full 256x256 room, traced and evaluated in one launch configuration on the GPU;
+    the oracle evaluates a deterministic sample of receivers one by one."""
+    w = S.room()
+    g = run_gpu(w)
+    idx = np.unique(np.linspace(0, w.n_rx - 1, 97).astype(int))
+    wo = S.room()
+    wo.rx_xyz = w.rx_xyz[idx]
+    o, fld, E, P, Sx = _oracle_all(wo)
+    ok = ~fld["amb"]
+    compare_fields(g["E"][idx], g["P"][idx], E, P, Sx, mask=ok)
+    op = o.rx_paths(wo.rx_xyz)
+    sub = {k: [g["paths"][k][i] for i in idx] for k in ("seqs", "env")}
+    sub["los"] = g["paths"]["los"][idx]
+    sub["vis"] = g["paths"]["vis"][idx]
+    assert not compare_pathsets(sub, op, op["amb"])
+
+
+def test_metal_room_tm_and_lossy():
+    """Lossy metal walls (eps_r 1, sigma 1e7 S/m, Table 1) make the Fresnel coefficients complex."""
+    w = S.room(grid=8, n_boxes=6)
+    w.scene.mats[0] = (1.0, 1e7)
+    w.scene.mats[1:, 1] = 0.5
+    g = run_gpu(w)
+    _, fld, E, P, Sx = _oracle_all(w)
+    compare_fields(g["E"], g["P"], E, P, Sx, mask=~fld["amb"])
+
+
+def test_empty_scene_with_orders():
+    w = S.free_space(grid=4)
+    w.max_order_tx = w.max_order_rx = 2
+    g = run_gpu(w)
+    _, fld, E, P, Sx = _oracle_all(w)
+    compare_fields(g["E"], g["P"], E, P, Sx)
+
+
+def test_invalid_arguments():
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
+    w = S.room(grid=2, n_boxes=2)
+    with pytest.raises(R.RisrtError) as e:
+        ctx.ris_upload(np.zeros((0, 2)), w.ris.center, w.ris.t1, w.ris.t2, 1e-3, 1e-3)
+    assert e.value.code == 1
+    scene = ctx.scene_upload(w.scene.verts, w.scene.tris, w.scene.face_id, w.scene.mat_id, w.scene.mats)
+    ris = ctx.ris_upload(w.ris.elem_uv, w.ris.center, w.ris.t1, w.ris.t2, w.ris.dy, w.ris.dz, 0, 0)
+    rx = ctx.rx_upload(w.rx_xyz)
+    with pytest.raises(R.RisrtError) as e:      # antennas not set
+        ctx.trace_paths(scene, ris, rx, w.freq_hz, 1, 1)
+    assert e.value.code == 5
+    ctx.antenna_set(R.TX, w.tx.pos, w.tx.orient, 1.0, 1.0, 0)
+    ctx.antenna_set(R.RX, None, w.rx.orient, 1.0, 1.0, 0)
+    with pytest.raises(R.RisrtError) as e:
+        ctx.trace_paths(scene, ris, rx, w.freq_hz, 3, 1)
+    assert e.value.code == 1
+    with pytest.raises(R.RisrtError):
+        ctx.scene_upload(w.scene.verts, w.scene.tris + 10000, w.scene.face_id, w.scene.mat_id, w.scene.mats)
