@@ -1,0 +1,322 @@
+"""Benchmark of the RIS field hot path on the room workload (127-element hexagonal RIS on one wall of
+a 6x4x3 m room with 40 boxes, 256x256 receivers at 1.2 m, specular order <= 2 on both legs, 28 GHz).
+
+One step = trace_paths (candidates, BVH occlusion, direct-leg visibility, path records, c_m, E0)
++ eval_field for the workload's configurations, with the scene, RIS and receivers resident in HBM.
+Metric: RIS field evaluations per second, one unit = (receiver, RIS element, Rx-leg path, config).
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on the same workload and
+metric (bounded receiver samples per step) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_13034_gb300 import scenarios as S  # noqa: E402
+
+METRIC = "RIS field evals/s (rx*elem*path*config)"
+UNIT = "evals/s"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------------------------
+# algorithmic work per kernel (counted from the formulas, not from the binary)
+# ------------------------------------------------------------------------------------------------
+# FP32 lane operations of one field unit (one Rx-leg term b_mq times Gamma c_m, order-0 isotropic):
+# 2 sub + 3 FMA for L^2, rsqrt, L, cos, sqrt, 2 mul amplitude, 3 FMA + add + div for dL, FMA + round
+# + sub for the phase, sincos (2), complex scale (2 mul), complex c_m product (4) and accumulate (4).
+EVAL_OPS_PER_UNIT = 32
+# One image-method candidate test (Rx x face sequence): same-side test (3 FMA, sub, 2 compares),
+# and for the ~half that pass it the reflection point (sub, div, 3 sub, 3 FMA) and the in-face test
+# of a two-triangle face (6 x (3 FMA + sub) + 2 min + 2 compares): counted as 8 + 0.5 * 40.
+CAND_OPS_PER_TEST = 28
+
+
+def clocks_sampler(path):
+    try:
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def clocks_summary(path, device_index):
+    try:
+        rows = [r.split(",") for r in open(path).read().strip().splitlines()]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(device_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = float(rows[0][2])
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows)}
+    except Exception:
+        return None
+
+
+def cpu_oracle_rate(w, n_cfg, budget_s=15.0, steps=1):
+    """Time the FP64 oracle on deterministic receiver samples of the workload; returns
+    (evals/s, threads, sample description)."""
+    from oracle import oracle as O
+    o = O.Oracle(w)
+    rng_idx = np.arange(w.n_rx)
+
+    def sample(n, k):
+        idx = rng_idx[(np.arange(n) * 7919 + k * 104729) % w.n_rx]
+        return np.unique(idx)
+
+    # calibrate on a few receivers
+    t0 = time.perf_counter()
+    o.field(w.rx_xyz[sample(32, 0)])
+    per_rx = (time.perf_counter() - t0) / 32
+    n = int(max(32, min(w.n_rx, budget_s / max(per_rx, 1e-6))))
+    total_units, total_t = 0, 0.0
+    for k in range(steps):
+        idx = sample(n, k + 1)
+        rx = w.rx_xyz[idx]
+        paths = o.rx_paths(rx)
+        units = sum(w.n_elem * (1 + len(s)) for s in paths["seqs"]) * n_cfg
+        t0 = time.perf_counter()
+        fld = o.field(rx)
+        O.Oracle.evaluate(fld, w.gammas)
+        total_t += time.perf_counter() - t0
+        total_units += units
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return total_units / total_t, threads, f"{len(idx)} of {w.n_rx} receivers per step (stride sample), {steps} step(s)"
+
+
+def run_reference(args, w, n_cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    val, cores, samp = cpu_oracle_rate(w, n_cfg, budget_s=args.ref_budget, steps=max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "n_cfg": n_cfg},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samp},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="risrt", choices=["risrt", "reference"])
+    ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    w = S.room(grid=args.grid)
+    n_cfg = w.gammas.shape[0]
+    if args.impl == "reference":
+        run_reference(args, w, n_cfg)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2402_13034_gb300 import build as B
+    from paper_2402_13034_gb300 import risrt as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = R.Context(local, stream.cuda_stream)
+
+    # each rank processes its own receiver batch (weak scaling): the grid shifted by a rank offset
+    rx_host = w.rx_xyz.copy()
+    if rank:
+        rx_host[:, 0] += 1e-3 * rank
+    rx_dev = torch.from_numpy(rx_host).to(dev)
+    scene, ris, _ = R.upload_workload(ctx, w)
+    rxs = ctx.rx_bind(rx_dev)
+    gam = torch.from_numpy(w.gammas).to(dev)
+    E = torch.empty((n_cfg, w.n_rx), dtype=torch.complex64, device=dev)
+    P = torch.empty((n_cfg, w.n_rx), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    flags = R.flags_of(w)
+
+    ps = None
+
+    def step():
+        nonlocal ps
+        ps = ctx.trace_paths(scene, ris, rxs, w.freq_hz, w.max_order_tx, w.max_order_rx, flags, reuse=ps)
+        ctx.eval_field(ps, gam, E, P)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    units = ps.stats().units * n_cfg
+
+    # timed region: per-step CUDA events on the launching stream, L2 flushed between steps
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            f".clocks_{rank}.csv")
+    sampler = clocks_sampler(clk_path) if rank == 0 else None
+    ctx.profile_enable(True)
+    ctx.profile_reset()
+    launches0 = R.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = R.launch_count() - launches0
+    prof = ctx.profile()
+    ctx.profile_enable(False)
+    if sampler:
+        time.sleep(0.3)
+        sampler.terminate()
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(units)], device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units_all = float(u.item())
+    else:
+        units_all = float(units)
+    ms_per_step = total_ms / args.steps
+    value = units_all * args.steps / (total_ms / 1e3)
+
+    # per-kernel shares and the dominant kernel's roofline (live CUDA-event timing)
+    k_total = sum(v[0] for v in prof.values())
+    stages = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                  "share": v[0] / k_total if k_total else None} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+    peaks = _peaks()
+    st = ps.stats()
+    roof = None
+    if dom:
+        ms_launch = prof[dom][0] / prof[dom][1]
+        clk = clocks_summary(clk_path, local) if rank == 0 else None
+        sm_mhz = (peaks.get("sm_max_mhz") or 2070.0)
+        alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12      # T lane-ops/s: 152 SMs x 128 FP32 lanes x clock
+        if dom == "k_eval":
+            work = st.units * n_cfg * EVAL_OPS_PER_UNIT
+        elif dom == "k_candidates":
+            F = st.n_faces
+            n_seq = F + F * (F - 1)
+            work = w.n_rx * n_seq * CAND_OPS_PER_TEST * (2 if w.env_paths else 1) / max(1, prof[dom][1] / args.steps - 1)
+        else:
+            work = None
+        if work is not None:
+            achieved = work / (ms_launch / 1e3) / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "peak_note": f"FP32 lane-op issue peak at {sm_mhz:.0f} MHz (152 SMs x 128 lanes), derived"}
+        else:
+            roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None}
+
+    # end to end through the C ABI with host buffers (scene, RIS, receivers, configs up; P down)
+    e2e = None
+    if not args.no_e2e:
+        rx_pin = torch.from_numpy(rx_host).pin_memory()
+        g_pin = torch.from_numpy(w.gammas).pin_memory()
+        P_host = torch.empty((n_cfg, w.n_rx), dtype=torch.float32).pin_memory()
+        sc_ = w.scene
+        h2d = (sc_.verts.nbytes + sc_.tris.nbytes + sc_.face_id.nbytes + sc_.mat_id.nbytes + sc_.mats.nbytes
+               + w.ris.elem_uv.nbytes + rx_host.nbytes + w.gammas.nbytes)
+        d2h = P_host.numel() * 4
+
+        def e2e_step():
+            scene2, ris2, _ = R.upload_workload(ctx, w, rx_device=rx_dev)
+            rx2 = ctx.rx_upload(rx_pin.numpy())
+            g2 = g_pin.to(dev, non_blocking=True)
+            ps2 = ctx.trace_paths(scene2, ris2, rx2, w.freq_hz, w.max_order_tx, w.max_order_rx, flags)
+            ctx.eval_field(ps2, g2, E, P)
+            P_host.copy_(P, non_blocking=True)
+            torch.cuda.synchronize()
+            n_units = ps2.stats().units * n_cfg
+            for h in (ps2, rx2, ris2, scene2):
+                h.close()
+            return n_units
+
+        e2e_step()
+        t_e2e, u_e2e = 0.0, 0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            u_e2e += e2e_step()
+            t_e2e += time.perf_counter() - t0
+        e2e = {"value": u_e2e / t_e2e * (world if world > 1 else 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, samp = cpu_oracle_rate(w, n_cfg, budget_s=args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samp}
+
+    if rank == 0:
+        clk = clocks_summary(clk_path, local)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "faces": st.n_faces,
+                           "triangles": int(len(w.scene.tris)), "order_tx": w.max_order_tx,
+                           "order_rx": w.max_order_rx, "env_paths": bool(w.env_paths), "n_cfg": n_cfg,
+                           "units_per_step": units, "rx_paths": st.n_rx_paths, "env_paths_found": st.n_env_paths,
+                           "tx_paths": st.n_tx_paths, "fp64_refines": st.fp64_refines,
+                           "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+                "stages": stages}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -198,6 +198,27 @@ int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma
 int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out);
 
 /* ------------------------------------------------------------------------------------------------
+ * Tracing
+ * ---------------------------------------------------------------------------------------------- */
+
+/* on != 0: bracket every kernel this context launches with CUDA events on its stream and keep the
+ * elapsed time per kernel name (adds two event records per launch; off by default). */
+int risrt_profile_enable(risrt_ctx* ctx, int on);
+
+/* Total elapsed milliseconds and launch count of kernel `name` since the last reset, or of all
+ * kernels when name is NULL. Synchronises the pending events. Unknown names give 0 and 0. */
+int risrt_profile_query(risrt_ctx* ctx, const char* name, double* total_ms, int64_t* launches);
+
+/* Comma-separated names of the kernels timed so far, written to buf (NUL-terminated, truncated to
+ * cap). *needed receives the full length + 1 (may be NULL). */
+int risrt_profile_names(risrt_ctx* ctx, char* buf, size_t cap, size_t* needed);
+
+int risrt_profile_reset(risrt_ctx* ctx);
+
+/* Number of kernels the library has launched in this process (all contexts), for accounting. */
+int risrt_launch_count(int64_t* out);
+
+/* ------------------------------------------------------------------------------------------------
  * Destruction (each synchronises the context stream first; NULL is accepted)
  * ---------------------------------------------------------------------------------------------- */
 int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* scene);

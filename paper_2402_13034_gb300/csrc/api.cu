@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "internal.cuh"
@@ -15,6 +16,46 @@ int fail(risrt_ctx* ctx, int code, const std::string& msg)
     if (ctx) ctx->err = msg;
     else g_create_err = msg;
     return code;
+}
+
+std::atomic<long long> g_launches{0};
+
+void prof_begin(risrt_ctx* ctx, const char* name)
+{
+    if (!ctx || !ctx->profiling) return;
+    KernelPending p;
+    p.name = name;
+    for (cudaEvent_t* ev : {&p.a, &p.b}) {
+        if (!ctx->event_pool.empty()) {
+            *ev = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+        } else if (cudaEventCreate(ev) != cudaSuccess) {
+            return;
+        }
+    }
+    cudaEventRecord(p.a, ctx->stream);
+    ctx->pending.push_back(p);
+}
+
+void prof_end(risrt_ctx* ctx)
+{
+    if (!ctx || !ctx->profiling || ctx->pending.empty()) return;
+    cudaEventRecord(ctx->pending.back().b, ctx->stream);
+}
+
+static void prof_collect(risrt_ctx* ctx)
+{
+    for (KernelPending& p : ctx->pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(p.b);
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        auto& slot = ctx->ktime[p.name];
+        slot.first += ms;
+        slot.second += 1;
+        ctx->event_pool.push_back(p.a);
+        ctx->event_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
 }
 
 int cuda_fail(risrt_ctx* ctx, cudaError_t e, const char* where)
@@ -78,7 +119,68 @@ int risrt_destroy(risrt_ctx* ctx)
     if (!ctx) return RISRT_OK;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (KernelPending& p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
+    return RISRT_OK;
+}
+
+int risrt_profile_enable(risrt_ctx* ctx, int on)
+{
+    RISRT_CHECK_CTX(ctx);
+    ctx->profiling = on != 0;
+    return RISRT_OK;
+}
+
+int risrt_profile_query(risrt_ctx* ctx, const char* name, double* total_ms, int64_t* launches)
+{
+    RISRT_CHECK_CTX(ctx);
+    prof_collect(ctx);
+    double ms = 0.0;
+    int64_t n = 0;
+    for (auto& kv : ctx->ktime) {
+        if (name && kv.first != name) continue;
+        ms += kv.second.first;
+        n += kv.second.second;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = n;
+    return RISRT_OK;
+}
+
+int risrt_profile_names(risrt_ctx* ctx, char* buf, size_t cap, size_t* needed)
+{
+    RISRT_CHECK_CTX(ctx);
+    prof_collect(ctx);
+    std::string all;
+    for (auto& kv : ctx->ktime) {
+        if (!all.empty()) all += ",";
+        all += kv.first;
+    }
+    if (needed) *needed = all.size() + 1;
+    if (buf && cap > 0) {
+        size_t n = std::min(cap - 1, all.size());
+        memcpy(buf, all.data(), n);
+        buf[n] = 0;
+    }
+    return RISRT_OK;
+}
+
+int risrt_profile_reset(risrt_ctx* ctx)
+{
+    RISRT_CHECK_CTX(ctx);
+    prof_collect(ctx);
+    ctx->ktime.clear();
+    return RISRT_OK;
+}
+
+int risrt_launch_count(int64_t* out)
+{
+    if (!out) return RISRT_ERR_INVALID_ARG;
+    *out = g_launches.load();
     return RISRT_OK;
 }
 

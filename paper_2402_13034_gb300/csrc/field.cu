@@ -206,9 +206,9 @@ int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int
     for (int c0 = 0; c0 < n_cfg; c0 += kMaxCfgPerPass) {
         const int nc = std::min(kMaxCfgPerPass, n_cfg - c0);
 #define RISRT_EVAL(PAT, NCV)                                                                                  \
-    k_eval<PAT, NCV><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, \
+    RISRT_KERNEL(ctx, "k_eval", (k_eval<PAT, NCV><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, \
                                                                 ps->cm, gamma, ps->M, ps->n_rx, c0, nc, ps->E0, E, P, \
-                                                                inv_lam, ps->rx_gain, tm, inv_2eta0)
+                                                                inv_lam, ps->rx_gain, tm, inv_2eta0)))
 #define RISRT_EVAL_NC(PAT)           \
     do {                             \
         if (nc == 1) RISRT_EVAL(PAT, 1); \
@@ -222,7 +222,6 @@ int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int
         }
 #undef RISRT_EVAL_NC
 #undef RISRT_EVAL
-        RISRT_LAUNCH(ctx, "k_eval");
     }
     return RISRT_OK;
 }
@@ -232,21 +231,16 @@ int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0)
     const float inv_lam = (float)(ps->freq / kC0);
     const int tm = (ps->flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
     const unsigned grid = nblk(ps->n_rx, kEvalWarps);
+#define RISRT_BUILD_A(PAT)                                                                                  \
+    RISRT_KERNEL(ctx, "k_build_A", (k_build_A<PAT><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(                       \
+                                       ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, ps->M, ps->n_rx, A,   \
+                                       inv_lam, ps->rx_gain, tm)))
     switch (ps->rx_pattern) {
-        case RISRT_PATTERN_COS_POW:
-            k_build_A<RISRT_PATTERN_COS_POW><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
-                ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, ps->M, ps->n_rx, A, inv_lam, ps->rx_gain, tm);
-            break;
-        case RISRT_PATTERN_MONOPOLE_QW:
-            k_build_A<RISRT_PATTERN_MONOPOLE_QW><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
-                ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, ps->M, ps->n_rx, A, inv_lam, ps->rx_gain, tm);
-            break;
-        default:
-            k_build_A<RISRT_PATTERN_ISO><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
-                ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, ps->M, ps->n_rx, A, inv_lam, ps->rx_gain, tm);
-            break;
+        case RISRT_PATTERN_COS_POW: RISRT_BUILD_A(RISRT_PATTERN_COS_POW); break;
+        case RISRT_PATTERN_MONOPOLE_QW: RISRT_BUILD_A(RISRT_PATTERN_MONOPOLE_QW); break;
+        default: RISRT_BUILD_A(RISRT_PATTERN_ISO); break;
     }
-    RISRT_LAUNCH(ctx, "k_build_A");
+#undef RISRT_BUILD_A
     if (E0) RISRT_CUDA(ctx, cudaMemcpyAsync(E0, ps->E0, sizeof(float2) * ps->n_rx, cudaMemcpyDeviceToDevice, ctx->stream));
     return RISRT_OK;
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -111,12 +113,22 @@ struct Antenna {
     bool set;
 };
 
+struct KernelPending {
+    const char* name;
+    cudaEvent_t a, b;
+};
+
 struct risrt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     std::string err;
     Antenna tx{}, rx{};
+    // tracing
+    bool profiling = false;
+    std::vector<KernelPending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, std::pair<double, int64_t>> ktime;
 };
 
 struct risrt_scene {
@@ -213,6 +225,19 @@ int cuda_fail(risrt_ctx* ctx, cudaError_t e, const char* where);
     do {                                                                 \
         cudaError_t _e = cudaGetLastError();                             \
         if (_e != cudaSuccess) return ::risrt::cuda_fail(ctx, _e, what); \
+    } while (0)
+
+extern std::atomic<long long> g_launches;
+void prof_begin(risrt_ctx* ctx, const char* name);
+void prof_end(risrt_ctx* ctx);
+// Launch a kernel (the `launch` expression) with optional event timing and error check.
+#define RISRT_KERNEL(ctx, name, launch)                                  \
+    do {                                                                 \
+        ::risrt::prof_begin(ctx, name);                                  \
+        launch;                                                          \
+        ::risrt::g_launches.fetch_add(1, std::memory_order_relaxed);     \
+        ::risrt::prof_end(ctx);                                          \
+        RISRT_LAUNCH(ctx, name);                                         \
     } while (0)
 
 int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_t n_verts,

@@ -102,6 +102,7 @@ cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void*
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
     k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb);
     k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+    g_launches.fetch_add(3, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -199,6 +200,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits
         cudaError_t e = exclusive_scan_i64(hist, offs, 256 * n_tiles, scan_tmp, s);
         if (e != cudaSuccess) return e;
         k_sort_scatter<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, n_tiles, offs);
+        g_launches.fetch_add(2, std::memory_order_relaxed);
         std::swap(ka, kb);
         std::swap(va, vb);
     }
@@ -508,8 +510,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &d_bb, 8))) return rc;
     unsigned bb_init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0, 0, 0};
     RISRT_CUDA(ctx, cudaMemcpyAsync(d_bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
-    k_bounds<<<std::min<int64_t>(nblk(n_verts, 256), 1024), 256, 0, s>>>(d_verts, n_verts, d_bb);
-    RISRT_LAUNCH(ctx, "k_bounds");
+    RISRT_KERNEL(ctx, "k_bounds", (k_bounds<<<std::min<int64_t>(nblk(n_verts, 256), 1024), 256, 0, s>>>(d_verts, n_verts, d_bb)));
 
     // Morton codes and stable sort
     uint32_t *keys, *vals;
@@ -518,8 +519,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &vals, nt))) return rc;
     size_t tmp_bytes = std::max(sort_temp_bytes(nt), scan_temp_bytes(F) + 64);
     if ((rc = dmalloc(ctx, (char**)&tmp, tmp_bytes))) return rc;
-    k_morton<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, keys, vals);
-    RISRT_LAUNCH(ctx, "k_morton");
+    RISRT_KERNEL(ctx, "k_morton", (k_morton<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, keys, vals)));
     RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nt, 30, tmp, s));
 
     // leaves, hierarchy, refit
@@ -528,9 +528,8 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &sc->tri_geom, nt))) return rc;
     if ((rc = dmalloc(ctx, &sc->tri_face, nt))) return rc;
     if ((rc = dmalloc(ctx, &leaf_of_orig, nt))) return rc;
-    k_leaves<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, d_face, vals, nt, sc->tri_verts, sc->tri_geom,
-                                           sc->tri_face, leaf_of_orig);
-    RISRT_LAUNCH(ctx, "k_leaves");
+    RISRT_KERNEL(ctx, "k_leaves", (k_leaves<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, d_face, vals, nt, sc->tri_verts, sc->tri_geom,
+                                           sc->tri_face, leaf_of_orig)));
 
     unsigned bb_host[8];
     RISRT_CUDA(ctx, cudaMemcpyAsync(bb_host, d_bb, sizeof(bb_host), cudaMemcpyDeviceToHost, s));
@@ -551,10 +550,8 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, cudaMemsetAsync(parent_int, 0xff, sizeof(int) * n_int, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nt, s));
     if (nt > 1) {
-        k_karras<<<nblk(nt - 1, 256), 256, 0, s>>>(keys, (int)nt, sc->nodes, parent_int, parent_leaf);
-        RISRT_LAUNCH(ctx, "k_karras");
-        k_refit<<<nblk(nt, 256), 256, 0, s>>>(sc->tri_verts, (int)nt, sc->nodes, parent_int, parent_leaf, flags, pad);
-        RISRT_LAUNCH(ctx, "k_refit");
+        RISRT_KERNEL(ctx, "k_karras", (k_karras<<<nblk(nt - 1, 256), 256, 0, s>>>(keys, (int)nt, sc->nodes, parent_int, parent_leaf)));
+        RISRT_KERNEL(ctx, "k_refit", (k_refit<<<nblk(nt, 256), 256, 0, s>>>(sc->tri_verts, (int)nt, sc->nodes, parent_int, parent_leaf, flags, pad)));
         sc->root = 0;
     } else {
         sc->root = ~0;
@@ -573,14 +570,11 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, cudaMemsetAsync(first, 0x7f, sizeof(int) * F, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int) * F, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * F, s));
-    k_face_first<<<nblk(nt, 256), 256, 0, s>>>(d_face, nt, first, count);
-    RISRT_LAUNCH(ctx, "k_face_first");
-    k_i32_to_i64<<<nblk(F, 256), 256, 0, s>>>(count, count64, F);
+    RISRT_KERNEL(ctx, "k_face_first", (k_face_first<<<nblk(nt, 256), 256, 0, s>>>(d_face, nt, first, count)));
+    RISRT_KERNEL(ctx, "k_i32_to_i64", (k_i32_to_i64<<<nblk(F, 256), 256, 0, s>>>(count, count64, F)));
     RISRT_CUDA(ctx, exclusive_scan_i64(count64, start, F, tmp, s));
-    k_face_fill<<<nblk(nt, 256), 256, 0, s>>>(d_face, nt, leaf_of_orig, start, cursor, sc->face_tris);
-    RISRT_LAUNCH(ctx, "k_face_fill");
-    k_face_plane<<<nblk(F, 128), 128, 0, s>>>(d_verts, d_tris, d_mat, first, start, count, F, sc->faces);
-    RISRT_LAUNCH(ctx, "k_face_plane");
+    RISRT_KERNEL(ctx, "k_face_fill", (k_face_fill<<<nblk(nt, 256), 256, 0, s>>>(d_face, nt, leaf_of_orig, start, cursor, sc->face_tris)));
+    RISRT_KERNEL(ctx, "k_face_plane", (k_face_plane<<<nblk(F, 128), 128, 0, s>>>(d_verts, d_tris, d_mat, first, start, count, F, sc->faces)));
 
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));
     cudaFree(d_verts); cudaFree(d_tris); cudaFree(d_face); cudaFree(d_mat); cudaFree(d_bb);

@@ -618,7 +618,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         unsigned* d_ext;
         RISRT_CUDA(ctx, cudaMalloc(&d_ext, sizeof(unsigned)));
         RISRT_CUDA(ctx, cudaMemsetAsync(d_ext, 0, sizeof(unsigned), s));
-        k_abs_max<<<std::min<unsigned>(nblk(3 * n_rx, 256), 1024u), 256, 0, s>>>(rxs->xyz, 3 * n_rx, d_ext);
+        RISRT_KERNEL(ctx, "k_abs_max", (k_abs_max<<<std::min<unsigned>(nblk(3 * n_rx, 256), 1024u), 256, 0, s>>>(rxs->xyz, 3 * n_rx, d_ext)));
         unsigned h_ext = 0;
         cudaError_t e1 = cudaMemcpyAsync(&h_ext, d_ext, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
@@ -733,11 +733,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             tab[i].n = 0;
             int64_t nid = n_ids_of[i];
             if (nid == 0) continue;
-            k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, flag);
-            RISRT_LAUNCH(ctx, "k_seq_allowed");
+            RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, flag)));
             RISRT_CUDA(ctx, exclusive_scan_i64(flag, pos, nid, scan_tmp, s));
-            k_seq_build<<<nblk(nid, 256), 256, 0, s>>>(S, nid, flag, pos, src_of[i], tab[i].e, tab[i].d);
-            RISRT_LAUNCH(ctx, "k_seq_build");
+            RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(nid, 256), 256, 0, s>>>(S, nid, flag, pos, src_of[i], tab[i].e, tab[i].d)));
             int64_t n_allowed = 0;
             int64_t last[2];
             RISRT_CUDA(ctx, cudaMemcpyAsync(&last[0], pos + nid - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -752,27 +750,23 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, s));
             if (t.n > 0) {
                 dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
-                k_candidates<<<grid, kCandThreads, 0, s>>>(S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
-                                                           cs.cnt, cs.cap, flags_dev, counters);
-                RISRT_LAUNCH(ctx, "k_candidates");
+                RISRT_KERNEL(ctx, "k_candidates", (k_candidates<<<grid, kCandThreads, 0, s>>>(S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
+                                                           cs.cnt, cs.cap, flags_dev, counters)));
                 int64_t nthreads = n_dst * cs.cap;
-                k_validate<<<nblk(nthreads, 128), 128, 0, s>>>(S, dst, n_dst, src, src_face, dst_face, t.e, t.d,
-                                                               cs.cand, cs.cnt, cs.cap, tol_base, counters, flags_dev + 1);
-                RISRT_LAUNCH(ctx, "k_validate");
+                RISRT_KERNEL(ctx, "k_validate", (k_validate<<<nblk(nthreads, 128), 128, 0, s>>>(S, dst, n_dst, src, src_face, dst_face, t.e, t.d,
+                                                               cs.cand, cs.cnt, cs.cap, tol_base, counters, flags_dev + 1)));
             }
             const int warps = 4;
             size_t shm = sizeof(int) * (size_t)cs.cap * warps;
             if (shm > 48 * 1024) cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-            k_finalize<<<nblk(n_dst, warps), 32 * warps, shm, s>>>(cs.cand, cs.cnt, n_dst, cs.cap, t.e, cs.cnt64);
-            RISRT_LAUNCH(ctx, "k_finalize");
+            RISRT_KERNEL(ctx, "k_finalize", (k_finalize<<<nblk(n_dst, warps), 32 * warps, shm, s>>>(cs.cand, cs.cnt, n_dst, cs.cap, t.e, cs.cnt64)));
             return RISRT_OK;
         };
 
         // Tx leg (destination: RIS centre, mounted on host_face)
         if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg))) return rc;
-        k_tx_vis<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, ris->host_face, tol_base, tx_vis, counters,
-                                              flags_dev + 1);
-        RISRT_LAUNCH(ctx, "k_tx_vis");
+        RISRT_KERNEL(ctx, "k_tx_vis", (k_tx_vis<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, ris->host_face, tol_base, tx_vis, counters,
+                                              flags_dev + 1)));
         // Rx leg (source: RIS centre) and environment paths (source: Tx)
         const float* rxp = rxs->xyz;
         if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx))) return rc;
@@ -780,11 +774,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         // direct legs
         {
             int64_t nthreads = n_rx * W * 32;
-            k_direct_vis<<<nblk(nthreads, 128), 128, 0, s>>>(S, rxp, n_rx, ris->elem, M, W, fr, ris->host_face,
-                                                             tol_base, ps->vis, counters, flags_dev + 1);
-            RISRT_LAUNCH(ctx, "k_direct_vis");
-            k_los<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1);
-            RISRT_LAUNCH(ctx, "k_los");
+            RISRT_KERNEL(ctx, "k_direct_vis", (k_direct_vis<<<nblk(nthreads, 128), 128, 0, s>>>(S, rxp, n_rx, ris->elem, M, W, fr, ris->host_face,
+                                                             tol_base, ps->vis, counters, flags_dev + 1)));
+            RISRT_KERNEL(ctx, "k_los", (k_los<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1)));
         }
         int host_flags[2];
         RISRT_CUDA(ctx, cudaMemcpyAsync(host_flags, flags_dev, sizeof(host_flags), cudaMemcpyDeviceToHost, s));
@@ -813,11 +805,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         for (int i = 0; i < n_tx; ++i) ps->tx_seq_host[i] = tx_entries[i].info.z;
 
         // c_m
-        k_cm<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand, n_tx, tab[0].e, tab[0].d, ps->cm);
-        RISRT_LAUNCH(ctx, "k_cm");
+        RISRT_KERNEL(ctx, "k_cm", (k_cm<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand, n_tx, tab[0].e, tab[0].d, ps->cm)));
 
         // Rx-leg offsets and records
-        k_count_total<<<nblk(n_rx, 256), 256, 0, s>>>(crx.cnt64, n_rx, tot);
+        RISRT_KERNEL(ctx, "k_count_total", (k_count_total<<<nblk(n_rx, 256), 256, 0, s>>>(crx.cnt64, n_rx, tot)));
         RISRT_CUDA(ctx, cudaMemsetAsync(tot + n_rx, 0, sizeof(int64_t), s));
         RISRT_CUDA(ctx, exclusive_scan_i64(tot, ps->rx_off, n_rx + 1, scan_tmp, s));
         int64_t n_paths = 0;
@@ -840,18 +831,14 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         if ((rc = grow(ctx, &ps->env_seq, &ps->cap_env, std::max<int64_t>(n_env, 1)))) return rc;
         ps->n_paths = n_paths;
         ps->n_env = n_env;
-        k_records<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
-                                                      tab[1].e, ps->rec, ps->rx_seq);
-        RISRT_LAUNCH(ctx, "k_records");
-        k_e0<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand, cenv.cap,
-                                                 env ? cenv.cnt64 : nullptr, tab[2].e, tab[2].d, ps->E0);
-        RISRT_LAUNCH(ctx, "k_e0");
+        RISRT_KERNEL(ctx, "k_records", (k_records<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
+                                                      tab[1].e, ps->rec, ps->rx_seq)));
+        RISRT_KERNEL(ctx, "k_e0", (k_e0<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand, cenv.cap,
+                                                 env ? cenv.cnt64 : nullptr, tab[2].e, tab[2].d, ps->E0)));
         if (env && n_env > 0) {
-            k_env_ids<<<nblk(n_rx, 128), 128, 0, s>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off, n_rx, tab[2].e, ps->env_seq);
-            RISRT_LAUNCH(ctx, "k_env_ids");
+            RISRT_KERNEL(ctx, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, s>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off, n_rx, tab[2].e, ps->env_seq)));
         }
-        k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1);
-        RISRT_LAUNCH(ctx, "k_units");
+        RISRT_KERNEL(ctx, "k_units", (k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1)));
         unsigned long long host_ctr[2];
         RISRT_CUDA(ctx, cudaMemcpyAsync(host_ctr, counters, sizeof(host_ctr), cudaMemcpyDeviceToHost, s));
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));

@@ -41,6 +41,11 @@ _SIGS = {
     "risrt_pathset_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
+    "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
+    "risrt_profile_query": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "risrt_profile_names": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "risrt_profile_reset": (C.c_int, [_P]),
+    "risrt_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "risrt_scene_destroy": (C.c_int, [_P, _P]),
     "risrt_ris_destroy": (C.c_int, [_P, _P]),
     "risrt_rxset_destroy": (C.c_int, [_P, _P]),
@@ -205,6 +210,26 @@ class Context:
     def set_stream(self, stream_handle: int | None):
         self._check(load().risrt_set_stream(self._ptr, None if stream_handle is None else C.c_void_p(stream_handle)))
 
+    # --- tracing -------------------------------------------------------------------------------
+    def profile_enable(self, on: bool = True):
+        self._check(load().risrt_profile_enable(self._ptr, int(on)))
+
+    def profile_reset(self):
+        self._check(load().risrt_profile_reset(self._ptr))
+
+    def profile(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last reset (synchronises)."""
+        need = C.c_size_t()
+        self._check(load().risrt_profile_names(self._ptr, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value)
+        self._check(load().risrt_profile_names(self._ptr, buf, need.value, None))
+        out = {}
+        for name in filter(None, buf.value.decode().split(",")):
+            ms, n = C.c_double(), C.c_int64()
+            self._check(load().risrt_profile_query(self._ptr, name.encode(), C.byref(ms), C.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
     # --- inputs --------------------------------------------------------------------------------
     def scene_upload(self, verts, tris, face_id, mat_id, mats) -> Scene:
         v = _f32(verts)
@@ -260,6 +285,15 @@ class Context:
     def build_A(self, ps: PathSet, A_out, E0_out=None):
         self._check(load().risrt_build_A(self._ptr, ps.ptr, _dev_ptr(A_out, "torch.complex64"),
                                          _dev_ptr(E0_out, "torch.complex64")))
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    n = C.c_int64()
+    rc = load().risrt_launch_count(C.byref(n))
+    if rc:
+        raise RisrtError(rc, "launch count")
+    return n.value
 
 
 def flags_of(w) -> int:
