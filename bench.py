@@ -310,6 +310,8 @@ def main():
                            "order_rx": w.max_order_rx, "env_paths": bool(w.env_paths), "n_cfg": n_cfg,
                            "units_per_step": units, "rx_paths": st.n_rx_paths, "env_paths_found": st.n_env_paths,
                            "tx_paths": st.n_tx_paths, "fp64_refines": st.fp64_refines,
+                           "candidates": st.n_candidates, "segments": st.n_segments,
+                           "bvh_node_visits": st.node_visits, "tri_tests": st.tri_tests,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
                 "stages": stages}

@@ -162,6 +162,10 @@ typedef struct {
     int32_t n_tx_paths;    /* valid reflected Tx-leg sequences */
     int64_t units;         /* field evaluation units: sum over receivers of M x (Rx-leg entries) */
     int64_t fp64_refines;  /* geometric decisions settled in FP64 in the last trace */
+    int64_t n_candidates;  /* geometric path candidates whose segments were traced */
+    int64_t n_segments;    /* candidate segments traced through the BVH (early exit on a block) */
+    int64_t node_visits;   /* BVH nodes visited by those segments */
+    int64_t tri_tests;     /* triangle tests of those segments */
 } risrt_pathset_stats;
 
 int risrt_pathset_stats_get(const risrt_pathset* ps, risrt_pathset_stats* out);

@@ -392,6 +392,10 @@ int risrt_pathset_stats_get(const risrt_pathset* ps, risrt_pathset_stats* out)
     out->n_tx_paths = (int32_t)ps->tx_seq_host.size();
     out->units = ps->units;
     out->fp64_refines = ps->fp64_refines;
+    out->n_candidates = ps->n_candidates;
+    out->n_segments = ps->n_segments;
+    out->node_visits = ps->node_visits;
+    out->tri_tests = ps->tri_tests;
     return RISRT_OK;
 }
 
@@ -453,7 +457,7 @@ int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
         cudaStreamSynchronize(ctx->stream);
     }
     cudaFree(sc->nodes); cudaFree(sc->tri_geom); cudaFree(sc->tri_verts); cudaFree(sc->tri_face);
-    cudaFree(sc->faces); cudaFree(sc->face_tris); cudaFree(sc->mats);
+    cudaFree(sc->faces); cudaFree(sc->face_tris); cudaFree(sc->face_test); cudaFree(sc->mats);
     delete sc;
     return RISRT_OK;
 }

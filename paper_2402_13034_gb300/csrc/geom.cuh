@@ -124,18 +124,32 @@ __device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, float3 a, floa
 
 __device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d)); }
 
+struct TraceCounters {
+    unsigned long long cand, segs, nodes, tris;
+};
+
+// Warp-aggregated add of the per-thread counters (all lanes of the warp must call it).
+__device__ __forceinline__ void flush_counters(const TraceCounters& t, unsigned long long* ctr)
+{
+    unsigned long long v[4] = {t.cand, t.segs, t.nodes, t.tris};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        unsigned long long x = v[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&ctr[i], x);
+    }
+}
+
 // Is segment A->B blocked (faces ign0 / ign1 skipped)? `refines` counts FP64 settlements,
 // `err` is set if the traversal stack would overflow (never expected; treated as blocked).
 __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
-                           unsigned long long* refines, int* err)
+                           unsigned long long* refines, int* err, TraceCounters* tc = nullptr)
 {
     if (S.root == -1) return false;
     float3 a = to_f(A), b = to_f(B);
     float3 dir = b - a;
     float len = sqrtf(dot(dir, dir));
     float3 inv = f3(safe_inv(dir.x), safe_inv(dir.y), safe_inv(dir.z));
-    d3 dirD = B - A;
-    double lenD = norm(dirD);
     float tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
     int stack[64];
     int sp = 0;
@@ -146,15 +160,18 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
             int i = ~c;
             int f = S.tri_face[i];
             if (f == ign0 || f == ign1) continue;
+            if (tc) ++tc->tris;
             int r = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
             if (r == 1) return true;
             if (r == 2) {
                 if (refines) atomicAdd(refines, 1ull);
-                if (tri_hit_fp64(S.tri_verts[i], A, dirD, lenD)) return true;
+                const d3 dirD = B - A;
+                if (tri_hit_fp64(S.tri_verts[i], A, dirD, norm(dirD))) return true;
             }
             continue;
         }
         const BvhNode nd = S.nodes[c];
+        if (tc) ++tc->nodes;
         bool hl = box_overlap(nd.l_lo, nd.l_hi, a, inv);
         bool hr = box_overlap(nd.r_lo, nd.r_hi, a, inv);
         if (sp + 2 > 64) {
@@ -203,6 +220,17 @@ __device__ __forceinline__ int in_face_fp32(const DeviceScene& S, int f, float3 
         if (emin >= -tol) res = 2;
     }
     return res;
+}
+
+// FP32 classification against a convex face outline (4 edges; unused edges never bind).
+__device__ __forceinline__ int in_outline_fp32(const FaceTest& t, float3 q, float tol)
+{
+    float emin = dot(xyz(t.e[0]), q) - t.e[0].w;
+#pragma unroll
+    for (int i = 1; i < 4; ++i) emin = fminf(emin, dot(xyz(t.e[i]), q) - t.e[i].w);
+    if (emin > tol) return 1;
+    if (emin < -tol) return 0;
+    return 2;
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -86,16 +86,25 @@ struct Face {
     int pad;
 };
 
+// Convex outline of a face for the FP32 in-face filter: n inward edge planes (m, c), distance to
+// edge i = m_i.q - c_i; n = 0 when the face is not a single triangle or a convex two-triangle quad.
+struct FaceTest {
+    float4 e[4];
+    int n;
+    int pad[3];
+};
+
 struct DeviceScene {
     int64_t n_tris;
     int n_faces;
     int root;                    // root child code (internal index, or ~leaf for one triangle); -1 if empty
     const BvhNode* nodes;
-    const TriGeom* tri_geom;     // [n_tris] leaf order
-    const TriVerts* tri_verts;   // [n_tris] leaf order
-    const int* tri_face;         // [n_tris] leaf order
+    const TriGeom* tri_geom;     // [n_refs] leaf (reference) order
+    const TriVerts* tri_verts;   // [n_refs] leaf order
+    const int* tri_face;         // [n_refs] leaf order
     const Face* faces;           // [n_faces]
     const int* face_tris;        // CSR: triangles (leaf order) of each face
+    const FaceTest* face_test;   // [n_faces]
     const float2* mats;          // [n_mat] (eps_r, sigma)
 };
 
@@ -133,6 +142,7 @@ struct risrt_ctx {
 
 struct risrt_scene {
     int64_t n_tris = 0;
+    int64_t n_refs = 0;              // BVH leaves (triangle references)
     int n_faces = 0;
     int n_mat = 0;
     int root = -1;
@@ -142,12 +152,13 @@ struct risrt_scene {
     int* tri_face = nullptr;
     risrt::Face* faces = nullptr;
     int* face_tris = nullptr;
+    risrt::FaceTest* face_test = nullptr;
     float2* mats = nullptr;
     float scene_extent = 0.f;     // max |coordinate| over vertices
     risrt::DeviceScene dev() const {
         risrt::DeviceScene s;
         s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.nodes = nodes; s.tri_geom = tri_geom;
-        s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.mats = mats;
+        s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.face_test = face_test; s.mats = mats;
         return s;
     }
 };
@@ -203,6 +214,7 @@ struct risrt_pathset {
     std::vector<uint8_t> tx_vis_host;
     int64_t units = 0;
     int64_t fp64_refines = 0;
+    int64_t n_candidates = 0, n_segments = 0, node_visits = 0, tri_tests = 0;
     int64_t cap_rx = 0;              // capacity of the per-Rx arrays
     // scratch (grown as needed, kept for reuse)
     void* scratch = nullptr;

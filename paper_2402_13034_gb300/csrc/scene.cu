@@ -256,37 +256,107 @@ __device__ __forceinline__ unsigned spread10(unsigned x)
     return x;
 }
 
-__global__ void k_morton(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
-                         const unsigned* __restrict__ bb, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+// Triangle references: a triangle whose box is longer than a cell (1/8 of the scene's largest
+// span) in some axis is split into a grid of references, each bounded by the triangle's box
+// intersected with one grid cell, so large walls do not inflate the boxes of the tree above them.
+// Every point of the triangle lies in one reference's box, so traversal still finds every hit.
+struct RefGrid {
+    int n[3];
+};
+
+__device__ __forceinline__ void tri_box(const float* verts, const int32_t* tris, int64_t t, float lo[3], float hi[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        float a = verts[3 * tris[3 * t] + k], b = verts[3 * tris[3 * t + 1] + k], c = verts[3 * tris[3 * t + 2] + k];
+        lo[k] = fminf(a, fminf(b, c));
+        hi[k] = fmaxf(a, fmaxf(b, c));
+    }
+}
+
+__device__ __forceinline__ RefGrid ref_grid(const float lo[3], const float hi[3], float cell)
+{
+    RefGrid g;
+    for (int k = 0; k < 3; ++k) {
+        int n = (int)ceilf((hi[k] - lo[k]) / cell);
+        g.n[k] = max(1, min(n, 16));
+    }
+    return g;
+}
+
+__device__ __forceinline__ float scene_cell(const unsigned* bb)
+{
+    float span = 0.f;
+    for (int k = 0; k < 3; ++k) span = fmaxf(span, from_ordered(bb[3 + k]) - from_ordered(bb[k]));
+    return fmaxf(span * 0.125f, 1e-6f);
+}
+
+__global__ void k_ref_count(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
+                            const unsigned* __restrict__ bb, int64_t* __restrict__ cnt)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
-    float lo[3], inv[3];
-    for (int k = 0; k < 3; ++k) {
-        lo[k] = from_ordered(bb[k]);
-        float span = from_ordered(bb[3 + k]) - lo[k];
-        inv[k] = span > 0.f ? 1.f / span : 0.f;
-    }
-    unsigned code = 0;
-    for (int k = 0; k < 3; ++k) {
-        float c = (verts[3 * tris[3 * t] + k] + verts[3 * tris[3 * t + 1] + k] + verts[3 * tris[3 * t + 2] + k]) * (1.f / 3.f);
-        float u = (c - lo[k]) * inv[k];
-        unsigned q = (unsigned)fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
-        code |= spread10(q) << (2 - k);
-    }
-    keys[t] = code;
-    vals[t] = (uint32_t)t;
+    float lo[3], hi[3];
+    tri_box(verts, tris, t, lo, hi);
+    RefGrid g = ref_grid(lo, hi, scene_cell(bb));
+    cnt[t] = (int64_t)g.n[0] * g.n[1] * g.n[2];
 }
 
-// Per leaf (sorted order): exact float vertices, FP32 plane and edge planes computed in FP64.
+// References of every triangle with their boxes; 30-bit Morton code of each box centre.
+__global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
+                           const unsigned* __restrict__ bb, const int64_t* __restrict__ off,
+                           uint32_t* __restrict__ ref_tri, float4* __restrict__ ref_lo, float4* __restrict__ ref_hi,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    float lo[3], hi[3];
+    tri_box(verts, tris, t, lo, hi);
+    RefGrid g = ref_grid(lo, hi, scene_cell(bb));
+    float slo[3], inv[3];
+    for (int k = 0; k < 3; ++k) {
+        slo[k] = from_ordered(bb[k]);
+        float span = from_ordered(bb[3 + k]) - slo[k];
+        inv[k] = span > 0.f ? 1.f / span : 0.f;
+    }
+    int64_t r = off[t];
+    for (int i = 0; i < g.n[0]; ++i)
+        for (int j = 0; j < g.n[1]; ++j)
+            for (int l = 0; l < g.n[2]; ++l, ++r) {
+                const int c[3] = {i, j, l};
+                float blo[3], bhi[3];
+                unsigned code = 0;
+                for (int k = 0; k < 3; ++k) {
+                    float w = (hi[k] - lo[k]) / g.n[k];
+                    blo[k] = c[k] == 0 ? lo[k] : lo[k] + w * c[k];
+                    bhi[k] = c[k] == g.n[k] - 1 ? hi[k] : lo[k] + w * (c[k] + 1);
+                    float u = (0.5f * (blo[k] + bhi[k]) - slo[k]) * inv[k];
+                    unsigned q = (unsigned)fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+                    code |= spread10(q) << (2 - k);
+                }
+                ref_tri[r] = (uint32_t)t;
+                ref_lo[r] = make_float4(blo[0], blo[1], blo[2], 0.f);
+                ref_hi[r] = make_float4(bhi[0], bhi[1], bhi[2], 0.f);
+                keys[r] = code;
+                vals[r] = (uint32_t)r;
+            }
+}
+
+// Per leaf (sorted reference order): exact float vertices of the referenced triangle, FP32 plane and
+// edge planes computed in FP64, and the reference box for the refit. leaf_of_orig[t] receives one
+// leaf of triangle t (all leaves of a triangle carry identical triangle data).
 __global__ void k_leaves(const float* __restrict__ verts, const int32_t* __restrict__ tris,
-                         const int32_t* __restrict__ face, const uint32_t* __restrict__ order, int64_t nt,
-                         TriVerts* __restrict__ tv, TriGeom* __restrict__ tg, int* __restrict__ tf,
+                         const int32_t* __restrict__ face, const uint32_t* __restrict__ order, int64_t n_ref,
+                         const uint32_t* __restrict__ ref_tri, const float4* __restrict__ ref_lo,
+                         const float4* __restrict__ ref_hi, TriVerts* __restrict__ tv, TriGeom* __restrict__ tg,
+                         int* __restrict__ tf, float4* __restrict__ leaf_lo, float4* __restrict__ leaf_hi,
                          int* __restrict__ leaf_of_orig)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nt) return;
-    int64_t t = order[i];
+    if (i >= n_ref) return;
+    const int64_t ref = order[i];
+    const int64_t t = ref_tri[ref];
+    leaf_lo[i] = ref_lo[ref];
+    leaf_hi[i] = ref_hi[ref];
     leaf_of_orig[t] = (int)i;
     float3 v[3];
     for (int j = 0; j < 3; ++j) {
@@ -374,17 +444,13 @@ __device__ __forceinline__ void store_slot(BvhNode* node, bool right, float3 lo,
 }
 
 // Bottom-up refit: the second child to finish a node merges both boxes and moves up.
-__global__ void k_refit(const TriVerts* __restrict__ tv, int n, BvhNode* nodes,
+__global__ void k_refit(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi, int n, BvhNode* nodes,
                         const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
                         int* flags, float pad)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    TriVerts v = tv[i];
-    float3 lo = f3(fminf(v.v0.x, fminf(v.v1.x, v.v2.x)), fminf(v.v0.y, fminf(v.v1.y, v.v2.y)),
-                   fminf(v.v0.z, fminf(v.v1.z, v.v2.z)));
-    float3 hi = f3(fmaxf(v.v0.x, fmaxf(v.v1.x, v.v2.x)), fmaxf(v.v0.y, fmaxf(v.v1.y, v.v2.y)),
-                   fmaxf(v.v0.z, fmaxf(v.v1.z, v.v2.z)));
+    float3 lo = xyz(leaf_lo[i]), hi = xyz(leaf_hi[i]);
     lo = lo - f3(pad, pad, pad);
     hi = hi + f3(pad, pad, pad);
     int child = ~i;
@@ -456,6 +522,63 @@ __global__ void k_face_plane(const float* __restrict__ verts, const int32_t* __r
     faces[f] = fc;
 }
 
+__device__ __forceinline__ bool same3(float4 a, float4 b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
+
+// Outline of each face for the FP32 in-face filter: a single triangle keeps its three edges; two
+// triangles sharing an edge keep their four outer edges when the quad is convex.
+__global__ void k_face_test(const Face* __restrict__ faces, const int* __restrict__ face_tris,
+                            const TriVerts* __restrict__ tv, const TriGeom* __restrict__ tg, int F,
+                            FaceTest* __restrict__ out)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const Face fc = faces[f];
+    FaceTest t;
+    t.n = 0;
+    t.pad[0] = t.pad[1] = t.pad[2] = 0;
+    for (int i = 0; i < 4; ++i) t.e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int cnt = fc.tri_end - fc.tri_begin;
+    if (cnt == 1) {
+        const TriGeom g = tg[face_tris[fc.tri_begin]];
+        for (int i = 0; i < 3; ++i) t.e[i] = g.edge[i];
+        t.e[3] = make_float4(0.f, 0.f, 0.f, -1e30f);   // never the closest edge
+        t.n = 3;
+    } else if (cnt == 2) {
+        const int a = face_tris[fc.tri_begin], b = face_tris[fc.tri_begin + 1];
+        const float4 va[3] = {tv[a].v0, tv[a].v1, tv[a].v2};
+        const float4 vb[3] = {tv[b].v0, tv[b].v1, tv[b].v2};
+        // vertex of each triangle that is not on the shared edge (edge i is opposite vertex i)
+        int oa = -1, ob = -1;
+        for (int i = 0; i < 3; ++i) {
+            int hits = 0;
+            for (int j = 0; j < 3; ++j) hits += same3(va[i], vb[j]);
+            if (!hits) oa = i;
+        }
+        for (int j = 0; j < 3; ++j) {
+            int hits = 0;
+            for (int i = 0; i < 3; ++i) hits += same3(va[i], vb[j]);
+            if (!hits) ob = j;
+        }
+        if (oa >= 0 && ob >= 0) {
+            const TriGeom ga = tg[a], gb = tg[b];
+            int n = 0;
+            for (int i = 0; i < 3; ++i) if (i != oa) t.e[n++] = ga.edge[i];
+            for (int j = 0; j < 3; ++j) if (j != ob) t.e[n++] = gb.edge[j];
+            // convex if every vertex lies on the inner side of every outer edge
+            bool convex = true;
+            for (int i = 0; i < 4 && convex; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    float4 v = va[j];
+                    if (t.e[i].x * v.x + t.e[i].y * v.y + t.e[i].z * v.z - t.e[i].w < -1e-5f) convex = false;
+                    v = vb[j];
+                    if (t.e[i].x * v.x + t.e[i].y * v.y + t.e[i].z * v.z - t.e[i].w < -1e-5f) convex = false;
+                }
+            t.n = convex ? 4 : 0;
+        }
+    }
+    out[f] = t;
+}
+
 __global__ void k_i32_to_i64(const int* __restrict__ a, int64_t* __restrict__ b, int64_t n)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -512,24 +635,45 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, cudaMemcpyAsync(d_bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
     RISRT_KERNEL(ctx, "k_bounds", (k_bounds<<<std::min<int64_t>(nblk(n_verts, 256), 1024), 256, 0, s>>>(d_verts, n_verts, d_bb)));
 
-    // Morton codes and stable sort
-    uint32_t *keys, *vals;
+    // triangle references (large triangles split over a grid), Morton codes, stable sort
+    int64_t *ref_cnt, *ref_off;
+    if ((rc = dmalloc(ctx, &ref_cnt, nt + 1))) return rc;
+    if ((rc = dmalloc(ctx, &ref_off, nt + 1))) return rc;
+    void* tmp0;
+    if ((rc = dmalloc(ctx, (char**)&tmp0, scan_temp_bytes(nt + 1) + 64))) return rc;
+    RISRT_CUDA(ctx, cudaMemsetAsync(ref_cnt + nt, 0, sizeof(int64_t), s));
+    RISRT_KERNEL(ctx, "k_ref_count", (k_ref_count<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_cnt)));
+    RISRT_CUDA(ctx, exclusive_scan_i64(ref_cnt, ref_off, nt + 1, tmp0, s));
+    int64_t nr = 0;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&nr, ref_off + nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    if (nr > ((int64_t)1 << 27)) return fail(ctx, RISRT_ERR_CAPACITY, "too many BVH references");
+    sc->n_refs = nr;
+    uint32_t *keys, *vals, *ref_tri;
+    float4 *ref_lo, *ref_hi, *leaf_lo, *leaf_hi;
     void* tmp;
-    if ((rc = dmalloc(ctx, &keys, nt))) return rc;
-    if ((rc = dmalloc(ctx, &vals, nt))) return rc;
-    size_t tmp_bytes = std::max(sort_temp_bytes(nt), scan_temp_bytes(F) + 64);
+    if ((rc = dmalloc(ctx, &keys, nr))) return rc;
+    if ((rc = dmalloc(ctx, &vals, nr))) return rc;
+    if ((rc = dmalloc(ctx, &ref_tri, nr))) return rc;
+    if ((rc = dmalloc(ctx, &ref_lo, nr))) return rc;
+    if ((rc = dmalloc(ctx, &ref_hi, nr))) return rc;
+    if ((rc = dmalloc(ctx, &leaf_lo, nr))) return rc;
+    if ((rc = dmalloc(ctx, &leaf_hi, nr))) return rc;
+    size_t tmp_bytes = std::max(sort_temp_bytes(nr), scan_temp_bytes(F) + 64);
     if ((rc = dmalloc(ctx, (char**)&tmp, tmp_bytes))) return rc;
-    RISRT_KERNEL(ctx, "k_morton", (k_morton<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, keys, vals)));
-    RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nt, 30, tmp, s));
+    RISRT_KERNEL(ctx, "k_ref_emit", (k_ref_emit<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_off, ref_tri,
+                                                                            ref_lo, ref_hi, keys, vals)));
+    RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nr, 30, tmp, s));
 
     // leaves, hierarchy, refit
     int* leaf_of_orig;
-    if ((rc = dmalloc(ctx, &sc->tri_verts, nt))) return rc;
-    if ((rc = dmalloc(ctx, &sc->tri_geom, nt))) return rc;
-    if ((rc = dmalloc(ctx, &sc->tri_face, nt))) return rc;
+    if ((rc = dmalloc(ctx, &sc->tri_verts, nr))) return rc;
+    if ((rc = dmalloc(ctx, &sc->tri_geom, nr))) return rc;
+    if ((rc = dmalloc(ctx, &sc->tri_face, nr))) return rc;
     if ((rc = dmalloc(ctx, &leaf_of_orig, nt))) return rc;
-    RISRT_KERNEL(ctx, "k_leaves", (k_leaves<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, d_face, vals, nt, sc->tri_verts, sc->tri_geom,
-                                           sc->tri_face, leaf_of_orig)));
+    RISRT_KERNEL(ctx, "k_leaves", (k_leaves<<<nblk(nr, 256), 256, 0, s>>>(d_verts, d_tris, d_face, vals, nr, ref_tri, ref_lo,
+                                                                        ref_hi, sc->tri_verts, sc->tri_geom, sc->tri_face,
+                                                                        leaf_lo, leaf_hi, leaf_of_orig)));
 
     unsigned bb_host[8];
     RISRT_CUDA(ctx, cudaMemcpyAsync(bb_host, d_bb, sizeof(bb_host), cudaMemcpyDeviceToHost, s));
@@ -539,19 +683,19 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     sc->scene_extent = ext;
     const float pad = 1e-4f * (1.f + ext);
 
-    int n_int = (int)std::max<int64_t>(nt - 1, 1);
+    int n_int = (int)std::max<int64_t>(nr - 1, 1);
     int *parent_int, *parent_leaf, *flags;
     if ((rc = dmalloc(ctx, &sc->nodes, n_int))) return rc;
     if ((rc = dmalloc(ctx, &parent_int, n_int))) return rc;
-    if ((rc = dmalloc(ctx, &parent_leaf, nt))) return rc;
+    if ((rc = dmalloc(ctx, &parent_leaf, nr))) return rc;
     if ((rc = dmalloc(ctx, &flags, n_int))) return rc;
     RISRT_CUDA(ctx, cudaMemsetAsync(sc->nodes, 0, sizeof(BvhNode) * n_int, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * n_int, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(parent_int, 0xff, sizeof(int) * n_int, s));
-    RISRT_CUDA(ctx, cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nt, s));
-    if (nt > 1) {
-        RISRT_KERNEL(ctx, "k_karras", (k_karras<<<nblk(nt - 1, 256), 256, 0, s>>>(keys, (int)nt, sc->nodes, parent_int, parent_leaf)));
-        RISRT_KERNEL(ctx, "k_refit", (k_refit<<<nblk(nt, 256), 256, 0, s>>>(sc->tri_verts, (int)nt, sc->nodes, parent_int, parent_leaf, flags, pad)));
+    RISRT_CUDA(ctx, cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nr, s));
+    if (nr > 1) {
+        RISRT_KERNEL(ctx, "k_karras", (k_karras<<<nblk(nr - 1, 256), 256, 0, s>>>(keys, (int)nr, sc->nodes, parent_int, parent_leaf)));
+        RISRT_KERNEL(ctx, "k_refit", (k_refit<<<nblk(nr, 256), 256, 0, s>>>(leaf_lo, leaf_hi, (int)nr, sc->nodes, parent_int, parent_leaf, flags, pad)));
         sc->root = 0;
     } else {
         sc->root = ~0;
@@ -567,6 +711,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &start, F))) return rc;
     if ((rc = dmalloc(ctx, &sc->face_tris, nt))) return rc;
     if ((rc = dmalloc(ctx, &sc->faces, F))) return rc;
+    if ((rc = dmalloc(ctx, &sc->face_test, F))) return rc;
     RISRT_CUDA(ctx, cudaMemsetAsync(first, 0x7f, sizeof(int) * F, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int) * F, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * F, s));
@@ -575,10 +720,14 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, exclusive_scan_i64(count64, start, F, tmp, s));
     RISRT_KERNEL(ctx, "k_face_fill", (k_face_fill<<<nblk(nt, 256), 256, 0, s>>>(d_face, nt, leaf_of_orig, start, cursor, sc->face_tris)));
     RISRT_KERNEL(ctx, "k_face_plane", (k_face_plane<<<nblk(F, 128), 128, 0, s>>>(d_verts, d_tris, d_mat, first, start, count, F, sc->faces)));
+    RISRT_KERNEL(ctx, "k_face_test", (k_face_test<<<nblk(F, 128), 128, 0, s>>>(sc->faces, sc->face_tris, sc->tri_verts,
+                                                                               sc->tri_geom, F, sc->face_test)));
 
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));
     cudaFree(d_verts); cudaFree(d_tris); cudaFree(d_face); cudaFree(d_mat); cudaFree(d_bb);
-    cudaFree(keys); cudaFree(vals); cudaFree(tmp); cudaFree(leaf_of_orig);
+    cudaFree(keys); cudaFree(vals); cudaFree(tmp); cudaFree(leaf_of_orig); cudaFree(tmp0);
+    cudaFree(ref_cnt); cudaFree(ref_off); cudaFree(ref_tri); cudaFree(ref_lo); cudaFree(ref_hi);
+    cudaFree(leaf_lo); cudaFree(leaf_hi);
     cudaFree(parent_int); cudaFree(parent_leaf); cudaFree(flags);
     cudaFree(first); cudaFree(count); cudaFree(cursor); cudaFree(count64); cudaFree(start);
     return RISRT_OK;

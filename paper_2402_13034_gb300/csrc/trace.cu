@@ -44,9 +44,57 @@ __device__ __forceinline__ bool coplanar_d(const Face& a, const Face& b)
 }
 __device__ __forceinline__ bool contains_point(const Face& a, d3 p) { return fabs(dot(ld3(a.plane), p) - a.plane.w) < 1e-6; }
 
+// Can face f2 hold the second reflection point of a path src -> f1 -> f2 -> (anything)? The point
+// must lie strictly on the source's side of plane f1 and inside the cone from the source image S1
+// through f1 (the union over f1's triangles of the trihedral cones with apex S1). Returns false only
+// when every vertex of f2 is separated by more than 1e-9 m, so no destination can make the sequence
+// valid; the test is independent of the receiver.
+__device__ bool beam_reaches(const DeviceScene& S, d3 src, int f1, int f2)
+{
+    const Face F1 = S.faces[f1], F2 = S.faces[f2];
+    const d3 n1 = ld3(F1.plane);
+    const double s0 = dot(n1, src) - F1.plane.w;
+    const double sgn = s0 > 0 ? 1.0 : -1.0;
+    const double tol = 1e-9;
+    // strictly on the source side of f1
+    bool any_front = false;
+    for (int j = F2.tri_begin; j < F2.tri_end && !any_front; ++j) {
+        const TriVerts tv = S.tri_verts[S.face_tris[j]];
+        const d3 v[3] = {ldv(tv.v0), ldv(tv.v1), ldv(tv.v2)};
+        for (int i = 0; i < 3; ++i)
+            if (sgn * (dot(n1, v[i]) - F1.plane.w) > tol) any_front = true;
+    }
+    if (!any_front) return false;
+    const d3 S1 = mirror_pt(src, n1, F1.plane.w);
+    for (int a = F1.tri_begin; a < F1.tri_end; ++a) {
+        const TriVerts ta = S.tri_verts[S.face_tris[a]];
+        const d3 P[3] = {ldv(ta.v0), ldv(ta.v1), ldv(ta.v2)};
+        bool separated = false;
+        for (int e = 0; e < 3 && !separated; ++e) {
+            const d3 p = P[e], q = P[(e + 1) % 3], r = P[(e + 2) % 3];
+            d3 nn = cross(p - S1, q - S1);
+            const double len = norm(nn);
+            if (len == 0.0) continue;
+            nn = nn * (1.0 / len);
+            if (dot(nn, r - S1) < 0) nn = nn * -1.0;
+            bool all_out = true;
+            for (int j = F2.tri_begin; j < F2.tri_end && all_out; ++j) {
+                const TriVerts tv = S.tri_verts[S.face_tris[j]];
+                const d3 v[3] = {ldv(tv.v0), ldv(tv.v1), ldv(tv.v2)};
+                for (int i = 0; i < 3; ++i)
+                    if (dot(nn, v[i] - S1) >= -tol) all_out = false;
+            }
+            separated = all_out;
+        }
+        if (!separated) return true;
+    }
+    return false;
+}
+
 // mode 0: Tx leg (last face may not contain the RIS centre); 1: Rx leg (first face may not);
-// 2: Tx -> Rx environment paths.
-__global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, int64_t* __restrict__ flag)
+// 2: Tx -> Rx environment paths. Order-2 sequences whose second face is outside the beam of the
+// first are dropped (beam_reaches).
+__global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, d3 src, int64_t* __restrict__ flag)
 {
     int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (id >= n_ids) return;
@@ -64,6 +112,8 @@ __global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, 
     d3 c = fr_c(fr);
     if (mode == 0 && contains_point(S.faces[k == 2 ? f2 : f1], c)) ok = false;
     if (mode == 1 && contains_point(S.faces[f1], c)) ok = false;
+    if (ok && k == 2 && fabs(dot(ld3(S.faces[f1].plane), src) - S.faces[f1].plane.w) > 0.0 && !beam_reaches(S, src, f1, f2))
+        ok = false;
     flag[id] = ok ? 1 : 0;
 }
 
@@ -120,6 +170,17 @@ constexpr int kCandChunk = 2048;
 //  (D) order 2: the first reflection point lies in its face.
 // Each test is decided in FP32 when its margin exceeds the FP32 error bound, otherwise the whole
 // candidate is settled by the FP64 check.
+constexpr int kMaxSmemFaces = 1024;
+
+template <bool SMEM_FACES>
+__device__ __forceinline__ int face_class(const DeviceScene& S, const FaceTest* sh_faces, int f, float3 q, float tol)
+{
+    const FaceTest& t = SMEM_FACES ? sh_faces[f] : S.face_test[f];
+    if (t.n) return in_outline_fp32(t, q, tol);
+    return in_face_fp32(S, f, q, tol);
+}
+
+template <bool SMEM_FACES>
 __global__ void __launch_bounds__(kCandThreads)
 k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3 src,
              const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int n_seq,
@@ -127,6 +188,9 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3
              int* __restrict__ overflow, unsigned long long* __restrict__ refines)
 {
     __shared__ SeqEntry sh[kCandThreads];
+    extern __shared__ FaceTest sh_faces[];
+    if (SMEM_FACES)
+        for (int f = threadIdx.x; f < S.n_faces; f += blockDim.x) sh_faces[f] = S.face_test[f];
     const int64_t r = blockIdx.x * (int64_t)kCandThreads + threadIdx.x;
     const bool active = r < n_dst;
     const float3 R = active ? f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]) : f3(0.f, 0.f, 0.f);
@@ -155,7 +219,7 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3
             const float cond = sqrtf(dot(d, d)) / fmaxf(fabsf(den), 1e-30f);
             const float tol = tol_base * fminf(cond, 1e6f);
             const int k = e.info.w;
-            const int cB = in_face_fp32(S, k == 2 ? e.info.y : e.info.x, P, tol);
+            const int cB = face_class<SMEM_FACES>(S, sh_faces, k == 2 ? e.info.y : e.info.x, P, tol);
             if (cB == 0) continue;
             unsure |= cB == 2;
             if (k == 2) {
@@ -171,7 +235,7 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3
                 const float3 P1 = P + d1 * (s1P / den1);
                 const float cond1 = sqrtf(dot(d1, d1)) / fmaxf(fabsf(den1), 1e-30f);
                 const float tol1 = tol * fminf(cond1, 1e6f) + tol_base;
-                const int cD = in_face_fp32(S, e.info.x, P1, tol1);
+                const int cD = face_class<SMEM_FACES>(S, sh_faces, e.info.x, P1, tol1);
                 if (cD == 0) continue;
                 unsure |= cD == 2;
             }
@@ -189,31 +253,181 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3
     }
 }
 
-// Occlusion of every segment of every candidate (thread per candidate slot); invalid -> -1.
-__global__ void k_validate(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3 src,
-                           int src_face, int dst_face, const SeqEntry* __restrict__ seqs,
-                           const SeqEntryD* __restrict__ seqd, int* __restrict__ cand,
-                           const int* __restrict__ cand_cnt, int cap, float tol_base,
-                           unsigned long long* refines, int* err)
+// Dense list of the (destination, slot) pairs holding a geometric candidate, receiver-major.
+__global__ void k_cand_counts(const int* __restrict__ cand_cnt, int64_t n_dst, int cap, int64_t* __restrict__ out)
 {
-    int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t r = gid / cap;
-    int slot = (int)(gid % cap);
-    if (r >= n_dst || slot >= min(cand_cnt[r], cap)) return;
-    int si = cand[r * (int64_t)cap + slot];
-    const int4 info = seqs[si].info;
-    const d3 R = D3((double)dst_xyz[3 * r], (double)dst_xyz[3 * r + 1], (double)dst_xyz[3 * r + 2]);
-    d3 pts[4];
-    seq_points_fp64(S, R, info, seqd[si], src, pts);
-    const int k = info.w;
-    const int fa[2] = {info.x, info.y};
-    bool ok = true;
-    for (int j = 0; j <= k && ok; ++j) {
-        int i0 = j == 0 ? src_face : fa[j - 1];
-        int i1 = j == k ? dst_face : fa[j];
-        if (seg_blocked(S, pts[j], pts[j + 1], i0, i1, tol_base, refines, err)) ok = false;
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n_dst) out[r] = min(cand_cnt[r], cap);
+    if (r == n_dst) out[r] = 0;
+}
+
+__global__ void k_dense_list(const int* __restrict__ cand_cnt, const int64_t* __restrict__ off, int64_t n_dst, int cap,
+                             int* __restrict__ dense_r, int* __restrict__ dense_slot)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= n_dst) return;
+    const int n = min(cand_cnt[r], cap);
+    const int64_t o = off[r];
+    for (int slot = lane; slot < n; slot += 32) {
+        dense_r[o + slot] = (int)r;
+        dense_slot[o + slot] = slot;
     }
-    if (!ok) cand[r * (int64_t)cap + slot] = -1;
+}
+
+// FP32 reflection points of every dense candidate (same back-trace as the candidate filter): the
+// last point P (next to the destination) and, for order 2, the first point P1.
+__global__ void k_cand_points(const float* __restrict__ dst_xyz, const SeqEntry* __restrict__ seqs,
+                              const int* __restrict__ cand, int cap, const int* __restrict__ dense_r,
+                              const int* __restrict__ dense_slot, long long total, float4* __restrict__ pts)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int r = dense_r[i];
+    const int si = cand[(int64_t)r * cap + dense_slot[i]];
+    const SeqEntry e = seqs[si];
+    const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
+    const float sR = dot(xyz(e.pL), R) - e.pL.w;
+    const float3 P = R + (xyz(e.sL) - R) * (sR / (sR + e.sL.w));
+    float3 P1 = P;
+    if (e.info.w == 2) {
+        const float s1P = dot(xyz(e.p1), P) - e.p1.w;
+        P1 = P + (xyz(e.s1) - P) * (s1P / (s1P + e.s1.w));
+    }
+    pts[2 * i] = make_float4(P.x, P.y, P.z, 0.f);
+    pts[2 * i + 1] = make_float4(P1.x, P1.y, P1.z, 0.f);
+}
+
+// Occlusion of every segment of every candidate (segments in propagation order, early exit on the
+// first block); blocked candidates are set to -1. Persistent while-while traversal: each lane pulls
+// the next candidate from a warp-aggregated atomic counter as soon as its current one is finished,
+// and every loop iteration advances each busy lane by at most kSteps BVH visits, so lanes stay
+// busy while traversal lengths differ. FP64 endpoints are rebuilt only for the rare triangle whose
+// FP32 classification is too close to call. ctr[0..3]: candidates, segments, nodes, triangle tests.
+constexpr int kValThreads = 128;
+constexpr int kSteps = 8;
+
+__global__ void __launch_bounds__(kValThreads, 8)
+k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_face, int dst_face,
+           const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int* __restrict__ cand, int cap,
+           const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const float4* __restrict__ dpts,
+           long long total, unsigned long long* __restrict__ next, float tol_base, unsigned long long* refines,
+           int* err, unsigned long long* ctr)
+{
+    const float3 srcf = to_f(src);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    TraceCounters tc{};
+    long long item = -1;
+    int r = 0, slot = 0, si = 0, j = 0;
+    int4 info = make_int4(0, 0, 0, 0);
+    float3 p[4];
+    float3 a = f3(0.f, 0.f, 0.f), dir = a, inv = a;
+    float len = 0.f, tb = 0.f;
+    int ign0 = -1, ign1 = -1;
+    int stack[64];
+    int sp = 0;
+    bool blocked = false;
+
+    auto start_segment = [&]() {
+        a = p[j];
+        dir = p[j + 1] - a;
+        len = sqrtf(dot(dir, dir));
+        inv = f3(safe_inv(dir.x), safe_inv(dir.y), safe_inv(dir.z));
+        tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
+        ign0 = j == 0 ? src_face : (j == 1 ? info.x : info.y);
+        ign1 = j == info.w ? dst_face : (j == 0 ? info.x : info.y);
+        stack[0] = S.root;
+        sp = 1;
+        ++tc.segs;
+    };
+
+    while (true) {
+        const bool need = item < 0;
+        const unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                item = (long long)(base + __popc(m & ((1u << lane) - 1u)));
+                if (item < total) {
+                    r = dense_r[item];
+                    slot = dense_slot[item];
+                    si = cand[(int64_t)r * cap + slot];
+                    info = seqs[si].info;
+                    const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
+                    const float3 PL = xyz(dpts[2 * item]), P1 = xyz(dpts[2 * item + 1]);
+                    p[0] = srcf;
+                    if (info.w == 2) {
+                        p[1] = P1;
+                        p[2] = PL;
+                        p[3] = R;
+                    } else {
+                        p[1] = PL;
+                        p[2] = R;
+                        p[3] = R;
+                    }
+                    j = 0;
+                    blocked = false;
+                    ++tc.cand;
+                    start_segment();
+                }
+            }
+        }
+        const bool active = item >= 0 && item < total;
+        if (!__any_sync(FULL, active)) break;
+        if (!active) continue;
+        for (int it = 0; it < kSteps && sp > 0; ++it) {
+            const int c = stack[--sp];
+            if (c < 0) {
+                const int i = ~c;
+                const int f = S.tri_face[i];
+                if (f == ign0 || f == ign1) continue;
+                ++tc.tris;
+                const int h = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
+                bool hit = h == 1;
+                if (h == 2) {
+                    atomicAdd(refines, 1ull);
+                    const d3 R = D3((double)dst_xyz[3 * r], (double)dst_xyz[3 * r + 1], (double)dst_xyz[3 * r + 2]);
+                    d3 pts[4];
+                    seq_points_fp64(S, R, info, seqd[si], src, pts);
+                    const d3 dD = pts[j + 1] - pts[j];
+                    hit = tri_hit_fp64(S.tri_verts[i], pts[j], dD, norm(dD));
+                }
+                if (hit) {
+                    blocked = true;
+                    sp = 0;
+                }
+                continue;
+            }
+            const BvhNode nd = S.nodes[c];
+            ++tc.nodes;
+            const bool hl = box_overlap(nd.l_lo, nd.l_hi, a, inv);
+            const bool hr = box_overlap(nd.r_lo, nd.r_hi, a, inv);
+            if (sp + 2 > 64) {
+                atomicExch(err, 1);
+                blocked = true;
+                sp = 0;
+                break;
+            }
+            if (hr) stack[sp++] = __float_as_int(nd.l_hi.w);
+            if (hl) stack[sp++] = __float_as_int(nd.l_lo.w);
+        }
+        if (sp == 0) {
+            if (blocked) {
+                cand[(int64_t)r * cap + slot] = -1;
+                item = -1;
+            } else if (j < info.w) {
+                ++j;
+                start_segment();
+            } else {
+                item = -1;
+            }
+        }
+    }
+    flush_counters(tc, ctr);
 }
 
 // Per destination (one warp): keep the valid candidates, sorted by sequence id (rank sort; ids are
@@ -556,6 +770,7 @@ struct Candidates {
     int* cand = nullptr;
     int* cnt = nullptr;
     int64_t* cnt64 = nullptr;
+    int64_t* cnt64_tmp = nullptr;
     int cap = 0;
 };
 
@@ -678,6 +893,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             unsigned long long* counters;
             int* flags_dev;
             float* c_xyz;
+            int *dense_r, *dense_slot;
+            int64_t* dense_off;
+            float4* dense_pts;
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -693,9 +911,16 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.tot = A.get<int64_t>(n_rx + 1);
             L.env_cnt_tot = A.get<int64_t>(n_rx + 1);
             L.tx_vis = A.get<uint8_t>(M);
-            L.counters = A.get<unsigned long long>(4);
+            L.counters = A.get<unsigned long long>(8);
             L.flags_dev = A.get<int>(4);
             L.c_xyz = A.get<float>(3);
+            L.dense_r = A.get<int>((size_t)n_rx * cap);
+            L.dense_slot = A.get<int>((size_t)n_rx * cap);
+            L.dense_off = A.get<int64_t>(n_rx + 1);
+            L.dense_pts = A.get<float4>((size_t)n_rx * cap * 2);
+            L.crx.cnt64_tmp = A.get<int64_t>(n_rx + 1);
+            L.cenv.cnt64_tmp = L.crx.cnt64_tmp;
+            L.ctx_leg.cnt64_tmp = A.get<int64_t>(2);
         };
         Arena measure;
         Layout Lm;
@@ -720,7 +945,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         unsigned long long* counters = L.counters;
         int* flags_dev = L.flags_dev;
         float* c_xyz = L.c_xyz;
-        RISRT_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 4, s));
+        RISRT_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 8, s));
         RISRT_CUDA(ctx, cudaMemsetAsync(flags_dev, 0, sizeof(int) * 4, s));
         float cxyz[3] = {ris->center[0], ris->center[1], ris->center[2]};
         RISRT_CUDA(ctx, cudaMemcpyAsync(c_xyz, cxyz, sizeof(cxyz), cudaMemcpyHostToDevice, s));
@@ -733,7 +958,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             tab[i].n = 0;
             int64_t nid = n_ids_of[i];
             if (nid == 0) continue;
-            RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, flag)));
+            RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, src_of[i], flag)));
             RISRT_CUDA(ctx, exclusive_scan_i64(flag, pos, nid, scan_tmp, s));
             RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(nid, 256), 256, 0, s>>>(S, nid, flag, pos, src_of[i], tab[i].e, tab[i].d)));
             int64_t n_allowed = 0;
@@ -750,11 +975,35 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, s));
             if (t.n > 0) {
                 dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
-                RISRT_KERNEL(ctx, "k_candidates", (k_candidates<<<grid, kCandThreads, 0, s>>>(S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
-                                                           cs.cnt, cs.cap, flags_dev, counters)));
-                int64_t nthreads = n_dst * cs.cap;
-                RISRT_KERNEL(ctx, "k_validate", (k_validate<<<nblk(nthreads, 128), 128, 0, s>>>(S, dst, n_dst, src, src_face, dst_face, t.e, t.d,
-                                                               cs.cand, cs.cnt, cs.cap, tol_base, counters, flags_dev + 1)));
+                if (F <= kMaxSmemFaces) {
+                    const size_t shm = sizeof(FaceTest) * (size_t)F;
+                    cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+                    RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
+                                                          S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
+                                                          cs.cnt, cs.cap, flags_dev, counters)));
+                } else {
+                    RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
+                                                          S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
+                                                          cs.cnt, cs.cap, flags_dev, counters)));
+                }
+                // dense candidate list, then persistent validation
+                RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, s>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
+                RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, n_dst + 1, scan_tmp, s));
+                RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, s>>>(cs.cnt, L.dense_off, n_dst, cs.cap,
+                                                                                                   L.dense_r, L.dense_slot)));
+                long long total = 0;
+                RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + n_dst, sizeof(long long), cudaMemcpyDeviceToHost, s));
+                RISRT_CUDA(ctx, cudaMemsetAsync(counters + 6, 0, sizeof(unsigned long long), s));
+                RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+                if (total > 0) {
+                    RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<nblk(total, 256), 256, 0, s>>>(
+                                                           dst, t.e, cs.cand, cs.cap, L.dense_r, L.dense_slot, total, L.dense_pts)));
+                    const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * 8, (total + kValThreads - 1) / kValThreads);
+                    RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
+                                                        S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, L.dense_r,
+                                                        L.dense_slot, L.dense_pts, total, counters + 6, tol_base, counters, flags_dev + 1,
+                                                        counters + 2)));
+                }
             }
             const int warps = 4;
             size_t shm = sizeof(int) * (size_t)cs.cap * warps;
@@ -839,11 +1088,15 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_KERNEL(ctx, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, s>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off, n_rx, tab[2].e, ps->env_seq)));
         }
         RISRT_KERNEL(ctx, "k_units", (k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1)));
-        unsigned long long host_ctr[2];
+        unsigned long long host_ctr[6];
         RISRT_CUDA(ctx, cudaMemcpyAsync(host_ctr, counters, sizeof(host_ctr), cudaMemcpyDeviceToHost, s));
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));
         ps->fp64_refines = (int64_t)host_ctr[0];
         ps->units = (int64_t)host_ctr[1];
+        ps->n_candidates = (int64_t)host_ctr[2];
+        ps->n_segments = (int64_t)host_ctr[3];
+        ps->node_visits = (int64_t)host_ctr[4];
+        ps->tri_tests = (int64_t)host_ctr[5];
         return RISRT_OK;
     }
     return fail(ctx, RISRT_ERR_CAPACITY, "too many geometric path candidates per receiver");

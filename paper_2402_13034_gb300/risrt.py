@@ -62,7 +62,8 @@ class RisrtError(RuntimeError):
 class PathsetStats(C.Structure):
     _fields_ = [("n_rx", C.c_int64), ("M", C.c_int32), ("n_faces", C.c_int32), ("n_rx_paths", C.c_int64),
                 ("n_env_paths", C.c_int64), ("n_tx_paths", C.c_int32), ("units", C.c_int64),
-                ("fp64_refines", C.c_int64)]
+                ("fp64_refines", C.c_int64), ("n_candidates", C.c_int64), ("n_segments", C.c_int64),
+                ("node_visits", C.c_int64), ("tri_tests", C.c_int64)]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
