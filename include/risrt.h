@@ -202,6 +202,30 @@ int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma
 int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out);
 
 /* ------------------------------------------------------------------------------------------------
+ * Allocation-free path search (this entry point has no counterpart in the paper; it exists for
+ * callers that may not allocate device memory while they run, e.g. code executing where the CUDA
+ * allocator must not be touched or hosts that give the library a fixed memory budget)
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Valid reflected face sequences (length 1..max_order, ids as in risrt_pathset_export, ascending)
+ * between the points src and dst: the same search trace_paths runs for the Tx leg (src = Tx with
+ * src_face -1, dst = RIS centre with dst_face = the RIS host face), with the same validity rules
+ * (a face whose plane contains dst may not be the last bounce). It calls no cudaMalloc, cudaFree or
+ * allocating routine: its scratch is a 12 MiB array inside the library image, held by every GPU that
+ * loads the library until the process exits. Sizes beyond it fail with RISRT_ERR_CAPACITY (order 2
+ * fits scenes of up to about 250 faces, order 1 up to about 70000; at most 4096 geometric
+ * candidates). The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Every call uses the same array and clears what it
+ * needs, so calls whose GPU work overlaps (other streams, other threads, other contexts on the same
+ * device) race and must be serialised by the caller. Synchronises the context's stream.
+ *   src, dst     host [3] float points
+ *   ids_host     host [cap] int64, receives the ids; *n_host receives their number
+ * Errors: RISRT_ERR_INVALID_ARG; RISRT_ERR_CAPACITY (also when cap < number found). */
+int risrt_find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* scene, const float src[3], int32_t src_face,
+                             const float dst[3], int32_t dst_face, int32_t max_order, int64_t* ids_host,
+                             int32_t cap, int32_t* n_host);
+
+/* ------------------------------------------------------------------------------------------------
  * Tracing
  * ---------------------------------------------------------------------------------------------- */
 

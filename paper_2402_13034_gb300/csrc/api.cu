@@ -449,6 +449,22 @@ int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* 
     return build_A(ctx, ps, (float2*)A_out, (float2*)E0_out);
 }
 
+int risrt_find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* scene, const float src[3], int32_t src_face,
+                             const float dst[3], int32_t dst_face, int32_t max_order, int64_t* ids_host,
+                             int32_t cap, int32_t* n_host)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!scene || !src || !dst || !n_host || (cap > 0 && !ids_host) || cap < 0)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument or negative capacity");
+    if (max_order < 0 || max_order > 2) return fail(ctx, RISRT_ERR_INVALID_ARG, "order must be in [0, 2]");
+    if (src_face >= scene->n_faces || dst_face >= scene->n_faces)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "face index out of range");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(src[k]) || !std::isfinite(dst[k])) return fail(ctx, RISRT_ERR_INVALID_ARG, "non-finite point");
+    *n_host = 0;
+    return find_paths_noalloc(ctx, scene, src, src_face, dst, dst_face, max_order, ids_host, cap, n_host);
+}
+
 int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
 {
     if (!sc) return RISRT_OK;

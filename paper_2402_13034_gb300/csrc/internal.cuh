@@ -259,6 +259,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 double freq, int max_order_tx, int max_order_rx, uint32_t flags, risrt_pathset* ps);
 int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
 int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0);
+int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src[3], int src_face, const float dst[3],
+                       int dst_face, int max_order, int64_t* ids_host, int cap_host, int* n_host);
 
 // device-wide exclusive scan (int64 in/out), n <= 2^31; temp from scan_temp_bytes
 size_t scan_temp_bytes(int64_t n);

@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "geom.cuh"
 
@@ -321,7 +323,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     long long item = -1;
     int r = 0, slot = 0, si = 0, j = 0;
     int4 info = make_int4(0, 0, 0, 0);
-    float3 p[4];
+    float3 p[4] = {f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f)};
     float3 a = f3(0.f, 0.f, 0.f), dir = a, inv = a;
     float len = 0.f, tb = 0.f;
     int ign0 = -1, ign1 = -1;
@@ -1100,6 +1102,194 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         return RISRT_OK;
     }
     return fail(ctx, RISRT_ERR_CAPACITY, "too many geometric path candidates per receiver");
+}
+
+}  // namespace risrt
+
+// ================================================================================================
+// Allocation-free path search between two points.
+//
+// Some callers cannot allocate device memory while they run: code inside a region where the CUDA
+// allocator must not be touched (for instance a host callback or a section that runs while another
+// component owns every allocation), or hosts that hand this library a fixed memory budget and
+// forbid growth. For them, this entry point runs the reflected-path search of the Tx leg
+// (sequence table, candidate filter, BVH validation) on a scratch array that is part of the
+// library image itself, so it never calls cudaMalloc, cudaFree or any allocating routine.
+// ================================================================================================
+namespace risrt {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)12 << 20;   // 12 MiB on every GPU that loads the library
+constexpr int kNoAllocCands = 4096;                          // geometric candidates per call
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+}  // namespace risrt
+
+// The scratch array. In host code its name is only a stand-in for the device symbol: the device
+// address is obtained with cudaGetSymbolAddress below, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[risrt::kNoAllocScratchBytes];
+
+namespace risrt {
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on first use per device).
+int noalloc_scratch(risrt_ctx* ctx, char** out)
+{
+    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "device index too large for the static scratch table");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[ctx->device] = p;
+    }
+    *out = (char*)g_noalloc_ptr[ctx->device];
+    return RISRT_OK;
+}
+
+__global__ void k_ids_of(const int* __restrict__ cand, const int64_t* __restrict__ cnt,
+                         const SeqEntry* __restrict__ seqs, int64_t* __restrict__ ids)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (int)cnt[0]) ids[i] = seqs[cand[i]].info.z;
+}
+
+}  // namespace
+
+int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3], int src_face, const float dst3[3],
+                       int dst_face, int max_order, int64_t* ids_host, int cap_host, int* n_host)
+{
+    cudaStream_t s = ctx->stream;
+    const DeviceScene S = sc->dev();
+    const int F = sc->n_faces;
+    if (sc->n_tris == 0) max_order = 0;
+    const int64_t n_ids = max_order >= 2 ? (int64_t)F + (int64_t)F * F : (max_order >= 1 ? F : 0);
+    const int cap = kNoAllocCands;
+    Frame fr{};
+    for (int k = 0; k < 3; ++k) fr.c[k] = dst3[k];   // the exclusion rule looks at the destination
+    const d3 src = D3((double)src3[0], (double)src3[1], (double)src3[2]);
+    float ext = sc->scene_extent;
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, std::max(std::fabs(src3[k]), std::fabs(dst3[k])));
+    const float tol_base = 4e-6f * (1.f + 3.f * ext);
+
+    // layout inside the static array (measured first, then checked against its size)
+    struct Lay {
+        int64_t *flag, *pos, *cnt64, *cnt64_tmp, *dense_off, *ids;
+        void* scan_tmp;
+        SeqEntry* e;
+        SeqEntryD* d;
+        int *cand, *cnt, *dense_r, *dense_slot, *flags;
+        float4* dense_pts;
+        unsigned long long* counters;
+        float* dst;
+    };
+    auto layout = [&](Arena& A, Lay& L) {
+        L.flag = A.get<int64_t>(n_ids + 1);
+        L.pos = A.get<int64_t>(n_ids + 1);
+        L.scan_tmp = A.get<char>(scan_temp_bytes(std::max<int64_t>(n_ids, 2)));
+        L.e = A.get<SeqEntry>(n_ids + 1);
+        L.d = A.get<SeqEntryD>(n_ids + 1);
+        L.cand = A.get<int>(cap);
+        L.cnt = A.get<int>(1);
+        L.cnt64 = A.get<int64_t>(1);
+        L.cnt64_tmp = A.get<int64_t>(2);
+        L.dense_off = A.get<int64_t>(2);
+        L.dense_r = A.get<int>(cap);
+        L.dense_slot = A.get<int>(cap);
+        L.dense_pts = A.get<float4>(2 * (size_t)cap);
+        L.ids = A.get<int64_t>(cap);
+        L.counters = A.get<unsigned long long>(8);
+        L.flags = A.get<int>(4);
+        L.dst = A.get<float>(3);
+    };
+    Arena measure;
+    Lay Lm;
+    layout(measure, Lm);
+    if (measure.used > kNoAllocScratchBytes)
+        return fail(ctx, RISRT_ERR_CAPACITY,
+                    "path search needs " + std::to_string(measure.used) + " bytes, above the 12 MiB static scratch "
+                    "(order 2 fits up to about 250 faces, order 1 up to about 70000)");
+    char* base;
+    int rc = noalloc_scratch(ctx, &base);
+    if (rc) return rc;
+    Arena A{base, 0};
+    Lay L;
+    layout(A, L);
+
+    // the array keeps the previous call's contents: clear what must start at zero
+    RISRT_CUDA(ctx, cudaMemsetAsync(L.counters, 0, sizeof(unsigned long long) * 8, s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(L.flags, 0, sizeof(int) * 4, s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(L.cnt, 0, sizeof(int), s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(L.cnt64, 0, sizeof(int64_t), s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(L.dst, dst3, sizeof(float) * 3, cudaMemcpyHostToDevice, s));
+
+    int n_seq = 0;
+    if (n_ids > 0) {
+        RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(n_ids, 256), 256, 0, s>>>(S, n_ids, 0, fr, src, L.flag)));
+        RISRT_CUDA(ctx, exclusive_scan_i64(L.flag, L.pos, n_ids, L.scan_tmp, s));
+        RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(n_ids, 256), 256, 0, s>>>(S, n_ids, L.flag, L.pos, src, L.e, L.d)));
+        int64_t last[2];
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&last[0], L.pos + n_ids - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&last[1], L.flag + n_ids - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        n_seq = (int)(last[0] + last[1]);
+    }
+    if (n_seq > 0) {
+        dim3 grid(1, std::min<unsigned>(nblk(n_seq, kCandChunk), 32768u));
+        if (F <= kMaxSmemFaces) {
+            const size_t shm = sizeof(FaceTest) * (size_t)F;
+            cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
+                                                  S, L.dst, 1, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
+                                                  L.flags, L.counters)));
+        } else {
+            RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
+                                                  S, L.dst, 1, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
+                                                  L.flags, L.counters)));
+        }
+        RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<1, 32, 0, s>>>(L.cnt, 1, cap, L.cnt64_tmp)));
+        RISRT_CUDA(ctx, exclusive_scan_i64(L.cnt64_tmp, L.dense_off, 2, L.scan_tmp, s));
+        RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<1, 32, 0, s>>>(L.cnt, L.dense_off, 1, cap, L.dense_r, L.dense_slot)));
+        long long total = 0;
+        int host_flags[1] = {0};
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + 1, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(host_flags, L.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        if (host_flags[0]) return fail(ctx, RISRT_ERR_CAPACITY, "more than 4096 geometric candidates");
+        if (total > 0) {
+            RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<nblk(total, 256), 256, 0, s>>>(
+                                                   L.dst, L.e, L.cand, cap, L.dense_r, L.dense_slot, total, L.dense_pts)));
+            const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * 8, (total + kValThreads - 1) / kValThreads);
+            RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
+                                                S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
+                                                L.dense_slot, L.dense_pts, total, L.counters + 6, tol_base, L.counters,
+                                                L.flags + 1, L.counters + 2)));
+        }
+        const size_t shm = sizeof(int) * (size_t)cap;
+        cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RISRT_KERNEL(ctx, "k_finalize", (k_finalize<<<1, 32, shm, s>>>(L.cand, L.cnt, 1, cap, L.e, L.cnt64)));
+        RISRT_KERNEL(ctx, "k_ids_of", (k_ids_of<<<nblk(cap, 256), 256, 0, s>>>(L.cand, L.cnt64, L.e, L.ids)));
+    }
+    int64_t n = 0;
+    int stack_err = 0;
+    if (n_seq > 0) {
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n, L.cnt64, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&stack_err, L.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    if (stack_err) return fail(ctx, RISRT_ERR_CAPACITY, "BVH traversal stack overflow");
+    *n_host = (int)n;
+    if (n > cap_host) return fail(ctx, RISRT_ERR_CAPACITY, "ids_host is smaller than the number of paths found");
+    if (n > 0) {
+        RISRT_CUDA(ctx, cudaMemcpyAsync(ids_host, L.ids, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    return RISRT_OK;
 }
 
 }  // namespace risrt

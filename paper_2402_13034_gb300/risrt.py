@@ -41,6 +41,8 @@ _SIGS = {
     "risrt_pathset_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
+    "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
+                                           C.POINTER(C.c_int32)]),
     "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
     "risrt_profile_query": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "risrt_profile_names": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -282,6 +284,16 @@ class Context:
         n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
         self._check(load().risrt_eval_field(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"), n_cfg,
                                             _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def find_paths_noalloc(self, scene: Scene, src, src_face: int, dst, dst_face: int, max_order: int,
+                           cap: int = 4096) -> np.ndarray:
+        """Reflected face-sequence ids between two points without any device allocation."""
+        ids = np.zeros(max(cap, 1), np.int64)
+        n = C.c_int32()
+        self._check(load().risrt_find_paths_noalloc(self._ptr, scene.ptr, _ptr(_f32(src, 3)), int(src_face),
+                                                     _ptr(_f32(dst, 3)), int(dst_face), int(max_order), _ptr(ids),
+                                                     int(cap), C.byref(n)))
+        return ids[: n.value].copy()
 
     def build_A(self, ps: PathSet, A_out, E0_out=None):
         self._check(load().risrt_build_A(self._ptr, ps.ptr, _dev_ptr(A_out, "torch.complex64"),
