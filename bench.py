@@ -47,6 +47,89 @@ EVAL_OPS_PER_UNIT = 32
 # and for the ~half that pass it the reflection point (sub, div, 3 sub, 3 FMA) and the in-face test
 # of a two-triangle face (6 x (3 FMA + sub) + 2 min + 2 compares): counted as 8 + 0.5 * 40.
 CAND_OPS_PER_TEST = 28
+# BVH traversal: a node visit is two slab tests (6 sub/mul, 6 min/max, 4 compare each) = 24 lane ops;
+# a triangle test is a plane distance, hit point and three edge functions = 20 lane ops.
+VISIT_OPS, TRI_OPS = 24, 20
+PRECISIONS = {0: "fp32_simt", 1: "bf16", 2: "bf16x2", 3: "fp16"}
+
+
+def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
+    """E = E0 + A Gamma for every receiver and configuration on the sweep workload (room with a
+    32x32 RIS, 65,536 receivers, 4,096 two-bit configurations), per precision."""
+    import torch
+    from oracle import oracle as O
+    w = S.sweep(n_cfg=n_cfg)
+    scene, ris, rx = R.upload_workload(ctx, w)
+    ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w))
+    n, M = w.n_rx, w.n_elem
+    A = torch.empty((n, M), dtype=torch.complex64, device=dev)
+    E0 = torch.empty(n, dtype=torch.complex64, device=dev)
+    G = torch.from_numpy(w.gammas).to(dev)
+    P = torch.empty((n, n_cfg), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    ctx.profile_enable(True)
+    ctx.build_A(ps, A, E0)
+    t_A = timed(lambda: ctx.build_A(ps, A, E0), reps)
+    rows = np.unique(np.linspace(0, n - 1, oracle_rows).astype(int))
+    wo = S.sweep(n_cfg=n_cfg)
+    wo.rx_xyz = w.rx_xyz[rows]
+    fld = O.Oracle(wo).field(wo.rx_xyz)
+    E_ref, P_ref, S_ref = O.Oracle.evaluate(fld, w.gammas)
+    ok = ~fld["amb"]
+    strong = ok[:, None] & (P_ref >= 1e-3 * P_ref.max(0, keepdims=True))
+    flop = 8.0 * n * M * n_cfg
+    out = {"workload": w.name, "n_rx": n, "elements": M, "configs": n_cfg, "algorithmic_flop": flop,
+           "build_A_ms": t_A, "build_A_GBps": n * M * 8 / (t_A / 1e3) / 1e9}
+    for prec, name in PRECISIONS.items():
+        ws = ctx.sweep_workspace(n, M, n_cfg, prec)
+        ctx.sweep_configs(A, E0, G, P, prec, ws)
+        ctx.profile_reset()
+        ms = timed(lambda: ctx.sweep_configs(A, E0, G, P, prec, ws), reps if prec else 1)
+        prof = ctx.profile()
+        Pg = P[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
+        db = np.abs(10 * np.log10(np.maximum(Pg[strong], 1e-300) / P_ref[strong]))
+        dE = np.abs(np.sqrt(Pg * 2 * 120 * np.pi) - np.abs(E_ref)) / np.where(S_ref > 0, S_ref, 1)
+        ent = {"ms": ms, "tflops": flop / (ms / 1e3) / 1e12,
+               "db_err": {"median": float(np.median(db)), "p99": float(np.percentile(db, 99)),
+                          "max": float(db.max())},
+               "max_field_err_over_S": float(dE[ok].max())}
+        if "k_sweep_tc" in prof:
+            kms = prof["k_sweep_tc"][0] / prof["k_sweep_tc"][1]
+            Kp = ((4 if prec == 2 else 2) * M + 63) // 64 * 64
+            Np = (2 * n_cfg + 255) // 256 * 256
+            Mp = (n + 127) // 128 * 128
+            ent["kernel_ms"] = kms
+            ent["tensor_flop_per_launch"] = 2.0 * Mp * Np * Kp
+            ent["kernel_tflops_executed"] = 2.0 * Mp * Np * Kp / (kms / 1e3) / 1e12
+        out[name] = ent
+    ctx.profile_enable(False)
+    out["speedup_bf16_vs_fp32"] = out["fp32_simt"]["ms"] / out["bf16"]["ms"]
+    out["speedup_bf16x2_vs_fp32"] = out["fp32_simt"]["ms"] / out["bf16x2"]["ms"]
+    peaks = _peaks()
+    pk = peaks.get("bf16_tflops", 1876.6)
+    b = out["bf16"]
+    out["roofline"] = {"kernel": "k_sweep_tc", "bound": "tensor", "achieved": b.get("kernel_tflops_executed"),
+                       "peak": pk, "unit": "TFLOP/s",
+                       "frac": (b.get("kernel_tflops_executed") or 0) / pk, "traffic": None,
+                       "peak_note": "measured bf16 burst peak (cuBLAS) of this pool" if "bf16_tflops" in peaks
+                       else "fallback 1900 TF/s"}
+    for h in (ps, rx, ris, scene):
+        h.close()
+    return out
 
 
 def clocks_sampler(path):
@@ -136,6 +219,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
 
     w = S.room(grid=args.grid)
@@ -245,6 +329,8 @@ def main():
         alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12      # T lane-ops/s: 152 SMs x 128 FP32 lanes x clock
         if dom == "k_eval":
             work = st.units * n_cfg * EVAL_OPS_PER_UNIT
+        elif dom == "k_validate":
+            work = (st.node_visits * VISIT_OPS + st.tri_tests * TRI_OPS) / max(1, prof[dom][1] / args.steps - 1)
         elif dom == "k_candidates":
             F = st.n_faces
             n_seq = F + F * (F - 1)
@@ -295,6 +381,10 @@ def main():
         e2e = {"value": u_e2e / t_e2e * (world if world > 1 else 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = bench_sweep(ctx, R, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, samp = cpu_oracle_rate(w, n_cfg, budget_s=args.cpu_budget)
@@ -314,7 +404,7 @@ def main():
                            "bvh_node_visits": st.node_visits, "tri_tests": st.tri_tests,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
-                "stages": stages}
+                "stages": stages, "sweep": sweep}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -202,6 +202,33 @@ int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma
 int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out);
 
 /* ------------------------------------------------------------------------------------------------
+ * Configuration sweep (Eq. 9 is linear in Gamma; Eq. 10)
+ * ---------------------------------------------------------------------------------------------- */
+
+enum {
+    RISRT_PREC_FP32 = 0,    /* complex GEMM on the CUDA cores, FP32 */
+    RISRT_PREC_BF16 = 1,    /* tensor cores (tcgen05), BF16 operands, FP32 accumulation */
+    RISRT_PREC_BF16X2 = 2,  /* tensor cores, A split into BF16 hi + lo (Gamma rounded to BF16) */
+    RISRT_PREC_FP16 = 3     /* tensor cores, FP16 operands, A scaled by a power of two */
+};
+
+/* Bytes of device workspace risrt_sweep_configs needs for these sizes and precision (0 for FP32). */
+int risrt_sweep_workspace_size(int64_t n_rx, int32_t M, int32_t n_cfg, int precision, size_t* bytes);
+
+/* For every receiver r and configuration c:
+ *   P[r][c] = |E0[r] + sum_m A[r][m] Gamma[c][m]|^2 / (2 eta0)
+ *   A      [n_rx][M] complex64 (risrt_build_A)      E0 [n_rx] complex64 or NULL
+ *   gamma  [n_cfg][M] complex64                       P_out [n_rx][n_cfg] float
+ * The tensor-core precisions run the complex product as one real GEMM ([Re A | Im A] against
+ * interleaved [Re G, -Im G] / [Im G, Re G] rows) with the |E|^2 epilogue fused; they need a
+ * workspace of risrt_sweep_workspace_size bytes (16-byte aligned) and synchronise the stream.
+ * 1 <= M <= 65536, 1 <= n_cfg. Errors: RISRT_ERR_INVALID_ARG; RISRT_ERR_TIMEOUT if a pipeline wait
+ * in the tensor-core kernel expired (the kernel then stops and the output is incomplete). */
+int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M,
+                        const float* gamma, int32_t n_cfg, int precision, float* P_out, void* workspace,
+                        size_t workspace_bytes);
+
+/* ------------------------------------------------------------------------------------------------
  * Allocation-free path search (this entry point has no counterpart in the paper; it exists for
  * callers that may not allocate device memory while they run, e.g. code executing where the CUDA
  * allocator must not be touched or hosts that give the library a fixed memory budget)

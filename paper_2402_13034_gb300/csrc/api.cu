@@ -6,6 +6,7 @@
 #include <new>
 
 #include "internal.cuh"
+#include "sweep.cuh"
 
 namespace risrt {
 
@@ -447,6 +448,29 @@ int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* 
     if (!ps || !A_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
     if (((uintptr_t)A_out | (uintptr_t)E0_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
     return build_A(ctx, ps, (float2*)A_out, (float2*)E0_out);
+}
+
+int risrt_sweep_workspace_size(int64_t n_rx, int32_t M, int32_t n_cfg, int precision, size_t* bytes)
+{
+    if (!bytes || n_rx < 1 || M < 1 || n_cfg < 1 || precision < RISRT_PREC_FP32 || precision > RISRT_PREC_FP16)
+        return RISRT_ERR_INVALID_ARG;
+    *bytes = sweep_workspace_bytes(n_rx, M, n_cfg, precision);
+    return RISRT_OK;
+}
+
+int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M, const float* gamma,
+                        int32_t n_cfg, int precision, float* P_out, void* workspace, size_t workspace_bytes)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!A || !gamma || !P_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || M < 1 || M > 65536 || n_cfg < 1 || n_cfg > (1 << 24))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
+    if (precision < RISRT_PREC_FP32 || precision > RISRT_PREC_FP16) return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown precision");
+    if (((uintptr_t)A | (uintptr_t)gamma | (uintptr_t)E0) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    if (precision != RISRT_PREC_FP32 && ((uintptr_t)workspace & 15u))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    return sweep_configs(ctx, (const float2*)A, (const float2*)E0, n_rx, M, (const float2*)gamma, n_cfg, precision, P_out,
+                         workspace, workspace_bytes);
 }
 
 int risrt_find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* scene, const float src[3], int32_t src_face,

@@ -1,0 +1,30 @@
+// Shapes shared by the sweep packing kernels and the tensor-core GEMM.
+#pragma once
+
+#include "internal.cuh"
+
+namespace risrt {
+
+constexpr int kTcBM = 128;   // receivers per tile (TMEM lanes)
+constexpr int kTcBN = 256;   // real output columns per tile (128 configurations, re/im interleaved)
+constexpr int kTcBK = 64;    // 16-bit elements per stage row (128 B, one swizzle atom)
+constexpr int kTcStages = 4;
+
+struct SweepShape {
+    bool split;        // split-BF16: X carries hi and lo parts, K doubles
+    int Kp;            // padded K (multiple of kTcBK)
+    int Np;            // padded 2C (multiple of kTcBN)
+    int64_t Mp;        // padded receiver count (multiple of kTcBM)
+    size_t x_bytes, y_bytes;
+};
+
+SweepShape sweep_shape(int64_t n_rx, int M, int C, int precision);
+size_t sweep_workspace_bytes(int64_t n_rx, int M, int C, int precision);
+int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_rx, int M, const float2* G, int C,
+                  int precision, float* P, void* ws, size_t ws_bytes);
+// D = X . Y^T on tcgen05 (X: [n_rx][Kp], Y: [Np][Kp], 16-bit, K-major), then
+// P[r][c] = ((D[r][2c] + e0s Re E0[r])^2 + (D[r][2c+1] + e0s Im E0[r])^2) * pscale.
+int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh, bool fp16, const float2* E0,
+             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev);
+
+}  // namespace risrt

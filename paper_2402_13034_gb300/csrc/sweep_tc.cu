@@ -1,0 +1,277 @@
+// Tensor-core sweep GEMM for sm_103a: D = X . Y^T with X [receivers][K], Y [2C][K] in BF16 or FP16
+// (both K-major), FP32 accumulation in tensor memory, and the |E|^2 / (2 eta0) epilogue fused.
+//
+// One CTA computes a 128 x 256 tile (128 receivers x 128 configurations):
+//   warp 0     TMA producer: 128B-swizzled X and Y tiles of 64 K elements into a 4-stage ring
+//   warp 1     allocates 256 TMEM columns; one thread issues tcgen05.mma (M=128, N=256, K=16)
+//   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes, square re/im pairs, store P
+// Every mbarrier wait has a clock deadline; on expiry the kernel records an error, waits (again
+// bounded) for its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+
+#include <cstring>
+
+#include "sweep.cuh"
+
+namespace risrt {
+namespace {
+
+constexpr int kStageA = kTcBM * kTcBK * 2;   // 16 KB
+constexpr int kStageB = kTcBN * kTcBK * 2;   // 32 KB
+constexpr int kTmemCols = kTcBN;             // FP32 accumulator, one column per output column
+constexpr int kSmemBytes = kTcStages * (kStageA + kStageB) + 1024 + 256;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false once the deadline passes.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, long long deadline)
+{
+    while (!mbar_try(a, parity))
+        if (clock64() > deadline) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address (16-byte units)
+    d |= (uint64_t)1 << 16;                      // leading byte offset (not used by swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;                      // descriptor version for sm_100-class MMAs
+    d |= (uint64_t)2 << 61;                      // swizzle mode: 128 B
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(192, 1)
+k_sweep_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int num_kb, uint32_t idesc,
+           const float2* __restrict__ E0, int64_t n_rx, int C, float* __restrict__ P, float pscale, float e0scale,
+           unsigned* __restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kTcStages * kStageA;
+    uint64_t* full = (uint64_t*)(sB + kTcStages * kStageB);
+    uint64_t* empty = full + kTcStages;
+    uint64_t* tfull = empty + kTcStages;
+    uint32_t* tmem_slot = (uint32_t*)(tfull + 1);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * kTcBM;
+    const int n0 = blockIdx.y * kTcBN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(tfull), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const long long deadline = clock64() + kWaitCycles;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            int issued = 0;
+            for (int kb = 0; kb < num_kb; ++kb) {
+                const int s = kb % kTcStages;
+                const uint32_t ph = (kb / kTcStages) & 1;
+                if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, deadline) || *(volatile int*)&abort_flag) {
+                    atomicExch(err, 1u);
+                    *(volatile int*)&abort_flag = 1;
+                    break;
+                }
+                mbar_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
+                tma_load_2d(smem_u32(sA + s * kStageA), &tmX, smem_u32(&full[s]), kb * kTcBK, (int)m0);
+                tma_load_2d(smem_u32(sB + s * kStageB), &tmY, smem_u32(&full[s]), kb * kTcBK, n0);
+                ++issued;
+            }
+            if (*(volatile int*)&abort_flag) {   // let this CTA's own copies land before the shared memory is released
+                const long long d2 = clock64() + kWaitCycles;
+                for (int kb = (issued > kTcStages ? issued - kTcStages : 0); kb < issued; ++kb)
+                    mbar_wait(smem_u32(&full[kb % kTcStages]), (kb / kTcStages) & 1, d2);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            bool ok = true;
+            for (int kb = 0; kb < num_kb && ok; ++kb) {
+                const int s = kb % kTcStages;
+                if (!mbar_wait(smem_u32(&full[s]), (kb / kTcStages) & 1, deadline) || *(volatile int*)&abort_flag) {
+                    atomicExch(err, 1u);
+                    *(volatile int*)&abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t a0 = smem_u32(sA + s * kStageA), b0 = smem_u32(sB + s * kStageB);
+#pragma unroll
+                for (int k = 0; k < kTcBK / 16; ++k)
+                    mma_f16(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc, (kb | k) != 0);
+                mma_commit(smem_u32(&empty[s]));   // frees the stage once these MMAs have read it
+            }
+            mma_commit(smem_u32(tfull));           // accumulator complete (or issued work drained)
+        }
+    } else {   // epilogue warps 2..5: TMEM lanes 32*(warp%4) .. +31
+        const bool ok = mbar_wait(smem_u32(tfull), 0, deadline + kWaitCycles);
+        if (!ok) {
+            atomicExch(err, 1u);
+            *(volatile int*)&abort_flag = 1;
+        }
+        fence_after();
+        const int lane_base = 32 * (warp & 3);
+        const int64_t row = m0 + lane_base + lane;
+        const bool live = ok && !*(volatile int*)&abort_flag && row < n_rx;
+        float2 e0 = make_float2(0.f, 0.f);
+        if (live && E0) {
+            e0 = E0[row];
+            e0.x *= e0scale;
+            e0.y *= e0scale;
+        }
+        for (int j = 0; j < kTcBN / 16; ++j) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(j * 16), v);
+            if (!live) continue;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = (n0 >> 1) + j * 8 + q;
+                if (c < C) {
+                    const float er = v[2 * q] + e0.x, ei = v[2 * q + 1] + e0.y;
+                    P[row * C + c] = (er * er + ei * ei) * pscale;
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, bool fp16, int64_t rows, int cols, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh, bool fp16, const float2* E0,
+             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev)
+{
+    cudaStream_t s = ctx->stream;
+    CUtensorMap mX, mY;
+    if (((uintptr_t)X & 15) || ((uintptr_t)Y & 15)) return fail(ctx, RISRT_ERR_INVALID_ARG, "operands not 16-byte aligned");
+    if (!make_map(&mX, X, fp16, n_rx, sh.Kp, kTcBM) || !make_map(&mY, Y, fp16, sh.Np, sh.Kp, kTcBN))
+        return fail(ctx, RISRT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    // instruction descriptor (kind::f16): D = F32, A = B = BF16 or F16, both K-major, N/8, M/16
+    const uint32_t fmt = fp16 ? 0u : 1u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcBN >> 3) << 17) |
+                           ((uint32_t)(kTcBM >> 4) << 24);
+    RISRT_CUDA(ctx, cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    RISRT_CUDA(ctx, cudaMemsetAsync(err_dev, 0, sizeof(unsigned), s));
+    dim3 grid((unsigned)(sh.Mp / kTcBM), (unsigned)(sh.Np / kTcBN));
+    RISRT_KERNEL(ctx, "k_sweep_tc", (k_sweep_tc<<<grid, 192, kSmemBytes, s>>>(mX, mY, sh.Kp / kTcBK, idesc, E0, n_rx, C, P,
+                                                                            pscale, e0scale, err_dev)));
+    unsigned h = 0;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    if (h) return fail(ctx, RISRT_ERR_TIMEOUT, "tensor-core sweep: a pipeline wait expired");
+    return RISRT_OK;
+}
+
+}  // namespace risrt

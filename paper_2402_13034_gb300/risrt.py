@@ -19,6 +19,7 @@ OK = 0
 TX, RX = 0, 1
 PATTERN_ISO, PATTERN_COS_POW, PATTERN_MONOPOLE_QW = 0, 1, 2
 FLAG_ENV_PATHS, FLAG_FRESNEL_TM = 1, 2
+PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP16 = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -41,6 +42,8 @@ _SIGS = {
     "risrt_pathset_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
+    "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
+    "risrt_sweep_configs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int, _P, _P, C.c_size_t]),
     "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
                                            C.POINTER(C.c_int32)]),
     "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
@@ -284,6 +287,28 @@ class Context:
         n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
         self._check(load().risrt_eval_field(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"), n_cfg,
                                             _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def sweep_workspace(self, n_rx: int, M: int, n_cfg: int, precision: int):
+        """A device workspace tensor for sweep_configs (None for FP32)."""
+        import torch
+        nb = C.c_size_t()
+        rc = load().risrt_sweep_workspace_size(int(n_rx), int(M), int(n_cfg), int(precision), C.byref(nb))
+        if rc:
+            raise RisrtError(rc, "sweep workspace size")
+        if nb.value == 0:
+            return None
+        return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def sweep_configs(self, A, E0, gamma, P_out, precision: int, workspace=None):
+        """A: complex64 CUDA [n_rx, M]; E0: complex64 [n_rx] or None; gamma: complex64 [C, M];
+        P_out: float32 [n_rx, C]."""
+        n_rx, M = A.shape
+        n_cfg = gamma.shape[0]
+        ws_ptr = None if workspace is None else C.c_void_p(workspace.data_ptr())
+        ws_n = 0 if workspace is None else workspace.numel()
+        self._check(load().risrt_sweep_configs(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
+                                               int(n_rx), int(M), _dev_ptr(gamma, "torch.complex64"), int(n_cfg),
+                                               int(precision), _dev_ptr(P_out, "torch.float32"), ws_ptr, ws_n))
 
     def find_paths_noalloc(self, scene: Scene, src, src_face: int, dst, dst_face: int, max_order: int,
                            cap: int = 4096) -> np.ndarray:
