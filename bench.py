@@ -53,6 +53,58 @@ VISIT_OPS, TRI_OPS = 24, 20
 PRECISIONS = {0: "fp32_simt", 1: "bf16", 2: "bf16x2", 3: "fp16"}
 
 
+def bench_gradient(ctx, R, dev, steps=200, reps=5):
+    """Adjoint phase gradient on the office workload (20k triangles, 64x64 RIS, 16,384 target
+    receivers, 64 starting configurations): trace, A, time of one forward+adjoint step, and a
+    200-step Adam ascent."""
+    import torch
+    from paper_2402_13034_gb300.autograd import PhaseObjective, ascend
+    w = S.office()
+    scene, ris, rx = R.upload_workload(ctx, w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w))
+    torch.cuda.synchronize()
+    t_trace = time.perf_counter() - t0
+    n, M = w.n_rx, w.n_elem
+    A = torch.empty((n, M), dtype=torch.complex64, device=dev)
+    E0 = torch.empty(n, dtype=torch.complex64, device=dev)
+    ctx.build_A(ps, A, E0)
+    phases = torch.from_numpy(w.extra["phases"]).to(dev)
+    Bn = phases.shape[0]
+    obj = PhaseObjective(ctx, A, E0)
+    J = torch.empty(Bn, device=dev)
+    g = torch.empty((Bn, M), device=dev)
+    ws = obj.workspace(Bn)
+    ctx.grad_phases(A, E0, None, phases, None, J, g, ws)
+    stream = torch.cuda.current_stream(dev)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.grad_phases(A, E0, None, phases, None, J, g, ws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    t0 = time.perf_counter()
+    _, hist = ascend(obj, phases, steps=steps, lr=0.05)
+    torch.cuda.synchronize()
+    t_asc = time.perf_counter() - t0
+    h = hist.cpu().numpy()
+    st = ps.stats()
+    flop = 2 * 8.0 * n * M * Bn
+    out = {"workload": w.name, "triangles": int(len(w.scene.tris)), "elements": M, "targets": n, "configs": Bn,
+           "trace_s": t_trace, "rx_paths": st.n_rx_paths, "ms_per_grad_step": ms,
+           "tflops": flop / (ms / 1e3) / 1e12, "A_bytes_read_per_step": 2 * n * M * 8,
+           "hbm_GBps_equiv": 2 * n * M * 8 / (ms / 1e3) / 1e9, "ascent_steps": steps,
+           "ascent_s": t_asc, "J_mean_start": float(h[0].mean()), "J_mean_end": float(h[-1].mean()),
+           "J_gain_db_per_rx": float((h[-1].mean() - h[0].mean()) / n * 10 / np.log(10))}
+    for hh in (ps, rx, ris, scene):
+        hh.close()
+    return out
+
+
 def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
     """E = E0 + A Gamma for every receiver and configuration on the sweep workload (room with a
     32x32 RIS, 65,536 receivers, 4,096 two-bit configurations), per precision."""
@@ -220,6 +272,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     args = ap.parse_args()
 
     w = S.room(grid=args.grid)
@@ -384,6 +437,9 @@ def main():
     sweep = None
     if rank == 0 and not args.no_sweep:
         sweep = bench_sweep(ctx, R, dev)
+    grad = None
+    if rank == 0 and not args.no_grad:
+        grad = bench_gradient(ctx, R, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -404,7 +460,7 @@ def main():
                            "bvh_node_visits": st.node_visits, "tri_tests": st.tri_tests,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
-                "stages": stages, "sweep": sweep}
+                "stages": stages, "sweep": sweep, "gradient": grad}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

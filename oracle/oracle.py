@@ -226,3 +226,20 @@ class Oracle:
         if g.ndim == 1:
             return E[:, 0], P[:, 0], S[:, 0]
         return E, P, S
+
+
+def log_power_and_grad(fld: dict, phases: np.ndarray, amp=None):
+    """Objective J_b = sum_r log P_b(r) over the receivers of ``fld`` and its analytic gradient with
+    respect to every element phase, in FP64 (from Eq. 9 and Eq. 10):
+    dJ/dphi_bm = sum_r 2 Re(conj(E_b(r)) dE_b(r)/dphi_bm) / |E_b(r)|^2, dE/dphi_bm = j A[r][m] Gamma_bm.
+    |E|^2 is clamped below at 1e-30 of its maximum over the receivers of each configuration."""
+    ph = np.atleast_2d(np.asarray(phases, np.float64))
+    a = np.ones(ph.shape[1]) if amp is None else np.asarray(amp, np.float64)
+    G = a[None, :] * np.exp(1j * ph)                       # [B, M]
+    E = fld["E0"][None, :] + G @ fld["A"].T                # [B, n]
+    p2 = np.abs(E) ** 2
+    p2 = np.maximum(p2, 1e-30 * p2.max(axis=1, keepdims=True))
+    J = np.sum(np.log(p2 / (2 * ETA0)), axis=1)
+    dE = 1j * G[:, None, :] * fld["A"][None, :, :]         # [B, n, M]
+    grad = np.sum(2 * np.real(np.conj(E)[:, :, None] * dE) / p2[:, :, None], axis=1)
+    return J, grad

@@ -473,6 +473,34 @@ int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t
                          workspace, workspace_bytes);
 }
 
+int risrt_grad_workspace_size(int32_t n_target, int32_t B, size_t* bytes)
+{
+    if (!bytes || n_target < 1 || B < 1) return RISRT_ERR_INVALID_ARG;
+    *bytes = grad_workspace_bytes(n_target, B) + 64;
+    return RISRT_OK;
+}
+
+int risrt_grad_phases(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M, const int32_t* target,
+                      int32_t n_target, const float* phases, const float* amp, int32_t B, float* J_out, float* grad_out,
+                      void* workspace, size_t workspace_bytes)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!A || !phases || !J_out || !grad_out || !workspace) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (n_rx < 1 || M < 1 || M > 65536 || n_target < 1 || B < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
+    if (!target && n_target > n_rx) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_target > n_rx without a target list");
+    if (workspace_bytes < grad_workspace_bytes(n_target, B) + 64) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace too small");
+    if (((uintptr_t)A | (uintptr_t)E0 | (uintptr_t)workspace) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "misaligned array");
+    if (target) {
+        int rc = check_targets(ctx, target, n_target, n_rx, workspace, workspace_bytes);
+        if (rc) return rc;
+    }
+    int rc = grad_phases(ctx, (const float2*)A, (const float2*)E0, M, target, n_target, phases, amp, B, J_out, grad_out,
+                         workspace);
+    if (rc) return rc;
+    RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RISRT_OK;
+}
+
 int risrt_find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* scene, const float src[3], int32_t src_face,
                              const float dst[3], int32_t dst_face, int32_t max_order, int64_t* ids_host,
                              int32_t cap, int32_t* n_host)

@@ -1,0 +1,229 @@
+// Adjoint of the received power with respect to every element's phase (from Eq. 9 and Eq. 10):
+//   Gamma_bm = amp_m e^{j phi_bm},  E_b(r) = E0(r) + sum_m A[r][m] Gamma_bm,  P = |E|^2 / (2 eta0)
+//   J_b = sum_{r in T} log P_b(r)
+//   dJ_b/dphi_bm = -2 Im( Gamma_bm sum_{r in T} A[r][m] conj(E_b(r)) / |E_b(r)|^2 )
+// |E|^2 is clamped from below at 1e-30 max_r |E_b(r)|^2 on both sides of the comparison.
+// Three passes, all FP32 on the CUDA cores: forward GEMM over the target rows (E), the per-config
+// clamp, log and weights w = conj(E)/|E|^2, and the backward GEMM A^T w with the phase epilogue.
+#include "internal.cuh"
+
+namespace risrt {
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+__global__ void k_check_targets(const int* __restrict__ target, int n_t, int64_t n_rx, int* __restrict__ bad)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_t && (target[t] < 0 || target[t] >= n_rx)) atomicExch(bad, 1);
+}
+
+constexpr int kFR = 64, kFB = 64, kFK = 16;   // forward tile: 64 target rows x 64 configs
+
+// E[b][t] = E0[r_t] + sum_m A[r_t][m] Gamma_bm for target t (row r_t).
+__global__ void __launch_bounds__(256)
+k_adj_forward(const float2* __restrict__ A, const float2* __restrict__ E0, int M, const int* __restrict__ target,
+              int n_t, const float* __restrict__ phases, const float* __restrict__ amp, int B, float2* __restrict__ E)
+{
+    __shared__ float2 sA[kFK][kFR + 1];
+    __shared__ float2 sG[kFK][kFB + 1];
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tb = tid % 16;    // 4 rows x 4 configs per thread
+    const int t0 = blockIdx.x * kFR, b0 = blockIdx.y * kFB;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < M; k0 += kFK) {
+        for (int i = tid; i < kFR * kFK; i += 256) {
+            const int rr = i / kFK, kk = i % kFK;
+            const int t = t0 + rr, k = k0 + kk;
+            float2 v = make_float2(0.f, 0.f);
+            if (t < n_t && k < M) {
+                const int64_t r = target ? target[t] : t;
+                v = A[r * M + k];
+            }
+            sA[kk][rr] = v;
+        }
+        for (int i = tid; i < kFB * kFK; i += 256) {
+            const int bb = i / kFK, kk = i % kFK;
+            const int b = b0 + bb, k = k0 + kk;
+            float2 g = make_float2(0.f, 0.f);
+            if (b < B && k < M) {
+                float sn, cs;
+                sincosf(phases[(int64_t)b * M + k], &sn, &cs);
+                const float a = amp ? amp[k] : 1.f;
+                g = make_float2(a * cs, a * sn);
+            }
+            sG[kk][bb] = g;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kFK; ++kk) {
+            float2 a[4], g[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sA[kk][tr + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[j] = sG[kk][tb + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fmaf(a[i].x, g[j].x, fmaf(-a[i].y, g[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(a[i].x, g[j].y, fmaf(a[i].y, g[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int t = t0 + tr + 16 * i;
+        if (t >= n_t) continue;
+        const int64_t r = target ? target[t] : t;
+        const float2 e0 = E0 ? E0[r] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = b0 + tb + 16 * j;
+            if (b < B) E[(int64_t)b * n_t + t] = make_float2(acc[i][j].x + e0.x, acc[i][j].y + e0.y);
+        }
+    }
+}
+
+// Per configuration (one block): clamp floor, J_b = sum log(|E|^2 / (2 eta0)), w = conj(E)/|E|^2.
+// Fixed-order reductions (block tree) keep J deterministic.
+__global__ void __launch_bounds__(512)
+k_adj_weights(float2* __restrict__ E, int n_t, float* __restrict__ J, float inv_2eta0)
+{
+    __shared__ double red[512];
+    const int b = blockIdx.x;
+    float2* e = E + (int64_t)b * n_t;
+    float mx = 0.f;
+    for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
+        const float2 v = e[t];
+        mx = fmaxf(mx, v.x * v.x + v.y * v.y);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const float floor_ = (float)(red[0] * 1e-30);
+    __syncthreads();
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
+        const float2 v = e[t];
+        const float p = fmaxf(v.x * v.x + v.y * v.y, floor_);
+        acc += log((double)p * (double)inv_2eta0);
+        e[t] = make_float2(v.x / p, -v.y / p);      // w = conj(E) / |E|^2 (E is overwritten)
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) J[b] = (float)red[0];
+}
+
+constexpr int kBM = 64, kBB = 64, kBK = 16;   // backward tile: 64 elements x 64 configs
+
+// g[b][m] = sum_t A[r_t][m] w[b][t];  grad[b][m] = -2 Im(Gamma_bm g[b][m]).
+__global__ void __launch_bounds__(256)
+k_adj_backward(const float2* __restrict__ A, int M, const int* __restrict__ target, int n_t,
+               const float2* __restrict__ W, const float* __restrict__ phases, const float* __restrict__ amp, int B,
+               float* __restrict__ grad)
+{
+    __shared__ float2 sA[kBK][kBM + 1];
+    __shared__ float2 sW[kBK][kBB + 1];
+    const int tid = threadIdx.x;
+    const int tm = tid % 16, tb = tid / 16;   // 4 elements x 4 configs per thread
+    const int m0 = blockIdx.x * kBM, b0 = blockIdx.y * kBB;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < n_t; k0 += kBK) {
+        for (int i = tid; i < kBM * kBK; i += 256) {        // coalesced along elements
+            const int kk = i / kBM, mm = i % kBM;
+            const int t = k0 + kk, m = m0 + mm;
+            float2 v = make_float2(0.f, 0.f);
+            if (t < n_t && m < M) {
+                const int64_t r = target ? target[t] : t;
+                v = A[r * M + m];
+            }
+            sA[kk][mm] = v;
+        }
+        for (int i = tid; i < kBB * kBK; i += 256) {
+            const int bb = i / kBK, kk = i % kBK;
+            const int b = b0 + bb, t = k0 + kk;
+            sW[kk][bb] = (b < B && t < n_t) ? W[(int64_t)b * n_t + t] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            float2 a[4], w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sA[kk][tm + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = sW[kk][tb + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fmaf(a[i].x, w[j].x, fmaf(-a[i].y, w[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(a[i].x, w[j].y, fmaf(a[i].y, w[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + tm + 16 * i;
+        if (m >= M) continue;
+        const float a = amp ? amp[m] : 1.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = b0 + tb + 16 * j;
+            if (b >= B) continue;
+            float sn, cs;
+            sincosf(phases[(int64_t)b * M + m], &sn, &cs);
+            // Im(Gamma g) with Gamma = a (cs + j sn)
+            const float im = a * (cs * acc[i][j].y + sn * acc[i][j].x);
+            grad[(int64_t)b * M + m] = -2.f * im;
+        }
+    }
+}
+
+}  // namespace
+
+size_t grad_workspace_bytes(int n_t, int B) { return sizeof(float2) * (size_t)n_t * B + 256; }
+
+int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes)
+{
+    int* bad = (int*)((char*)ws + ws_bytes - 16);
+    RISRT_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    RISRT_KERNEL(ctx, "k_check_targets", (k_check_targets<<<nblk(n_t, 256), 256, 0, ctx->stream>>>(target, n_t, n_rx, bad)));
+    int h = 0;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h) return fail(ctx, RISRT_ERR_INVALID_ARG, "a target row is outside [0, n_rx)");
+    return RISRT_OK;
+}
+
+int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
+                const float* phases, const float* amp, int B, float* J, float* grad, void* ws)
+{
+    cudaStream_t s = ctx->stream;
+    float2* E = (float2*)ws;
+    RISRT_KERNEL(ctx, "k_adj_forward", (k_adj_forward<<<dim3(nblk(n_t, kFR), nblk(B, kFB)), 256, 0, s>>>(
+                                           A, E0, M, target, n_t, phases, amp, B, E)));
+    RISRT_KERNEL(ctx, "k_adj_weights", (k_adj_weights<<<B, 512, 0, s>>>(E, n_t, J, (float)(1.0 / (2.0 * kEta0)))));
+    RISRT_KERNEL(ctx, "k_adj_backward", (k_adj_backward<<<dim3(nblk(M, kBM), nblk(B, kBB)), 256, 0, s>>>(
+                                            A, M, target, n_t, E, phases, amp, B, grad)));
+    return RISRT_OK;
+}
+
+}  // namespace risrt

@@ -44,6 +44,9 @@ _SIGS = {
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
     "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_sweep_configs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int, _P, _P, C.c_size_t]),
+    "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P,
+                                    C.c_size_t]),
     "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
                                            C.POINTER(C.c_int32)]),
     "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
@@ -309,6 +312,27 @@ class Context:
         self._check(load().risrt_sweep_configs(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
                                                int(n_rx), int(M), _dev_ptr(gamma, "torch.complex64"), int(n_cfg),
                                                int(precision), _dev_ptr(P_out, "torch.float32"), ws_ptr, ws_n))
+
+    def grad_workspace(self, n_target: int, B: int):
+        import torch
+        nb = C.c_size_t()
+        rc = load().risrt_grad_workspace_size(int(n_target), int(B), C.byref(nb))
+        if rc:
+            raise RisrtError(rc, "grad workspace size")
+        return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def grad_phases(self, A, E0, target, phases, amp, J_out, grad_out, workspace=None):
+        """A: complex64 CUDA [n_rx, M]; target: int32 CUDA [n_t] or None (first n_t rows given by
+        phases' companion J); phases: float32 [B, M]; amp: float32 [M] or None; J_out [B]; grad_out [B, M]."""
+        n_rx, M = A.shape
+        B = phases.shape[0]
+        n_t = target.numel() if target is not None else n_rx
+        ws = workspace if workspace is not None else self.grad_workspace(n_t, B)
+        self._check(load().risrt_grad_phases(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
+                                             int(n_rx), int(M), _dev_ptr(target, "torch.int32"), int(n_t),
+                                             _dev_ptr(phases, "torch.float32"), _dev_ptr(amp, "torch.float32"), int(B),
+                                             _dev_ptr(J_out, "torch.float32"), _dev_ptr(grad_out, "torch.float32"),
+                                             C.c_void_p(ws.data_ptr()), ws.numel()))
 
     def find_paths_noalloc(self, scene: Scene, src, src_face: int, dst, dst_face: int, max_order: int,
                            cap: int = 4096) -> np.ndarray:
