@@ -105,6 +105,42 @@ def bench_gradient(ctx, R, dev, steps=200, reps=5):
     return out
 
 
+def bench_serving(dev_index, n_req=64, rate_hz=2000.0, slots=4):
+    """Seeded Poisson stream (mean rate_hz) of coverage and sweep requests over three room scenes
+    with 10/40/80 boxes and 37- or 127-element RIS, grids 16^2..128^2, 1..64 configurations;
+    requests are submitted at their arrival times."""
+    from paper_2402_13034_gb300 import serve
+    scenes = {}
+    for i, nb in enumerate((10, 40, 80)):
+        w = S.room(grid=8, n_boxes=nb, seed_index=10 + i)
+        w.name = f"room_{nb}boxes"
+        if i == 0:
+            w.ris.elem_uv = S.hex_layout(3, S.C0 / w.freq_hz / 2)
+            w.gammas = w.gammas[:, :37]
+        scenes[w.name] = w
+    reqs = serve.poisson_requests(S.SEED_BASE + 4, n_req, rate_hz, scenes)
+    srv = serve.Server(device=dev_index, slots=slots)
+    for name, w in scenes.items():
+        srv.add_scene(name, w.scene)
+    # warm the slot contexts and scene caches with one request per scene
+    srv.drain([srv.submit(r) for _, r in reqs[:3]])
+    t0 = time.perf_counter()
+    futs = []
+    for t_arr, r in reqs:
+        dt = t0 + t_arr - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        futs.append(srv.submit(r))
+    res = srv.drain(futs)
+    wall = time.perf_counter() - t0
+    srv.close()
+    out = serve.latency_stats(res)
+    out.update({"requests": n_req, "offered_rate_hz": rate_hz, "throughput_req_s": n_req / wall, "slots": slots,
+                "peak_admitted_bytes": srv.admission.peak, "budget_bytes": srv.admission.budget,
+                "units_per_s": None})
+    return out
+
+
 def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
     """E = E0 + A Gamma for every receiver and configuration on the sweep workload (room with a
     32x32 RIS, 65,536 receivers, 4,096 two-bit configurations), per precision."""
@@ -273,6 +309,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
 
     w = S.room(grid=args.grid)
@@ -440,6 +477,9 @@ def main():
     grad = None
     if rank == 0 and not args.no_grad:
         grad = bench_gradient(ctx, R, dev)
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = bench_serving(local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -460,7 +500,7 @@ def main():
                            "bvh_node_visits": st.node_visits, "tri_tests": st.tri_tests,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
-                "stages": stages, "sweep": sweep, "gradient": grad}
+                "stages": stages, "sweep": sweep, "gradient": grad, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

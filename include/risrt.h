@@ -232,8 +232,8 @@ int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t
  * Phase gradient (adjoint of Eq. 9 and Eq. 10)
  * ---------------------------------------------------------------------------------------------- */
 
-/* Workspace bytes for risrt_grad_phases (n_target receivers, B configurations). */
-int risrt_grad_workspace_size(int32_t n_target, int32_t B, size_t* bytes);
+/* Workspace bytes for risrt_grad_phases (n_target receivers, B configurations, M elements). */
+int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, size_t* bytes);
 
 /* For B phase configurations Gamma_bm = amp_m e^{j phases[b][m]}:
  *   J[b]       = sum_{t} log P_b(target[t]),  P = |E0 + A Gamma_b|^2 / (2 eta0)
@@ -242,7 +242,8 @@ int risrt_grad_workspace_size(int32_t n_target, int32_t B, size_t* bytes);
  *   A [n_rx][M] complex64, E0 [n_rx] complex64 or NULL, target [n_target] int32 rows of A
  *   (NULL: rows 0..n_target-1), phases [B][M] float, amp [M] float or NULL (1), J_out [B] float,
  *   grad_out [B][M] float, workspace of risrt_grad_workspace_size bytes. All device memory.
- * FP32 arithmetic, A read twice (forward and adjoint GEMM). Synchronises the stream (the target
+ * FP32 arithmetic, A read twice (forward and adjoint GEMM, each split over its reduction axis with the
+ * partial sums added in a fixed order, so results do not depend on scheduling). Synchronises the stream (the target
  * rows are validated on the device). Errors: RISRT_ERR_INVALID_ARG (sizes, a target row outside
  * [0, n_rx)). */
 int risrt_grad_phases(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M,

@@ -37,7 +37,7 @@ class PhaseObjective:
     def workspace(self, B: int):
         if B not in self._ws:
             n_t = self.target.numel() if self.target is not None else self.A.shape[0]
-            self._ws[B] = self.lib.grad_workspace(n_t, B)
+            self._ws[B] = self.lib.grad_workspace(n_t, B, self.A.shape[1])
         return self._ws[B]
 
     def __call__(self, phases):

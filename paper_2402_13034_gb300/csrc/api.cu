@@ -473,10 +473,10 @@ int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t
                          workspace, workspace_bytes);
 }
 
-int risrt_grad_workspace_size(int32_t n_target, int32_t B, size_t* bytes)
+int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, size_t* bytes)
 {
-    if (!bytes || n_target < 1 || B < 1) return RISRT_ERR_INVALID_ARG;
-    *bytes = grad_workspace_bytes(n_target, B) + 64;
+    if (!bytes || n_target < 1 || B < 1 || M < 1) return RISRT_ERR_INVALID_ARG;
+    *bytes = grad_workspace_bytes(n_target, B, M) + 64;
     return RISRT_OK;
 }
 
@@ -488,7 +488,7 @@ int risrt_grad_phases(risrt_ctx* ctx, const float* A, const float* E0, int64_t n
     if (!A || !phases || !J_out || !grad_out || !workspace) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
     if (n_rx < 1 || M < 1 || M > 65536 || n_target < 1 || B < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
     if (!target && n_target > n_rx) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_target > n_rx without a target list");
-    if (workspace_bytes < grad_workspace_bytes(n_target, B) + 64) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace too small");
+    if (workspace_bytes < grad_workspace_bytes(n_target, B, M) + 64) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace too small");
     if (((uintptr_t)A | (uintptr_t)E0 | (uintptr_t)workspace) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "misaligned array");
     if (target) {
         int rc = check_targets(ctx, target, n_target, n_rx, workspace, workspace_bytes);

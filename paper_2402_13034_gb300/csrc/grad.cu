@@ -5,6 +5,8 @@
 // |E|^2 is clamped from below at 1e-30 max_r |E_b(r)|^2 on both sides of the comparison.
 // Three passes, all FP32 on the CUDA cores: forward GEMM over the target rows (E), the per-config
 // clamp, log and weights w = conj(E)/|E|^2, and the backward GEMM A^T w with the phase epilogue.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace risrt {
@@ -23,24 +25,26 @@ constexpr int kFR = 64, kFB = 64, kFK = 16;   // forward tile: 64 target rows x 
 // E[b][t] = E0[r_t] + sum_m A[r_t][m] Gamma_bm for target t (row r_t).
 __global__ void __launch_bounds__(256)
 k_adj_forward(const float2* __restrict__ A, const float2* __restrict__ E0, int M, const int* __restrict__ target,
-              int n_t, const float* __restrict__ phases, const float* __restrict__ amp, int B, float2* __restrict__ E)
+              int n_t, const float* __restrict__ phases, const float* __restrict__ amp, int B, int k_chunk,
+              float2* __restrict__ E)
 {
     __shared__ float2 sA[kFK][kFR + 1];
     __shared__ float2 sG[kFK][kFB + 1];
     const int tid = threadIdx.x;
     const int tr = tid / 16, tb = tid % 16;    // 4 rows x 4 configs per thread
     const int t0 = blockIdx.x * kFR, b0 = blockIdx.y * kFB;
+    const int k_begin = blockIdx.z * k_chunk, k_end = min(M, k_begin + k_chunk);
     float2 acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    for (int k0 = 0; k0 < M; k0 += kFK) {
+    for (int k0 = k_begin; k0 < k_end; k0 += kFK) {
         for (int i = tid; i < kFR * kFK; i += 256) {
             const int rr = i / kFK, kk = i % kFK;
             const int t = t0 + rr, k = k0 + kk;
             float2 v = make_float2(0.f, 0.f);
-            if (t < n_t && k < M) {
+            if (t < n_t && k < k_end) {
                 const int64_t r = target ? target[t] : t;
                 v = A[r * M + k];
             }
@@ -50,7 +54,7 @@ k_adj_forward(const float2* __restrict__ A, const float2* __restrict__ E0, int M
             const int bb = i / kFK, kk = i % kFK;
             const int b = b0 + bb, k = k0 + kk;
             float2 g = make_float2(0.f, 0.f);
-            if (b < B && k < M) {
+            if (b < B && k < k_end) {
                 float sn, cs;
                 sincosf(phases[(int64_t)b * M + k], &sn, &cs);
                 const float a = amp ? amp[k] : 1.f;
@@ -81,11 +85,12 @@ k_adj_forward(const float2* __restrict__ A, const float2* __restrict__ E0, int M
         const int t = t0 + tr + 16 * i;
         if (t >= n_t) continue;
         const int64_t r = target ? target[t] : t;
-        const float2 e0 = E0 ? E0[r] : make_float2(0.f, 0.f);
+        const float2 e0 = (E0 && blockIdx.z == 0) ? E0[r] : make_float2(0.f, 0.f);
+        float2* Ez = E + (int64_t)blockIdx.z * B * n_t;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int b = b0 + tb + 16 * j;
-            if (b < B) E[(int64_t)b * n_t + t] = make_float2(acc[i][j].x + e0.x, acc[i][j].y + e0.y);
+            if (b < B) Ez[(int64_t)b * n_t + t] = make_float2(acc[i][j].x + e0.x, acc[i][j].y + e0.y);
         }
     }
 }
@@ -93,14 +98,20 @@ k_adj_forward(const float2* __restrict__ A, const float2* __restrict__ E0, int M
 // Per configuration (one block): clamp floor, J_b = sum log(|E|^2 / (2 eta0)), w = conj(E)/|E|^2.
 // Fixed-order reductions (block tree) keep J deterministic.
 __global__ void __launch_bounds__(512)
-k_adj_weights(float2* __restrict__ E, int n_t, float* __restrict__ J, float inv_2eta0)
+k_adj_weights(float2* __restrict__ E, int n_t, int B, int splits, float* __restrict__ J, float inv_2eta0)
 {
     __shared__ double red[512];
     const int b = blockIdx.x;
     float2* e = E + (int64_t)b * n_t;
     float mx = 0.f;
     for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
-        const float2 v = e[t];
+        float2 v = e[t];
+        for (int z = 1; z < splits; ++z) {          // fixed-order sum of the split-K partials
+            const float2 u = E[((int64_t)z * B + b) * n_t + t];
+            v.x += u.x;
+            v.y += u.y;
+        }
+        e[t] = v;
         mx = fmaxf(mx, v.x * v.x + v.y * v.y);
     }
     red[threadIdx.x] = mx;
@@ -132,25 +143,25 @@ constexpr int kBM = 64, kBB = 64, kBK = 16;   // backward tile: 64 elements x 64
 // g[b][m] = sum_t A[r_t][m] w[b][t];  grad[b][m] = -2 Im(Gamma_bm g[b][m]).
 __global__ void __launch_bounds__(256)
 k_adj_backward(const float2* __restrict__ A, int M, const int* __restrict__ target, int n_t,
-               const float2* __restrict__ W, const float* __restrict__ phases, const float* __restrict__ amp, int B,
-               float* __restrict__ grad)
+               const float2* __restrict__ W, int B, int t_chunk, float2* __restrict__ Gp)
 {
     __shared__ float2 sA[kBK][kBM + 1];
     __shared__ float2 sW[kBK][kBB + 1];
     const int tid = threadIdx.x;
     const int tm = tid % 16, tb = tid / 16;   // 4 elements x 4 configs per thread
     const int m0 = blockIdx.x * kBM, b0 = blockIdx.y * kBB;
+    const int t_begin = blockIdx.z * t_chunk, t_end = min(n_t, t_begin + t_chunk);
     float2 acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    for (int k0 = 0; k0 < n_t; k0 += kBK) {
+    for (int k0 = t_begin; k0 < t_end; k0 += kBK) {
         for (int i = tid; i < kBM * kBK; i += 256) {        // coalesced along elements
             const int kk = i / kBM, mm = i % kBM;
             const int t = k0 + kk, m = m0 + mm;
             float2 v = make_float2(0.f, 0.f);
-            if (t < n_t && m < M) {
+            if (t < t_end && m < M) {
                 const int64_t r = target ? target[t] : t;
                 v = A[r * M + m];
             }
@@ -159,7 +170,7 @@ k_adj_backward(const float2* __restrict__ A, int M, const int* __restrict__ targ
         for (int i = tid; i < kBB * kBK; i += 256) {
             const int bb = i / kBK, kk = i % kBK;
             const int b = b0 + bb, t = k0 + kk;
-            sW[kk][bb] = (b < B && t < n_t) ? W[(int64_t)b * n_t + t] : make_float2(0.f, 0.f);
+            sW[kk][bb] = (b < B && t < t_end) ? W[(int64_t)b * n_t + t] : make_float2(0.f, 0.f);
         }
         __syncthreads();
 #pragma unroll
@@ -179,27 +190,64 @@ k_adj_backward(const float2* __restrict__ A, int M, const int* __restrict__ targ
         }
         __syncthreads();
     }
+    float2* Gz = Gp + (int64_t)blockIdx.z * B * M;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int m = m0 + tm + 16 * i;
         if (m >= M) continue;
-        const float a = amp ? amp[m] : 1.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int b = b0 + tb + 16 * j;
-            if (b >= B) continue;
-            float sn, cs;
-            sincosf(phases[(int64_t)b * M + m], &sn, &cs);
-            // Im(Gamma g) with Gamma = a (cs + j sn)
-            const float im = a * (cs * acc[i][j].y + sn * acc[i][j].x);
-            grad[(int64_t)b * M + m] = -2.f * im;
+            if (b < B) Gz[(int64_t)b * M + m] = acc[i][j];
         }
     }
 }
 
+// grad[b][m] = -2 Im(Gamma_bm g[b][m]), g summed over the split partials in a fixed order.
+__global__ void k_adj_grad(const float2* __restrict__ Gp, int splits, const float* __restrict__ phases,
+                           const float* __restrict__ amp, int B, int M, float* __restrict__ grad)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * M) return;
+    const int m = (int)(i % M);
+    float2 g = Gp[i];
+    for (int z = 1; z < splits; ++z) {
+        const float2 u = Gp[(int64_t)z * B * M + i];
+        g.x += u.x;
+        g.y += u.y;
+    }
+    float sn, cs;
+    sincosf(phases[i], &sn, &cs);
+    const float a = amp ? amp[m] : 1.f;
+    grad[i] = -2.f * a * (cs * g.y + sn * g.x);     // Im(Gamma g), Gamma = a (cs + j sn)
+}
+
 }  // namespace
 
-size_t grad_workspace_bytes(int n_t, int B) { return sizeof(float2) * (size_t)n_t * B + 256; }
+struct GradSplits {
+    int fwd, bwd, k_chunk, t_chunk;
+};
+
+GradSplits grad_splits(int n_t, int B, int M)
+{
+    GradSplits g;
+    const int target_blocks = 4 * 152;
+    const int fw_tiles = (int)(nblk(n_t, kFR) * nblk(B, kFB));
+    g.fwd = std::max(1, std::min(16, (target_blocks + fw_tiles - 1) / fw_tiles));
+    g.k_chunk = (int)((nblk(M, g.fwd) + kFK - 1) / kFK * kFK);
+    g.fwd = (int)nblk(M, g.k_chunk);
+    const int bw_tiles = (int)(nblk(M, kBM) * nblk(B, kBB));
+    g.bwd = std::max(1, std::min(64, (target_blocks + bw_tiles - 1) / bw_tiles));
+    g.t_chunk = (int)((nblk(n_t, g.bwd) + kBK - 1) / kBK * kBK);
+    g.bwd = (int)nblk(n_t, g.t_chunk);
+    return g;
+}
+
+size_t grad_workspace_bytes(int n_t, int B, int M)
+{
+    GradSplits g = grad_splits(n_t, B, M);
+    return sizeof(float2) * ((size_t)g.fwd * n_t * B + (size_t)g.bwd * B * M) + 256;
+}
 
 int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes)
 {
@@ -217,12 +265,15 @@ int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const 
                 const float* phases, const float* amp, int B, float* J, float* grad, void* ws)
 {
     cudaStream_t s = ctx->stream;
-    float2* E = (float2*)ws;
-    RISRT_KERNEL(ctx, "k_adj_forward", (k_adj_forward<<<dim3(nblk(n_t, kFR), nblk(B, kFB)), 256, 0, s>>>(
-                                           A, E0, M, target, n_t, phases, amp, B, E)));
-    RISRT_KERNEL(ctx, "k_adj_weights", (k_adj_weights<<<B, 512, 0, s>>>(E, n_t, J, (float)(1.0 / (2.0 * kEta0)))));
-    RISRT_KERNEL(ctx, "k_adj_backward", (k_adj_backward<<<dim3(nblk(M, kBM), nblk(B, kBB)), 256, 0, s>>>(
-                                            A, M, target, n_t, E, phases, amp, B, grad)));
+    const GradSplits g = grad_splits(n_t, B, M);
+    float2* E = (float2*)ws;                               // [fwd][B][n_t] partials, then w in split 0
+    float2* Gp = E + (size_t)g.fwd * n_t * B;              // [bwd][B][M]
+    RISRT_KERNEL(ctx, "k_adj_forward", (k_adj_forward<<<dim3(nblk(n_t, kFR), nblk(B, kFB), g.fwd), 256, 0, s>>>(
+                                           A, E0, M, target, n_t, phases, amp, B, g.k_chunk, E)));
+    RISRT_KERNEL(ctx, "k_adj_weights", (k_adj_weights<<<B, 512, 0, s>>>(E, n_t, B, g.fwd, J, (float)(1.0 / (2.0 * kEta0)))));
+    RISRT_KERNEL(ctx, "k_adj_backward", (k_adj_backward<<<dim3(nblk(M, kBM), nblk(B, kBB), g.bwd), 256, 0, s>>>(
+                                            A, M, target, n_t, E, B, g.t_chunk, Gp)));
+    RISRT_KERNEL(ctx, "k_adj_grad", (k_adj_grad<<<nblk((int64_t)B * M, 256), 256, 0, s>>>(Gp, g.bwd, phases, amp, B, M, grad)));
     return RISRT_OK;
 }
 

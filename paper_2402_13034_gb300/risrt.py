@@ -44,7 +44,7 @@ _SIGS = {
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
     "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_sweep_configs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int, _P, _P, C.c_size_t]),
-    "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
     "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P,
                                     C.c_size_t]),
     "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
@@ -313,10 +313,10 @@ class Context:
                                                int(n_rx), int(M), _dev_ptr(gamma, "torch.complex64"), int(n_cfg),
                                                int(precision), _dev_ptr(P_out, "torch.float32"), ws_ptr, ws_n))
 
-    def grad_workspace(self, n_target: int, B: int):
+    def grad_workspace(self, n_target: int, B: int, M: int):
         import torch
         nb = C.c_size_t()
-        rc = load().risrt_grad_workspace_size(int(n_target), int(B), C.byref(nb))
+        rc = load().risrt_grad_workspace_size(int(n_target), int(B), int(M), C.byref(nb))
         if rc:
             raise RisrtError(rc, "grad workspace size")
         return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
@@ -327,7 +327,7 @@ class Context:
         n_rx, M = A.shape
         B = phases.shape[0]
         n_t = target.numel() if target is not None else n_rx
-        ws = workspace if workspace is not None else self.grad_workspace(n_t, B)
+        ws = workspace if workspace is not None else self.grad_workspace(n_t, B, M)
         self._check(load().risrt_grad_phases(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
                                              int(n_rx), int(M), _dev_ptr(target, "torch.int32"), int(n_t),
                                              _dev_ptr(phases, "torch.float32"), _dev_ptr(amp, "torch.float32"), int(B),
