@@ -296,6 +296,40 @@ def run_reference(args, w, n_cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """Small fixed cases for profilers: 'trace' (room workload at --grid, two traces and an eval) and
+    'sweep' (16,384 receivers x 1,024 elements x 1,024 configurations, --precision)."""
+    import torch
+    from paper_2402_13034_gb300 import build as B
+    from paper_2402_13034_gb300 import risrt as R
+    B.build()
+    ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
+    if args.case == "trace":
+        w = S.room(grid=args.grid)
+        scene, ris, rx = R.upload_workload(ctx, w)
+        g = torch.from_numpy(w.gammas).cuda()
+        E = torch.empty((g.shape[0], w.n_rx), dtype=torch.complex64, device="cuda")
+        P = torch.empty((g.shape[0], w.n_rx), dtype=torch.float32, device="cuda")
+        ps = None
+        for _ in range(2):
+            ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w), reuse=ps)
+            ctx.eval_field(ps, g, E, P)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "trace", "grid": args.grid, "units": ps.stats().units}))
+    else:
+        n, M, C = 16384, 1024, 1024
+        rng = np.random.default_rng(0)
+        A = torch.from_numpy(((rng.standard_normal((n, M)) + 1j * rng.standard_normal((n, M))) * 1e-3)
+                             .astype(np.complex64)).cuda()
+        G = torch.from_numpy(np.array([1, 1j, -1, -1j], np.complex64)[rng.integers(0, 4, (C, M))]).cuda()
+        P = torch.empty((n, C), dtype=torch.float32, device="cuda")
+        ws = ctx.sweep_workspace(n, M, C, args.precision)
+        for _ in range(3):
+            ctx.sweep_configs(A, None, G, P, args.precision, ws)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "sweep", "n": n, "M": M, "C": C, "precision": args.precision}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,7 +344,13 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--case", choices=["trace", "sweep"], default=None,
+                    help="run a small fixed case for a profiler instead of the benchmark")
+    ap.add_argument("--precision", type=int, default=1)
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
 
     w = S.room(grid=args.grid)
     n_cfg = w.gammas.shape[0]

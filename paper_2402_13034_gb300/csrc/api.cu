@@ -525,7 +525,7 @@ int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
         cudaStreamSynchronize(ctx->stream);
     }
     cudaFree(sc->nodes); cudaFree(sc->tri_geom); cudaFree(sc->tri_verts); cudaFree(sc->tri_face);
-    cudaFree(sc->faces); cudaFree(sc->face_tris); cudaFree(sc->face_test); cudaFree(sc->mats);
+    cudaFree(sc->faces); cudaFree(sc->face_tris); cudaFree(sc->face_test); cudaFree(sc->tri_leaf); cudaFree(sc->mats);
     delete sc;
     return RISRT_OK;
 }
@@ -564,6 +564,8 @@ int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps)
     cudaFree(ps->rec); cudaFree(ps->rx_off); cudaFree(ps->vis); cudaFree(ps->E0); cudaFree(ps->cm);
     cudaFree(ps->elem); cudaFree(ps->rx_seq); cudaFree(ps->env_seq); cudaFree(ps->env_off); cudaFree(ps->los);
     cudaFree(ps->scratch);
+    cudaFree(ps->occ_idx[0]);
+    cudaFree(ps->occ_idx[1]);
     delete ps;
     return RISRT_OK;
 }

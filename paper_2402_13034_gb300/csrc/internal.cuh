@@ -105,6 +105,7 @@ struct DeviceScene {
     const Face* faces;           // [n_faces]
     const int* face_tris;        // CSR: triangles (leaf order) of each face
     const FaceTest* face_test;   // [n_faces]
+    const int* tri_leaf;         // [n_tris] one leaf (reference) of every input triangle
     const float2* mats;          // [n_mat] (eps_r, sigma)
 };
 
@@ -153,12 +154,13 @@ struct risrt_scene {
     risrt::Face* faces = nullptr;
     int* face_tris = nullptr;
     risrt::FaceTest* face_test = nullptr;
+    int* tri_leaf = nullptr;
     float2* mats = nullptr;
     float scene_extent = 0.f;     // max |coordinate| over vertices
     risrt::DeviceScene dev() const {
         risrt::DeviceScene s;
         s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.nodes = nodes; s.tri_geom = tri_geom;
-        s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.face_test = face_test; s.mats = mats;
+        s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.face_test = face_test; s.tri_leaf = tri_leaf; s.mats = mats;
         return s;
     }
 };
@@ -219,6 +221,8 @@ struct risrt_pathset {
     // scratch (grown as needed, kept for reuse)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    int* occ_idx[2] = {nullptr, nullptr};   // occluder lists (from the Tx, from the RIS centre)
+    int64_t occ_cap[2] = {0, 0};
     int cand_cap = 0;                // per-Rx geometric candidate capacity
 };
 

@@ -668,6 +668,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     // leaves, hierarchy, refit
     int* leaf_of_orig;
     if ((rc = dmalloc(ctx, &sc->tri_verts, nr))) return rc;
+    if ((rc = dmalloc(ctx, &sc->tri_leaf, nt))) return rc;
     if ((rc = dmalloc(ctx, &sc->tri_geom, nr))) return rc;
     if ((rc = dmalloc(ctx, &sc->tri_face, nr))) return rc;
     if ((rc = dmalloc(ctx, &leaf_of_orig, nt))) return rc;
@@ -723,6 +724,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_KERNEL(ctx, "k_face_test", (k_face_test<<<nblk(F, 128), 128, 0, s>>>(sc->faces, sc->face_tris, sc->tri_verts,
                                                                                sc->tri_geom, F, sc->face_test)));
 
+    RISRT_CUDA(ctx, cudaMemcpyAsync(sc->tri_leaf, leaf_of_orig, sizeof(int) * nt, cudaMemcpyDeviceToDevice, s));
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));
     cudaFree(d_verts); cudaFree(d_tris); cudaFree(d_face); cudaFree(d_mat); cudaFree(d_bb);
     cudaFree(keys); cudaFree(vals); cudaFree(tmp); cudaFree(leaf_of_orig); cudaFree(tmp0);

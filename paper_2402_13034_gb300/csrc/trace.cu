@@ -216,9 +216,11 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3
             // (B) last reflection point P = R + t (S_L - R), t = sR / (sR + sp)
             const float den = sR + sp;
             const float3 d = xyz(e.sL) - R;
-            const float t = sR / den;
+            const float iden = __frcp_rn(den);
+            const float t = sR * iden;
             const float3 P = R + d * t;
-            const float cond = sqrtf(dot(d, d)) / fmaxf(fabsf(den), 1e-30f);
+            const float d2 = dot(d, d);
+            const float cond = d2 * rsqrtf(d2) * fabsf(iden);   // |d| / |den| (a few ulps suffice: tol has margin)
             const float tol = tol_base * fminf(cond, 1e6f);
             const int k = e.info.w;
             const int cB = face_class<SMEM_FACES>(S, sh_faces, k == 2 ? e.info.y : e.info.x, P, tol);
@@ -234,8 +236,10 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3
                 // (D) P1 = P + t1 (S1 - P), t1 = s1P / (s1P + ssrc)
                 const float den1 = s1P + ssrc;
                 const float3 d1 = xyz(e.s1) - P;
-                const float3 P1 = P + d1 * (s1P / den1);
-                const float cond1 = sqrtf(dot(d1, d1)) / fmaxf(fabsf(den1), 1e-30f);
+                const float iden1 = __frcp_rn(den1);
+                const float3 P1 = P + d1 * (s1P * iden1);
+                const float d12 = dot(d1, d1);
+                const float cond1 = d12 * rsqrtf(d12) * fabsf(iden1);
                 const float tol1 = tol * fminf(cond1, 1e6f) + tol_base;
                 const int cD = face_class<SMEM_FACES>(S, sh_faces, e.info.x, P1, tol1);
                 if (cD == 0) continue;
@@ -277,6 +281,131 @@ __global__ void k_dense_list(const int* __restrict__ cand_cnt, const int64_t* __
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// occluder lists: the first segment of every path from a source S runs from S to a point of the
+// first face f, so it stays inside the union over f's triangles of the pyramids with apex S; only
+// triangles that can meet one of those pyramids can block it. A triangle is left out only when a
+// plane of the pyramid (three sides, the face plane) separates it by more than 1e-6 m, or when the
+// pyramid lies on one side of the triangle's own plane.
+// ------------------------------------------------------------------------------------------------
+__device__ bool tri_meets_pyramid(d3 S0, const d3* q, const d3* v)
+{
+    const double tol = 1e-6;
+    // beyond the base plane, on the far side from the apex
+    d3 nb = cross(q[1] - q[0], q[2] - q[0]);
+    const double nbl = norm(nb);
+    if (nbl == 0.0) return true;
+    nb = nb * (1.0 / nbl);
+    const double sa = dot(nb, S0 - q[0]);
+    const double sg = sa > 0 ? 1.0 : -1.0;
+    if (sg * dot(nb, v[0] - q[0]) < -tol && sg * dot(nb, v[1] - q[0]) < -tol && sg * dot(nb, v[2] - q[0]) < -tol)
+        return false;
+    // the three side planes through the apex
+    for (int e = 0; e < 3; ++e) {
+        const d3 p0 = q[e], p1 = q[(e + 1) % 3], p2 = q[(e + 2) % 3];
+        d3 n = cross(p0 - S0, p1 - S0);
+        const double l = norm(n);
+        if (l == 0.0) continue;
+        n = n * (1.0 / l);
+        if (dot(n, p2 - S0) < 0) n = n * -1.0;
+        if (dot(n, v[0] - S0) < -tol && dot(n, v[1] - S0) < -tol && dot(n, v[2] - S0) < -tol) return false;
+    }
+    // the triangle's own plane
+    d3 nt = cross(v[1] - v[0], v[2] - v[0]);
+    const double ntl = norm(nt);
+    if (ntl > 0.0) {
+        nt = nt * (1.0 / ntl);
+        const double s0 = dot(nt, S0 - v[0]);
+        bool all_pos = s0 > tol, all_neg = s0 < -tol;
+        for (int k = 0; k < 3; ++k) {
+            const double sk = dot(nt, q[k] - v[0]);
+            all_pos = all_pos && sk > tol;
+            all_neg = all_neg && sk < -tol;
+        }
+        if (all_pos || all_neg) return false;
+    }
+    return true;
+}
+
+// One thread per (face, input triangle): count (mode 0) or write (mode 1) the occluders of face f.
+__global__ void k_occ_lists(DeviceScene S, d3 src, int64_t n_tris, int mode, int* __restrict__ cnt,
+                            const int* __restrict__ off, int* __restrict__ cursor, int* __restrict__ idx)
+{
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t f = gid / n_tris;
+    const int64_t t = gid % n_tris;
+    if (f >= S.n_faces) return;
+    const int leaf = S.tri_leaf[t];
+    const TriVerts tv = S.tri_verts[leaf];
+    const d3 v[3] = {ldv(tv.v0), ldv(tv.v1), ldv(tv.v2)};
+    const Face fc = S.faces[(int)f];
+    // cheap box prefilter: pyramid box (apex and face vertices) against the triangle box
+    float lo[3] = {(float)src.x, (float)src.y, (float)src.z}, hi[3] = {lo[0], lo[1], lo[2]};
+    for (int j = fc.tri_begin; j < fc.tri_end; ++j) {
+        const TriVerts fv = S.tri_verts[S.face_tris[j]];
+        const float4 w[3] = {fv.v0, fv.v1, fv.v2};
+        for (int k = 0; k < 3; ++k) {
+            lo[0] = fminf(lo[0], w[k].x); lo[1] = fminf(lo[1], w[k].y); lo[2] = fminf(lo[2], w[k].z);
+            hi[0] = fmaxf(hi[0], w[k].x); hi[1] = fmaxf(hi[1], w[k].y); hi[2] = fmaxf(hi[2], w[k].z);
+        }
+    }
+    const float pad = 1e-4f;
+    const float4 tw[3] = {tv.v0, tv.v1, tv.v2};
+    const float tlo[3] = {fminf(tw[0].x, fminf(tw[1].x, tw[2].x)), fminf(tw[0].y, fminf(tw[1].y, tw[2].y)),
+                          fminf(tw[0].z, fminf(tw[1].z, tw[2].z))};
+    const float thi[3] = {fmaxf(tw[0].x, fmaxf(tw[1].x, tw[2].x)), fmaxf(tw[0].y, fmaxf(tw[1].y, tw[2].y)),
+                          fmaxf(tw[0].z, fmaxf(tw[1].z, tw[2].z))};
+    for (int k = 0; k < 3; ++k)
+        if (tlo[k] > hi[k] + pad || thi[k] < lo[k] - pad) return;
+    bool meets = false;
+    for (int j = fc.tri_begin; j < fc.tri_end && !meets; ++j) {
+        const TriVerts fv = S.tri_verts[S.face_tris[j]];
+        const d3 q[3] = {ldv(fv.v0), ldv(fv.v1), ldv(fv.v2)};
+        meets = tri_meets_pyramid(src, q, v);
+    }
+    if (!meets) return;
+    if (mode == 0) atomicAdd(&cnt[f], 1);
+    else idx[off[f] + atomicAdd(&cursor[f], 1)] = leaf;
+}
+
+__global__ void k_i32_scan_prep(const int* __restrict__ a, int64_t n, int64_t* __restrict__ b)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+    if (i == n) b[i] = 0;
+}
+
+__global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int* __restrict__ b)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int)a[i];
+}
+
+// Counting sort of the dense candidate list by first face, so the lanes of a warp share one
+// occluder list (and similar first segments).
+__global__ void k_face_hist(const SeqEntry* __restrict__ seqs, const int* __restrict__ cand, int cap,
+                            const int* __restrict__ dense_r, const int* __restrict__ dense_slot, long long total,
+                            int* __restrict__ hist)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    atomicAdd(&hist[seqs[cand[(int64_t)dense_r[i] * cap + dense_slot[i]]].info.x], 1);
+}
+
+__global__ void k_face_scatter(const SeqEntry* __restrict__ seqs, const int* __restrict__ cand, int cap,
+                               const int* __restrict__ dense_r, const int* __restrict__ dense_slot, long long total,
+                               const int64_t* __restrict__ off, int* __restrict__ cursor, int* __restrict__ out_r,
+                               int* __restrict__ out_slot)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int r = dense_r[i], sl = dense_slot[i];
+    const int f = seqs[cand[(int64_t)r * cap + sl]].info.x;
+    const int64_t o = off[f] + atomicAdd(&cursor[f], 1);
+    out_r[o] = r;
+    out_slot[o] = sl;
+}
+
 // FP32 reflection points of every dense candidate (same back-trace as the candidate filter): the
 // last point P (next to the destination) and, for order 2, the first point P1.
 __global__ void k_cand_points(const float* __restrict__ dst_xyz, const SeqEntry* __restrict__ seqs,
@@ -307,14 +436,26 @@ __global__ void k_cand_points(const float* __restrict__ dst_xyz, const SeqEntry*
 // busy while traversal lengths differ. FP64 endpoints are rebuilt only for the rare triangle whose
 // FP32 classification is too close to call. ctr[0..3]: candidates, segments, nodes, triangle tests.
 constexpr int kValThreads = 128;
-constexpr int kSteps = 8;
+#ifndef RISRT_VALIDATE_STEPS
+#define RISRT_VALIDATE_STEPS 16    // BVH visits per lane between refills (measured on the room workload)
+#endif
+#ifndef RISRT_MAX_OCC_LIST
+#define RISRT_MAX_OCC_LIST (-1)    // occluder lists up to this length replace BVH traversal; -1: off
+#endif
+#ifndef RISRT_GROUP_BY_FACE
+#define RISRT_GROUP_BY_FACE 0
+#endif
+constexpr int kSteps = RISRT_VALIDATE_STEPS;
 
-__global__ void __launch_bounds__(kValThreads, 8)
+#ifndef RISRT_VALIDATE_MINB
+#define RISRT_VALIDATE_MINB 6      // blocks per SM the register budget targets (measured)
+#endif
+__global__ void __launch_bounds__(kValThreads, RISRT_VALIDATE_MINB)
 k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_face, int dst_face,
            const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int* __restrict__ cand, int cap,
            const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const float4* __restrict__ dpts,
            long long total, unsigned long long* __restrict__ next, float tol_base, unsigned long long* refines,
-           int* err, unsigned long long* ctr)
+           int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx)
 {
     const float3 srcf = to_f(src);
     const unsigned FULL = 0xffffffffu;
@@ -329,6 +470,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     int ign0 = -1, ign1 = -1;
     int stack[64];
     int sp = 0;
+    int li = 0, le = 0;          // occluder-list cursor (segment 0 only)
+    bool list_mode = false;
     bool blocked = false;
 
     auto start_segment = [&]() {
@@ -339,9 +482,33 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
         ign0 = j == 0 ? src_face : (j == 1 ? info.x : info.y);
         ign1 = j == info.w ? dst_face : (j == 0 ? info.x : info.y);
-        stack[0] = S.root;
-        sp = 1;
+        list_mode = j == 0 && occ_off != nullptr && occ_off[info.x + 1] - occ_off[info.x] <= RISRT_MAX_OCC_LIST;
+        if (list_mode) {            // only triangles that can meet the pyramid from the source through f1
+            li = occ_off[info.x];
+            le = occ_off[info.x + 1];
+            sp = 0;
+        } else {
+            stack[0] = S.root;
+            sp = 1;
+        }
         ++tc.segs;
+    };
+
+    auto test_leaf = [&](int i) -> bool {
+        const int f = S.tri_face[i];
+        if (f == ign0 || f == ign1) return false;
+        ++tc.tris;
+        const int h = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
+        bool hit = h == 1;
+        if (h == 2) {
+            atomicAdd(refines, 1ull);
+            const d3 R = D3((double)dst_xyz[3 * r], (double)dst_xyz[3 * r + 1], (double)dst_xyz[3 * r + 2]);
+            d3 pts[4];
+            seq_points_fp64(S, R, info, seqd[si], src, pts);
+            const d3 dD = pts[j + 1] - pts[j];
+            hit = tri_hit_fp64(S.tri_verts[i], pts[j], dD, norm(dD));
+        }
+        return hit;
     };
 
     while (true) {
@@ -381,43 +548,38 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         const bool active = item >= 0 && item < total;
         if (!__any_sync(FULL, active)) break;
         if (!active) continue;
-        for (int it = 0; it < kSteps && sp > 0; ++it) {
-            const int c = stack[--sp];
-            if (c < 0) {
-                const int i = ~c;
-                const int f = S.tri_face[i];
-                if (f == ign0 || f == ign1) continue;
-                ++tc.tris;
-                const int h = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
-                bool hit = h == 1;
-                if (h == 2) {
-                    atomicAdd(refines, 1ull);
-                    const d3 R = D3((double)dst_xyz[3 * r], (double)dst_xyz[3 * r + 1], (double)dst_xyz[3 * r + 2]);
-                    d3 pts[4];
-                    seq_points_fp64(S, R, info, seqd[si], src, pts);
-                    const d3 dD = pts[j + 1] - pts[j];
-                    hit = tri_hit_fp64(S.tri_verts[i], pts[j], dD, norm(dD));
+        if (list_mode) {
+            for (int it = 0; it < kSteps && li < le; ++it) {
+                if (test_leaf(occ_idx[li++])) {
+                    blocked = true;
+                    li = le;
                 }
-                if (hit) {
+            }
+        } else {
+            for (int it = 0; it < kSteps && sp > 0; ++it) {
+                const int c = stack[--sp];
+                if (c < 0) {
+                    if (test_leaf(~c)) {
+                        blocked = true;
+                        sp = 0;
+                    }
+                    continue;
+                }
+                const BvhNode nd = S.nodes[c];
+                ++tc.nodes;
+                const bool hl = box_overlap(nd.l_lo, nd.l_hi, a, inv);
+                const bool hr = box_overlap(nd.r_lo, nd.r_hi, a, inv);
+                if (sp + 2 > 64) {
+                    atomicExch(err, 1);
                     blocked = true;
                     sp = 0;
+                    break;
                 }
-                continue;
+                if (hr) stack[sp++] = __float_as_int(nd.l_hi.w);
+                if (hl) stack[sp++] = __float_as_int(nd.l_lo.w);
             }
-            const BvhNode nd = S.nodes[c];
-            ++tc.nodes;
-            const bool hl = box_overlap(nd.l_lo, nd.l_hi, a, inv);
-            const bool hr = box_overlap(nd.r_lo, nd.r_hi, a, inv);
-            if (sp + 2 > 64) {
-                atomicExch(err, 1);
-                blocked = true;
-                sp = 0;
-                break;
-            }
-            if (hr) stack[sp++] = __float_as_int(nd.l_hi.w);
-            if (hl) stack[sp++] = __float_as_int(nd.l_lo.w);
         }
-        if (sp == 0) {
+        if (list_mode ? li >= le : sp == 0) {
             if (blocked) {
                 cand[(int64_t)r * cap + slot] = -1;
                 item = -1;
@@ -778,6 +940,33 @@ struct Candidates {
 
 }  // namespace
 
+// Occluder lists of every face for one source (CSR, leaf indices). Returns with *off == nullptr when
+// the scene is too large for the face x triangle pass (the BVH is used instead).
+static int build_occ_lists(risrt_ctx* ctx, const DeviceScene& S, int64_t n_tris, d3 src, int* cnt, int64_t* off64,
+                           int* off, int* cursor, void* scan_tmp, int** idx, int64_t* idx_cap, const int** off_out)
+{
+    cudaStream_t s = ctx->stream;
+    const int F = S.n_faces;
+    *off_out = nullptr;
+    if (F == 0 || (double)F * (double)n_tris > 4e8) return RISRT_OK;
+    const int64_t pairs = (int64_t)F * n_tris;
+    RISRT_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int) * (F + 1), s));
+    RISRT_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * F, s));
+    RISRT_KERNEL(ctx, "k_occ_lists", (k_occ_lists<<<nblk(pairs, 256), 256, 0, s>>>(S, src, n_tris, 0, cnt, nullptr, nullptr, nullptr)));
+    RISRT_KERNEL(ctx, "k_i32_scan_prep", (k_i32_scan_prep<<<nblk(F + 1, 256), 256, 0, s>>>(cnt, F, off64)));
+    RISRT_CUDA(ctx, exclusive_scan_i64(off64, off64, F + 1, scan_tmp, s));
+    int64_t total = 0;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&total, off64 + F, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    if (total > INT32_MAX) return RISRT_OK;
+    int rc = grow(ctx, idx, idx_cap, std::max<int64_t>(total, 1));
+    if (rc) return rc;
+    RISRT_KERNEL(ctx, "k_i64_to_i32", (k_i64_to_i32<<<nblk(F + 1, 256), 256, 0, s>>>(off64, F + 1, off)));
+    RISRT_KERNEL(ctx, "k_occ_lists", (k_occ_lists<<<nblk(pairs, 256), 256, 0, s>>>(S, src, n_tris, 1, nullptr, off, cursor, *idx)));
+    *off_out = off;
+    return RISRT_OK;
+}
+
 int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rxs, double freq,
                 int max_tx, int max_rx, uint32_t flags, risrt_pathset* ps)
 {
@@ -898,6 +1087,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             int *dense_r, *dense_slot;
             int64_t* dense_off;
             float4* dense_pts;
+            int* occ_cnt[2];
+            int64_t* occ_off64[2];
+            int* occ_off[2];
+            int* occ_cursor[2];
+            int *dense_r2, *dense_slot2;
+            int64_t* face_off64;
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -923,6 +1118,15 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.crx.cnt64_tmp = A.get<int64_t>(n_rx + 1);
             L.cenv.cnt64_tmp = L.crx.cnt64_tmp;
             L.ctx_leg.cnt64_tmp = A.get<int64_t>(2);
+            for (int q = 0; q < 2; ++q) {
+                L.occ_cnt[q] = A.get<int>(F + 1);
+                L.occ_off64[q] = A.get<int64_t>(F + 1);
+                L.occ_off[q] = A.get<int>(F + 1);
+                L.occ_cursor[q] = A.get<int>(F + 1);
+            }
+            L.dense_r2 = A.get<int>((size_t)n_rx * cap);
+            L.dense_slot2 = A.get<int>((size_t)n_rx * cap);
+            L.face_off64 = A.get<int64_t>(F + 1);
         };
         Arena measure;
         Layout Lm;
@@ -972,8 +1176,19 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             tab[i].n = (int)n_allowed;
         }
 
+        // occluder lists of the first segments, from the Tx (Tx leg, environment) and the RIS centre
+        const int* occ_off_src[2] = {nullptr, nullptr};      // 0: Tx, 1: RIS centre
+        if (RISRT_MAX_OCC_LIST >= 0 && (max_tx > 0 || max_env > 0))
+            if ((rc = build_occ_lists(ctx, S, sc->n_tris, Tpos, L.occ_cnt[0], L.occ_off64[0], L.occ_off[0],
+                                      L.occ_cursor[0], scan_tmp, &ps->occ_idx[0], &ps->occ_cap[0], &occ_off_src[0])))
+                return rc;
+        if (RISRT_MAX_OCC_LIST >= 0 && max_rx > 0)
+            if ((rc = build_occ_lists(ctx, S, sc->n_tris, Cpos, L.occ_cnt[1], L.occ_off64[1], L.occ_off[1],
+                                      L.occ_cursor[1], scan_tmp, &ps->occ_idx[1], &ps->occ_cap[1], &occ_off_src[1])))
+                return rc;
+
         auto run_candidates = [&](const SeqTable& t, const float* dst, int64_t n_dst, d3 src, int src_face,
-                                  int dst_face, Candidates& cs) -> int {
+                                  int dst_face, Candidates& cs, int occ) -> int {
             RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, s));
             if (t.n > 0) {
                 dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
@@ -997,14 +1212,30 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + n_dst, sizeof(long long), cudaMemcpyDeviceToHost, s));
                 RISRT_CUDA(ctx, cudaMemsetAsync(counters + 6, 0, sizeof(unsigned long long), s));
                 RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+                int *vr = L.dense_r, *vs = L.dense_slot;
+                if (RISRT_GROUP_BY_FACE && total > 0 && occ_off_src[occ]) {   // group by first face (list coherence)
+                    int* hist = L.occ_cnt[occ];
+                    RISRT_CUDA(ctx, cudaMemsetAsync(hist, 0, sizeof(int) * (F + 1), s));
+                    RISRT_CUDA(ctx, cudaMemsetAsync(L.occ_cursor[occ], 0, sizeof(int) * (F + 1), s));
+                    RISRT_KERNEL(ctx, "k_face_hist", (k_face_hist<<<nblk(total, 256), 256, 0, s>>>(t.e, cs.cand, cs.cap, L.dense_r,
+                                                                                              L.dense_slot, total, hist)));
+                    RISRT_KERNEL(ctx, "k_i32_scan_prep", (k_i32_scan_prep<<<nblk(F + 1, 256), 256, 0, s>>>(hist, F, L.face_off64)));
+                    RISRT_CUDA(ctx, exclusive_scan_i64(L.face_off64, L.face_off64, F + 1, scan_tmp, s));
+                    RISRT_KERNEL(ctx, "k_face_scatter", (k_face_scatter<<<nblk(total, 256), 256, 0, s>>>(
+                                                            t.e, cs.cand, cs.cap, L.dense_r, L.dense_slot, total,
+                                                            L.face_off64, L.occ_cursor[occ], L.dense_r2, L.dense_slot2)));
+                    vr = L.dense_r2;
+                    vs = L.dense_slot2;
+                }
                 if (total > 0) {
                     RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<nblk(total, 256), 256, 0, s>>>(
-                                                           dst, t.e, cs.cand, cs.cap, L.dense_r, L.dense_slot, total, L.dense_pts)));
-                    const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * 8, (total + kValThreads - 1) / kValThreads);
+                                                           dst, t.e, cs.cand, cs.cap, vr, vs, total, L.dense_pts)));
+                    const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * RISRT_VALIDATE_MINB,
+                                                                          (total + kValThreads - 1) / kValThreads);
                     RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
-                                                        S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, L.dense_r,
-                                                        L.dense_slot, L.dense_pts, total, counters + 6, tol_base, counters, flags_dev + 1,
-                                                        counters + 2)));
+                                                        S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
+                                                        vs, L.dense_pts, total, counters + 6, tol_base, counters, flags_dev + 1,
+                                                        counters + 2, occ_off_src[occ], ps->occ_idx[occ])));
                 }
             }
             const int warps = 4;
@@ -1015,13 +1246,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         };
 
         // Tx leg (destination: RIS centre, mounted on host_face)
-        if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg))) return rc;
+        if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg, 0))) return rc;
         RISRT_KERNEL(ctx, "k_tx_vis", (k_tx_vis<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, ris->host_face, tol_base, tx_vis, counters,
                                               flags_dev + 1)));
         // Rx leg (source: RIS centre) and environment paths (source: Tx)
         const float* rxp = rxs->xyz;
-        if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx))) return rc;
-        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv))) return rc;
+        if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx, 1))) return rc;
+        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv, 0))) return rc;
         // direct legs
         {
             int64_t nthreads = n_rx * W * 32;
@@ -1268,7 +1499,7 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                 S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
                                                 L.dense_slot, L.dense_pts, total, L.counters + 6, tol_base, L.counters,
-                                                L.flags + 1, L.counters + 2)));
+                                                L.flags + 1, L.counters + 2, nullptr, nullptr)));
         }
         const size_t shm = sizeof(int) * (size_t)cap;
         cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
