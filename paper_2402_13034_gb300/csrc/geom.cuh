@@ -122,6 +122,17 @@ __device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, float3 a, floa
     return tmin <= tmax;
 }
 
+// Entry parameter of the segment into the box, or +inf when it misses.
+__device__ __forceinline__ float box_entry(float4 lo, float4 hi, float3 a, float3 inv)
+{
+    float tx0 = (lo.x - a.x) * inv.x, tx1 = (hi.x - a.x) * inv.x;
+    float ty0 = (lo.y - a.y) * inv.y, ty1 = (hi.y - a.y) * inv.y;
+    float tz0 = (lo.z - a.z) * inv.z, tz1 = (hi.z - a.z) * inv.z;
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), 1.f));
+    return tmin <= tmax ? tmin : __int_as_float(0x7f800000);
+}
+
 __device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d)); }
 
 struct TraceCounters {
@@ -172,14 +183,18 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
         }
         const BvhNode nd = S.nodes[c];
         if (tc) ++tc->nodes;
-        bool hl = box_overlap(nd.l_lo, nd.l_hi, a, inv);
-        bool hr = box_overlap(nd.r_lo, nd.r_hi, a, inv);
+        const float el = box_entry(nd.l_lo, nd.l_hi, a, inv);
+        const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
         if (sp + 2 > 64) {
             if (err) atomicExch(err, 1);
             return true;
         }
-        if (hr) stack[sp++] = __float_as_int(nd.l_hi.w);
-        if (hl) stack[sp++] = __float_as_int(nd.l_lo.w);
+        // any hit ends the query, so the child entered first along the segment is visited first
+        const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
+        const bool lfirst = el <= er;
+        const float efar = lfirst ? er : el, enear = lfirst ? el : er;
+        if (efar < 1e30f) stack[sp++] = lfirst ? cr : cl;
+        if (enear < 1e30f) stack[sp++] = lfirst ? cl : cr;
     }
     return false;
 }

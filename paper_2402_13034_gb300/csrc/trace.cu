@@ -182,30 +182,98 @@ __device__ __forceinline__ int face_class(const DeviceScene& S, const FaceTest* 
     return in_face_fp32(S, f, q, tol);
 }
 
+// Can any destination inside the box [lo, hi] make sequence e geometrically valid? It must lie on
+// the previous image's side of the last plane and inside the cone from the last image through the
+// last face (union over the face's triangles). False only when the whole box is separated by more
+// than `margin`, far beyond FP32 error, so skipping it for every destination in the box changes no
+// decision.
+__device__ bool box_in_beam(const DeviceScene& S, const SeqEntry& e, float3 lo, float3 hi, float margin)
+{
+    const float3 nL = xyz(e.pL);
+    const float sp = e.sL.w;
+    bool same = false;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float3 q = f3((c & 1) ? hi.x : lo.x, (c & 2) ? hi.y : lo.y, (c & 4) ? hi.z : lo.z);
+        const float sR = dot(nL, q) - e.pL.w;
+        if (sp > 0.f ? sR > -margin : sR < margin) same = true;
+    }
+    if (!same) return false;
+    const float3 ap = xyz(e.sL);
+    const Face fc = S.faces[e.info.w == 2 ? e.info.y : e.info.x];
+    for (int j = fc.tri_begin; j < fc.tri_end; ++j) {
+        const TriVerts tv = S.tri_verts[S.face_tris[j]];
+        const float3 v[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
+        bool separated = false;
+        for (int k = 0; k < 3 && !separated; ++k) {
+            float3 n = cross(v[k] - ap, v[(k + 1) % 3] - ap);
+            const float l2 = dot(n, n);
+            if (!(l2 > 0.f)) continue;
+            n = n * rsqrtf(l2);
+            if (dot(n, v[(k + 2) % 3] - ap) < 0.f) n = n * -1.f;
+            bool all_out = true;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float3 q = f3((c & 1) ? hi.x : lo.x, (c & 2) ? hi.y : lo.y, (c & 4) ? hi.z : lo.z);
+                if (dot(n, q - ap) >= -margin) all_out = false;
+            }
+            separated = all_out;
+        }
+        if (!separated) return true;
+    }
+    return false;
+}
+
 template <bool SMEM_FACES>
 __global__ void __launch_bounds__(kCandThreads)
-k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, d3 src,
+k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, const int* __restrict__ order, d3 src,
              const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int n_seq,
              float tol_base, int* __restrict__ cand, int* __restrict__ cand_cnt, int cap,
              int* __restrict__ overflow, unsigned long long* __restrict__ refines)
 {
     __shared__ SeqEntry sh[kCandThreads];
+    __shared__ unsigned char keep[kCandThreads];
+    __shared__ float3 sh_R[kCandThreads];
+    __shared__ float3 box[2];
     extern __shared__ FaceTest sh_faces[];
     if (SMEM_FACES)
         for (int f = threadIdx.x; f < S.n_faces; f += blockDim.x) sh_faces[f] = S.face_test[f];
-    const int64_t r = blockIdx.x * (int64_t)kCandThreads + threadIdx.x;
-    const bool active = r < n_dst;
+    // destinations in spatial (Morton) order, so a block covers a compact patch
+    const int64_t ri = blockIdx.x * (int64_t)kCandThreads + threadIdx.x;
+    const bool active = ri < n_dst;
+    const int64_t r = active ? (order ? (int64_t)order[ri] : ri) : 0;
     const float3 R = active ? f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]) : f3(0.f, 0.f, 0.f);
+    sh_R[threadIdx.x] = R;
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int64_t rem = n_dst - blockIdx.x * (int64_t)kCandThreads;
+        const int n_act = rem < kCandThreads ? (int)rem : kCandThreads;
+        float3 b = sh_R[0];
+        for (int i = 1; i < n_act; ++i) {
+            const float3 q = sh_R[i];
+            b = threadIdx.x == 0 ? f3(fminf(b.x, q.x), fminf(b.y, q.y), fminf(b.z, q.z))
+                                 : f3(fmaxf(b.x, q.x), fmaxf(b.y, q.y), fmaxf(b.z, q.z));
+        }
+        box[threadIdx.x] = b;
+    }
+    __syncthreads();
+    const float3 blo = box[0], bhi = box[1];
+    const float margin = 1e-3f + 1e-5f * (fabsf(blo.x) + fabsf(blo.y) + fabsf(blo.z) + fabsf(bhi.x) + fabsf(bhi.y) + fabsf(bhi.z));
     for (int64_t chunk = blockIdx.y; chunk * kCandChunk < n_seq; chunk += gridDim.y) {
     const int s_begin = (int)(chunk * kCandChunk);
     const int s_end = min(n_seq, s_begin + kCandChunk);
     for (int s0 = s_begin; s0 < s_end; s0 += kCandThreads) {
         __syncthreads();
-        if (s0 + threadIdx.x < s_end) sh[threadIdx.x] = seqs[s0 + threadIdx.x];
+        if (s0 + threadIdx.x < s_end) {
+            const SeqEntry e = seqs[s0 + threadIdx.x];
+            sh[threadIdx.x] = e;
+            keep[threadIdx.x] = box_in_beam(S, e, blo, bhi, margin) ? 1 : 0;
+        }
         __syncthreads();
         const int cnt = min(kCandThreads, s_end - s0);
         if (!active) continue;
         for (int j = 0; j < cnt; ++j) {
+            if (!keep[j]) continue;                  // uniform over the block
             const SeqEntry& e = sh[j];
             // (A)
             const float sR = dot(xyz(e.pL), R) - e.pL.w;
@@ -567,16 +635,19 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                 }
                 const BvhNode nd = S.nodes[c];
                 ++tc.nodes;
-                const bool hl = box_overlap(nd.l_lo, nd.l_hi, a, inv);
-                const bool hr = box_overlap(nd.r_lo, nd.r_hi, a, inv);
+                const float el = box_entry(nd.l_lo, nd.l_hi, a, inv);
+                const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
                 if (sp + 2 > 64) {
                     atomicExch(err, 1);
                     blocked = true;
                     sp = 0;
                     break;
                 }
-                if (hr) stack[sp++] = __float_as_int(nd.l_hi.w);
-                if (hl) stack[sp++] = __float_as_int(nd.l_lo.w);
+                const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
+                const bool lfirst = el <= er;               // nearer child on top of the stack
+                const float efar = lfirst ? er : el, enear = lfirst ? el : er;
+                if (efar < 1e30f) stack[sp++] = lfirst ? cr : cl;
+                if (enear < 1e30f) stack[sp++] = lfirst ? cl : cr;
             }
         }
         if (list_mode ? li >= le : sp == 0) {
@@ -882,6 +953,54 @@ __global__ void k_abs_max(const float* __restrict__ v, int64_t n, unsigned* __re
     atomicMax(out, m);
 }
 
+__device__ __forceinline__ unsigned ord_bits(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_ord(unsigned o) { return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o); }
+
+__global__ void k_rx_bounds(const float* __restrict__ xyz, int64_t n, unsigned* __restrict__ bb)
+{
+    unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            const unsigned o = ord_bits(xyz[3 * i + k]);
+            lo[k] = min(lo[k], o);
+            hi[k] = max(hi[k], o);
+        }
+    for (int k = 0; k < 3; ++k) {
+        atomicMin(&bb[k], lo[k]);
+        atomicMax(&bb[3 + k], hi[k]);
+    }
+}
+
+__device__ __forceinline__ unsigned spread10b(unsigned x)
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+// 30-bit Morton code of every receiver (spatial order for the candidate search).
+__global__ void k_rx_morton(const float* __restrict__ xyz, int64_t n, const unsigned* __restrict__ bb,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned code = 0;
+    for (int k = 0; k < 3; ++k) {
+        const float lo = from_ord(bb[k]), span = from_ord(bb[3 + k]) - lo;
+        const float u = span > 0.f ? (xyz[3 * i + k] - lo) / span : 0.f;
+        code |= spread10b((unsigned)fminf(fmaxf(u * 1024.f, 0.f), 1023.f)) << (2 - k);
+    }
+    keys[i] = code;
+    vals[i] = (uint32_t)i;
+}
+
 __global__ void k_units(const int64_t* __restrict__ off, int64_t n_rx, int M, unsigned long long* units)
 {
     __shared__ unsigned long long s;
@@ -1093,6 +1212,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             int* occ_cursor[2];
             int *dense_r2, *dense_slot2;
             int64_t* face_off64;
+            uint32_t *rx_keys, *rx_order_u;
+            void* rx_sort_tmp;
+            unsigned* rx_bb;
+            int* rx_order;
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -1124,6 +1247,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 L.occ_off[q] = A.get<int>(F + 1);
                 L.occ_cursor[q] = A.get<int>(F + 1);
             }
+            L.rx_keys = A.get<uint32_t>(n_rx);
+            L.rx_order_u = A.get<uint32_t>(n_rx);
+            L.rx_sort_tmp = A.get<char>(sort_temp_bytes(n_rx));
+            L.rx_bb = A.get<unsigned>(8);
             L.dense_r2 = A.get<int>((size_t)n_rx * cap);
             L.dense_slot2 = A.get<int>((size_t)n_rx * cap);
             L.face_off64 = A.get<int64_t>(F + 1);
@@ -1187,6 +1314,18 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                       L.occ_cursor[1], scan_tmp, &ps->occ_idx[1], &ps->occ_cap[1], &occ_off_src[1])))
                 return rc;
 
+        // receivers in Morton order for the candidate search
+        {
+            const unsigned bb_init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
+            RISRT_CUDA(ctx, cudaMemcpyAsync(L.rx_bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
+            RISRT_KERNEL(ctx, "k_rx_bounds", (k_rx_bounds<<<std::min<unsigned>(nblk(n_rx, 256), 1024u), 256, 0, s>>>(
+                                                 rxs->xyz, n_rx, L.rx_bb)));
+            RISRT_KERNEL(ctx, "k_rx_morton", (k_rx_morton<<<nblk(n_rx, 256), 256, 0, s>>>(rxs->xyz, n_rx, L.rx_bb, L.rx_keys,
+                                                                                          L.rx_order_u)));
+            RISRT_CUDA(ctx, radix_sort_pairs(L.rx_keys, L.rx_order_u, n_rx, 30, L.rx_sort_tmp, s));
+            L.rx_order = (int*)L.rx_order_u;
+        }
+
         auto run_candidates = [&](const SeqTable& t, const float* dst, int64_t n_dst, d3 src, int src_face,
                                   int dst_face, Candidates& cs, int occ) -> int {
             RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, s));
@@ -1196,12 +1335,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     const size_t shm = sizeof(FaceTest) * (size_t)F;
                     cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
-                                                          S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
-                                                          cs.cnt, cs.cap, flags_dev, counters)));
+                                                          S, dst, n_dst, n_dst > 1 ? L.rx_order : nullptr, src, t.e, t.d,
+                                                          t.n, tol_base, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
                 } else {
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
-                                                          S, dst, n_dst, src, t.e, t.d, t.n, tol_base, cs.cand,
-                                                          cs.cnt, cs.cap, flags_dev, counters)));
+                                                          S, dst, n_dst, n_dst > 1 ? L.rx_order : nullptr, src, t.e, t.d,
+                                                          t.n, tol_base, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
                 }
                 // dense candidate list, then persistent validation
                 RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, s>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
@@ -1476,11 +1615,11 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             const size_t shm = sizeof(FaceTest) * (size_t)F;
             cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
-                                                  S, L.dst, 1, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
+                                                  S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
                                                   L.flags, L.counters)));
         } else {
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
-                                                  S, L.dst, 1, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
+                                                  S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
                                                   L.flags, L.counters)));
         }
         RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<1, 32, 0, s>>>(L.cnt, 1, cap, L.cnt64_tmp)));
