@@ -195,11 +195,14 @@ def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
                "db_err": {"median": float(np.median(db)), "p99": float(np.percentile(db, 99)),
                           "max": float(db.max())},
                "max_field_err_over_S": float(dE[ok].max())}
-        if "k_sweep_tc" in prof:
-            kms = prof["k_sweep_tc"][0] / prof["k_sweep_tc"][1]
+        kname = next((k for k in ("k_sweep_tc_pair", "k_sweep_tc") if k in prof), None)
+        if kname:
+            kms = prof[kname][0] / prof[kname][1]
             Kp = ((4 if prec == 2 else 2) * M + 63) // 64 * 64
             Np = (2 * n_cfg + 255) // 256 * 256
-            Mp = (n + 127) // 128 * 128
+            bm = 256 if kname == "k_sweep_tc_pair" else 128
+            Mp = (n + bm - 1) // bm * bm
+            ent["kernel"] = kname
             ent["kernel_ms"] = kms
             ent["tensor_flop_per_launch"] = 2.0 * Mp * Np * Kp
             ent["kernel_tflops_executed"] = 2.0 * Mp * Np * Kp / (kms / 1e3) / 1e12
@@ -210,7 +213,7 @@ def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
     peaks = _peaks()
     pk = peaks.get("bf16_tflops", 1876.6)
     b = out["bf16"]
-    out["roofline"] = {"kernel": "k_sweep_tc", "bound": "tensor", "achieved": b.get("kernel_tflops_executed"),
+    out["roofline"] = {"kernel": b.get("kernel", "k_sweep_tc"), "bound": "tensor", "achieved": b.get("kernel_tflops_executed"),
                        "peak": pk, "unit": "TFLOP/s",
                        "frac": (b.get("kernel_tflops_executed") or 0) / pk, "traffic": None,
                        "peak_note": "measured bf16 burst peak (cuBLAS) of this pool" if "bf16_tflops" in peaks

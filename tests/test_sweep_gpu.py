@@ -113,3 +113,29 @@ def test_sweep_invalid_arguments():
         ctx.sweep_configs(A, None, G, P, 7, None)
     with pytest.raises(R.RisrtError):          # tensor-core precision without a workspace
         ctx.sweep_configs(A, None, G, P, 1, None)
+
+
+@pytest.mark.parametrize("n,M,C", [(1000, 300, 300), (4097, 1024, 129), (16384, 256, 1024)])
+@pytest.mark.parametrize("prec", [1, 3])
+def test_pair_and_single_cta_kernels(n, M, C, prec, monkeypatch):
+    """The two-CTA persistent kernel (256 x 256 tiles, double-buffered accumulators, several tiles per
+    cluster at the largest size) and the one-CTA-per-tile kernel agree, and both stay within the
+    precision's bound against FP64 on sampled receivers (ragged last tile: 4097 rows leaves the second
+    CTA of the last pair without receivers)."""
+    rng = np.random.default_rng(n * 7 + M + C)
+    A = ((rng.standard_normal((n, M)) + 1j * rng.standard_normal((n, M))) * 1e-3).astype(np.complex64)
+    E0 = ((rng.standard_normal(n) + 1j * rng.standard_normal(n)) * 1e-3).astype(np.complex64)
+    G = np.array([1, 1j, -1, -1j], np.complex64)[rng.integers(0, 4, (C, M))]
+    rows = np.unique(np.concatenate([np.arange(min(n, 64)), rng.integers(0, n, 384), [n - 1]]))
+    E = E0[rows, None].astype(np.complex128) + A[rows].astype(np.complex128) @ G.T.astype(np.complex128)
+    Sx = np.abs(E0[rows])[:, None] + np.abs(A[rows]).astype(np.float64) @ np.abs(G).T.astype(np.float64)
+    out = {}
+    for pair in ("1", "0"):
+        monkeypatch.setenv("RISRT_SWEEP_PAIR", pair)
+        P = _run(_ctx(), A, E0, G, prec)
+        assert P.min() >= 0 and np.isfinite(P).all()
+        dE = np.abs(np.sqrt(P[rows] * 2 * ETA0) - np.abs(E)) / Sx
+        assert dE.max() <= TOL[prec], (pair, dE.max())
+        out[pair] = P
+    scale = max(out["0"].max(), 1e-30)
+    assert np.abs(out["1"] - out["0"]).max() <= 1e-6 * scale
