@@ -349,6 +349,60 @@ __global__ void k_dense_list(const int* __restrict__ cand_cnt, const int64_t* __
     }
 }
 
+// Dense list in coherent order: one warp per group of 32 receivers taken in Morton order; the warp
+// merges the group's candidate rows by sequence id (smallest head first), so consecutive items mostly
+// share one image sequence and come from neighbouring receivers, and the traversals of a warp follow
+// similar paths through the BVH. Rows need not be sorted: every item is emitted exactly once either way.
+// counts: out[g] = number of candidates of group g, out[n_groups] = 0 (exclusive scan input).
+__global__ void k_group_counts(const int* __restrict__ cand_cnt, const int* __restrict__ order, int64_t n_dst, int cap,
+                               int64_t n_groups, int64_t* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (g > n_groups) return;
+    if (g == n_groups) {
+        if (lane == 0) out[g] = 0;
+        return;
+    }
+    const int64_t i = g * 32 + lane;
+    int c = 0;
+    if (i < n_dst) c = min(cand_cnt[order ? order[i] : (int)i], cap);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) out[g] = c;
+}
+
+__global__ void k_dense_merge(const int* __restrict__ cand, const int* __restrict__ cand_cnt, const int* __restrict__ order,
+                              int64_t n_dst, int cap, int64_t n_groups, const int64_t* __restrict__ off,
+                              int* __restrict__ dense_r, int* __restrict__ dense_slot)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (g >= n_groups) return;
+    const int64_t i = g * 32 + lane;
+    const int r = i < n_dst ? (order ? order[i] : (int)i) : 0;
+    const int c = i < n_dst ? min(cand_cnt[r], cap) : 0;
+    const int* row = cand + (int64_t)r * cap;
+    int64_t base = off[g];
+    int h = 0;
+    int key = c > 0 ? row[0] : INT_MAX;
+    while (true) {
+        int m = key;
+        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
+        if (m == INT_MAX) break;
+        const bool mine = key == m;
+        const unsigned b = __ballot_sync(FULL, mine);
+        if (mine) {
+            const int64_t pos = base + __popc(b & ((1u << lane) - 1u));
+            dense_r[pos] = r;
+            dense_slot[pos] = h;
+            ++h;
+            key = h < c ? row[h] : INT_MAX;
+        }
+        base += __popc(b);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // occluder lists: the first segment of every path from a source S runs from S to a point of the
 // first face f, so it stays inside the union over f's triangles of the pyramids with apex S; only
@@ -1343,12 +1397,25 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                                           t.n, tol_base, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
                 }
                 // dense candidate list, then persistent validation
-                RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, s>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
-                RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, n_dst + 1, scan_tmp, s));
-                RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, s>>>(cs.cnt, L.dense_off, n_dst, cs.cap,
-                                                                                                   L.dense_r, L.dense_slot)));
+                int64_t n_off = n_dst;   // entries of dense_off before the total
+                if (n_dst > 1) {
+                    const int64_t ng = (n_dst + 31) / 32;
+                    const int* ord = L.rx_order;
+                    RISRT_KERNEL(ctx, "k_group_counts", (k_group_counts<<<nblk((ng + 1) * 32, 128), 128, 0, s>>>(
+                                                            cs.cnt, ord, n_dst, cs.cap, ng, cs.cnt64_tmp)));
+                    RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, ng + 1, scan_tmp, s));
+                    RISRT_KERNEL(ctx, "k_dense_merge", (k_dense_merge<<<nblk(ng * 32, 128), 128, 0, s>>>(
+                                                           cs.cand, cs.cnt, ord, n_dst, cs.cap, ng, L.dense_off, L.dense_r,
+                                                           L.dense_slot)));
+                    n_off = ng;
+                } else {
+                    RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, s>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
+                    RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, n_dst + 1, scan_tmp, s));
+                    RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, s>>>(cs.cnt, L.dense_off, n_dst, cs.cap,
+                                                                                                       L.dense_r, L.dense_slot)));
+                }
                 long long total = 0;
-                RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + n_dst, sizeof(long long), cudaMemcpyDeviceToHost, s));
+                RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + n_off, sizeof(long long), cudaMemcpyDeviceToHost, s));
                 RISRT_CUDA(ctx, cudaMemsetAsync(counters + 6, 0, sizeof(unsigned long long), s));
                 RISRT_CUDA(ctx, cudaStreamSynchronize(s));
                 int *vr = L.dense_r, *vs = L.dense_slot;
