@@ -4,49 +4,12 @@
 // evaluated in the RIS frame from the unfolded receiver image I_q: w = I_q - c, L = |w - u_m|,
 // cos(theta_out) = (w - u_m).n / L, per-bounce cos(theta_i) = |(w - u_m).n'_j| / L, and the phase
 // 2 pi frac(frac(D0/lambda) + dL/lambda) with D0 = |w| from FP64 and dL = (|u|^2 - 2 u.w)/(L + D0).
-#include "internal.cuh"
+#include "cplx32.cuh"
 
 namespace risrt {
 namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
-struct cf { float re, im; };
-__device__ __forceinline__ cf cmulf(cf a, cf b) { return cf{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-
-// principal complex square root in FP32
-__device__ __forceinline__ cf csqrtf_(float x, float y)
-{
-    float r = hypotf(x, y);
-    if (r == 0.f) return cf{0.f, 0.f};
-    if (x >= 0.f) {
-        float s = sqrtf(0.5f * (r + x));
-        return cf{s, y / (2.f * s)};
-    }
-    float s = copysignf(sqrtf(0.5f * (r - x)), y);
-    return cf{y / (2.f * s), s};
-}
-
-// Fresnel coefficient at incidence cos_i for permittivity (er, ei); TE or TM (Collin).
-__device__ __forceinline__ cf fresnel_f(float c, float er, float ei, bool tm)
-{
-    float s2 = fmaxf(1.f - c * c, 0.f);
-    if (!tm && ei == 0.f && er >= s2) {      // lossless dielectric: real coefficient
-        float root = sqrtf(er - s2);
-        return cf{(c - root) / (c + root), 0.f};
-    }
-    cf root = csqrtf_(er - s2, ei);
-    cf a, b;
-    if (!tm) {
-        a = cf{c - root.re, -root.im};
-        b = cf{c + root.re, root.im};
-    } else {
-        a = cf{er * c - root.re, ei * c - root.im};
-        b = cf{er * c + root.re, ei * c + root.im};
-    }
-    float inv = 1.f / (b.re * b.re + b.im * b.im);
-    return cf{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
-}
 
 template <int PAT>
 __device__ __forceinline__ float rx_pattern(float c, float gain)

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <string>
 
+#include "cplx32.cuh"
 #include "geom.cuh"
 
 namespace risrt {
@@ -788,6 +789,8 @@ __global__ void k_tx_vis(DeviceScene S, const float4* __restrict__ elem, int M, 
 // ------------------------------------------------------------------------------------------------
 struct WaveD {
     double lam, k, omega;
+    double inv_lam;        // 1 / lambda
+    float inv_we;          // 1 / (omega eps0): eps_c = eps_r - j sigma / (omega eps0)
     int tm;
 };
 
@@ -877,6 +880,22 @@ __device__ __forceinline__ float4 local4(const Frame& fr, d3 v, float w)
     return make_float4((float)dot(v, fr_t1(fr)), (float)dot(v, fr_t2(fr)), (float)dot(v, fr_n(fr)), w);
 }
 
+// FP32 face data for the per-path terms: unit normal and complex permittivity of the face's material.
+__device__ __forceinline__ float3 face_n32(const DeviceScene& S, int f)
+{
+    const float4 p = S.faces[f].plane32;
+    return f3(p.x, p.y, p.z);
+}
+__device__ __forceinline__ float2 face_eps32(const DeviceScene& S, int f, const WaveD& wv)
+{
+    const float2 m = S.mats[S.faces[f].mat];
+    return make_float2(m.x, -m.y * wv.inv_we);
+}
+__device__ __forceinline__ float3 mirror_dir_f(float3 v, float3 n) { return v - n * (2.f * dot(n, v)); }
+
+// Per (Rx, path) record for the field kernel. FP64 only where the phase needs it: the receiver image
+// I (mirrored through the bounce planes in reverse order), w = I - c in the RIS frame, D0 = |w| and
+// frac(D0 / lambda); the normals, pattern axis and permittivities are FP32 (they enter amplitudes only).
 __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, Frame fr, WaveD wv,
                           AntD rxa, const int* __restrict__ cand, int cap, const int64_t* __restrict__ off,
                           const SeqEntry* __restrict__ seqs, PathRec* __restrict__ rec, int64_t* __restrict__ rec_seq)
@@ -888,7 +907,11 @@ __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n
     const int n = (int)(off[r + 1] - o);
     const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
     const d3 c = fr_c(fr);
-    const d3 zr = D3(rxa.z[0], rxa.z[1], rxa.z[2]);
+    const float3 t1 = f3((float)fr.t1[0], (float)fr.t1[1], (float)fr.t1[2]);
+    const float3 t2 = f3((float)fr.t2[0], (float)fr.t2[1], (float)fr.t2[2]);
+    const float3 nn = f3((float)fr.n[0], (float)fr.n[1], (float)fr.n[2]);
+    const float3 zr = f3((float)rxa.z[0], (float)rxa.z[1], (float)rxa.z[2]);
+    auto local = [&](float3 v, float wv_) { return make_float4(dot(v, t1), dot(v, t2), dot(v, nn), wv_); };
     for (int q = lane; q < n; q += 32) {
         int k = 0;
         int fa[2] = {-1, -1};
@@ -900,40 +923,43 @@ __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n
             fa[1] = info.y;
             id = info.z;
         }
-        // Rx mirrored through the bounce planes in reverse order: I = M_f1(M_f2(R))
         d3 I = R;
         for (int j = k - 1; j >= 0; --j) {
             dv4 pl = S.faces[fa[j]].plane;
             I = mirror_pt(I, ld3(pl), pl.w);
         }
-        d3 w = I - c;
-        double D0 = norm(w);
-        double fr0 = D0 / wv.lam - floor(D0 / wv.lam);
+        const d3 w = I - c;
+        const double D0 = sqrt(dot(w, w));
+        const double x = D0 * wv.inv_lam;
+        const float fr0 = (float)(x - floor(x));
         // Rx pattern axis unfolded: v = L_f1 L_f2 z_r
-        d3 v = zr;
-        for (int j = k - 1; j >= 0; --j) v = mirror_dir(v, ld3(S.faces[fa[j]].plane));
-        d3 n1 = D3(0, 0, 0), n2 = D3(0, 0, 0);
-        cd e1 = cd{1.0, 0.0}, e2 = cd{1.0, 0.0};
+        float3 v = zr;
+        for (int j = k - 1; j >= 0; --j) v = mirror_dir_f(v, face_n32(S, fa[j]));
+        float3 n1 = f3(0.f, 0.f, 0.f), n2 = n1;
+        float2 e1 = make_float2(1.f, 0.f), e2 = e1;
         if (k >= 1) {
-            n1 = ld3(S.faces[fa[0]].plane);
-            e1 = mat_eps(S, fa[0], wv);
+            n1 = face_n32(S, fa[0]);
+            e1 = face_eps32(S, fa[0], wv);
         }
         if (k == 2) {
-            n2 = mirror_dir(ld3(S.faces[fa[1]].plane), n1);
-            e2 = mat_eps(S, fa[1], wv);
+            n2 = mirror_dir_f(face_n32(S, fa[1]), n1);
+            e2 = face_eps32(S, fa[1], wv);
         }
         PathRec pr;
-        pr.w = local4(fr, w, (float)D0);
-        pr.a = make_float4((float)fr0, __int_as_float(k), (float)e1.re, (float)e1.im);
-        pr.n1 = local4(fr, n1, (float)e2.re);
-        pr.n2 = local4(fr, n2, (float)e2.im);
-        pr.v = local4(fr, v, 0.f);
+        pr.w = local4(fr, w, (float)D0);   // FP64 projection: |w_local| must match D0 for the phase
+        pr.a = make_float4(fr0, __int_as_float(k), e1.x, e1.y);
+        pr.n1 = local(n1, e2.x);
+        pr.n2 = local(n2, e2.y);
+        pr.v = local(v, 0.f);
         rec[o + q] = pr;
         rec_seq[o + q] = id;
     }
 }
 
-// E0 per receiver (one warp): LOS (if unblocked) + environment paths, FP64; fixed reduction order.
+// E0 per receiver (one warp): LOS (if unblocked) + environment paths (Eqs. 2-3 of the direct and
+// reflected Tx -> Rx rays), each from its unfolded image source Ts. FP64 for the unfolded length L and
+// frac(L / lambda); FP32 for directions, Fresnel products, patterns and amplitudes. Fixed order: lane-
+// strided paths, then a shuffle tree.
 __global__ void k_e0(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, AntD tx, AntD rxa, WaveD wv,
                      const uint8_t* __restrict__ los, const int* __restrict__ cand, int cap,
                      const int64_t* __restrict__ cnt, const SeqEntry* __restrict__ seqs,
@@ -944,10 +970,12 @@ __global__ void k_e0(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, 
     if (r >= n_rx) return;
     const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
     const d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
-    const d3 zt = D3(tx.z[0], tx.z[1], tx.z[2]);
-    const d3 zr = D3(rxa.z[0], rxa.z[1], rxa.z[2]);
+    const float3 zt = f3((float)tx.z[0], (float)tx.z[1], (float)tx.z[2]);
+    const float3 zr = f3((float)rxa.z[0], (float)rxa.z[1], (float)rxa.z[2]);
+    const float gt = (float)tx.gain, gr = (float)rxa.gain;
+    const float amp0 = (float)(sqrt(2.0 * kEta0 * tx.power * tx.gain) * sqrt(rxa.gain) * wv.lam / (4.0 * kPi));
     const int n = cnt ? (int)cnt[r] : 0;
-    cd acc = cd{0.0, 0.0};
+    float are = 0.f, aim = 0.f;
     for (int q = lane - 1; q < n; q += 32) {     // q = -1: LOS
         d3 Ts = T;
         int fa[2] = {-1, -1};
@@ -962,23 +990,39 @@ __global__ void k_e0(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, 
             fa[1] = info.y;
             Ts = k == 2 ? ld3(seqd[si].S2) : ld3(seqd[si].S1);
         }
-        double L;
-        d3 dep, arr;
-        cd Rf;
-        unfolded_from_source(S, Ts, R, fa, k, wv, &L, &dep, &arr, &Rf);
-        double Ft = pattern_d(tx.pattern, tx.gain, dot(dep, zt));
-        double Fr = pattern_d(rxa.pattern, rxa.gain, -dot(arr, zr));
-        double amp = sqrt(2.0 * kEta0 * tx.power * tx.gain * Ft) * sqrt(rxa.gain * Fr) * wv.lam / (4.0 * kPi * L);
-        double ph = -2.0 * kPi * (L / wv.lam - floor(L / wv.lam));
-        double sn, cs;
-        sincos(ph, &sn, &cs);
-        acc = cadd(acc, cmul(Rf, cd{amp * cs, amp * sn}));
+        const d3 d = R - Ts;
+        const double L = sqrt(dot(d, d));
+        const double x = L * wv.inv_lam;
+        const float ph = (float)(x - floor(x));
+        float3 u = to_f(d);                       // arrival direction: the last segment is real
+        u = u * rsqrtf(dot(u, u));
+        cf Rp = cf{1.f, 0.f};
+        if (k >= 1) {                             // last bounce plane real, the earlier one mirrored across it
+            const float3 nl = face_n32(S, fa[k - 1]);
+            const float2 el = face_eps32(S, fa[k - 1], wv);
+            Rp = fresnel_f(fabsf(dot(u, nl)), el.x, el.y, wv.tm);
+            if (k == 2) {
+                const float3 n1 = mirror_dir_f(face_n32(S, fa[0]), nl);
+                const float2 e1 = face_eps32(S, fa[0], wv);
+                Rp = cmulf(Rp, fresnel_f(fabsf(dot(u, n1)), e1.x, e1.y, wv.tm));
+            }
+        }
+        float3 dep = u;                           // real first-segment direction: L_f1 L_f2 u
+        for (int j = k - 1; j >= 0; --j) dep = mirror_dir_f(dep, face_n32(S, fa[j]));
+        const float Ft = pattern_f(tx.pattern, gt, dot(dep, zt));
+        const float Fr = pattern_f(rxa.pattern, gr, -dot(u, zr));
+        const float amp = amp0 * sqrtf(Ft * Fr) / (float)L;
+        float sn, cs;
+        sincospif(2.f * ph, &sn, &cs);            // e^{-j 2 pi frac(L / lambda)}
+        const cf t = cmulf(Rp, cf{amp * cs, -amp * sn});
+        are += t.re;
+        aim += t.im;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        acc.re += __shfl_down_sync(0xffffffffu, acc.re, o);
-        acc.im += __shfl_down_sync(0xffffffffu, acc.im, o);
+        are += __shfl_down_sync(0xffffffffu, are, o);
+        aim += __shfl_down_sync(0xffffffffu, aim, o);
     }
-    if (lane == 0) E0[r] = make_float2((float)acc.re, (float)acc.im);
+    if (lane == 0) E0[r] = make_float2(are, aim);
 }
 
 __global__ void k_los(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, AntD tx, float tol_base,
@@ -1184,6 +1228,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     wv.lam = kC0 / freq;
     wv.k = 2.0 * kPi / wv.lam;
     wv.omega = 2.0 * kPi * freq;
+    wv.inv_lam = 1.0 / wv.lam;
+    wv.inv_we = (float)(1.0 / (wv.omega * kEps0));
     wv.tm = (flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
     double G = ris->elem_gain > 0 ? (double)ris->elem_gain : 4.0 * kPi * (double)ris->dy * (double)ris->dz / (wv.lam * wv.lam);
     double K = sqrt(G * (double)ris->dy * (double)ris->dz / (4.0 * kPi)) * wv.lam / (4.0 * kPi);
