@@ -183,28 +183,19 @@ __device__ __forceinline__ int face_class(const DeviceScene& S, const FaceTest* 
     return in_face_fp32(S, f, q, tol);
 }
 
-// Can any destination inside the box [lo, hi] make sequence e geometrically valid? It must lie on
-// the previous image's side of the last plane and inside the cone from the last image through the
-// last face (union over the face's triangles). False only when the whole box is separated by more
-// than `margin`, far beyond FP32 error, so skipping it for every destination in the box changes no
-// decision.
-__device__ bool box_in_beam(const DeviceScene& S, const SeqEntry& e, float3 lo, float3 hi, float margin)
+// Does the box [lo, hi] reach into the pyramid from apex `ap` through one of face f's triangles
+// (optionally mirrored across the plane (mn, md))? False only when, for every triangle, one side
+// plane of its pyramid has all eight corners outside by more than `margin`.
+__device__ bool box_meets_pyramid(const DeviceScene& S, float3 ap, int f, bool mirror, float3 mn, float md, float3 lo,
+                                  float3 hi, float margin)
 {
-    const float3 nL = xyz(e.pL);
-    const float sp = e.sL.w;
-    bool same = false;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float3 q = f3((c & 1) ? hi.x : lo.x, (c & 2) ? hi.y : lo.y, (c & 4) ? hi.z : lo.z);
-        const float sR = dot(nL, q) - e.pL.w;
-        if (sp > 0.f ? sR > -margin : sR < margin) same = true;
-    }
-    if (!same) return false;
-    const float3 ap = xyz(e.sL);
-    const Face fc = S.faces[e.info.w == 2 ? e.info.y : e.info.x];
+    const Face fc = S.faces[f];
     for (int j = fc.tri_begin; j < fc.tri_end; ++j) {
         const TriVerts tv = S.tri_verts[S.face_tris[j]];
-        const float3 v[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
+        float3 v[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
+        if (mirror)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v[k] = v[k] - mn * (2.f * (dot(mn, v[k]) - md));
         bool separated = false;
         for (int k = 0; k < 3 && !separated; ++k) {
             float3 n = cross(v[k] - ap, v[(k + 1) % 3] - ap);
@@ -225,12 +216,107 @@ __device__ bool box_in_beam(const DeviceScene& S, const SeqEntry& e, float3 lo, 
     return false;
 }
 
+// Can any destination inside the box [lo, hi] make sequence e geometrically valid? It must lie on
+// the previous image's side of the last plane, inside the pyramid from the last image S_L through the
+// last face, and for order 2 also inside the pyramid from S_L through the first face mirrored across
+// the last plane (unfolded, the straight line from S_2 to the destination crosses the mirror image of
+// the first reflection point). False only when the whole box is separated by more than `margin`, far
+// beyond FP32 error, so skipping it for every destination in the box changes no decision.
+__device__ bool box_in_beam(const DeviceScene& S, const SeqEntry& e, float3 lo, float3 hi, float margin)
+{
+    const float3 nL = xyz(e.pL);
+    const float sp = e.sL.w;
+    bool same = false;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float3 q = f3((c & 1) ? hi.x : lo.x, (c & 2) ? hi.y : lo.y, (c & 4) ? hi.z : lo.z);
+        const float sR = dot(nL, q) - e.pL.w;
+        if (sp > 0.f ? sR > -margin : sR < margin) same = true;
+    }
+    if (!same) return false;
+    const float3 ap = xyz(e.sL);
+    const bool two = e.info.w == 2;
+    if (!box_meets_pyramid(S, ap, two ? e.info.y : e.info.x, false, nL, e.pL.w, lo, hi, margin)) return false;
+    return !two || box_meets_pyramid(S, ap, e.info.x, true, nL, e.pL.w, lo, hi, margin);
+}
+
+// Deferred FP64 settlements. A warp settles one too-close-to-call FP32 decision with all its FP64
+// instructions even when one lane needs it, and FP64 issues at a small fraction of the FP32 rate, so
+// the filters queue such cases and a dense kernel settles them afterwards, 32 per warp. q == nullptr,
+// or a full queue, settles inline instead.
+struct RefineQ {
+    int4* q;
+    int cap;
+    unsigned* cnt;
+};
+
+// Margin of the beam culling for a box: far beyond the FP32 error of the plane and corner arithmetic.
+__device__ __forceinline__ float cull_margin(float3 lo, float3 hi)
+{
+    return 1e-3f + 1e-5f * (fabsf(lo.x) + fabsf(lo.y) + fabsf(lo.z) + fabsf(hi.x) + fabsf(hi.y) + fabsf(hi.z));
+}
+
+// Super-patches: kSuperRx destinations consecutive in Morton order. Their bounding boxes (one block each).
+constexpr int kSuperRx = 1024;
+__global__ void k_patch_boxes(const float* __restrict__ dst_xyz, const int* __restrict__ order, int64_t n_dst,
+                              float4* __restrict__ boxes)
+{
+    __shared__ float3 wlo[8], whi[8];
+    const float inf = __int_as_float(0x7f800000);
+    float3 lo = f3(inf, inf, inf), hi = f3(-inf, -inf, -inf);
+    const int64_t b0 = blockIdx.x * (int64_t)kSuperRx;
+    for (int i = threadIdx.x; i < kSuperRx && b0 + i < n_dst; i += blockDim.x) {
+        const int64_t r = order[b0 + i];
+        const float3 q = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
+        lo = f3(fminf(lo.x, q.x), fminf(lo.y, q.y), fminf(lo.z, q.z));
+        hi = f3(fmaxf(hi.x, q.x), fmaxf(hi.y, q.y), fmaxf(hi.z, q.z));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = f3(fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o)), fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o)),
+                fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o)));
+        hi = f3(fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o)), fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o)),
+                fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o)));
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        wlo[warp] = lo;
+        whi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = f3(fminf(lo.x, wlo[w].x), fminf(lo.y, wlo[w].y), fminf(lo.z, wlo[w].z));
+            hi = f3(fmaxf(hi.x, whi[w].x), fmaxf(hi.y, whi[w].y), fmaxf(hi.z, whi[w].z));
+        }
+        boxes[2 * blockIdx.x] = make_float4(lo.x, lo.y, lo.z, 0.f);
+        boxes[2 * blockIdx.x + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    }
+}
+
+// One bit per (super-patch, sequence): can a destination of the super-patch make the sequence valid
+// (box_in_beam on the super-patch box)? Word w of super-patch p covers sequences 32w .. 32w + 31.
+__global__ void k_seq_cull(DeviceScene S, const SeqEntry* __restrict__ seqs, int n_seq, const float4* __restrict__ boxes,
+                           int64_t n_super, int words, unsigned* __restrict__ mask)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t sp = blockIdx.y; sp < n_super; sp += gridDim.y) {
+        bool k = false;
+        if (i < n_seq) {
+            const float3 lo = xyz(boxes[2 * sp]), hi = xyz(boxes[2 * sp + 1]);
+            k = box_in_beam(S, seqs[i], lo, hi, cull_margin(lo, hi));
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, k);
+        if ((threadIdx.x & 31) == 0 && (i >> 5) < words) mask[sp * words + (i >> 5)] = b;
+    }
+}
+
 template <bool SMEM_FACES>
 __global__ void __launch_bounds__(kCandThreads)
 k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, const int* __restrict__ order, d3 src,
              const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int n_seq,
              float tol_base, int* __restrict__ cand, int* __restrict__ cand_cnt, int cap,
-             int* __restrict__ overflow, unsigned long long* __restrict__ refines)
+             int* __restrict__ overflow, unsigned long long* __restrict__ refines, const unsigned* __restrict__ smask,
+             int words, RefineQ rq)
 {
     __shared__ SeqEntry sh[kCandThreads];
     __shared__ unsigned char keep[kCandThreads];
@@ -259,16 +345,30 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
     }
     __syncthreads();
     const float3 blo = box[0], bhi = box[1];
-    const float margin = 1e-3f + 1e-5f * (fabsf(blo.x) + fabsf(blo.y) + fabsf(blo.z) + fabsf(bhi.x) + fabsf(bhi.y) + fabsf(bhi.z));
+    const float margin = cull_margin(blo, bhi);
+    // this block's super-patch survivors (kSuperRx / kCandThreads blocks per super-patch)
+    const unsigned* sm = smask ? smask + (int64_t)(blockIdx.x / (kSuperRx / kCandThreads)) * words : nullptr;
     for (int64_t chunk = blockIdx.y; chunk * kCandChunk < n_seq; chunk += gridDim.y) {
     const int s_begin = (int)(chunk * kCandChunk);
     const int s_end = min(n_seq, s_begin + kCandChunk);
     for (int s0 = s_begin; s0 < s_end; s0 += kCandThreads) {
+        if (sm) {                                     // no survivor in this round: skip it (uniform)
+            unsigned any = 0;
+#pragma unroll
+            for (int q = 0; q < kCandThreads / 32; ++q)
+                if ((s0 >> 5) + q < words) any |= sm[(s0 >> 5) + q];
+            if (!any) continue;
+        }
         __syncthreads();
         if (s0 + threadIdx.x < s_end) {
-            const SeqEntry e = seqs[s0 + threadIdx.x];
-            sh[threadIdx.x] = e;
-            keep[threadIdx.x] = box_in_beam(S, e, blo, bhi, margin) ? 1 : 0;
+            const int si = s0 + threadIdx.x;
+            unsigned char k = 0;
+            if (!sm || ((sm[si >> 5] >> (si & 31)) & 1u)) {
+                const SeqEntry e = seqs[si];
+                sh[threadIdx.x] = e;
+                k = box_in_beam(S, e, blo, bhi, margin) ? 1 : 0;
+            }
+            keep[threadIdx.x] = k;
         }
         __syncthreads();
         const int cnt = min(kCandThreads, s_end - s0);
@@ -315,6 +415,13 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
                 unsure |= cD == 2;
             }
             if (unsure) {
+                if (rq.q) {
+                    const unsigned pos = atomicAdd(rq.cnt, 1u);
+                    if (pos < (unsigned)rq.cap) {
+                        rq.q[pos] = make_int4((int)r, s0 + j, 0, 0);
+                        continue;
+                    }
+                }
                 atomicAdd(refines, 1ull);
                 d3 pts[4];
                 const d3 Rd = D3((double)R.x, (double)R.y, (double)R.z);
@@ -329,6 +436,26 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
 }
 
 // Dense list of the (destination, slot) pairs holding a geometric candidate, receiver-major.
+// Settle the queued candidate decisions in FP64 (seq_geom_fp64, the same check as the inline path).
+__global__ void k_refine_cand(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, const SeqEntry* __restrict__ seqs,
+                              const SeqEntryD* __restrict__ seqd, RefineQ rq, int* __restrict__ cand,
+                              int* __restrict__ cand_cnt, int cap, int* __restrict__ overflow,
+                              unsigned long long* __restrict__ refines)
+{
+    const unsigned n = min(*rq.cnt, (unsigned)rq.cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(refines, (unsigned long long)n);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 q = rq.q[i];
+        const int64_t r = q.x;
+        const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
+        d3 pts[4];
+        if (!seq_geom_fp64(S, src, D3((double)R.x, (double)R.y, (double)R.z), seqs[q.y].info, seqd[q.y], pts)) continue;
+        const int slot = atomicAdd(&cand_cnt[r], 1);
+        if (slot < cap) cand[r * (int64_t)cap + slot] = q.y;
+        else atomicExch(overflow, 1);
+    }
+}
+
 __global__ void k_cand_counts(const int* __restrict__ cand_cnt, int64_t n_dst, int cap, int64_t* __restrict__ out)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -578,7 +705,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
            const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int* __restrict__ cand, int cap,
            const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const float4* __restrict__ dpts,
            long long total, unsigned long long* __restrict__ next, float tol_base, unsigned long long* refines,
-           int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx)
+           int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx,
+           RefineQ rq)
 {
     const float3 srcf = to_f(src);
     const unsigned FULL = 0xffffffffu;
@@ -624,6 +752,13 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         const int h = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
         bool hit = h == 1;
         if (h == 2) {
+            if (rq.q) {             // settled later; the traversal goes on as if this triangle missed
+                const unsigned pos = atomicAdd(rq.cnt, 1u);
+                if (pos < (unsigned)rq.cap) {
+                    rq.q[pos] = make_int4((int)item, j, i, 0);
+                    return false;
+                }
+            }
             atomicAdd(refines, 1ull);
             const d3 R = D3((double)dst_xyz[3 * r], (double)dst_xyz[3 * r + 1], (double)dst_xyz[3 * r + 2]);
             d3 pts[4];
@@ -718,6 +853,28 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         }
     }
     flush_counters(tc, ctr);
+}
+
+// Settle the queued triangle tests of the validation in FP64: a hit blocks the candidate (the
+// traversal treated the triangle as missed, so only a hit changes the outcome).
+__global__ void k_refine_val(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, const SeqEntry* __restrict__ seqs,
+                             const SeqEntryD* __restrict__ seqd, int* __restrict__ cand, int cap,
+                             const int* __restrict__ dense_r, const int* __restrict__ dense_slot, RefineQ rq,
+                             unsigned long long* __restrict__ refines)
+{
+    const unsigned n = min(*rq.cnt, (unsigned)rq.cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(refines, (unsigned long long)n);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 q = rq.q[i];
+        const int r = dense_r[q.x], slot = dense_slot[q.x];
+        const int si = cand[(int64_t)r * cap + slot];
+        if (si < 0) continue;                    // already blocked
+        const d3 R = D3((double)dst_xyz[3 * r], (double)dst_xyz[3 * r + 1], (double)dst_xyz[3 * r + 2]);
+        d3 pts[4];
+        seq_points_fp64(S, R, seqs[si].info, seqd[si], src, pts);
+        const d3 dD = pts[q.y + 1] - pts[q.y];
+        if (tri_hit_fp64(S.tri_verts[q.z], pts[q.y], dD, norm(dD))) cand[(int64_t)r * cap + slot] = -1;
+    }
 }
 
 // Per destination (one warp): keep the valid candidates, sorted by sequence id (rank sort; ids are
@@ -1292,6 +1449,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     const int64_t n_ids_env = max_env >= 2 ? (int64_t)F + (int64_t)F * F : (max_env >= 1 ? F : 0);
     const int64_t n_ids_max = std::max(n_ids_tx, std::max(n_ids_rx, n_ids_env));
     int cap = ps->cand_cap > 0 ? ps->cand_cap : 512;
+    const int rq_cap = (int)std::min<int64_t>(16 * n_rx + 4096, (int64_t)1 << 22);
 
     for (int attempt = 0; attempt < 6; ++attempt) {
         struct Layout {
@@ -1316,6 +1474,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             void* rx_sort_tmp;
             unsigned* rx_bb;
             int* rx_order;
+            float4* sp_box;          // super-patch boxes [n_super][2]
+            unsigned* sp_mask;       // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
+            int4* rq;                // deferred FP64 settlements (candidates, then validation)
+            unsigned* rq_cnt;
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -1354,6 +1516,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.dense_r2 = A.get<int>((size_t)n_rx * cap);
             L.dense_slot2 = A.get<int>((size_t)n_rx * cap);
             L.face_off64 = A.get<int64_t>(F + 1);
+            const int64_t n_super = (n_rx + kSuperRx - 1) / kSuperRx;
+            L.sp_box = A.get<float4>((size_t)n_super * 2);
+            L.sp_mask = A.get<unsigned>((size_t)n_super * ((n_ids_max + 31) / 32 + 1));
+            L.rq = A.get<int4>((size_t)rq_cap);
+            L.rq_cnt = A.get<unsigned>(2);
         };
         Arena measure;
         Layout Lm;
@@ -1431,17 +1598,33 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, s));
             if (t.n > 0) {
                 dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
+                const RefineQ rq{L.rq, rq_cap, L.rq_cnt};
+                RISRT_CUDA(ctx, cudaMemsetAsync(L.rq_cnt, 0, sizeof(unsigned) * 2, s));
+                // sequences that can reach each super-patch of kSuperRx Morton-consecutive destinations
+                const unsigned* smask = nullptr;
+                const int words = (t.n + 31) / 32;
+                if (n_dst > kCandThreads) {
+                    const int64_t n_super = (n_dst + kSuperRx - 1) / kSuperRx;
+                    RISRT_KERNEL(ctx, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, s>>>(dst, L.rx_order, n_dst,
+                                                                                                      L.sp_box)));
+                    RISRT_KERNEL(ctx, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
+                                                                  256, 0, s>>>(S, t.e, t.n, L.sp_box, n_super, words, L.sp_mask)));
+                    smask = L.sp_mask;
+                }
+                const int* ord = n_dst > 1 ? L.rx_order : nullptr;
                 if (F <= kMaxSmemFaces) {
                     const size_t shm = sizeof(FaceTest) * (size_t)F;
                     cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
-                                                          S, dst, n_dst, n_dst > 1 ? L.rx_order : nullptr, src, t.e, t.d,
-                                                          t.n, tol_base, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
+                                                          S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
+                                                          cs.cap, flags_dev, counters, smask, words, rq)));
                 } else {
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
-                                                          S, dst, n_dst, n_dst > 1 ? L.rx_order : nullptr, src, t.e, t.d,
-                                                          t.n, tol_base, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
+                                                          S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
+                                                          cs.cap, flags_dev, counters, smask, words, rq)));
                 }
+                RISRT_KERNEL(ctx, "k_refine_cand", (k_refine_cand<<<ctx->sm_count * 2, 256, 0, s>>>(
+                                                       S, dst, src, t.e, t.d, rq, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
                 // dense candidate list, then persistent validation
                 int64_t n_off = n_dst;   // entries of dense_off before the total
                 if (n_dst > 1) {
@@ -1480,6 +1663,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     vs = L.dense_slot2;
                 }
                 if (total > 0) {
+                    // the validation queue reuses the buffer (the candidate settlements are done); item ids are int
+                    const RefineQ vq{total < ((long long)1 << 31) ? L.rq : nullptr, rq_cap, L.rq_cnt + 1};
                     RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<nblk(total, 256), 256, 0, s>>>(
                                                            dst, t.e, cs.cand, cs.cap, vr, vs, total, L.dense_pts)));
                     const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * RISRT_VALIDATE_MINB,
@@ -1487,7 +1672,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                         S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
                                                         vs, L.dense_pts, total, counters + 6, tol_base, counters, flags_dev + 1,
-                                                        counters + 2, occ_off_src[occ], ps->occ_idx[occ])));
+                                                        counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq)));
+                    RISRT_KERNEL(ctx, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, s>>>(
+                                                          S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
                 }
             }
             const int warps = 4;
@@ -1729,11 +1916,11 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
-                                                  L.flags, L.counters)));
+                                                  L.flags, L.counters, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
         } else {
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
-                                                  L.flags, L.counters)));
+                                                  L.flags, L.counters, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
         }
         RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<1, 32, 0, s>>>(L.cnt, 1, cap, L.cnt64_tmp)));
         RISRT_CUDA(ctx, exclusive_scan_i64(L.cnt64_tmp, L.dense_off, 2, L.scan_tmp, s));
@@ -1751,7 +1938,7 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                 S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
                                                 L.dense_slot, L.dense_pts, total, L.counters + 6, tol_base, L.counters,
-                                                L.flags + 1, L.counters + 2, nullptr, nullptr)));
+                                                L.flags + 1, L.counters + 2, nullptr, nullptr, RefineQ{nullptr, 0, nullptr})));
         }
         const size_t shm = sizeof(int) * (size_t)cap;
         cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
