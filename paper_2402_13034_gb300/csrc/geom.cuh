@@ -156,7 +156,7 @@ __device__ __forceinline__ void flush_counters(const TraceCounters& t, unsigned 
 __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
                            unsigned long long* refines, int* err, TraceCounters* tc = nullptr)
 {
-    if (S.root == -1) return false;
+    if (S.root == kNoRoot) return false;
     float3 a = to_f(A), b = to_f(B);
     float3 dir = b - a;
     float len = sqrtf(dot(dir, dir));
@@ -164,37 +164,48 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
     float tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
     int stack[64];
     int sp = 0;
-    stack[sp++] = S.root;
-    while (sp > 0) {
-        int c = stack[--sp];
+    int c = S.root;          // current node in a register; only the farther of two entered children is pushed
+    while (true) {
         if (c < 0) {
             int i = ~c;
             int f = S.tri_face[i];
-            if (f == ign0 || f == ign1) continue;
-            if (tc) ++tc->tris;
-            int r = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
-            if (r == 1) return true;
-            if (r == 2) {
-                if (refines) atomicAdd(refines, 1ull);
-                const d3 dirD = B - A;
-                if (tri_hit_fp64(S.tri_verts[i], A, dirD, norm(dirD))) return true;
+            if (f != ign0 && f != ign1) {
+                if (tc) ++tc->tris;
+                int r = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
+                if (r == 1) return true;
+                if (r == 2) {
+                    if (refines) atomicAdd(refines, 1ull);
+                    const d3 dirD = B - A;
+                    if (tri_hit_fp64(S.tri_verts[i], A, dirD, norm(dirD))) return true;
+                }
             }
+            if (sp == 0) break;
+            c = stack[--sp];
             continue;
         }
         const BvhNode nd = S.nodes[c];
         if (tc) ++tc->nodes;
         const float el = box_entry(nd.l_lo, nd.l_hi, a, inv);
         const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
-        if (sp + 2 > 64) {
-            if (err) atomicExch(err, 1);
-            return true;
-        }
         // any hit ends the query, so the child entered first along the segment is visited first
         const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-        const bool lfirst = el <= er;
-        const float efar = lfirst ? er : el, enear = lfirst ? el : er;
-        if (efar < 1e30f) stack[sp++] = lfirst ? cr : cl;
-        if (enear < 1e30f) stack[sp++] = lfirst ? cl : cr;
+        const bool hl = el < 1e30f, hr = er < 1e30f;
+        if (hl && hr) {
+            if (sp >= 64) {
+                if (err) atomicExch(err, 1);
+                return true;
+            }
+            const bool lfirst = el <= er;
+            stack[sp++] = lfirst ? cr : cl;
+            c = lfirst ? cl : cr;
+        } else if (hl) {
+            c = cl;
+        } else if (hr) {
+            c = cr;
+        } else {
+            if (sp == 0) break;
+            c = stack[--sp];
+        }
     }
     return false;
 }

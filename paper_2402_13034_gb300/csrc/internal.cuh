@@ -19,6 +19,7 @@ constexpr double kEta0 = 120.0 * kPi;        // Eq. 1: free-space impedance 120 
 constexpr double kEps0 = 8.8541878128e-12;   // F/m
 constexpr float kSegEps = 1e-4f;             // occluder hits within this of a segment end are ignored
 constexpr double kSegEpsD = 1e-4;
+constexpr int kNoRoot = (int)0x80000000;   // BVH root of a scene without triangles
 
 // ------------------------------------------------------------------------------------------------
 // small vector helpers
@@ -97,7 +98,7 @@ struct FaceTest {
 struct DeviceScene {
     int64_t n_tris;
     int n_faces;
-    int root;                    // root child code (internal index, or ~leaf for one triangle); -1 if empty
+    int root;                    // root child code (internal index, or ~leaf for one triangle); kNoRoot if empty
     const BvhNode* nodes;
     const TriGeom* tri_geom;     // [n_refs] leaf (reference) order
     const TriVerts* tri_verts;   // [n_refs] leaf order
@@ -146,7 +147,7 @@ struct risrt_scene {
     int64_t n_refs = 0;              // BVH leaves (triangle references)
     int n_faces = 0;
     int n_mat = 0;
-    int root = -1;
+    int root = risrt::kNoRoot;
     risrt::BvhNode* nodes = nullptr;
     risrt::TriGeom* tri_geom = nullptr;
     risrt::TriVerts* tri_verts = nullptr;

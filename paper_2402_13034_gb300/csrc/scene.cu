@@ -612,7 +612,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &sc->mats, n_mat))) return rc;
     RISRT_CUDA(ctx, cudaMemcpyAsync(sc->mats, mats_host, sizeof(float2) * n_mat, cudaMemcpyHostToDevice, s));
     if (nt == 0) {
-        sc->root = -1;
+        sc->root = kNoRoot;
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));
         return RISRT_OK;
     }

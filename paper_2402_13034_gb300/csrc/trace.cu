@@ -687,7 +687,7 @@ __global__ void k_cand_points(const float* __restrict__ dst_xyz, const SeqEntry*
 // FP32 classification is too close to call. ctr[0..3]: candidates, segments, nodes, triangle tests.
 constexpr int kValThreads = 128;
 #ifndef RISRT_VALIDATE_STEPS
-#define RISRT_VALIDATE_STEPS 16    // BVH visits per lane between refills (measured on the room workload)
+#define RISRT_VALIDATE_STEPS 64    // BVH visits per lane between refills (measured on the room workload)
 #endif
 #ifndef RISRT_MAX_OCC_LIST
 #define RISRT_MAX_OCC_LIST (-1)    // occluder lists up to this length replace BVH traversal; -1: off
@@ -721,6 +721,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     int ign0 = -1, ign1 = -1;
     int stack[64];
     int sp = 0;
+    constexpr int kNone = 0x7fffffff;
+    int cur = kNone;             // current node in a register; only the farther of two entered children is pushed
     int li = 0, le = 0;          // occluder-list cursor (segment 0 only)
     bool list_mode = false;
     bool blocked = false;
@@ -739,8 +741,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
             le = occ_off[info.x + 1];
             sp = 0;
         } else {
-            stack[0] = S.root;
-            sp = 1;
+            cur = S.root == kNoRoot ? kNone : S.root;
+            sp = 0;
         }
         ++tc.segs;
     };
@@ -814,33 +816,44 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                 }
             }
         } else {
-            for (int it = 0; it < kSteps && sp > 0; ++it) {
-                const int c = stack[--sp];
-                if (c < 0) {
-                    if (test_leaf(~c)) {
+            for (int it = 0; it < kSteps && cur != kNone; ++it) {
+                if (cur < 0) {
+                    if (test_leaf(~cur)) {
                         blocked = true;
+                        cur = kNone;
                         sp = 0;
+                        break;
                     }
+                    cur = sp > 0 ? stack[--sp] : kNone;
                     continue;
                 }
-                const BvhNode nd = S.nodes[c];
+                const BvhNode nd = S.nodes[cur];
                 ++tc.nodes;
                 const float el = box_entry(nd.l_lo, nd.l_hi, a, inv);
                 const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
-                if (sp + 2 > 64) {
-                    atomicExch(err, 1);
-                    blocked = true;
-                    sp = 0;
-                    break;
-                }
                 const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-                const bool lfirst = el <= er;               // nearer child on top of the stack
-                const float efar = lfirst ? er : el, enear = lfirst ? el : er;
-                if (efar < 1e30f) stack[sp++] = lfirst ? cr : cl;
-                if (enear < 1e30f) stack[sp++] = lfirst ? cl : cr;
+                const bool hl = el < 1e30f, hr = er < 1e30f;
+                if (hl && hr) {
+                    if (sp >= 64) {
+                        atomicExch(err, 1);
+                        blocked = true;
+                        cur = kNone;
+                        sp = 0;
+                        break;
+                    }
+                    const bool lfirst = el <= er;     // nearer child next, the other on the stack
+                    stack[sp++] = lfirst ? cr : cl;
+                    cur = lfirst ? cl : cr;
+                } else if (hl) {
+                    cur = cl;
+                } else if (hr) {
+                    cur = cr;
+                } else {
+                    cur = sp > 0 ? stack[--sp] : kNone;
+                }
             }
         }
-        if (list_mode ? li >= le : sp == 0) {
+        if (list_mode ? li >= le : cur == kNone) {
             if (blocked) {
                 cand[(int64_t)r * cap + slot] = -1;
                 item = -1;

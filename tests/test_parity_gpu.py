@@ -138,6 +138,26 @@ def test_empty_scene_with_orders():
     compare_fields(g["E"], g["P"], E, P, Sx)
 
 
+def test_single_triangle_occluder():
+    """A scene of one triangle (a BVH whose root is a leaf): it blocks the LOS of some receivers and
+    reflects on order-1 paths of both legs and of the environment; path sets and fields match."""
+    w = S.free_space(grid=12)
+    w.scene = S.Scene(np.array([[-1.0, -1.2, 1.75], [1.0, -1.2, 1.75], [0.0, 0.0, 1.75]], np.float32),
+                      np.array([[0, 1, 2]], np.int32), np.zeros(1, np.int32), np.zeros(1, np.int32),
+                      np.array([[5.3, 0.1]], np.float32))
+    w.max_order_tx = w.max_order_rx = 1
+    w.env_paths = True
+    g = run_gpu(w)
+    o, fld, E, P, Sx = _oracle_all(w)
+    op = o.rx_paths(w.rx_xyz)
+    bad = compare_pathsets(g["paths"], op, op["amb"], o.tx_leg())
+    assert not bad, bad[:10]
+    compare_fields(g["E"], g["P"], E, P, Sx, mask=~fld["amb"])
+    # the triangle removes the LOS of some receivers and not of others
+    los = np.asarray(op["los"], bool)
+    assert los.any() and (~los).any()
+
+
 def test_invalid_arguments():
     import torch
     from paper_2402_13034_gb300 import risrt as R
