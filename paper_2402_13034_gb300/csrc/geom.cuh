@@ -165,6 +165,7 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
     int stack[64];
     int sp = 0;
     int c = S.root;          // current node in a register; only the farther of two entered children is pushed
+    const int g0 = ign0 >= 0 ? ign0 : -3, g1 = ign1 >= 0 ? ign1 : -3;   // subtrees of one ignored face are skipped
     while (true) {
         if (c < 0) {
             int i = ~c;
@@ -189,7 +190,8 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
         const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
         // any hit ends the query, so the child entered first along the segment is visited first
         const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-        const bool hl = el < 1e30f, hr = er < 1e30f;
+        const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
+        const bool hl = el < 1e30f && fl != g0 && fl != g1, hr = er < 1e30f && fr != g0 && fr != g1;
         if (hl && hr) {
             if (sp >= 64) {
                 if (err) atomicExch(err, 1);

@@ -75,8 +75,8 @@ struct TriVerts {
 struct BvhNode {
     float4 l_lo;         // xyz, w = left child (int bits)
     float4 l_hi;         // xyz, w = right child (int bits)
-    float4 r_lo;
-    float4 r_hi;
+    float4 r_lo;         // xyz, w = the single face of every leaf under the left child, or -1 (int bits)
+    float4 r_hi;         // xyz, w = the same for the right child
 };
 
 struct Face {

@@ -433,7 +433,7 @@ __global__ void k_karras(const uint32_t* __restrict__ keys, int n, BvhNode* __re
     if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
 }
 
-__device__ __forceinline__ void store_slot(BvhNode* node, bool right, float3 lo, float3 hi)
+__device__ __forceinline__ void store_slot(BvhNode* node, bool right, float3 lo, float3 hi, int face)
 {
     float* base = right ? &node->r_lo.x : &node->l_lo.x;
     float* baseh = right ? &node->r_hi.x : &node->l_hi.x;
@@ -441,24 +441,28 @@ __device__ __forceinline__ void store_slot(BvhNode* node, bool right, float3 lo,
     volatile float* vh = baseh;
     vl[0] = lo.x; vl[1] = lo.y; vl[2] = lo.z;
     vh[0] = hi.x; vh[1] = hi.y; vh[2] = hi.z;
+    *(volatile float*)(right ? &node->r_hi.w : &node->r_lo.w) = __int_as_float(face);
 }
 
 // Bottom-up refit: the second child to finish a node merges both boxes and moves up.
+// Each child slot also records the one face all leaves below it belong to, or -1 when they mix
+// faces (r_lo.w: left child, r_hi.w: right child), so a traversal can skip subtrees of ignored faces.
 __global__ void k_refit(const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi, int n, BvhNode* nodes,
                         const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
-                        int* flags, float pad)
+                        const int* __restrict__ leaf_face, int* flags, float pad)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float3 lo = xyz(leaf_lo[i]), hi = xyz(leaf_hi[i]);
     lo = lo - f3(pad, pad, pad);
     hi = hi + f3(pad, pad, pad);
+    int face = leaf_face[i];
     int child = ~i;
     int p = parent_leaf[i];
     while (p >= 0) {
         BvhNode* node = nodes + p;
         bool right = __float_as_int(((volatile float*)&node->l_hi.w)[0]) == child;
-        store_slot(node, right, lo, hi);
+        store_slot(node, right, lo, hi, face);
         __threadfence();
         if (atomicAdd(&flags[p], 1) == 0) return;
         __threadfence();
@@ -467,6 +471,8 @@ __global__ void k_refit(const float4* __restrict__ leaf_lo, const float4* __rest
         float3 b_lo = f3(q[8], q[9], q[10]), b_hi = f3(q[12], q[13], q[14]);
         lo = f3(fminf(a_lo.x, b_lo.x), fminf(a_lo.y, b_lo.y), fminf(a_lo.z, b_lo.z));
         hi = f3(fmaxf(a_hi.x, b_hi.x), fmaxf(a_hi.y, b_hi.y), fmaxf(a_hi.z, b_hi.z));
+        const int fa = __float_as_int(q[11]), fb = __float_as_int(q[15]);
+        face = fa == fb ? fa : -1;
         child = p;
         p = parent_int[p];
     }
@@ -696,7 +702,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nr, s));
     if (nr > 1) {
         RISRT_KERNEL(ctx, "k_karras", (k_karras<<<nblk(nr - 1, 256), 256, 0, s>>>(keys, (int)nr, sc->nodes, parent_int, parent_leaf)));
-        RISRT_KERNEL(ctx, "k_refit", (k_refit<<<nblk(nr, 256), 256, 0, s>>>(leaf_lo, leaf_hi, (int)nr, sc->nodes, parent_int, parent_leaf, flags, pad)));
+        RISRT_KERNEL(ctx, "k_refit", (k_refit<<<nblk(nr, 256), 256, 0, s>>>(leaf_lo, leaf_hi, (int)nr, sc->nodes, parent_int, parent_leaf, sc->tri_face, flags, pad)));
         sc->root = 0;
     } else {
         sc->root = ~0;

@@ -718,7 +718,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     float3 p[4] = {f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f)};
     float3 a = f3(0.f, 0.f, 0.f), dir = a, inv = a;
     float len = 0.f, tb = 0.f;
-    int ign0 = -1, ign1 = -1;
+    int ign0 = -1, ign1 = -1, g0 = -3, g1 = -3;
     int stack[64];
     int sp = 0;
     constexpr int kNone = 0x7fffffff;
@@ -735,6 +735,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
         ign0 = j == 0 ? src_face : (j == 1 ? info.x : info.y);
         ign1 = j == info.w ? dst_face : (j == 0 ? info.x : info.y);
+        g0 = ign0 >= 0 ? ign0 : -3;        // subtrees of one ignored face are skipped
+        g1 = ign1 >= 0 ? ign1 : -3;
         list_mode = j == 0 && occ_off != nullptr && occ_off[info.x + 1] - occ_off[info.x] <= RISRT_MAX_OCC_LIST;
         if (list_mode) {            // only triangles that can meet the pyramid from the source through f1
             li = occ_off[info.x];
@@ -832,7 +834,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                 const float el = box_entry(nd.l_lo, nd.l_hi, a, inv);
                 const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
                 const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-                const bool hl = el < 1e30f, hr = er < 1e30f;
+                const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
+                const bool hl = el < 1e30f && fl != g0 && fl != g1, hr = er < 1e30f && fr != g0 && fr != g1;
                 if (hl && hr) {
                     if (sp >= 64) {
                         atomicExch(err, 1);
