@@ -52,6 +52,29 @@ CAND_OPS_PER_TEST = 28
 VISIT_OPS, TRI_OPS = 24, 20
 PRECISIONS = {0: "fp32_simt", 1: "bf16", 2: "bf16x2", 3: "fp16"}
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a dominant kernel from one
+# ncu capture of the bench workload, valid only for the kernel sources it was taken with: a changed
+# source reports null traffic until the capture is repeated.
+MEASURED_TRAFFIC = {
+    "k_validate": {"bytes_per_launch": 309.8e6, "sha256_16": "3524bf28d42c97c7",
+                   "sources": ["trace.cu", "geom.cuh", "internal.cuh"],
+                   "profile": "profiles/k_validate_room_256x256_dram.md"},
+}
+
+
+def measured_traffic(kernel):
+    import hashlib
+    t = MEASURED_TRAFFIC.get(kernel)
+    if not t:
+        return None, None
+    h = hashlib.sha256()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_2402_13034_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != t["sha256_16"]:
+        return None, "kernel sources changed since the ncu capture"
+    return t["bytes_per_launch"], t["profile"]
+
 
 def bench_gradient(ctx, R, dev, steps=200, reps=5):
     """Adjoint phase gradient on the office workload (20k triangles, 64x64 RIS, 16,384 target
@@ -472,8 +495,9 @@ def main():
             work = None
         if work is not None:
             achieved = work / (ms_launch / 1e3) / 1e12
+            traffic, tnote = measured_traffic(dom)
             roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                    "frac": achieved / alu_peak, "traffic": None,
+                    "frac": achieved / alu_peak, "traffic": traffic, "traffic_note": tnote,
                     "peak_note": f"FP32 lane-op issue peak at {sm_mhz:.0f} MHz (152 SMs x 128 lanes), derived"}
         else:
             roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
