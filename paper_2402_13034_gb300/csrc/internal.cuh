@@ -95,6 +95,19 @@ struct FaceTest {
     int pad[3];
 };
 
+// Cell grid over a face's plane for the visibility maps from a fixed source point: cell (i, j) covers
+// o + a u + b v with a in [a0 + i du, a0 + (i + 1) du], b in [b0 + j dv, b0 + (j + 1) dv]; its map
+// entry sits at off + i * nv + j.
+struct FaceGrid {
+    float4 o;            // xyz origin (a vertex of the face), w = du
+    float4 u;            // xyz unit in-plane axis, w = a0
+    float4 v;            // xyz unit in-plane axis (normal x u), w = b0
+    int nu, nv;
+    int off;
+    float dv;
+};
+constexpr float kMapDelta = 1e-3f;   // a cell's map entry holds for points up to this far outside it
+
 struct DeviceScene {
     int64_t n_tris;
     int n_faces;
@@ -108,6 +121,9 @@ struct DeviceScene {
     const FaceTest* face_test;   // [n_faces]
     const int* tri_leaf;         // [n_tris] one leaf (reference) of every input triangle
     const float2* mats;          // [n_mat] (eps_r, sigma)
+    const FaceGrid* face_grid;   // [n_faces]
+    const int* cell_face;        // [n_cells] face of every map cell
+    int64_t n_cells;
 };
 
 }  // namespace risrt
@@ -158,10 +174,14 @@ struct risrt_scene {
     int* tri_leaf = nullptr;
     float2* mats = nullptr;
     float scene_extent = 0.f;     // max |coordinate| over vertices
+    risrt::FaceGrid* face_grid = nullptr;
+    int* cell_face = nullptr;
+    int64_t n_cells = 0;
     risrt::DeviceScene dev() const {
         risrt::DeviceScene s;
         s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.nodes = nodes; s.tri_geom = tri_geom;
         s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.face_test = face_test; s.tri_leaf = tri_leaf; s.mats = mats;
+        s.face_grid = face_grid; s.cell_face = cell_face; s.n_cells = n_cells;
         return s;
     }
 };

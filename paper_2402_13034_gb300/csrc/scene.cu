@@ -500,6 +500,76 @@ __global__ void k_face_fill(const int32_t* __restrict__ face, int64_t nt, const 
     face_tris[start[f] + k] = leaf_of_orig[t];
 }
 
+// Per face: an orthonormal frame in its plane (origin at a vertex, u along an edge of the first
+// triangle, v = normal x u), the bounds of its vertices in (u, v), and a grid of cells of side about
+// h (1 to 128 per axis). cnt[f] = cells of face f (exclusive-scan input, cnt[F] = 0).
+__global__ void k_face_grid(const Face* __restrict__ faces, const int* __restrict__ face_tris,
+                            const TriVerts* __restrict__ tri_verts, int F, double h, FaceGrid* __restrict__ grid,
+                            int64_t* __restrict__ cnt)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f > F) return;
+    if (f == F) {
+        cnt[F] = 0;
+        return;
+    }
+    const Face fc = faces[f];
+    if (fc.tri_end <= fc.tri_begin) {      // a face id without triangles: one cell, never looked up
+        FaceGrid g = {};
+        g.o.w = 1.f;
+        g.dv = 1.f;
+        g.nu = g.nv = 1;
+        grid[f] = g;
+        cnt[f] = 1;
+        return;
+    }
+    const d3 n = D3(fc.plane.x, fc.plane.y, fc.plane.z);
+    const TriVerts t0 = tri_verts[face_tris[fc.tri_begin]];
+    const d3 o = D3(t0.v0.x, t0.v0.y, t0.v0.z);
+    d3 e = D3(t0.v1.x, t0.v1.y, t0.v1.z) - o;
+    e = e - n * dot(n, e);
+    double el = norm(e);
+    if (!(el > 0.0)) {            // degenerate first edge: any direction in the plane
+        e = fabs(n.x) < 0.9 ? cross(n, D3(1, 0, 0)) : cross(n, D3(0, 1, 0));
+        el = norm(e);
+    }
+    const d3 u = e * (1.0 / el);
+    const d3 v = cross(n, u);
+    double a0 = 1e300, a1 = -1e300, b0 = 1e300, b1 = -1e300;
+    for (int j = fc.tri_begin; j < fc.tri_end; ++j) {
+        const TriVerts tv = tri_verts[face_tris[j]];
+        const float4 q[3] = {tv.v0, tv.v1, tv.v2};
+        for (int k = 0; k < 3; ++k) {
+            const d3 p = D3(q[k].x, q[k].y, q[k].z) - o;
+            const double a = dot(p, u), b = dot(p, v);
+            a0 = fmin(a0, a); a1 = fmax(a1, a);
+            b0 = fmin(b0, b); b1 = fmax(b1, b);
+        }
+    }
+    const int nu = (int)fmin(fmax(ceil((a1 - a0) / h), 1.0), 128.0);
+    const int nv = (int)fmin(fmax(ceil((b1 - b0) / h), 1.0), 128.0);
+    FaceGrid g;
+    g.o = make_float4((float)o.x, (float)o.y, (float)o.z, (float)fmax((a1 - a0) / nu, 1e-6));
+    g.u = make_float4((float)u.x, (float)u.y, (float)u.z, (float)a0);
+    g.v = make_float4((float)v.x, (float)v.y, (float)v.z, (float)b0);
+    g.nu = nu;
+    g.nv = nv;
+    g.off = 0;
+    g.dv = (float)fmax((b1 - b0) / nv, 1e-6);
+    grid[f] = g;
+    cnt[f] = (int64_t)nu * nv;
+}
+
+__global__ void k_cell_face(FaceGrid* __restrict__ grid, const int64_t* __restrict__ off, int F, int* __restrict__ cell_face)
+{
+    const int f = blockIdx.x;
+    if (f >= F) return;
+    const int64_t o = off[f];
+    const int n = grid[f].nu * grid[f].nv;
+    if (threadIdx.x == 0) grid[f].off = (int)o;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cell_face[o + i] = f;
+}
+
 // Face plane in FP64 from the face's first triangle (lowest input index), as the image method's
 // mirror plane (Sec. II-B).
 __global__ void k_face_plane(const float* __restrict__ verts, const int32_t* __restrict__ tris,
@@ -729,6 +799,27 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_KERNEL(ctx, "k_face_plane", (k_face_plane<<<nblk(F, 128), 128, 0, s>>>(d_verts, d_tris, d_mat, first, start, count, F, sc->faces)));
     RISRT_KERNEL(ctx, "k_face_test", (k_face_test<<<nblk(F, 128), 128, 0, s>>>(sc->faces, sc->face_tris, sc->tri_verts,
                                                                                sc->tri_geom, F, sc->face_test)));
+
+    // cell grids of the faces for the per-source visibility maps (cells of about 1/96 of the extent)
+    {
+        int64_t *gcnt, *goff;
+        if ((rc = dmalloc(ctx, &gcnt, F + 1))) return rc;
+        if ((rc = dmalloc(ctx, &goff, F + 1))) return rc;
+        if ((rc = dmalloc(ctx, &sc->face_grid, F))) return rc;
+        const double h = fmax((double)sc->scene_extent, 1e-3) / 96.0;
+        RISRT_KERNEL(ctx, "k_face_grid", (k_face_grid<<<nblk(F + 1, 128), 128, 0, s>>>(sc->faces, sc->face_tris, sc->tri_verts,
+                                                                                    F, h, sc->face_grid, gcnt)));
+        RISRT_CUDA(ctx, exclusive_scan_i64(gcnt, goff, F + 1, tmp, s));
+        int64_t n_cells = 0;
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_cells, goff + F, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        sc->n_cells = n_cells;
+        if ((rc = dmalloc(ctx, &sc->cell_face, n_cells > 0 ? n_cells : 1))) return rc;
+        RISRT_KERNEL(ctx, "k_cell_face", (k_cell_face<<<F, 256, 0, s>>>(sc->face_grid, goff, F, sc->cell_face)));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        cudaFree(gcnt);
+        cudaFree(goff);
+    }
 
     RISRT_CUDA(ctx, cudaMemcpyAsync(sc->tri_leaf, leaf_of_orig, sizeof(int) * nt, cudaMemcpyDeviceToDevice, s));
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));

@@ -669,14 +669,221 @@ __global__ void k_cand_points(const float* __restrict__ dst_xyz, const SeqEntry*
     const SeqEntry e = seqs[si];
     const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
     const float sR = dot(xyz(e.pL), R) - e.pL.w;
-    const float3 P = R + (xyz(e.sL) - R) * (sR / (sR + e.sL.w));
+    const float den = sR + e.sL.w;
+    const float t = sR / den;
+    const float3 d = xyz(e.sL) - R;
+    const float3 P = R + d * t;
+    // first-order bound on |P - P_exact| from the FP32 roundings of the inputs (images, planes and
+    // signed distances are FP32 copies of FP64 values) and of these operations, doubled
+    const float eps = 5.9604645e-8f;
+    auto l1 = [](float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); };
+    const float mag = l1(R) + l1(xyz(e.sL)) + fabsf(e.pL.w);
+    const float e_s = 8.f * eps * mag;
+    const float e_den = e_s + 2.f * eps * fabsf(e.sL.w) + eps * fabsf(den);
+    const float e_t = (e_s + fabsf(t) * e_den) / fabsf(den) + 2.f * eps * fabsf(t);
+    const float errP = l1(d) * e_t + (fabsf(t) + 1.f) * 4.f * eps * mag;
     float3 P1 = P;
+    float errP1 = errP;
     if (e.info.w == 2) {
         const float s1P = dot(xyz(e.p1), P) - e.p1.w;
-        P1 = P + (xyz(e.s1) - P) * (s1P / (s1P + e.s1.w));
+        const float den1 = s1P + e.s1.w;
+        const float t1 = s1P / den1;
+        const float3 d1 = xyz(e.s1) - P;
+        P1 = P + d1 * t1;
+        const float mag1 = l1(P) + l1(xyz(e.s1)) + fabsf(e.p1.w);
+        const float e_s1 = l1(xyz(e.p1)) * errP + 8.f * eps * mag1;
+        const float e_den1 = e_s1 + 2.f * eps * fabsf(e.s1.w) + eps * fabsf(den1);
+        const float e_t1 = (e_s1 + fabsf(t1) * e_den1) / fabsf(den1) + 2.f * eps * fabsf(t1);
+        errP1 = errP + l1(d1) * e_t1 + fabsf(t1) * (errP + 4.f * eps * l1(xyz(e.s1))) + 4.f * eps * mag1;
     }
-    pts[2 * i] = make_float4(P.x, P.y, P.z, 0.f);
-    pts[2 * i + 1] = make_float4(P1.x, P1.y, P1.z, 0.f);
+    pts[2 * i] = make_float4(P.x, P.y, P.z, 2.f * errP);
+    pts[2 * i + 1] = make_float4(P1.x, P1.y, P1.z, 2.f * errP1);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Visibility maps from a fixed source S (the RIS centre for the Rx leg, the Tx for environment
+// paths): every path's first segment runs from S to its first reflection point on face f1. Per cell
+// of f1's grid, enlarged by kMapDelta, the pyramid from S through the cell contains all those
+// segments; 1 = no triangle (other than of src_face and f1) can meet the pyramid, so every such
+// segment is unblocked; 2 = one triangle meets every ray of the pyramid inside it, at least
+// kSegEps + margin from both ends, so every such segment is blocked; 0 = undecided (traverse). The
+// walk stops at the first triangle that may meet the pyramid: it either covers the whole pyramid
+// (2) or leaves the cell undecided, which bounds the work per cell.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool box_outside(float4 lo, float4 hi, float3 n, float3 q, float m)
+{
+    const float3 c = f3(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z));
+    const float3 h = f3(0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z));
+    return dot(n, c - q) - (fabsf(n.x) * h.x + fabsf(n.y) * h.y + fabsf(n.z) * h.z) > m;
+}
+
+// Does triangle (V0, V1, V2) meet every ray S -> C_k (k < 4) of the pyramid inside itself, by at
+// least m from its edges, with hit parameters t such that t D and (1 - t) D stay above kSegEps + m,
+// D the distance of S to the cell's plane? Then, by convexity of the central projection of the cell,
+// it blocks every segment from S to a point of the cell. FP32: m is far above its rounding.
+__device__ bool tri_covers(const float3* C, float3 Sf, const TriVerts& tv, float D, float m)
+{
+    const float3 V[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
+    float3 nT = cross(V[1] - V[0], V[2] - V[0]);
+    const float nn2 = dot(nT, nT);
+    if (!(nn2 > 0.f)) return false;
+    nT = nT * rsqrtf(nn2);
+    float tmin = 3e38f, tmax = -3e38f, sgn = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        const float3 dk = C[k] - Sf;
+        const float den = dot(nT, dk);
+        if (fabsf(den) <= 1e-3f * sqrtf(dot(dk, dk))) return false;
+        if (sgn != 0.f && (den > 0.f) != (sgn > 0.f)) return false;
+        sgn = den;
+        const float t = dot(nT, V[0] - Sf) / den;
+        tmin = fminf(tmin, t);
+        tmax = fmaxf(tmax, t);
+        const float3 X = Sf + dk * t;
+        for (int e = 0; e < 3; ++e) {
+            const float3 ed = V[(e + 1) % 3] - V[e];
+            if (dot(cross(ed, X - V[e]), nT) < m * sqrtf(dot(ed, ed))) return false;
+        }
+    }
+    return tmin * D >= kSegEps + m && (1.f - tmax) * D >= kSegEps + m;
+}
+
+// The same for a face with a convex outline (one triangle or a convex two-triangle quad): every ray
+// S -> C_k meets the face plane inside the outline by at least m, so every segment from S to the
+// cell meets one of the face's triangles (the outline is their union).
+__device__ bool face_covers(const DeviceScene& S, int ft, const float3* C, float3 Sf, float D, float m)
+{
+    const FaceTest ot = S.face_test[ft];
+    if (ot.n == 0) return false;
+    const float4 pl = S.faces[ft].plane32;
+    const float3 nT = xyz(pl);
+    float tmin = 3e38f, tmax = -3e38f, sgn = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        const float3 dk = C[k] - Sf;
+        const float den = dot(nT, dk);
+        if (fabsf(den) <= 1e-3f * sqrtf(dot(dk, dk))) return false;
+        if (sgn != 0.f && (den > 0.f) != (sgn > 0.f)) return false;
+        sgn = den;
+        const float t = (pl.w - dot(nT, Sf)) / den;
+        tmin = fminf(tmin, t);
+        tmax = fmaxf(tmax, t);
+        const float3 X = Sf + dk * t;
+        for (int i = 0; i < ot.n; ++i)
+            if (dot(xyz(ot.e[i]), X) - ot.e[i].w < m) return false;
+    }
+    return tmin * D >= kSegEps + m && (1.f - tmax) * D >= kSegEps + m;
+}
+
+constexpr int kMapLeafBudget = 8;    // triangles that may meet a cell's pyramid examined before giving up
+#ifndef RISRT_MAP_NODE_BUDGET
+#define RISRT_MAP_NODE_BUDGET 64     // BVH nodes visited per cell before giving up (measured: bounds the slowest cells)
+#endif
+
+__global__ void __launch_bounds__(128) k_src_map(DeviceScene S, d3 src, int src_face, float margin, uint8_t* __restrict__ map)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= S.n_cells) return;
+    const int f = S.cell_face[c];
+    const FaceGrid g = S.face_grid[f];
+    const int idx = (int)(c - g.off);
+    const int ci = idx / g.nv, cj = idx % g.nv;
+    const Face fc = S.faces[f];
+    const double sd = dot(ld3(fc.plane), src) - fc.plane.w;   // signed distance of S to the face plane
+    uint8_t state = 0;
+    if (fabs(sd) > 1e-2 && fc.tri_end > fc.tri_begin && S.root != kNoRoot && f != src_face) {
+        const float3 o = xyz(g.o), u = xyz(g.u), v = xyz(g.v);
+        const float a0 = g.u.w + ci * g.o.w - kMapDelta, a1 = g.u.w + (ci + 1) * g.o.w + kMapDelta;
+        const float b0 = g.v.w + cj * g.dv - kMapDelta, b1 = g.v.w + (cj + 1) * g.dv + kMapDelta;
+        const float3 C[4] = {o + u * a0 + v * b0, o + u * a1 + v * b0, o + u * a1 + v * b1, o + u * a0 + v * b1};
+        const float3 Sf = to_f(src);
+        // the pyramid's planes, outside = positive side: four through S, the fifth the face plane
+        float3 pn[5];
+        for (int k = 0; k < 4; ++k) {
+            float3 n = cross(C[k] - Sf, C[(k + 1) % 4] - Sf);
+            n = n * rsqrtf(fmaxf(dot(n, n), 1e-30f));
+            if (dot(n, C[(k + 2) % 4] - Sf) > 0.f) n = n * -1.f;
+            pn[k] = n;
+        }
+        pn[4] = sd > 0.0 ? f3(-(float)fc.plane.x, -(float)fc.plane.y, -(float)fc.plane.z)
+                         : f3((float)fc.plane.x, (float)fc.plane.y, (float)fc.plane.z);
+        auto pq = [&](int k) { return k < 4 ? Sf : C[0]; };
+        const float D = (float)fabs(sd);
+        const int g0 = src_face >= 0 ? src_face : -3, g1 = f;
+        bool mixed = false, covered = false;
+        int budget = 0, visits = 0;
+        // children entered first along the cell's centre ray are visited first (nearer occluders)
+        const float3 cdir = (C[0] + C[2]) * 0.5f - Sf;
+        const float3 cinv = f3(safe_inv(cdir.x), safe_inv(cdir.y), safe_inv(cdir.z));
+        int stack[64];
+        int sp = 0;
+        int cur = S.root;
+        while (true) {
+            if (cur < 0) {
+                const int L = ~cur;
+                const int ft = S.tri_face[L];
+                if (ft != src_face && ft != f) {
+                    const TriVerts tv = S.tri_verts[L];
+                    const float3 V[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
+                    bool sep = false;
+                    for (int k = 0; k < 5 && !sep; ++k) {
+                        const float3 q = pq(k);
+                        sep = dot(pn[k], V[0] - q) > margin && dot(pn[k], V[1] - q) > margin && dot(pn[k], V[2] - q) > margin;
+                    }
+                    if (!sep) {                 // the pyramid's five corners on one side of the triangle's plane
+                        float3 nT = cross(V[1] - V[0], V[2] - V[0]);
+                        nT = nT * rsqrtf(fmaxf(dot(nT, nT), 1e-30f));
+                        const float s0 = dot(nT, Sf - V[0]);
+                        bool pos = s0 > margin, neg = s0 < -margin;
+                        for (int k = 0; k < 4; ++k) {
+                            const float sk = dot(nT, C[k] - V[0]);
+                            pos = pos && sk > margin;
+                            neg = neg && sk < -margin;
+                        }
+                        sep = pos || neg;
+                    }
+                    if (!sep) {             // a covering face decides; a few misses leave the cell undecided
+                        mixed = true;
+                        covered = face_covers(S, ft, C, Sf, D, margin) || tri_covers(C, Sf, tv, D, margin);
+                        if (covered || ++budget >= kMapLeafBudget) break;
+                    }
+                }
+                if (sp == 0) break;
+                cur = stack[--sp];
+                continue;
+            }
+            if (++visits > RISRT_MAP_NODE_BUDGET) {
+                mixed = true;
+                covered = false;
+                break;
+            }
+            const BvhNode nd = S.nodes[cur];
+            const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
+            const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
+            bool hl = fl != g0 && fl != g1, hr = fr != g0 && fr != g1;
+            for (int k = 0; k < 5; ++k) {
+                hl = hl && !box_outside(nd.l_lo, nd.l_hi, pn[k], pq(k), margin);
+                hr = hr && !box_outside(nd.r_lo, nd.r_hi, pn[k], pq(k), margin);
+            }
+            if (hl && hr) {
+                if (sp >= 64) {                 // never expected; the cell stays undecided
+                    mixed = true;
+                    covered = false;
+                    break;
+                }
+                const bool lfirst = box_entry(nd.l_lo, nd.l_hi, Sf, cinv) <= box_entry(nd.r_lo, nd.r_hi, Sf, cinv);
+                stack[sp++] = lfirst ? cr : cl;
+                cur = lfirst ? cl : cr;
+            } else if (hl) {
+                cur = cl;
+            } else if (hr) {
+                cur = cr;
+            } else {
+                if (sp == 0) break;
+                cur = stack[--sp];
+            }
+        }
+        state = covered ? 2 : (mixed ? 0 : 1);
+    }
+    map[c] = state;
 }
 
 // Occlusion of every segment of every candidate (segments in propagation order, early exit on the
@@ -706,7 +913,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
            const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const float4* __restrict__ dpts,
            long long total, unsigned long long* __restrict__ next, float tol_base, unsigned long long* refines,
            int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx,
-           RefineQ rq)
+           RefineQ rq, const uint8_t* __restrict__ smap)
 {
     const float3 srcf = to_f(src);
     const unsigned FULL = 0xffffffffu;
@@ -745,6 +952,22 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         } else {
             cur = S.root == kNoRoot ? kNone : S.root;
             sp = 0;
+            if (j == 0 && smap) {       // first segment: the source's visibility map of face f1
+                const float4 q1 = dpts[2 * item + 1];
+                if (q1.w <= 0.5f * kMapDelta) {
+                    const FaceGrid g = S.face_grid[info.x];
+                    const float3 dq = xyz(q1) - xyz(g.o);
+                    const float fa = floorf((dot(dq, xyz(g.u)) - g.u.w) / g.o.w);
+                    const float fb = floorf((dot(dq, xyz(g.v)) - g.v.w) / g.dv);
+                    if (fa >= 0.f && fa < (float)g.nu && fb >= 0.f && fb < (float)g.nv) {
+                        const uint8_t st = smap[g.off + (int)fa * g.nv + (int)fb];
+                        if (st != 0) {
+                            cur = kNone;
+                            blocked = st == 2;
+                        }
+                    }
+                }
+            }
         }
         ++tc.segs;
     };
@@ -1494,6 +1717,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             unsigned* sp_mask;       // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
             int4* rq;                // deferred FP64 settlements (candidates, then validation)
             unsigned* rq_cnt;
+            uint8_t* smap[2];        // visibility maps of the face cells from the Tx and from the RIS centre
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -1537,6 +1761,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.sp_mask = A.get<unsigned>((size_t)n_super * ((n_ids_max + 31) / 32 + 1));
             L.rq = A.get<int4>((size_t)rq_cap);
             L.rq_cnt = A.get<unsigned>(2);
+            for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
         };
         Arena measure;
         Layout Lm;
@@ -1596,6 +1821,16 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             if ((rc = build_occ_lists(ctx, S, sc->n_tris, Cpos, L.occ_cnt[1], L.occ_off64[1], L.occ_off[1],
                                       L.occ_cursor[1], scan_tmp, &ps->occ_idx[1], &ps->occ_cap[1], &occ_off_src[1])))
                 return rc;
+
+        // visibility maps of the face cells from the Tx (environment paths) and the RIS centre (Rx leg)
+        if (sc->n_cells > 0 && n_rx > 1) {
+            const float mg = 1e-4f * (1.f + ext);
+            if (max_env > 0)
+                RISRT_KERNEL(ctx, "k_src_map", (k_src_map<<<nblk(sc->n_cells, 128), 128, 0, s>>>(S, Tpos, -1, mg, L.smap[0])));
+            if (max_rx > 0)
+                RISRT_KERNEL(ctx, "k_src_map", (k_src_map<<<nblk(sc->n_cells, 128), 128, 0, s>>>(S, Cpos, ris->host_face, mg,
+                                                                                               L.smap[1])));
+        }
 
         // receivers in Morton order for the candidate search
         {
@@ -1688,7 +1923,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                         S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
                                                         vs, L.dense_pts, total, counters + 6, tol_base, counters, flags_dev + 1,
-                                                        counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq)));
+                                                        counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq,
+                                                        n_dst > 1 && sc->n_cells > 0 ? L.smap[occ] : nullptr)));
                     RISRT_KERNEL(ctx, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, s>>>(
                                                           S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
                 }
@@ -1954,7 +2190,8 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                 S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
                                                 L.dense_slot, L.dense_pts, total, L.counters + 6, tol_base, L.counters,
-                                                L.flags + 1, L.counters + 2, nullptr, nullptr, RefineQ{nullptr, 0, nullptr})));
+                                                L.flags + 1, L.counters + 2, nullptr, nullptr, RefineQ{nullptr, 0, nullptr},
+                                                nullptr)));
         }
         const size_t shm = sizeof(int) * (size_t)cap;
         cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
