@@ -7,50 +7,6 @@
 
 namespace risrt {
 
-struct cd { double re, im; };
-__device__ __forceinline__ cd cmul(cd a, cd b) { return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ __forceinline__ cd cadd(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cd cdiv(cd a, cd b)
-{
-    double den = b.re * b.re + b.im * b.im;
-    return cd{(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
-}
-// principal square root, numerically stable in both half planes
-__device__ __forceinline__ cd csqrt_d(cd z)
-{
-    double r = hypot(z.re, z.im);
-    if (r == 0.0) return cd{0.0, 0.0};
-    if (z.re >= 0.0) {
-        double s = sqrt(0.5 * (r + z.re));
-        return cd{s, z.im / (2.0 * s)};
-    }
-    double s = copysign(sqrt(0.5 * (r - z.re)), z.im);
-    return cd{z.im / (2.0 * s), s};
-}
-
-// Fresnel coefficient (Collin) for complex permittivity eps at incidence cos_i; TE or TM.
-__device__ __forceinline__ cd fresnel_d(double cos_i, cd eps, bool tm)
-{
-    double s2 = 1.0 - cos_i * cos_i;
-    cd root = csqrt_d(cd{eps.re - s2, eps.im});
-    if (!tm) return cdiv(cd{cos_i - root.re, -root.im}, cd{cos_i + root.re, root.im});
-    cd ec = cd{eps.re * cos_i, eps.im * cos_i};
-    return cdiv(cd{ec.re - root.re, ec.im - root.im}, cd{ec.re + root.re, ec.im + root.im});
-}
-
-// Antenna pattern F(cos theta) in FP64 (Sec. III-B): isotropic, cos^(G/2-1), quarter-wave monopole.
-__device__ __forceinline__ double pattern_d(int pat, double gain, double c)
-{
-    if (pat == RISRT_PATTERN_COS_POW) return c > 0.0 ? pow(c, 0.5 * gain - 1.0) : 0.0;
-    if (pat == RISRT_PATTERN_MONOPOLE_QW) {
-        double s2 = 1.0 - c * c;
-        if (s2 <= 0.0) return 0.0;
-        double v = (cospi(0.5 * c) - cospi(0.5)) / sqrt(s2);
-        return v * v;
-    }
-    return 1.0;
-}
-
 __device__ __forceinline__ d3 ld3(const dv4& p) { return D3(p.x, p.y, p.z); }
 __device__ __forceinline__ d3 ldv(const float4& p) { return D3((double)p.x, (double)p.y, (double)p.z); }
 

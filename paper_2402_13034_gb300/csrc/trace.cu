@@ -52,40 +52,43 @@ __device__ __forceinline__ bool contains_point(const Face& a, d3 p) { return fab
 // through f1 (the union over f1's triangles of the trihedral cones with apex S1). Returns false only
 // when every vertex of f2 is separated by more than 1e-9 m, so no destination can make the sequence
 // valid; the test is independent of the receiver.
-__device__ bool beam_reaches(const DeviceScene& S, d3 src, int f1, int f2)
+// Can a path from src reflect on f1 and then reach face f2? f2 must have a point in front of f1 (on
+// the source side) and inside the beam from the image S1 of src through f1. Decided in FP32 with a
+// margin far above its rounding: a sequence is dropped only when the separation is certain (every
+// vertex of f2 behind f1, or outside one side plane of each of f1's triangles, by more than m);
+// sequences kept in doubt are settled exactly by the candidate tests later.
+__device__ bool beam_reaches(const DeviceScene& S, d3 src, int f1, int f2, float m)
 {
     const Face F1 = S.faces[f1], F2 = S.faces[f2];
-    const d3 n1 = ld3(F1.plane);
-    const double s0 = dot(n1, src) - F1.plane.w;
-    const double sgn = s0 > 0 ? 1.0 : -1.0;
-    const double tol = 1e-9;
-    // strictly on the source side of f1
+    const float3 n1 = xyz(F1.plane32);
+    const float s0 = dot(n1, to_f(src)) - F1.plane32.w;
+    const float sgn = s0 > 0.f ? 1.f : -1.f;
     bool any_front = false;
     for (int j = F2.tri_begin; j < F2.tri_end && !any_front; ++j) {
         const TriVerts tv = S.tri_verts[S.face_tris[j]];
-        const d3 v[3] = {ldv(tv.v0), ldv(tv.v1), ldv(tv.v2)};
+        const float3 v[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
         for (int i = 0; i < 3; ++i)
-            if (sgn * (dot(n1, v[i]) - F1.plane.w) > tol) any_front = true;
+            if (sgn * (dot(n1, v[i]) - F1.plane32.w) > -m) any_front = true;
     }
     if (!any_front) return false;
-    const d3 S1 = mirror_pt(src, n1, F1.plane.w);
+    const float3 S1 = to_f(mirror_pt(src, ld3(F1.plane), F1.plane.w));
     for (int a = F1.tri_begin; a < F1.tri_end; ++a) {
         const TriVerts ta = S.tri_verts[S.face_tris[a]];
-        const d3 P[3] = {ldv(ta.v0), ldv(ta.v1), ldv(ta.v2)};
+        const float3 P[3] = {xyz(ta.v0), xyz(ta.v1), xyz(ta.v2)};
         bool separated = false;
         for (int e = 0; e < 3 && !separated; ++e) {
-            const d3 p = P[e], q = P[(e + 1) % 3], r = P[(e + 2) % 3];
-            d3 nn = cross(p - S1, q - S1);
-            const double len = norm(nn);
-            if (len == 0.0) continue;
-            nn = nn * (1.0 / len);
-            if (dot(nn, r - S1) < 0) nn = nn * -1.0;
+            const float3 p = P[e], q = P[(e + 1) % 3], r = P[(e + 2) % 3];
+            float3 nn = cross(p - S1, q - S1);
+            const float l2 = dot(nn, nn);
+            if (!(l2 > 0.f)) continue;
+            nn = nn * rsqrtf(l2);
+            if (dot(nn, r - S1) < 0.f) nn = nn * -1.f;
             bool all_out = true;
             for (int j = F2.tri_begin; j < F2.tri_end && all_out; ++j) {
                 const TriVerts tv = S.tri_verts[S.face_tris[j]];
-                const d3 v[3] = {ldv(tv.v0), ldv(tv.v1), ldv(tv.v2)};
+                const float3 v[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
                 for (int i = 0; i < 3; ++i)
-                    if (dot(nn, v[i] - S1) >= -tol) all_out = false;
+                    if (dot(nn, v[i] - S1) >= -m) all_out = false;
             }
             separated = all_out;
         }
@@ -97,7 +100,8 @@ __device__ bool beam_reaches(const DeviceScene& S, d3 src, int f1, int f2)
 // mode 0: Tx leg (last face may not contain the RIS centre); 1: Rx leg (first face may not);
 // 2: Tx -> Rx environment paths. Order-2 sequences whose second face is outside the beam of the
 // first are dropped (beam_reaches).
-__global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, d3 src, int64_t* __restrict__ flag)
+__global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, d3 src, float margin,
+                              int64_t* __restrict__ flag)
 {
     int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (id >= n_ids) return;
@@ -115,7 +119,7 @@ __global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, 
     d3 c = fr_c(fr);
     if (mode == 0 && contains_point(S.faces[k == 2 ? f2 : f1], c)) ok = false;
     if (mode == 1 && contains_point(S.faces[f1], c)) ok = false;
-    if (ok && k == 2 && fabs(dot(ld3(S.faces[f1].plane), src) - S.faces[f1].plane.w) > 0.0 && !beam_reaches(S, src, f1, f2))
+    if (ok && k == 2 && fabs(dot(ld3(S.faces[f1].plane), src) - S.faces[f1].plane.w) > 0.0 && !beam_reaches(S, src, f1, f2, margin))
         ok = false;
     flag[id] = ok ? 1 : 0;
 }
@@ -1190,76 +1194,85 @@ struct WaveD {
     int tm;
 };
 
-__device__ __forceinline__ cd mat_eps(const DeviceScene& S, int face, const WaveD& wv)
-{
-    float2 m = S.mats[S.faces[face].mat];
-    return cd{(double)m.x, -(double)m.y / (wv.omega * kEps0)};
-}
 
-// Unfolded-leg quantities from a source image Ts to point X: length, departure direction of the
-// real first segment (mirrors applied back), Fresnel product. faces[0..k-1] in propagation order.
-__device__ __forceinline__ void unfolded_from_source(const DeviceScene& S, d3 Ts, d3 X, const int* fa, int k,
-                                                     const WaveD& wv, double* L, d3* dep, d3* arr, cd* R)
-{
-    d3 d = X - Ts;
-    *L = norm(d);
-    d = d * (1.0 / *L);
-    *arr = d;                      // the last segment is real in this unfolding
-    cd Rp = cd{1.0, 0.0};
-    // last bounce plane is real; earlier planes are mirrored across the later ones
-    if (k >= 1) {
-        d3 nl = ld3(S.faces[fa[k - 1]].plane);
-        Rp = cmul(Rp, fresnel_d(fabs(dot(d, nl)), mat_eps(S, fa[k - 1], wv), wv.tm));
-        if (k == 2) {
-            d3 n1 = mirror_dir(ld3(S.faces[fa[0]].plane), nl);
-            Rp = cmul(Rp, fresnel_d(fabs(dot(d, n1)), mat_eps(S, fa[0], wv), wv.tm));
-        }
-    }
-    d3 dd = d;                     // real first-segment direction: L_f1 L_f2 d
-    for (int j = k - 1; j >= 0; --j) dd = mirror_dir(dd, ld3(S.faces[fa[j]].plane));
-    *dep = dd;
-    *R = Rp;
-}
 
+// FP32 face data for the per-path terms: unit normal and complex permittivity of the face's material.
+__device__ __forceinline__ float3 face_n32(const DeviceScene& S, int f)
+{
+    const float4 p = S.faces[f].plane32;
+    return f3(p.x, p.y, p.z);
+}
+__device__ __forceinline__ float2 face_eps32(const DeviceScene& S, int f, const WaveD& wv)
+{
+    const float2 m = S.mats[S.faces[f].mat];
+    return make_float2(m.x, -m.y * wv.inv_we);
+}
+__device__ __forceinline__ float3 mirror_dir_f(float3 v, float3 n) { return v - n * (2.f * dot(n, v)); }
+
+// One warp per element, lanes over its Tx-leg paths (LOS first): FP64 for the unfolded length L and
+// frac(L / lambda), FP32 for directions, Fresnel products and patterns (they enter amplitudes only);
+// fixed reduction order (lane-strided paths, shuffle tree).
 __global__ void k_cm(DeviceScene S, const float4* __restrict__ elem, int M, Frame fr, AntD tx, WaveD wv, double K,
                      const uint8_t* __restrict__ tx_vis, const int* __restrict__ tx_seq, int n_tx,
                      const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, float2* __restrict__ cm)
 {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int m = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (m >= M) return;
-    d3 e = elem_pos(fr, elem[m]);
-    d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
-    d3 z = D3(tx.z[0], tx.z[1], tx.z[2]);
-    d3 n = fr_n(fr);
-    cd acc = cd{0.0, 0.0};
-    for (int p = -1; p < n_tx; ++p) {
+    const d3 e = elem_pos(fr, elem[m]);
+    const d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
+    const float3 z = f3((float)tx.z[0], (float)tx.z[1], (float)tx.z[2]);
+    const float3 nr = f3((float)fr.n[0], (float)fr.n[1], (float)fr.n[2]);
+    const float gt = (float)tx.gain;
+    const float amp0 = (float)sqrt(2.0 * kEta0 * tx.power * tx.gain);
+    float are = 0.f, aim = 0.f;
+    for (int p = lane - 1; p < n_tx; p += 32) {
         d3 Ts = T;
         int fa[2] = {-1, -1};
         int k = 0;
         if (p < 0) {
             if (!tx_vis[m]) continue;
         } else {
-            int si = tx_seq[p];
-            int4 info = seqs[si].info;
+            const int si = tx_seq[p];
+            const int4 info = seqs[si].info;
             k = info.w;
             fa[0] = info.x;
             fa[1] = info.y;
             Ts = k == 2 ? ld3(seqd[si].S2) : ld3(seqd[si].S1);
         }
-        double L;
-        d3 dep, arr;
-        cd R;
-        unfolded_from_source(S, Ts, e, fa, k, wv, &L, &dep, &arr, &R);
-        double Ft = pattern_d(tx.pattern, tx.gain, dot(dep, z));
-        double cin = -dot(arr, n);
-        double Fin = cin > 0.0 ? cin : 0.0;
-        double amp = sqrt(2.0 * kEta0 * tx.power * tx.gain * Ft) * sqrt(Fin) / L;
-        double ph = -2.0 * kPi * (L / wv.lam - floor(L / wv.lam));
-        double sn, cs;
-        sincos(ph, &sn, &cs);
-        acc = cadd(acc, cmul(R, cd{amp * cs, amp * sn}));
+        const d3 d = e - Ts;
+        const double L = sqrt(dot(d, d));
+        const double x = L * wv.inv_lam;
+        const float ph = (float)(x - floor(x));
+        float3 u = to_f(d);                       // arrival direction at the element: the last segment is real
+        u = u * rsqrtf(dot(u, u));
+        cf Rp = cf{1.f, 0.f};
+        if (k >= 1) {
+            const float3 nl = face_n32(S, fa[k - 1]);
+            const float2 el = face_eps32(S, fa[k - 1], wv);
+            Rp = fresnel_f(fabsf(dot(u, nl)), el.x, el.y, wv.tm);
+            if (k == 2) {
+                const float3 n1 = mirror_dir_f(face_n32(S, fa[0]), nl);
+                const float2 e1 = face_eps32(S, fa[0], wv);
+                Rp = cmulf(Rp, fresnel_f(fabsf(dot(u, n1)), e1.x, e1.y, wv.tm));
+            }
+        }
+        float3 dep = u;
+        for (int j = k - 1; j >= 0; --j) dep = mirror_dir_f(dep, face_n32(S, fa[j]));
+        const float Ft = pattern_f(tx.pattern, gt, dot(dep, z));
+        const float Fin = fmaxf(-dot(u, nr), 0.f);  // element pattern max(cos, 0) toward the Tx side
+        const float amp = amp0 * sqrtf(Ft * Fin) / (float)L;
+        float sn, cs;
+        sincospif(2.f * ph, &sn, &cs);            // e^{-j 2 pi frac(L / lambda)}
+        const cf t = cmulf(Rp, cf{amp * cs, -amp * sn});
+        are += t.re;
+        aim += t.im;
     }
-    cm[m] = make_float2((float)(K * acc.re), (float)(K * acc.im));
+    for (int o = 16; o > 0; o >>= 1) {
+        are += __shfl_down_sync(0xffffffffu, are, o);
+        aim += __shfl_down_sync(0xffffffffu, aim, o);
+    }
+    if (lane == 0) cm[m] = make_float2((float)(K * are), (float)(K * aim));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1276,18 +1289,6 @@ __device__ __forceinline__ float4 local4(const Frame& fr, d3 v, float w)
     return make_float4((float)dot(v, fr_t1(fr)), (float)dot(v, fr_t2(fr)), (float)dot(v, fr_n(fr)), w);
 }
 
-// FP32 face data for the per-path terms: unit normal and complex permittivity of the face's material.
-__device__ __forceinline__ float3 face_n32(const DeviceScene& S, int f)
-{
-    const float4 p = S.faces[f].plane32;
-    return f3(p.x, p.y, p.z);
-}
-__device__ __forceinline__ float2 face_eps32(const DeviceScene& S, int f, const WaveD& wv)
-{
-    const float2 m = S.mats[S.faces[f].mat];
-    return make_float2(m.x, -m.y * wv.inv_we);
-}
-__device__ __forceinline__ float3 mirror_dir_f(float3 v, float3 n) { return v - n * (2.f * dot(n, v)); }
 
 // Per (Rx, path) record for the field kernel. FP64 only where the phase needs it: the receiver image
 // I (mirrored through the bounce planes in reverse order), w = I - c in the RIS frame, D0 = |w| and
@@ -1799,7 +1800,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             tab[i].n = 0;
             int64_t nid = n_ids_of[i];
             if (nid == 0) continue;
-            RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, src_of[i], flag)));
+            RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, src_of[i], 1e-4f * (1.f + ext), flag)));
             RISRT_CUDA(ctx, exclusive_scan_i64(flag, pos, nid, scan_tmp, s));
             RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(nid, 256), 256, 0, s>>>(S, nid, flag, pos, src_of[i], tab[i].e, tab[i].d)));
             int64_t n_allowed = 0;
@@ -1978,7 +1979,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         for (int i = 0; i < n_tx; ++i) ps->tx_seq_host[i] = tx_entries[i].info.z;
 
         // c_m
-        RISRT_KERNEL(ctx, "k_cm", (k_cm<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand, n_tx, tab[0].e, tab[0].d, ps->cm)));
+        RISRT_KERNEL(ctx, "k_cm", (k_cm<<<nblk((int64_t)M * 32, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand, n_tx, tab[0].e, tab[0].d, ps->cm)));
 
         // Rx-leg offsets and records
         RISRT_KERNEL(ctx, "k_count_total", (k_count_total<<<nblk(n_rx, 256), 256, 0, s>>>(crx.cnt64, n_rx, tot)));
@@ -2152,7 +2153,7 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
 
     int n_seq = 0;
     if (n_ids > 0) {
-        RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(n_ids, 256), 256, 0, s>>>(S, n_ids, 0, fr, src, L.flag)));
+        RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(n_ids, 256), 256, 0, s>>>(S, n_ids, 0, fr, src, 1e-4f * (1.f + ext), L.flag)));
         RISRT_CUDA(ctx, exclusive_scan_i64(L.flag, L.pos, n_ids, L.scan_tmp, s));
         RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(n_ids, 256), 256, 0, s>>>(S, n_ids, L.flag, L.pos, src, L.e, L.d)));
         int64_t last[2];
