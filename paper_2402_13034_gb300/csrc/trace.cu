@@ -782,6 +782,102 @@ constexpr int kMapLeafBudget = 8;    // triangles that may meet a cell's pyramid
 #define RISRT_MAP_NODE_BUDGET 64     // BVH nodes visited per cell before giving up (measured: bounds the slowest cells)
 #endif
 
+// Classify the pyramid with apex A and base quad C[0..3] (a convex quad on a plane with unit normal
+// nb pointing away from A, at distance D from A), ignoring triangles of faces ig0 and ig1: 1 = no
+// triangle can meet it, 2 = one face (or triangle) meets every ray from A to the base with the
+// margins of face_covers / tri_covers, 0 = undecided. The walk visits children entered first along
+// the centre ray first and gives up after kMapLeafBudget candidate triangles or
+// RISRT_MAP_NODE_BUDGET nodes.
+__device__ uint8_t classify_pyramid(const DeviceScene& S, float3 A, const float3* C, float3 nb, float D, int ig0, int ig1,
+                                    float margin)
+{
+    if (S.root == kNoRoot) return 1;
+    // the pyramid's planes, outside = positive side: four through A, the fifth the base plane
+    float3 pn[5];
+    for (int k = 0; k < 4; ++k) {
+        float3 n = cross(C[k] - A, C[(k + 1) % 4] - A);
+        n = n * rsqrtf(fmaxf(dot(n, n), 1e-30f));
+        if (dot(n, C[(k + 2) % 4] - A) > 0.f) n = n * -1.f;
+        pn[k] = n;
+    }
+    pn[4] = nb;
+    auto pq = [&](int k) { return k < 4 ? A : C[0]; };
+    const int g0 = ig0 >= 0 ? ig0 : -3, g1 = ig1 >= 0 ? ig1 : -3;
+    bool mixed = false, covered = false;
+    int budget = 0, visits = 0;
+    const float3 cdir = (C[0] + C[2]) * 0.5f - A;
+    const float3 cinv = f3(safe_inv(cdir.x), safe_inv(cdir.y), safe_inv(cdir.z));
+    int stack[64];
+    int sp = 0;
+    int cur = S.root;
+    while (true) {
+        if (cur < 0) {
+            const int L = ~cur;
+            const int ft = S.tri_face[L];
+            if (ft != ig0 && ft != ig1) {
+                const TriVerts tv = S.tri_verts[L];
+                const float3 V[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
+                bool sep = false;
+                for (int k = 0; k < 5 && !sep; ++k) {
+                    const float3 q = pq(k);
+                    sep = dot(pn[k], V[0] - q) > margin && dot(pn[k], V[1] - q) > margin && dot(pn[k], V[2] - q) > margin;
+                }
+                if (!sep) {                     // the pyramid's five corners on one side of the triangle's plane
+                    float3 nT = cross(V[1] - V[0], V[2] - V[0]);
+                    nT = nT * rsqrtf(fmaxf(dot(nT, nT), 1e-30f));
+                    const float s0 = dot(nT, A - V[0]);
+                    bool pos = s0 > margin, neg = s0 < -margin;
+                    for (int k = 0; k < 4; ++k) {
+                        const float sk = dot(nT, C[k] - V[0]);
+                        pos = pos && sk > margin;
+                        neg = neg && sk < -margin;
+                    }
+                    sep = pos || neg;
+                }
+                if (!sep) {                     // a covering face decides; a few misses leave it undecided
+                    mixed = true;
+                    covered = face_covers(S, ft, C, A, D, margin) || tri_covers(C, A, tv, D, margin);
+                    if (covered || ++budget >= kMapLeafBudget) break;
+                }
+            }
+            if (sp == 0) break;
+            cur = stack[--sp];
+            continue;
+        }
+        if (++visits > RISRT_MAP_NODE_BUDGET) {
+            mixed = true;
+            covered = false;
+            break;
+        }
+        const BvhNode nd = S.nodes[cur];
+        const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
+        const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
+        bool hl = fl != g0 && fl != g1, hr = fr != g0 && fr != g1;
+        for (int k = 0; k < 5; ++k) {
+            hl = hl && !box_outside(nd.l_lo, nd.l_hi, pn[k], pq(k), margin);
+            hr = hr && !box_outside(nd.r_lo, nd.r_hi, pn[k], pq(k), margin);
+        }
+        if (hl && hr) {
+            if (sp >= 64) {                     // never expected; undecided
+                mixed = true;
+                covered = false;
+                break;
+            }
+            const bool lfirst = box_entry(nd.l_lo, nd.l_hi, A, cinv) <= box_entry(nd.r_lo, nd.r_hi, A, cinv);
+            stack[sp++] = lfirst ? cr : cl;
+            cur = lfirst ? cl : cr;
+        } else if (hl) {
+            cur = cl;
+        } else if (hr) {
+            cur = cr;
+        } else {
+            if (sp == 0) break;
+            cur = stack[--sp];
+        }
+    }
+    return covered ? 2 : (mixed ? 0 : 1);
+}
+
 __global__ void __launch_bounds__(128) k_src_map(DeviceScene S, d3 src, int src_face, float margin, uint8_t* __restrict__ map)
 {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -793,101 +889,62 @@ __global__ void __launch_bounds__(128) k_src_map(DeviceScene S, d3 src, int src_
     const Face fc = S.faces[f];
     const double sd = dot(ld3(fc.plane), src) - fc.plane.w;   // signed distance of S to the face plane
     uint8_t state = 0;
-    if (fabs(sd) > 1e-2 && fc.tri_end > fc.tri_begin && S.root != kNoRoot && f != src_face) {
+    if (fabs(sd) > 1e-2 && fc.tri_end > fc.tri_begin && f != src_face) {
         const float3 o = xyz(g.o), u = xyz(g.u), v = xyz(g.v);
         const float a0 = g.u.w + ci * g.o.w - kMapDelta, a1 = g.u.w + (ci + 1) * g.o.w + kMapDelta;
         const float b0 = g.v.w + cj * g.dv - kMapDelta, b1 = g.v.w + (cj + 1) * g.dv + kMapDelta;
         const float3 C[4] = {o + u * a0 + v * b0, o + u * a1 + v * b0, o + u * a1 + v * b1, o + u * a0 + v * b1};
-        const float3 Sf = to_f(src);
-        // the pyramid's planes, outside = positive side: four through S, the fifth the face plane
-        float3 pn[5];
-        for (int k = 0; k < 4; ++k) {
-            float3 n = cross(C[k] - Sf, C[(k + 1) % 4] - Sf);
-            n = n * rsqrtf(fmaxf(dot(n, n), 1e-30f));
-            if (dot(n, C[(k + 2) % 4] - Sf) > 0.f) n = n * -1.f;
-            pn[k] = n;
-        }
-        pn[4] = sd > 0.0 ? f3(-(float)fc.plane.x, -(float)fc.plane.y, -(float)fc.plane.z)
-                         : f3((float)fc.plane.x, (float)fc.plane.y, (float)fc.plane.z);
-        auto pq = [&](int k) { return k < 4 ? Sf : C[0]; };
-        const float D = (float)fabs(sd);
-        const int g0 = src_face >= 0 ? src_face : -3, g1 = f;
-        bool mixed = false, covered = false;
-        int budget = 0, visits = 0;
-        // children entered first along the cell's centre ray are visited first (nearer occluders)
-        const float3 cdir = (C[0] + C[2]) * 0.5f - Sf;
-        const float3 cinv = f3(safe_inv(cdir.x), safe_inv(cdir.y), safe_inv(cdir.z));
-        int stack[64];
-        int sp = 0;
-        int cur = S.root;
-        while (true) {
-            if (cur < 0) {
-                const int L = ~cur;
-                const int ft = S.tri_face[L];
-                if (ft != src_face && ft != f) {
-                    const TriVerts tv = S.tri_verts[L];
-                    const float3 V[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
-                    bool sep = false;
-                    for (int k = 0; k < 5 && !sep; ++k) {
-                        const float3 q = pq(k);
-                        sep = dot(pn[k], V[0] - q) > margin && dot(pn[k], V[1] - q) > margin && dot(pn[k], V[2] - q) > margin;
-                    }
-                    if (!sep) {                 // the pyramid's five corners on one side of the triangle's plane
-                        float3 nT = cross(V[1] - V[0], V[2] - V[0]);
-                        nT = nT * rsqrtf(fmaxf(dot(nT, nT), 1e-30f));
-                        const float s0 = dot(nT, Sf - V[0]);
-                        bool pos = s0 > margin, neg = s0 < -margin;
-                        for (int k = 0; k < 4; ++k) {
-                            const float sk = dot(nT, C[k] - V[0]);
-                            pos = pos && sk > margin;
-                            neg = neg && sk < -margin;
-                        }
-                        sep = pos || neg;
-                    }
-                    if (!sep) {             // a covering face decides; a few misses leave the cell undecided
-                        mixed = true;
-                        covered = face_covers(S, ft, C, Sf, D, margin) || tri_covers(C, Sf, tv, D, margin);
-                        if (covered || ++budget >= kMapLeafBudget) break;
-                    }
-                }
-                if (sp == 0) break;
-                cur = stack[--sp];
-                continue;
-            }
-            if (++visits > RISRT_MAP_NODE_BUDGET) {
-                mixed = true;
-                covered = false;
-                break;
-            }
-            const BvhNode nd = S.nodes[cur];
-            const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-            const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
-            bool hl = fl != g0 && fl != g1, hr = fr != g0 && fr != g1;
-            for (int k = 0; k < 5; ++k) {
-                hl = hl && !box_outside(nd.l_lo, nd.l_hi, pn[k], pq(k), margin);
-                hr = hr && !box_outside(nd.r_lo, nd.r_hi, pn[k], pq(k), margin);
-            }
-            if (hl && hr) {
-                if (sp >= 64) {                 // never expected; the cell stays undecided
-                    mixed = true;
-                    covered = false;
-                    break;
-                }
-                const bool lfirst = box_entry(nd.l_lo, nd.l_hi, Sf, cinv) <= box_entry(nd.r_lo, nd.r_hi, Sf, cinv);
-                stack[sp++] = lfirst ? cr : cl;
-                cur = lfirst ? cl : cr;
-            } else if (hl) {
-                cur = cl;
-            } else if (hr) {
-                cur = cr;
-            } else {
-                if (sp == 0) break;
-                cur = stack[--sp];
-            }
-        }
-        state = covered ? 2 : (mixed ? 0 : 1);
+        const float3 nb = sd > 0.0 ? f3(-(float)fc.plane.x, -(float)fc.plane.y, -(float)fc.plane.z)
+                                   : f3((float)fc.plane.x, (float)fc.plane.y, (float)fc.plane.z);
+        state = classify_pyramid(S, to_f(src), C, nb, (float)fabs(sd), src_face, f, margin);
     }
     map[c] = state;
+}
+
+// Bounds (a_min, a_max, b_min, b_max) of the element centres in the RIS frame (one block).
+__global__ void k_elem_bounds(const float4* __restrict__ elem, int M, float4* __restrict__ out)
+{
+    __shared__ float4 red[256];
+    float4 b = make_float4(3e38f, -3e38f, 3e38f, -3e38f);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float4 e = elem[m];
+        b = make_float4(fminf(b.x, e.x), fmaxf(b.y, e.x), fminf(b.z, e.y), fmaxf(b.w, e.y));
+    }
+    red[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            const float4 q = red[threadIdx.x + o];
+            b = make_float4(fminf(b.x, q.x), fmaxf(b.y, q.y), fminf(b.z, q.z), fmaxf(b.w, q.w));
+            red[threadIdx.x] = b;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// Per receiver: the pyramid from R through the RIS aperture (the element centres' bounding rectangle
+// in the RIS plane, enlarged by kMapDelta) contains every element -> R segment, so its class decides
+// all of them at once (1 all visible, 2 all blocked, 0 trace each element).
+__global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, Frame fr,
+                                                     const float4* __restrict__ eb, int host_face, float margin,
+                                                     uint8_t* __restrict__ state)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rx) return;
+    const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+    const d3 c = fr_c(fr), n = fr_n(fr), t1 = fr_t1(fr), t2 = fr_t2(fr);
+    const double sd = dot(n, R - c);
+    uint8_t st = 0;
+    if (fabs(sd) > 1e-2) {
+        const float4 b = *eb;
+        const double a0 = b.x - kMapDelta, a1 = b.y + kMapDelta, b0 = b.z - kMapDelta, b1 = b.w + kMapDelta;
+        const float3 C[4] = {to_f(c + t1 * a0 + t2 * b0), to_f(c + t1 * a1 + t2 * b0), to_f(c + t1 * a1 + t2 * b1),
+                             to_f(c + t1 * a0 + t2 * b1)};
+        const float3 nb = to_f(sd > 0.0 ? n * -1.0 : n);
+        st = classify_pyramid(S, to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
+    }
+    state[r] = st;
 }
 
 // Occlusion of every segment of every candidate (segments in propagation order, early exit on the
@@ -1154,9 +1211,11 @@ __global__ void k_finalize(int* __restrict__ cand, const int* __restrict__ cand_
 // direct legs
 // ------------------------------------------------------------------------------------------------
 // e_m -> Rx visibility bits, one warp per (Rx, 32 elements): coherent rays from a small aperture.
+// Element -> receiver visibility, one warp per (receiver, 32 elements). A receiver whose aperture
+// pyramid is decided (k_rx_aperture: 1 all visible, 2 all blocked) takes that answer for every element.
 __global__ void k_direct_vis(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, const float4* __restrict__ elem,
                              int M, int W, Frame fr, int host_face, float tol_base, uint32_t* __restrict__ vis,
-                             unsigned long long* refines, int* err)
+                             unsigned long long* refines, int* err, const uint8_t* __restrict__ rx_state)
 {
     const int lane = threadIdx.x & 31;
     int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1165,10 +1224,15 @@ __global__ void k_direct_vis(DeviceScene S, const float* __restrict__ rx, int64_
     if (r >= n_rx) return;
     int m = w * 32 + lane;
     bool blocked = true;
+    const uint8_t st = rx_state ? rx_state[r] : 0;
     if (m < M) {
-        d3 e = elem_pos(fr, elem[m]);
-        d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
-        blocked = seg_blocked(S, e, R, host_face, -1, tol_base, refines, err);
+        if (st != 0) {
+            blocked = st == 2;
+        } else {
+            d3 e = elem_pos(fr, elem[m]);
+            d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+            blocked = seg_blocked(S, e, R, host_face, -1, tol_base, refines, err);
+        }
     }
     unsigned b = __ballot_sync(0xffffffffu, !blocked);
     if (lane == 0) vis[r * W + w] = b;
@@ -1719,6 +1783,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             int4* rq;                // deferred FP64 settlements (candidates, then validation)
             unsigned* rq_cnt;
             uint8_t* smap[2];        // visibility maps of the face cells from the Tx and from the RIS centre
+            float4* elem_bb;         // element centre bounds in the RIS frame
+            uint8_t* rx_state;       // per receiver: class of its RIS-aperture pyramid
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -1763,6 +1829,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.rq = A.get<int4>((size_t)rq_cap);
             L.rq_cnt = A.get<unsigned>(2);
             for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
+            L.elem_bb = A.get<float4>(1);
+            L.rx_state = A.get<uint8_t>((size_t)n_rx);
         };
         Arena measure;
         Layout Lm;
@@ -1948,8 +2016,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         // direct legs
         {
             int64_t nthreads = n_rx * W * 32;
+            RISRT_KERNEL(ctx, "k_elem_bounds", (k_elem_bounds<<<1, 256, 0, s>>>(ris->elem, M, L.elem_bb)));
+            RISRT_KERNEL(ctx, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, fr, L.elem_bb,
+                                                                                           ris->host_face, 1e-4f * (1.f + ext),
+                                                                                           L.rx_state)));
             RISRT_KERNEL(ctx, "k_direct_vis", (k_direct_vis<<<nblk(nthreads, 128), 128, 0, s>>>(S, rxp, n_rx, ris->elem, M, W, fr, ris->host_face,
-                                                             tol_base, ps->vis, counters, flags_dev + 1)));
+                                                             tol_base, ps->vis, counters, flags_dev + 1, L.rx_state)));
             RISRT_KERNEL(ctx, "k_los", (k_los<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1)));
         }
         int host_flags[2];
