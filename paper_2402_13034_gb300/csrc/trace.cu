@@ -314,16 +314,47 @@ __global__ void k_seq_cull(DeviceScene S, const SeqEntry* __restrict__ seqs, int
     }
 }
 
+// Indices of the set bits of each super-patch's sequence mask, in increasing order (one block of 256
+// threads per super-patch): list[p * stride + i] for i < cnt[p].
+__global__ void k_mask_compact(const unsigned* __restrict__ mask, int words, int64_t n_super, int64_t stride,
+                               int* __restrict__ list, int* __restrict__ cnt)
+{
+    __shared__ int part[256];
+    for (int64_t sp = blockIdx.x; sp < n_super; sp += gridDim.x) {
+        const unsigned* m = mask + sp * words;
+        const int per = (words + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+        int c = 0;
+        for (int w = w0; w < w1; ++w) c += __popc(m[w]);
+        part[threadIdx.x] = c;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scan of the per-thread counts
+            const int v = (int)threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+            __syncthreads();
+            part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        int pos = part[threadIdx.x] - c;
+        int* out = list + sp * stride;
+        for (int w = w0; w < w1; ++w)
+            for (unsigned b = m[w]; b; b &= b - 1) out[pos++] = w * 32 + __ffs(b) - 1;
+        if (threadIdx.x == blockDim.x - 1) cnt[sp] = part[threadIdx.x];
+        __syncthreads();
+    }
+}
+
 template <bool SMEM_FACES>
 __global__ void __launch_bounds__(kCandThreads)
 k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, const int* __restrict__ order, d3 src,
              const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int n_seq,
              float tol_base, int* __restrict__ cand, int* __restrict__ cand_cnt, int cap,
-             int* __restrict__ overflow, unsigned long long* __restrict__ refines, const unsigned* __restrict__ smask,
-             int words, RefineQ rq)
+             int* __restrict__ overflow, unsigned long long* __restrict__ refines, const int* __restrict__ slist,
+             const int* __restrict__ slist_cnt, int64_t slist_stride, RefineQ rq)
 {
     __shared__ SeqEntry sh[kCandThreads];
-    __shared__ unsigned char keep[kCandThreads];
+    __shared__ int sh_idx[kCandThreads];
+    __shared__ unsigned char kept[kCandThreads];
+    __shared__ int wcnt[kCandThreads / 32];
     __shared__ float3 sh_R[kCandThreads];
     __shared__ float3 box[2];
     extern __shared__ FaceTest sh_faces[];
@@ -350,35 +381,39 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
     __syncthreads();
     const float3 blo = box[0], bhi = box[1];
     const float margin = cull_margin(blo, bhi);
-    // this block's super-patch survivors (kSuperRx / kCandThreads blocks per super-patch)
-    const unsigned* sm = smask ? smask + (int64_t)(blockIdx.x / (kSuperRx / kCandThreads)) * words : nullptr;
-    for (int64_t chunk = blockIdx.y; chunk * kCandChunk < n_seq; chunk += gridDim.y) {
-    const int s_begin = (int)(chunk * kCandChunk);
-    const int s_end = min(n_seq, s_begin + kCandChunk);
-    for (int s0 = s_begin; s0 < s_end; s0 += kCandThreads) {
-        if (sm) {                                     // no survivor in this round: skip it (uniform)
-            unsigned any = 0;
+    // the sequences that may reach this block's super-patch (kSuperRx / kCandThreads blocks per
+    // super-patch), or all of them without a list; rounds of kCandThreads staged and beam-tested
+    // against this block's box, then the survivors compacted so every thread loops over them only
+    const int64_t spi = blockIdx.x / (kSuperRx / kCandThreads);
+    const int* lst = slist ? slist + spi * slist_stride : nullptr;
+    const int lcnt = slist ? slist_cnt[spi] : n_seq;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int p0 = blockIdx.y * kCandThreads; p0 < lcnt; p0 += gridDim.y * kCandThreads) {
+        __syncthreads();
+        const int pi = p0 + threadIdx.x;
+        bool k = false;
+        if (pi < lcnt) {
+            const int si = lst ? lst[pi] : pi;
+            const SeqEntry e = seqs[si];
+            sh[threadIdx.x] = e;
+            sh_idx[threadIdx.x] = si;
+            k = box_in_beam(S, e, blo, bhi, margin);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, k);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int base = 0, n_kept = 0;
 #pragma unroll
-            for (int q = 0; q < kCandThreads / 32; ++q)
-                if ((s0 >> 5) + q < words) any |= sm[(s0 >> 5) + q];
-            if (!any) continue;
+        for (int w = 0; w < kCandThreads / 32; ++w) {
+            base += w < warp ? wcnt[w] : 0;
+            n_kept += wcnt[w];
         }
+        if (k) kept[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)threadIdx.x;
         __syncthreads();
-        if (s0 + threadIdx.x < s_end) {
-            const int si = s0 + threadIdx.x;
-            unsigned char k = 0;
-            if (!sm || ((sm[si >> 5] >> (si & 31)) & 1u)) {
-                const SeqEntry e = seqs[si];
-                sh[threadIdx.x] = e;
-                k = box_in_beam(S, e, blo, bhi, margin) ? 1 : 0;
-            }
-            keep[threadIdx.x] = k;
-        }
-        __syncthreads();
-        const int cnt = min(kCandThreads, s_end - s0);
         if (!active) continue;
-        for (int j = 0; j < cnt; ++j) {
-            if (!keep[j]) continue;                  // uniform over the block
+        for (int q = 0; q < n_kept; ++q) {
+            const int j = kept[q];
+            const int sidx = sh_idx[j];
             const SeqEntry& e = sh[j];
             // (A)
             const float sR = dot(xyz(e.pL), R) - e.pL.w;
@@ -422,24 +457,22 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
                 if (rq.q) {
                     const unsigned pos = atomicAdd(rq.cnt, 1u);
                     if (pos < (unsigned)rq.cap) {
-                        rq.q[pos] = make_int4((int)r, s0 + j, 0, 0);
+                        rq.q[pos] = make_int4((int)r, sidx, 0, 0);
                         continue;
                     }
                 }
                 atomicAdd(refines, 1ull);
                 d3 pts[4];
                 const d3 Rd = D3((double)R.x, (double)R.y, (double)R.z);
-                if (!seq_geom_fp64(S, src, Rd, e.info, seqd[s0 + j], pts)) continue;
+                if (!seq_geom_fp64(S, src, Rd, e.info, seqd[sidx], pts)) continue;
             }
             int slot = atomicAdd(&cand_cnt[r], 1);
-            if (slot < cap) cand[r * (int64_t)cap + slot] = s0 + j;
+            if (slot < cap) cand[r * (int64_t)cap + slot] = sidx;
             else atomicExch(overflow, 1);
         }
     }
-    }
 }
 
-// Dense list of the (destination, slot) pairs holding a geometric candidate, receiver-major.
 // Settle the queued candidate decisions in FP64 (seq_geom_fp64, the same check as the inline path).
 __global__ void k_refine_cand(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, const SeqEntry* __restrict__ seqs,
                               const SeqEntryD* __restrict__ seqd, RefineQ rq, int* __restrict__ cand,
@@ -460,6 +493,7 @@ __global__ void k_refine_cand(DeviceScene S, const float* __restrict__ dst_xyz, 
     }
 }
 
+// Dense list of the (destination, slot) pairs holding a geometric candidate, receiver-major.
 __global__ void k_cand_counts(const int* __restrict__ cand_cnt, int64_t n_dst, int cap, int64_t* __restrict__ out)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1780,6 +1814,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             int* rx_order;
             float4* sp_box;          // super-patch boxes [n_super][2]
             unsigned* sp_mask;       // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
+            int* sp_list;            // [n_super][32 ceil(n_seq / 32)] the same as index lists
+            int* sp_cnt;             // [n_super]
             int4* rq;                // deferred FP64 settlements (candidates, then validation)
             unsigned* rq_cnt;
             uint8_t* smap[2];        // visibility maps of the face cells from the Tx and from the RIS centre
@@ -1826,6 +1862,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             const int64_t n_super = (n_rx + kSuperRx - 1) / kSuperRx;
             L.sp_box = A.get<float4>((size_t)n_super * 2);
             L.sp_mask = A.get<unsigned>((size_t)n_super * ((n_ids_max + 31) / 32 + 1));
+            L.sp_list = A.get<int>((size_t)n_super * ((n_ids_max + 31) / 32 + 1) * 32);
+            L.sp_cnt = A.get<int>((size_t)n_super);
             L.rq = A.get<int4>((size_t)rq_cap);
             L.rq_cnt = A.get<unsigned>(2);
             for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
@@ -1921,15 +1959,21 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 const RefineQ rq{L.rq, rq_cap, L.rq_cnt};
                 RISRT_CUDA(ctx, cudaMemsetAsync(L.rq_cnt, 0, sizeof(unsigned) * 2, s));
                 // sequences that can reach each super-patch of kSuperRx Morton-consecutive destinations
-                const unsigned* smask = nullptr;
                 const int words = (t.n + 31) / 32;
+                const int* slist = nullptr;
+                const int* slist_cnt = nullptr;
+                int64_t slist_stride = 0;
                 if (n_dst > kCandThreads) {
                     const int64_t n_super = (n_dst + kSuperRx - 1) / kSuperRx;
                     RISRT_KERNEL(ctx, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, s>>>(dst, L.rx_order, n_dst,
                                                                                                       L.sp_box)));
                     RISRT_KERNEL(ctx, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
                                                                   256, 0, s>>>(S, t.e, t.n, L.sp_box, n_super, words, L.sp_mask)));
-                    smask = L.sp_mask;
+                    RISRT_KERNEL(ctx, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, s>>>(
+                                                            L.sp_mask, words, n_super, (int64_t)words * 32, L.sp_list, L.sp_cnt)));
+                    slist = L.sp_list;
+                    slist_cnt = L.sp_cnt;
+                    slist_stride = (int64_t)words * 32;
                 }
                 const int* ord = n_dst > 1 ? L.rx_order : nullptr;
                 if (F <= kMaxSmemFaces) {
@@ -1937,11 +1981,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
-                                                          cs.cap, flags_dev, counters, smask, words, rq)));
+                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq)));
                 } else {
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
-                                                          cs.cap, flags_dev, counters, smask, words, rq)));
+                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq)));
                 }
                 RISRT_KERNEL(ctx, "k_refine_cand", (k_refine_cand<<<ctx->sm_count * 2, 256, 0, s>>>(
                                                        S, dst, src, t.e, t.d, rq, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
@@ -2241,11 +2285,11 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
-                                                  L.flags, L.counters, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
+                                                  L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
         } else {
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
-                                                  L.flags, L.counters, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
+                                                  L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
         }
         RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<1, 32, 0, s>>>(L.cnt, 1, cap, L.cnt64_tmp)));
         RISRT_CUDA(ctx, exclusive_scan_i64(L.cnt64_tmp, L.dense_off, 2, L.scan_tmp, s));
