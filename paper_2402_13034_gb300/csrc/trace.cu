@@ -1929,8 +1929,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                       L.occ_cursor[1], scan_tmp, &ps->occ_idx[1], &ps->occ_cap[1], &occ_off_src[1])))
                 return rc;
 
-        // visibility maps of the face cells from the Tx (environment paths) and the RIS centre (Rx leg)
-        if (sc->n_cells > 0 && n_rx > 1) {
+        // visibility maps of the face cells from the Tx (environment paths) and the RIS centre (Rx leg);
+        // they cost a fixed pass over all cells, so only traces with more receivers than half the
+        // cells use them
+        const bool use_maps = sc->n_cells > 0 && n_rx > 1 && 2 * n_rx >= sc->n_cells;
+        if (use_maps) {
             const float mg = 1e-4f * (1.f + ext);
             if (max_env > 0)
                 RISRT_KERNEL(ctx, "k_src_map", (k_src_map<<<nblk(sc->n_cells, 128), 128, 0, s>>>(S, Tpos, -1, mg, L.smap[0])));
@@ -2037,7 +2040,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                                         S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
                                                         vs, L.dense_pts, total, counters + 6, tol_base, counters, flags_dev + 1,
                                                         counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq,
-                                                        n_dst > 1 && sc->n_cells > 0 ? L.smap[occ] : nullptr)));
+                                                        n_dst > 1 && use_maps ? L.smap[occ] : nullptr)));
                     RISRT_KERNEL(ctx, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, s>>>(
                                                           S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
                 }
