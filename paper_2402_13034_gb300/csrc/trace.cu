@@ -3,6 +3,7 @@
 // visibility (one ray per element, Sec. IV-A), and the resident path set with FP64 phase references.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -1932,7 +1933,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         // visibility maps of the face cells from the Tx (environment paths) and the RIS centre (Rx leg);
         // they cost a fixed pass over all cells, so only traces with more receivers than half the
         // cells use them
-        const bool use_maps = sc->n_cells > 0 && n_rx > 1 && 2 * n_rx >= sc->n_cells;
+        // (RISRT_MAPS=0 / 1 forces them off / on: both give the same decisions)
+        const char* maps_env = getenv("RISRT_MAPS");
+        const bool use_maps = sc->n_cells > 0 && n_rx > 1 &&
+                              (maps_env && maps_env[0] ? maps_env[0] == '1' : 2 * n_rx >= sc->n_cells);
         if (use_maps) {
             const float mg = 1e-4f * (1.f + ext);
             if (max_env > 0)

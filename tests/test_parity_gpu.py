@@ -179,3 +179,24 @@ def test_invalid_arguments():
     assert e.value.code == 1
     with pytest.raises(R.RisrtError):
         ctx.scene_upload(w.scene.verts, w.scene.tris + 10000, w.scene.face_id, w.scene.mat_id, w.scene.mats)
+
+
+def test_visibility_maps_change_no_decision(monkeypatch):
+    """The first-segment visibility maps and the receiver aperture pyramids decide occlusion without
+    traversal; with them forced on and off the path sets are bit-identical, the fields equal, and
+    both match the oracle."""
+    w = S.room(grid=48)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("RISRT_MAPS", flag)
+        out[flag] = run_gpu(w)
+    a, b = out["1"]["paths"], out["0"]["paths"]
+    for key in ("seqs", "env"):
+        assert all(np.array_equal(np.sort(x), np.sort(y)) for x, y in zip(a[key], b[key]))
+    assert np.array_equal(np.asarray(a["los"]), np.asarray(b["los"]))
+    assert all(np.array_equal(x, y) for x, y in zip(a["vis"], b["vis"]))
+    assert np.array_equal(out["1"]["E"], out["0"]["E"])
+    o = O.Oracle(w)
+    op = o.rx_paths(w.rx_xyz)
+    bad = compare_pathsets(a, op, op["amb"], o.tx_leg())
+    assert not bad, bad[:10]
