@@ -283,6 +283,75 @@ __device__ __forceinline__ RefGrid ref_grid(const float lo[3], const float hi[3]
     return g;
 }
 
+// Box of the part of triangle t inside [blo, bhi] (Sutherland-Hodgman against the box's six planes,
+// the box grown by e to absorb rounding); false if the triangle misses the box. Explicit rounding
+// (no contraction): the counting and the emitting kernels must take the same decisions.
+__device__ bool clip_tri_box(const float* verts, const int32_t* tris, int64_t t, const float blo[3], const float bhi[3],
+                             float e, float olo[3], float ohi[3])
+{
+    float P[9][3], Q[9][3];
+    int n = 3;
+    for (int v = 0; v < 3; ++v)
+        for (int k = 0; k < 3; ++k) P[v][k] = verts[3 * tris[3 * t + v] + k];
+    for (int pl = 0; pl < 6 && n > 0; ++pl) {
+        const int k = pl >> 1;
+        const bool upper = pl & 1;
+        const float lim = upper ? __fadd_rn(bhi[k], e) : __fsub_rn(blo[k], e);
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            const float* a = P[i];
+            const float* b = P[(i + 1) % n];
+            const float da = upper ? __fsub_rn(lim, a[k]) : __fsub_rn(a[k], lim);
+            const float db = upper ? __fsub_rn(lim, b[k]) : __fsub_rn(b[k], lim);
+            if (da >= 0.f && m < 9) {
+                for (int c = 0; c < 3; ++c) Q[m][c] = a[c];
+                ++m;
+            }
+            if ((da >= 0.f) != (db >= 0.f) && m < 9) {
+                const float u = __fdiv_rn(da, __fsub_rn(da, db));
+                for (int c = 0; c < 3; ++c) Q[m][c] = __fadd_rn(a[c], __fmul_rn(u, __fsub_rn(b[c], a[c])));
+                Q[m][k] = lim;
+                ++m;
+            }
+        }
+        n = m;
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) P[i][c] = Q[i][c];
+    }
+    if (n == 0) return false;
+    for (int c = 0; c < 3; ++c) {
+        olo[c] = P[0][c];
+        ohi[c] = P[0][c];
+    }
+    for (int i = 1; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            olo[c] = fminf(olo[c], P[i][c]);
+            ohi[c] = fmaxf(ohi[c], P[i][c]);
+        }
+    for (int c = 0; c < 3; ++c) {         // stay inside the grown cell
+        olo[c] = fmaxf(olo[c], __fsub_rn(blo[c], e));
+        ohi[c] = fminf(ohi[c], __fadd_rn(bhi[c], e));
+    }
+    return true;
+}
+
+// Cell (i, j, l) of the reference grid of a triangle's box.
+__device__ __forceinline__ void ref_cell(const float lo[3], const float hi[3], const RefGrid& g, const int c[3], float blo[3],
+                                         float bhi[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        const float w = __fdiv_rn(__fsub_rn(hi[k], lo[k]), (float)g.n[k]);
+        blo[k] = c[k] == 0 ? lo[k] : __fadd_rn(lo[k], __fmul_rn(w, (float)c[k]));
+        bhi[k] = c[k] == g.n[k] - 1 ? hi[k] : __fadd_rn(lo[k], __fmul_rn(w, (float)(c[k] + 1)));
+    }
+}
+
+__device__ __forceinline__ float clip_eps(const float lo[3], const float hi[3])
+{
+    return 1e-6f * (1.f + fmaxf(fmaxf(fabsf(lo[0]), fabsf(hi[0])), fmaxf(fmaxf(fabsf(lo[1]), fabsf(hi[1])),
+                                                                            fmaxf(fabsf(lo[2]), fabsf(hi[2])))));
+}
+
 __device__ __forceinline__ float scene_cell(const unsigned* bb)
 {
     float span = 0.f;
@@ -298,12 +367,27 @@ __global__ void k_ref_count(const float* __restrict__ verts, const int32_t* __re
     float lo[3], hi[3];
     tri_box(verts, tris, t, lo, hi);
     RefGrid g = ref_grid(lo, hi, scene_cell(bb));
-    cnt[t] = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    if (g.n[0] * g.n[1] * g.n[2] == 1) {
+        cnt[t] = 1;
+        return;
+    }
+    const float e = clip_eps(lo, hi);
+    int64_t n = 0;
+    for (int i = 0; i < g.n[0]; ++i)
+        for (int j = 0; j < g.n[1]; ++j)
+            for (int l = 0; l < g.n[2]; ++l) {
+                const int c[3] = {i, j, l};
+                float blo[3], bhi[3], olo[3], ohi[3];
+                ref_cell(lo, hi, g, c, blo, bhi);
+                n += clip_tri_box(verts, tris, t, blo, bhi, e, olo, ohi) ? 1 : 0;
+            }
+    cnt[t] = n > 0 ? n : 1;          // a triangle always keeps at least one reference
 }
 
 // References of every triangle with their boxes; 30-bit Morton code of each box centre.
 __global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
                            const unsigned* __restrict__ bb, const int64_t* __restrict__ off,
+                           const int64_t* __restrict__ cnt,
                            uint32_t* __restrict__ ref_tri, float4* __restrict__ ref_lo, float4* __restrict__ ref_hi,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
@@ -318,27 +402,40 @@ __global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __res
         float span = from_ordered(bb[3 + k]) - slo[k];
         inv[k] = span > 0.f ? 1.f / span : 0.f;
     }
+    // one reference per grid cell the triangle meets, boxed tightly around the part inside the cell
+    // (a triangle in a single cell keeps its own box); never more references than counted, and any
+    // shortfall filled with the triangle's whole box (conservative)
+    const bool single = g.n[0] * g.n[1] * g.n[2] == 1;
+    const float e = clip_eps(lo, hi);
+    const int64_t r_end = off[t] + cnt[t];
     int64_t r = off[t];
+    auto emit = [&](const float* olo, const float* ohi) {
+        unsigned code = 0;
+        for (int k = 0; k < 3; ++k) {
+            float u = (0.5f * (olo[k] + ohi[k]) - slo[k]) * inv[k];
+            unsigned q = (unsigned)fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+            code |= spread10(q) << (2 - k);
+        }
+        ref_tri[r] = (uint32_t)t;
+        ref_lo[r] = make_float4(olo[0], olo[1], olo[2], 0.f);
+        ref_hi[r] = make_float4(ohi[0], ohi[1], ohi[2], 0.f);
+        keys[r] = code;
+        vals[r] = (uint32_t)r;
+        ++r;
+    };
     for (int i = 0; i < g.n[0]; ++i)
         for (int j = 0; j < g.n[1]; ++j)
-            for (int l = 0; l < g.n[2]; ++l, ++r) {
+            for (int l = 0; l < g.n[2]; ++l) {
                 const int c[3] = {i, j, l};
-                float blo[3], bhi[3];
-                unsigned code = 0;
-                for (int k = 0; k < 3; ++k) {
-                    float w = (hi[k] - lo[k]) / g.n[k];
-                    blo[k] = c[k] == 0 ? lo[k] : lo[k] + w * c[k];
-                    bhi[k] = c[k] == g.n[k] - 1 ? hi[k] : lo[k] + w * (c[k] + 1);
-                    float u = (0.5f * (blo[k] + bhi[k]) - slo[k]) * inv[k];
-                    unsigned q = (unsigned)fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
-                    code |= spread10(q) << (2 - k);
+                float blo[3], bhi[3], olo[3], ohi[3];
+                ref_cell(lo, hi, g, c, blo, bhi);
+                if (single) {
+                    emit(blo, bhi);
+                    continue;
                 }
-                ref_tri[r] = (uint32_t)t;
-                ref_lo[r] = make_float4(blo[0], blo[1], blo[2], 0.f);
-                ref_hi[r] = make_float4(bhi[0], bhi[1], bhi[2], 0.f);
-                keys[r] = code;
-                vals[r] = (uint32_t)r;
+                if (r < r_end && clip_tri_box(verts, tris, t, blo, bhi, e, olo, ohi)) emit(olo, ohi);
             }
+    while (r < r_end) emit(lo, hi);
 }
 
 // Per leaf (sorted reference order): exact float vertices of the referenced triangle, FP32 plane and
@@ -737,7 +834,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &leaf_hi, nr))) return rc;
     size_t tmp_bytes = std::max(sort_temp_bytes(nr), scan_temp_bytes(F) + 64);
     if ((rc = dmalloc(ctx, (char**)&tmp, tmp_bytes))) return rc;
-    RISRT_KERNEL(ctx, "k_ref_emit", (k_ref_emit<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_off, ref_tri,
+    RISRT_KERNEL(ctx, "k_ref_emit", (k_ref_emit<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_off, ref_cnt, ref_tri,
                                                                             ref_lo, ref_hi, keys, vals)));
     RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nr, 30, tmp, s));
 

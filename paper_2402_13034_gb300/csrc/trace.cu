@@ -1001,7 +1001,7 @@ constexpr int kValThreads = 128;
 constexpr int kSteps = RISRT_VALIDATE_STEPS;
 
 #ifndef RISRT_VALIDATE_MINB
-#define RISRT_VALIDATE_MINB 6      // blocks per SM the register budget targets (measured)
+#define RISRT_VALIDATE_MINB 5      // blocks per SM the register budget targets (measured)
 #endif
 __global__ void __launch_bounds__(kValThreads, RISRT_VALIDATE_MINB)
 k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_face, int dst_face,
