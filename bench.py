@@ -47,9 +47,10 @@ EVAL_OPS_PER_UNIT = 32
 # and for the ~half that pass it the reflection point (sub, div, 3 sub, 3 FMA) and the in-face test
 # of a two-triangle face (6 x (3 FMA + sub) + 2 min + 2 compares): counted as 8 + 0.5 * 40.
 CAND_OPS_PER_TEST = 28
-# BVH traversal: a node visit is two slab tests (6 sub/mul, 6 min/max, 4 compare each) = 24 lane ops;
-# a triangle test is a plane distance, hit point and three edge functions = 20 lane ops.
-VISIT_OPS, TRI_OPS = 24, 20
+# BVH traversal: a visit of a four-wide node is four slab tests of 12 lane ops each (6 sub/mul and
+# 6 min/max) = 48 lane ops; a triangle test is a plane distance, hit point and three edge functions
+# = 20 lane ops.
+VISIT_OPS, TRI_OPS = 48, 20
 PRECISIONS = {0: "fp32_simt", 1: "bf16", 2: "bf16x2", 3: "fp16"}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a dominant kernel from one

@@ -524,7 +524,7 @@ int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
     }
-    cudaFree(sc->nodes); cudaFree(sc->tri_geom); cudaFree(sc->tri_verts); cudaFree(sc->tri_face);
+    cudaFree(sc->nodes); cudaFree(sc->nodes4); cudaFree(sc->tri_geom); cudaFree(sc->tri_verts); cudaFree(sc->tri_face);
     cudaFree(sc->faces); cudaFree(sc->face_tris); cudaFree(sc->face_test); cudaFree(sc->tri_leaf); cudaFree(sc->mats);
     cudaFree(sc->face_grid); cudaFree(sc->cell_face);
     delete sc;

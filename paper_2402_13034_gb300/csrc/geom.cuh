@@ -107,6 +107,33 @@ __device__ __forceinline__ void flush_counters(const TraceCounters& t, unsigned 
     }
 }
 
+// One step of a four-wide walk along the segment a + t dir, t in [0, 1] (inv = 1 / dir): the children
+// the segment enters, except subtrees made only of the faces g0 / g1, nearest entry first. Returns
+// the nearest (kNoChild if none) and pushes the others farthest first; the caller keeps 3 free
+// stack entries.
+__device__ __forceinline__ int bvh4_step(const Bvh4Node& nd, float3 a, float3 inv, int g0, int g1, int* stack, int& sp)
+{
+    float t[4];
+    int c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c[k] = __float_as_int(nd.lo[k].w);
+        const int f = __float_as_int(nd.hi[k].w);
+        t[k] = (c[k] != kNoChild && f != g0 && f != g1) ? box_entry(nd.lo[k], nd.hi[k], a, inv) : 3e38f;
+    }
+    auto cs = [&](int i, int j) {
+        if (t[j] < t[i]) {
+            const float tt = t[i]; t[i] = t[j]; t[j] = tt;
+            const int cc = c[i]; c[i] = c[j]; c[j] = cc;
+        }
+    };
+    cs(0, 1); cs(2, 3); cs(0, 2); cs(1, 3); cs(1, 2);
+#pragma unroll
+    for (int k = 3; k >= 1; --k)
+        if (t[k] < 1e30f) stack[sp++] = c[k];
+    return t[0] < 1e30f ? c[0] : kNoChild;
+}
+
 // Is segment A->B blocked (faces ign0 / ign1 skipped)? `refines` counts FP64 settlements,
 // `err` is set if the traversal stack would overflow (never expected; treated as blocked).
 __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
@@ -120,7 +147,7 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
     float tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
     int stack[64];
     int sp = 0;
-    int c = S.root;          // current node in a register; only the farther of two entered children is pushed
+    int c = S.root;          // current node in a register; the other entered children go on the stack
     const int g0 = ign0 >= 0 ? ign0 : -3, g1 = ign1 >= 0 ? ign1 : -3;   // subtrees of one ignored face are skipped
     while (true) {
         if (c < 0) {
@@ -140,27 +167,15 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
             c = stack[--sp];
             continue;
         }
-        const BvhNode nd = S.nodes[c];
+        if (sp + 3 > 64) {          // never expected (stack depth ~ 3 x tree depth / 2); treated as blocked
+            if (err) atomicExch(err, 1);
+            return true;
+        }
+        const Bvh4Node nd = S.nodes4[c];
         if (tc) ++tc->nodes;
-        const float el = box_entry(nd.l_lo, nd.l_hi, a, inv);
-        const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
-        // any hit ends the query, so the child entered first along the segment is visited first
-        const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-        const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
-        const bool hl = el < 1e30f && fl != g0 && fl != g1, hr = er < 1e30f && fr != g0 && fr != g1;
-        if (hl && hr) {
-            if (sp >= 64) {
-                if (err) atomicExch(err, 1);
-                return true;
-            }
-            const bool lfirst = el <= er;
-            stack[sp++] = lfirst ? cr : cl;
-            c = lfirst ? cl : cr;
-        } else if (hl) {
-            c = cl;
-        } else if (hr) {
-            c = cr;
-        } else {
+        // any hit ends the query, so the children entered first along the segment are visited first
+        c = bvh4_step(nd, a, inv, g0, g1, stack, sp);
+        if (c == kNoChild) {
             if (sp == 0) break;
             c = stack[--sp];
         }

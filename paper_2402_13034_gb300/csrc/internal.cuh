@@ -79,6 +79,15 @@ struct BvhNode {
     float4 r_hi;         // xyz, w = the same for the right child
 };
 
+// Four-wide view of the binary BVH: entry i holds the children of binary node i's children (a leaf
+// child stays as it is), so a walk that starts at the root and follows these codes visits every
+// other level. Empty slots have code kNoChild and an inverted box.
+struct Bvh4Node {
+    float4 lo[4];        // xyz child box min, w = child code (binary internal index, ~leaf or kNoChild)
+    float4 hi[4];        // xyz child box max, w = the single face under the child, or -1 (int bits)
+};
+constexpr int kNoChild = 0x7fffffff;
+
 struct Face {
     dv4 plane;       // FP64 unit normal (from the face's first triangle) and offset
     float4 plane32;
@@ -113,6 +122,7 @@ struct DeviceScene {
     int n_faces;
     int root;                    // root child code (internal index, or ~leaf for one triangle); kNoRoot if empty
     const BvhNode* nodes;
+    const Bvh4Node* nodes4;      // [internal nodes] four-wide view used by the traversals
     const TriGeom* tri_geom;     // [n_refs] leaf (reference) order
     const TriVerts* tri_verts;   // [n_refs] leaf order
     const int* tri_face;         // [n_refs] leaf order
@@ -165,6 +175,7 @@ struct risrt_scene {
     int n_mat = 0;
     int root = risrt::kNoRoot;
     risrt::BvhNode* nodes = nullptr;
+    risrt::Bvh4Node* nodes4 = nullptr;
     risrt::TriGeom* tri_geom = nullptr;
     risrt::TriVerts* tri_verts = nullptr;
     int* tri_face = nullptr;
@@ -179,7 +190,7 @@ struct risrt_scene {
     int64_t n_cells = 0;
     risrt::DeviceScene dev() const {
         risrt::DeviceScene s;
-        s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.nodes = nodes; s.tri_geom = tri_geom;
+        s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.nodes = nodes; s.nodes4 = nodes4; s.tri_geom = tri_geom;
         s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.face_test = face_test; s.tri_leaf = tri_leaf; s.mats = mats;
         s.face_grid = face_grid; s.cell_face = cell_face; s.n_cells = n_cells;
         return s;

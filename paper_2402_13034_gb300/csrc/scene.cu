@@ -575,6 +575,39 @@ __global__ void k_refit(const float4* __restrict__ leaf_lo, const float4* __rest
     }
 }
 
+// Four-wide nodes: the slots of binary node i are its children, each internal child replaced by its
+// own two children (tighter boxes, half the levels).
+__global__ void k_bvh4(const BvhNode* __restrict__ nodes, int n_int, Bvh4Node* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    const BvhNode nd = nodes[i];
+    Bvh4Node o;
+    int k = 0;
+    auto put = [&](float4 lo, float4 hi, int code, float face) {
+        o.lo[k] = make_float4(lo.x, lo.y, lo.z, __int_as_float(code));
+        o.hi[k] = make_float4(hi.x, hi.y, hi.z, face);
+        ++k;
+    };
+    for (int side = 0; side < 2; ++side) {
+        const float4 lo = side ? nd.r_lo : nd.l_lo, hi = side ? nd.r_hi : nd.l_hi;
+        const int code = __float_as_int(side ? nd.l_hi.w : nd.l_lo.w);
+        const float face = side ? nd.r_hi.w : nd.r_lo.w;
+        if (code < 0) {
+            put(lo, hi, code, face);
+        } else {
+            const BvhNode c = nodes[code];
+            put(c.l_lo, c.l_hi, __float_as_int(c.l_lo.w), c.r_lo.w);
+            put(c.r_lo, c.r_hi, __float_as_int(c.l_hi.w), c.r_hi.w);
+        }
+    }
+    for (; k < 4; ++k) {
+        o.lo[k] = make_float4(1e30f, 1e30f, 1e30f, __int_as_float(kNoChild));
+        o.hi[k] = make_float4(-1e30f, -1e30f, -1e30f, __int_as_float(-1));
+    }
+    out[i] = o;
+}
+
 // ------------------------------------------------------------------------------------------------
 // faces
 // ------------------------------------------------------------------------------------------------
@@ -860,6 +893,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     int n_int = (int)std::max<int64_t>(nr - 1, 1);
     int *parent_int, *parent_leaf, *flags;
     if ((rc = dmalloc(ctx, &sc->nodes, n_int))) return rc;
+    if ((rc = dmalloc(ctx, &sc->nodes4, n_int))) return rc;
     if ((rc = dmalloc(ctx, &parent_int, n_int))) return rc;
     if ((rc = dmalloc(ctx, &parent_leaf, nr))) return rc;
     if ((rc = dmalloc(ctx, &flags, n_int))) return rc;
@@ -870,6 +904,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if (nr > 1) {
         RISRT_KERNEL(ctx, "k_karras", (k_karras<<<nblk(nr - 1, 256), 256, 0, s>>>(keys, (int)nr, sc->nodes, parent_int, parent_leaf)));
         RISRT_KERNEL(ctx, "k_refit", (k_refit<<<nblk(nr, 256), 256, 0, s>>>(leaf_lo, leaf_hi, (int)nr, sc->nodes, parent_int, parent_leaf, sc->tri_face, flags, pad)));
+        RISRT_KERNEL(ctx, "k_bvh4", (k_bvh4<<<nblk(n_int, 256), 256, 0, s>>>(sc->nodes, n_int, sc->nodes4)));
         sc->root = 0;
     } else {
         sc->root = ~0;

@@ -814,7 +814,7 @@ __device__ bool face_covers(const DeviceScene& S, int ft, const float3* C, float
 
 constexpr int kMapLeafBudget = 8;    // triangles that may meet a cell's pyramid examined before giving up
 #ifndef RISRT_MAP_NODE_BUDGET
-#define RISRT_MAP_NODE_BUDGET 64     // BVH nodes visited per cell before giving up (measured: bounds the slowest cells)
+#define RISRT_MAP_NODE_BUDGET 32     // four-wide BVH nodes visited per cell before giving up (measured: bounds the slowest cells)
 #endif
 
 // Classify the pyramid with apex A and base quad C[0..3] (a convex quad on a plane with unit normal
@@ -884,27 +884,34 @@ __device__ uint8_t classify_pyramid(const DeviceScene& S, float3 A, const float3
             covered = false;
             break;
         }
-        const BvhNode nd = S.nodes[cur];
-        const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-        const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
-        bool hl = fl != g0 && fl != g1, hr = fr != g0 && fr != g1;
-        for (int k = 0; k < 5; ++k) {
-            hl = hl && !box_outside(nd.l_lo, nd.l_hi, pn[k], pq(k), margin);
-            hr = hr && !box_outside(nd.r_lo, nd.r_hi, pn[k], pq(k), margin);
+        if (sp + 3 > 64) {                      // never expected; undecided
+            mixed = true;
+            covered = false;
+            break;
         }
-        if (hl && hr) {
-            if (sp >= 64) {                     // never expected; undecided
-                mixed = true;
-                covered = false;
-                break;
+        const Bvh4Node nd = S.nodes4[cur];
+        float t[4];
+        int ch[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ch[q] = __float_as_int(nd.lo[q].w);
+            const int fq = __float_as_int(nd.hi[q].w);
+            bool in = ch[q] != kNoChild && fq != g0 && fq != g1;
+            for (int k = 0; k < 5 && in; ++k) in = !box_outside(nd.lo[q], nd.hi[q], pn[k], pq(k), margin);
+            // entered children in the order the centre ray meets them (boxes it misses last)
+            t[q] = in ? fminf(box_entry(nd.lo[q], nd.hi[q], A, cinv), 1e30f) : 3e38f;
+        }
+        auto cs = [&](int i, int j) {
+            if (t[j] < t[i]) {
+                const float tt = t[i]; t[i] = t[j]; t[j] = tt;
+                const int cc = ch[i]; ch[i] = ch[j]; ch[j] = cc;
             }
-            const bool lfirst = box_entry(nd.l_lo, nd.l_hi, A, cinv) <= box_entry(nd.r_lo, nd.r_hi, A, cinv);
-            stack[sp++] = lfirst ? cr : cl;
-            cur = lfirst ? cl : cr;
-        } else if (hl) {
-            cur = cl;
-        } else if (hr) {
-            cur = cr;
+        };
+        cs(0, 1); cs(2, 3); cs(0, 2); cs(1, 3); cs(1, 2);
+        for (int q = 3; q >= 1; --q)
+            if (t[q] < 2e38f) stack[sp++] = ch[q];
+        if (t[0] < 2e38f) {
+            cur = ch[0];
         } else {
             if (sp == 0) break;
             cur = stack[--sp];
@@ -1025,7 +1032,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     int stack[64];
     int sp = 0;
     constexpr int kNone = 0x7fffffff;
-    int cur = kNone;             // current node in a register; only the farther of two entered children is pushed
+    int cur = kNone;             // current node in a register; the other entered children go on the stack
     int li = 0, le = 0;          // occluder-list cursor (segment 0 only)
     bool list_mode = false;
     bool blocked = false;
@@ -1148,31 +1155,17 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                     cur = sp > 0 ? stack[--sp] : kNone;
                     continue;
                 }
-                const BvhNode nd = S.nodes[cur];
-                ++tc.nodes;
-                const float el = box_entry(nd.l_lo, nd.l_hi, a, inv);
-                const float er = box_entry(nd.r_lo, nd.r_hi, a, inv);
-                const int cl = __float_as_int(nd.l_lo.w), cr = __float_as_int(nd.l_hi.w);
-                const int fl = __float_as_int(nd.r_lo.w), fr = __float_as_int(nd.r_hi.w);
-                const bool hl = el < 1e30f && fl != g0 && fl != g1, hr = er < 1e30f && fr != g0 && fr != g1;
-                if (hl && hr) {
-                    if (sp >= 64) {
-                        atomicExch(err, 1);
-                        blocked = true;
-                        cur = kNone;
-                        sp = 0;
-                        break;
-                    }
-                    const bool lfirst = el <= er;     // nearer child next, the other on the stack
-                    stack[sp++] = lfirst ? cr : cl;
-                    cur = lfirst ? cl : cr;
-                } else if (hl) {
-                    cur = cl;
-                } else if (hr) {
-                    cur = cr;
-                } else {
-                    cur = sp > 0 ? stack[--sp] : kNone;
+                if (sp + 3 > 64) {           // never expected (stack depth ~ 3 x tree depth / 2)
+                    atomicExch(err, 1);
+                    blocked = true;
+                    cur = kNone;
+                    sp = 0;
+                    break;
                 }
+                const Bvh4Node nd = S.nodes4[cur];
+                ++tc.nodes;
+                cur = bvh4_step(nd, a, inv, g0, g1, stack, sp);   // nearest entered child next
+                if (cur == kNoChild) cur = sp > 0 ? stack[--sp] : kNone;
             }
         }
         if (list_mode ? li >= le : cur == kNone) {
