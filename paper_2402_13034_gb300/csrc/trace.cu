@@ -255,6 +255,17 @@ struct RefineQ {
     unsigned* cnt;
 };
 
+// The validation work list written by the candidate search itself: every warp's 32 lanes are
+// Morton-adjacent destinations testing one sequence at a time, so the lanes that pass form a run of
+// one sequence over neighbouring destinations; a warp stages its runs in shared memory and appends
+// them in chunks (one atomic per chunk). r == nullptr: no list (it is built afterwards).
+struct DenseOut {
+    int* r;
+    int* slot;
+    unsigned long long* cnt;
+};
+constexpr int kDenseBuf = 256;   // staged work-list entries per warp
+
 // Margin of the beam culling for a box: far beyond the FP32 error of the plane and corner arithmetic.
 __device__ __forceinline__ float cull_margin(float3 lo, float3 hi)
 {
@@ -350,8 +361,9 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
              const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int n_seq,
              float tol_base, int* __restrict__ cand, int* __restrict__ cand_cnt, int cap,
              int* __restrict__ overflow, unsigned long long* __restrict__ refines, const int* __restrict__ slist,
-             const int* __restrict__ slist_cnt, int64_t slist_stride, RefineQ rq)
+             const int* __restrict__ slist_cnt, int64_t slist_stride, RefineQ rq, DenseOut dl)
 {
+    __shared__ int2 dbuf[kCandThreads / 32][kDenseBuf];
     __shared__ SeqEntry sh[kCandThreads];
     __shared__ int sh_idx[kCandThreads];
     __shared__ unsigned char kept[kCandThreads];
@@ -389,6 +401,20 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
     const int* lst = slist ? slist + spi * slist_stride : nullptr;
     const int lcnt = slist ? slist_cnt[spi] : n_seq;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int wn = 0;                                      // staged work-list entries of this warp (uniform)
+    auto flush = [&]() {
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0 && wn > 0) base = atomicAdd(dl.cnt, (unsigned long long)wn);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int k = lane; k < wn; k += 32) {
+            const int2 v = dbuf[warp][k];
+            dl.r[base + k] = v.x;
+            dl.slot[base + k] = v.y;
+        }
+        __syncwarp();
+        wn = 0;
+    };
     for (int p0 = blockIdx.y * kCandThreads; p0 < lcnt; p0 += gridDim.y * kCandThreads) {
         __syncthreads();
         const int pi = p0 + threadIdx.x;
@@ -411,74 +437,95 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
         }
         if (k) kept[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)threadIdx.x;
         __syncthreads();
-        if (!active) continue;
         for (int q = 0; q < n_kept; ++q) {
             const int j = kept[q];
             const int sidx = sh_idx[j];
             const SeqEntry& e = sh[j];
-            // (A)
-            const float sR = dot(xyz(e.pL), R) - e.pL.w;
-            const float sp = e.sL.w;
-            const bool clearA = fabsf(sR) > tol_base && fabsf(sp) > tol_base;
-            if (clearA && sp * sR < 0.f) continue;
-            bool unsure = !clearA;
-            // (B) last reflection point P = R + t (S_L - R), t = sR / (sR + sp)
-            const float den = sR + sp;
-            const float3 d = xyz(e.sL) - R;
-            const float iden = __frcp_rn(den);
-            const float t = sR * iden;
-            const float3 P = R + d * t;
-            const float d2 = dot(d, d);
-            const float cond = d2 * rsqrtf(d2) * fabsf(iden);   // |d| / |den| (a few ulps suffice: tol has margin)
-            const float tol = tol_base * fminf(cond, 1e6f);
-            const int k = e.info.w;
-            const int cB = face_class<SMEM_FACES>(S, sh_faces, k == 2 ? e.info.y : e.info.x, P, tol);
-            if (cB == 0) continue;
-            unsure |= cB == 2;
-            if (k == 2) {
-                // (C)
-                const float s1P = dot(xyz(e.p1), P) - e.p1.w;
-                const float ssrc = e.s1.w;
-                const bool clearC = fabsf(s1P) > tol && fabsf(ssrc) > tol_base;
-                if (clearC && s1P * ssrc < 0.f) continue;
-                unsure |= !clearC;
-                // (D) P1 = P + t1 (S1 - P), t1 = s1P / (s1P + ssrc)
-                const float den1 = s1P + ssrc;
-                const float3 d1 = xyz(e.s1) - P;
-                const float iden1 = __frcp_rn(den1);
-                const float3 P1 = P + d1 * (s1P * iden1);
-                const float d12 = dot(d1, d1);
-                const float cond1 = d12 * rsqrtf(d12) * fabsf(iden1);
-                const float tol1 = tol * fminf(cond1, 1e6f) + tol_base;
-                const int cD = face_class<SMEM_FACES>(S, sh_faces, e.info.x, P1, tol1);
-                if (cD == 0) continue;
-                unsure |= cD == 2;
-            }
-            if (unsure) {
-                if (rq.q) {
-                    const unsigned pos = atomicAdd(rq.cnt, 1u);
-                    if (pos < (unsigned)rq.cap) {
-                        rq.q[pos] = make_int4((int)r, sidx, 0, 0);
-                        continue;
-                    }
+            // the geometric tests (A)-(D); false when they reject, or when the decision is queued
+            auto passes = [&]() -> bool {
+                // (A)
+                const float sR = dot(xyz(e.pL), R) - e.pL.w;
+                const float sp = e.sL.w;
+                const bool clearA = fabsf(sR) > tol_base && fabsf(sp) > tol_base;
+                if (clearA && sp * sR < 0.f) return false;
+                bool unsure = !clearA;
+                // (B) last reflection point P = R + t (S_L - R), t = sR / (sR + sp)
+                const float den = sR + sp;
+                const float3 d = xyz(e.sL) - R;
+                const float iden = __frcp_rn(den);
+                const float t = sR * iden;
+                const float3 P = R + d * t;
+                const float d2 = dot(d, d);
+                const float cond = d2 * rsqrtf(d2) * fabsf(iden);   // |d| / |den| (a few ulps suffice: tol has margin)
+                const float tol = tol_base * fminf(cond, 1e6f);
+                const int k = e.info.w;
+                const int cB = face_class<SMEM_FACES>(S, sh_faces, k == 2 ? e.info.y : e.info.x, P, tol);
+                if (cB == 0) return false;
+                unsure |= cB == 2;
+                if (k == 2) {
+                    // (C)
+                    const float s1P = dot(xyz(e.p1), P) - e.p1.w;
+                    const float ssrc = e.s1.w;
+                    const bool clearC = fabsf(s1P) > tol && fabsf(ssrc) > tol_base;
+                    if (clearC && s1P * ssrc < 0.f) return false;
+                    unsure |= !clearC;
+                    // (D) P1 = P + t1 (S1 - P), t1 = s1P / (s1P + ssrc)
+                    const float den1 = s1P + ssrc;
+                    const float3 d1 = xyz(e.s1) - P;
+                    const float iden1 = __frcp_rn(den1);
+                    const float3 P1 = P + d1 * (s1P * iden1);
+                    const float d12 = dot(d1, d1);
+                    const float cond1 = d12 * rsqrtf(d12) * fabsf(iden1);
+                    const float tol1 = tol * fminf(cond1, 1e6f) + tol_base;
+                    const int cD = face_class<SMEM_FACES>(S, sh_faces, e.info.x, P1, tol1);
+                    if (cD == 0) return false;
+                    unsure |= cD == 2;
                 }
-                atomicAdd(refines, 1ull);
-                d3 pts[4];
-                const d3 Rd = D3((double)R.x, (double)R.y, (double)R.z);
-                if (!seq_geom_fp64(S, src, Rd, e.info, seqd[sidx], pts)) continue;
+                if (unsure) {
+                    if (rq.q) {
+                        const unsigned pos = atomicAdd(rq.cnt, 1u);
+                        if (pos < (unsigned)rq.cap) {
+                            rq.q[pos] = make_int4((int)r, sidx, 0, 0);
+                            return false;
+                        }
+                    }
+                    atomicAdd(refines, 1ull);
+                    d3 pts[4];
+                    const d3 Rd = D3((double)R.x, (double)R.y, (double)R.z);
+                    if (!seq_geom_fp64(S, src, Rd, e.info, seqd[sidx], pts)) return false;
+                }
+                return true;
+            };
+            bool pass = active && passes();
+            int slot = -1;
+            if (pass) {
+                slot = atomicAdd(&cand_cnt[r], 1);
+                if (slot < cap) {
+                    cand[r * (int64_t)cap + slot] = sidx;
+                } else {
+                    atomicExch(overflow, 1);
+                    pass = false;
+                }
             }
-            int slot = atomicAdd(&cand_cnt[r], 1);
-            if (slot < cap) cand[r * (int64_t)cap + slot] = sidx;
-            else atomicExch(overflow, 1);
+            if (dl.r) {                              // this warp's run of sequence sidx
+                const unsigned b = __ballot_sync(0xffffffffu, pass);
+                const int nb = __popc(b);
+                if (nb) {
+                    if (wn + nb > kDenseBuf) flush();
+                    if (pass) dbuf[warp][wn + __popc(b & ((1u << lane) - 1u))] = make_int2((int)r, slot);
+                    wn += nb;
+                }
+            }
         }
     }
+    if (dl.r) flush();
 }
 
 // Settle the queued candidate decisions in FP64 (seq_geom_fp64, the same check as the inline path).
 __global__ void k_refine_cand(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, const SeqEntry* __restrict__ seqs,
                               const SeqEntryD* __restrict__ seqd, RefineQ rq, int* __restrict__ cand,
                               int* __restrict__ cand_cnt, int cap, int* __restrict__ overflow,
-                              unsigned long long* __restrict__ refines)
+                              unsigned long long* __restrict__ refines, DenseOut dl)
 {
     const unsigned n = min(*rq.cnt, (unsigned)rq.cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(refines, (unsigned long long)n);
@@ -489,8 +536,16 @@ __global__ void k_refine_cand(DeviceScene S, const float* __restrict__ dst_xyz, 
         d3 pts[4];
         if (!seq_geom_fp64(S, src, D3((double)R.x, (double)R.y, (double)R.z), seqs[q.y].info, seqd[q.y], pts)) continue;
         const int slot = atomicAdd(&cand_cnt[r], 1);
-        if (slot < cap) cand[r * (int64_t)cap + slot] = q.y;
-        else atomicExch(overflow, 1);
+        if (slot < cap) {
+            cand[r * (int64_t)cap + slot] = q.y;
+            if (dl.r) {                              // appended to the work list as well
+                const unsigned long long pos = atomicAdd(dl.cnt, 1ull);
+                dl.r[pos] = (int)r;
+                dl.slot[pos] = slot;
+            }
+        } else {
+            atomicExch(overflow, 1);
+        }
     }
 }
 
@@ -513,60 +568,6 @@ __global__ void k_dense_list(const int* __restrict__ cand_cnt, const int64_t* __
     for (int slot = lane; slot < n; slot += 32) {
         dense_r[o + slot] = (int)r;
         dense_slot[o + slot] = slot;
-    }
-}
-
-// Dense list in coherent order: one warp per group of 32 receivers taken in Morton order; the warp
-// merges the group's candidate rows by sequence id (smallest head first), so consecutive items mostly
-// share one image sequence and come from neighbouring receivers, and the traversals of a warp follow
-// similar paths through the BVH. Rows need not be sorted: every item is emitted exactly once either way.
-// counts: out[g] = number of candidates of group g, out[n_groups] = 0 (exclusive scan input).
-__global__ void k_group_counts(const int* __restrict__ cand_cnt, const int* __restrict__ order, int64_t n_dst, int cap,
-                               int64_t n_groups, int64_t* __restrict__ out)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (g > n_groups) return;
-    if (g == n_groups) {
-        if (lane == 0) out[g] = 0;
-        return;
-    }
-    const int64_t i = g * 32 + lane;
-    int c = 0;
-    if (i < n_dst) c = min(cand_cnt[order ? order[i] : (int)i], cap);
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if (lane == 0) out[g] = c;
-}
-
-__global__ void k_dense_merge(const int* __restrict__ cand, const int* __restrict__ cand_cnt, const int* __restrict__ order,
-                              int64_t n_dst, int cap, int64_t n_groups, const int64_t* __restrict__ off,
-                              int* __restrict__ dense_r, int* __restrict__ dense_slot)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (g >= n_groups) return;
-    const int64_t i = g * 32 + lane;
-    const int r = i < n_dst ? (order ? order[i] : (int)i) : 0;
-    const int c = i < n_dst ? min(cand_cnt[r], cap) : 0;
-    const int* row = cand + (int64_t)r * cap;
-    int64_t base = off[g];
-    int h = 0;
-    int key = c > 0 ? row[0] : INT_MAX;
-    while (true) {
-        int m = key;
-        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
-        if (m == INT_MAX) break;
-        const bool mine = key == m;
-        const unsigned b = __ballot_sync(FULL, mine);
-        if (mine) {
-            const int64_t pos = base + __popc(b & ((1u << lane) - 1u));
-            dense_r[pos] = r;
-            dense_slot[pos] = h;
-            ++h;
-            key = h < c ? row[h] : INT_MAX;
-        }
-        base += __popc(b);
     }
 }
 
@@ -1806,6 +1807,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             void* rx_sort_tmp;
             unsigned* rx_bb;
             int* rx_order;
+            unsigned long long* dense_cnt;   // entries of the work list written by the candidate search
             float4* sp_box;          // super-patch boxes [n_super][2]
             unsigned* sp_mask;       // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
             int* sp_list;            // [n_super][32 ceil(n_seq / 32)] the same as index lists
@@ -1854,6 +1856,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.dense_slot2 = A.get<int>((size_t)n_rx * cap);
             L.face_off64 = A.get<int64_t>(F + 1);
             const int64_t n_super = (n_rx + kSuperRx - 1) / kSuperRx;
+            L.dense_cnt = A.get<unsigned long long>(1);
             L.sp_box = A.get<float4>((size_t)n_super * 2);
             L.sp_mask = A.get<unsigned>((size_t)n_super * ((n_ids_max + 31) / 32 + 1));
             L.sp_list = A.get<int>((size_t)n_super * ((n_ids_max + 31) / 32 + 1) * 32);
@@ -1958,6 +1961,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
                 const RefineQ rq{L.rq, rq_cap, L.rq_cnt};
                 RISRT_CUDA(ctx, cudaMemsetAsync(L.rq_cnt, 0, sizeof(unsigned) * 2, s));
+                // many destinations: the candidate search writes the validation work list itself
+                const DenseOut dl = n_dst > 1 ? DenseOut{L.dense_r, L.dense_slot, L.dense_cnt} : DenseOut{nullptr, nullptr, nullptr};
+                if (dl.r) RISRT_CUDA(ctx, cudaMemsetAsync(L.dense_cnt, 0, sizeof(unsigned long long), s));
                 // sequences that can reach each super-patch of kSuperRx Morton-consecutive destinations
                 const int words = (t.n + 31) / 32;
                 const int* slist = nullptr;
@@ -1981,34 +1987,25 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
-                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq)));
+                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl)));
                 } else {
                     RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
-                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq)));
+                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl)));
                 }
                 RISRT_KERNEL(ctx, "k_refine_cand", (k_refine_cand<<<ctx->sm_count * 2, 256, 0, s>>>(
-                                                       S, dst, src, t.e, t.d, rq, cs.cand, cs.cnt, cs.cap, flags_dev, counters)));
-                // dense candidate list, then persistent validation
-                int64_t n_off = n_dst;   // entries of dense_off before the total
-                if (n_dst > 1) {
-                    const int64_t ng = (n_dst + 31) / 32;
-                    const int* ord = L.rx_order;
-                    RISRT_KERNEL(ctx, "k_group_counts", (k_group_counts<<<nblk((ng + 1) * 32, 128), 128, 0, s>>>(
-                                                            cs.cnt, ord, n_dst, cs.cap, ng, cs.cnt64_tmp)));
-                    RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, ng + 1, scan_tmp, s));
-                    RISRT_KERNEL(ctx, "k_dense_merge", (k_dense_merge<<<nblk(ng * 32, 128), 128, 0, s>>>(
-                                                           cs.cand, cs.cnt, ord, n_dst, cs.cap, ng, L.dense_off, L.dense_r,
-                                                           L.dense_slot)));
-                    n_off = ng;
+                                                       S, dst, src, t.e, t.d, rq, cs.cand, cs.cnt, cs.cap, flags_dev, counters, dl)));
+                // dense candidate list (written above for many destinations), then persistent validation
+                long long total = 0;
+                if (dl.r) {
+                    RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_cnt, sizeof(long long), cudaMemcpyDeviceToHost, s));
                 } else {
                     RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, s>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
                     RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, n_dst + 1, scan_tmp, s));
                     RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, s>>>(cs.cnt, L.dense_off, n_dst, cs.cap,
                                                                                                        L.dense_r, L.dense_slot)));
+                    RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + n_dst, sizeof(long long), cudaMemcpyDeviceToHost, s));
                 }
-                long long total = 0;
-                RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + n_off, sizeof(long long), cudaMemcpyDeviceToHost, s));
                 RISRT_CUDA(ctx, cudaMemsetAsync(counters + 6, 0, sizeof(unsigned long long), s));
                 RISRT_CUDA(ctx, cudaStreamSynchronize(s));
                 int *vr = L.dense_r, *vs = L.dense_slot;
@@ -2285,11 +2282,13 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
-                                                  L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
+                                                  L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr},
+                                                  DenseOut{nullptr, nullptr, nullptr})));
         } else {
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
-                                                  L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr})));
+                                                  L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr},
+                                                  DenseOut{nullptr, nullptr, nullptr})));
         }
         RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<1, 32, 0, s>>>(L.cnt, 1, cap, L.cnt64_tmp)));
         RISRT_CUDA(ctx, exclusive_scan_i64(L.cnt64_tmp, L.dense_off, 2, L.scan_tmp, s));
