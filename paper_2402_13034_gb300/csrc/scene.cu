@@ -359,40 +359,47 @@ __device__ __forceinline__ float scene_cell(const unsigned* bb)
     return fmaxf(span * 0.125f, 1e-6f);
 }
 
+// One warp per triangle, lanes over the cells of its reference grid (cell c = (i, j, l) with
+// c = (i n1 + j) n2 + l): the number of cells the triangle meets (at least 1).
 __global__ void k_ref_count(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
                             const unsigned* __restrict__ bb, int64_t* __restrict__ cnt)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nt) return;                              // whole warps leave together
     float lo[3], hi[3];
     tri_box(verts, tris, t, lo, hi);
     RefGrid g = ref_grid(lo, hi, scene_cell(bb));
-    if (g.n[0] * g.n[1] * g.n[2] == 1) {
-        cnt[t] = 1;
+    const int nc = g.n[0] * g.n[1] * g.n[2];
+    if (nc == 1) {
+        if (lane == 0) cnt[t] = 1;
         return;
     }
     const float e = clip_eps(lo, hi);
-    int64_t n = 0;
-    for (int i = 0; i < g.n[0]; ++i)
-        for (int j = 0; j < g.n[1]; ++j)
-            for (int l = 0; l < g.n[2]; ++l) {
-                const int c[3] = {i, j, l};
-                float blo[3], bhi[3], olo[3], ohi[3];
-                ref_cell(lo, hi, g, c, blo, bhi);
-                n += clip_tri_box(verts, tris, t, blo, bhi, e, olo, ohi) ? 1 : 0;
-            }
-    cnt[t] = n > 0 ? n : 1;          // a triangle always keeps at least one reference
+    int n = 0;
+    for (int cc = lane; cc < nc; cc += 32) {
+        const int c[3] = {cc / (g.n[1] * g.n[2]), (cc / g.n[2]) % g.n[1], cc % g.n[2]};
+        float blo[3], bhi[3], olo[3], ohi[3];
+        ref_cell(lo, hi, g, c, blo, bhi);
+        n += clip_tri_box(verts, tris, t, blo, bhi, e, olo, ohi) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) cnt[t] = n > 0 ? n : 1;            // a triangle always keeps at least one reference
 }
 
-// References of every triangle with their boxes; 30-bit Morton code of each box centre.
+// References of every triangle with their boxes; 30-bit Morton code of each box centre. One warp per
+// triangle: one reference per grid cell the triangle meets, in cell order, boxed tightly around the
+// part inside the cell (a triangle in a single cell keeps its own box); never more references than
+// counted, and any shortfall filled with the triangle's whole box (conservative).
 __global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
                            const unsigned* __restrict__ bb, const int64_t* __restrict__ off,
                            const int64_t* __restrict__ cnt,
                            uint32_t* __restrict__ ref_tri, float4* __restrict__ ref_lo, float4* __restrict__ ref_hi,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nt) return;                              // whole warps leave together
     float lo[3], hi[3];
     tri_box(verts, tris, t, lo, hi);
     RefGrid g = ref_grid(lo, hi, scene_cell(bb));
@@ -402,14 +409,7 @@ __global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __res
         float span = from_ordered(bb[3 + k]) - slo[k];
         inv[k] = span > 0.f ? 1.f / span : 0.f;
     }
-    // one reference per grid cell the triangle meets, boxed tightly around the part inside the cell
-    // (a triangle in a single cell keeps its own box); never more references than counted, and any
-    // shortfall filled with the triangle's whole box (conservative)
-    const bool single = g.n[0] * g.n[1] * g.n[2] == 1;
-    const float e = clip_eps(lo, hi);
-    const int64_t r_end = off[t] + cnt[t];
-    int64_t r = off[t];
-    auto emit = [&](const float* olo, const float* ohi) {
+    auto emit = [&](int64_t r, const float* olo, const float* ohi) {
         unsigned code = 0;
         for (int k = 0; k < 3; ++k) {
             float u = (0.5f * (olo[k] + ohi[k]) - slo[k]) * inv[k];
@@ -421,21 +421,31 @@ __global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __res
         ref_hi[r] = make_float4(ohi[0], ohi[1], ohi[2], 0.f);
         keys[r] = code;
         vals[r] = (uint32_t)r;
-        ++r;
     };
-    for (int i = 0; i < g.n[0]; ++i)
-        for (int j = 0; j < g.n[1]; ++j)
-            for (int l = 0; l < g.n[2]; ++l) {
-                const int c[3] = {i, j, l};
-                float blo[3], bhi[3], olo[3], ohi[3];
-                ref_cell(lo, hi, g, c, blo, bhi);
-                if (single) {
-                    emit(blo, bhi);
-                    continue;
-                }
-                if (r < r_end && clip_tri_box(verts, tris, t, blo, bhi, e, olo, ohi)) emit(olo, ohi);
-            }
-    while (r < r_end) emit(lo, hi);
+    const int nc = g.n[0] * g.n[1] * g.n[2];
+    const int64_t r0 = off[t], r_end = r0 + cnt[t];
+    if (nc == 1) {
+        if (lane == 0) emit(r0, lo, hi);
+        return;
+    }
+    const float e = clip_eps(lo, hi);
+    int64_t r = r0;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int cc = c0 + lane;
+        float olo[3], ohi[3];
+        bool in = false;
+        if (cc < nc) {
+            const int c[3] = {cc / (g.n[1] * g.n[2]), (cc / g.n[2]) % g.n[1], cc % g.n[2]};
+            float blo[3], bhi[3];
+            ref_cell(lo, hi, g, c, blo, bhi);
+            in = clip_tri_box(verts, tris, t, blo, bhi, e, olo, ohi);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, in);
+        const int64_t mine = r + __popc(b & ((1u << lane) - 1u));
+        if (in && mine < r_end) emit(mine, olo, ohi);
+        r += __popc(b);
+    }
+    for (int64_t q = r + lane; q < r_end; q += 32) emit(q, lo, hi);
 }
 
 // Per leaf (sorted reference order): exact float vertices of the referenced triangle, FP32 plane and
@@ -848,7 +858,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     void* tmp0;
     if ((rc = dmalloc(ctx, (char**)&tmp0, scan_temp_bytes(nt + 1) + 64))) return rc;
     RISRT_CUDA(ctx, cudaMemsetAsync(ref_cnt + nt, 0, sizeof(int64_t), s));
-    RISRT_KERNEL(ctx, "k_ref_count", (k_ref_count<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_cnt)));
+    RISRT_KERNEL(ctx, "k_ref_count", (k_ref_count<<<nblk(nt * 32, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_cnt)));
     RISRT_CUDA(ctx, exclusive_scan_i64(ref_cnt, ref_off, nt + 1, tmp0, s));
     int64_t nr = 0;
     RISRT_CUDA(ctx, cudaMemcpyAsync(&nr, ref_off + nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -867,7 +877,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &leaf_hi, nr))) return rc;
     size_t tmp_bytes = std::max(sort_temp_bytes(nr), scan_temp_bytes(F) + 64);
     if ((rc = dmalloc(ctx, (char**)&tmp, tmp_bytes))) return rc;
-    RISRT_KERNEL(ctx, "k_ref_emit", (k_ref_emit<<<nblk(nt, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_off, ref_cnt, ref_tri,
+    RISRT_KERNEL(ctx, "k_ref_emit", (k_ref_emit<<<nblk(nt * 32, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_off, ref_cnt, ref_tri,
                                                                             ref_lo, ref_hi, keys, vals)));
     RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nr, 30, tmp, s));
 
