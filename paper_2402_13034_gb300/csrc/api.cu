@@ -125,6 +125,7 @@ int risrt_destroy(risrt_ctx* ctx)
         cudaEventDestroy(p.b);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->small) cudaFree(ctx->small);
     delete ctx;
     return RISRT_OK;
 }

@@ -159,6 +159,7 @@ struct risrt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int sm_count = 0;
+    void* small = nullptr;       // 256 B of device memory for per-call reductions (allocated on first use)
     std::string err;
     Antenna tx{}, rx{};
     // tracing
@@ -210,6 +211,7 @@ struct risrt_rxset {
     int64_t n = 0;
     float* xyz = nullptr;        // [n][3] device
     bool owned = false;
+    mutable float ext = -1.f;    // max |coordinate|, cached for uploaded (library-owned) sets; -1: unknown
 };
 
 // Rx-leg path record (structure of arrays, one entry per (rx, path)); see field.cu for use.

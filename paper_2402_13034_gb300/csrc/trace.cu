@@ -125,6 +125,13 @@ __global__ void k_seq_allowed(DeviceScene S, int64_t n_ids, int mode, Frame fr, 
     flag[id] = ok ? 1 : 0;
 }
 
+// Number of allowed sequences: last exclusive-scan position + last flag.
+__global__ void k_seq_count(const int64_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t n_ids,
+                            int64_t* __restrict__ out)
+{
+    if (threadIdx.x == 0) *out = pos[n_ids - 1] + flag[n_ids - 1];
+}
+
 __global__ void k_seq_build(DeviceScene S, int64_t n_ids, const int64_t* __restrict__ flag,
                             const int64_t* __restrict__ pos, d3 src, SeqEntry* __restrict__ out,
                             SeqEntryD* __restrict__ outd)
@@ -673,71 +680,52 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int* __re
 
 // Counting sort of the dense candidate list by first face, so the lanes of a warp share one
 // occluder list (and similar first segments).
-__global__ void k_face_hist(const SeqEntry* __restrict__ seqs, const int* __restrict__ cand, int cap,
-                            const int* __restrict__ dense_r, const int* __restrict__ dense_slot, long long total,
-                            int* __restrict__ hist)
-{
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    atomicAdd(&hist[seqs[cand[(int64_t)dense_r[i] * cap + dense_slot[i]]].info.x], 1);
-}
 
-__global__ void k_face_scatter(const SeqEntry* __restrict__ seqs, const int* __restrict__ cand, int cap,
-                               const int* __restrict__ dense_r, const int* __restrict__ dense_slot, long long total,
-                               const int64_t* __restrict__ off, int* __restrict__ cursor, int* __restrict__ out_r,
-                               int* __restrict__ out_slot)
-{
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    const int r = dense_r[i], sl = dense_slot[i];
-    const int f = seqs[cand[(int64_t)r * cap + sl]].info.x;
-    const int64_t o = off[f] + atomicAdd(&cursor[f], 1);
-    out_r[o] = r;
-    out_slot[o] = sl;
-}
 
 // FP32 reflection points of every dense candidate (same back-trace as the candidate filter): the
 // last point P (next to the destination) and, for order 2, the first point P1.
 __global__ void k_cand_points(const float* __restrict__ dst_xyz, const SeqEntry* __restrict__ seqs,
                               const int* __restrict__ cand, int cap, const int* __restrict__ dense_r,
-                              const int* __restrict__ dense_slot, long long total, float4* __restrict__ pts)
+                              const int* __restrict__ dense_slot, const long long* __restrict__ d_total,
+                              float4* __restrict__ pts)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    const int r = dense_r[i];
-    const int si = cand[(int64_t)r * cap + dense_slot[i]];
-    const SeqEntry e = seqs[si];
-    const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
-    const float sR = dot(xyz(e.pL), R) - e.pL.w;
-    const float den = sR + e.sL.w;
-    const float t = sR / den;
-    const float3 d = xyz(e.sL) - R;
-    const float3 P = R + d * t;
-    // first-order bound on |P - P_exact| from the FP32 roundings of the inputs (images, planes and
-    // signed distances are FP32 copies of FP64 values) and of these operations, doubled
-    const float eps = 5.9604645e-8f;
-    auto l1 = [](float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); };
-    const float mag = l1(R) + l1(xyz(e.sL)) + fabsf(e.pL.w);
-    const float e_s = 8.f * eps * mag;
-    const float e_den = e_s + 2.f * eps * fabsf(e.sL.w) + eps * fabsf(den);
-    const float e_t = (e_s + fabsf(t) * e_den) / fabsf(den) + 2.f * eps * fabsf(t);
-    const float errP = l1(d) * e_t + (fabsf(t) + 1.f) * 4.f * eps * mag;
-    float3 P1 = P;
-    float errP1 = errP;
-    if (e.info.w == 2) {
-        const float s1P = dot(xyz(e.p1), P) - e.p1.w;
-        const float den1 = s1P + e.s1.w;
-        const float t1 = s1P / den1;
-        const float3 d1 = xyz(e.s1) - P;
-        P1 = P + d1 * t1;
-        const float mag1 = l1(P) + l1(xyz(e.s1)) + fabsf(e.p1.w);
-        const float e_s1 = l1(xyz(e.p1)) * errP + 8.f * eps * mag1;
-        const float e_den1 = e_s1 + 2.f * eps * fabsf(e.s1.w) + eps * fabsf(den1);
-        const float e_t1 = (e_s1 + fabsf(t1) * e_den1) / fabsf(den1) + 2.f * eps * fabsf(t1);
-        errP1 = errP + l1(d1) * e_t1 + fabsf(t1) * (errP + 4.f * eps * l1(xyz(e.s1))) + 4.f * eps * mag1;
+    const long long total = *d_total;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int r = dense_r[i];
+        const int si = cand[(int64_t)r * cap + dense_slot[i]];
+        const SeqEntry e = seqs[si];
+        const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
+        const float sR = dot(xyz(e.pL), R) - e.pL.w;
+        const float den = sR + e.sL.w;
+        const float t = sR / den;
+        const float3 d = xyz(e.sL) - R;
+        const float3 P = R + d * t;
+        // first-order bound on |P - P_exact| from the FP32 roundings of the inputs (images, planes and
+        // signed distances are FP32 copies of FP64 values) and of these operations, doubled
+        const float eps = 5.9604645e-8f;
+        auto l1 = [](float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); };
+        const float mag = l1(R) + l1(xyz(e.sL)) + fabsf(e.pL.w);
+        const float e_s = 8.f * eps * mag;
+        const float e_den = e_s + 2.f * eps * fabsf(e.sL.w) + eps * fabsf(den);
+        const float e_t = (e_s + fabsf(t) * e_den) / fabsf(den) + 2.f * eps * fabsf(t);
+        const float errP = l1(d) * e_t + (fabsf(t) + 1.f) * 4.f * eps * mag;
+        float3 P1 = P;
+        float errP1 = errP;
+        if (e.info.w == 2) {
+            const float s1P = dot(xyz(e.p1), P) - e.p1.w;
+            const float den1 = s1P + e.s1.w;
+            const float t1 = s1P / den1;
+            const float3 d1 = xyz(e.s1) - P;
+            P1 = P + d1 * t1;
+            const float mag1 = l1(P) + l1(xyz(e.s1)) + fabsf(e.p1.w);
+            const float e_s1 = l1(xyz(e.p1)) * errP + 8.f * eps * mag1;
+            const float e_den1 = e_s1 + 2.f * eps * fabsf(e.s1.w) + eps * fabsf(den1);
+            const float e_t1 = (e_s1 + fabsf(t1) * e_den1) / fabsf(den1) + 2.f * eps * fabsf(t1);
+            errP1 = errP + l1(d1) * e_t1 + fabsf(t1) * (errP + 4.f * eps * l1(xyz(e.s1))) + 4.f * eps * mag1;
+        }
+        pts[2 * i] = make_float4(P.x, P.y, P.z, 2.f * errP);
+        pts[2 * i + 1] = make_float4(P1.x, P1.y, P1.z, 2.f * errP1);
     }
-    pts[2 * i] = make_float4(P.x, P.y, P.z, 2.f * errP);
-    pts[2 * i + 1] = make_float4(P1.x, P1.y, P1.z, 2.f * errP1);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1003,9 +991,6 @@ constexpr int kValThreads = 128;
 #ifndef RISRT_MAX_OCC_LIST
 #define RISRT_MAX_OCC_LIST (-1)    // occluder lists up to this length replace BVH traversal; -1: off
 #endif
-#ifndef RISRT_GROUP_BY_FACE
-#define RISRT_GROUP_BY_FACE 0
-#endif
 constexpr int kSteps = RISRT_VALIDATE_STEPS;
 
 #ifndef RISRT_VALIDATE_MINB
@@ -1015,10 +1000,12 @@ __global__ void __launch_bounds__(kValThreads, RISRT_VALIDATE_MINB)
 k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_face, int dst_face,
            const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int* __restrict__ cand, int cap,
            const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const float4* __restrict__ dpts,
-           long long total, unsigned long long* __restrict__ next, float tol_base, unsigned long long* refines,
+           const long long* __restrict__ d_total, unsigned long long* __restrict__ next, float tol_base,
+           unsigned long long* refines,
            int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx,
            RefineQ rq, const uint8_t* __restrict__ smap)
 {
+    const long long total = *d_total;
     const float3 srcf = to_f(src);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1083,7 +1070,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         const int h = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
         bool hit = h == 1;
         if (h == 2) {
-            if (rq.q) {             // settled later; the traversal goes on as if this triangle missed
+            if (rq.q && item < 0x7fffffffLL) {   // settled later; the traversal goes on as if this triangle missed
                 const unsigned pos = atomicAdd(rq.cnt, 1u);
                 if (pos < (unsigned)rq.cap) {
                     rq.q[pos] = make_int4((int)item, j, i, 0);
@@ -1383,6 +1370,9 @@ __device__ __forceinline__ float4 local4(const Frame& fr, d3 v, float w)
 }
 
 
+// Receivers have a handful of paths each: a group of 8 lanes per receiver keeps most lanes busy.
+constexpr int kRecGroup = 8;
+
 // Per (Rx, path) record for the field kernel. FP64 only where the phase needs it: the receiver image
 // I (mirrored through the bounce planes in reverse order), w = I - c in the RIS frame, D0 = |w| and
 // frac(D0 / lambda); the normals, pattern axis and permittivities are FP32 (they enter amplitudes only).
@@ -1390,8 +1380,8 @@ __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n
                           AntD rxa, const int* __restrict__ cand, int cap, const int64_t* __restrict__ off,
                           const SeqEntry* __restrict__ seqs, PathRec* __restrict__ rec, int64_t* __restrict__ rec_seq)
 {
-    const int lane = threadIdx.x & 31;
-    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & (kRecGroup - 1);   // kRecGroup lanes per receiver, over its paths
+    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kRecGroup;
     if (r >= n_rx) return;
     const int64_t o = off[r];
     const int n = (int)(off[r + 1] - o);
@@ -1402,7 +1392,7 @@ __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n
     const float3 nn = f3((float)fr.n[0], (float)fr.n[1], (float)fr.n[2]);
     const float3 zr = f3((float)rxa.z[0], (float)rxa.z[1], (float)rxa.z[2]);
     auto local = [&](float3 v, float wv_) { return make_float4(dot(v, t1), dot(v, t2), dot(v, nn), wv_); };
-    for (int q = lane; q < n; q += 32) {
+    for (int q = lane; q < n; q += kRecGroup) {
         int k = 0;
         int fa[2] = {-1, -1};
         int64_t id = -1;
@@ -1446,7 +1436,7 @@ __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n
     }
 }
 
-// E0 per receiver (one warp): LOS (if unblocked) + environment paths (Eqs. 2-3 of the direct and
+// E0 per receiver (a group of kRecGroup lanes): LOS (if unblocked) + environment paths (Eqs. 2-3 of the direct and
 // reflected Tx -> Rx rays), each from its unfolded image source Ts. FP64 for the unfolded length L and
 // frac(L / lambda); FP32 for directions, Fresnel products, patterns and amplitudes. Fixed order: lane-
 // strided paths, then a shuffle tree.
@@ -1455,18 +1445,19 @@ __global__ void k_e0(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, 
                      const int64_t* __restrict__ cnt, const SeqEntry* __restrict__ seqs,
                      const SeqEntryD* __restrict__ seqd, float2* __restrict__ E0)
 {
-    const int lane = threadIdx.x & 31;
-    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (r >= n_rx) return;
+    const int lane = threadIdx.x & (kRecGroup - 1);   // kRecGroup lanes per receiver, over its paths
+    const int64_t r0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kRecGroup;
+    const bool live = r0 < n_rx;                      // every lane reaches the shuffles below
+    const int64_t r = live ? r0 : 0;
     const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
     const d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
     const float3 zt = f3((float)tx.z[0], (float)tx.z[1], (float)tx.z[2]);
     const float3 zr = f3((float)rxa.z[0], (float)rxa.z[1], (float)rxa.z[2]);
     const float gt = (float)tx.gain, gr = (float)rxa.gain;
     const float amp0 = (float)(sqrt(2.0 * kEta0 * tx.power * tx.gain) * sqrt(rxa.gain) * wv.lam / (4.0 * kPi));
-    const int n = cnt ? (int)cnt[r] : 0;
+    const int n = live ? (cnt ? (int)cnt[r] : 0) : -1;
     float are = 0.f, aim = 0.f;
-    for (int q = lane - 1; q < n; q += 32) {     // q = -1: LOS
+    for (int q = lane - 1; q < n; q += kRecGroup) {   // q = -1: LOS
         d3 Ts = T;
         int fa[2] = {-1, -1};
         int k = 0;
@@ -1508,11 +1499,11 @@ __global__ void k_e0(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, 
         are += t.re;
         aim += t.im;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        are += __shfl_down_sync(0xffffffffu, are, o);
-        aim += __shfl_down_sync(0xffffffffu, aim, o);
+    for (int o = kRecGroup / 2; o > 0; o >>= 1) {   // fixed order within the group
+        are += __shfl_down_sync(0xffffffffu, are, o, kRecGroup);
+        aim += __shfl_down_sync(0xffffffffu, aim, o, kRecGroup);
     }
-    if (lane == 0) E0[r] = make_float2(are, aim);
+    if (lane == 0 && live) E0[r] = make_float2(are, aim);
 }
 
 __global__ void k_los(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, AntD tx, float tol_base,
@@ -1729,19 +1720,19 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         ext = std::max(ext, std::fabs(ctx->tx.pos[k]));
         ext = std::max(ext, std::fabs(ris->center[k]));
     }
-    {   // receivers' extent (max |coordinate|) enters the FP32 error bound
-        unsigned* d_ext;
-        RISRT_CUDA(ctx, cudaMalloc(&d_ext, sizeof(unsigned)));
-        RISRT_CUDA(ctx, cudaMemsetAsync(d_ext, 0, sizeof(unsigned), s));
-        RISRT_KERNEL(ctx, "k_abs_max", (k_abs_max<<<std::min<unsigned>(nblk(3 * n_rx, 256), 1024u), 256, 0, s>>>(rxs->xyz, 3 * n_rx, d_ext)));
-        unsigned h_ext = 0;
-        cudaError_t e1 = cudaMemcpyAsync(&h_ext, d_ext, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-        cudaError_t e2 = cudaStreamSynchronize(s);
-        cudaFree(d_ext);
-        RISRT_CUDA(ctx, e1);
-        RISRT_CUDA(ctx, e2);
-        float rx_ext;
-        memcpy(&rx_ext, &h_ext, sizeof(float));
+    {   // receivers' extent (max |coordinate|) enters the FP32 error bound; an uploaded set keeps it
+        float rx_ext = rxs->owned ? rxs->ext : -1.f;
+        if (rx_ext < 0.f) {
+            if (!ctx->small) RISRT_CUDA(ctx, cudaMalloc(&ctx->small, 256));
+            unsigned* d_ext = (unsigned*)ctx->small;
+            RISRT_CUDA(ctx, cudaMemsetAsync(d_ext, 0, sizeof(unsigned), s));
+            RISRT_KERNEL(ctx, "k_abs_max", (k_abs_max<<<std::min<unsigned>(nblk(3 * n_rx, 256), 1024u), 256, 0, s>>>(rxs->xyz, 3 * n_rx, d_ext)));
+            unsigned h_ext = 0;
+            RISRT_CUDA(ctx, cudaMemcpyAsync(&h_ext, d_ext, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+            RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+            memcpy(&rx_ext, &h_ext, sizeof(float));
+            if (rxs->owned) rxs->ext = rx_ext;
+        }
         ext = std::max(ext, rx_ext);
     }
     const float tol_base = 4e-6f * (1.f + 3.f * ext);
@@ -1801,13 +1792,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             int64_t* occ_off64[2];
             int* occ_off[2];
             int* occ_cursor[2];
-            int *dense_r2, *dense_slot2;
-            int64_t* face_off64;
             uint32_t *rx_keys, *rx_order_u;
             void* rx_sort_tmp;
             unsigned* rx_bb;
             int* rx_order;
             unsigned long long* dense_cnt;   // entries of the work list written by the candidate search
+            int64_t* seq_n;                  // sizes of the three sequence tables
             float4* sp_box;          // super-patch boxes [n_super][2]
             unsigned* sp_mask;       // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
             int* sp_list;            // [n_super][32 ceil(n_seq / 32)] the same as index lists
@@ -1852,11 +1842,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.rx_order_u = A.get<uint32_t>(n_rx);
             L.rx_sort_tmp = A.get<char>(sort_temp_bytes(n_rx));
             L.rx_bb = A.get<unsigned>(8);
-            L.dense_r2 = A.get<int>((size_t)n_rx * cap);
-            L.dense_slot2 = A.get<int>((size_t)n_rx * cap);
-            L.face_off64 = A.get<int64_t>(F + 1);
             const int64_t n_super = (n_rx + kSuperRx - 1) / kSuperRx;
             L.dense_cnt = A.get<unsigned long long>(1);
+            L.seq_n = A.get<int64_t>(3);
             L.sp_box = A.get<float4>((size_t)n_super * 2);
             L.sp_mask = A.get<unsigned>((size_t)n_super * ((n_ids_max + 31) / 32 + 1));
             L.sp_list = A.get<int>((size_t)n_super * ((n_ids_max + 31) / 32 + 1) * 32);
@@ -1899,20 +1887,20 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         const d3 Cpos = D3(fr.c[0], fr.c[1], fr.c[2]);
         const int64_t n_ids_of[3] = {n_ids_tx, n_ids_rx, n_ids_env};
         const d3 src_of[3] = {Tpos, Cpos, Tpos};
+        RISRT_CUDA(ctx, cudaMemsetAsync(L.seq_n, 0, sizeof(int64_t) * 3, s));
         for (int i = 0; i < 3; ++i) {
-            tab[i].n = 0;
             int64_t nid = n_ids_of[i];
             if (nid == 0) continue;
             RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(nid, 256), 256, 0, s>>>(S, nid, i, fr, src_of[i], 1e-4f * (1.f + ext), flag)));
             RISRT_CUDA(ctx, exclusive_scan_i64(flag, pos, nid, scan_tmp, s));
             RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(nid, 256), 256, 0, s>>>(S, nid, flag, pos, src_of[i], tab[i].e, tab[i].d)));
-            int64_t n_allowed = 0;
-            int64_t last[2];
-            RISRT_CUDA(ctx, cudaMemcpyAsync(&last[0], pos + nid - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            RISRT_CUDA(ctx, cudaMemcpyAsync(&last[1], flag + nid - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            RISRT_KERNEL(ctx, "k_seq_count", (k_seq_count<<<1, 32, 0, s>>>(flag, pos, nid, L.seq_n + i)));
+        }
+        {   // the three table sizes in one read-back
+            int64_t n_allowed[3];
+            RISRT_CUDA(ctx, cudaMemcpyAsync(n_allowed, L.seq_n, sizeof(n_allowed), cudaMemcpyDeviceToHost, s));
             RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-            n_allowed = last[0] + last[1];
-            tab[i].n = (int)n_allowed;
+            for (int i = 0; i < 3; ++i) tab[i].n = (int)n_allowed[i];
         }
 
         // occluder lists of the first segments, from the Tx (Tx leg, environment) and the RIS centre
@@ -1995,49 +1983,30 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 }
                 RISRT_KERNEL(ctx, "k_refine_cand", (k_refine_cand<<<ctx->sm_count * 2, 256, 0, s>>>(
                                                        S, dst, src, t.e, t.d, rq, cs.cand, cs.cnt, cs.cap, flags_dev, counters, dl)));
-                // dense candidate list (written above for many destinations), then persistent validation
-                long long total = 0;
-                if (dl.r) {
-                    RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_cnt, sizeof(long long), cudaMemcpyDeviceToHost, s));
-                } else {
+                // dense candidate list (written above for many destinations), then persistent validation;
+                // its length stays on the device (no host round trip)
+                const long long* d_total = (const long long*)L.dense_cnt;
+                if (!dl.r) {
                     RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, s>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
                     RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, n_dst + 1, scan_tmp, s));
                     RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, s>>>(cs.cnt, L.dense_off, n_dst, cs.cap,
                                                                                                        L.dense_r, L.dense_slot)));
-                    RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + n_dst, sizeof(long long), cudaMemcpyDeviceToHost, s));
+                    d_total = (const long long*)(L.dense_off + n_dst);
                 }
                 RISRT_CUDA(ctx, cudaMemsetAsync(counters + 6, 0, sizeof(unsigned long long), s));
-                RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-                int *vr = L.dense_r, *vs = L.dense_slot;
-                if (RISRT_GROUP_BY_FACE && total > 0 && occ_off_src[occ]) {   // group by first face (list coherence)
-                    int* hist = L.occ_cnt[occ];
-                    RISRT_CUDA(ctx, cudaMemsetAsync(hist, 0, sizeof(int) * (F + 1), s));
-                    RISRT_CUDA(ctx, cudaMemsetAsync(L.occ_cursor[occ], 0, sizeof(int) * (F + 1), s));
-                    RISRT_KERNEL(ctx, "k_face_hist", (k_face_hist<<<nblk(total, 256), 256, 0, s>>>(t.e, cs.cand, cs.cap, L.dense_r,
-                                                                                              L.dense_slot, total, hist)));
-                    RISRT_KERNEL(ctx, "k_i32_scan_prep", (k_i32_scan_prep<<<nblk(F + 1, 256), 256, 0, s>>>(hist, F, L.face_off64)));
-                    RISRT_CUDA(ctx, exclusive_scan_i64(L.face_off64, L.face_off64, F + 1, scan_tmp, s));
-                    RISRT_KERNEL(ctx, "k_face_scatter", (k_face_scatter<<<nblk(total, 256), 256, 0, s>>>(
-                                                            t.e, cs.cand, cs.cap, L.dense_r, L.dense_slot, total,
-                                                            L.face_off64, L.occ_cursor[occ], L.dense_r2, L.dense_slot2)));
-                    vr = L.dense_r2;
-                    vs = L.dense_slot2;
-                }
-                if (total > 0) {
-                    // the validation queue reuses the buffer (the candidate settlements are done); item ids are int
-                    const RefineQ vq{total < ((long long)1 << 31) ? L.rq : nullptr, rq_cap, L.rq_cnt + 1};
-                    RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<nblk(total, 256), 256, 0, s>>>(
-                                                           dst, t.e, cs.cand, cs.cap, vr, vs, total, L.dense_pts)));
-                    const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * RISRT_VALIDATE_MINB,
-                                                                          (total + kValThreads - 1) / kValThreads);
-                    RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
-                                                        S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
-                                                        vs, L.dense_pts, total, counters + 6, tol_base, counters, flags_dev + 1,
-                                                        counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq,
-                                                        n_dst > 1 && use_maps ? L.smap[occ] : nullptr)));
-                    RISRT_KERNEL(ctx, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, s>>>(
-                                                          S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
-                }
+                const int *vr = L.dense_r, *vs = L.dense_slot;
+                // the validation queue reuses the buffer (the candidate settlements are done)
+                const RefineQ vq{L.rq, rq_cap, L.rq_cnt + 1};
+                RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<ctx->sm_count * 32, 256, 0, s>>>(
+                                                       dst, t.e, cs.cand, cs.cap, vr, vs, d_total, L.dense_pts)));
+                const unsigned blocks = (unsigned)ctx->sm_count * RISRT_VALIDATE_MINB;
+                RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
+                                                    S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
+                                                    vs, L.dense_pts, d_total, counters + 6, tol_base, counters, flags_dev + 1,
+                                                    counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq,
+                                                    n_dst > 1 && use_maps ? L.smap[occ] : nullptr)));
+                RISRT_KERNEL(ctx, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, s>>>(
+                                                      S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
             }
             const int warps = 4;
             size_t shm = sizeof(int) * (size_t)cs.cap * warps;
@@ -2118,9 +2087,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         if ((rc = grow(ctx, &ps->env_seq, &ps->cap_env, std::max<int64_t>(n_env, 1)))) return rc;
         ps->n_paths = n_paths;
         ps->n_env = n_env;
-        RISRT_KERNEL(ctx, "k_records", (k_records<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
+        RISRT_KERNEL(ctx, "k_records", (k_records<<<nblk(n_rx * kRecGroup, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
                                                       tab[1].e, ps->rec, ps->rx_seq)));
-        RISRT_KERNEL(ctx, "k_e0", (k_e0<<<nblk(n_rx * 32, 128), 128, 0, s>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand, cenv.cap,
+        RISRT_KERNEL(ctx, "k_e0", (k_e0<<<nblk(n_rx * kRecGroup, 128), 128, 0, s>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand, cenv.cap,
                                                  env ? cenv.cnt64 : nullptr, tab[2].e, tab[2].d, ps->E0)));
         if (env && n_env > 0) {
             RISRT_KERNEL(ctx, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, s>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off, n_rx, tab[2].e, ps->env_seq)));
@@ -2301,11 +2270,13 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
         if (host_flags[0]) return fail(ctx, RISRT_ERR_CAPACITY, "more than 4096 geometric candidates");
         if (total > 0) {
             RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<nblk(total, 256), 256, 0, s>>>(
-                                                   L.dst, L.e, L.cand, cap, L.dense_r, L.dense_slot, total, L.dense_pts)));
+                                                   L.dst, L.e, L.cand, cap, L.dense_r, L.dense_slot,
+                                                   (const long long*)(L.dense_off + 1), L.dense_pts)));
             const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * 8, (total + kValThreads - 1) / kValThreads);
             RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                 S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
-                                                L.dense_slot, L.dense_pts, total, L.counters + 6, tol_base, L.counters,
+                                                L.dense_slot, L.dense_pts, (const long long*)(L.dense_off + 1), L.counters + 6,
+                                                tol_base, L.counters,
                                                 L.flags + 1, L.counters + 2, nullptr, nullptr, RefineQ{nullptr, 0, nullptr},
                                                 nullptr)));
         }
