@@ -383,9 +383,28 @@ int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris*
     return RISRT_OK;
 }
 
+// Waits for the trace that filled ps and brings its device-side statistics to the host (once).
+static int pathset_sync(const risrt_pathset* ps)
+{
+    if (ps->stream && cudaStreamSynchronize(ps->stream) != cudaSuccess) return RISRT_ERR_CUDA;
+    if (ps->stats_pending) {
+        unsigned long long c[6];
+        if (cudaMemcpy(c, ps->ctr_dev, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+        ps->fp64_refines = (int64_t)c[0];
+        ps->units = (int64_t)c[1];
+        ps->n_candidates = (int64_t)c[2];
+        ps->n_segments = (int64_t)c[3];
+        ps->node_visits = (int64_t)c[4];
+        ps->tri_tests = (int64_t)c[5];
+        ps->stats_pending = false;
+    }
+    return RISRT_OK;
+}
+
 int risrt_pathset_stats_get(const risrt_pathset* ps, risrt_pathset_stats* out)
 {
     if (!ps || !out) return RISRT_ERR_INVALID_ARG;
+    if (int rc = pathset_sync(ps)) return rc;
     out->n_rx = ps->n_rx;
     out->M = ps->M;
     out->n_faces = ps->n_faces;
@@ -406,6 +425,7 @@ int risrt_pathset_export(const risrt_pathset* ps, int32_t* rx_count_host, int64_
                          uint8_t* tx_vis_host)
 {
     if (!ps) return RISRT_ERR_INVALID_ARG;
+    if (int rc = pathset_sync(ps)) return rc;
     const int64_t n = ps->n_rx;
     std::vector<int64_t> off(n + 1), eoff(n + 1);
     if (cudaMemcpy(off.data(), ps->rx_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
@@ -566,6 +586,7 @@ int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps)
     cudaFree(ps->rec); cudaFree(ps->rx_off); cudaFree(ps->vis); cudaFree(ps->E0); cudaFree(ps->cm);
     cudaFree(ps->elem); cudaFree(ps->rx_seq); cudaFree(ps->env_seq); cudaFree(ps->env_off); cudaFree(ps->los);
     cudaFree(ps->scratch);
+    cudaFree(ps->ctr_dev);
     cudaFree(ps->occ_idx[0]);
     cudaFree(ps->occ_idx[1]);
     delete ps;

@@ -248,9 +248,14 @@ struct risrt_pathset {
     uint8_t* los = nullptr;          // [n_rx]
     std::vector<int64_t> tx_seq_host;
     std::vector<uint8_t> tx_vis_host;
-    int64_t units = 0;
-    int64_t fp64_refines = 0;
-    int64_t n_candidates = 0, n_segments = 0, node_visits = 0, tri_tests = 0;
+    // statistics: counted on the device, fetched when first asked for (the trace does not wait)
+    mutable int64_t units = 0;
+    mutable int64_t fp64_refines = 0;
+    mutable int64_t n_candidates = 0, n_segments = 0, node_visits = 0, tri_tests = 0;
+    unsigned long long* ctr_dev = nullptr;   // [6] copy of the trace's counters
+    mutable bool stats_pending = false;
+    cudaStream_t stream = nullptr;           // stream of the trace that filled this set
+    int64_t cap_rx_seq = 0;
     int64_t cap_rx = 0;              // capacity of the per-Rx arrays
     // scratch (grown as needed, kept for reuse)
     void* scratch = nullptr;

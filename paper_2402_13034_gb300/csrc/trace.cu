@@ -1293,9 +1293,11 @@ __device__ __forceinline__ float3 mirror_dir_f(float3 v, float3 n) { return v - 
 // frac(L / lambda), FP32 for directions, Fresnel products and patterns (they enter amplitudes only);
 // fixed reduction order (lane-strided paths, shuffle tree).
 __global__ void k_cm(DeviceScene S, const float4* __restrict__ elem, int M, Frame fr, AntD tx, WaveD wv, double K,
-                     const uint8_t* __restrict__ tx_vis, const int* __restrict__ tx_seq, int n_tx,
-                     const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, float2* __restrict__ cm)
+                     const uint8_t* __restrict__ tx_vis, const int* __restrict__ tx_seq,
+                     const int64_t* __restrict__ n_tx_dev, const SeqEntry* __restrict__ seqs,
+                     const SeqEntryD* __restrict__ seqd, float2* __restrict__ cm)
 {
+    const int n_tx = (int)*n_tx_dev;
     const int lane = threadIdx.x & 31;
     const int m = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (m >= M) return;
@@ -1353,6 +1355,14 @@ __global__ void k_cm(DeviceScene S, const float4* __restrict__ elem, int M, Fram
         aim += __shfl_down_sync(0xffffffffu, aim, o);
     }
     if (lane == 0) cm[m] = make_float2((float)(K * are), (float)(K * aim));
+}
+
+// Sequence ids of the Tx-leg paths (for the host copy of the path set).
+__global__ void k_tx_ids(const int* __restrict__ cand, const int64_t* __restrict__ n_dev, int cap,
+                         const SeqEntry* __restrict__ seqs, int64_t* __restrict__ ids)
+{
+    const int n = (int)min(*n_dev, (int64_t)cap);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ids[i] = seqs[cand[i]].info.z;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1798,6 +1808,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             int* rx_order;
             unsigned long long* dense_cnt;   // entries of the work list written by the candidate search
             int64_t* seq_n;                  // sizes of the three sequence tables
+            int64_t* tx_ids;                 // [cap] sequence ids of the Tx-leg paths
             float4* sp_box;          // super-patch boxes [n_super][2]
             unsigned* sp_mask;       // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
             int* sp_list;            // [n_super][32 ceil(n_seq / 32)] the same as index lists
@@ -1845,6 +1856,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             const int64_t n_super = (n_rx + kSuperRx - 1) / kSuperRx;
             L.dense_cnt = A.get<unsigned long long>(1);
             L.seq_n = A.get<int64_t>(3);
+            L.tx_ids = A.get<int64_t>((size_t)cap);
             L.sp_box = A.get<float4>((size_t)n_super * 2);
             L.sp_mask = A.get<unsigned>((size_t)n_super * ((n_ids_max + 31) / 32 + 1));
             L.sp_list = A.get<int>((size_t)n_super * ((n_ids_max + 31) / 32 + 1) * 32);
@@ -2034,41 +2046,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                                              tol_base, ps->vis, counters, flags_dev + 1, L.rx_state)));
             RISRT_KERNEL(ctx, "k_los", (k_los<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1)));
         }
-        int host_flags[2];
-        RISRT_CUDA(ctx, cudaMemcpyAsync(host_flags, flags_dev, sizeof(host_flags), cudaMemcpyDeviceToHost, s));
-        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-        if (host_flags[1]) return fail(ctx, RISRT_ERR_CAPACITY, "BVH traversal stack overflow");
-        if (host_flags[0]) {       // a destination had more geometric candidates than slots: retry
-            cap *= 4;
-            ps->cand_cap = cap;
-            continue;
-        }
-
-        // Tx-leg results to the host (small)
-        int64_t n_tx64 = 0;
-        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_tx64, ctx_leg.cnt64, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-        const int n_tx = (int)n_tx64;
-        std::vector<int> tx_idx(n_tx);
-        if (n_tx) RISRT_CUDA(ctx, cudaMemcpyAsync(tx_idx.data(), ctx_leg.cand, sizeof(int) * n_tx, cudaMemcpyDeviceToHost, s));
-        ps->tx_vis_host.resize(M);
-        RISRT_CUDA(ctx, cudaMemcpyAsync(ps->tx_vis_host.data(), tx_vis, M, cudaMemcpyDeviceToHost, s));
-        std::vector<SeqEntry> tx_entries(n_tx);
-        for (int i = 0; i < n_tx; ++i)
-            RISRT_CUDA(ctx, cudaMemcpyAsync(&tx_entries[i], tab[0].e + tx_idx[i], sizeof(SeqEntry), cudaMemcpyDeviceToHost, s));
-        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-        ps->tx_seq_host.resize(n_tx);
-        for (int i = 0; i < n_tx; ++i) ps->tx_seq_host[i] = tx_entries[i].info.z;
-
-        // c_m
-        RISRT_KERNEL(ctx, "k_cm", (k_cm<<<nblk((int64_t)M * 32, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand, n_tx, tab[0].e, tab[0].d, ps->cm)));
-
-        // Rx-leg offsets and records
+        // c_m (its path count stays on the device), Tx-leg ids, Rx-leg and environment offsets
+        RISRT_KERNEL(ctx, "k_cm", (k_cm<<<nblk((int64_t)M * 32, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand,
+                                                                                 ctx_leg.cnt64, tab[0].e, tab[0].d, ps->cm)));
+        RISRT_KERNEL(ctx, "k_tx_ids", (k_tx_ids<<<1, 256, 0, s>>>(ctx_leg.cand, ctx_leg.cnt64, cap, tab[0].e, L.tx_ids)));
         RISRT_KERNEL(ctx, "k_count_total", (k_count_total<<<nblk(n_rx, 256), 256, 0, s>>>(crx.cnt64, n_rx, tot)));
         RISRT_CUDA(ctx, cudaMemsetAsync(tot + n_rx, 0, sizeof(int64_t), s));
         RISRT_CUDA(ctx, exclusive_scan_i64(tot, ps->rx_off, n_rx + 1, scan_tmp, s));
-        int64_t n_paths = 0;
-        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_paths, ps->rx_off + n_rx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         if (env) {
             RISRT_CUDA(ctx, cudaMemcpyAsync(env_cnt_tot, cenv.cnt64, sizeof(int64_t) * n_rx, cudaMemcpyDeviceToDevice, s));
             RISRT_CUDA(ctx, cudaMemsetAsync(env_cnt_tot + n_rx, 0, sizeof(int64_t), s));
@@ -2076,14 +2060,30 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         } else {
             RISRT_CUDA(ctx, cudaMemsetAsync(ps->env_off, 0, sizeof(int64_t) * (n_rx + 1), s));
         }
-        int64_t n_env = 0;
+        // one read-back: error flags, path counts, Tx-leg ids and visibility
+        int host_flags[2];
+        int64_t n_tx64 = 0, n_paths = 0, n_env = 0;
+        std::vector<int64_t> tx_ids_host(cap);
+        ps->tx_vis_host.resize(M);
+        RISRT_CUDA(ctx, cudaMemcpyAsync(host_flags, flags_dev, sizeof(host_flags), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_tx64, ctx_leg.cnt64, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n_paths, ps->rx_off + n_rx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         RISRT_CUDA(ctx, cudaMemcpyAsync(&n_env, ps->env_off + n_rx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(tx_ids_host.data(), L.tx_ids, sizeof(int64_t) * cap, cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(ps->tx_vis_host.data(), tx_vis, M, cudaMemcpyDeviceToHost, s));
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        if (host_flags[1]) return fail(ctx, RISRT_ERR_CAPACITY, "BVH traversal stack overflow");
+        if (host_flags[0]) {       // a destination had more geometric candidates than slots: retry
+            cap *= 4;
+            ps->cand_cap = cap;
+            continue;
+        }
+        const int n_tx = (int)std::min<int64_t>(n_tx64, cap);
+        ps->tx_seq_host.assign(tx_ids_host.begin(), tx_ids_host.begin() + n_tx);
+
+        // Rx-leg records, E0, environment ids
         if ((rc = grow(ctx, &ps->rec, &ps->cap_paths, n_paths))) return rc;
-        int64_t cap_seq = ps->cap_paths;
-        if (ps->rx_seq) cudaFree(ps->rx_seq);
-        ps->rx_seq = nullptr;
-        RISRT_CUDA(ctx, cudaMalloc(&ps->rx_seq, sizeof(int64_t) * std::max<int64_t>(cap_seq, 1)));
+        if ((rc = grow(ctx, &ps->rx_seq, &ps->cap_rx_seq, std::max<int64_t>(n_paths, 1)))) return rc;
         if ((rc = grow(ctx, &ps->env_seq, &ps->cap_env, std::max<int64_t>(n_env, 1)))) return rc;
         ps->n_paths = n_paths;
         ps->n_env = n_env;
@@ -2095,15 +2095,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_KERNEL(ctx, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, s>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off, n_rx, tab[2].e, ps->env_seq)));
         }
         RISRT_KERNEL(ctx, "k_units", (k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1)));
-        unsigned long long host_ctr[6];
-        RISRT_CUDA(ctx, cudaMemcpyAsync(host_ctr, counters, sizeof(host_ctr), cudaMemcpyDeviceToHost, s));
-        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-        ps->fp64_refines = (int64_t)host_ctr[0];
-        ps->units = (int64_t)host_ctr[1];
-        ps->n_candidates = (int64_t)host_ctr[2];
-        ps->n_segments = (int64_t)host_ctr[3];
-        ps->node_visits = (int64_t)host_ctr[4];
-        ps->tri_tests = (int64_t)host_ctr[5];
+        // statistics stay on the device until asked for (risrt_pathset_stats_get waits for them)
+        if (!ps->ctr_dev) RISRT_CUDA(ctx, cudaMalloc(&ps->ctr_dev, sizeof(unsigned long long) * 6));
+        RISRT_CUDA(ctx, cudaMemcpyAsync(ps->ctr_dev, counters, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToDevice, s));
+        ps->stats_pending = true;
+        ps->stream = s;
         return RISRT_OK;
     }
     return fail(ctx, RISRT_ERR_CAPACITY, "too many geometric path candidates per receiver");
