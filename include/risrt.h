@@ -282,6 +282,11 @@ int risrt_find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* scene, const flo
  * elapsed time per kernel name (adds two event records per launch; off by default). */
 int risrt_profile_enable(risrt_ctx* ctx, int on);
 
+/* Restrict the profiling of risrt_profile_enable to the kernels named `name` (NULL or "" for all),
+ * so that a timed run brackets only the kernel it reports on. Returns RISRT_ERR_INVALID_ARG for a
+ * NULL context. */
+int risrt_profile_only(risrt_ctx* ctx, const char* name);
+
 /* Total elapsed milliseconds and launch count of kernel `name` since the last reset, or of all
  * kernels when name is NULL. Synchronises the pending events. Unknown names give 0 and 0. */
 int risrt_profile_query(risrt_ctx* ctx, const char* name, double* total_ms, int64_t* launches);

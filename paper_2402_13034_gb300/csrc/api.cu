@@ -24,6 +24,11 @@ std::atomic<long long> g_launches{0};
 void prof_begin(risrt_ctx* ctx, const char* name)
 {
     if (!ctx || !ctx->profiling) return;
+    if (!ctx->prof_only.empty() && ctx->prof_only != name) {
+        ctx->prof_skip = true;
+        return;
+    }
+    ctx->prof_skip = false;
     KernelPending p;
     p.name = name;
     for (cudaEvent_t* ev : {&p.a, &p.b}) {
@@ -40,7 +45,7 @@ void prof_begin(risrt_ctx* ctx, const char* name)
 
 void prof_end(risrt_ctx* ctx)
 {
-    if (!ctx || !ctx->profiling || ctx->pending.empty()) return;
+    if (!ctx || !ctx->profiling || ctx->prof_skip || ctx->pending.empty()) return;
     cudaEventRecord(ctx->pending.back().b, ctx->stream);
 }
 
@@ -134,6 +139,13 @@ int risrt_profile_enable(risrt_ctx* ctx, int on)
 {
     RISRT_CHECK_CTX(ctx);
     ctx->profiling = on != 0;
+    return RISRT_OK;
+}
+
+int risrt_profile_only(risrt_ctx* ctx, const char* name)
+{
+    RISRT_CHECK_CTX(ctx);
+    ctx->prof_only = name ? name : "";
     return RISRT_OK;
 }
 

@@ -164,6 +164,8 @@ struct risrt_ctx {
     Antenna tx{}, rx{};
     // tracing
     bool profiling = false;
+    std::string prof_only;       // non-empty: only kernels of this name are bracketed
+    bool prof_skip = false;      // the launch being bracketed is not one of them
     std::vector<KernelPending> pending;
     std::vector<cudaEvent_t> event_pool;
     std::map<std::string, std::pair<double, int64_t>> ktime;

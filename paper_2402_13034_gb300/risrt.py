@@ -50,6 +50,7 @@ _SIGS = {
     "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
                                            C.POINTER(C.c_int32)]),
     "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
+    "risrt_profile_only": (C.c_int, [_P, C.c_char_p]),
     "risrt_profile_query": (C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "risrt_profile_names": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "risrt_profile_reset": (C.c_int, [_P]),
@@ -222,6 +223,10 @@ class Context:
     # --- tracing -------------------------------------------------------------------------------
     def profile_enable(self, on: bool = True):
         self._check(load().risrt_profile_enable(self._ptr, int(on)))
+
+    def profile_only(self, name=None):
+        """Bracket only the kernels called `name` while profiling (None: all kernels)."""
+        self._check(load().risrt_profile_only(self._ptr, name.encode() if name else None))
 
     def profile_reset(self):
         self._check(load().risrt_profile_reset(self._ptr))
