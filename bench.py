@@ -107,21 +107,30 @@ def bench_gradient(ctx, R, dev, steps=200, reps=5):
     ctx.build_A(ps, A, E0)
     phases = torch.from_numpy(w.extra["phases"]).to(dev)
     Bn = phases.shape[0]
-    obj = PhaseObjective(ctx, A, E0)
     J = torch.empty(Bn, device=dev)
     g = torch.empty((Bn, M), device=dev)
-    ws = obj.workspace(Bn)
-    ctx.grad_phases(A, E0, None, phases, None, J, g, ws)
     stream = torch.cuda.current_stream(dev)
-    ts = []
-    for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ctx.grad_phases(A, E0, None, phases, None, J, g, ws)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    ms = float(np.median(ts))
+    per_prec = {}
+    # FP32 CUDA cores; split-BF16 tensor cores packing A on every call; the same with A kept packed
+    # (the ascent's steady state: only the phase-dependent operands are rebuilt)
+    for key, prec, keep in (("fp32", 0, False), ("bf16x2_cold", 2, False), ("bf16x2", 2, True)):
+        o = PhaseObjective(ctx, A, E0, precision=prec)
+        ws = o.workspace(Bn)
+        ctx.grad_phases(A, E0, None, phases, None, J, g, ws, prec)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.grad_phases(A, E0, None, phases, None, J, g, ws, prec, keep_a=keep)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        per_prec[key] = float(np.median(ts))
+        del ws, o
+    ms = per_prec["bf16x2"]
+    obj = PhaseObjective(ctx, A, E0, precision=2)
+    ascend(obj, phases, steps=2, lr=0.05)        # first use of autograd and Adam (one-time set-up)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, hist = ascend(obj, phases, steps=steps, lr=0.05)
     torch.cuda.synchronize()
@@ -131,9 +140,11 @@ def bench_gradient(ctx, R, dev, steps=200, reps=5):
     flop = 2 * 8.0 * n * M * Bn
     out = {"workload": w.name, "triangles": int(len(w.scene.tris)), "elements": M, "targets": n, "configs": Bn,
            "trace_s": t_trace, "rx_paths": st.n_rx_paths, "ms_per_grad_step": ms,
+           "precision": "bf16x2 (split BF16, tensor cores, A kept packed)",
+           "ms_per_grad_step_packing_A": per_prec["bf16x2_cold"], "ms_per_grad_step_fp32": per_prec["fp32"],
            "tflops": flop / (ms / 1e3) / 1e12, "A_bytes_read_per_step": 2 * n * M * 8,
            "hbm_GBps_equiv": 2 * n * M * 8 / (ms / 1e3) / 1e9, "ascent_steps": steps,
-           "ascent_s": t_asc, "J_mean_start": float(h[0].mean()), "J_mean_end": float(h[-1].mean()),
+           "ascent_s": t_asc, "ascent_ms_per_step": t_asc / steps * 1e3, "J_mean_start": float(h[0].mean()), "J_mean_end": float(h[-1].mean()),
            "J_gain_db_per_rx": float((h[-1].mean() - h[0].mean()) / n * 10 / np.log(10))}
     for hh in (ps, rx, ris, scene):
         hh.close()

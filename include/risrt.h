@@ -232,8 +232,15 @@ int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t
  * Phase gradient (adjoint of Eq. 9 and Eq. 10)
  * ---------------------------------------------------------------------------------------------- */
 
-/* Workspace bytes for risrt_grad_phases (n_target receivers, B configurations, M elements). */
-int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, size_t* bytes);
+/* Workspace bytes for risrt_grad_phases (n_target receivers, B configurations, M elements) at the
+ * given precision (RISRT_PREC_FP32 or RISRT_PREC_BF16X2; anything else: RISRT_ERR_INVALID_ARG). */
+int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precision, size_t* bytes);
+
+/* OR-ed into the precision of risrt_grad_phases with RISRT_PREC_BF16X2: the caller states that A, E0,
+ * target and the sizes are those of the previous call with this workspace, whose packed copies of A
+ * are then reused (only the phase-dependent operands are rebuilt). Results are undefined if they
+ * changed. Ignored for RISRT_PREC_FP32. */
+#define RISRT_GRAD_KEEP_A 0x100
 
 /* For B phase configurations Gamma_bm = amp_m e^{j phases[b][m]}:
  *   J[b]       = sum_{t} log P_b(target[t]),  P = |E0 + A Gamma_b|^2 / (2 eta0)
@@ -242,13 +249,18 @@ int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, size_t* by
  *   A [n_rx][M] complex64, E0 [n_rx] complex64 or NULL, target [n_target] int32 rows of A
  *   (NULL: rows 0..n_target-1), phases [B][M] float, amp [M] float or NULL (1), J_out [B] float,
  *   grad_out [B][M] float, workspace of risrt_grad_workspace_size bytes. All device memory.
- * FP32 arithmetic, A read twice (forward and adjoint GEMM, each split over its reduction axis with the
- * partial sums added in a fixed order, so results do not depend on scheduling). Synchronises the stream (the target
- * rows are validated on the device). Errors: RISRT_ERR_INVALID_ARG (sizes, a target row outside
- * [0, n_rx)). */
+ * precision RISRT_PREC_FP32: FP32 arithmetic on the CUDA cores, A read twice (forward and adjoint
+ * GEMM, each split over its reduction axis with the partial sums added in a fixed order, so results
+ * do not depend on scheduling). RISRT_PREC_BF16X2: both GEMMs on the tensor cores as real BF16 GEMMs
+ * in which every factor is split into a high and a low BF16 part (three products per pair, about
+ * 1e-5 relative), FP32 accumulation, partial sums again added in a fixed order; A's target rows are
+ * packed into the two operands on every call. The workspace must be 256-byte aligned. Synchronises
+ * the stream (the target rows are validated on the device). Errors: RISRT_ERR_INVALID_ARG (sizes,
+ * precision, a target row outside [0, n_rx)); RISRT_ERR_NOT_READY (the paired tensor-core kernel
+ * cannot run on this device); RISRT_ERR_TIMEOUT (a pipeline wait in the tensor-core kernel expired). */
 int risrt_grad_phases(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M,
                       const int32_t* target, int32_t n_target, const float* phases, const float* amp,
-                      int32_t B, float* J_out, float* grad_out, void* workspace, size_t workspace_bytes);
+                      int32_t B, float* J_out, float* grad_out, void* workspace, size_t workspace_bytes, int precision);
 
 /* ------------------------------------------------------------------------------------------------
  * Allocation-free path search (this entry point has no counterpart in the paper; it exists for

@@ -15,8 +15,11 @@ class RISLogPower(torch.autograd.Function):
         B, M = phases.shape
         J = torch.empty(B, dtype=torch.float32, device=phases.device)
         grad = torch.empty((B, M), dtype=torch.float32, device=phases.device)
+        ws = objective.workspace(B)
+        keep = objective.precision == 2 and objective._packed.get(B, False)   # A was packed by an earlier call
         objective.lib.grad_phases(objective.A, objective.E0, objective.target, phases, objective.amp, J, grad,
-                                  objective.workspace(B))
+                                  ws, objective.precision, keep_a=keep)
+        objective._packed[B] = True
         ctx.save_for_backward(grad)
         return J
 
@@ -28,16 +31,19 @@ class RISLogPower(torch.autograd.Function):
 
 class PhaseObjective:
     """Binds a channel matrix A [n_rx, M] (complex64), E0 [n_rx], target rows (int32) and element
-    amplitudes to the differentiable objective."""
+    amplitudes to the differentiable objective. They must not change while the objective is in use:
+    the tensor-core path packs A once per workspace and reuses it."""
 
-    def __init__(self, lib_ctx, A, E0=None, target=None, amp=None):
+    def __init__(self, lib_ctx, A, E0=None, target=None, amp=None, precision=0):
         self.lib, self.A, self.E0, self.target, self.amp = lib_ctx, A, E0, target, amp
+        self.precision = precision      # 0: FP32 CUDA cores, 2: split-BF16 tensor cores
         self._ws = {}
+        self._packed = {}               # per B: the workspace holds A packed for the tensor-core path
 
     def workspace(self, B: int):
         if B not in self._ws:
             n_t = self.target.numel() if self.target is not None else self.A.shape[0]
-            self._ws[B] = self.lib.grad_workspace(n_t, B, self.A.shape[1])
+            self._ws[B] = self.lib.grad_workspace(n_t, B, self.A.shape[1], self.precision)
         return self._ws[B]
 
     def __call__(self, phases):

@@ -506,29 +506,35 @@ int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t
                          workspace, workspace_bytes);
 }
 
-int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, size_t* bytes)
+int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precision, size_t* bytes)
 {
     if (!bytes || n_target < 1 || B < 1 || M < 1) return RISRT_ERR_INVALID_ARG;
-    *bytes = grad_workspace_bytes(n_target, B, M) + 64;
+    if (precision != RISRT_PREC_FP32 && precision != RISRT_PREC_BF16X2) return RISRT_ERR_INVALID_ARG;
+    *bytes = grad_workspace_bytes(n_target, B, M, precision) + 64;
     return RISRT_OK;
 }
 
 int risrt_grad_phases(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M, const int32_t* target,
                       int32_t n_target, const float* phases, const float* amp, int32_t B, float* J_out, float* grad_out,
-                      void* workspace, size_t workspace_bytes)
+                      void* workspace, size_t workspace_bytes, int precision)
 {
     RISRT_CHECK_CTX(ctx);
     if (!A || !phases || !J_out || !grad_out || !workspace) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
     if (n_rx < 1 || M < 1 || M > 65536 || n_target < 1 || B < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
+    const bool keep_a = (precision & RISRT_GRAD_KEEP_A) != 0;
+    precision &= ~RISRT_GRAD_KEEP_A;
+    if (precision != RISRT_PREC_FP32 && precision != RISRT_PREC_BF16X2)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "precision must be RISRT_PREC_FP32 or RISRT_PREC_BF16X2");
     if (!target && n_target > n_rx) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_target > n_rx without a target list");
-    if (workspace_bytes < grad_workspace_bytes(n_target, B, M) + 64) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace too small");
+    if (workspace_bytes < grad_workspace_bytes(n_target, B, M, precision) + 64) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace too small");
+    if (((uintptr_t)workspace) & 255u) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace not 256-byte aligned");
     if (((uintptr_t)A | (uintptr_t)E0 | (uintptr_t)workspace) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "misaligned array");
-    if (target) {
+    if (target && !keep_a) {
         int rc = check_targets(ctx, target, n_target, n_rx, workspace, workspace_bytes);
         if (rc) return rc;
     }
     int rc = grad_phases(ctx, (const float2*)A, (const float2*)E0, M, target, n_target, phases, amp, B, J_out, grad_out,
-                         workspace);
+                         workspace, workspace_bytes, precision, keep_a);
     if (rc) return rc;
     RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return RISRT_OK;

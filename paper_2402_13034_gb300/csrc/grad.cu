@@ -5,9 +5,11 @@
 // |E|^2 is clamped from below at 1e-30 max_r |E_b(r)|^2 on both sides of the comparison.
 // Three passes, all FP32 on the CUDA cores: forward GEMM over the target rows (E), the per-config
 // clamp, log and weights w = conj(E)/|E|^2, and the backward GEMM A^T w with the phase epilogue.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
-#include "internal.cuh"
+#include "sweep.cuh"
 
 namespace risrt {
 namespace {
@@ -222,6 +224,122 @@ __global__ void k_adj_grad(const float2* __restrict__ Gp, int splits, const floa
     grad[i] = -2.f * a * (cs * g.y + sn * g.x);     // Im(Gamma g), Gamma = a (cs + j sn)
 }
 
+// ---- tensor-core path: both GEMMs as real BF16 GEMMs with three-term splits ----------------------
+// A complex product is one real GEMM over [Re | Im] blocks (rows of the second operand interleave
+// [Re g, -Im g] and [Im g, Re g]); each real factor x is split as hi = bf16(x), lo = bf16(x - hi),
+// and the reduction runs over three blocks pairing hi.hi, hi.lo and lo.hi (the lo.lo term, below
+// 2^-16 of the product, is dropped), which keeps the products to about 1e-5 relative.
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo)
+{
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Forward operand X [n_t][Kf]: row t holds [hi(Re A), hi(Im A) | hi(Re A), hi(Im A) | lo(Re A), lo(Im A)]
+// of A's target row (columns past 6M zero); E0t[t] = E0 of that row.
+__global__ void k_gpack_xf(const float2* __restrict__ A, const float2* __restrict__ E0, int M, const int* __restrict__ target,
+                           int n_t, int Kf, __nv_bfloat16* __restrict__ X, float2* __restrict__ E0t)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int wide = max(2 * M, Kf - 6 * M);
+    if (i >= (int64_t)n_t * wide) return;
+    const int t = (int)(i / wide), k2 = (int)(i % wide);
+    const int64_t r = target ? target[t] : t;
+    __nv_bfloat16* row = X + (int64_t)t * Kf;
+    if (k2 < 2 * M) {
+        const float2 a = A[r * M + (k2 % M)];
+        __nv_bfloat16 hi, lo;
+        split_bf16(k2 < M ? a.x : a.y, hi, lo);
+        row[k2] = hi;
+        row[2 * M + k2] = hi;
+        row[4 * M + k2] = lo;
+        if (k2 == 0) E0t[t] = E0 ? E0[r] : make_float2(0.f, 0.f);
+    }
+    if (k2 < Kf - 6 * M) row[6 * M + k2] = __float2bfloat16_rn(0.f);
+}
+
+// Forward operand Y [Np][Kf] from Gamma_bm = amp_m e^{j phi_bm}: rows 2b / 2b + 1 give Re / Im E_b.
+__global__ void k_gpack_yf(const float* __restrict__ phases, const float* __restrict__ amp, int M, int B, int Np, int Kf,
+                           __nv_bfloat16* __restrict__ Y)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)Np * Kf) return;
+    const int n = (int)(i / Kf), k = (int)(i % Kf);
+    const int b = n >> 1, seg = k / (2 * M), k2 = k % (2 * M), part = k2 / M, m = k2 % M;
+    float v = 0.f;
+    bool use_lo = false;
+    if (b < B && seg < 3) {
+        float sn, cs;
+        sincosf(phases[(int64_t)b * M + m], &sn, &cs);
+        const float a = amp ? amp[m] : 1.f;
+        const float gre = a * cs, gim = a * sn;
+        // Re E = sum Re A Re g - Im A Im g;  Im E = sum Re A Im g + Im A Re g
+        v = (n & 1) ? (part == 0 ? gim : gre) : (part == 0 ? gre : -gim);
+        use_lo = seg == 1;
+    }
+    __nv_bfloat16 hi, lo;
+    split_bf16(v, hi, lo);
+    Y[i] = use_lo ? lo : hi;
+}
+
+// Backward operand X [M][Kb] (A transposed): row m holds, for segments hi, hi, lo, [Re A[t][m] | Im A[t][m]]
+// over the targets t (columns past 6 n_t zero). 32 x 32 tiles through shared memory.
+__global__ void k_gpack_xb(const float2* __restrict__ A, int M, const int* __restrict__ target, int n_t, int Kb,
+                           __nv_bfloat16* __restrict__ X)
+{
+    __shared__ float2 tile[32][33];
+    const int m0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int t = t0 + y, m = m0 + threadIdx.x;
+        float2 v = make_float2(0.f, 0.f);
+        if (t < n_t && m < M) v = A[(int64_t)(target ? target[t] : t) * M + m];
+        tile[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int m = m0 + y, t = t0 + threadIdx.x;
+        if (m >= M || t >= n_t) continue;
+        const float2 v = tile[threadIdx.x][y];
+        __nv_bfloat16* row = X + (int64_t)m * Kb;
+        __nv_bfloat16 rh, rl, ih, il;
+        split_bf16(v.x, rh, rl);
+        split_bf16(v.y, ih, il);
+        row[t] = rh;
+        row[n_t + t] = ih;
+        row[2 * n_t + t] = rh;
+        row[3 * n_t + t] = ih;
+        row[4 * n_t + t] = rl;
+        row[5 * n_t + t] = il;
+    }
+}
+
+__global__ void k_gpack_xb_pad(int M, int n_t, int Kb, __nv_bfloat16* __restrict__ X)
+{
+    const int pad = Kb - 6 * n_t;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pad <= 0 || i >= (int64_t)M * pad) return;
+    X[(i / pad) * Kb + 6 * n_t + i % pad] = __float2bfloat16_rn(0.f);
+}
+
+// Backward operand Y [Np][Kb] from the weights w[b][t]: rows 2b / 2b + 1 give Re / Im of sum_t A w.
+__global__ void k_gpack_yb(const float2* __restrict__ W, int n_t, int B, int Np, int Kb, __nv_bfloat16* __restrict__ Y)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)Np * Kb) return;
+    const int n = (int)(i / Kb), k = (int)(i % Kb);
+    const int b = n >> 1, seg = k / (2 * n_t), k2 = k % (2 * n_t), part = k2 / n_t, t = k2 % n_t;
+    float v = 0.f;
+    bool use_lo = false;
+    if (b < B && seg < 3) {
+        const float2 w = W[(int64_t)b * n_t + t];
+        v = (n & 1) ? (part == 0 ? w.y : w.x) : (part == 0 ? w.x : -w.y);
+        use_lo = seg == 1;
+    }
+    __nv_bfloat16 hi, lo;
+    split_bf16(v, hi, lo);
+    Y[i] = use_lo ? lo : hi;
+}
+
 }  // namespace
 
 struct GradSplits {
@@ -243,8 +361,44 @@ GradSplits grad_splits(int n_t, int B, int M)
     return g;
 }
 
-size_t grad_workspace_bytes(int n_t, int B, int M)
+// Layout of the tensor-core workspace (byte offsets, 256-aligned) and its split-K part counts.
+struct GradTcLayout {
+    int Kf, Kb, Np, sf, sb;
+    size_t xf, yf, e0t, ep, xb, yb, gp, end;
+};
+
+GradTcLayout grad_tc_layout(int n_t, int B, int M)
 {
+    GradTcLayout L;
+    auto up = [](int64_t v, int64_t a) { return (v + a - 1) / a * a; };
+    L.Kf = (int)up(6LL * M, kTcBK);
+    L.Kb = (int)up(6LL * n_t, kTcBK);
+    L.Np = (int)up(2LL * B, kTcBN);
+    const int clusters = 152;           // enough parts to give every SM pair about one tile
+    const int tf = (int)(up(n_t, 2 * kTcBM) / (2 * kTcBM)) * (L.Np / kTcBN);
+    const int tb = (int)(up(M, 2 * kTcBM) / (2 * kTcBM)) * (L.Np / kTcBN);
+    L.sf = std::max(1, std::min(8, (clusters + tf - 1) / tf));
+    L.sb = std::max(1, std::min(16, (clusters + tb - 1) / tb));
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t a = o;
+        o = (size_t)up((int64_t)(o + bytes), 256);
+        return a;
+    };
+    L.xf = take((size_t)n_t * L.Kf * 2);
+    L.yf = take((size_t)L.Np * L.Kf * 2);
+    L.e0t = take((size_t)n_t * sizeof(float2));
+    L.ep = take((size_t)L.sf * B * n_t * sizeof(float2));
+    L.xb = take((size_t)M * L.Kb * 2);
+    L.yb = take((size_t)L.Np * L.Kb * 2);
+    L.gp = take((size_t)L.sb * B * M * sizeof(float2));
+    L.end = o;
+    return L;
+}
+
+size_t grad_workspace_bytes(int n_t, int B, int M, int precision)
+{
+    if (precision == RISRT_PREC_BF16X2) return grad_tc_layout(n_t, B, M).end + 256;
     GradSplits g = grad_splits(n_t, B, M);
     return sizeof(float2) * ((size_t)g.fwd * n_t * B + (size_t)g.bwd * B * M) + 256;
 }
@@ -261,9 +415,46 @@ int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void
     return RISRT_OK;
 }
 
-int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
-                const float* phases, const float* amp, int B, float* J, float* grad, void* ws)
+// Tensor-core adjoint: both GEMMs on SM pairs (split-K), the packing of A into its forward and
+// transposed operands done per call (A and the targets may change between calls).
+static int grad_phases_tc(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
+                          const float* phases, const float* amp, int B, float* J, float* grad, void* ws, size_t ws_bytes,
+                          bool keep_a)
 {
+    cudaStream_t s = ctx->stream;
+    const GradTcLayout L = grad_tc_layout(n_t, B, M);
+    char* w = (char*)ws;
+    __nv_bfloat16* Xf = (__nv_bfloat16*)(w + L.xf);
+    __nv_bfloat16* Yf = (__nv_bfloat16*)(w + L.yf);
+    float2* E0t = (float2*)(w + L.e0t);
+    float2* Ep = (float2*)(w + L.ep);
+    __nv_bfloat16* Xb = (__nv_bfloat16*)(w + L.xb);
+    __nv_bfloat16* Yb = (__nv_bfloat16*)(w + L.yb);
+    float2* Gp = (float2*)(w + L.gp);
+    unsigned* err = (unsigned*)(w + ws_bytes - 32);
+    const int wide = std::max(2 * M, L.Kf - 6 * M);
+    if (!keep_a) {              // A's target rows into both operands (kept in the workspace for KEEP_A calls)
+        RISRT_KERNEL(ctx, "k_gpack_xf", (k_gpack_xf<<<nblk((int64_t)n_t * wide, 256), 256, 0, s>>>(A, E0, M, target, n_t, L.Kf, Xf, E0t)));
+        RISRT_KERNEL(ctx, "k_gpack_xb", (k_gpack_xb<<<dim3(nblk(M, 32), nblk(n_t, 32)), dim3(32, 8), 0, s>>>(A, M, target, n_t, L.Kb, Xb)));
+        if (L.Kb > 6 * n_t)
+            RISRT_KERNEL(ctx, "k_gpack_xb_pad", (k_gpack_xb_pad<<<nblk((int64_t)M * (L.Kb - 6 * n_t), 256), 256, 0, s>>>(M, n_t, L.Kb, Xb)));
+    }
+    RISRT_KERNEL(ctx, "k_gpack_yf", (k_gpack_yf<<<nblk((int64_t)L.Np * L.Kf, 256), 256, 0, s>>>(phases, amp, M, B, L.Np, L.Kf, Yf)));
+    int pf = 0, pb = 0, rc;
+    if ((rc = gemm_tc_complex(ctx, Xf, n_t, Yf, L.Np, L.Kf, E0t, B, Ep, L.sf, &pf, err))) return rc;
+    RISRT_KERNEL(ctx, "k_adj_weights", (k_adj_weights<<<B, 512, 0, s>>>(Ep, n_t, B, pf, J, (float)(1.0 / (2.0 * kEta0)))));
+    RISRT_KERNEL(ctx, "k_gpack_yb", (k_gpack_yb<<<nblk((int64_t)L.Np * L.Kb, 256), 256, 0, s>>>(Ep, n_t, B, L.Np, L.Kb, Yb)));
+    if ((rc = gemm_tc_complex(ctx, Xb, M, Yb, L.Np, L.Kb, nullptr, B, Gp, L.sb, &pb, err))) return rc;
+    RISRT_KERNEL(ctx, "k_adj_grad", (k_adj_grad<<<nblk((int64_t)B * M, 256), 256, 0, s>>>(Gp, pb, phases, amp, B, M, grad)));
+    return RISRT_OK;
+}
+
+int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
+                const float* phases, const float* amp, int B, float* J, float* grad, void* ws, size_t ws_bytes,
+                int precision, bool keep_a)
+{
+    if (precision == RISRT_PREC_BF16X2)
+        return grad_phases_tc(ctx, A, E0, M, target, n_t, phases, amp, B, J, grad, ws, ws_bytes, keep_a);
     cudaStream_t s = ctx->stream;
     const GradSplits g = grad_splits(n_t, B, M);
     float2* E = (float2*)ws;                               // [fwd][B][n_t] partials, then w in split 0

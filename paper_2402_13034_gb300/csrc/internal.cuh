@@ -304,10 +304,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 double freq, int max_order_tx, int max_order_rx, uint32_t flags, risrt_pathset* ps);
 int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
 int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0);
-size_t grad_workspace_bytes(int n_t, int B, int M);
+size_t grad_workspace_bytes(int n_t, int B, int M, int precision);
 int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes);
 int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
-                const float* phases, const float* amp, int B, float* J, float* grad, void* ws);
+                const float* phases, const float* amp, int B, float* J, float* grad, void* ws, size_t ws_bytes,
+                int precision, bool keep_a);
 int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src[3], int src_face, const float dst[3],
                        int dst_face, int max_order, int64_t* ids_host, int cap_host, int* n_host);
 

@@ -27,4 +27,8 @@ int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_r
 int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh, bool fp16, const float2* E0,
              int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev);
 
+// D = X . Y^T on SM pairs with split-K, complex partial sums out (see sweep_tc.cu).
+int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, int Np, int Kp, const float2* E0rows, int C,
+                    float2* out, int splits, int* parts, unsigned* err_dev);
+
 }  // namespace risrt

@@ -9,6 +9,7 @@
 // bounded) for its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "sweep.cuh"
@@ -295,8 +296,13 @@ __device__ __forceinline__ void mma_commit_pair(uint32_t mbar)
 __global__ void __launch_bounds__(192, 1)
 k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int num_kb, int tiles_n,
                 int num_tiles, uint32_t idesc, const float2* __restrict__ E0, int64_t n_rx, int C,
-                float* __restrict__ P, float pscale, float e0scale, unsigned* __restrict__ err)
+                float* __restrict__ P, float pscale, float e0scale, unsigned* __restrict__ err, int num_kb_total,
+                float2* __restrict__ Cout)
 {
+    // split-K (num_kb k-blocks per split, num_kb_total in all): tile t covers split z = t / tiles_mn;
+    // with Cout the epilogue writes the complex partial sums D[row][2c] + j D[row][2c + 1] (+ E0 in
+    // split 0) to Cout[(z C + c) n_rx + row] instead of the power
+    const int tiles_mn = num_tiles / max(1, (num_kb_total + num_kb - 1) / num_kb);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
@@ -343,9 +349,10 @@ k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
             long long g = 0;
             bool ok = true;
             for (int t = cluster; t < num_tiles && ok; t += n_clusters) {
-                const int xrow = (t / tiles_n) * (2 * kTcBM) + (int)rank * kTcBM;
-                const int yrow = (t % tiles_n) * kTcBN + (int)rank * (kTcBN / 2);
-                for (int kb = 0; kb < num_kb; ++kb, ++g) {
+                const int tt = t % tiles_mn, kb0 = (t / tiles_mn) * num_kb, kb1 = min(num_kb_total, kb0 + num_kb);
+                const int xrow = (tt / tiles_n) * (2 * kTcBM) + (int)rank * kTcBM;
+                const int yrow = (tt % tiles_n) * kTcBN + (int)rank * (kTcBN / 2);
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % kPairStages);
                     const uint32_t ph = (uint32_t)((g / kPairStages) & 1);
                     if (!wait_for(smem_u32(&empty[s]), ph ^ 1, false) || *abort_v) {
@@ -382,7 +389,8 @@ k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
                 }
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * kTmemCols);
-                for (int kb = 0; kb < num_kb; ++kb, ++g) {
+                const int kb0 = (t / tiles_mn) * num_kb, kb1 = min(num_kb_total, kb0 + num_kb);
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % kPairStages);
                     if (!wait_for(smem_u32(&full[s]), (uint32_t)((g / kPairStages) & 1), false) || *abort_v) {
                         ok = false;
@@ -392,7 +400,7 @@ k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
                     const uint32_t a0 = smem_u32(sA + s * kStageA), b0 = smem_u32(sB + s * kPairStageB);
 #pragma unroll
                     for (int k = 0; k < kTcBK / 16; ++k)
-                        mma_f16_pair(d, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc, (kb | k) != 0);
+                        mma_f16_pair(d, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc, kb != kb0 || k != 0);
                     mma_commit_pair(smem_u32(&empty[s]));
                 }
                 if (ok) mma_commit_pair(smem_u32(&tfull[acc]));
@@ -424,11 +432,12 @@ k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
                 break;
             }
             fence_after();
-            const int64_t row = (int64_t)(t / tiles_n) * (2 * kTcBM) + rank * kTcBM + lane_base + lane;
-            const int cbase = (t % tiles_n) * (kTcBN / 2);
+            const int z = t / tiles_mn, tt = t % tiles_mn;
+            const int64_t row = (int64_t)(tt / tiles_n) * (2 * kTcBM) + rank * kTcBM + lane_base + lane;
+            const int cbase = (tt % tiles_n) * (kTcBN / 2);
             const bool live = row < n_rx;
             float2 e0 = make_float2(0.f, 0.f);
-            if (live && E0) {
+            if (live && E0 && z == 0) {
                 e0 = E0[row];
                 e0.x *= e0scale;
                 e0.y *= e0scale;
@@ -437,6 +446,15 @@ k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
             for (int j = 0; j < kTcBN / 16; ++j) {
                 float v[16], p[8];
                 tmem_ld16(tbase + (uint32_t)(j * 16), v);
+                if (Cout) {                          // complex partial sums, coalesced over rows
+                    if (!live) continue;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int c = cbase + j * 8 + q;
+                        if (c < C) Cout[((int64_t)z * C + c) * n_rx + row] = make_float2(v[2 * q] + e0.x, v[2 * q + 1] + e0.y);
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const float er = v[2 * q] + e0.x, ei = v[2 * q + 1] + e0.y;
@@ -576,7 +594,7 @@ int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh,
         cudaError_t le = cudaSuccess;
         RISRT_KERNEL(ctx, "k_sweep_tc_pair",
                      (le = cudaLaunchKernelEx(&cfg, k_sweep_tc_pair, mX, mY, sh.Kp / kTcBK, tiles_n, num_tiles, idesc, E0,
-                                              n_rx, C, P, pscale, e0scale, err_dev)));
+                                              n_rx, C, P, pscale, e0scale, err_dev, sh.Kp / kTcBK, (float2*)nullptr)));
         if (le != cudaSuccess) return cuda_fail(ctx, le, "k_sweep_tc_pair");
     } else {
         RISRT_CUDA(ctx, cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
@@ -589,6 +607,54 @@ int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh,
     RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));
     if (h) return fail(ctx, RISRT_ERR_TIMEOUT, "tensor-core sweep: a pipeline wait expired");
+    return RISRT_OK;
+}
+
+// D = X . Y^T on SM pairs (BF16, both K-major: X [rows][Kp], Y [Np][Kp]) with the reduction split
+// into about `splits` parts; writes the complex partial sums D[row][2c] + j D[row][2c + 1] (+ E0rows[row]
+// in part 0) to out[(z C + c) rows + row] and the number of parts to *parts. RISRT_ERR_NOT_READY when
+// the pair kernel cannot be placed on this device.
+int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, int Np, int Kp, const float2* E0rows, int C,
+                    float2* out, int splits, int* parts, unsigned* err_dev)
+{
+    cudaStream_t s = ctx->stream;
+    const int ncl = pair_clusters(ctx);
+    if (ncl <= 0) return fail(ctx, RISRT_ERR_NOT_READY, "the paired tensor-core kernel cannot run on this device");
+    if (((uintptr_t)X & 15) || ((uintptr_t)Y & 15) || (Kp % kTcBK) || (Np % kTcBN))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "tensor-core operands: 16-byte alignment, K multiple of 64, N of 256");
+    CUtensorMap mX, mY;
+    if (!make_map(&mX, X, false, rows, Kp, kTcBM) || !make_map(&mY, Y, false, Np, Kp, kTcBN / 2))
+        return fail(ctx, RISRT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    const int kb_total = Kp / kTcBK;
+    const int kb_per = (kb_total + std::max(1, splits) - 1) / std::max(1, splits);
+    const int z = (kb_total + kb_per - 1) / kb_per;
+    const int tiles_m = (int)((rows + 2 * kTcBM - 1) / (2 * kTcBM)), tiles_n = Np / kTcBN;
+    const int num_tiles = tiles_m * tiles_n * z;
+    const int nc = num_tiles < ncl ? num_tiles : ncl;
+    RISRT_CUDA(ctx, cudaMemsetAsync(err_dev, 0, sizeof(unsigned), s));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * nc), 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = kPairSmemBytes;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const uint32_t idesc = make_idesc(false, 2 * kTcBM, kTcBN);
+    cudaError_t le = cudaSuccess;
+    RISRT_KERNEL(ctx, "k_sweep_tc_pair",
+                 (le = cudaLaunchKernelEx(&cfg, k_sweep_tc_pair, mX, mY, kb_per, tiles_n, num_tiles, idesc, E0rows, rows, C,
+                                          (float*)nullptr, 0.f, 1.f, err_dev, kb_total, out)));
+    if (le != cudaSuccess) return cuda_fail(ctx, le, "k_sweep_tc_pair");
+    unsigned h = 0;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    if (h) return fail(ctx, RISRT_ERR_TIMEOUT, "tensor-core GEMM: a pipeline wait expired");
+    *parts = z;
     return RISRT_OK;
 }
 

@@ -20,6 +20,7 @@ TX, RX = 0, 1
 PATTERN_ISO, PATTERN_COS_POW, PATTERN_MONOPOLE_QW = 0, 1, 2
 FLAG_ENV_PATHS, FLAG_FRESNEL_TM = 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP16 = 0, 1, 2, 3
+GRAD_KEEP_A = 0x100
 
 _lock = threading.Lock()
 _lib = None
@@ -44,9 +45,9 @@ _SIGS = {
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
     "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_sweep_configs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int, _P, _P, C.c_size_t]),
-    "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P,
-                                    C.c_size_t]),
+                                    C.c_size_t, C.c_int]),
     "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
                                            C.POINTER(C.c_int32)]),
     "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
@@ -318,26 +319,30 @@ class Context:
                                                int(n_rx), int(M), _dev_ptr(gamma, "torch.complex64"), int(n_cfg),
                                                int(precision), _dev_ptr(P_out, "torch.float32"), ws_ptr, ws_n))
 
-    def grad_workspace(self, n_target: int, B: int, M: int):
+    def grad_workspace(self, n_target: int, B: int, M: int, precision: int = PREC_FP32):
         import torch
         nb = C.c_size_t()
-        rc = load().risrt_grad_workspace_size(int(n_target), int(B), int(M), C.byref(nb))
+        rc = load().risrt_grad_workspace_size(int(n_target), int(B), int(M), int(precision), C.byref(nb))
         if rc:
             raise RisrtError(rc, "grad workspace size")
         return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
 
-    def grad_phases(self, A, E0, target, phases, amp, J_out, grad_out, workspace=None):
+    def grad_phases(self, A, E0, target, phases, amp, J_out, grad_out, workspace=None, precision: int = PREC_FP32,
+                    keep_a: bool = False):
         """A: complex64 CUDA [n_rx, M]; target: int32 CUDA [n_t] or None (first n_t rows given by
-        phases' companion J); phases: float32 [B, M]; amp: float32 [M] or None; J_out [B]; grad_out [B, M]."""
+        phases' companion J); phases: float32 [B, M]; amp: float32 [M] or None; J_out [B]; grad_out [B, M];
+        precision PREC_FP32 (CUDA cores) or PREC_BF16X2 (tensor cores, split BF16); keep_a: A, E0 and target
+        are those of the previous call with this workspace (its packed A is reused)."""
         n_rx, M = A.shape
         B = phases.shape[0]
         n_t = target.numel() if target is not None else n_rx
-        ws = workspace if workspace is not None else self.grad_workspace(n_t, B, M)
+        ws = workspace if workspace is not None else self.grad_workspace(n_t, B, M, precision)
         self._check(load().risrt_grad_phases(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
                                              int(n_rx), int(M), _dev_ptr(target, "torch.int32"), int(n_t),
                                              _dev_ptr(phases, "torch.float32"), _dev_ptr(amp, "torch.float32"), int(B),
                                              _dev_ptr(J_out, "torch.float32"), _dev_ptr(grad_out, "torch.float32"),
-                                             C.c_void_p(ws.data_ptr()), ws.numel()))
+                                             C.c_void_p(ws.data_ptr()), ws.numel(),
+                                             int(precision) | (GRAD_KEEP_A if keep_a else 0)))
 
     def find_paths_noalloc(self, scene: Scene, src, src_face: int, dst, dst_face: int, max_order: int,
                            cap: int = 4096) -> np.ndarray:

@@ -30,8 +30,17 @@ def test_oracle_gradient_matches_finite_differences():
         assert np.allclose(fd, g[:, m], rtol=1e-6, atol=1e-8 * np.abs(g).max())
 
 
+# Relative gradient error bound per precision. FP32: rounding of the two FP32 GEMMs. Split BF16:
+# every factor is carried to about 2^-17 relative (hi + lo BF16) and the lo.lo term is dropped, so a
+# product is good to about 2^-16, some 250 times the FP32 unit roundoff; the error of E is relative to
+# sum |A||Gamma| rather than to |E|, which near-null targets amplify through w = conj(E)/|E|^2, and
+# 5e-3 covers that on random channels (observed 1.2e-3) where FP32 stays below 1e-5.
+GRAD_TOL = {0: 1e-4, 2: 5e-3}
+
+
 @pytest.mark.gpu
-def test_grad_phases_against_oracle():
+@pytest.mark.parametrize("prec", [0, 2])
+def test_grad_phases_against_oracle(prec):
     import torch
     from paper_2402_13034_gb300 import build as B
     from paper_2402_13034_gb300 import risrt as R
@@ -51,13 +60,13 @@ def test_grad_phases_against_oracle():
     amp = (0.5 + rng.random(w.n_elem)).astype(np.float32)
     J = torch.empty(Bn, device="cuda")
     g = torch.empty((Bn, w.n_elem), device="cuda")
-    ctx.grad_phases(A, E0, target, torch.from_numpy(ph).cuda(), torch.from_numpy(amp).cuda(), J, g)
+    ctx.grad_phases(A, E0, target, torch.from_numpy(ph).cuda(), torch.from_numpy(amp).cuda(), J, g, precision=prec)
     f = {"E0": fld["E0"][ok], "A": fld["A"][ok]}
     J_ref, g_ref = O.log_power_and_grad(f, ph.astype(np.float64), amp.astype(np.float64))
     Jg, gg = J.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(Jg - J_ref) <= 1e-4 * np.abs(J_ref) + 1e-3)
     rel = np.linalg.norm(gg - g_ref, axis=1) / np.linalg.norm(g_ref, axis=1)
-    assert rel.max() <= 1e-4, rel
+    assert rel.max() <= GRAD_TOL[prec], rel
 
 
 @pytest.mark.gpu
@@ -70,3 +79,37 @@ def test_grad_phases_rejects_bad_target():
     with pytest.raises(R.RisrtError):
         ctx.grad_phases(A, None, torch.tensor([0, 9], dtype=torch.int32, device="cuda"), ph, None,
                         torch.empty(1, device="cuda"), torch.empty((1, 3), device="cuda"))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n_rx,n_t,M,Bn", [(3000, 2900, 700, 20), (600, 517, 1024, 3)])
+def test_grad_tensor_core_many_tiles(n_rx, n_t, M, Bn):
+    """Split-BF16 tensor-core adjoint on random channels large enough for several tiles and split-K
+    parts (ragged row, element and configuration counts), against the FP64 definition of J and of its
+    gradient (oracle.log_power_and_grad) on the same A; the FP32 path is checked the same way."""
+    import torch
+    from paper_2402_13034_gb300 import build as B
+    from paper_2402_13034_gb300 import risrt as R
+    B.build()
+    rng = np.random.default_rng(n_t + M)
+    A = ((rng.standard_normal((n_rx, M)) + 1j * rng.standard_normal((n_rx, M))) * 1e-3).astype(np.complex64)
+    E0 = ((rng.standard_normal(n_rx) + 1j * rng.standard_normal(n_rx)) * 1e-3).astype(np.complex64)
+    target = np.sort(rng.choice(n_rx, n_t, replace=False)).astype(np.int32)
+    ph = (rng.random((Bn, M)) * 2 * np.pi).astype(np.float32)
+    amp = (0.5 + rng.random(M)).astype(np.float32)
+    ph2 = (ph + 0.3 * rng.standard_normal((Bn, M))).astype(np.float32)
+    f = {"E0": E0[target].astype(np.complex128), "A": A[target].astype(np.complex128)}
+    ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
+    Ad, E0d, td = torch.from_numpy(A).cuda(), torch.from_numpy(E0).cuda(), torch.from_numpy(target).cuda()
+    for prec in (2, 0):
+        J = torch.empty(Bn, device="cuda")
+        g = torch.empty((Bn, M), device="cuda")
+        ws = ctx.grad_workspace(n_t, Bn, M, prec)
+        # a first call packs A into the workspace; the second (new phases) reuses it with keep_a
+        for p, keep in ((ph, False), (ph2, True)):
+            ctx.grad_phases(Ad, E0d, td, torch.from_numpy(p).cuda(), torch.from_numpy(amp).cuda(), J, g, ws, prec, keep_a=keep)
+            J_ref, g_ref = O.log_power_and_grad(f, p.astype(np.float64), amp.astype(np.float64))
+            Jg, gg = J.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(Jg - J_ref) <= 1e-4 * np.abs(J_ref) + 1e-3), (prec, keep, np.abs(Jg - J_ref).max())
+            rel = np.linalg.norm(gg - g_ref, axis=1) / np.linalg.norm(g_ref, axis=1)
+            assert rel.max() <= GRAD_TOL[prec], (prec, keep, rel.max())
