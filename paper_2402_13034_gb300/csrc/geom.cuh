@@ -134,12 +134,32 @@ __device__ __forceinline__ int bvh4_step(const Bvh4Node& nd, float3 a, float3 in
     return t[0] < 1e30f ? c[0] : kNoChild;
 }
 
+// Segment ends in the scene box (exact comparisons): a segment between two such points meets the plane
+// of a shell triangle at most at an end or lies in it, and neither counts as a hit (hits closer than
+// the tolerance to an end are ignored; a segment in a triangle's plane passes), so its traversal
+// starts at root_main and never sees the shell.
+__device__ __forceinline__ bool in_scene_box(const DeviceScene& S, float3 p)
+{
+    return p.x >= S.box_lo.x && p.y >= S.box_lo.y && p.z >= S.box_lo.z && p.x <= S.box_hi.x && p.y <= S.box_hi.y &&
+           p.z <= S.box_hi.z;
+}
+__device__ __forceinline__ bool in_scene_box(const DeviceScene& S, d3 p)
+{
+    return p.x >= (double)S.box_lo.x && p.y >= (double)S.box_lo.y && p.z >= (double)S.box_lo.z &&
+           p.x <= (double)S.box_hi.x && p.y <= (double)S.box_hi.y && p.z <= (double)S.box_hi.z;
+}
+__device__ __forceinline__ int occ_root(const DeviceScene& S, bool ends_in_box)
+{
+    return ends_in_box ? S.root_main : S.root;
+}
+
 // Is segment A->B blocked (faces ign0 / ign1 skipped)? `refines` counts FP64 settlements,
 // `err` is set if the traversal stack would overflow (never expected; treated as blocked).
 __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
                            unsigned long long* refines, int* err, TraceCounters* tc = nullptr)
 {
-    if (S.root == kNoRoot) return false;
+    const int root = occ_root(S, in_scene_box(S, A) && in_scene_box(S, B));
+    if (root == kNoRoot) return false;
     float3 a = to_f(A), b = to_f(B);
     float3 dir = b - a;
     float len = sqrtf(dot(dir, dir));
@@ -147,7 +167,7 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
     float tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
     int stack[64];
     int sp = 0;
-    int c = S.root;          // current node in a register; the other entered children go on the stack
+    int c = root;            // current node in a register; the other entered children go on the stack
     const int g0 = ign0 >= 0 ? ign0 : -3, g1 = ign1 >= 0 ? ign1 : -3;   // subtrees of one ignored face are skipped
     while (true) {
         if (c < 0) {

@@ -121,6 +121,11 @@ struct DeviceScene {
     int64_t n_tris;
     int n_faces;
     int root;                    // root child code (internal index, or ~leaf for one triangle); kNoRoot if empty
+    // Subtree of the references that can stop a segment whose two ends lie in the scene box
+    // [box_lo, box_hi]: the triangles whose plane has the whole box on one closed side (the shell of a
+    // box-shaped room, or faces lying in it) sit in a sibling subtree of it. kNoRoot if there are none.
+    int root_main;
+    float3 box_lo, box_hi;
     const BvhNode* nodes;
     const Bvh4Node* nodes4;      // [internal nodes] four-wide view used by the traversals
     const TriGeom* tri_geom;     // [n_refs] leaf (reference) order
@@ -177,6 +182,9 @@ struct risrt_scene {
     int n_faces = 0;
     int n_mat = 0;
     int root = risrt::kNoRoot;
+    int root_main = risrt::kNoRoot;
+    int64_t n_shell_refs = 0;        // references of shell triangles (planes with the scene box on one side)
+    float box_lo[3] = {0.f, 0.f, 0.f}, box_hi[3] = {0.f, 0.f, 0.f};
     risrt::BvhNode* nodes = nullptr;
     risrt::Bvh4Node* nodes4 = nullptr;
     risrt::TriGeom* tri_geom = nullptr;
@@ -193,7 +201,9 @@ struct risrt_scene {
     int64_t n_cells = 0;
     risrt::DeviceScene dev() const {
         risrt::DeviceScene s;
-        s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.nodes = nodes; s.nodes4 = nodes4; s.tri_geom = tri_geom;
+        s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.root_main = root_main; s.nodes = nodes;
+        s.box_lo = make_float3(box_lo[0], box_lo[1], box_lo[2]);
+        s.box_hi = make_float3(box_hi[0], box_hi[1], box_hi[2]); s.nodes4 = nodes4; s.tri_geom = tri_geom;
         s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.face_test = face_test; s.tri_leaf = tri_leaf; s.mats = mats;
         s.face_grid = face_grid; s.cell_face = cell_face; s.n_cells = n_cells;
         return s;

@@ -2,6 +2,7 @@
 // after Karras 2012 -> bottom-up box refit), plus the device-wide scan and sort they use.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.cuh"
@@ -226,6 +227,14 @@ __device__ __forceinline__ float from_ordered(unsigned o)
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
+inline float from_ordered_host(unsigned o)
+{
+    const unsigned b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    float f;
+    memcpy(&f, &b, sizeof(f));
+    return f;
+}
+
 __global__ void k_bounds(const float* __restrict__ verts, int64_t nv, unsigned* __restrict__ bb)
 {
     // bb[0..2] = ordered min, bb[3..5] = ordered max, bb[6] = max |coord| bits
@@ -387,19 +396,56 @@ __global__ void k_ref_count(const float* __restrict__ verts, const int32_t* __re
     if (lane == 0) cnt[t] = n > 0 ? n : 1;            // a triangle always keeps at least one reference
 }
 
+// Shell triangle: its plane has the whole scene box (bb) on one closed side, so no segment with both
+// ends in the box crosses it (a wall, the floor or the ceiling of a box-shaped room, or a face lying
+// in one of them). The tolerance only absorbs the rounding of the FP64 plane.
+__device__ bool shell_tri(const float* verts, const int32_t* tris, int64_t t, const unsigned* bb)
+{
+    d3 v[3];
+    for (int j = 0; j < 3; ++j) {
+        const float* p = verts + 3 * (int64_t)tris[3 * t + j];
+        v[j] = D3((double)p[0], (double)p[1], (double)p[2]);
+    }
+    d3 n = cross(v[1] - v[0], v[2] - v[0]);
+    const double nn = norm(n);
+    if (!(nn > 0.0)) return false;
+    n = n * (1.0 / nn);
+    const double d = dot(n, v[0]);
+    double lo[3], hi[3], ext = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = (double)from_ordered(bb[k]);
+        hi[k] = (double)from_ordered(bb[3 + k]);
+        ext = fmax(ext, fmax(fabs(lo[k]), fabs(hi[k])));
+    }
+    const double tol = 1e-12 * (1.0 + ext);
+    double smin = 1e300, smax = -1e300;
+    for (int c = 0; c < 8; ++c) {
+        const d3 q = D3((c & 1) ? hi[0] : lo[0], (c & 2) ? hi[1] : lo[1], (c & 4) ? hi[2] : lo[2]);
+        const double sd = dot(n, q) - d;
+        smin = fmin(smin, sd);
+        smax = fmax(smax, sd);
+    }
+    return smin >= -tol || smax <= tol;
+}
+
 // References of every triangle with their boxes; 30-bit Morton code of each box centre. One warp per
 // triangle: one reference per grid cell the triangle meets, in cell order, boxed tightly around the
 // part inside the cell (a triangle in a single cell keeps its own box); never more references than
-// counted, and any shortfall filled with the triangle's whole box (conservative).
+// counted, and any shortfall filled with the triangle's whole box (conservative). With `shell` set,
+// the keys of shell triangles' references carry bit 30, so they sort after all others and the
+// root's first child covers exactly the rest; shell_refs counts them.
 __global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t nt,
                            const unsigned* __restrict__ bb, const int64_t* __restrict__ off,
                            const int64_t* __restrict__ cnt,
                            uint32_t* __restrict__ ref_tri, float4* __restrict__ ref_lo, float4* __restrict__ ref_hi,
-                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int shell,
+                           unsigned long long* __restrict__ shell_refs)
 {
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (t >= nt) return;                              // whole warps leave together
+    const unsigned shell_bit = shell && shell_tri(verts, tris, t, bb) ? (1u << 30) : 0u;
+    if (shell_bit && lane == 0) atomicAdd(shell_refs, (unsigned long long)cnt[t]);
     float lo[3], hi[3];
     tri_box(verts, tris, t, lo, hi);
     RefGrid g = ref_grid(lo, hi, scene_cell(bb));
@@ -419,7 +465,7 @@ __global__ void k_ref_emit(const float* __restrict__ verts, const int32_t* __res
         ref_tri[r] = (uint32_t)t;
         ref_lo[r] = make_float4(olo[0], olo[1], olo[2], 0.f);
         ref_hi[r] = make_float4(ohi[0], ohi[1], ohi[2], 0.f);
-        keys[r] = code;
+        keys[r] = code | shell_bit;
         vals[r] = (uint32_t)r;
     };
     const int nc = g.n[0] * g.n[1] * g.n[2];
@@ -845,9 +891,12 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, cudaMemcpyAsync(d_mat, mat_host, sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
 
     // scene bounds
+    // bb[0..6] bounds (k_bounds), bb[8..9] the number of shell references (64-bit)
     unsigned* d_bb;
-    if ((rc = dmalloc(ctx, &d_bb, 8))) return rc;
-    unsigned bb_init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0, 0, 0};
+    if ((rc = dmalloc(ctx, &d_bb, 10))) return rc;
+    unsigned bb_init[10] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0, 0, 0, 0, 0};
+    const char* shell_env = getenv("RISRT_SHELL");      // "0": shell triangles stay in the main tree
+    const int shell_on = !(shell_env && shell_env[0] == '0');
     RISRT_CUDA(ctx, cudaMemcpyAsync(d_bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
     RISRT_KERNEL(ctx, "k_bounds", (k_bounds<<<std::min<int64_t>(nblk(n_verts, 256), 1024), 256, 0, s>>>(d_verts, n_verts, d_bb)));
 
@@ -878,8 +927,9 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     size_t tmp_bytes = std::max(sort_temp_bytes(nr), scan_temp_bytes(F) + 64);
     if ((rc = dmalloc(ctx, (char**)&tmp, tmp_bytes))) return rc;
     RISRT_KERNEL(ctx, "k_ref_emit", (k_ref_emit<<<nblk(nt * 32, 256), 256, 0, s>>>(d_verts, d_tris, nt, d_bb, ref_off, ref_cnt, ref_tri,
-                                                                            ref_lo, ref_hi, keys, vals)));
-    RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nr, 30, tmp, s));
+                                                                            ref_lo, ref_hi, keys, vals, shell_on,
+                                                                            (unsigned long long*)(d_bb + 8))));
+    RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, nr, 31, tmp, s));
 
     // leaves, hierarchy, refit
     int* leaf_of_orig;
@@ -892,12 +942,19 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
                                                                         ref_hi, sc->tri_verts, sc->tri_geom, sc->tri_face,
                                                                         leaf_lo, leaf_hi, leaf_of_orig)));
 
-    unsigned bb_host[8];
+    unsigned bb_host[10];
     RISRT_CUDA(ctx, cudaMemcpyAsync(bb_host, d_bb, sizeof(bb_host), cudaMemcpyDeviceToHost, s));
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));
     float ext;
     memcpy(&ext, &bb_host[6], 4);
     sc->scene_extent = ext;
+    for (int k = 0; k < 3; ++k) {
+        sc->box_lo[k] = from_ordered_host(bb_host[k]);
+        sc->box_hi[k] = from_ordered_host(bb_host[3 + k]);
+    }
+    uint64_t n_shell = 0;
+    memcpy(&n_shell, &bb_host[8], sizeof(n_shell));
+    sc->n_shell_refs = (int64_t)n_shell;
     const float pad = 1e-4f * (1.f + ext);
 
     int n_int = (int)std::max<int64_t>(nr - 1, 1);
@@ -919,6 +976,12 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     } else {
         sc->root = ~0;
     }
+    // The shell references sort last (key bit 30), so the root splits at that bit: its first child,
+    // leaf 0 or internal node n_main - 1 (the radix tree's split position), covers the others.
+    const int64_t n_main = nr - sc->n_shell_refs;
+    if (sc->n_shell_refs == 0) sc->root_main = sc->root;
+    else if (n_main == 0) sc->root_main = kNoRoot;
+    else sc->root_main = n_main == 1 ? ~0 : (int)(n_main - 1);
 
     // faces: first triangle, triangle lists, FP64 planes
     int *first, *count, *cursor;

@@ -812,10 +812,10 @@ constexpr int kMapLeafBudget = 8;    // triangles that may meet a cell's pyramid
 // margins of face_covers / tri_covers, 0 = undecided. The walk visits children entered first along
 // the centre ray first and gives up after kMapLeafBudget candidate triangles or
 // RISRT_MAP_NODE_BUDGET nodes.
-__device__ uint8_t classify_pyramid(const DeviceScene& S, float3 A, const float3* C, float3 nb, float D, int ig0, int ig1,
-                                    float margin)
+__device__ uint8_t classify_pyramid(const DeviceScene& S, int root, float3 A, const float3* C, float3 nb, float D, int ig0,
+                                    int ig1, float margin)
 {
-    if (S.root == kNoRoot) return 1;
+    if (root == kNoRoot) return 1;
     // the pyramid's planes, outside = positive side: four through A, the fifth the base plane
     float3 pn[5];
     for (int k = 0; k < 4; ++k) {
@@ -833,7 +833,7 @@ __device__ uint8_t classify_pyramid(const DeviceScene& S, float3 A, const float3
     const float3 cinv = f3(safe_inv(cdir.x), safe_inv(cdir.y), safe_inv(cdir.z));
     int stack[64];
     int sp = 0;
-    int cur = S.root;
+    int cur = root;
     while (true) {
         if (cur < 0) {
             const int L = ~cur;
@@ -927,7 +927,9 @@ __global__ void __launch_bounds__(128) k_src_map(DeviceScene S, d3 src, int src_
         const float3 C[4] = {o + u * a0 + v * b0, o + u * a1 + v * b0, o + u * a1 + v * b1, o + u * a0 + v * b1};
         const float3 nb = sd > 0.0 ? f3(-(float)fc.plane.x, -(float)fc.plane.y, -(float)fc.plane.z)
                                    : f3((float)fc.plane.x, (float)fc.plane.y, (float)fc.plane.z);
-        state = classify_pyramid(S, to_f(src), C, nb, (float)fabs(sd), src_face, f, margin);
+        // the map answers segments from the source to points of face f, which lie in the scene box
+        state = classify_pyramid(S, occ_root(S, in_scene_box(S, src)), to_f(src), C, nb, (float)fabs(sd), src_face, f,
+                                 margin);
     }
     map[c] = state;
 }
@@ -970,10 +972,14 @@ __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float*
     if (fabs(sd) > 1e-2) {
         const float4 b = *eb;
         const double a0 = b.x - kMapDelta, a1 = b.y + kMapDelta, b0 = b.z - kMapDelta, b1 = b.w + kMapDelta;
-        const float3 C[4] = {to_f(c + t1 * a0 + t2 * b0), to_f(c + t1 * a1 + t2 * b0), to_f(c + t1 * a1 + t2 * b1),
-                             to_f(c + t1 * a0 + t2 * b1)};
+        const d3 Cd[4] = {c + t1 * a0 + t2 * b0, c + t1 * a1 + t2 * b0, c + t1 * a1 + t2 * b1, c + t1 * a0 + t2 * b1};
+        const float3 C[4] = {to_f(Cd[0]), to_f(Cd[1]), to_f(Cd[2]), to_f(Cd[3])};
         const float3 nb = to_f(sd > 0.0 ? n * -1.0 : n);
-        st = classify_pyramid(S, to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
+        // the elements lie in the aperture rectangle: with its corners and R in the scene box, every
+        // element -> R segment does too
+        const bool in_box = in_scene_box(S, R) && in_scene_box(S, Cd[0]) && in_scene_box(S, Cd[1]) &&
+                            in_scene_box(S, Cd[2]) && in_scene_box(S, Cd[3]);
+        st = classify_pyramid(S, occ_root(S, in_box), to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
     }
     state[r] = st;
 }
@@ -1007,6 +1013,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
 {
     const long long total = *d_total;
     const float3 srcf = to_f(src);
+    const bool src_in = in_scene_box(S, src);   // with both ends in the scene box a segment skips the shell
+    bool dst_in = false;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     TraceCounters tc{};
@@ -1041,7 +1049,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
             le = occ_off[info.x + 1];
             sp = 0;
         } else {
-            cur = S.root == kNoRoot ? kNone : S.root;
+            const int root = occ_root(S, (j > 0 || src_in) && (j < info.w || dst_in));   // path points lie on faces
+            cur = root == kNoRoot ? kNone : root;
             sp = 0;
             if (j == 0 && smap) {       // first segment: the source's visibility map of face f1
                 const float4 q1 = dpts[2 * item + 1];
@@ -1103,6 +1112,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                     si = cand[(int64_t)r * cap + slot];
                     info = seqs[si].info;
                     const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
+                    dst_in = in_scene_box(S, R);
                     const float3 PL = xyz(dpts[2 * item]), P1 = xyz(dpts[2 * item + 1]);
                     p[0] = srcf;
                     if (info.w == 2) {

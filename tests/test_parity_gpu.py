@@ -200,3 +200,46 @@ def test_visibility_maps_change_no_decision(monkeypatch):
     op = o.rx_paths(w.rx_xyz)
     bad = compare_pathsets(a, op, op["amb"], o.tx_leg())
     assert not bad, bad[:10]
+
+
+def test_shell_subtree_changes_no_decision(monkeypatch):
+    """The room's walls, floor and ceiling (and the box bottoms lying in the floor) have the whole scene
+    on one side, so segments with both ends in the scene box skip them; with that subtree split off and
+    without it the path sets are bit-identical and the fields equal."""
+    w = S.room(grid=40)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("RISRT_SHELL", flag)
+        out[flag] = run_gpu(w)
+    a, b = out["1"]["paths"], out["0"]["paths"]
+    for key in ("seqs", "env"):
+        assert all(np.array_equal(np.sort(x), np.sort(y)) for x, y in zip(a[key], b[key]))
+    assert np.array_equal(np.asarray(a["los"]), np.asarray(b["los"]))
+    assert all(np.array_equal(x, y) for x, y in zip(a["vis"], b["vis"]))
+    assert np.array_equal(out["1"]["E"], out["0"]["E"])
+
+
+@pytest.mark.parametrize("maps", ["1", "0"])
+def test_endpoints_outside_scene_box(monkeypatch, maps):
+    """A room without its ceiling, the Tx outside wall x = 6 above the wall tops' height and receivers
+    outside the room: segments with an end outside the scene box must still be tested against the walls
+    (some pass over them, some are stopped); path sets and fields match the oracle."""
+    monkeypatch.setenv("RISRT_MAPS", maps)
+    w = S.room(grid=10, n_boxes=8)
+    keep = w.scene.face_id != 5                   # face 5 is the ceiling (z = 3)
+    fid = w.scene.face_id[keep]
+    w.scene = S.Scene(w.scene.verts, w.scene.tris[keep], np.where(fid > 5, fid - 1, fid).astype(np.int32),
+                      w.scene.mat_id[keep], w.scene.mats)
+    w.tx.pos = np.array([6.45, 1.7, 3.42], np.float32)
+    extra = np.array([[6.5, 1.0, 1.2], [3.0, 4.5, 1.2], [3.0, 2.0, 3.3], [-0.4, 2.0, 1.5], [2.0, 1.0, -0.3]],
+                     np.float32)
+    w.rx_xyz = np.concatenate([w.rx_xyz, extra]).astype(np.float32)
+    w.env_paths = True
+    g = run_gpu(w)
+    o, fld, E, P, Sx = _oracle_all(w)
+    op = o.rx_paths(w.rx_xyz)
+    bad = compare_pathsets(g["paths"], op, op["amb"], o.tx_leg())
+    assert not bad, bad[:10]
+    compare_fields(g["E"], g["P"], E, P, Sx, mask=~fld["amb"])
+    los = np.asarray(op["los"], bool)
+    assert los.any() and (~los).any()             # the Tx sees over the walls into part of the room
