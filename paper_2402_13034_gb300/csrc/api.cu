@@ -21,32 +21,37 @@ int fail(risrt_ctx* ctx, int code, const std::string& msg)
 
 std::atomic<long long> g_launches{0};
 
-void prof_begin(risrt_ctx* ctx, const char* name)
+void prof_begin(risrt_ctx* ctx, const char* name, cudaStream_t st)
 {
     if (!ctx || !ctx->profiling) return;
-    if (!ctx->prof_only.empty() && ctx->prof_only != name) {
-        ctx->prof_skip = true;
-        return;
-    }
-    ctx->prof_skip = false;
+    ctx->prof_skip = true;
+    if (!ctx->prof_only.empty() && ctx->prof_only != name) return;
     KernelPending p;
     p.name = name;
+    p.stream = st;
+    int got = 0;
     for (cudaEvent_t* ev : {&p.a, &p.b}) {
         if (!ctx->event_pool.empty()) {
             *ev = ctx->event_pool.back();
             ctx->event_pool.pop_back();
         } else if (cudaEventCreate(ev) != cudaSuccess) {
-            return;
+            break;
         }
+        ++got;
     }
-    cudaEventRecord(p.a, ctx->stream);
+    if (got < 2) {                       // no events: this launch goes unbracketed
+        if (got == 1) ctx->event_pool.push_back(p.a);
+        return;
+    }
+    ctx->prof_skip = false;
+    cudaEventRecord(p.a, st);
     ctx->pending.push_back(p);
 }
 
 void prof_end(risrt_ctx* ctx)
 {
     if (!ctx || !ctx->profiling || ctx->prof_skip || ctx->pending.empty()) return;
-    cudaEventRecord(ctx->pending.back().b, ctx->stream);
+    cudaEventRecord(ctx->pending.back().b, ctx->pending.back().stream);
 }
 
 static void prof_collect(risrt_ctx* ctx)
@@ -130,6 +135,13 @@ int risrt_destroy(risrt_ctx* ctx)
         cudaEventDestroy(p.b);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    for (cudaStream_t st : ctx->side)
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (cudaEvent_t e : ctx->ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->small) cudaFree(ctx->small);
     delete ctx;
     return RISRT_OK;

@@ -158,6 +158,7 @@ struct Antenna {
 struct KernelPending {
     const char* name;
     cudaEvent_t a, b;
+    cudaStream_t stream;         // the launch's stream: both events are recorded on it
 };
 
 struct risrt_ctx {
@@ -165,6 +166,8 @@ struct risrt_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     void* small = nullptr;       // 256 B of device memory for per-call reductions (allocated on first use)
+    cudaStream_t side[2] = {nullptr, nullptr};   // concurrent parts of a trace (created on first use)
+    cudaEvent_t ev[5] = {};                      // their fork / join events
     std::string err;
     Antenna tx{}, rx{};
     // tracing
@@ -295,17 +298,18 @@ int cuda_fail(risrt_ctx* ctx, cudaError_t e, const char* where);
     } while (0)
 
 extern std::atomic<long long> g_launches;
-void prof_begin(risrt_ctx* ctx, const char* name);
+void prof_begin(risrt_ctx* ctx, const char* name, cudaStream_t st);   // events on the launch's stream st
 void prof_end(risrt_ctx* ctx);
 // Launch a kernel (the `launch` expression) with optional event timing and error check.
-#define RISRT_KERNEL(ctx, name, launch)                                  \
+#define RISRT_KERNEL_ON(ctx, st, name, launch)                           \
     do {                                                                 \
-        ::risrt::prof_begin(ctx, name);                                  \
+        ::risrt::prof_begin(ctx, name, st);                              \
         launch;                                                          \
         ::risrt::g_launches.fetch_add(1, std::memory_order_relaxed);     \
         ::risrt::prof_end(ctx);                                          \
         RISRT_LAUNCH(ctx, name);                                         \
     } while (0)
+#define RISRT_KERNEL(ctx, name, launch) RISRT_KERNEL_ON(ctx, ((ctx) ? (ctx)->stream : cudaStream_t(0)), name, launch)
 
 int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_t n_verts,
                 const int32_t* tris_host, const int32_t* face_host, const int32_t* mat_host,

@@ -1656,6 +1656,22 @@ struct Candidates {
     int cap = 0;
 };
 
+// Scratch of one candidate search + validation: the work list (receiver, slot, path points), its
+// length, the queue of FP64 settlements, scan space and the validation's work counter. Searches that
+// run concurrently on different streams each need their own.
+struct LegBufs {
+    int *dense_r = nullptr, *dense_slot = nullptr;
+    int64_t* dense_off = nullptr;
+    float4* dense_pts = nullptr;
+    unsigned long long* dense_cnt = nullptr;
+    int4* rq = nullptr;
+    int rq_cap = 0;
+    unsigned* rq_cnt = nullptr;
+    void* scan_tmp = nullptr;
+    unsigned long long* work = nullptr;
+};
+constexpr int kTxLegQueue = 4096;   // settlements queued by the Tx leg (more are settled in place)
+
 }  // namespace
 
 // Occluder lists of every face for one source (CSR, leaf indices). Returns with *off == nullptr when
@@ -1682,6 +1698,20 @@ static int build_occ_lists(risrt_ctx* ctx, const DeviceScene& S, int64_t n_tris,
     RISRT_KERNEL(ctx, "k_i64_to_i32", (k_i64_to_i32<<<nblk(F + 1, 256), 256, 0, s>>>(off64, F + 1, off)));
     RISRT_KERNEL(ctx, "k_occ_lists", (k_occ_lists<<<nblk(pairs, 256), 256, 0, s>>>(S, src, n_tris, 1, nullptr, off, cursor, *idx)));
     *off_out = off;
+    return RISRT_OK;
+}
+
+// The context's two side streams and the events that order them against its stream (created on first
+// use, non-blocking, released with the context).
+static int side_streams(risrt_ctx* ctx)
+{
+    if (ctx->side[0]) return RISRT_OK;
+    for (cudaStream_t& st : ctx->side)
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(ctx, RISRT_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+    for (cudaEvent_t& ev : ctx->ev)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, RISRT_ERR_CUDA, "cudaEventCreateWithFlags failed");
     return RISRT_OK;
 }
 
@@ -1795,6 +1825,29 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     int cap = ps->cand_cap > 0 ? ps->cand_cap : 512;
     const int rq_cap = (int)std::min<int64_t>(16 * n_rx + 4096, (int64_t)1 << 22);
 
+    // Streams of the concurrent parts (the trace's own stream when profiling every kernel, so that
+    // each kernel's events bracket it alone, or when RISRT_OVERLAP=0)
+    cudaStream_t sA = s, sB = s;
+    {
+        const char* ov = getenv("RISRT_OVERLAP");
+        const bool overlap = !(ov && ov[0] == '0') && !(ctx->profiling && ctx->prof_only.empty());
+        if (overlap) {
+            if ((rc = side_streams(ctx))) return rc;
+            sA = ctx->side[0];
+            sB = ctx->side[1];
+        }
+    }
+    auto fork = [&](cudaStream_t to, cudaEvent_t ev) {
+        if (to == s) return;
+        cudaEventRecord(ev, s);
+        cudaStreamWaitEvent(to, ev, 0);
+    };
+    auto join = [&](cudaStream_t from, cudaEvent_t ev) {
+        if (from == s) return;
+        cudaEventRecord(ev, from);
+        cudaStreamWaitEvent(s, ev, 0);
+    };
+
     for (int attempt = 0; attempt < 6; ++attempt) {
         struct Layout {
             SeqTable tab[3];
@@ -1828,6 +1881,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             uint8_t* smap[2];        // visibility maps of the face cells from the Tx and from the RIS centre
             float4* elem_bb;         // element centre bounds in the RIS frame
             uint8_t* rx_state;       // per receiver: class of its RIS-aperture pyramid
+            LegBufs main, tx;        // work list, settlement queue and scan space of the receiver legs / of the
+                                     // Tx leg (which runs beside them on a second stream)
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -1876,6 +1931,18 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
             L.elem_bb = A.get<float4>(1);
             L.rx_state = A.get<uint8_t>((size_t)n_rx);
+            L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_off, L.dense_pts, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
+                             L.scan_tmp, L.counters + 6};
+            L.tx.dense_r = A.get<int>((size_t)cap);
+            L.tx.dense_slot = A.get<int>((size_t)cap);
+            L.tx.dense_off = A.get<int64_t>(2);
+            L.tx.dense_pts = A.get<float4>((size_t)cap * 2);
+            L.tx.dense_cnt = A.get<unsigned long long>(1);
+            L.tx.rq_cap = kTxLegQueue;
+            L.tx.rq = A.get<int4>((size_t)kTxLegQueue);
+            L.tx.rq_cnt = A.get<unsigned>(2);
+            L.tx.scan_tmp = A.get<char>(scan_temp_bytes(2));
+            L.tx.work = A.get<unsigned long long>(1);
         };
         Arena measure;
         Layout Lm;
@@ -1904,9 +1971,41 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         RISRT_CUDA(ctx, cudaMemsetAsync(flags_dev, 0, sizeof(int) * 4, s));
         float cxyz[3] = {ris->center[0], ris->center[1], ris->center[2]};
         RISRT_CUDA(ctx, cudaMemcpyAsync(c_xyz, cxyz, sizeof(cxyz), cudaMemcpyHostToDevice, s));
-
+        const float* rxp = rxs->xyz;
         const d3 Tpos = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
         const d3 Cpos = D3(fr.c[0], fr.c[1], fr.c[2]);
+
+        // Work that needs only the inputs runs beside the sequence tables and the candidate search on
+        // stream sB: the visibility maps (the receiver legs' validations wait for them) and the direct
+        // legs. The Tx leg runs on sA. Both join the trace's stream before the path offsets.
+        fork(sB, ctx->ev[0]);
+        // visibility maps of the face cells from the Tx (environment paths) and the RIS centre (Rx leg);
+        // they cost a fixed pass over all cells, so only traces with more receivers than half the
+        // cells use them (RISRT_MAPS=0 / 1 forces them off / on: both give the same decisions)
+        const char* maps_env = getenv("RISRT_MAPS");
+        const bool use_maps = sc->n_cells > 0 && n_rx > 1 &&
+                              (maps_env && maps_env[0] ? maps_env[0] == '1' : 2 * n_rx >= sc->n_cells);
+        if (use_maps) {
+            const float mg = 1e-4f * (1.f + ext);
+            if (max_env > 0)
+                RISRT_KERNEL_ON(ctx, sB, "k_src_map", (k_src_map<<<nblk(sc->n_cells, 128), 128, 0, sB>>>(S, Tpos, -1, mg, L.smap[0])));
+            if (max_rx > 0)
+                RISRT_KERNEL_ON(ctx, sB, "k_src_map", (k_src_map<<<nblk(sc->n_cells, 128), 128, 0, sB>>>(S, Cpos, ris->host_face, mg,
+                                                                                                L.smap[1])));
+        }
+        if (sB != s) RISRT_CUDA(ctx, cudaEventRecord(ctx->ev[1], sB));
+        // direct legs: element -> receiver visibility (aperture pyramids, then rays where undecided), LOS
+        {
+            int64_t nthreads = n_rx * W * 32;
+            RISRT_KERNEL_ON(ctx, sB, "k_elem_bounds", (k_elem_bounds<<<1, 256, 0, sB>>>(ris->elem, M, L.elem_bb)));
+            RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.elem_bb,
+                                                                                            ris->host_face, 1e-4f * (1.f + ext),
+                                                                                            L.rx_state)));
+            RISRT_KERNEL_ON(ctx, sB, "k_direct_vis", (k_direct_vis<<<nblk(nthreads, 128), 128, 0, sB>>>(S, rxp, n_rx, ris->elem, M, W, fr, ris->host_face,
+                                                             tol_base, ps->vis, counters, flags_dev + 1, L.rx_state)));
+            RISRT_KERNEL_ON(ctx, sB, "k_los", (k_los<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1)));
+        }
+
         const int64_t n_ids_of[3] = {n_ids_tx, n_ids_rx, n_ids_env};
         const d3 src_of[3] = {Tpos, Cpos, Tpos};
         RISRT_CUDA(ctx, cudaMemsetAsync(L.seq_n, 0, sizeof(int64_t) * 3, s));
@@ -1936,22 +2035,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                       L.occ_cursor[1], scan_tmp, &ps->occ_idx[1], &ps->occ_cap[1], &occ_off_src[1])))
                 return rc;
 
-        // visibility maps of the face cells from the Tx (environment paths) and the RIS centre (Rx leg);
-        // they cost a fixed pass over all cells, so only traces with more receivers than half the
-        // cells use them
-        // (RISRT_MAPS=0 / 1 forces them off / on: both give the same decisions)
-        const char* maps_env = getenv("RISRT_MAPS");
-        const bool use_maps = sc->n_cells > 0 && n_rx > 1 &&
-                              (maps_env && maps_env[0] ? maps_env[0] == '1' : 2 * n_rx >= sc->n_cells);
-        if (use_maps) {
-            const float mg = 1e-4f * (1.f + ext);
-            if (max_env > 0)
-                RISRT_KERNEL(ctx, "k_src_map", (k_src_map<<<nblk(sc->n_cells, 128), 128, 0, s>>>(S, Tpos, -1, mg, L.smap[0])));
-            if (max_rx > 0)
-                RISRT_KERNEL(ctx, "k_src_map", (k_src_map<<<nblk(sc->n_cells, 128), 128, 0, s>>>(S, Cpos, ris->host_face, mg,
-                                                                                               L.smap[1])));
-        }
-
         // receivers in Morton order for the candidate search
         {
             const unsigned bb_init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
@@ -1964,16 +2047,19 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.rx_order = (int*)L.rx_order_u;
         }
 
+        // One leg's candidate search and validation on stream st with scratch lb; the validation of a
+        // many-destination leg first waits for maps_ready (the visibility maps, built on another stream).
         auto run_candidates = [&](const SeqTable& t, const float* dst, int64_t n_dst, d3 src, int src_face,
-                                  int dst_face, Candidates& cs, int occ) -> int {
-            RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, s));
+                                  int dst_face, Candidates& cs, int occ, cudaStream_t st, const LegBufs& lb,
+                                  cudaEvent_t maps_ready) -> int {
+            RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, st));
             if (t.n > 0) {
                 dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
-                const RefineQ rq{L.rq, rq_cap, L.rq_cnt};
-                RISRT_CUDA(ctx, cudaMemsetAsync(L.rq_cnt, 0, sizeof(unsigned) * 2, s));
+                const RefineQ rq{lb.rq, lb.rq_cap, lb.rq_cnt};
+                RISRT_CUDA(ctx, cudaMemsetAsync(lb.rq_cnt, 0, sizeof(unsigned) * 2, st));
                 // many destinations: the candidate search writes the validation work list itself
-                const DenseOut dl = n_dst > 1 ? DenseOut{L.dense_r, L.dense_slot, L.dense_cnt} : DenseOut{nullptr, nullptr, nullptr};
-                if (dl.r) RISRT_CUDA(ctx, cudaMemsetAsync(L.dense_cnt, 0, sizeof(unsigned long long), s));
+                const DenseOut dl = n_dst > 1 ? DenseOut{lb.dense_r, lb.dense_slot, lb.dense_cnt} : DenseOut{nullptr, nullptr, nullptr};
+                if (dl.r) RISRT_CUDA(ctx, cudaMemsetAsync(lb.dense_cnt, 0, sizeof(unsigned long long), st));
                 // sequences that can reach each super-patch of kSuperRx Morton-consecutive destinations
                 const int words = (t.n + 31) / 32;
                 const int* slist = nullptr;
@@ -1981,11 +2067,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 int64_t slist_stride = 0;
                 if (n_dst > kCandThreads) {
                     const int64_t n_super = (n_dst + kSuperRx - 1) / kSuperRx;
-                    RISRT_KERNEL(ctx, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, s>>>(dst, L.rx_order, n_dst,
-                                                                                                      L.sp_box)));
-                    RISRT_KERNEL(ctx, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
-                                                                  256, 0, s>>>(S, t.e, t.n, L.sp_box, n_super, words, L.sp_mask)));
-                    RISRT_KERNEL(ctx, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, s>>>(
+                    RISRT_KERNEL_ON(ctx, st, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, st>>>(dst, L.rx_order, n_dst,
+                                                                                                       L.sp_box)));
+                    RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
+                                                                  256, 0, st>>>(S, t.e, t.n, L.sp_box, n_super, words, L.sp_mask)));
+                    RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
                                                             L.sp_mask, words, n_super, (int64_t)words * 32, L.sp_list, L.sp_cnt)));
                     slist = L.sp_list;
                     slist_cnt = L.sp_cnt;
@@ -1995,71 +2081,65 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 if (F <= kMaxSmemFaces) {
                     const size_t shm = sizeof(FaceTest) * (size_t)F;
                     cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-                    RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
+                    RISRT_KERNEL_ON(ctx, st, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, st>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
                                                           cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl)));
                 } else {
-                    RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
+                    RISRT_KERNEL_ON(ctx, st, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, st>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
                                                           cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl)));
                 }
-                RISRT_KERNEL(ctx, "k_refine_cand", (k_refine_cand<<<ctx->sm_count * 2, 256, 0, s>>>(
+                RISRT_KERNEL_ON(ctx, st, "k_refine_cand", (k_refine_cand<<<ctx->sm_count * 2, 256, 0, st>>>(
                                                        S, dst, src, t.e, t.d, rq, cs.cand, cs.cnt, cs.cap, flags_dev, counters, dl)));
                 // dense candidate list (written above for many destinations), then persistent validation;
                 // its length stays on the device (no host round trip)
-                const long long* d_total = (const long long*)L.dense_cnt;
+                const long long* d_total = (const long long*)lb.dense_cnt;
                 if (!dl.r) {
-                    RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, s>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
-                    RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, L.dense_off, n_dst + 1, scan_tmp, s));
-                    RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, s>>>(cs.cnt, L.dense_off, n_dst, cs.cap,
-                                                                                                       L.dense_r, L.dense_slot)));
-                    d_total = (const long long*)(L.dense_off + n_dst);
+                    RISRT_KERNEL_ON(ctx, st, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, st>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
+                    RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, lb.dense_off, n_dst + 1, lb.scan_tmp, st));
+                    RISRT_KERNEL_ON(ctx, st, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, st>>>(cs.cnt, lb.dense_off, n_dst, cs.cap,
+                                                                                                        lb.dense_r, lb.dense_slot)));
+                    d_total = (const long long*)(lb.dense_off + n_dst);
                 }
-                RISRT_CUDA(ctx, cudaMemsetAsync(counters + 6, 0, sizeof(unsigned long long), s));
-                const int *vr = L.dense_r, *vs = L.dense_slot;
+                RISRT_CUDA(ctx, cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long), st));
+                const int *vr = lb.dense_r, *vs = lb.dense_slot;
                 // the validation queue reuses the buffer (the candidate settlements are done)
-                const RefineQ vq{L.rq, rq_cap, L.rq_cnt + 1};
-                RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<ctx->sm_count * 32, 256, 0, s>>>(
-                                                       dst, t.e, cs.cand, cs.cap, vr, vs, d_total, L.dense_pts)));
+                const RefineQ vq{lb.rq, lb.rq_cap, lb.rq_cnt + 1};
+                RISRT_KERNEL_ON(ctx, st, "k_cand_points", (k_cand_points<<<ctx->sm_count * 32, 256, 0, st>>>(
+                                                       dst, t.e, cs.cand, cs.cap, vr, vs, d_total, lb.dense_pts)));
+                const uint8_t* smap = n_dst > 1 && use_maps ? L.smap[occ] : nullptr;
+                if (smap && maps_ready) RISRT_CUDA(ctx, cudaStreamWaitEvent(st, maps_ready, 0));
                 const unsigned blocks = (unsigned)ctx->sm_count * RISRT_VALIDATE_MINB;
-                RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
+                RISRT_KERNEL_ON(ctx, st, "k_validate", (k_validate<<<blocks, kValThreads, 0, st>>>(
                                                     S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
-                                                    vs, L.dense_pts, d_total, counters + 6, tol_base, counters, flags_dev + 1,
-                                                    counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq,
-                                                    n_dst > 1 && use_maps ? L.smap[occ] : nullptr)));
-                RISRT_KERNEL(ctx, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, s>>>(
+                                                    vs, lb.dense_pts, d_total, lb.work, tol_base, counters, flags_dev + 1,
+                                                    counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq, smap)));
+                RISRT_KERNEL_ON(ctx, st, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, st>>>(
                                                       S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
             }
             const int warps = 4;
             size_t shm = sizeof(int) * (size_t)cs.cap * warps;
             if (shm > 48 * 1024) cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-            RISRT_KERNEL(ctx, "k_finalize", (k_finalize<<<nblk(n_dst, warps), 32 * warps, shm, s>>>(cs.cand, cs.cnt, n_dst, cs.cap, t.e, cs.cnt64)));
+            RISRT_KERNEL_ON(ctx, st, "k_finalize", (k_finalize<<<nblk(n_dst, warps), 32 * warps, shm, st>>>(cs.cand, cs.cnt, n_dst, cs.cap, t.e, cs.cnt64)));
             return RISRT_OK;
         };
 
-        // Tx leg (destination: RIS centre, mounted on host_face)
-        if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg, 0))) return rc;
-        RISRT_KERNEL(ctx, "k_tx_vis", (k_tx_vis<<<nblk(M, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, ris->host_face, tol_base, tx_vis, counters,
+        // Tx leg (destination: RIS centre, mounted on host_face), its element visibility, c_m (its path
+        // count stays on the device) and path ids, beside the receiver legs on stream sA
+        fork(sA, ctx->ev[2]);
+        if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg, 0, sA, L.tx, nullptr))) return rc;
+        RISRT_KERNEL_ON(ctx, sA, "k_tx_vis", (k_tx_vis<<<nblk(M, 128), 128, 0, sA>>>(S, ris->elem, M, fr, tx, ris->host_face, tol_base, tx_vis, counters,
                                               flags_dev + 1)));
-        // Rx leg (source: RIS centre) and environment paths (source: Tx)
-        const float* rxp = rxs->xyz;
-        if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx, 1))) return rc;
-        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv, 0))) return rc;
-        // direct legs
-        {
-            int64_t nthreads = n_rx * W * 32;
-            RISRT_KERNEL(ctx, "k_elem_bounds", (k_elem_bounds<<<1, 256, 0, s>>>(ris->elem, M, L.elem_bb)));
-            RISRT_KERNEL(ctx, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, fr, L.elem_bb,
-                                                                                           ris->host_face, 1e-4f * (1.f + ext),
-                                                                                           L.rx_state)));
-            RISRT_KERNEL(ctx, "k_direct_vis", (k_direct_vis<<<nblk(nthreads, 128), 128, 0, s>>>(S, rxp, n_rx, ris->elem, M, W, fr, ris->host_face,
-                                                             tol_base, ps->vis, counters, flags_dev + 1, L.rx_state)));
-            RISRT_KERNEL(ctx, "k_los", (k_los<<<nblk(n_rx, 128), 128, 0, s>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1)));
-        }
-        // c_m (its path count stays on the device), Tx-leg ids, Rx-leg and environment offsets
-        RISRT_KERNEL(ctx, "k_cm", (k_cm<<<nblk((int64_t)M * 32, 128), 128, 0, s>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand,
-                                                                                 ctx_leg.cnt64, tab[0].e, tab[0].d, ps->cm)));
-        RISRT_KERNEL(ctx, "k_tx_ids", (k_tx_ids<<<1, 256, 0, s>>>(ctx_leg.cand, ctx_leg.cnt64, cap, tab[0].e, L.tx_ids)));
+        RISRT_KERNEL_ON(ctx, sA, "k_cm", (k_cm<<<nblk((int64_t)M * 32, 128), 128, 0, sA>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand,
+                                                                                  ctx_leg.cnt64, tab[0].e, tab[0].d, ps->cm)));
+        RISRT_KERNEL_ON(ctx, sA, "k_tx_ids", (k_tx_ids<<<1, 256, 0, sA>>>(ctx_leg.cand, ctx_leg.cnt64, cap, tab[0].e, L.tx_ids)));
+        // Rx leg (source: RIS centre) and environment paths (source: Tx); their validations use the maps
+        const cudaEvent_t maps_ready = sB != s ? ctx->ev[1] : nullptr;
+        if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx, 1, s, L.main, maps_ready))) return rc;
+        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv, 0, s, L.main, maps_ready))) return rc;
+        join(sA, ctx->ev[3]);
+        join(sB, ctx->ev[4]);
+        // Rx-leg and environment offsets
         RISRT_KERNEL(ctx, "k_count_total", (k_count_total<<<nblk(n_rx, 256), 256, 0, s>>>(crx.cnt64, n_rx, tot)));
         RISRT_CUDA(ctx, cudaMemsetAsync(tot + n_rx, 0, sizeof(int64_t), s));
         RISRT_CUDA(ctx, exclusive_scan_i64(tot, ps->rx_off, n_rx + 1, scan_tmp, s));

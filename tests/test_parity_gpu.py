@@ -202,14 +202,16 @@ def test_visibility_maps_change_no_decision(monkeypatch):
     assert not bad, bad[:10]
 
 
-def test_shell_subtree_changes_no_decision(monkeypatch):
-    """The room's walls, floor and ceiling (and the box bottoms lying in the floor) have the whole scene
-    on one side, so segments with both ends in the scene box skip them; with that subtree split off and
-    without it the path sets are bit-identical and the fields equal."""
+@pytest.mark.parametrize("switch", ["RISRT_SHELL", "RISRT_OVERLAP"])
+def test_switches_change_no_decision(monkeypatch, switch):
+    """RISRT_SHELL: the room's walls, floor and ceiling (and the box bottoms lying in the floor) have the
+    whole scene on one side, so segments with both ends in the scene box skip them. RISRT_OVERLAP: the
+    Tx leg, the visibility maps and the direct legs run on side streams beside the receiver legs. With
+    either switched off the path sets are bit-identical and the fields equal."""
     w = S.room(grid=40)
     out = {}
     for flag in ("1", "0"):
-        monkeypatch.setenv("RISRT_SHELL", flag)
+        monkeypatch.setenv(switch, flag)
         out[flag] = run_gpu(w)
     a, b = out["1"]["paths"], out["0"]["paths"]
     for key in ("seqs", "env"):
