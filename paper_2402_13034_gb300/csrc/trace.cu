@@ -678,54 +678,40 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int* __re
     if (i < n) b[i] = (int)a[i];
 }
 
-// Counting sort of the dense candidate list by first face, so the lanes of a warp share one
-// occluder list (and similar first segments).
-
-
-// FP32 reflection points of every dense candidate (same back-trace as the candidate filter): the
-// last point P (next to the destination) and, for order 2, the first point P1.
-__global__ void k_cand_points(const float* __restrict__ dst_xyz, const SeqEntry* __restrict__ seqs,
-                              const int* __restrict__ cand, int cap, const int* __restrict__ dense_r,
-                              const int* __restrict__ dense_slot, const long long* __restrict__ d_total,
-                              float4* __restrict__ pts)
+// FP32 reflection points of a candidate (the same back-trace as the candidate filter): q0 = the last
+// point P (next to the destination R), q1 = the first point P1 (order 2; P for order 1); w holds a
+// first-order bound on each point's error from the FP32 roundings of the inputs (images, planes and
+// signed distances are FP32 copies of FP64 values) and of these operations, doubled.
+__device__ __forceinline__ void path_points(const SeqEntry& e, float3 R, float4& q0, float4& q1)
 {
-    const long long total = *d_total;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int r = dense_r[i];
-        const int si = cand[(int64_t)r * cap + dense_slot[i]];
-        const SeqEntry e = seqs[si];
-        const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
-        const float sR = dot(xyz(e.pL), R) - e.pL.w;
-        const float den = sR + e.sL.w;
-        const float t = sR / den;
-        const float3 d = xyz(e.sL) - R;
-        const float3 P = R + d * t;
-        // first-order bound on |P - P_exact| from the FP32 roundings of the inputs (images, planes and
-        // signed distances are FP32 copies of FP64 values) and of these operations, doubled
-        const float eps = 5.9604645e-8f;
-        auto l1 = [](float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); };
-        const float mag = l1(R) + l1(xyz(e.sL)) + fabsf(e.pL.w);
-        const float e_s = 8.f * eps * mag;
-        const float e_den = e_s + 2.f * eps * fabsf(e.sL.w) + eps * fabsf(den);
-        const float e_t = (e_s + fabsf(t) * e_den) / fabsf(den) + 2.f * eps * fabsf(t);
-        const float errP = l1(d) * e_t + (fabsf(t) + 1.f) * 4.f * eps * mag;
-        float3 P1 = P;
-        float errP1 = errP;
-        if (e.info.w == 2) {
-            const float s1P = dot(xyz(e.p1), P) - e.p1.w;
-            const float den1 = s1P + e.s1.w;
-            const float t1 = s1P / den1;
-            const float3 d1 = xyz(e.s1) - P;
-            P1 = P + d1 * t1;
-            const float mag1 = l1(P) + l1(xyz(e.s1)) + fabsf(e.p1.w);
-            const float e_s1 = l1(xyz(e.p1)) * errP + 8.f * eps * mag1;
-            const float e_den1 = e_s1 + 2.f * eps * fabsf(e.s1.w) + eps * fabsf(den1);
-            const float e_t1 = (e_s1 + fabsf(t1) * e_den1) / fabsf(den1) + 2.f * eps * fabsf(t1);
-            errP1 = errP + l1(d1) * e_t1 + fabsf(t1) * (errP + 4.f * eps * l1(xyz(e.s1))) + 4.f * eps * mag1;
-        }
-        pts[2 * i] = make_float4(P.x, P.y, P.z, 2.f * errP);
-        pts[2 * i + 1] = make_float4(P1.x, P1.y, P1.z, 2.f * errP1);
+    const float sR = dot(xyz(e.pL), R) - e.pL.w;
+    const float den = sR + e.sL.w;
+    const float t = sR / den;
+    const float3 d = xyz(e.sL) - R;
+    const float3 P = R + d * t;
+    const float eps = 5.9604645e-8f;
+    auto l1 = [](float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); };
+    const float mag = l1(R) + l1(xyz(e.sL)) + fabsf(e.pL.w);
+    const float e_s = 8.f * eps * mag;
+    const float e_den = e_s + 2.f * eps * fabsf(e.sL.w) + eps * fabsf(den);
+    const float e_t = (e_s + fabsf(t) * e_den) / fabsf(den) + 2.f * eps * fabsf(t);
+    const float errP = l1(d) * e_t + (fabsf(t) + 1.f) * 4.f * eps * mag;
+    float3 P1 = P;
+    float errP1 = errP;
+    if (e.info.w == 2) {
+        const float s1P = dot(xyz(e.p1), P) - e.p1.w;
+        const float den1 = s1P + e.s1.w;
+        const float t1 = s1P / den1;
+        const float3 d1 = xyz(e.s1) - P;
+        P1 = P + d1 * t1;
+        const float mag1 = l1(P) + l1(xyz(e.s1)) + fabsf(e.p1.w);
+        const float e_s1 = l1(xyz(e.p1)) * errP + 8.f * eps * mag1;
+        const float e_den1 = e_s1 + 2.f * eps * fabsf(e.s1.w) + eps * fabsf(den1);
+        const float e_t1 = (e_s1 + fabsf(t1) * e_den1) / fabsf(den1) + 2.f * eps * fabsf(t1);
+        errP1 = errP + l1(d1) * e_t1 + fabsf(t1) * (errP + 4.f * eps * l1(xyz(e.s1))) + 4.f * eps * mag1;
     }
+    q0 = make_float4(P.x, P.y, P.z, 2.f * errP);
+    q1 = make_float4(P1.x, P1.y, P1.z, 2.f * errP1);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1005,7 +991,7 @@ constexpr int kSteps = RISRT_VALIDATE_STEPS;
 __global__ void __launch_bounds__(kValThreads, RISRT_VALIDATE_MINB)
 k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_face, int dst_face,
            const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int* __restrict__ cand, int cap,
-           const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const float4* __restrict__ dpts,
+           const int* __restrict__ dense_r, const int* __restrict__ dense_slot,
            const long long* __restrict__ d_total, unsigned long long* __restrict__ next, float tol_base,
            unsigned long long* refines,
            int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx,
@@ -1015,6 +1001,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     const float3 srcf = to_f(src);
     const bool src_in = in_scene_box(S, src);   // with both ends in the scene box a segment skips the shell
     bool dst_in = false;
+    float p1err = 0.f;                            // error bound of the first reflection point
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     TraceCounters tc{};
@@ -1053,10 +1040,9 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
             cur = root == kNoRoot ? kNone : root;
             sp = 0;
             if (j == 0 && smap) {       // first segment: the source's visibility map of face f1
-                const float4 q1 = dpts[2 * item + 1];
-                if (q1.w <= 0.5f * kMapDelta) {
+                if (p1err <= 0.5f * kMapDelta) {
                     const FaceGrid g = S.face_grid[info.x];
-                    const float3 dq = xyz(q1) - xyz(g.o);
+                    const float3 dq = p[1] - xyz(g.o);
                     const float fa = floorf((dot(dq, xyz(g.u)) - g.u.w) / g.o.w);
                     const float fb = floorf((dot(dq, xyz(g.v)) - g.v.w) / g.dv);
                     if (fa >= 0.f && fa < (float)g.nu && fb >= 0.f && fb < (float)g.nv) {
@@ -1110,10 +1096,14 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                     r = dense_r[item];
                     slot = dense_slot[item];
                     si = cand[(int64_t)r * cap + slot];
-                    info = seqs[si].info;
+                    const SeqEntry e = seqs[si];
+                    info = e.info;
                     const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
                     dst_in = in_scene_box(S, R);
-                    const float3 PL = xyz(dpts[2 * item]), P1 = xyz(dpts[2 * item + 1]);
+                    float4 q0, q1;
+                    path_points(e, R, q0, q1);
+                    p1err = q1.w;
+                    const float3 PL = xyz(q0), P1 = xyz(q1);
                     p[0] = srcf;
                     if (info.w == 2) {
                         p[1] = P1;
@@ -1656,13 +1646,12 @@ struct Candidates {
     int cap = 0;
 };
 
-// Scratch of one candidate search + validation: the work list (receiver, slot, path points), its
+// Scratch of one candidate search + validation: the work list (receiver, slot), its
 // length, the queue of FP64 settlements, scan space and the validation's work counter. Searches that
 // run concurrently on different streams each need their own.
 struct LegBufs {
     int *dense_r = nullptr, *dense_slot = nullptr;
     int64_t* dense_off = nullptr;
-    float4* dense_pts = nullptr;
     unsigned long long* dense_cnt = nullptr;
     int4* rq = nullptr;
     int rq_cap = 0;
@@ -1860,7 +1849,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             float* c_xyz;
             int *dense_r, *dense_slot;
             int64_t* dense_off;
-            float4* dense_pts;
             int* occ_cnt[2];
             int64_t* occ_off64[2];
             int* occ_off[2];
@@ -1904,7 +1892,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.dense_r = A.get<int>((size_t)n_rx * cap);
             L.dense_slot = A.get<int>((size_t)n_rx * cap);
             L.dense_off = A.get<int64_t>(n_rx + 1);
-            L.dense_pts = A.get<float4>((size_t)n_rx * cap * 2);
             L.crx.cnt64_tmp = A.get<int64_t>(n_rx + 1);
             L.cenv.cnt64_tmp = L.crx.cnt64_tmp;
             L.ctx_leg.cnt64_tmp = A.get<int64_t>(2);
@@ -1931,12 +1918,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
             L.elem_bb = A.get<float4>(1);
             L.rx_state = A.get<uint8_t>((size_t)n_rx);
-            L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_off, L.dense_pts, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
+            L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_off, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
                              L.scan_tmp, L.counters + 6};
             L.tx.dense_r = A.get<int>((size_t)cap);
             L.tx.dense_slot = A.get<int>((size_t)cap);
             L.tx.dense_off = A.get<int64_t>(2);
-            L.tx.dense_pts = A.get<float4>((size_t)cap * 2);
             L.tx.dense_cnt = A.get<unsigned long long>(1);
             L.tx.rq_cap = kTxLegQueue;
             L.tx.rq = A.get<int4>((size_t)kTxLegQueue);
@@ -2105,14 +2091,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 const int *vr = lb.dense_r, *vs = lb.dense_slot;
                 // the validation queue reuses the buffer (the candidate settlements are done)
                 const RefineQ vq{lb.rq, lb.rq_cap, lb.rq_cnt + 1};
-                RISRT_KERNEL_ON(ctx, st, "k_cand_points", (k_cand_points<<<ctx->sm_count * 32, 256, 0, st>>>(
-                                                       dst, t.e, cs.cand, cs.cap, vr, vs, d_total, lb.dense_pts)));
                 const uint8_t* smap = n_dst > 1 && use_maps ? L.smap[occ] : nullptr;
                 if (smap && maps_ready) RISRT_CUDA(ctx, cudaStreamWaitEvent(st, maps_ready, 0));
                 const unsigned blocks = (unsigned)ctx->sm_count * RISRT_VALIDATE_MINB;
                 RISRT_KERNEL_ON(ctx, st, "k_validate", (k_validate<<<blocks, kValThreads, 0, st>>>(
                                                     S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
-                                                    vs, lb.dense_pts, d_total, lb.work, tol_base, counters, flags_dev + 1,
+                                                    vs, d_total, lb.work, tol_base, counters, flags_dev + 1,
                                                     counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq, smap)));
                 RISRT_KERNEL_ON(ctx, st, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, st>>>(
                                                       S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
@@ -2275,7 +2259,6 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
         SeqEntry* e;
         SeqEntryD* d;
         int *cand, *cnt, *dense_r, *dense_slot, *flags;
-        float4* dense_pts;
         unsigned long long* counters;
         float* dst;
     };
@@ -2292,7 +2275,6 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
         L.dense_off = A.get<int64_t>(2);
         L.dense_r = A.get<int>(cap);
         L.dense_slot = A.get<int>(cap);
-        L.dense_pts = A.get<float4>(2 * (size_t)cap);
         L.ids = A.get<int64_t>(cap);
         L.counters = A.get<unsigned long long>(8);
         L.flags = A.get<int>(4);
@@ -2355,13 +2337,10 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));
         if (host_flags[0]) return fail(ctx, RISRT_ERR_CAPACITY, "more than 4096 geometric candidates");
         if (total > 0) {
-            RISRT_KERNEL(ctx, "k_cand_points", (k_cand_points<<<nblk(total, 256), 256, 0, s>>>(
-                                                   L.dst, L.e, L.cand, cap, L.dense_r, L.dense_slot,
-                                                   (const long long*)(L.dense_off + 1), L.dense_pts)));
             const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * 8, (total + kValThreads - 1) / kValThreads);
             RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                 S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
-                                                L.dense_slot, L.dense_pts, (const long long*)(L.dense_off + 1), L.counters + 6,
+                                                L.dense_slot, (const long long*)(L.dense_off + 1), L.counters + 6,
                                                 tol_base, L.counters,
                                                 L.flags + 1, L.counters + 2, nullptr, nullptr, RefineQ{nullptr, 0, nullptr},
                                                 nullptr)));
