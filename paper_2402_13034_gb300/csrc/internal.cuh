@@ -166,8 +166,8 @@ struct risrt_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     void* small = nullptr;       // 256 B of device memory for per-call reductions (allocated on first use)
-    cudaStream_t side[2] = {nullptr, nullptr};   // concurrent parts of a trace (created on first use)
-    cudaEvent_t ev[5] = {};                      // their fork / join events
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // concurrent parts of a trace (created on first use)
+    cudaEvent_t ev[7] = {};                               // their fork / join events
     std::string err;
     Antenna tx{}, rx{};
     // tracing

@@ -271,7 +271,10 @@ struct DenseOut {
     int* slot;
     unsigned long long* cnt;
 };
-constexpr int kDenseBuf = 256;   // staged work-list entries per warp
+#ifndef RISRT_DENSE_BUF
+#define RISRT_DENSE_BUF 256
+#endif
+constexpr int kDenseBuf = RISRT_DENSE_BUF;   // staged work-list entries per warp (must be >= 32)
 
 // Margin of the beam culling for a box: far beyond the FP32 error of the plane and corner arithmetic.
 __device__ __forceinline__ float cull_margin(float3 lo, float3 hi)
@@ -1658,6 +1661,10 @@ struct LegBufs {
     unsigned* rq_cnt = nullptr;
     void* scan_tmp = nullptr;
     unsigned long long* work = nullptr;
+    float4* sp_box = nullptr;        // super-patch boxes [n_super][2]
+    unsigned* sp_mask = nullptr;     // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
+    int* sp_list = nullptr;          // [n_super][32 ceil(n_seq / 32)] the same as index lists
+    int* sp_cnt = nullptr;           // [n_super]
 };
 constexpr int kTxLegQueue = 4096;   // settlements queued by the Tx leg (more are settled in place)
 
@@ -1816,7 +1823,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
 
     // Streams of the concurrent parts (the trace's own stream when profiling every kernel, so that
     // each kernel's events bracket it alone, or when RISRT_OVERLAP=0)
-    cudaStream_t sA = s, sB = s;
+    cudaStream_t sA = s, sB = s, sC = s;
     {
         const char* ov = getenv("RISRT_OVERLAP");
         const bool overlap = !(ov && ov[0] == '0') && !(ctx->profiling && ctx->prof_only.empty());
@@ -1824,6 +1831,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             if ((rc = side_streams(ctx))) return rc;
             sA = ctx->side[0];
             sB = ctx->side[1];
+            sC = ctx->side[2];
         }
     }
     auto fork = [&](cudaStream_t to, cudaEvent_t ev) {
@@ -1860,17 +1868,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             unsigned long long* dense_cnt;   // entries of the work list written by the candidate search
             int64_t* seq_n;                  // sizes of the three sequence tables
             int64_t* tx_ids;                 // [cap] sequence ids of the Tx-leg paths
-            float4* sp_box;          // super-patch boxes [n_super][2]
-            unsigned* sp_mask;       // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
-            int* sp_list;            // [n_super][32 ceil(n_seq / 32)] the same as index lists
-            int* sp_cnt;             // [n_super]
             int4* rq;                // deferred FP64 settlements (candidates, then validation)
             unsigned* rq_cnt;
             uint8_t* smap[2];        // visibility maps of the face cells from the Tx and from the RIS centre
             float4* elem_bb;         // element centre bounds in the RIS frame
             uint8_t* rx_state;       // per receiver: class of its RIS-aperture pyramid
-            LegBufs main, tx;        // work list, settlement queue and scan space of the receiver legs / of the
-                                     // Tx leg (which runs beside them on a second stream)
+            LegBufs main, env, tx;   // work lists, settlement queues and scan space of the Rx leg, of the
+                                     // environment paths and of the Tx leg (they run on separate streams)
         };
         auto layout = [&](Arena& A, Layout& L) {
             for (int i = 0; i < 3; ++i) {
@@ -1893,7 +1897,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.dense_slot = A.get<int>((size_t)n_rx * cap);
             L.dense_off = A.get<int64_t>(n_rx + 1);
             L.crx.cnt64_tmp = A.get<int64_t>(n_rx + 1);
-            L.cenv.cnt64_tmp = L.crx.cnt64_tmp;
+            L.cenv.cnt64_tmp = A.get<int64_t>(env ? n_rx + 1 : 1);
             L.ctx_leg.cnt64_tmp = A.get<int64_t>(2);
             for (int q = 0; q < 2; ++q) {
                 L.occ_cnt[q] = A.get<int>(F + 1);
@@ -1909,10 +1913,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.dense_cnt = A.get<unsigned long long>(1);
             L.seq_n = A.get<int64_t>(3);
             L.tx_ids = A.get<int64_t>((size_t)cap);
-            L.sp_box = A.get<float4>((size_t)n_super * 2);
-            L.sp_mask = A.get<unsigned>((size_t)n_super * ((n_ids_max + 31) / 32 + 1));
-            L.sp_list = A.get<int>((size_t)n_super * ((n_ids_max + 31) / 32 + 1) * 32);
-            L.sp_cnt = A.get<int>((size_t)n_super);
             L.rq = A.get<int4>((size_t)rq_cap);
             L.rq_cnt = A.get<unsigned>(2);
             for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
@@ -1920,6 +1920,24 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.rx_state = A.get<uint8_t>((size_t)n_rx);
             L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_off, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
                              L.scan_tmp, L.counters + 6};
+            // the environment paths run beside the Rx leg: their own work list, queue and scan space
+            const size_t n_env_rx = env ? (size_t)n_rx : 1;
+            L.env.dense_r = A.get<int>(n_env_rx * cap);
+            L.env.dense_slot = A.get<int>(n_env_rx * cap);
+            L.env.dense_off = A.get<int64_t>(n_env_rx + 1);
+            L.env.dense_cnt = A.get<unsigned long long>(1);
+            L.env.rq_cap = env ? rq_cap : 1;
+            L.env.rq = A.get<int4>((size_t)L.env.rq_cap);
+            L.env.rq_cnt = A.get<unsigned>(2);
+            L.env.scan_tmp = A.get<char>(scan_temp_bytes((int64_t)n_env_rx + 1));
+            L.env.work = A.get<unsigned long long>(1);
+            for (LegBufs* lb : {&L.main, &L.env}) {
+                const size_t ns = lb == &L.env && !env ? 1 : (size_t)n_super;
+                lb->sp_box = A.get<float4>(ns * 2);
+                lb->sp_mask = A.get<unsigned>(ns * ((n_ids_max + 31) / 32 + 1));
+                lb->sp_list = A.get<int>(ns * ((n_ids_max + 31) / 32 + 1) * 32);
+                lb->sp_cnt = A.get<int>(ns);
+            }
             L.tx.dense_r = A.get<int>((size_t)cap);
             L.tx.dense_slot = A.get<int>((size_t)cap);
             L.tx.dense_off = A.get<int64_t>(2);
@@ -1963,7 +1981,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
 
         // Work that needs only the inputs runs beside the sequence tables and the candidate search on
         // stream sB: the visibility maps (the receiver legs' validations wait for them) and the direct
-        // legs. The Tx leg runs on sA. Both join the trace's stream before the path offsets.
+        // legs. The Tx leg runs on sA, the environment paths on sC beside the Rx leg. All join the
+        // trace's stream before the path offsets.
         fork(sB, ctx->ev[0]);
         // visibility maps of the face cells from the Tx (environment paths) and the RIS centre (Rx leg);
         // they cost a fixed pass over all cells, so only traces with more receivers than half the
@@ -2054,13 +2073,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 if (n_dst > kCandThreads) {
                     const int64_t n_super = (n_dst + kSuperRx - 1) / kSuperRx;
                     RISRT_KERNEL_ON(ctx, st, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, st>>>(dst, L.rx_order, n_dst,
-                                                                                                       L.sp_box)));
+                                                                                                       lb.sp_box)));
                     RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
-                                                                  256, 0, st>>>(S, t.e, t.n, L.sp_box, n_super, words, L.sp_mask)));
+                                                                  256, 0, st>>>(S, t.e, t.n, lb.sp_box, n_super, words, lb.sp_mask)));
                     RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
-                                                            L.sp_mask, words, n_super, (int64_t)words * 32, L.sp_list, L.sp_cnt)));
-                    slist = L.sp_list;
-                    slist_cnt = L.sp_cnt;
+                                                            lb.sp_mask, words, n_super, (int64_t)words * 32, lb.sp_list, lb.sp_cnt)));
+                    slist = lb.sp_list;
+                    slist_cnt = lb.sp_cnt;
                     slist_stride = (int64_t)words * 32;
                 }
                 const int* ord = n_dst > 1 ? L.rx_order : nullptr;
@@ -2119,10 +2138,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         RISRT_KERNEL_ON(ctx, sA, "k_tx_ids", (k_tx_ids<<<1, 256, 0, sA>>>(ctx_leg.cand, ctx_leg.cnt64, cap, tab[0].e, L.tx_ids)));
         // Rx leg (source: RIS centre) and environment paths (source: Tx); their validations use the maps
         const cudaEvent_t maps_ready = sB != s ? ctx->ev[1] : nullptr;
+        fork(sC, ctx->ev[5]);
         if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx, 1, s, L.main, maps_ready))) return rc;
-        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv, 0, s, L.main, maps_ready))) return rc;
+        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv, 0, sC, L.env, maps_ready))) return rc;
         join(sA, ctx->ev[3]);
         join(sB, ctx->ev[4]);
+        join(sC, ctx->ev[6]);
         // Rx-leg and environment offsets
         RISRT_KERNEL(ctx, "k_count_total", (k_count_total<<<nblk(n_rx, 256), 256, 0, s>>>(crx.cnt64, n_rx, tot)));
         RISRT_CUDA(ctx, cudaMemsetAsync(tot + n_rx, 0, sizeof(int64_t), s));
