@@ -137,7 +137,7 @@ __device__ __forceinline__ int bvh4_step(const Bvh4Node& nd, float3 a, float3 in
 // Segment ends in the scene box (exact comparisons): a segment between two such points meets the plane
 // of a shell triangle at most at an end or lies in it, and neither counts as a hit (hits closer than
 // the tolerance to an end are ignored; a segment in a triangle's plane passes), so its traversal
-// starts at root_main and never sees the shell.
+// visits root_main only and never sees the shell.
 __device__ __forceinline__ bool in_scene_box(const DeviceScene& S, float3 p)
 {
     return p.x >= S.box_lo.x && p.y >= S.box_lo.y && p.z >= S.box_lo.z && p.x <= S.box_hi.x && p.y <= S.box_hi.y &&
@@ -148,9 +148,16 @@ __device__ __forceinline__ bool in_scene_box(const DeviceScene& S, d3 p)
     return p.x >= (double)S.box_lo.x && p.y >= (double)S.box_lo.y && p.z >= (double)S.box_lo.z &&
            p.x <= (double)S.box_hi.x && p.y <= (double)S.box_hi.y && p.z <= (double)S.box_hi.z;
 }
-__device__ __forceinline__ int occ_root(const DeviceScene& S, bool ends_in_box)
+// First node of an occlusion walk; a segment with an end outside the scene box also pushes the shell
+// subtree onto the walk's stack. kNoRoot: nothing to visit.
+__device__ __forceinline__ int occ_start(const DeviceScene& S, bool ends_in_box, int* stack, int& sp)
 {
-    return ends_in_box ? S.root_main : S.root;
+    int first = S.root_main;
+    if (!ends_in_box && S.root_shell != kNoRoot) {
+        if (first == kNoRoot) first = S.root_shell;
+        else stack[sp++] = S.root_shell;
+    }
+    return first;
 }
 
 // Is segment A->B blocked (faces ign0 / ign1 skipped)? `refines` counts FP64 settlements,
@@ -158,16 +165,15 @@ __device__ __forceinline__ int occ_root(const DeviceScene& S, bool ends_in_box)
 __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
                            unsigned long long* refines, int* err, TraceCounters* tc = nullptr)
 {
-    const int root = occ_root(S, in_scene_box(S, A) && in_scene_box(S, B));
-    if (root == kNoRoot) return false;
+    int stack[64];
+    int sp = 0;
+    int c = occ_start(S, in_scene_box(S, A) && in_scene_box(S, B), stack, sp);   // current node in a register;
+    if (c == kNoRoot) return false;                                               // entered children go on the stack
     float3 a = to_f(A), b = to_f(B);
     float3 dir = b - a;
     float len = sqrtf(dot(dir, dir));
     float3 inv = f3(safe_inv(dir.x), safe_inv(dir.y), safe_inv(dir.z));
     float tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
-    int stack[64];
-    int sp = 0;
-    int c = root;            // current node in a register; the other entered children go on the stack
     const int g0 = ign0 >= 0 ? ign0 : -3, g1 = ign1 >= 0 ? ign1 : -3;   // subtrees of one ignored face are skipped
     while (true) {
         if (c < 0) {

@@ -120,14 +120,16 @@ constexpr float kMapDelta = 1e-3f;   // a cell's map entry holds for points up t
 struct DeviceScene {
     int64_t n_tris;
     int n_faces;
-    int root;                    // root child code (internal index, or ~leaf for one triangle); kNoRoot if empty
-    // Subtree of the references that can stop a segment whose two ends lie in the scene box
-    // [box_lo, box_hi]: the triangles whose plane has the whole box on one closed side (the shell of a
-    // box-shaped room, or faces lying in it) sit in a sibling subtree of it. kNoRoot if there are none.
-    int root_main;
+    // Occlusion walks start at root_main: the subtree of the references that can stop a segment whose
+    // two ends lie in the scene box [box_lo, box_hi]. The triangles whose plane has the whole box on one
+    // closed side (the shell of a box-shaped room, or faces lying in it) sit in the subtree root_shell,
+    // which only segments with an end outside the box visit. Codes index nodes4 (>= 0) or are ~leaf;
+    // kNoRoot when a subtree is empty.
+    int root_main, root_shell;
+    int n_nodes4;                // compact four-wide nodes, top levels first
     float3 box_lo, box_hi;
     const BvhNode* nodes;
-    const Bvh4Node* nodes4;      // [internal nodes] four-wide view used by the traversals
+    const Bvh4Node* nodes4;      // [n_nodes4] compact four-wide tree used by the traversals
     const TriGeom* tri_geom;     // [n_refs] leaf (reference) order
     const TriVerts* tri_verts;   // [n_refs] leaf order
     const int* tri_face;         // [n_refs] leaf order
@@ -184,8 +186,9 @@ struct risrt_scene {
     int64_t n_refs = 0;              // BVH leaves (triangle references)
     int n_faces = 0;
     int n_mat = 0;
-    int root = risrt::kNoRoot;
     int root_main = risrt::kNoRoot;
+    int root_shell = risrt::kNoRoot;
+    int n_nodes4 = 0;
     int64_t n_shell_refs = 0;        // references of shell triangles (planes with the scene box on one side)
     float box_lo[3] = {0.f, 0.f, 0.f}, box_hi[3] = {0.f, 0.f, 0.f};
     risrt::BvhNode* nodes = nullptr;
@@ -204,7 +207,8 @@ struct risrt_scene {
     int64_t n_cells = 0;
     risrt::DeviceScene dev() const {
         risrt::DeviceScene s;
-        s.n_tris = n_tris; s.n_faces = n_faces; s.root = root; s.root_main = root_main; s.nodes = nodes;
+        s.n_tris = n_tris; s.n_faces = n_faces; s.root_main = root_main; s.root_shell = root_shell; s.n_nodes4 = n_nodes4;
+        s.nodes = nodes;
         s.box_lo = make_float3(box_lo[0], box_lo[1], box_lo[2]);
         s.box_hi = make_float3(box_hi[0], box_hi[1], box_hi[2]); s.nodes4 = nodes4; s.tri_geom = tri_geom;
         s.tri_verts = tri_verts; s.tri_face = tri_face; s.faces = faces; s.face_tris = face_tris; s.face_test = face_test; s.tri_leaf = tri_leaf; s.mats = mats;

@@ -664,6 +664,47 @@ __global__ void k_bvh4(const BvhNode* __restrict__ nodes, int n_int, Bvh4Node* _
     out[i] = o;
 }
 
+// Compact four-wide tree. A walk that starts at a node of the binary tree and follows the four-wide
+// views visits the nodes of one depth parity only: depth 1 (the roots of the main and the shell
+// subtree) when the root splits them, else depth 0 (the root). Those nodes get a sort key that orders
+// them by depth, then by index, so the compact array starts with the top levels (which the
+// validation keeps in shared memory); the others sort last. parent_int[root] = -1.
+__global__ void k_node_keys(const int* __restrict__ parent_int, int n_int, int parity, uint32_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals, unsigned* __restrict__ n_sel)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int d = 0;
+    for (int p = parent_int[i]; p >= 0 && d < n_int; p = parent_int[p]) ++d;
+    const bool sel = (d & 1) == parity;
+    keys[i] = sel ? ((uint32_t)min(d >> 1, 31) << 27) | (uint32_t)i : 0xffffffffu;
+    vals[i] = (uint32_t)i;
+    if (sel) atomicAdd(n_sel, 1u);
+}
+
+__global__ void k_compact_index(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int n_int,
+                                int* __restrict__ cidx)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n_int && keys[j] != 0xffffffffu) cidx[vals[j]] = j;
+}
+
+// Entry j of the compact tree: the four-wide view of binary node vals[j], its internal child codes
+// (nodes of the same parity) replaced by their compact positions.
+__global__ void k_bvh4_compact(const Bvh4Node* __restrict__ nodes4, const uint32_t* __restrict__ vals,
+                               const int* __restrict__ cidx, int n4c, Bvh4Node* __restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n4c) return;
+    Bvh4Node nd = nodes4[vals[j]];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = __float_as_int(nd.lo[k].w);
+        if (c >= 0 && c != kNoChild) nd.lo[k].w = __int_as_float(cidx[c]);
+    }
+    out[j] = nd;
+}
+
 // ------------------------------------------------------------------------------------------------
 // faces
 // ------------------------------------------------------------------------------------------------
@@ -874,7 +915,6 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     if ((rc = dmalloc(ctx, &sc->mats, n_mat))) return rc;
     RISRT_CUDA(ctx, cudaMemcpyAsync(sc->mats, mats_host, sizeof(float2) * n_mat, cudaMemcpyHostToDevice, s));
     if (nt == 0) {
-        sc->root = kNoRoot;
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));
         return RISRT_OK;
     }
@@ -891,10 +931,11 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, cudaMemcpyAsync(d_mat, mat_host, sizeof(int32_t) * nt, cudaMemcpyHostToDevice, s));
 
     // scene bounds
-    // bb[0..6] bounds (k_bounds), bb[8..9] the number of shell references (64-bit)
+    // bb[0..6] bounds (k_bounds), bb[8..9] the number of shell references (64-bit), bb[10] the number
+    // of four-wide nodes
     unsigned* d_bb;
-    if ((rc = dmalloc(ctx, &d_bb, 10))) return rc;
-    unsigned bb_init[10] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0, 0, 0, 0, 0};
+    if ((rc = dmalloc(ctx, &d_bb, 12))) return rc;
+    unsigned bb_init[12] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const char* shell_env = getenv("RISRT_SHELL");      // "0": shell triangles stay in the main tree
     const int shell_on = !(shell_env && shell_env[0] == '0');
     RISRT_CUDA(ctx, cudaMemcpyAsync(d_bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
@@ -968,20 +1009,47 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     RISRT_CUDA(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * n_int, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(parent_int, 0xff, sizeof(int) * n_int, s));
     RISRT_CUDA(ctx, cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * nr, s));
+    // The shell references sort last (key bit 30), so when both kinds exist the root splits at that
+    // bit: its first child (leaf 0 or internal node n_main - 1, the radix tree's split position) covers
+    // the others, its second (leaf n_main or internal node n_main) the shell.
+    const int64_t n_shell_refs = sc->n_shell_refs, n_main = nr - n_shell_refs;
+    const bool split = n_shell_refs > 0 && n_main > 0;
+    int* cidx = nullptr;
+    if ((rc = dmalloc(ctx, &cidx, n_int))) return rc;
     if (nr > 1) {
         RISRT_KERNEL(ctx, "k_karras", (k_karras<<<nblk(nr - 1, 256), 256, 0, s>>>(keys, (int)nr, sc->nodes, parent_int, parent_leaf)));
         RISRT_KERNEL(ctx, "k_refit", (k_refit<<<nblk(nr, 256), 256, 0, s>>>(leaf_lo, leaf_hi, (int)nr, sc->nodes, parent_int, parent_leaf, sc->tri_face, flags, pad)));
         RISRT_KERNEL(ctx, "k_bvh4", (k_bvh4<<<nblk(n_int, 256), 256, 0, s>>>(sc->nodes, n_int, sc->nodes4)));
-        sc->root = 0;
+        // compact four-wide tree in breadth-first order (the reference keys and values are free now)
+        RISRT_KERNEL(ctx, "k_node_keys", (k_node_keys<<<nblk(n_int, 256), 256, 0, s>>>(parent_int, n_int, split ? 1 : 0, keys, vals,
+                                                                                     d_bb + 10)));
+        RISRT_CUDA(ctx, radix_sort_pairs(keys, vals, n_int, 32, tmp, s));
+        RISRT_CUDA(ctx, cudaMemsetAsync(cidx, 0xff, sizeof(int) * n_int, s));
+        RISRT_KERNEL(ctx, "k_compact_index", (k_compact_index<<<nblk(n_int, 256), 256, 0, s>>>(keys, vals, n_int, cidx)));
+        unsigned n4c = 0;
+        RISRT_CUDA(ctx, cudaMemcpyAsync(&n4c, d_bb + 10, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        Bvh4Node* compact;
+        if ((rc = dmalloc(ctx, &compact, std::max<unsigned>(n4c, 1u)))) return rc;
+        RISRT_KERNEL(ctx, "k_bvh4_compact", (k_bvh4_compact<<<nblk(n4c, 128), 128, 0, s>>>(sc->nodes4, vals, cidx, (int)n4c, compact)));
+        RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+        cudaFree(sc->nodes4);
+        sc->nodes4 = compact;
+        sc->n_nodes4 = (int)n4c;
+        // walk starts: the depth-1 nodes sort first, the main subtree's root before the shell's
+        if (split) {
+            sc->root_main = n_main > 1 ? 0 : ~0;
+            sc->root_shell = n_shell_refs > 1 ? (n_main > 1 ? 1 : 0) : ~(int)n_main;
+        } else if (n_shell_refs == 0) {
+            sc->root_main = 0;
+        } else {
+            sc->root_shell = 0;
+        }
+    } else if (n_shell_refs == 0) {
+        sc->root_main = ~0;
     } else {
-        sc->root = ~0;
+        sc->root_shell = ~0;
     }
-    // The shell references sort last (key bit 30), so the root splits at that bit: its first child,
-    // leaf 0 or internal node n_main - 1 (the radix tree's split position), covers the others.
-    const int64_t n_main = nr - sc->n_shell_refs;
-    if (sc->n_shell_refs == 0) sc->root_main = sc->root;
-    else if (n_main == 0) sc->root_main = kNoRoot;
-    else sc->root_main = n_main == 1 ? ~0 : (int)(n_main - 1);
 
     // faces: first triangle, triangle lists, FP64 planes
     int *first, *count, *cursor;
@@ -1032,7 +1100,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
     cudaFree(keys); cudaFree(vals); cudaFree(tmp); cudaFree(leaf_of_orig); cudaFree(tmp0);
     cudaFree(ref_cnt); cudaFree(ref_off); cudaFree(ref_tri); cudaFree(ref_lo); cudaFree(ref_hi);
     cudaFree(leaf_lo); cudaFree(leaf_hi);
-    cudaFree(parent_int); cudaFree(parent_leaf); cudaFree(flags);
+    cudaFree(parent_int); cudaFree(parent_leaf); cudaFree(flags); cudaFree(cidx);
     cudaFree(first); cudaFree(count); cudaFree(cursor); cudaFree(count64); cudaFree(start);
     return RISRT_OK;
 }

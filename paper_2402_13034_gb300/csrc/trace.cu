@@ -269,10 +269,11 @@ struct RefineQ {
 struct DenseOut {
     int* r;
     int* slot;
+    int* seq;                    // the candidate's sequence index (its slot's content)
     unsigned long long* cnt;
 };
 #ifndef RISRT_DENSE_BUF
-#define RISRT_DENSE_BUF 256
+#define RISRT_DENSE_BUF 192
 #endif
 constexpr int kDenseBuf = RISRT_DENSE_BUF;   // staged work-list entries per warp (must be >= 32)
 
@@ -374,6 +375,7 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
              const int* __restrict__ slist_cnt, int64_t slist_stride, RefineQ rq, DenseOut dl)
 {
     __shared__ int2 dbuf[kCandThreads / 32][kDenseBuf];
+    __shared__ int dseq[kCandThreads / 32][kDenseBuf];
     __shared__ SeqEntry sh[kCandThreads];
     __shared__ int sh_idx[kCandThreads];
     __shared__ unsigned char kept[kCandThreads];
@@ -421,6 +423,7 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
             const int2 v = dbuf[warp][k];
             dl.r[base + k] = v.x;
             dl.slot[base + k] = v.y;
+            dl.seq[base + k] = dseq[warp][k];
         }
         __syncwarp();
         wn = 0;
@@ -522,7 +525,11 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
                 const int nb = __popc(b);
                 if (nb) {
                     if (wn + nb > kDenseBuf) flush();
-                    if (pass) dbuf[warp][wn + __popc(b & ((1u << lane) - 1u))] = make_int2((int)r, slot);
+                    if (pass) {
+                        const int k = wn + __popc(b & ((1u << lane) - 1u));
+                        dbuf[warp][k] = make_int2((int)r, slot);
+                        dseq[warp][k] = sidx;
+                    }
                     wn += nb;
                 }
             }
@@ -552,6 +559,7 @@ __global__ void k_refine_cand(DeviceScene S, const float* __restrict__ dst_xyz, 
                 const unsigned long long pos = atomicAdd(dl.cnt, 1ull);
                 dl.r[pos] = (int)r;
                 dl.slot[pos] = slot;
+                dl.seq[pos] = q.y;
             }
         } else {
             atomicExch(overflow, 1);
@@ -567,8 +575,9 @@ __global__ void k_cand_counts(const int* __restrict__ cand_cnt, int64_t n_dst, i
     if (r == n_dst) out[r] = 0;
 }
 
-__global__ void k_dense_list(const int* __restrict__ cand_cnt, const int64_t* __restrict__ off, int64_t n_dst, int cap,
-                             int* __restrict__ dense_r, int* __restrict__ dense_slot)
+__global__ void k_dense_list(const int* __restrict__ cand_cnt, const int* __restrict__ cand, const int64_t* __restrict__ off,
+                             int64_t n_dst, int cap, int* __restrict__ dense_r, int* __restrict__ dense_slot,
+                             int* __restrict__ dense_seq)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -578,6 +587,7 @@ __global__ void k_dense_list(const int* __restrict__ cand_cnt, const int64_t* __
     for (int slot = lane; slot < n; slot += 32) {
         dense_r[o + slot] = (int)r;
         dense_slot[o + slot] = slot;
+        dense_seq[o + slot] = cand[r * (int64_t)cap + slot];
     }
 }
 
@@ -801,10 +811,13 @@ constexpr int kMapLeafBudget = 8;    // triangles that may meet a cell's pyramid
 // margins of face_covers / tri_covers, 0 = undecided. The walk visits children entered first along
 // the centre ray first and gives up after kMapLeafBudget candidate triangles or
 // RISRT_MAP_NODE_BUDGET nodes.
-__device__ uint8_t classify_pyramid(const DeviceScene& S, int root, float3 A, const float3* C, float3 nb, float D, int ig0,
-                                    int ig1, float margin)
+__device__ uint8_t classify_pyramid(const DeviceScene& S, bool in_box, float3 A, const float3* C, float3 nb, float D,
+                                    int ig0, int ig1, float margin)
 {
-    if (root == kNoRoot) return 1;
+    int stack[64];
+    int sp = 0;
+    int cur = occ_start(S, in_box, stack, sp);
+    if (cur == kNoRoot) return 1;
     // the pyramid's planes, outside = positive side: four through A, the fifth the base plane
     float3 pn[5];
     for (int k = 0; k < 4; ++k) {
@@ -820,9 +833,6 @@ __device__ uint8_t classify_pyramid(const DeviceScene& S, int root, float3 A, co
     int budget = 0, visits = 0;
     const float3 cdir = (C[0] + C[2]) * 0.5f - A;
     const float3 cinv = f3(safe_inv(cdir.x), safe_inv(cdir.y), safe_inv(cdir.z));
-    int stack[64];
-    int sp = 0;
-    int cur = root;
     while (true) {
         if (cur < 0) {
             const int L = ~cur;
@@ -917,8 +927,7 @@ __global__ void __launch_bounds__(128) k_src_map(DeviceScene S, d3 src, int src_
         const float3 nb = sd > 0.0 ? f3(-(float)fc.plane.x, -(float)fc.plane.y, -(float)fc.plane.z)
                                    : f3((float)fc.plane.x, (float)fc.plane.y, (float)fc.plane.z);
         // the map answers segments from the source to points of face f, which lie in the scene box
-        state = classify_pyramid(S, occ_root(S, in_scene_box(S, src)), to_f(src), C, nb, (float)fabs(sd), src_face, f,
-                                 margin);
+        state = classify_pyramid(S, in_scene_box(S, src), to_f(src), C, nb, (float)fabs(sd), src_face, f, margin);
     }
     map[c] = state;
 }
@@ -968,7 +977,7 @@ __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float*
         // element -> R segment does too
         const bool in_box = in_scene_box(S, R) && in_scene_box(S, Cd[0]) && in_scene_box(S, Cd[1]) &&
                             in_scene_box(S, Cd[2]) && in_scene_box(S, Cd[3]);
-        st = classify_pyramid(S, occ_root(S, in_box), to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
+        st = classify_pyramid(S, in_box, to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
     }
     state[r] = st;
 }
@@ -979,7 +988,16 @@ __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float*
 // and every loop iteration advances each busy lane by at most kSteps BVH visits, so lanes stay
 // busy while traversal lengths differ. FP64 endpoints are rebuilt only for the rare triangle whose
 // FP32 classification is too close to call. ctr[0..3]: candidates, segments, nodes, triangle tests.
-constexpr int kValThreads = 128;
+#ifndef RISRT_VALIDATE_THREADS
+#define RISRT_VALIDATE_THREADS 128
+#endif
+constexpr int kValThreads = RISRT_VALIDATE_THREADS;
+// Top four-wide nodes each block keeps in shared memory (128 B each). Off by default: on the room
+// workload the node loads hit L1 and a copy per block only takes L1 capacity (measured).
+#ifndef RISRT_VALIDATE_SMEM_NODES
+#define RISRT_VALIDATE_SMEM_NODES 0
+#endif
+constexpr int kValSmemNodes = RISRT_VALIDATE_SMEM_NODES;
 #ifndef RISRT_VALIDATE_STEPS
 #define RISRT_VALIDATE_STEPS 64    // BVH visits per lane between refills (measured on the room workload)
 #endif
@@ -994,12 +1012,17 @@ constexpr int kSteps = RISRT_VALIDATE_STEPS;
 __global__ void __launch_bounds__(kValThreads, RISRT_VALIDATE_MINB)
 k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_face, int dst_face,
            const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int* __restrict__ cand, int cap,
-           const int* __restrict__ dense_r, const int* __restrict__ dense_slot,
+           const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const int* __restrict__ dense_seq,
            const long long* __restrict__ d_total, unsigned long long* __restrict__ next, float tol_base,
            unsigned long long* refines,
            int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx,
-           RefineQ rq, const uint8_t* __restrict__ smap)
+           RefineQ rq, const uint8_t* __restrict__ smap, int n_sh)
 {
+    // the first n_sh nodes of the compact tree (its top levels) in shared memory
+    extern __shared__ float4 sh_nodes[];
+    for (int i = threadIdx.x; i < n_sh * 8; i += blockDim.x) sh_nodes[i] = reinterpret_cast<const float4*>(S.nodes4)[i];
+    __syncthreads();
+    const Bvh4Node* shn = reinterpret_cast<const Bvh4Node*>(sh_nodes);
     const long long total = *d_total;
     const float3 srcf = to_f(src);
     const bool src_in = in_scene_box(S, src);   // with both ends in the scene box a segment skips the shell
@@ -1039,9 +1062,9 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
             le = occ_off[info.x + 1];
             sp = 0;
         } else {
-            const int root = occ_root(S, (j > 0 || src_in) && (j < info.w || dst_in));   // path points lie on faces
-            cur = root == kNoRoot ? kNone : root;
             sp = 0;
+            const int first = occ_start(S, (j > 0 || src_in) && (j < info.w || dst_in), stack, sp);   // path points
+            cur = first == kNoRoot ? kNone : first;                                                   // lie on faces
             if (j == 0 && smap) {       // first segment: the source's visibility map of face f1
                 if (p1err <= 0.5f * kMapDelta) {
                     const FaceGrid g = S.face_grid[info.x];
@@ -1052,6 +1075,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                         const uint8_t st = smap[g.off + (int)fa * g.nv + (int)fb];
                         if (st != 0) {
                             cur = kNone;
+                            sp = 0;
                             blocked = st == 2;
                         }
                     }
@@ -1098,7 +1122,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                 if (item < total) {
                     r = dense_r[item];
                     slot = dense_slot[item];
-                    si = cand[(int64_t)r * cap + slot];
+                    si = dense_seq[item];
                     const SeqEntry e = seqs[si];
                     info = e.info;
                     const float3 R = f3(dst_xyz[3 * r], dst_xyz[3 * r + 1], dst_xyz[3 * r + 2]);
@@ -1153,7 +1177,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                     sp = 0;
                     break;
                 }
-                const Bvh4Node nd = S.nodes4[cur];
+                const Bvh4Node nd = cur < n_sh ? shn[cur] : S.nodes4[cur];
                 ++tc.nodes;
                 cur = bvh4_step(nd, a, inv, g0, g1, stack, sp);   // nearest entered child next
                 if (cur == kNoChild) cur = sp > 0 ? stack[--sp] : kNone;
@@ -1653,7 +1677,7 @@ struct Candidates {
 // length, the queue of FP64 settlements, scan space and the validation's work counter. Searches that
 // run concurrently on different streams each need their own.
 struct LegBufs {
-    int *dense_r = nullptr, *dense_slot = nullptr;
+    int *dense_r = nullptr, *dense_slot = nullptr, *dense_seq = nullptr;
     int64_t* dense_off = nullptr;
     unsigned long long* dense_cnt = nullptr;
     int4* rq = nullptr;
@@ -1855,7 +1879,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             unsigned long long* counters;
             int* flags_dev;
             float* c_xyz;
-            int *dense_r, *dense_slot;
+            int *dense_r, *dense_slot, *dense_seq;
             int64_t* dense_off;
             int* occ_cnt[2];
             int64_t* occ_off64[2];
@@ -1895,6 +1919,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.c_xyz = A.get<float>(3);
             L.dense_r = A.get<int>((size_t)n_rx * cap);
             L.dense_slot = A.get<int>((size_t)n_rx * cap);
+            L.dense_seq = A.get<int>((size_t)n_rx * cap);
             L.dense_off = A.get<int64_t>(n_rx + 1);
             L.crx.cnt64_tmp = A.get<int64_t>(n_rx + 1);
             L.cenv.cnt64_tmp = A.get<int64_t>(env ? n_rx + 1 : 1);
@@ -1918,12 +1943,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
             L.elem_bb = A.get<float4>(1);
             L.rx_state = A.get<uint8_t>((size_t)n_rx);
-            L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_off, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
+            L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_seq, L.dense_off, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
                              L.scan_tmp, L.counters + 6};
             // the environment paths run beside the Rx leg: their own work list, queue and scan space
             const size_t n_env_rx = env ? (size_t)n_rx : 1;
             L.env.dense_r = A.get<int>(n_env_rx * cap);
             L.env.dense_slot = A.get<int>(n_env_rx * cap);
+            L.env.dense_seq = A.get<int>(n_env_rx * cap);
             L.env.dense_off = A.get<int64_t>(n_env_rx + 1);
             L.env.dense_cnt = A.get<unsigned long long>(1);
             L.env.rq_cap = env ? rq_cap : 1;
@@ -1940,6 +1966,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             }
             L.tx.dense_r = A.get<int>((size_t)cap);
             L.tx.dense_slot = A.get<int>((size_t)cap);
+            L.tx.dense_seq = A.get<int>((size_t)cap);
             L.tx.dense_off = A.get<int64_t>(2);
             L.tx.dense_cnt = A.get<unsigned long long>(1);
             L.tx.rq_cap = kTxLegQueue;
@@ -2063,7 +2090,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 const RefineQ rq{lb.rq, lb.rq_cap, lb.rq_cnt};
                 RISRT_CUDA(ctx, cudaMemsetAsync(lb.rq_cnt, 0, sizeof(unsigned) * 2, st));
                 // many destinations: the candidate search writes the validation work list itself
-                const DenseOut dl = n_dst > 1 ? DenseOut{lb.dense_r, lb.dense_slot, lb.dense_cnt} : DenseOut{nullptr, nullptr, nullptr};
+                const DenseOut dl = n_dst > 1 ? DenseOut{lb.dense_r, lb.dense_slot, lb.dense_seq, lb.dense_cnt}
+                                              : DenseOut{nullptr, nullptr, nullptr, nullptr};
                 if (dl.r) RISRT_CUDA(ctx, cudaMemsetAsync(lb.dense_cnt, 0, sizeof(unsigned long long), st));
                 // sequences that can reach each super-patch of kSuperRx Morton-consecutive destinations
                 const int words = (t.n + 31) / 32;
@@ -2102,8 +2130,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 if (!dl.r) {
                     RISRT_KERNEL_ON(ctx, st, "k_cand_counts", (k_cand_counts<<<nblk(n_dst + 1, 256), 256, 0, st>>>(cs.cnt, n_dst, cs.cap, cs.cnt64_tmp)));
                     RISRT_CUDA(ctx, exclusive_scan_i64(cs.cnt64_tmp, lb.dense_off, n_dst + 1, lb.scan_tmp, st));
-                    RISRT_KERNEL_ON(ctx, st, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, st>>>(cs.cnt, lb.dense_off, n_dst, cs.cap,
-                                                                                                        lb.dense_r, lb.dense_slot)));
+                    RISRT_KERNEL_ON(ctx, st, "k_dense_list", (k_dense_list<<<nblk(n_dst * 32, 128), 128, 0, st>>>(
+                                                                cs.cnt, cs.cand, lb.dense_off, n_dst, cs.cap, lb.dense_r,
+                                                                lb.dense_slot, lb.dense_seq)));
                     d_total = (const long long*)(lb.dense_off + n_dst);
                 }
                 RISRT_CUDA(ctx, cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long), st));
@@ -2113,10 +2142,14 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 const uint8_t* smap = n_dst > 1 && use_maps ? L.smap[occ] : nullptr;
                 if (smap && maps_ready) RISRT_CUDA(ctx, cudaStreamWaitEvent(st, maps_ready, 0));
                 const unsigned blocks = (unsigned)ctx->sm_count * RISRT_VALIDATE_MINB;
-                RISRT_KERNEL_ON(ctx, st, "k_validate", (k_validate<<<blocks, kValThreads, 0, st>>>(
+                const int n_sh = std::min(S.n_nodes4, kValSmemNodes);
+                const size_t val_shm = sizeof(Bvh4Node) * (size_t)n_sh;
+                if (val_shm > 48 * 1024)
+                    RISRT_CUDA(ctx, cudaFuncSetAttribute(k_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)val_shm));
+                RISRT_KERNEL_ON(ctx, st, "k_validate", (k_validate<<<blocks, kValThreads, val_shm, st>>>(
                                                     S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
-                                                    vs, d_total, lb.work, tol_base, counters, flags_dev + 1,
-                                                    counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq, smap)));
+                                                    vs, lb.dense_seq, d_total, lb.work, tol_base, counters, flags_dev + 1,
+                                                    counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq, smap, n_sh)));
                 RISRT_KERNEL_ON(ctx, st, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, st>>>(
                                                       S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
             }
@@ -2279,7 +2312,7 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
         void* scan_tmp;
         SeqEntry* e;
         SeqEntryD* d;
-        int *cand, *cnt, *dense_r, *dense_slot, *flags;
+        int *cand, *cnt, *dense_r, *dense_slot, *dense_seq, *flags;
         unsigned long long* counters;
         float* dst;
     };
@@ -2296,6 +2329,7 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
         L.dense_off = A.get<int64_t>(2);
         L.dense_r = A.get<int>(cap);
         L.dense_slot = A.get<int>(cap);
+        L.dense_seq = A.get<int>(cap);
         L.ids = A.get<int64_t>(cap);
         L.counters = A.get<unsigned long long>(8);
         L.flags = A.get<int>(4);
@@ -2341,16 +2375,17 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
                                                   L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr},
-                                                  DenseOut{nullptr, nullptr, nullptr})));
+                                                  DenseOut{nullptr, nullptr, nullptr, nullptr})));
         } else {
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
                                                   L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr},
-                                                  DenseOut{nullptr, nullptr, nullptr})));
+                                                  DenseOut{nullptr, nullptr, nullptr, nullptr})));
         }
         RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<1, 32, 0, s>>>(L.cnt, 1, cap, L.cnt64_tmp)));
         RISRT_CUDA(ctx, exclusive_scan_i64(L.cnt64_tmp, L.dense_off, 2, L.scan_tmp, s));
-        RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<1, 32, 0, s>>>(L.cnt, L.dense_off, 1, cap, L.dense_r, L.dense_slot)));
+        RISRT_KERNEL(ctx, "k_dense_list", (k_dense_list<<<1, 32, 0, s>>>(L.cnt, L.cand, L.dense_off, 1, cap, L.dense_r,
+                                                                          L.dense_slot, L.dense_seq)));
         long long total = 0;
         int host_flags[1] = {0};
         RISRT_CUDA(ctx, cudaMemcpyAsync(&total, L.dense_off + 1, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -2361,10 +2396,10 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             const unsigned blocks = (unsigned)std::min<long long>((long long)ctx->sm_count * 8, (total + kValThreads - 1) / kValThreads);
             RISRT_KERNEL(ctx, "k_validate", (k_validate<<<blocks, kValThreads, 0, s>>>(
                                                 S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
-                                                L.dense_slot, (const long long*)(L.dense_off + 1), L.counters + 6,
+                                                L.dense_slot, L.dense_seq, (const long long*)(L.dense_off + 1), L.counters + 6,
                                                 tol_base, L.counters,
                                                 L.flags + 1, L.counters + 2, nullptr, nullptr, RefineQ{nullptr, 0, nullptr},
-                                                nullptr)));
+                                                nullptr, 0)));
         }
         const size_t shm = sizeof(int) * (size_t)cap;
         cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
