@@ -152,38 +152,51 @@ def bench_gradient(ctx, R, dev, steps=200, reps=5):
 
 
 def bench_serving(dev_index, n_req=64, rate_hz=2000.0, slots=4):
-    """Seeded Poisson stream (mean rate_hz) of coverage and sweep requests over three room scenes
-    with 10/40/80 boxes and 37- or 127-element RIS, grids 16^2..128^2, 1..64 configurations;
-    requests are submitted at their arrival times."""
+    """Seeded Poisson stream (mean rate_hz) of the serving mix: scenes of 492 (room), ~20k (office)
+    and ~200k (hall) triangles, RIS of 37 / 127 / 1,024 / 4,096 elements, receiver grids of 1k-1M
+    points, 1-512 configurations, coverage or sweep; half the sweeps query one of four resident
+    channels. Requests are submitted at their arrival times."""
     from paper_2402_13034_gb300 import serve
     scenes = {}
-    for i, nb in enumerate((10, 40, 80)):
-        w = S.room(grid=8, n_boxes=nb, seed_index=10 + i)
-        w.name = f"room_{nb}boxes"
-        if i == 0:
-            w.ris.elem_uv = S.hex_layout(3, S.C0 / w.freq_hz / 2)
-            w.gammas = w.gammas[:, :37]
-        scenes[w.name] = w
-    reqs = serve.poisson_requests(S.SEED_BASE + 4, n_req, rate_hz, scenes)
+    for w, name in ((S.room(grid=8), "room_492tri"), (S.office(), "office_20ktri"), (S.hall(target_grid=8), "hall_200ktri")):
+        w.name = name
+        scenes[name] = w
+    reqs = serve.mixed_requests(S.SEED_BASE + 4, n_req, rate_hz, scenes)
     srv = serve.Server(device=dev_index, slots=slots)
     for name, w in scenes.items():
         srv.add_scene(name, w.scene)
-    # warm the slot contexts and scene caches with one request per scene
-    srv.drain([srv.submit(r) for _, r in reqs[:3]])
-    t0 = time.perf_counter()
-    futs = []
-    for t_arr, r in reqs:
-        dt = t0 + t_arr - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        futs.append(srv.submit(r))
-    res = srv.drain(futs)
-    wall = time.perf_counter() - t0
-    srv.close()
+    # warm the slot contexts and scene caches (one small coverage request per scene and slot)
+    warm = []
+    for name, w in scenes.items():
+        for _ in range(slots):
+            warm.append(serve.Request("coverage", name, w.ris, w.tx, w.rx, w.rx_xyz[:64], w.gammas[:1], w.freq_hz,
+                                      1, 1, True))
+    try:
+        srv.drain([srv.submit(r) for r in warm])
+        t0 = time.perf_counter()
+        futs = []
+        for t_arr, r in reqs:
+            dt = t0 + t_arr - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            futs.append(srv.submit(r))
+        for f in futs:                       # wait for all; requests above the budget are rejected
+            f.exception(timeout=600)
+        wall = time.perf_counter() - t0
+    finally:
+        srv.close()
+    done = [(f.result(), r) for f, (_, r) in zip(futs, reqs) if f.exception() is None]
+    res = [d for d, _ in done]
     out = serve.latency_stats(res)
-    out.update({"requests": n_req, "offered_rate_hz": rate_hz, "throughput_req_s": n_req / wall, "slots": slots,
+    work = sum(len(r.rx_xyz) * r.gammas.shape[1] * r.gammas.shape[0] for _, r in done)
+    out.update({"requests": n_req, "rejected": n_req - len(res), "offered_rate_hz": rate_hz,
+                "throughput_req_s": len(res) / wall, "slots": slots,
                 "peak_admitted_bytes": srv.admission.peak, "budget_bytes": srv.admission.budget,
-                "units_per_s": None})
+                "channel_budget_bytes": srv.channel_budget, "channel_hits": srv.channel_hits,
+                "graph_replays": srv.graph_replays,
+                "rx_elem_cfg_per_s": work / wall,
+                "mix": {name: len(w.scene.tris) for name, w in scenes.items()}})
+    del res, done
     return out
 
 

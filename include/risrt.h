@@ -228,6 +228,23 @@ int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t
                         const float* gamma, int32_t n_cfg, int precision, float* P_out, void* workspace,
                         size_t workspace_bytes);
 
+/* OR-ed into the precision of risrt_sweep_configs with RISRT_PREC_BF16 or RISRT_PREC_BF16X2
+ * (RISRT_ERR_INVALID_ARG with RISRT_PREC_FP16; ignored with RISRT_PREC_FP32):
+ * RISRT_SWEEP_KEEP_A: the caller states that A, n_rx, M, the precision, the workspace and its size
+ *   are those of an earlier call, whose packed copy of A in the workspace is then reused (only gamma
+ *   is packed); n_cfg may differ while it fits the workspace. Results are undefined if A changed.
+ *   Calls sharing a workspace must not overlap in time.
+ * RISRT_SWEEP_DEFER_CHECK: the call only enqueues work on the stream and does not synchronise, so it
+ *   can be captured into a CUDA graph; the tensor-core kernel's wait-timeout flag is left in the
+ *   workspace for risrt_sweep_check. */
+#define RISRT_SWEEP_KEEP_A 0x100
+#define RISRT_SWEEP_DEFER_CHECK 0x200
+
+/* After sweeps with RISRT_SWEEP_DEFER_CHECK on this workspace: waits for the context's stream and
+ * returns RISRT_ERR_TIMEOUT if a pipeline wait of the last such sweep expired (its output is then
+ * incomplete), else RISRT_OK. The flag is cleared by every sweep. */
+int risrt_sweep_check(risrt_ctx* ctx, const void* workspace, size_t workspace_bytes);
+
 /* ------------------------------------------------------------------------------------------------
  * Phase gradient (adjoint of Eq. 9 and Eq. 10)
  * ---------------------------------------------------------------------------------------------- */

@@ -510,12 +510,24 @@ int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t
     if (!A || !gamma || !P_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
     if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || M < 1 || M > 65536 || n_cfg < 1 || n_cfg > (1 << 24))
         return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
-    if (precision < RISRT_PREC_FP32 || precision > RISRT_PREC_FP16) return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown precision");
+    const int opts = precision & ~0xff;
+    precision &= 0xff;
+    if (precision < RISRT_PREC_FP32 || precision > RISRT_PREC_FP16 || (opts & ~(RISRT_SWEEP_KEEP_A | RISRT_SWEEP_DEFER_CHECK)))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown precision or option");
+    if (opts && precision == RISRT_PREC_FP16)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "RISRT_SWEEP_KEEP_A / DEFER_CHECK need RISRT_PREC_BF16 or BF16X2");
     if (((uintptr_t)A | (uintptr_t)gamma | (uintptr_t)E0) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
     if (precision != RISRT_PREC_FP32 && ((uintptr_t)workspace & 15u))
         return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
     return sweep_configs(ctx, (const float2*)A, (const float2*)E0, n_rx, M, (const float2*)gamma, n_cfg, precision, P_out,
-                         workspace, workspace_bytes);
+                         workspace, workspace_bytes, (opts & RISRT_SWEEP_KEEP_A) != 0, (opts & RISRT_SWEEP_DEFER_CHECK) != 0);
+}
+
+int risrt_sweep_check(risrt_ctx* ctx, const void* workspace, size_t workspace_bytes)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!workspace || workspace_bytes < 64) return fail(ctx, RISRT_ERR_INVALID_ARG, "no workspace");
+    return sweep_check(ctx, workspace, workspace_bytes);
 }
 
 int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precision, size_t* bytes)

@@ -173,7 +173,7 @@ size_t sweep_workspace_bytes(int64_t n_rx, int M, int C, int precision)
 }
 
 int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_rx, int M, const float2* G, int C,
-                  int precision, float* P, void* ws, size_t ws_bytes)
+                  int precision, float* P, void* ws, size_t ws_bytes, bool keep_a, bool defer)
 {
     cudaStream_t s = ctx->stream;
     const float inv2eta = (float)(1.0 / (2.0 * kEta0));
@@ -206,13 +206,24 @@ int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_r
         RISRT_KERNEL(ctx, "k_pack_X", (k_pack_X<__half><<<nblk(nx, 256), 256, 0, s>>>(A, n_rx, M, sh.Kp, false, xscale, (__half*)X)));
         RISRT_KERNEL(ctx, "k_pack_Y", (k_pack_Y<__half><<<nblk(ny, 256), 256, 0, s>>>(G, C, M, sh.Np, sh.Kp, false, (__half*)Y)));
     } else {
-        RISRT_KERNEL(ctx, "k_pack_X", (k_pack_X<__nv_bfloat16><<<nblk(nx, 256), 256, 0, s>>>(A, n_rx, M, sh.Kp, sh.split, 1.f,
-                                                                                            (__nv_bfloat16*)X)));
+        if (!keep_a)   // with keep_a the workspace already holds A packed by an earlier call
+            RISRT_KERNEL(ctx, "k_pack_X", (k_pack_X<__nv_bfloat16><<<nblk(nx, 256), 256, 0, s>>>(A, n_rx, M, sh.Kp, sh.split, 1.f,
+                                                                                                (__nv_bfloat16*)X)));
         RISRT_KERNEL(ctx, "k_pack_Y", (k_pack_Y<__nv_bfloat16><<<nblk(ny, 256), 256, 0, s>>>(G, C, M, sh.Np, sh.Kp, sh.split,
                                                                                             (__nv_bfloat16*)Y)));
     }
     return sweep_tc(ctx, X, Y, sh, precision == RISRT_PREC_FP16, E0, n_rx, C, P, inv2eta / (xscale * xscale), xscale,
-                    d_max + 1);
+                    d_max + 1, defer);
+}
+
+int sweep_check(risrt_ctx* ctx, const void* ws, size_t ws_bytes)
+{
+    const unsigned* err_dev = (const unsigned*)((const char*)ws + ws_bytes - 16) + 1;   // as in sweep_configs
+    unsigned h = 0;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h) return fail(ctx, RISRT_ERR_TIMEOUT, "tensor-core sweep: a pipeline wait expired");
+    return RISRT_OK;
 }
 
 }  // namespace risrt

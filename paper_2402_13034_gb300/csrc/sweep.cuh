@@ -21,11 +21,13 @@ struct SweepShape {
 SweepShape sweep_shape(int64_t n_rx, int M, int C, int precision);
 size_t sweep_workspace_bytes(int64_t n_rx, int M, int C, int precision);
 int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_rx, int M, const float2* G, int C,
-                  int precision, float* P, void* ws, size_t ws_bytes);
+                  int precision, float* P, void* ws, size_t ws_bytes, bool keep_a = false, bool defer = false);
+// The deferred wait-timeout flag of the last sweep on this workspace (waits for the stream).
+int sweep_check(risrt_ctx* ctx, const void* ws, size_t ws_bytes);
 // D = X . Y^T on tcgen05 (X: [n_rx][Kp], Y: [Np][Kp], 16-bit, K-major), then
 // P[r][c] = ((D[r][2c] + e0s Re E0[r])^2 + (D[r][2c+1] + e0s Im E0[r])^2) * pscale.
 int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh, bool fp16, const float2* E0,
-             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev);
+             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev, bool defer = false);
 
 // D = X . Y^T on SM pairs with split-K, complex partial sums out (see sweep_tc.cu).
 int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, int Np, int Kp, const float2* E0rows, int C,

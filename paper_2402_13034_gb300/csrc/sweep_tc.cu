@@ -564,7 +564,7 @@ uint32_t make_idesc(bool fp16, int m, int n)
 }  // namespace
 
 int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh, bool fp16, const float2* E0,
-             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev)
+             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev, bool defer)
 {
     cudaStream_t s = ctx->stream;
     CUtensorMap mX, mY;
@@ -603,6 +603,7 @@ int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh,
         RISRT_KERNEL(ctx, "k_sweep_tc", (k_sweep_tc<<<grid, 192, kSmemBytes, s>>>(mX, mY, sh.Kp / kTcBK, idesc, E0, n_rx,
                                                                                 C, P, pscale, e0scale, err_dev)));
     }
+    if (defer) return RISRT_OK;          // the flag stays in the workspace (risrt_sweep_check)
     unsigned h = 0;
     RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));

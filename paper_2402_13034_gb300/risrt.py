@@ -21,6 +21,8 @@ PATTERN_ISO, PATTERN_COS_POW, PATTERN_MONOPOLE_QW = 0, 1, 2
 FLAG_ENV_PATHS, FLAG_FRESNEL_TM = 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP16 = 0, 1, 2, 3
 GRAD_KEEP_A = 0x100
+SWEEP_KEEP_A = 0x100
+SWEEP_DEFER_CHECK = 0x200
 
 _lock = threading.Lock()
 _lib = None
@@ -45,6 +47,7 @@ _SIGS = {
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
     "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_sweep_configs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int, _P, _P, C.c_size_t]),
+    "risrt_sweep_check": (C.c_int, [_P, _P, C.c_size_t]),
     "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P,
                                     C.c_size_t, C.c_int]),
@@ -308,16 +311,23 @@ class Context:
             return None
         return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
 
-    def sweep_configs(self, A, E0, gamma, P_out, precision: int, workspace=None):
+    def sweep_configs(self, A, E0, gamma, P_out, precision: int, workspace=None, keep_a: bool = False,
+                      defer_check: bool = False):
         """A: complex64 CUDA [n_rx, M]; E0: complex64 [n_rx] or None; gamma: complex64 [C, M];
-        P_out: float32 [n_rx, C]."""
+        P_out: float32 [n_rx, C]. keep_a: reuse A as packed into the workspace by an earlier call;
+        defer_check: enqueue only (capturable), check later with sweep_check."""
         n_rx, M = A.shape
         n_cfg = gamma.shape[0]
         ws_ptr = None if workspace is None else C.c_void_p(workspace.data_ptr())
         ws_n = 0 if workspace is None else workspace.numel()
+        opts = (SWEEP_KEEP_A if keep_a else 0) | (SWEEP_DEFER_CHECK if defer_check else 0)
         self._check(load().risrt_sweep_configs(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
                                                int(n_rx), int(M), _dev_ptr(gamma, "torch.complex64"), int(n_cfg),
-                                               int(precision), _dev_ptr(P_out, "torch.float32"), ws_ptr, ws_n))
+                                               int(precision) | opts, _dev_ptr(P_out, "torch.float32"), ws_ptr, ws_n))
+
+    def sweep_check(self, workspace):
+        """Waits for the stream; raises RisrtError if a deferred-check sweep on this workspace timed out."""
+        self._check(load().risrt_sweep_check(self._ptr, C.c_void_p(workspace.data_ptr()), workspace.numel()))
 
     def grad_workspace(self, n_target: int, B: int, M: int, precision: int = PREC_FP32):
         import torch

@@ -372,6 +372,25 @@ def office(n_boxes: int = 1660, target_grid: int = 128, n_start: int = 64, ris_s
     return w
 
 
+def hall(n_boxes: int = 16600, target_grid: int = 256) -> Workload:
+    """60x40x3 m hall with ~16,600 random boxes (~200k triangles), the largest scene of the serving
+    mix: 64x64 RIS on wall x=0 centred (0,20,1.5), Tx (30,10,2.5), 256x256 Rx over the floor at
+    1.2 m, order <= 1."""
+    rng = SplitMix64(SEED_BASE + 5)
+    f = 28e9
+    lam = C0 / f
+    center = np.array([0.0, 20.0, 1.5], np.float32)
+    txp = np.array([30.0, 10.0, 2.5], np.float32)
+    scene, host = room_with_boxes(rng, (60.0, 40.0, 3.0), n_boxes, [txp, center], sxy=(0.2, 0.8), sz=(0.3, 1.0))
+    ris = RIS(square_layout(64, lam / 2), center, np.array([0, 1, 0], np.float32),
+              np.array([0, 0, 1], np.float32), lam / 2, lam / 2, 0.0, host)
+    tx = Antenna(txp, identity_orient(), 1.0, 1.0, PATTERN_ISO)
+    rx = Antenna(np.zeros(3, np.float32), identity_orient(), 1.0, 1.0, PATTERN_ISO)
+    rx_xyz = linspace_grid(0.2, 59.8, target_grid, 0.2, 39.8, target_grid, 1.2, jitter=True)
+    g = phase_configs(rng, 1, ris.elem_uv.shape[0])
+    return Workload(f"hall_{ris.elem_uv.shape[0]}el_{len(scene.tris)}tri", f, scene, ris, tx, rx, rx_xyz, g, 1, 1, True)
+
+
 def paper_anechoic(grid_step: float = 0.01) -> Workload:
     """Table 1 set-up without walls: 127-element hex RIS (12 cm / 13 pitch) centred u=(0,0,0.5),
     normal +x, d_y=d_z=6.6 mm, 23.8 GHz, Pt 10 dBm, horn Tx Gt 19 dB aimed at u, monopole Rx

@@ -4,8 +4,12 @@ Requests (coverage maps and configuration sweeps over scenes of uneven size) are
 stream slot is free and their estimated device-memory footprint fits the budget; every admitted
 request runs on its own CUDA stream through its own library context, so the work of requests that
 arrived at different times overlaps on the device. Scene BVHs stay resident in a cache shared by
-all slots. A request's arithmetic does not depend on what else runs (per-request buffers, fixed
-reduction orders), so its result is bitwise the same alone or in a mix.
+all slots, and so do channel matrices: sweep requests that name the same channel (scene, RIS, Tx and
+receiver grid) after the first one skip the trace and the matrix build, reuse the matrix packed for
+the tensor cores, and replay a CUDA graph of the sweep captured for their configuration count. A
+request's arithmetic does not depend on what else runs (per-request buffers, fixed reduction
+orders, and a resident sweep computes exactly what the full one does), so its result is bitwise the
+same alone or in a mix.
 
 The admission policy (AdmissionController) is plain host logic and is tested without a GPU.
 """
@@ -41,6 +45,7 @@ class Request:
     max_order_rx: int = 1
     env_paths: bool = True
     precision: int = 2           # sweep precision (RISRT_PREC_*)
+    channel_key: str | None = None   # same key: same scene, RIS, Tx and receivers (sweeps reuse the channel)
     arrival: float = 0.0
     rid: int = -1
     meta: dict = field(default_factory=dict)
@@ -58,16 +63,38 @@ class Result:
 def estimate_footprint(req: Request, n_faces: int) -> int:
     """Upper estimate of the device bytes one request holds while it runs."""
     n, M, C = len(req.rx_xyz), req.gammas.shape[1], req.gammas.shape[0]
-    paths = n * (1 + (n_faces if req.max_order_rx >= 1 else 0) // 8 + 8)
     cap = 512
     n_ids = n_faces + (n_faces * n_faces if max(req.max_order_rx, req.max_order_tx) >= 2 else 0)
+    # path records: valid paths per receiver are few (about 12 in the room at order 2, 5 in the
+    # office at order 1); PATHS_PER_RX_EST per receiver is assumed, the 20% of memory left outside the
+    # budget absorbs a request above it
+    paths = n * min(PATHS_PER_RX_EST, 1 + n_ids)
     b = paths * 96 + n * ((M + 31) // 32) * 4 + n * 64
-    b += 3 * n_ids * 160 + 2 * n * cap * 4 * 6 + (64 << 10)
+    b += 3 * n_ids * 160 + 8 * n * cap * 4 + (64 << 10)   # candidate slabs, work lists of the legs
     b += n * C * 4 * 2 + C * M * 8 + n * 12
-    if req.kind == "sweep":
+    if uses_channel(req):
         Kp = (4 * M + 63) // 64 * 64
-        b += n * M * 8 + ((n + 127) // 128 * 128) * Kp * 2 + ((2 * C + 255) // 256 * 256) * Kp * 2
+        Cw = max(C, CHANNEL_CFG_CAP)
+        b += n * M * 8 + ((n + 255) // 256 * 256) * Kp * 2 + ((2 * Cw + 255) // 256 * 256) * Kp * 2 + n * C * 4
     return int(b)
+
+
+PATHS_PER_RX_EST = 64
+# Coverage requests whose direct evaluation would exceed this many (receiver, element,
+# configuration) terms run through the channel matrix on the tensor cores instead (split BF16,
+# about 1e-5 relative on the field), like sweeps.
+DIRECT_EVAL_LIMIT = 2e9
+# A channel's workspace is sized for this many configurations (or the request's, if more), so later
+# sweeps on it with up to as many configurations reuse the packed matrix.
+CHANNEL_CFG_CAP = 512
+# Resident sweeps capture a CUDA graph per configuration count when their output is at most this big.
+GRAPH_OUT_LIMIT = 512 << 20
+
+
+def uses_channel(req: Request) -> bool:
+    """Sweeps, and coverage requests too large to evaluate term by term, go through A."""
+    n, M, C = len(req.rx_xyz), req.gammas.shape[1], req.gammas.shape[0]
+    return req.kind == "sweep" or float(n) * M * C > DIRECT_EVAL_LIMIT
 
 
 # ------------------------------------------------------------------------------------------------
@@ -106,16 +133,39 @@ class AdmissionController:
 # ------------------------------------------------------------------------------------------------
 # server
 # ------------------------------------------------------------------------------------------------
+class _Channel:
+    """A resident channel: A [n, M] and E0 on the device, the sweep workspace holding A packed for
+    the tensor cores, and the captured sweep graphs per configuration count. One request uses it at
+    a time (lock)."""
+
+    def __init__(self, n, M, precision, A, E0, ws, cfg_cap, nbytes):
+        self.n, self.M, self.precision = n, M, precision
+        self.A, self.E0, self.ws = A, E0, ws
+        self.cfg_cap = cfg_cap
+        self.bytes = nbytes
+        self.graphs = {}
+        self.lock = threading.Lock()
+        self.dead = False
+
+
 class Server:
-    def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int | None = None, executor=None):
-        """executor(slot_index, request) -> np.ndarray replaces the GPU path (used by host tests)."""
+    def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int | None = None, executor=None,
+                 cache_fraction: float = 0.25):
+        """executor(slot_index, request) -> np.ndarray replaces the GPU path (used by host tests).
+        cache_fraction of the budget holds resident channels; the rest is for running requests."""
         self.device = device
         self._executor = executor
         if budget_bytes is None:
             import torch
             free, _ = torch.cuda.mem_get_info(device)
             budget_bytes = int(free * 0.8)
-        self.admission = AdmissionController(budget_bytes, slots)
+        self.channel_budget = int(budget_bytes * cache_fraction)
+        self.admission = AdmissionController(budget_bytes - self.channel_budget, slots)
+        self._channels = {}          # channel_key -> _Channel (insertion order = least recently used first)
+        self._chan_lock = threading.Lock()
+        self.channel_bytes = 0
+        self.channel_hits = 0
+        self.graph_replays = 0
         self._pending: "queue.Queue[tuple]" = queue.Queue()
         self._next_id = 0
         self._id_lock = threading.Lock()
@@ -232,6 +282,16 @@ class Server:
         from . import risrt as R
         ctx, stream = self._context(slot)
         with torch.cuda.stream(stream):
+            n, C, M = len(req.rx_xyz), req.gammas.shape[0], req.gammas.shape[1]
+            dev = f"cuda:{self.device}"
+            G = torch.from_numpy(np.ascontiguousarray(req.gammas, np.complex64)).to(dev, non_blocking=False)
+            if req.kind == "sweep" and req.channel_key is not None:
+                ch = self._channel_acquire(req.channel_key, n, M, C, req.precision)
+                if ch is not None:
+                    try:
+                        return self._sweep_resident(ctx, stream, ch, G)
+                    finally:
+                        ch.lock.release()
             scene = self._scene_handle(slot, ctx, req.scene_id)
             ris = ctx.ris_upload(req.ris.elem_uv, req.ris.center, req.ris.t1, req.ris.t2, req.ris.dy, req.ris.dz,
                                  req.ris.elem_gain, req.ris.host_face)
@@ -240,25 +300,100 @@ class Server:
             rx = ctx.rx_upload(req.rx_xyz)
             flags = R.FLAG_ENV_PATHS if req.env_paths else 0
             ps = ctx.trace_paths(scene, ris, rx, req.freq_hz, req.max_order_tx, req.max_order_rx, flags)
-            n, C, M = len(req.rx_xyz), req.gammas.shape[0], req.gammas.shape[1]
-            G = torch.from_numpy(np.ascontiguousarray(req.gammas, np.complex64)).to(f"cuda:{self.device}",
-                                                                                      non_blocking=False)
-            if req.kind == "coverage":
-                E = torch.empty((C, n), dtype=torch.complex64, device=G.device)
-                P = torch.empty((C, n), dtype=torch.float32, device=G.device)
+            keep = None
+            if not uses_channel(req):
+                E = torch.empty((C, n), dtype=torch.complex64, device=dev)
+                P = torch.empty((C, n), dtype=torch.float32, device=dev)
                 ctx.eval_field(ps, G, E, P)
                 out = P.t().contiguous()
             else:
-                A = torch.empty((n, M), dtype=torch.complex64, device=G.device)
-                E0 = torch.empty(n, dtype=torch.complex64, device=G.device)
+                A = torch.empty((n, M), dtype=torch.complex64, device=dev)
+                E0 = torch.empty(n, dtype=torch.complex64, device=dev)
                 ctx.build_A(ps, A, E0)
-                out = torch.empty((n, C), dtype=torch.float32, device=G.device)
-                ctx.sweep_configs(A, E0, G, out, req.precision, ctx.sweep_workspace(n, M, C, req.precision))
+                out = torch.empty((n, C), dtype=torch.float32, device=dev)
+                prec = req.precision if req.kind == "sweep" else R.PREC_BF16X2
+                ws = ctx.sweep_workspace(n, M, max(C, CHANNEL_CFG_CAP), prec)
+                ctx.sweep_configs(A, E0, G, out, prec, ws)
+                if req.kind == "sweep" and req.channel_key is not None and prec in (R.PREC_BF16, R.PREC_BF16X2):
+                    keep = (A, E0, ws, prec, max(C, CHANNEL_CFG_CAP))
             host = out.cpu().numpy()
             stream.synchronize()
             for h in (ps, rx, ris):
                 h.close()
+            if keep is not None:
+                self._channel_store(req.channel_key, n, M, *keep)
             return host
+
+    # -- resident channels --------------------------------------------------------------------------
+    def _channel_acquire(self, key, n, M, C, precision):
+        """The resident channel of this key, locked for this request, or None (not resident, or for
+        other sizes / precision, or too many configurations for its workspace)."""
+        with self._chan_lock:
+            ch = self._channels.get(key)
+            if ch is None or (ch.n, ch.M, ch.precision) != (n, M, precision) or C > ch.cfg_cap:
+                return None
+            self._channels[key] = self._channels.pop(key)        # most recently used last
+        ch.lock.acquire()
+        if ch.dead:                                              # evicted meanwhile
+            ch.lock.release()
+            return None
+        self.channel_hits += 1
+        return ch
+
+    def _sweep_resident(self, ctx, stream, ch, G):
+        """Sweep on a resident channel: A stays packed in its workspace; a CUDA graph of the sweep is
+        captured once per configuration count and replayed with the new configurations."""
+        import torch
+        n, C = ch.n, G.shape[0]
+        if n * C * 4 <= GRAPH_OUT_LIMIT:
+            gr = ch.graphs.get(C)
+            if gr is None:
+                G_static = torch.empty_like(G)
+                P_static = torch.empty((n, C), dtype=torch.float32, device=G.device)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                    ctx.sweep_configs(ch.A, ch.E0, G_static, P_static, ch.precision, ch.ws, keep_a=True,
+                                      defer_check=True)
+                gr = ch.graphs[C] = (g, G_static, P_static)
+                with self._chan_lock:
+                    extra = G_static.numel() * 8 + P_static.numel() * 4
+                    ch.bytes += extra
+                    self.channel_bytes += extra
+            g, G_static, P_static = gr
+            G_static.copy_(G)
+            g.replay()
+            ctx.sweep_check(ch.ws)
+            self.graph_replays += 1
+            return P_static.cpu().numpy()
+        out = torch.empty((n, C), dtype=torch.float32, device=G.device)
+        ctx.sweep_configs(ch.A, ch.E0, G, out, ch.precision, ch.ws, keep_a=True)
+        host = out.cpu().numpy()
+        stream.synchronize()
+        return host
+
+    def _channel_store(self, key, n, M, A, E0, ws, precision, cfg_cap):
+        """Keep a channel resident if it fits the channel budget after evicting least recently used
+        channels that no request is using."""
+        nbytes = A.numel() * 8 + E0.numel() * 8 + ws.numel()
+        if nbytes > self.channel_budget:
+            return
+        with self._chan_lock:
+            if key in self._channels:
+                return
+            for k in list(self._channels):
+                if self.channel_bytes + nbytes <= self.channel_budget:
+                    break
+                old = self._channels[k]
+                if old.lock.acquire(blocking=False):
+                    old.dead = True
+                    old.graphs.clear()
+                    self.channel_bytes -= old.bytes
+                    del self._channels[k]
+                    old.lock.release()
+            if self.channel_bytes + nbytes > self.channel_budget:
+                return
+            self._channels[key] = _Channel(n, M, precision, A, E0, ws, cfg_cap, nbytes)
+            self.channel_bytes += nbytes
 
     # -- lifecycle ----------------------------------------------------------------------------------
     def drain(self, futures, timeout: float = 600.0):
@@ -273,17 +408,26 @@ class Server:
             for _, handles in self._scenes.values():
                 for h in handles.values():
                     h.close()
+        with self._chan_lock:
+            for ch in self._channels.values():
+                ch.dead = True
+                ch.graphs.clear()
+            self._channels.clear()
+            self.channel_bytes = 0
         for c in self._contexts:
             if c is not None:
                 c[0].close()
 
 
 def latency_stats(results) -> dict:
+    """Latency (arrival to result), queueing (arrival to start) and service (start to result), ms."""
     lat = np.array([r.latency_s for r in results]) * 1e3
     q = np.array([r.queue_s for r in results]) * 1e3
+    sv = lat - q
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "queue_p50_ms": float(np.percentile(q, 50)),
-            "queue_p99_ms": float(np.percentile(q, 99)), "n": int(len(lat))}
+            "queue_p99_ms": float(np.percentile(q, 99)), "service_p50_ms": float(np.percentile(sv, 50)),
+            "service_p99_ms": float(np.percentile(sv, 99)), "n": int(len(lat))}
 
 
 def poisson_requests(seed: int, n: int, rate_hz: float, scenes: dict, kinds=("coverage", "sweep")):
@@ -303,3 +447,57 @@ def poisson_requests(seed: int, n: int, rate_hz: float, scenes: dict, kinds=("co
         g = S.phase_configs(rng, C, w.n_elem)
         out.append((t, Request(kind, w.name, w.ris, w.tx, w.rx, rx, g, w.freq_hz, 1, 1, True)))
     return out
+
+
+def _ris_of_size(w, n_elem: int):
+    """A RIS of n_elem elements (37 / 127 hexagonal, 1,024 / 4,096 square, lambda/2 pitch) with the
+    frame and host face of workload w's RIS."""
+    from . import scenarios as S
+    lam = S.C0 / w.freq_hz
+    layouts = {37: lambda: S.hex_layout(3, lam / 2), 127: lambda: S.hex_layout(6, lam / 2),
+               1024: lambda: S.square_layout(32, lam / 2), 4096: lambda: S.square_layout(64, lam / 2)}
+    r = w.ris
+    return S.RIS(layouts[n_elem](), r.center, r.t1, r.t2, lam / 2, lam / 2, 0.0, r.host_face)
+
+
+def mixed_requests(seed: int, n: int, rate_hz: float, scenes: dict, rx_range=(1e3, 1e6), cfg_range=(1, 512),
+                   ris_sizes=(37, 127, 1024, 4096), n_channels: int = 4, reuse: float = 0.5):
+    """Seeded Poisson stream of the serving mix: per request a scene (name -> scenarios.Workload), a
+    RIS of one of ris_sizes elements on that scene's RIS wall, a receiver grid of log-uniform size in
+    rx_range over the scene's floor (margin 0.15 m) at 1.2 m, a log-uniform configuration count in
+    cfg_range, and coverage or sweep with equal odds; a fraction `reuse` of the sweeps query one of
+    n_channels fixed channels (same scene, RIS, Tx and receivers, new configurations)."""
+    from . import scenarios as S
+    rng = S.SplitMix64(seed)
+    names = sorted(scenes)
+
+    def log_uniform(lo, hi):
+        return math.exp(math.log(lo) + rng.uniform() * (math.log(hi) - math.log(lo)))
+
+    def setup():
+        w = scenes[names[int(rng.uniform() * len(names)) % len(names)]]
+        ris = _ris_of_size(w, ris_sizes[int(rng.uniform() * len(ris_sizes)) % len(ris_sizes)])
+        side = max(1, int(round(math.sqrt(log_uniform(*rx_range)))))
+        v = w.scene.verts
+        x0, y0 = float(v[:, 0].min()) + 0.15, float(v[:, 1].min()) + 0.15
+        x1, y1 = float(v[:, 0].max()) - 0.15, float(v[:, 1].max()) - 0.15
+        return w, ris, S.linspace_grid(x0, x1, side, y0, y1, side, 1.2, jitter=True)
+
+    channels = [setup() for _ in range(n_channels)]
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += -math.log(max(rng.uniform(), 1e-300)) / rate_hz
+        kind = "sweep" if rng.uniform() < 0.5 else "coverage"
+        key = None
+        if kind == "sweep" and channels and rng.uniform() < reuse:
+            k = int(rng.uniform() * len(channels)) % len(channels)
+            w, ris, rx = channels[k]
+            key = f"channel{k}"
+        else:
+            w, ris, rx = setup()
+        C = max(1, min(int(cfg_range[1]), int(log_uniform(cfg_range[0], cfg_range[1] + 1))))
+        g = S.phase_configs(rng, C, ris.elem_uv.shape[0])
+        out.append((t, Request(kind, w.name, ris, w.tx, w.rx, rx, g, w.freq_hz, 1, 1, True, channel_key=key)))
+    return out
+

@@ -128,3 +128,54 @@ def test_results_identical_alone_and_in_mix():
     srv.close()
     for a, m in zip(alone, mixed):
         assert np.array_equal(a, m)
+
+
+def test_mixed_requests_span_the_serving_mix():
+    """The serving mix: receiver grids of 1k-1M points, 1-512 configurations, RIS of 37 to 4,096
+    elements, coverage and sweep, some sweeps on fixed channels (same scene, RIS and receivers)."""
+    w = S.room(grid=4)
+    w.name = "room"
+    reqs = [r for _, r in serve.mixed_requests(5, 200, 2000.0, {"room": w})]
+    n = np.array([len(r.rx_xyz) for r in reqs])
+    C = np.array([r.gammas.shape[0] for r in reqs])
+    M = {r.gammas.shape[1] for r in reqs}
+    assert n.min() >= 31 ** 2 and n.max() <= 1000 ** 2 and n.max() > 100_000 and n.min() < 5_000
+    assert C.min() >= 1 and C.max() <= 512 and C.max() > 100
+    assert M == {37, 127, 1024, 4096}
+    keyed = [r for r in reqs if r.channel_key is not None]
+    assert keyed and all(r.kind == "sweep" for r in keyed)
+    for r in keyed:                       # a channel is one scene, RIS and receiver grid
+        first = next(q for q in keyed if q.channel_key == r.channel_key)
+        assert r.rx_xyz is first.rx_xyz and r.ris is first.ris
+    assert any(serve.uses_channel(r) for r in reqs if r.kind == "coverage")
+    assert any(not serve.uses_channel(r) for r in reqs if r.kind == "coverage")
+
+
+@pytest.mark.gpu
+def test_resident_channel_and_graph_replay():
+    """Sweeps naming the same channel: the first traces, builds A and packs it for the tensor cores;
+    the later ones reuse it and replay a captured graph of the sweep per configuration count. Every
+    result is bitwise what the full computation (no channel key) gives for its configurations."""
+    from paper_2402_13034_gb300 import build as B
+    B.build()
+    w = S.room(grid=24, n_boxes=10)
+    w.name = "room_c"
+    reqs = []
+    for i, C in enumerate((8, 8, 3, 8, 3, 20)):
+        g = S.phase_configs(S.SplitMix64(100 + i), C, w.n_elem)
+        reqs.append(serve.Request("sweep", "room_c", w.ris, w.tx, w.rx, w.rx_xyz, g, w.freq_hz, 1, 1, True,
+                                  channel_key="c0"))
+    srv = serve.Server(slots=2)
+    srv.add_scene("room_c", w.scene)
+    got = [srv.submit(r).result(timeout=300).P for r in reqs]
+    hits, replays = srv.channel_hits, srv.graph_replays
+    srv.close()
+    assert hits == 5 and replays == 5
+    for r in reqs:
+        r.channel_key = None
+    srv = serve.Server(slots=2)
+    srv.add_scene("room_c", w.scene)
+    ref = [srv.submit(r).result(timeout=300).P for r in reqs]
+    srv.close()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)

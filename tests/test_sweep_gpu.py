@@ -139,3 +139,64 @@ def test_pair_and_single_cta_kernels(n, M, C, prec, monkeypatch):
         out[pair] = P
     scale = max(out["0"].max(), 1e-30)
     assert np.abs(out["1"] - out["0"]).max() <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_sweep_keep_a_and_graph_replay(prec):
+    """RISRT_SWEEP_KEEP_A reuses the packed channel matrix (only Gamma is packed), and
+    RISRT_SWEEP_DEFER_CHECK makes the sweep capturable: a CUDA graph of it, replayed on new
+    configurations written into its input buffer, gives bitwise the results of a full sweep; fewer
+    configurations than the workspace was sized for also reuse it."""
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    rng = np.random.default_rng(11)
+    n, M, Cmax = 3000, 700, 96
+    A = torch.from_numpy(((rng.standard_normal((n, M)) + 1j * rng.standard_normal((n, M))) * 1e-3).astype(np.complex64)).cuda()
+    E0 = torch.from_numpy(((rng.standard_normal(n) + 1j * rng.standard_normal(n)) * 1e-2).astype(np.complex64)).cuda()
+    gam = [torch.from_numpy(np.exp(2j * np.pi * rng.random((Cmax, M))).astype(np.complex64)).cuda() for _ in range(3)]
+    s = torch.cuda.Stream()
+    ctx = R.Context(0, s.cuda_stream)
+    ref_ctx = _ctx()
+
+    def full(G):
+        P = torch.empty((n, G.shape[0]), dtype=torch.float32, device="cuda")
+        ref_ctx.sweep_configs(A, E0, G, P, prec, ref_ctx.sweep_workspace(n, M, G.shape[0], prec))
+        torch.cuda.synchronize()
+        return P.cpu().numpy()
+
+    ws = ctx.sweep_workspace(n, M, Cmax, prec)
+    P = torch.empty((n, Cmax), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        ctx.sweep_configs(A, E0, gam[0], P, prec, ws)                       # packs A into ws
+        ctx.sweep_configs(A, E0, gam[1], P, prec, ws, keep_a=True)
+    s.synchronize()
+    assert np.array_equal(P.cpu().numpy(), full(gam[1]))
+    C2 = 33                                                                   # fewer configurations, same ws
+    P2 = torch.empty((n, C2), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        ctx.sweep_configs(A, E0, gam[2][:C2].contiguous(), P2, prec, ws, keep_a=True)
+    s.synchronize()
+    assert np.array_equal(P2.cpu().numpy(), full(gam[2][:C2].contiguous()))
+    # capture (A stays packed), then replay on new configurations
+    G_static = gam[0].clone()
+    P_static = torch.empty((n, Cmax), dtype=torch.float32, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.sweep_configs(A, E0, G_static, P_static, prec, ws, keep_a=True, defer_check=True)
+    for G in (gam[1], gam[2]):
+        with torch.cuda.stream(s):
+            G_static.copy_(G)
+            g.replay()
+        ctx.sweep_check(ws)
+        assert np.array_equal(P_static.cpu().numpy(), full(G))
+
+
+def test_sweep_options_rejected_for_fp16():
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    ctx = _ctx()
+    A = torch.zeros((128, 64), dtype=torch.complex64, device="cuda")
+    G = torch.zeros((4, 64), dtype=torch.complex64, device="cuda")
+    P = torch.empty((128, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(R.RisrtError):
+        ctx.sweep_configs(A, None, G, P, 3, ctx.sweep_workspace(128, 64, 4, 3), keep_a=True)
