@@ -146,7 +146,11 @@ int risrt_rx_bind(risrt_ctx* ctx, const float* rx_xyz, int64_t n_rx, risrt_rxset
  * Geometric decisions are filtered in FP32 and settled in FP64 when the FP32 margin is too small.
  * 0 <= max_order_tx, max_order_rx <= 2; order 2 needs F <= 40000 faces. freq_hz > 0.
  * *inout: NULL to create a new path set, or an existing path set of this context whose buffers are
- * reused (grown when needed). Synchronises the stream (path counts size the output).
+ * reused (grown when needed). Synchronises the stream (path counts size the output). The Tx leg, the
+ * environment paths and the visibility work run on three non-blocking streams the context creates
+ * on its first trace, ordered after the work already on the context's stream and joined back into
+ * it before the call returns (RISRT_OVERLAP=0 in the environment keeps everything on the context's
+ * stream; so does per-kernel profiling without a name filter).
  * Errors: RISRT_ERR_NOT_READY if the Tx or Rx antenna is unset; RISRT_ERR_INVALID_ARG. */
 int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris,
                       const risrt_rxset* rxset, double freq_hz, int32_t max_order_tx,
