@@ -21,6 +21,63 @@ int fail(risrt_ctx* ctx, int code, const std::string& msg)
 
 std::atomic<long long> g_launches{0};
 
+cudaError_t ctx_malloc(risrt_ctx* ctx, void** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 1;
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->pool_mu);
+        auto it = ctx->pool_free.lower_bound(bytes);
+        if (it != ctx->pool_free.end() && it->first <= 2 * bytes + ((size_t)1 << 20)) {
+            *p = it->second;
+            ctx->pool_cached -= it->first;
+            ctx->pool_free.erase(it);
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        // cached blocks may be what is missing: release them and try once more
+        if (ctx) {
+            std::lock_guard<std::mutex> lk(ctx->pool_mu);
+            for (auto& kv : ctx->pool_free) {
+                ctx->pool_size.erase(kv.second);
+                cudaFree(kv.second);
+            }
+            ctx->pool_free.clear();
+            ctx->pool_cached = 0;
+        }
+        cudaGetLastError();
+        e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return e;
+        }
+    }
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->pool_mu);
+        ctx->pool_size[*p] = bytes;
+    }
+    return cudaSuccess;
+}
+
+void ctx_free(risrt_ctx* ctx, void* p)
+{
+    if (!p) return;
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->pool_mu);
+        auto it = ctx->pool_size.find(p);
+        if (it != ctx->pool_size.end()) {
+            if (ctx->pool_cached + it->second <= kPoolLimit) {
+                ctx->pool_free.emplace(it->second, p);
+                ctx->pool_cached += it->second;
+                return;
+            }
+            ctx->pool_size.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
 void prof_begin(risrt_ctx* ctx, const char* name, cudaStream_t st)
 {
     if (!ctx || !ctx->profiling) return;
@@ -121,6 +178,8 @@ int risrt_create(risrt_ctx** out, int device, void* stream)
 int risrt_set_stream(risrt_ctx* ctx, void* stream)
 {
     if (!ctx) return fail(nullptr, RISRT_ERR_INVALID_ARG, "null context");
+    // blocks returned to the context's cache may still be in use by work on the old stream
+    if ((cudaStream_t)stream != ctx->stream) RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->stream = (cudaStream_t)stream;
     return RISRT_OK;
 }
@@ -143,6 +202,7 @@ int risrt_destroy(risrt_ctx* ctx)
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->small) cudaFree(ctx->small);
+    for (auto& kv : ctx->pool_free) cudaFree(kv.second);   // blocks of live objects stay theirs
     delete ctx;
     return RISRT_OK;
 }
@@ -246,6 +306,7 @@ int risrt_scene_upload(risrt_ctx* ctx, const float* verts_host, int64_t n_verts,
         if (!(mats_host[2 * i] >= 1.0f) || !(mats_host[2 * i + 1] >= 0.0f))
             return fail(ctx, RISRT_ERR_INVALID_ARG, "material needs eps_r >= 1 and sigma >= 0");
     risrt_scene* sc = new (std::nothrow) risrt_scene();
+    if (sc) sc->owner = ctx;
     if (!sc) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
     sc->n_tris = n_tris;
     sc->n_faces = F;
@@ -277,6 +338,7 @@ int risrt_ris_upload(risrt_ctx* ctx, const float* elem_uv_host, int32_t M, const
         return fail(ctx, RISRT_ERR_INVALID_ARG, "t1, t2 must be orthonormal");
     risrt_ris* r = new (std::nothrow) risrt_ris();
     if (!r) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    r->owner = ctx;
     r->M = M;
     memcpy(r->center, center, sizeof(float) * 3);
     memcpy(r->t1, t1, sizeof(float) * 3);
@@ -295,7 +357,7 @@ int risrt_ris_upload(risrt_ctx* ctx, const float* elem_uv_host, int32_t M, const
         }
         e[m] = make_float4(a, b, a * a + b * b, 0.f);
     }
-    cudaError_t err = cudaMalloc(&r->elem, sizeof(float4) * M);
+    cudaError_t err = ctx_malloc(ctx, (void**)&r->elem, sizeof(float4) * M);
     if (err != cudaSuccess) {
         delete r;
         return cuda_fail(ctx, err, "cudaMalloc");
@@ -303,7 +365,7 @@ int risrt_ris_upload(risrt_ctx* ctx, const float* elem_uv_host, int32_t M, const
     err = cudaMemcpyAsync(r->elem, e.data(), sizeof(float4) * M, cudaMemcpyHostToDevice, ctx->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
     if (err != cudaSuccess) {
-        cudaFree(r->elem);
+        ctx_free(ctx, r->elem);
         delete r;
         return cuda_fail(ctx, err, "element upload");
     }
@@ -346,16 +408,17 @@ int risrt_rx_upload(risrt_ctx* ctx, const float* rx_xyz_host, int64_t n_rx, risr
     if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || !rx_xyz_host) return fail(ctx, RISRT_ERR_INVALID_ARG, "need 1 <= n_rx <= 2^26");
     risrt_rxset* r = new (std::nothrow) risrt_rxset();
     if (!r) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    r->owner = ctx;
     r->n = n_rx;
     r->owned = true;
-    cudaError_t e = cudaMalloc(&r->xyz, sizeof(float) * 3 * n_rx);
+    cudaError_t e = ctx_malloc(ctx, (void**)&r->xyz, sizeof(float) * 3 * n_rx);
     if (e != cudaSuccess) {
         delete r;
         return cuda_fail(ctx, e, "cudaMalloc");
     }
     e = cudaMemcpyAsync(r->xyz, rx_xyz_host, sizeof(float) * 3 * n_rx, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {
-        cudaFree(r->xyz);
+        ctx_free(ctx, r->xyz);
         delete r;
         return cuda_fail(ctx, e, "cudaMemcpyAsync");
     }
@@ -371,6 +434,7 @@ int risrt_rx_bind(risrt_ctx* ctx, const float* rx_xyz, int64_t n_rx, risrt_rxset
     if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || !rx_xyz) return fail(ctx, RISRT_ERR_INVALID_ARG, "need 1 <= n_rx <= 2^26");
     risrt_rxset* r = new (std::nothrow) risrt_rxset();
     if (!r) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    r->owner = ctx;
     r->n = n_rx;
     r->xyz = const_cast<float*>(rx_xyz);
     r->owned = false;
@@ -395,6 +459,7 @@ int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris*
     bool created = false;
     if (!ps) {
         ps = new (std::nothrow) risrt_pathset();
+        if (ps) ps->owner = ctx;
         if (!ps) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
         created = true;
     }
@@ -587,9 +652,11 @@ int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
     }
-    cudaFree(sc->nodes); cudaFree(sc->nodes4); cudaFree(sc->tri_geom); cudaFree(sc->tri_verts); cudaFree(sc->tri_face);
-    cudaFree(sc->faces); cudaFree(sc->face_tris); cudaFree(sc->face_test); cudaFree(sc->tri_leaf); cudaFree(sc->mats);
-    cudaFree(sc->face_grid); cudaFree(sc->cell_face);
+    risrt_ctx* pc = ctx && ctx == sc->owner ? ctx : nullptr;
+    for (void* p : {(void*)sc->nodes, (void*)sc->nodes4, (void*)sc->tri_geom, (void*)sc->tri_verts, (void*)sc->tri_face,
+                    (void*)sc->faces, (void*)sc->face_tris, (void*)sc->face_test, (void*)sc->tri_leaf, (void*)sc->mats,
+                    (void*)sc->face_grid, (void*)sc->cell_face})
+        ctx_free(pc, p);
     delete sc;
     return RISRT_OK;
 }
@@ -601,7 +668,7 @@ int risrt_ris_destroy(risrt_ctx* ctx, risrt_ris* r)
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
     }
-    cudaFree(r->elem);
+    ctx_free(ctx && ctx == r->owner ? ctx : nullptr, r->elem);
     delete r;
     return RISRT_OK;
 }
@@ -613,7 +680,7 @@ int risrt_rxset_destroy(risrt_ctx* ctx, risrt_rxset* r)
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
     }
-    if (r->owned) cudaFree(r->xyz);
+    if (r->owned) ctx_free(ctx && ctx == r->owner ? ctx : nullptr, r->xyz);
     delete r;
     return RISRT_OK;
 }
@@ -625,12 +692,11 @@ int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps)
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
     }
-    cudaFree(ps->rec); cudaFree(ps->rx_off); cudaFree(ps->vis); cudaFree(ps->E0); cudaFree(ps->cm);
-    cudaFree(ps->elem); cudaFree(ps->rx_seq); cudaFree(ps->env_seq); cudaFree(ps->env_off); cudaFree(ps->los);
-    cudaFree(ps->scratch);
-    cudaFree(ps->ctr_dev);
-    cudaFree(ps->occ_idx[0]);
-    cudaFree(ps->occ_idx[1]);
+    risrt_ctx* pc = ctx && ctx == ps->owner ? ctx : nullptr;
+    for (void* p : {(void*)ps->rec, (void*)ps->rx_off, (void*)ps->vis, (void*)ps->E0, (void*)ps->cm, (void*)ps->elem,
+                    (void*)ps->rx_seq, (void*)ps->env_seq, (void*)ps->env_off, (void*)ps->los, ps->scratch,
+                    (void*)ps->ctr_dev, (void*)ps->occ_idx[0], (void*)ps->occ_idx[1]})
+        ctx_free(pc, p);
     delete ps;
     return RISRT_OK;
 }

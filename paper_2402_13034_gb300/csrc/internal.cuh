@@ -6,7 +6,9 @@
 
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "risrt.h"
@@ -170,6 +172,11 @@ struct risrt_ctx {
     void* small = nullptr;       // 256 B of device memory for per-call reductions (allocated on first use)
     cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // concurrent parts of a trace (created on first use)
     cudaEvent_t ev[7] = {};                               // their fork / join events
+    // device blocks this context allocated (ctx_malloc) and those returned for reuse (ctx_free)
+    std::mutex pool_mu;
+    std::multimap<size_t, void*> pool_free;
+    std::unordered_map<void*, size_t> pool_size;
+    size_t pool_cached = 0;
     std::string err;
     Antenna tx{}, rx{};
     // tracing
@@ -182,6 +189,7 @@ struct risrt_ctx {
 };
 
 struct risrt_scene {
+    risrt_ctx* owner = nullptr;      // context whose block cache holds this object's device memory
     int64_t n_tris = 0;
     int64_t n_refs = 0;              // BVH leaves (triangle references)
     int n_faces = 0;
@@ -218,6 +226,7 @@ struct risrt_scene {
 };
 
 struct risrt_ris {
+    risrt_ctx* owner = nullptr;      // context whose block cache holds this object's device memory
     int M = 0;
     float center[3], t1[3], t2[3];
     float dy = 0, dz = 0, elem_gain = 0;
@@ -227,6 +236,7 @@ struct risrt_ris {
 };
 
 struct risrt_rxset {
+    risrt_ctx* owner = nullptr;      // context whose block cache holds this object's device memory
     int64_t n = 0;
     float* xyz = nullptr;        // [n][3] device
     bool owned = false;
@@ -243,6 +253,7 @@ struct PathRec {
 };
 
 struct risrt_pathset {
+    risrt_ctx* owner = nullptr;      // context whose block cache holds this object's device memory
     int64_t n_rx = 0;
     int M = 0;
     int n_faces = 0;
@@ -257,6 +268,7 @@ struct risrt_pathset {
     int W = 0;
     float2* E0 = nullptr;            // [n_rx] LOS + environment field
     float2* cm = nullptr;            // [M] K * c_m (Tx leg, Eq. 4/5/7 factors)
+    int64_t cap_m = 0;               // elements cm and elem hold
     float4* elem = nullptr;          // [M] copy of the RIS element table (a, b, |u|^2, 0)
     int64_t n_paths = 0, cap_paths = 0;
     // inspection data
@@ -289,6 +301,15 @@ struct risrt_pathset {
 // ------------------------------------------------------------------------------------------------
 namespace risrt {
 int fail(risrt_ctx* ctx, int code, const std::string& msg);
+// Device memory of a context: ctx_malloc reuses a block that ctx_free returned (the smallest that
+// holds the request and is at most twice its size plus 1 MiB) or calls cudaMalloc; ctx_free keeps the
+// block for reuse up to kPoolLimit cached bytes per context, else frees it. A returned block may be
+// handed out again at once: callers return blocks only when later uses on the context's stream are
+// ordered after every earlier use (the destroy calls synchronise first). ctx == nullptr: plain
+// cudaMalloc / cudaFree.
+constexpr size_t kPoolLimit = (size_t)2 << 30;
+cudaError_t ctx_malloc(risrt_ctx* ctx, void** p, size_t bytes);
+void ctx_free(risrt_ctx* ctx, void* p);
 int cuda_fail(risrt_ctx* ctx, cudaError_t e, const char* where);
 #define RISRT_CUDA(ctx, call)                                           \
     do {                                                                \

@@ -891,7 +891,7 @@ __global__ void k_i32_to_i64(const int* __restrict__ a, int64_t* __restrict__ b,
 template <typename T>
 int dmalloc(risrt_ctx* ctx, T** p, size_t count)
 {
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+    cudaError_t e = ctx_malloc(ctx, (void**)p, sizeof(T) * (count > 0 ? count : 1));
     if (e != cudaSuccess) {
         *p = nullptr;
         return fail(ctx, RISRT_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
@@ -1033,7 +1033,7 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
         if ((rc = dmalloc(ctx, &compact, std::max<unsigned>(n4c, 1u)))) return rc;
         RISRT_KERNEL(ctx, "k_bvh4_compact", (k_bvh4_compact<<<nblk(n4c, 128), 128, 0, s>>>(sc->nodes4, vals, cidx, (int)n4c, compact)));
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-        cudaFree(sc->nodes4);
+        ctx_free(ctx, sc->nodes4);
         sc->nodes4 = compact;
         sc->n_nodes4 = (int)n4c;
         // walk starts: the depth-1 nodes sort first, the main subtree's root before the shell's
@@ -1090,18 +1090,17 @@ int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_
         if ((rc = dmalloc(ctx, &sc->cell_face, n_cells > 0 ? n_cells : 1))) return rc;
         RISRT_KERNEL(ctx, "k_cell_face", (k_cell_face<<<F, 256, 0, s>>>(sc->face_grid, goff, F, sc->cell_face)));
         RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-        cudaFree(gcnt);
-        cudaFree(goff);
+        ctx_free(ctx, gcnt);
+        ctx_free(ctx, goff);
     }
 
     RISRT_CUDA(ctx, cudaMemcpyAsync(sc->tri_leaf, leaf_of_orig, sizeof(int) * nt, cudaMemcpyDeviceToDevice, s));
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-    cudaFree(d_verts); cudaFree(d_tris); cudaFree(d_face); cudaFree(d_mat); cudaFree(d_bb);
-    cudaFree(keys); cudaFree(vals); cudaFree(tmp); cudaFree(leaf_of_orig); cudaFree(tmp0);
-    cudaFree(ref_cnt); cudaFree(ref_off); cudaFree(ref_tri); cudaFree(ref_lo); cudaFree(ref_hi);
-    cudaFree(leaf_lo); cudaFree(leaf_hi);
-    cudaFree(parent_int); cudaFree(parent_leaf); cudaFree(flags); cudaFree(cidx);
-    cudaFree(first); cudaFree(count); cudaFree(cursor); cudaFree(count64); cudaFree(start);
+    for (void* p : {(void*)d_verts, (void*)d_tris, (void*)d_face, (void*)d_mat, (void*)d_bb, (void*)keys, (void*)vals, tmp,
+                    (void*)leaf_of_orig, tmp0, (void*)ref_cnt, (void*)ref_off, (void*)ref_tri, (void*)ref_lo, (void*)ref_hi,
+                    (void*)leaf_lo, (void*)leaf_hi, (void*)parent_int, (void*)parent_leaf, (void*)flags, (void*)cidx,
+                    (void*)first, (void*)count, (void*)cursor, (void*)count64, (void*)start})
+        ctx_free(ctx, p);
     return RISRT_OK;
 }
 

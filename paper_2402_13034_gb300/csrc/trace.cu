@@ -1643,13 +1643,14 @@ struct Arena {   // bump allocator over one device buffer; with base == nullptr 
     }
 };
 
+// Device buffer of at least `need` elements, from (and returned to) the block cache of `pool`.
 template <typename T>
-int grow(risrt_ctx* ctx, T** p, int64_t* cap, int64_t need)
+int grow(risrt_ctx* ctx, risrt_ctx* pool, T** p, int64_t* cap, int64_t need)
 {
     if (*p && *cap >= need) return RISRT_OK;
-    if (*p) cudaFree(*p);
+    if (*p) ctx_free(pool, *p);
     int64_t c = std::max<int64_t>(need, 1);
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)c);
+    cudaError_t e = ctx_malloc(pool, (void**)p, sizeof(T) * (size_t)c);
     if (e != cudaSuccess) {
         *p = nullptr;
         *cap = 0;
@@ -1713,7 +1714,7 @@ static int build_occ_lists(risrt_ctx* ctx, const DeviceScene& S, int64_t n_tris,
     RISRT_CUDA(ctx, cudaMemcpyAsync(&total, off64 + F, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     RISRT_CUDA(ctx, cudaStreamSynchronize(s));
     if (total > INT32_MAX) return RISRT_OK;
-    int rc = grow(ctx, idx, idx_cap, std::max<int64_t>(total, 1));
+    int rc = grow(ctx, (risrt_ctx*)nullptr, idx, idx_cap, std::max<int64_t>(total, 1));
     if (rc) return rc;
     RISRT_KERNEL(ctx, "k_i64_to_i32", (k_i64_to_i32<<<nblk(F + 1, 256), 256, 0, s>>>(off64, F + 1, off)));
     RISRT_KERNEL(ctx, "k_occ_lists", (k_occ_lists<<<nblk(pairs, 256), 256, 0, s>>>(S, src, n_tris, 1, nullptr, off, cursor, *idx)));
@@ -1819,22 +1820,27 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
 
     // --- resident per-Rx arrays
     int rc;
+    // the path set's device memory comes from its owner's block cache (reused buffers are only
+    // touched by work ordered after their earlier uses on this stream)
+    risrt_ctx* pool = ps->owner == ctx ? ctx : nullptr;
     if (ps->cap_rx < n_rx || !ps->vis) {
-        cudaFree(ps->vis); cudaFree(ps->E0); cudaFree(ps->rx_off); cudaFree(ps->los); cudaFree(ps->env_off);
+        for (void* q : {(void*)ps->vis, (void*)ps->E0, (void*)ps->rx_off, (void*)ps->los, (void*)ps->env_off}) ctx_free(pool, q);
         ps->vis = nullptr; ps->E0 = nullptr; ps->rx_off = nullptr; ps->los = nullptr; ps->env_off = nullptr;
         int64_t c = 0;
-        if ((rc = grow(ctx, &ps->vis, &c, n_rx * W))) return rc;
-        c = 0; if ((rc = grow(ctx, &ps->E0, &c, n_rx))) return rc;
-        c = 0; if ((rc = grow(ctx, &ps->rx_off, &c, n_rx + 1))) return rc;
-        c = 0; if ((rc = grow(ctx, &ps->los, &c, n_rx))) return rc;
-        c = 0; if ((rc = grow(ctx, &ps->env_off, &c, n_rx + 1))) return rc;
+        if ((rc = grow(ctx, pool, &ps->vis, &c, n_rx * W))) return rc;
+        c = 0; if ((rc = grow(ctx, pool, &ps->E0, &c, n_rx))) return rc;
+        c = 0; if ((rc = grow(ctx, pool, &ps->rx_off, &c, n_rx + 1))) return rc;
+        c = 0; if ((rc = grow(ctx, pool, &ps->los, &c, n_rx))) return rc;
+        c = 0; if ((rc = grow(ctx, pool, &ps->env_off, &c, n_rx + 1))) return rc;
         ps->cap_rx = n_rx;
     }
-    if (ps->cm) cudaFree(ps->cm);
-    if (ps->elem) cudaFree(ps->elem);
-    ps->cm = nullptr; ps->elem = nullptr;
-    RISRT_CUDA(ctx, cudaMalloc(&ps->cm, sizeof(float2) * M));
-    RISRT_CUDA(ctx, cudaMalloc(&ps->elem, sizeof(float4) * M));
+    {
+        int64_t c = ps->cm ? ps->cap_m : 0;
+        if ((rc = grow(ctx, pool, &ps->cm, &c, M))) return rc;
+        c = ps->elem ? ps->cap_m : 0;
+        if ((rc = grow(ctx, pool, &ps->elem, &c, M))) return rc;
+        ps->cap_m = std::max<int64_t>(ps->cap_m, M);
+    }
     RISRT_CUDA(ctx, cudaMemcpyAsync(ps->elem, ris->elem, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s));
 
     // --- scratch: sequence tables, candidates, counters
@@ -1980,10 +1986,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         layout(measure, Lm);
         const size_t need = measure.used + 256;
         if (ps->scratch_bytes < need) {
-            cudaFree(ps->scratch);
+            ctx_free(pool, ps->scratch);
             ps->scratch = nullptr;
             ps->scratch_bytes = 0;
-            cudaError_t e = cudaMalloc(&ps->scratch, need);
+            cudaError_t e = ctx_malloc(pool, &ps->scratch, need);
             if (e != cudaSuccess) return fail(ctx, RISRT_ERR_OOM, "scratch allocation failed");
             ps->scratch_bytes = need;
         }
@@ -2210,9 +2216,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         ps->tx_seq_host.assign(tx_ids_host.begin(), tx_ids_host.begin() + n_tx);
 
         // Rx-leg records, E0, environment ids
-        if ((rc = grow(ctx, &ps->rec, &ps->cap_paths, n_paths))) return rc;
-        if ((rc = grow(ctx, &ps->rx_seq, &ps->cap_rx_seq, std::max<int64_t>(n_paths, 1)))) return rc;
-        if ((rc = grow(ctx, &ps->env_seq, &ps->cap_env, std::max<int64_t>(n_env, 1)))) return rc;
+        if ((rc = grow(ctx, pool, &ps->rec, &ps->cap_paths, n_paths))) return rc;
+        if ((rc = grow(ctx, pool, &ps->rx_seq, &ps->cap_rx_seq, std::max<int64_t>(n_paths, 1)))) return rc;
+        if ((rc = grow(ctx, pool, &ps->env_seq, &ps->cap_env, std::max<int64_t>(n_env, 1)))) return rc;
         ps->n_paths = n_paths;
         ps->n_env = n_env;
         RISRT_KERNEL(ctx, "k_records", (k_records<<<nblk(n_rx * kRecGroup, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
@@ -2224,7 +2230,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         }
         RISRT_KERNEL(ctx, "k_units", (k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1)));
         // statistics stay on the device until asked for (risrt_pathset_stats_get waits for them)
-        if (!ps->ctr_dev) RISRT_CUDA(ctx, cudaMalloc(&ps->ctr_dev, sizeof(unsigned long long) * 6));
+        if (!ps->ctr_dev) RISRT_CUDA(ctx, ctx_malloc(pool, (void**)&ps->ctr_dev, sizeof(unsigned long long) * 6));
         RISRT_CUDA(ctx, cudaMemcpyAsync(ps->ctr_dev, counters, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToDevice, s));
         ps->stats_pending = true;
         ps->stream = s;
