@@ -69,13 +69,20 @@ enum {
  * ---------------------------------------------------------------------------------------------- */
 
 /* Create a context on CUDA device `device`, enqueueing work on `stream` (a cudaStream_t; NULL means
- * the legacy default stream). Fails with RISRT_ERR_CUDA if the device cannot be used. */
+ * the legacy default stream). Fails with RISRT_ERR_CUDA if the device cannot be used.
+ * Scenes, RIS, receiver sets and path sets take their device memory from a block cache of the
+ * context that creates them; destroying them with that context returns the blocks to it (up to
+ * 2 GiB stay cached for reuse; an allocation that fails releases the cache and retries). Destroy
+ * objects before their context: an object destroyed with another context or NULL frees its memory
+ * with cudaFree. */
 int risrt_create(risrt_ctx** out, int device, void* stream);
 
-/* Change the stream later calls enqueue on. */
+/* Change the stream later calls enqueue on (synchronises the previous stream first, since cached
+ * blocks may still be in use by its work). */
 int risrt_set_stream(risrt_ctx* ctx, void* stream);
 
-/* Synchronise the context's stream and release every device resource of the context. */
+/* Synchronise the context's stream and release every device resource of the context, including
+ * its cached blocks. */
 int risrt_destroy(risrt_ctx* ctx);
 
 /* Message describing the last failure on ctx (or on creation when ctx is NULL). Never NULL. */
