@@ -24,6 +24,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2402_13034_gb300 import scenarios as S  # noqa: E402
+from paper_2402_13034_gb300.replicas import combine_over_ranks, rank_receivers  # noqa: E402
 
 METRIC = "RIS field evals/s (rx*elem*path*config)"
 UNIT = "evals/s"
@@ -440,9 +441,7 @@ def main():
     ctx = R.Context(local, stream.cuda_stream)
 
     # each rank processes its own receiver batch (weak scaling): the grid shifted by a rank offset
-    rx_host = w.rx_xyz.copy()
-    if rank:
-        rx_host[:, 0] += 1e-3 * rank
+    rx_host = rank_receivers(w.rx_xyz, rank)
     rx_dev = torch.from_numpy(rx_host).to(dev)
     scene, ris, _ = R.upload_workload(ctx, w)
     rxs = ctx.rx_bind(rx_dev)
@@ -504,16 +503,7 @@ def main():
     if sampler:
         time.sleep(0.3)
         sampler.terminate()
-    total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(units)], device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units_all = float(u.item())
-    else:
-        units_all = float(units)
+    total_ms, units_all = combine_over_ranks(float(np.sum(times)), float(units), dev)
     ms_per_step = total_ms / args.steps
     value = units_all * args.steps / (total_ms / 1e3)
 
@@ -591,7 +581,8 @@ def main():
             t0 = time.perf_counter()
             u_e2e += e2e_step()
             t_e2e += time.perf_counter() - t0
-        e2e = {"value": u_e2e / t_e2e * (world if world > 1 else 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        t_e2e, u_e2e = combine_over_ranks(t_e2e, u_e2e, dev)
+        e2e = {"value": u_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     sweep = None
