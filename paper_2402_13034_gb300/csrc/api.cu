@@ -695,7 +695,7 @@ int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps)
     risrt_ctx* pc = ctx && ctx == ps->owner ? ctx : nullptr;
     for (void* p : {(void*)ps->rec, (void*)ps->rx_off, (void*)ps->vis, (void*)ps->E0, (void*)ps->cm, (void*)ps->elem,
                     (void*)ps->rx_seq, (void*)ps->env_seq, (void*)ps->env_off, (void*)ps->los, ps->scratch,
-                    (void*)ps->ctr_dev, (void*)ps->occ_idx[0], (void*)ps->occ_idx[1]})
+                    (void*)ps->ctr_dev})
         ctx_free(pc, p);
     delete ps;
     return RISRT_OK;

@@ -291,8 +291,6 @@ struct risrt_pathset {
     // scratch (grown as needed, kept for reuse)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    int* occ_idx[2] = {nullptr, nullptr};   // occluder lists (from the Tx, from the RIS centre)
-    int64_t occ_cap[2] = {0, 0};
     int cand_cap = 0;                // per-Rx geometric candidate capacity
 };
 

@@ -591,106 +591,6 @@ __global__ void k_dense_list(const int* __restrict__ cand_cnt, const int* __rest
     }
 }
 
-// ------------------------------------------------------------------------------------------------
-// occluder lists: the first segment of every path from a source S runs from S to a point of the
-// first face f, so it stays inside the union over f's triangles of the pyramids with apex S; only
-// triangles that can meet one of those pyramids can block it. A triangle is left out only when a
-// plane of the pyramid (three sides, the face plane) separates it by more than 1e-6 m, or when the
-// pyramid lies on one side of the triangle's own plane.
-// ------------------------------------------------------------------------------------------------
-__device__ bool tri_meets_pyramid(d3 S0, const d3* q, const d3* v)
-{
-    const double tol = 1e-6;
-    // beyond the base plane, on the far side from the apex
-    d3 nb = cross(q[1] - q[0], q[2] - q[0]);
-    const double nbl = norm(nb);
-    if (nbl == 0.0) return true;
-    nb = nb * (1.0 / nbl);
-    const double sa = dot(nb, S0 - q[0]);
-    const double sg = sa > 0 ? 1.0 : -1.0;
-    if (sg * dot(nb, v[0] - q[0]) < -tol && sg * dot(nb, v[1] - q[0]) < -tol && sg * dot(nb, v[2] - q[0]) < -tol)
-        return false;
-    // the three side planes through the apex
-    for (int e = 0; e < 3; ++e) {
-        const d3 p0 = q[e], p1 = q[(e + 1) % 3], p2 = q[(e + 2) % 3];
-        d3 n = cross(p0 - S0, p1 - S0);
-        const double l = norm(n);
-        if (l == 0.0) continue;
-        n = n * (1.0 / l);
-        if (dot(n, p2 - S0) < 0) n = n * -1.0;
-        if (dot(n, v[0] - S0) < -tol && dot(n, v[1] - S0) < -tol && dot(n, v[2] - S0) < -tol) return false;
-    }
-    // the triangle's own plane
-    d3 nt = cross(v[1] - v[0], v[2] - v[0]);
-    const double ntl = norm(nt);
-    if (ntl > 0.0) {
-        nt = nt * (1.0 / ntl);
-        const double s0 = dot(nt, S0 - v[0]);
-        bool all_pos = s0 > tol, all_neg = s0 < -tol;
-        for (int k = 0; k < 3; ++k) {
-            const double sk = dot(nt, q[k] - v[0]);
-            all_pos = all_pos && sk > tol;
-            all_neg = all_neg && sk < -tol;
-        }
-        if (all_pos || all_neg) return false;
-    }
-    return true;
-}
-
-// One thread per (face, input triangle): count (mode 0) or write (mode 1) the occluders of face f.
-__global__ void k_occ_lists(DeviceScene S, d3 src, int64_t n_tris, int mode, int* __restrict__ cnt,
-                            const int* __restrict__ off, int* __restrict__ cursor, int* __restrict__ idx)
-{
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t f = gid / n_tris;
-    const int64_t t = gid % n_tris;
-    if (f >= S.n_faces) return;
-    const int leaf = S.tri_leaf[t];
-    const TriVerts tv = S.tri_verts[leaf];
-    const d3 v[3] = {ldv(tv.v0), ldv(tv.v1), ldv(tv.v2)};
-    const Face fc = S.faces[(int)f];
-    // cheap box prefilter: pyramid box (apex and face vertices) against the triangle box
-    float lo[3] = {(float)src.x, (float)src.y, (float)src.z}, hi[3] = {lo[0], lo[1], lo[2]};
-    for (int j = fc.tri_begin; j < fc.tri_end; ++j) {
-        const TriVerts fv = S.tri_verts[S.face_tris[j]];
-        const float4 w[3] = {fv.v0, fv.v1, fv.v2};
-        for (int k = 0; k < 3; ++k) {
-            lo[0] = fminf(lo[0], w[k].x); lo[1] = fminf(lo[1], w[k].y); lo[2] = fminf(lo[2], w[k].z);
-            hi[0] = fmaxf(hi[0], w[k].x); hi[1] = fmaxf(hi[1], w[k].y); hi[2] = fmaxf(hi[2], w[k].z);
-        }
-    }
-    const float pad = 1e-4f;
-    const float4 tw[3] = {tv.v0, tv.v1, tv.v2};
-    const float tlo[3] = {fminf(tw[0].x, fminf(tw[1].x, tw[2].x)), fminf(tw[0].y, fminf(tw[1].y, tw[2].y)),
-                          fminf(tw[0].z, fminf(tw[1].z, tw[2].z))};
-    const float thi[3] = {fmaxf(tw[0].x, fmaxf(tw[1].x, tw[2].x)), fmaxf(tw[0].y, fmaxf(tw[1].y, tw[2].y)),
-                          fmaxf(tw[0].z, fmaxf(tw[1].z, tw[2].z))};
-    for (int k = 0; k < 3; ++k)
-        if (tlo[k] > hi[k] + pad || thi[k] < lo[k] - pad) return;
-    bool meets = false;
-    for (int j = fc.tri_begin; j < fc.tri_end && !meets; ++j) {
-        const TriVerts fv = S.tri_verts[S.face_tris[j]];
-        const d3 q[3] = {ldv(fv.v0), ldv(fv.v1), ldv(fv.v2)};
-        meets = tri_meets_pyramid(src, q, v);
-    }
-    if (!meets) return;
-    if (mode == 0) atomicAdd(&cnt[f], 1);
-    else idx[off[f] + atomicAdd(&cursor[f], 1)] = leaf;
-}
-
-__global__ void k_i32_scan_prep(const int* __restrict__ a, int64_t n, int64_t* __restrict__ b)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = a[i];
-    if (i == n) b[i] = 0;
-}
-
-__global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int* __restrict__ b)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (int)a[i];
-}
-
 // FP32 reflection points of a candidate (the same back-trace as the candidate filter): q0 = the last
 // point P (next to the destination R), q1 = the first point P1 (order 2; P for order 1); w holds a
 // first-order bound on each point's error from the FP32 roundings of the inputs (images, planes and
@@ -988,21 +888,9 @@ __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float*
 // and every loop iteration advances each busy lane by at most kSteps BVH visits, so lanes stay
 // busy while traversal lengths differ. FP64 endpoints are rebuilt only for the rare triangle whose
 // FP32 classification is too close to call. ctr[0..3]: candidates, segments, nodes, triangle tests.
-#ifndef RISRT_VALIDATE_THREADS
-#define RISRT_VALIDATE_THREADS 128
-#endif
-constexpr int kValThreads = RISRT_VALIDATE_THREADS;
-// Top four-wide nodes each block keeps in shared memory (128 B each). Off by default: on the room
-// workload the node loads hit L1 and a copy per block only takes L1 capacity (measured).
-#ifndef RISRT_VALIDATE_SMEM_NODES
-#define RISRT_VALIDATE_SMEM_NODES 0
-#endif
-constexpr int kValSmemNodes = RISRT_VALIDATE_SMEM_NODES;
+constexpr int kValThreads = 128;
 #ifndef RISRT_VALIDATE_STEPS
 #define RISRT_VALIDATE_STEPS 64    // BVH visits per lane between refills (measured on the room workload)
-#endif
-#ifndef RISRT_MAX_OCC_LIST
-#define RISRT_MAX_OCC_LIST (-1)    // occluder lists up to this length replace BVH traversal; -1: off
 #endif
 constexpr int kSteps = RISRT_VALIDATE_STEPS;
 
@@ -1015,14 +903,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
            const int* __restrict__ dense_r, const int* __restrict__ dense_slot, const int* __restrict__ dense_seq,
            const long long* __restrict__ d_total, unsigned long long* __restrict__ next, float tol_base,
            unsigned long long* refines,
-           int* err, unsigned long long* ctr, const int* __restrict__ occ_off, const int* __restrict__ occ_idx,
-           RefineQ rq, const uint8_t* __restrict__ smap, int n_sh)
+           int* err, unsigned long long* ctr, RefineQ rq, const uint8_t* __restrict__ smap)
 {
-    // the first n_sh nodes of the compact tree (its top levels) in shared memory
-    extern __shared__ float4 sh_nodes[];
-    for (int i = threadIdx.x; i < n_sh * 8; i += blockDim.x) sh_nodes[i] = reinterpret_cast<const float4*>(S.nodes4)[i];
-    __syncthreads();
-    const Bvh4Node* shn = reinterpret_cast<const Bvh4Node*>(sh_nodes);
     const long long total = *d_total;
     const float3 srcf = to_f(src);
     const bool src_in = in_scene_box(S, src);   // with both ends in the scene box a segment skips the shell
@@ -1042,8 +924,6 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     int sp = 0;
     constexpr int kNone = 0x7fffffff;
     int cur = kNone;             // current node in a register; the other entered children go on the stack
-    int li = 0, le = 0;          // occluder-list cursor (segment 0 only)
-    bool list_mode = false;
     bool blocked = false;
 
     auto start_segment = [&]() {
@@ -1056,12 +936,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         ign1 = j == info.w ? dst_face : (j == 0 ? info.x : info.y);
         g0 = ign0 >= 0 ? ign0 : -3;        // subtrees of one ignored face are skipped
         g1 = ign1 >= 0 ? ign1 : -3;
-        list_mode = j == 0 && occ_off != nullptr && occ_off[info.x + 1] - occ_off[info.x] <= RISRT_MAX_OCC_LIST;
-        if (list_mode) {            // only triangles that can meet the pyramid from the source through f1
-            li = occ_off[info.x];
-            le = occ_off[info.x + 1];
-            sp = 0;
-        } else {
+        {
             sp = 0;
             const int first = occ_start(S, (j > 0 || src_in) && (j < info.w || dst_in), stack, sp);   // path points
             cur = first == kNoRoot ? kNone : first;                                                   // lie on faces
@@ -1151,14 +1026,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         const bool active = item >= 0 && item < total;
         if (!__any_sync(FULL, active)) break;
         if (!active) continue;
-        if (list_mode) {
-            for (int it = 0; it < kSteps && li < le; ++it) {
-                if (test_leaf(occ_idx[li++])) {
-                    blocked = true;
-                    li = le;
-                }
-            }
-        } else {
+        {
             for (int it = 0; it < kSteps && cur != kNone; ++it) {
                 if (cur < 0) {
                     if (test_leaf(~cur)) {
@@ -1177,13 +1045,13 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                     sp = 0;
                     break;
                 }
-                const Bvh4Node nd = cur < n_sh ? shn[cur] : S.nodes4[cur];
+                const Bvh4Node nd = S.nodes4[cur];
                 ++tc.nodes;
                 cur = bvh4_step(nd, a, inv, g0, g1, stack, sp);   // nearest entered child next
                 if (cur == kNoChild) cur = sp > 0 ? stack[--sp] : kNone;
             }
         }
-        if (list_mode ? li >= le : cur == kNone) {
+        if (cur == kNone) {
             if (blocked) {
                 cand[(int64_t)r * cap + slot] = -1;
                 item = -1;
@@ -1695,33 +1563,6 @@ constexpr int kTxLegQueue = 4096;   // settlements queued by the Tx leg (more ar
 
 }  // namespace
 
-// Occluder lists of every face for one source (CSR, leaf indices). Returns with *off == nullptr when
-// the scene is too large for the face x triangle pass (the BVH is used instead).
-static int build_occ_lists(risrt_ctx* ctx, const DeviceScene& S, int64_t n_tris, d3 src, int* cnt, int64_t* off64,
-                           int* off, int* cursor, void* scan_tmp, int** idx, int64_t* idx_cap, const int** off_out)
-{
-    cudaStream_t s = ctx->stream;
-    const int F = S.n_faces;
-    *off_out = nullptr;
-    if (F == 0 || (double)F * (double)n_tris > 4e8) return RISRT_OK;
-    const int64_t pairs = (int64_t)F * n_tris;
-    RISRT_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int) * (F + 1), s));
-    RISRT_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * F, s));
-    RISRT_KERNEL(ctx, "k_occ_lists", (k_occ_lists<<<nblk(pairs, 256), 256, 0, s>>>(S, src, n_tris, 0, cnt, nullptr, nullptr, nullptr)));
-    RISRT_KERNEL(ctx, "k_i32_scan_prep", (k_i32_scan_prep<<<nblk(F + 1, 256), 256, 0, s>>>(cnt, F, off64)));
-    RISRT_CUDA(ctx, exclusive_scan_i64(off64, off64, F + 1, scan_tmp, s));
-    int64_t total = 0;
-    RISRT_CUDA(ctx, cudaMemcpyAsync(&total, off64 + F, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-    if (total > INT32_MAX) return RISRT_OK;
-    int rc = grow(ctx, (risrt_ctx*)nullptr, idx, idx_cap, std::max<int64_t>(total, 1));
-    if (rc) return rc;
-    RISRT_KERNEL(ctx, "k_i64_to_i32", (k_i64_to_i32<<<nblk(F + 1, 256), 256, 0, s>>>(off64, F + 1, off)));
-    RISRT_KERNEL(ctx, "k_occ_lists", (k_occ_lists<<<nblk(pairs, 256), 256, 0, s>>>(S, src, n_tris, 1, nullptr, off, cursor, *idx)));
-    *off_out = off;
-    return RISRT_OK;
-}
-
 // The context's two side streams and the events that order them against its stream (created on first
 // use, non-blocking, released with the context).
 static int side_streams(risrt_ctx* ctx)
@@ -1887,10 +1728,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             float* c_xyz;
             int *dense_r, *dense_slot, *dense_seq;
             int64_t* dense_off;
-            int* occ_cnt[2];
-            int64_t* occ_off64[2];
-            int* occ_off[2];
-            int* occ_cursor[2];
             uint32_t *rx_keys, *rx_order_u;
             void* rx_sort_tmp;
             unsigned* rx_bb;
@@ -1930,12 +1767,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.crx.cnt64_tmp = A.get<int64_t>(n_rx + 1);
             L.cenv.cnt64_tmp = A.get<int64_t>(env ? n_rx + 1 : 1);
             L.ctx_leg.cnt64_tmp = A.get<int64_t>(2);
-            for (int q = 0; q < 2; ++q) {
-                L.occ_cnt[q] = A.get<int>(F + 1);
-                L.occ_off64[q] = A.get<int64_t>(F + 1);
-                L.occ_off[q] = A.get<int>(F + 1);
-                L.occ_cursor[q] = A.get<int>(F + 1);
-            }
             L.rx_keys = A.get<uint32_t>(n_rx);
             L.rx_order_u = A.get<uint32_t>(n_rx);
             L.rx_sort_tmp = A.get<char>(sort_temp_bytes(n_rx));
@@ -2062,17 +1893,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             for (int i = 0; i < 3; ++i) tab[i].n = (int)n_allowed[i];
         }
 
-        // occluder lists of the first segments, from the Tx (Tx leg, environment) and the RIS centre
-        const int* occ_off_src[2] = {nullptr, nullptr};      // 0: Tx, 1: RIS centre
-        if (RISRT_MAX_OCC_LIST >= 0 && (max_tx > 0 || max_env > 0))
-            if ((rc = build_occ_lists(ctx, S, sc->n_tris, Tpos, L.occ_cnt[0], L.occ_off64[0], L.occ_off[0],
-                                      L.occ_cursor[0], scan_tmp, &ps->occ_idx[0], &ps->occ_cap[0], &occ_off_src[0])))
-                return rc;
-        if (RISRT_MAX_OCC_LIST >= 0 && max_rx > 0)
-            if ((rc = build_occ_lists(ctx, S, sc->n_tris, Cpos, L.occ_cnt[1], L.occ_off64[1], L.occ_off[1],
-                                      L.occ_cursor[1], scan_tmp, &ps->occ_idx[1], &ps->occ_cap[1], &occ_off_src[1])))
-                return rc;
-
         // receivers in Morton order for the candidate search
         {
             const unsigned bb_init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
@@ -2088,7 +1908,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         // One leg's candidate search and validation on stream st with scratch lb; the validation of a
         // many-destination leg first waits for maps_ready (the visibility maps, built on another stream).
         auto run_candidates = [&](const SeqTable& t, const float* dst, int64_t n_dst, d3 src, int src_face,
-                                  int dst_face, Candidates& cs, int occ, cudaStream_t st, const LegBufs& lb,
+                                  int dst_face, Candidates& cs, int map_src, cudaStream_t st, const LegBufs& lb,
                                   cudaEvent_t maps_ready) -> int {
             RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, st));
             if (t.n > 0) {
@@ -2145,17 +1965,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 const int *vr = lb.dense_r, *vs = lb.dense_slot;
                 // the validation queue reuses the buffer (the candidate settlements are done)
                 const RefineQ vq{lb.rq, lb.rq_cap, lb.rq_cnt + 1};
-                const uint8_t* smap = n_dst > 1 && use_maps ? L.smap[occ] : nullptr;
+                const uint8_t* smap = n_dst > 1 && use_maps ? L.smap[map_src] : nullptr;   // 0: from the Tx, 1: from the RIS centre
                 if (smap && maps_ready) RISRT_CUDA(ctx, cudaStreamWaitEvent(st, maps_ready, 0));
                 const unsigned blocks = (unsigned)ctx->sm_count * RISRT_VALIDATE_MINB;
-                const int n_sh = std::min(S.n_nodes4, kValSmemNodes);
-                const size_t val_shm = sizeof(Bvh4Node) * (size_t)n_sh;
-                if (val_shm > 48 * 1024)
-                    RISRT_CUDA(ctx, cudaFuncSetAttribute(k_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)val_shm));
-                RISRT_KERNEL_ON(ctx, st, "k_validate", (k_validate<<<blocks, kValThreads, val_shm, st>>>(
+                RISRT_KERNEL_ON(ctx, st, "k_validate", (k_validate<<<blocks, kValThreads, 0, st>>>(
                                                     S, dst, src, src_face, dst_face, t.e, t.d, cs.cand, cs.cap, vr,
                                                     vs, lb.dense_seq, d_total, lb.work, tol_base, counters, flags_dev + 1,
-                                                    counters + 2, occ_off_src[occ], ps->occ_idx[occ], vq, smap, n_sh)));
+                                                    counters + 2, vq, smap)));
                 RISRT_KERNEL_ON(ctx, st, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, st>>>(
                                                       S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
             }
@@ -2404,8 +2220,7 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
                                                 S, L.dst, src, src_face, dst_face, L.e, L.d, L.cand, cap, L.dense_r,
                                                 L.dense_slot, L.dense_seq, (const long long*)(L.dense_off + 1), L.counters + 6,
                                                 tol_base, L.counters,
-                                                L.flags + 1, L.counters + 2, nullptr, nullptr, RefineQ{nullptr, 0, nullptr},
-                                                nullptr, 0)));
+                                                L.flags + 1, L.counters + 2, RefineQ{nullptr, 0, nullptr}, nullptr)));
         }
         const size_t shm = sizeof(int) * (size_t)cap;
         cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
