@@ -2037,14 +2037,19 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         if ((rc = grow(ctx, pool, &ps->env_seq, &ps->cap_env, std::max<int64_t>(n_env, 1)))) return rc;
         ps->n_paths = n_paths;
         ps->n_env = n_env;
+        // E0 and the environment ids (environment leg) beside the Rx-leg records
+        fork(sB, ctx->ev[0]);
+        RISRT_KERNEL_ON(ctx, sB, "k_e0", (k_e0<<<nblk(n_rx * kRecGroup, 128), 128, 0, sB>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand,
+                                                                                     cenv.cap, env ? cenv.cnt64 : nullptr,
+                                                                                     tab[2].e, tab[2].d, ps->E0)));
+        if (env && n_env > 0) {
+            RISRT_KERNEL_ON(ctx, sB, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, sB>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off,
+                                                                                           n_rx, tab[2].e, ps->env_seq)));
+        }
         RISRT_KERNEL(ctx, "k_records", (k_records<<<nblk(n_rx * kRecGroup, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
                                                       tab[1].e, ps->rec, ps->rx_seq)));
-        RISRT_KERNEL(ctx, "k_e0", (k_e0<<<nblk(n_rx * kRecGroup, 128), 128, 0, s>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand, cenv.cap,
-                                                 env ? cenv.cnt64 : nullptr, tab[2].e, tab[2].d, ps->E0)));
-        if (env && n_env > 0) {
-            RISRT_KERNEL(ctx, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, s>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off, n_rx, tab[2].e, ps->env_seq)));
-        }
         RISRT_KERNEL(ctx, "k_units", (k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1)));
+        join(sB, ctx->ev[4]);
         // statistics stay on the device until asked for (risrt_pathset_stats_get waits for them)
         if (!ps->ctr_dev) RISRT_CUDA(ctx, ctx_malloc(pool, (void**)&ps->ctr_dev, sizeof(unsigned long long) * 6));
         RISRT_CUDA(ctx, cudaMemcpyAsync(ps->ctr_dev, counters, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToDevice, s));
