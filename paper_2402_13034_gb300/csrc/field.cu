@@ -60,6 +60,75 @@ __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_
 
 constexpr int kEvalWarps = 8;
 constexpr int kMaxCfgPerPass = 4;
+constexpr int kElemMajorMin = 64;   // arrays of at least this many elements: lanes own elements
+
+// One warp per receiver, lanes own elements (m = lane + 32 k): each lane keeps its element's data in
+// registers and sums b_mq over the receiver's paths, whose records every lane of the warp reads at
+// the same address (one broadcast load per path); then c_m and the NC configurations' Gamma_m
+// scale the sum. For arrays of kElemMajorMin elements or more.
+template <int PAT, int NC>
+__global__ void __launch_bounds__(32 * kEvalWarps)
+k_eval_em(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const uint32_t* __restrict__ vis, int W,
+          const float4* __restrict__ elem, const float2* __restrict__ cm, const float2* __restrict__ gamma,
+          int M, int64_t n_rx, int cfg0, int n_cfg, const float2* __restrict__ E0, float2* __restrict__ E,
+          float* __restrict__ P, float inv_lam, float gr, int tm, float inv_2eta0)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)kEvalWarps + (threadIdx.x >> 5);
+    if (r >= n_rx) return;
+    const int64_t o = off[r];
+    const int nq = (int)(off[r + 1] - o);
+    cf acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = cf{0.f, 0.f};
+    for (int m0 = 0; m0 < M; m0 += 32) {
+        const int m = m0 + lane;
+        const bool valid = m < M;
+        const float4 e = valid ? elem[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool direct = valid && ((vis[r * W + (m >> 5)] >> (m & 31)) & 1u);
+        cf sum = cf{0.f, 0.f};
+        for (int q = 0; q < nq; ++q) {
+            const PathRec p = rec[o + q];
+            const bool on = valid && (__float_as_int(p.a.y) > 0 || direct);   // order 0: the direct leg
+            if (!on) continue;
+            const cf b = rx_leg_term<PAT>(p, e, inv_lam, gr, tm != 0);
+            sum.re += b.re;
+            sum.im += b.im;
+        }
+        if (valid) {
+            const float2 c2 = cm[m];
+            const cf cb = cmulf(sum, cf{c2.x, c2.y});
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (c < n_cfg) {
+                    const float2 g = gamma[(int64_t)(cfg0 + c) * M + m];
+                    acc[c].re += g.x * cb.re - g.y * cb.im;
+                    acc[c].im += g.x * cb.im + g.y * cb.re;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            acc[c].re += __shfl_down_sync(0xffffffffu, acc[c].re, s);
+            acc[c].im += __shfl_down_sync(0xffffffffu, acc[c].im, s);
+        }
+    }
+    if (lane == 0) {
+        const float2 e0 = E0[r];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (c < n_cfg) {
+                float er = e0.x + acc[c].re, ei = e0.y + acc[c].im;
+                int64_t oi = (int64_t)(cfg0 + c) * n_rx + r;
+                E[oi] = make_float2(er, ei);
+                if (P) P[oi] = (er * er + ei * ei) * inv_2eta0;
+            }
+        }
+    }
+}
 
 // One warp per receiver; lanes walk the flattened (path, element) index space so small arrays keep
 // every lane busy. NC configurations share each b_mq.
@@ -169,9 +238,16 @@ int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int
     for (int c0 = 0; c0 < n_cfg; c0 += kMaxCfgPerPass) {
         const int nc = std::min(kMaxCfgPerPass, n_cfg - c0);
 #define RISRT_EVAL(PAT, NCV)                                                                                  \
-    RISRT_KERNEL(ctx, "k_eval", (k_eval<PAT, NCV><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, \
-                                                                ps->cm, gamma, ps->M, ps->n_rx, c0, nc, ps->E0, E, P, \
-                                                                inv_lam, ps->rx_gain, tm, inv_2eta0)))
+    do {                                                                                                      \
+        if (ps->M >= kElemMajorMin)                                                                           \
+            RISRT_KERNEL(ctx, "k_eval", (k_eval_em<PAT, NCV><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(       \
+                                            ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, gamma, ps->M, \
+                                            ps->n_rx, c0, nc, ps->E0, E, P, inv_lam, ps->rx_gain, tm, inv_2eta0))); \
+        else                                                                                                  \
+            RISRT_KERNEL(ctx, "k_eval", (k_eval<PAT, NCV><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(          \
+                                            ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, gamma, ps->M, \
+                                            ps->n_rx, c0, nc, ps->E0, E, P, inv_lam, ps->rx_gain, tm, inv_2eta0))); \
+    } while (0)
 #define RISRT_EVAL_NC(PAT)           \
     do {                             \
         if (nc == 1) RISRT_EVAL(PAT, 1); \
