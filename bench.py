@@ -464,8 +464,8 @@ def main():
     units = ps.stats().units * n_cfg
 
     # timed region: per-step CUDA events on the launching stream, L2 flushed between steps
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f".clocks_{rank}.csv")
+    import tempfile
+    clk_path = os.path.join(os.environ.get("RISRT_CLOCKS_DIR", tempfile.gettempdir()), f".clocks_{rank}.csv")
     sampler = clocks_sampler(clk_path) if rank == 0 else None
     # inside the timed region only the dominant kernel (k_validate) is bracketed by CUDA events, for
     # its live launch duration; the per-kernel breakdown comes from profiled steps after it
