@@ -1565,20 +1565,12 @@ constexpr int kTxLegQueue = 4096;   // settlements queued by the Tx leg (more ar
 
 // The context's two side streams and the events that order them against its stream (created on first
 // use, non-blocking, released with the context).
-#ifndef RISRT_MAP_STREAM_PRIORITY
-#define RISRT_MAP_STREAM_PRIORITY 1
-#endif
 static int side_streams(risrt_ctx* ctx)
 {
     if (ctx->side[0]) return RISRT_OK;
-    // the stream of the visibility maps (side[1]) gets the highest priority: both receiver legs'
-    // validations wait for the maps
-    int lo = 0, hi = 0;
-    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) lo = hi = 0;
-    for (int i = 0; i < 3; ++i)
-        if (cudaStreamCreateWithPriority(&ctx->side[i], cudaStreamNonBlocking, RISRT_MAP_STREAM_PRIORITY && i == 1 ? hi : lo) !=
-            cudaSuccess)
-            return fail(ctx, RISRT_ERR_CUDA, "cudaStreamCreateWithPriority failed");
+    for (cudaStream_t& st : ctx->side)
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(ctx, RISRT_ERR_CUDA, "cudaStreamCreateWithFlags failed");
     for (cudaEvent_t& ev : ctx->ev)
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
             return fail(ctx, RISRT_ERR_CUDA, "cudaEventCreateWithFlags failed");
