@@ -884,10 +884,13 @@ __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float*
 
 // Occlusion of every segment of every candidate (segments in propagation order, early exit on the
 // first block); blocked candidates are set to -1. Persistent while-while traversal: each lane pulls
-// the next candidate from a warp-aggregated atomic counter as soon as its current one is finished,
-// and every loop iteration advances each busy lane by at most kSteps BVH visits, so lanes stay
-// busy while traversal lengths differ. FP64 endpoints are rebuilt only for the rare triangle whose
-// FP32 classification is too close to call. ctr[0..3]: candidates, segments, nodes, triangle tests.
+// the next work-list entry (receiver, slot, sequence) from a warp-aggregated atomic counter as soon
+// as its current one is finished, computes the candidate's FP32 path points and their error bounds
+// (path_points), and every loop iteration advances each busy lane by at most kSteps BVH visits, so
+// lanes stay busy while traversal lengths differ. A first segment whose point lies in a decided cell
+// of the source's visibility map takes the map's answer; a segment with both ends in the scene box
+// does not walk the shell subtree. Triangles too close to call in FP32 are queued for an FP64
+// settlement after the kernel. ctr[0..3]: candidates, segments, nodes, triangle tests.
 constexpr int kValThreads = 128;
 #ifndef RISRT_VALIDATE_STEPS
 #define RISRT_VALIDATE_STEPS 64    // BVH visits per lane between refills (measured on the room workload)
@@ -1563,7 +1566,7 @@ constexpr int kTxLegQueue = 4096;   // settlements queued by the Tx leg (more ar
 
 }  // namespace
 
-// The context's two side streams and the events that order them against its stream (created on first
+// The context's three side streams and the events that order them against its stream (created on first
 // use, non-blocking, released with the context).
 static int side_streams(risrt_ctx* ctx)
 {
