@@ -179,3 +179,36 @@ def test_resident_channel_and_graph_replay():
     srv.close()
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
+
+
+def test_channel_cache_lru_and_locks():
+    """Resident channels (host bookkeeping on CPU tensors): a channel is kept while it fits the channel
+    budget, least recently used ones that no request holds are evicted first, a held one is never
+    evicted, and a lookup with other sizes, precision or more configurations than the workspace was
+    sized for misses."""
+    import torch
+    srv = serve.Server(slots=1, budget_bytes=4 << 20, executor=_Fake(), cache_fraction=0.25)   # 1 MiB of channels
+
+    def chan(key, n=64, M=128, ws_bytes=200_000, cfg_cap=512):
+        A = torch.zeros((n, M), dtype=torch.complex64)              # 64 KiB
+        E0 = torch.zeros(n, dtype=torch.complex64)
+        ws = torch.zeros(ws_bytes, dtype=torch.uint8)
+        srv._channel_store(key, n, M, A, E0, ws, 2, cfg_cap)
+
+    for k in ("a", "b", "c", "d"):
+        chan(k)                                                      # ~266 KB each: 3 fit in 1 MiB
+    assert list(srv._channels) == ["b", "c", "d"] and srv.channel_bytes <= srv.channel_budget
+    ch = srv._channel_acquire("b", 64, 128, 8, 2)                   # held by a request (most recent now)
+    assert ch is not None and srv.channel_hits == 1
+    chan("e")                                                        # evicts c, the least recent unheld
+    assert list(srv._channels) == ["d", "b", "e"]
+    chan("f")                                                        # evicts d; b stays while held
+    assert "b" in srv._channels and "d" not in srv._channels
+    ch.lock.release()
+    assert srv._channel_acquire("e", 64, 127, 8, 2) is None         # other element count
+    assert srv._channel_acquire("e", 64, 128, 8, 1) is None         # other precision
+    assert srv._channel_acquire("e", 64, 128, 513, 2) is None       # more configurations than its workspace
+    chan("big", ws_bytes=2 << 20)                                    # larger than the channel budget: not kept
+    assert "big" not in srv._channels
+    srv.close()
+    assert srv.channel_bytes == 0 and not srv._channels
