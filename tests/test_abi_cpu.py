@@ -56,3 +56,38 @@ def test_create_without_gpu_reports_error(lib_path):
     from paper_2402_13034_gb300 import risrt as R
     with pytest.raises(R.RisrtError):
         R.Context(0)
+
+
+def test_workspace_size_queries_are_host_arithmetic(lib_path):
+    """Workspace sizes are answered on the host (no device needed): they grow with every dimension,
+    split BF16 needs more than BF16, the FP32 sweep needs none, and bad arguments are rejected."""
+    lib = ctypes.CDLL(lib_path)
+    lib.risrt_sweep_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_size_t)]
+    lib.risrt_grad_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_size_t)]
+
+    def sweep(n, M, C, prec):
+        b = ctypes.c_size_t(0)
+        rc = lib.risrt_sweep_workspace_size(n, M, C, prec, ctypes.byref(b))
+        return rc, b.value
+
+    def grad(nt, B, M, prec):
+        b = ctypes.c_size_t(0)
+        rc = lib.risrt_grad_workspace_size(nt, B, M, prec, ctypes.byref(b))
+        return rc, b.value
+
+    assert sweep(65536, 1024, 4096, 0) == (0, 0)
+    rc1, b1 = sweep(65536, 1024, 4096, 1)
+    rc2, b2 = sweep(65536, 1024, 4096, 2)
+    assert rc1 == rc2 == 0 and 0 < b1 < b2
+    assert sweep(65536, 1024, 64, 1)[1] < b1 < sweep(131072, 1024, 4096, 1)[1]
+    assert sweep(65536, 512, 4096, 1)[1] < b1
+    # the packed matrix alone (n x 2M BF16) is a lower bound
+    assert b1 >= 65536 * 2 * 1024 * 2
+    for bad in ((0, 1024, 64, 1), (1024, 0, 64, 1), (1024, 64, 0, 1), (1024, 64, 8, 7)):
+        assert sweep(*bad)[0] != 0
+    rcf, bf = grad(16384, 64, 4096, 0)
+    rcb, bb = grad(16384, 64, 4096, 2)
+    assert rcf == rcb == 0 and bf > 0 and bb > bf
+    assert grad(16384, 64, 4096, 1)[0] != 0 and grad(0, 64, 4096, 0)[0] != 0
