@@ -185,7 +185,10 @@ constexpr int kCandChunk = 2048;
 //  (D) order 2: the first reflection point lies in its face.
 // Each test is decided in FP32 when its margin exceeds the FP32 error bound, otherwise the whole
 // candidate is settled by the FP64 check.
-constexpr int kMaxSmemFaces = 1024;
+#ifndef RISRT_MAX_SMEM_FACES
+#define RISRT_MAX_SMEM_FACES 1024
+#endif
+constexpr int kMaxSmemFaces = RISRT_MAX_SMEM_FACES;
 
 template <bool SMEM_FACES>
 __device__ __forceinline__ int face_class(const DeviceScene& S, const FaceTest* sh_faces, int f, float3 q, float tol)
