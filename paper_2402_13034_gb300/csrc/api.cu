@@ -184,11 +184,19 @@ int risrt_set_stream(risrt_ctx* ctx, void* stream)
     return RISRT_OK;
 }
 
+// Wait for everything the context enqueued: its stream and the side streams of its traces.
+static void sync_ctx(risrt_ctx* ctx)
+{
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (cudaStream_t st : ctx->side)
+        if (st) cudaStreamSynchronize(st);
+}
+
 int risrt_destroy(risrt_ctx* ctx)
 {
     if (!ctx) return RISRT_OK;
-    cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
+    sync_ctx(ctx);
     for (KernelPending& p : ctx->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -648,10 +656,7 @@ int risrt_find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* scene, const flo
 int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
 {
     if (!sc) return RISRT_OK;
-    if (ctx) {
-        cudaSetDevice(ctx->device);
-        cudaStreamSynchronize(ctx->stream);
-    }
+    if (ctx) sync_ctx(ctx);
     risrt_ctx* pc = ctx && ctx == sc->owner ? ctx : nullptr;
     for (void* p : {(void*)sc->nodes, (void*)sc->nodes4, (void*)sc->tri_geom, (void*)sc->tri_verts, (void*)sc->tri_face,
                     (void*)sc->faces, (void*)sc->face_tris, (void*)sc->face_test, (void*)sc->tri_leaf, (void*)sc->mats,
@@ -664,10 +669,7 @@ int risrt_scene_destroy(risrt_ctx* ctx, risrt_scene* sc)
 int risrt_ris_destroy(risrt_ctx* ctx, risrt_ris* r)
 {
     if (!r) return RISRT_OK;
-    if (ctx) {
-        cudaSetDevice(ctx->device);
-        cudaStreamSynchronize(ctx->stream);
-    }
+    if (ctx) sync_ctx(ctx);
     ctx_free(ctx && ctx == r->owner ? ctx : nullptr, r->elem);
     delete r;
     return RISRT_OK;
@@ -676,10 +678,7 @@ int risrt_ris_destroy(risrt_ctx* ctx, risrt_ris* r)
 int risrt_rxset_destroy(risrt_ctx* ctx, risrt_rxset* r)
 {
     if (!r) return RISRT_OK;
-    if (ctx) {
-        cudaSetDevice(ctx->device);
-        cudaStreamSynchronize(ctx->stream);
-    }
+    if (ctx) sync_ctx(ctx);
     if (r->owned) ctx_free(ctx && ctx == r->owner ? ctx : nullptr, r->xyz);
     delete r;
     return RISRT_OK;
@@ -688,10 +687,7 @@ int risrt_rxset_destroy(risrt_ctx* ctx, risrt_rxset* r)
 int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps)
 {
     if (!ps) return RISRT_OK;
-    if (ctx) {
-        cudaSetDevice(ctx->device);
-        cudaStreamSynchronize(ctx->stream);
-    }
+    if (ctx) sync_ctx(ctx);
     risrt_ctx* pc = ctx && ctx == ps->owner ? ctx : nullptr;
     for (void* p : {(void*)ps->rec, (void*)ps->rx_off, (void*)ps->vis, (void*)ps->E0, (void*)ps->cm, (void*)ps->elem,
                     (void*)ps->rx_seq, (void*)ps->env_seq, (void*)ps->env_off, (void*)ps->los, ps->scratch,

@@ -1721,6 +1721,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         cudaEventRecord(ev, from);
         cudaStreamWaitEvent(s, ev, 0);
     };
+    // work an earlier trace left on the side streams (one that returned early with an error) comes
+    // before this trace's use of the path set's buffers
+    if (ctx->side[0]) {
+        join(ctx->side[0], ctx->ev[3]);
+        join(ctx->side[1], ctx->ev[4]);
+        join(ctx->side[2], ctx->ev[6]);
+    }
 
     for (int attempt = 0; attempt < 6; ++attempt) {
         struct Layout {
