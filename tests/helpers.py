@@ -2,7 +2,6 @@
 with the FP64 oracle on the same seeded inputs."""
 import numpy as np
 
-from oracle import oracle as O
 
 # Tolerances (field error relative to the incoherent magnitude S(r) everywhere; power and phase
 # where the coherent field is not a deep null).

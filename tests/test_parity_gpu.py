@@ -4,7 +4,6 @@ Path and visibility sets must agree bit for bit on every receiver without an amb
 fields must agree within 5e-5 of the incoherent magnitude S(r) everywhere, and power within 1e-4
 relative and phase within 1e-3 rad where |E| >= 0.05 S(r).
 """
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 from paper_2402_13034_gb300.replicas import combine_over_ranks, rank_receivers
 
