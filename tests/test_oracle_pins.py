@@ -496,3 +496,54 @@ def test_two_parallel_planes_order2_field():
         E += fres(dz / L) ** nb * friis(L)
     f = o.field(R.astype(np.float32)[None])
     assert abs(f["E0"][0] - E) < 1e-12 * abs(E)
+
+
+def test_shell_faces_never_block_inside_the_scene_box():
+    """The GPU traversal skips shell triangles (planes with the whole scene box on one closed side:
+    the room's walls, floor and ceiling and the box bottoms lying in the floor) for segments whose
+    two ends lie in the scene box. In the oracle, removing those triangles from the room changes no
+    unambiguous occlusion decision of such segments: reflection points on faces to receivers inside
+    the room, and segments between random points of the box."""
+    w = S.room(grid=4, n_boxes=12)
+    V = w.scene.verts.astype(np.float64)
+    lo, hi = V.min(0), V.max(0)
+    corners = np.array([[(lo, hi)[(c >> k) & 1][k] for k in range(3)] for c in range(8)])
+    shell = []
+    for t in w.scene.tris:
+        p = V[t]
+        n = np.cross(p[1] - p[0], p[2] - p[0])
+        n /= np.linalg.norm(n)
+        sd = corners @ n - n @ p[0]
+        shell.append(sd.min() >= -1e-9 or sd.max() <= 1e-9)
+    shell = np.array(shell)
+    assert shell.sum() == 12 + 2 * 12       # 6 room faces + 12 box bottoms, two triangles each
+    w2 = S.room(grid=4, n_boxes=12)
+    keep = ~shell
+    w2.scene = S.Scene(w.scene.verts, w.scene.tris[keep], w.scene.face_id[keep], w.scene.mat_id[keep], w.scene.mats)
+    full, inner = O.Oracle(w), O.Oracle(w2)
+    rng = np.random.default_rng(7)
+    tris = V[w.scene.tris]
+    n_blocked = n_checked = 0
+    for _ in range(400):
+        if rng.random() < 0.5:                  # a point on a random triangle (its face ignored) to a receiver
+            t = rng.integers(len(tris))
+            u, v = rng.random(2)
+            if u + v > 1:
+                u, v = 1 - u, 1 - v
+            a = tris[t][0] + u * (tris[t][1] - tris[t][0]) + v * (tris[t][2] - tris[t][0])
+            f = int(w.scene.face_id[t])
+            b = np.array([rng.uniform(lo[0], hi[0]), rng.uniform(lo[1], hi[1]), 1.2])
+            # the reduced scene keeps the face ids of the triangles it keeps
+            r_full = full.segment_blocked(a, b, f, -1)
+            r_in = inner.segment_blocked(a, b, f, -1)
+        else:
+            a = lo + rng.random(3) * (hi - lo)
+            b = lo + rng.random(3) * (hi - lo)
+            r_full = full.segment_blocked(a, b)
+            r_in = inner.segment_blocked(a, b)
+        if r_full[1] or r_in[1]:
+            continue
+        n_checked += 1
+        n_blocked += r_full[0]
+        assert r_full[0] == r_in[0], (a, b)
+    assert n_checked > 150 and 0 < n_blocked < n_checked
