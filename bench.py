@@ -315,7 +315,7 @@ def clocks_summary(path, device_index):
 
 def cpu_oracle_rate(w, n_cfg, budget_s=15.0, steps=1):
     """Time the FP64 oracle on deterministic receiver samples of the workload; returns
-    (evals/s, threads, sample description)."""
+    (evals/s, threads, sample description, ms per sample step)."""
     from oracle import oracle as O
     o = O.Oracle(w)
     rng_idx = np.arange(w.n_rx)
@@ -341,16 +341,18 @@ def cpu_oracle_rate(w, n_cfg, budget_s=15.0, steps=1):
         total_t += time.perf_counter() - t0
         total_units += units
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return total_units / total_t, threads, f"{len(idx)} of {w.n_rx} receivers per step (stride sample), {steps} step(s)"
+    return (total_units / total_t, threads, f"{len(idx)} of {w.n_rx} receivers per step (stride sample), {steps} step(s)",
+            total_t / steps * 1e3)
 
 
 def run_reference(args, w, n_cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    val, cores, samp = cpu_oracle_rate(w, n_cfg, budget_s=args.ref_budget, steps=max(1, args.steps))
+    val, cores, samp, ms = cpu_oracle_rate(w, n_cfg, budget_s=args.ref_budget, steps=max(1, args.steps))
+    # a step of this arm is one bounded receiver sample of the workload (see cpu_baseline.sample)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "n_cfg": n_cfg},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samp},
@@ -596,7 +598,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, samp = cpu_oracle_rate(w, n_cfg, budget_s=args.cpu_budget)
+        v, cores, samp, _ = cpu_oracle_rate(w, n_cfg, budget_s=args.cpu_budget)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samp}
 
     if rank == 0:
