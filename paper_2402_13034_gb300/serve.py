@@ -350,10 +350,15 @@ class Server:
             if gr is None:
                 G_static = torch.empty_like(G)
                 P_static = torch.empty((n, C), dtype=torch.float32, device=G.device)
+                # capture on this slot's stream without torch.cuda.graph's device-wide synchronize and
+                # allocator cache release, which would stall every other slot
                 g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                g.capture_begin(capture_error_mode="thread_local")
+                try:
                     ctx.sweep_configs(ch.A, ch.E0, G_static, P_static, ch.precision, ch.ws, keep_a=True,
                                       defer_check=True)
+                finally:
+                    g.capture_end()
                 gr = ch.graphs[C] = (g, G_static, P_static)
                 with self._chan_lock:
                     extra = G_static.numel() * 8 + P_static.numel() * 4
