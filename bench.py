@@ -342,19 +342,23 @@ def cpu_oracle_rate(w, n_cfg, budget_s=15.0, steps=1):
         total_units += units
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return (total_units / total_t, threads, f"{len(idx)} of {w.n_rx} receivers per step (stride sample), {steps} step(s)",
-            total_t / steps * 1e3)
+            total_t / steps * 1e3, len(idx))
 
 
 def run_reference(args, w, n_cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    val, cores, samp, ms = cpu_oracle_rate(w, n_cfg, budget_s=args.ref_budget, steps=max(1, args.steps))
-    # a step of this arm is one bounded receiver sample of the workload (see cpu_baseline.sample)
+    val, cores, samp, ms, n_sample = cpu_oracle_rate(w, n_cfg, budget_s=args.ref_budget, steps=max(1, args.steps))
+    # a step of this arm is one bounded receiver sample of the workload (see cpu_baseline.sample); the
+    # full grid would take about n_rx / n_sample times as long
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "n_cfg": n_cfg},
+            "ms_per_step_note": f"one step is a sample of {n_sample} of {w.n_rx} receivers, not the full grid",
+            "ms_full_grid_extrapolated": ms * w.n_rx / n_sample,
+            "config": {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "n_cfg": n_cfg,
+                       "receivers_per_step": n_sample},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samp},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -598,7 +602,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, samp, _ = cpu_oracle_rate(w, n_cfg, budget_s=args.cpu_budget)
+        v, cores, samp, _, _ = cpu_oracle_rate(w, n_cfg, budget_s=args.cpu_budget)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samp}
 
     if rank == 0:

@@ -1569,6 +1569,38 @@ constexpr int kTxLegQueue = 4096;   // settlements queued by the Tx leg (more ar
 
 }  // namespace
 
+// Dynamic shared memory is a per-function, per-device attribute shared by every context and thread of
+// the process, so it is raised once per device to the largest size any launch uses and never lowered:
+// k_candidates<true> holds up to kMaxSmemFaces face outlines, k_finalize up to kFinalizeSmemMax bytes
+// (its launches take fewer warps per block when the candidate slab is wide).
+constexpr int kFinalizeSmemMax = 128 * 1024;
+constexpr int kAttrMaxDevices = 64;
+
+static int trace_func_attrs(risrt_ctx* ctx)
+{
+    static std::mutex mu;
+    static bool done[kAttrMaxDevices] = {};
+    if (ctx->device < 0 || ctx->device >= kAttrMaxDevices)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "device index too large for the kernel attribute table");
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[ctx->device]) return RISRT_OK;
+    cudaError_t e = cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(FaceTest) * kMaxSmemFaces));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(k_candidates)");
+    e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kFinalizeSmemMax);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(k_finalize)");
+    done[ctx->device] = true;
+    return RISRT_OK;
+}
+
+// Warps per k_finalize block for a candidate slab `cap` wide (each warp stages one row in shared
+// memory); 0 if even one row does not fit.
+static int finalize_warps(int cap)
+{
+    const size_t row = sizeof(int) * (size_t)cap;
+    return (int)std::min<size_t>(4, kFinalizeSmemMax / row);
+}
+
 // The context's three side streams and the events that order them against its stream (created on first
 // use, non-blocking, released with the context).
 static int side_streams(risrt_ctx* ctx)
@@ -1587,6 +1619,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 int max_tx, int max_rx, uint32_t flags, risrt_pathset* ps)
 {
     cudaStream_t s = ctx->stream;
+    if (int arc = trace_func_attrs(ctx)) return arc;
     const DeviceScene S = sc->dev();
     const int F = sc->n_faces;
     const int M = ris->M;
@@ -1952,7 +1985,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 const int* ord = n_dst > 1 ? L.rx_order : nullptr;
                 if (F <= kMaxSmemFaces) {
                     const size_t shm = sizeof(FaceTest) * (size_t)F;
-                    cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
                     RISRT_KERNEL_ON(ctx, st, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, st>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
                                                           cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl)));
@@ -1988,9 +2020,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 RISRT_KERNEL_ON(ctx, st, "k_refine_val", (k_refine_val<<<ctx->sm_count * 2, 256, 0, st>>>(
                                                       S, dst, src, t.e, t.d, cs.cand, cs.cap, vr, vs, vq, counters)));
             }
-            const int warps = 4;
-            size_t shm = sizeof(int) * (size_t)cs.cap * warps;
-            if (shm > 48 * 1024) cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            const int warps = finalize_warps(cs.cap);
+            if (warps < 1) return fail(ctx, RISRT_ERR_CAPACITY, "more geometric candidates per destination than k_finalize can sort");
+            const size_t shm = sizeof(int) * (size_t)cs.cap * warps;
             RISRT_KERNEL_ON(ctx, st, "k_finalize", (k_finalize<<<nblk(n_dst, warps), 32 * warps, shm, st>>>(cs.cand, cs.cnt, n_dst, cs.cap, t.e, cs.cnt64)));
             return RISRT_OK;
         };
@@ -2134,6 +2166,7 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
                        int dst_face, int max_order, int64_t* ids_host, int cap_host, int* n_host)
 {
     cudaStream_t s = ctx->stream;
+    if (int arc = trace_func_attrs(ctx)) return arc;
     const DeviceScene S = sc->dev();
     const int F = sc->n_faces;
     if (sc->n_tris == 0) max_order = 0;
@@ -2211,7 +2244,6 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
         dim3 grid(1, std::min<unsigned>(nblk(n_seq, kCandChunk), 32768u));
         if (F <= kMaxSmemFaces) {
             const size_t shm = sizeof(FaceTest) * (size_t)F;
-            cudaFuncSetAttribute(k_candidates<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
                                                   L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr},
@@ -2241,7 +2273,6 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
                                                 L.flags + 1, L.counters + 2, RefineQ{nullptr, 0, nullptr}, nullptr)));
         }
         const size_t shm = sizeof(int) * (size_t)cap;
-        cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         RISRT_KERNEL(ctx, "k_finalize", (k_finalize<<<1, 32, shm, s>>>(L.cand, L.cnt, 1, cap, L.e, L.cnt64)));
         RISRT_KERNEL(ctx, "k_ids_of", (k_ids_of<<<nblk(cap, 256), 256, 0, s>>>(L.cand, L.cnt64, L.e, L.ids)));
     }
