@@ -67,10 +67,12 @@ def _load():
             lib.or_set_amb_tol.argtypes = [C.c_double]
             lib.or_n_faces.argtypes = [C.c_void_p]
             lib.or_tx_leg.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                       C.c_void_p]
             lib.or_rx_paths.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
                                         C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
-                                        C.c_void_p, C.c_void_p]
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_int32, C.c_void_p, C.c_void_p]
             lib.or_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
             lib.or_element_positions.argtypes = [C.c_void_p, C.c_void_p]
@@ -175,15 +177,33 @@ class Oracle:
         return self.F + faces[0] * self.F + faces[1]
 
     # --- path sets ----------------------------------------------------------------------------
-    def tx_leg(self, cap: int = 1 << 16):
+    def tx_leg(self, cap: int = 1 << 16, amb_cap: int = 1 << 12):
+        """Valid reflected Tx-leg sequences and per-element direct visibility. ``amb`` is set if any
+        decision is ambiguous; ``vis_amb`` / ``amb_seqs`` name the ambiguous decisions; ``n_dec``
+        counts every decision (elements plus allowed sequences)."""
         ids = np.zeros(cap, np.int64)
         n = np.zeros(1, np.int64)
         vis = np.zeros(self.M, np.uint8)
         amb = np.zeros(1, np.int32)
-        _load().or_tx_leg(self._ctx, _ptr(ids), cap, _ptr(n), _ptr(vis), _ptr(amb))
-        return dict(seqs=ids[: min(int(n[0]), cap)].copy(), vis=vis.astype(bool), amb=bool(amb[0]))
+        vis_amb = np.zeros(self.M, np.uint8)
+        amb_ids = np.zeros(amb_cap, np.int64)
+        n_amb = np.zeros(1, np.int64)
+        n_dec = np.zeros(1, np.int64)
+        _load().or_tx_leg(self._ctx, _ptr(ids), cap, _ptr(n), _ptr(vis), _ptr(amb), _ptr(vis_amb),
+                          _ptr(amb_ids), amb_cap, _ptr(n_amb), _ptr(n_dec))
+        if n[0] > cap or n_amb[0] > amb_cap:
+            raise RuntimeError("oracle Tx-leg capacity exceeded")
+        return dict(seqs=ids[: int(n[0])].copy(), vis=vis.astype(bool), amb=bool(amb[0]),
+                    vis_amb=vis_amb.astype(bool), amb_seqs=amb_ids[: int(n_amb[0])].copy(),
+                    n_dec=int(n_dec[0]))
 
-    def rx_paths(self, rx_xyz: np.ndarray, cap: int = 512, env_cap: int = 512):
+    ENV_TAG = 1 << 62
+
+    def rx_paths(self, rx_xyz: np.ndarray, cap: int = 512, env_cap: int = 512, amb_cap: int = 256):
+        """Per receiver: valid Rx-leg and environment sequences, LOS, direct visibility bits, whether
+        any decision is ambiguous (``amb``), and per decision: ``los_amb``, ``vis_amb`` bits,
+        ``amb_seqs`` (Rx-leg ids) / ``amb_env`` (environment ids) whose validity is ambiguous, and
+        ``n_dec``, the number of decisions taken."""
         rx = np.ascontiguousarray(rx_xyz, np.float32).reshape(-1, 3)
         n = len(rx)
         W = (self.M + 31) // 32
@@ -194,13 +214,26 @@ class Oracle:
         los = np.zeros(n, np.uint8)
         vis = np.zeros((n, W), np.uint32)
         amb = np.zeros(n, np.int32)
+        los_amb = np.zeros(n, np.uint8)
+        vis_amb = np.zeros((n, W), np.uint32)
+        amb_ids = np.full((n, amb_cap), -1, np.int64)
+        n_amb = np.zeros(n, np.int32)
+        n_dec = np.zeros(n, np.int64)
         _load().or_rx_paths(self._ctx, _ptr(rx), n, _ptr(seq), cap, _ptr(n_seq), _ptr(env), env_cap,
-                            _ptr(n_env), _ptr(los), _ptr(vis), _ptr(amb))
-        if (n_seq > cap).any() or (n_env > env_cap).any():
+                            _ptr(n_env), _ptr(los), _ptr(vis), _ptr(amb), _ptr(los_amb), _ptr(vis_amb),
+                            _ptr(amb_ids), amb_cap, _ptr(n_amb), _ptr(n_dec))
+        if (n_seq > cap).any() or (n_env > env_cap).any() or (n_amb > amb_cap).any():
             raise RuntimeError("oracle path capacity exceeded")
+        amb_rx, amb_env = [], []
+        for i in range(n):
+            a = amb_ids[i, : n_amb[i]]
+            tagged = (a & self.ENV_TAG) != 0
+            amb_rx.append(a[~tagged].copy())
+            amb_env.append((a[tagged] & ~self.ENV_TAG).copy())
         return dict(seqs=[seq[i, : n_seq[i]].copy() for i in range(n)],
                     env=[env[i, : n_env[i]].copy() for i in range(n)],
-                    los=los.astype(bool), vis=vis, amb=amb.astype(bool))
+                    los=los.astype(bool), vis=vis, amb=amb.astype(bool), los_amb=los_amb.astype(bool),
+                    vis_amb=vis_amb, amb_seqs=amb_rx, amb_env=amb_env, n_dec=n_dec)
 
     # --- field --------------------------------------------------------------------------------
     def field(self, rx_xyz: np.ndarray):

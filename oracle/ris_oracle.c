@@ -336,12 +336,13 @@ static int seg_blocked(const or_ctx* C, v3 a, v3 b, int ign0, int ign1, int* amb
 /* Resolve the ambiguity bits of seg_blocked: ambiguous only when some hit is marginal and no hit is robust. */
 static int seg_amb(int bits) { return (bits & 2) && !(bits & 4); }
 
+/* Occlusion of one segment. The decision is ambiguous when some hit (or a segment lying in a
+   triangle's plane) is marginal and no hit is robust: a robust hit blocks under any perturbation. */
 static int blocked_decision(const or_ctx* C, v3 a, v3 b, int ign0, int ign1, int* amb)
 {
     int bits = 0;
     int r = seg_blocked(C, a, b, ign0, ign1, &bits);
-    if (bits & 1) *amb = 1;
-    if (seg_amb(bits)) *amb = 1;
+    if (((bits & 1) || seg_amb(bits)) && !(bits & 4)) *amb = 1;
     return r;
 }
 
@@ -349,6 +350,10 @@ static int blocked_decision(const or_ctx* C, v3 a, v3 b, int ign0, int ign1, int
  * Image method (Sec. II-B): validate a face sequence between src and dst.
  * pts_out receives src, P_1..P_k, dst. Returns 1 if the path is geometrically valid and unblocked.
  * ------------------------------------------------------------------------------------------ */
+/* Each condition below is classified as passing, failing robustly (it fails under every perturbation
+   of AMB_TOL) or marginal. The path is valid when every condition passes; the decision is ambiguous
+   when some condition is marginal and none fails robustly (a robust failure rejects the sequence
+   whatever the marginal ones do). */
 static int validate_seq(const or_ctx* C, v3 src, int src_face, v3 dst, int dst_face,
                         const int* seq, int k, int* amb, v3* pts)
 {
@@ -358,7 +363,7 @@ static int validate_seq(const or_ctx* C, v3 src, int src_face, v3 dst, int dst_f
     pts[0] = src;
     pts[k + 1] = dst;
     v3 y = dst;
-    int ok = 1;
+    int ok = 1, marg = 0, rfail = 0;
     double cond = 1.0;                      /* growth of the point error along the back-trace */
     for (int j = k; j >= 1; --j) {          /* back-trace from dst towards the images */
         int f = seq[j - 1];
@@ -369,23 +374,37 @@ static int validate_seq(const or_ctx* C, v3 src, int src_face, v3 dst, int dst_f
         v3 p = add(y, scl(d, t));
         pts[j] = p;
         cond *= norm(d) / fabs(den);
-        if (!(t > 0.0 && t < 1.0)) ok = 0;
-        if (!in_face(C, f, p, AMB_TOL * cond, amb)) ok = 0;
+        if (!(t > 0.0 && t < 1.0)) {        /* the plane does not separate y from the image */
+            ok = 0;
+            double gap = (t <= 0.0 ? -t : t - 1.0) * norm(d);   /* distance to the boundary case */
+            if (gap > AMB_TOL * cond) rfail = 1; else marg = 1;
+        }
+        int a = 0;
+        int in = in_face(C, f, p, AMB_TOL * cond, &a);
+        if (!in) ok = 0;
+        if (a) marg = 1; else if (!in) rfail = 1;
         y = p;
     }
     for (int j = 1; j <= k; ++j) {          /* both neighbours strictly on the same side of each plane */
         int f = seq[j - 1];
         double s1 = sdist(C, pts[j - 1], f), s2 = sdist(C, pts[j + 1], f);
-        if (!(s1 * s2 > 0.0)) ok = 0;
-        if (fabs(s1) < AMB_TOL || fabs(s2) < AMB_TOL) *amb = 1;
+        int near = fabs(s1) < AMB_TOL || fabs(s2) < AMB_TOL;
+        if (!(s1 * s2 > 0.0)) {
+            ok = 0;
+            if (!near) rfail = 1;
+        }
+        if (near) marg = 1;
     }
-    if (!ok) return 0;
-    for (int j = 0; j <= k; ++j) {          /* every real segment unblocked */
+    for (int j = 0; j <= k && !rfail; ++j) {   /* every real segment unblocked */
         int i0 = j == 0 ? src_face : seq[j - 1];
         int i1 = j == k ? dst_face : seq[j];
-        if (blocked_decision(C, pts[j], pts[j + 1], i0, i1, amb)) return 0;
+        int a = 0;
+        int b = blocked_decision(C, pts[j], pts[j + 1], i0, i1, &a);
+        if (b) ok = 0;
+        if (a) marg = 1; else if (b) rfail = 1;
     }
-    return 1;
+    if (marg && !rfail) *amb = 1;
+    return ok;
 }
 
 /* Sequence enumeration: id f for (f); id F + f1*F + f2 for (f1, f2). Consecutive faces must not
@@ -423,65 +442,119 @@ static int seq_allowed(const or_ctx* C, const int* seq, int k, int mode)
 /* --------------------------------------------------------------------------------------------
  * Path sets
  * ------------------------------------------------------------------------------------------ */
-/* Tx leg: valid reflected sequences (ids ascending) and per-element direct visibility. */
+/* Tx leg: valid reflected sequences (ids ascending) and per-element direct visibility.
+   Per-decision ambiguity (each output may be NULL): vis_amb[m] for the element's direct ray,
+   amb_ids / *n_amb (capacity amb_cap) the sequences whose validity is ambiguous, *n_dec the number
+   of decisions taken (elements plus allowed sequences). */
 int or_tx_leg(const or_ctx* C, int64_t* seq_out, int64_t cap, int64_t* n_seq, uint8_t* vis_out,
-              int32_t* amb_out)
+              int32_t* amb_out, uint8_t* vis_amb, int64_t* amb_ids, int64_t amb_cap, int64_t* n_amb,
+              int64_t* n_dec)
 {
     int amb = 0;
-    int64_t n = 0;
+    int64_t n = 0, na = 0, nd = 0;
     int F = C->F, hf = C->P.host_face;
-    for (int m = 0; m < C->P.M; ++m)
-        vis_out[m] = !blocked_decision(C, C->tx, C->e[m], -1, hf, &amb);
+    for (int m = 0; m < C->P.M; ++m) {
+        int a = 0;
+        vis_out[m] = !blocked_decision(C, C->tx, C->e[m], -1, hf, &a);
+        if (vis_amb) vis_amb[m] = (uint8_t)(a != 0);
+        amb |= a;
+        ++nd;
+    }
     int64_t n_ids = C->P.max_order_tx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_tx >= 1 ? F : 0);
     for (int64_t id = 0; id < n_ids; ++id) {
         int seq[2];
         int k = decode_seq(C, id, seq);
         if (!seq_allowed(C, seq, k, 0)) continue;
         v3 pts[4];
-        if (validate_seq(C, C->tx, -1, C->c, hf, seq, k, &amb, pts)) {
+        int a = 0;
+        ++nd;
+        if (validate_seq(C, C->tx, -1, C->c, hf, seq, k, &a, pts)) {
             if (n < cap) seq_out[n] = id;
             ++n;
         }
+        if (a) {
+            if (amb_ids && na < amb_cap) amb_ids[na] = id;
+            ++na;
+        }
+        amb |= a;
     }
     *n_seq = n;
     *amb_out = amb;
+    if (n_amb) *n_amb = na;
+    if (n_dec) *n_dec = nd;
     return 0;
 }
 
 /* Per receiver: valid Rx-leg sequences (from the RIS centre), environment sequences (Tx -> Rx),
-   LOS visibility, per-element direct visibility bits and an ambiguity flag. */
+   LOS visibility, per-element direct visibility bits and an ambiguity flag (any decision of this
+   receiver ambiguous). Per-decision ambiguity (each output may be NULL): los_amb[i]; vis_amb bits
+   [n_rx][W] like vis_bits; amb_out_ids [n_rx][amb_cap] the Rx-leg (id) and environment (id | 2^62)
+   sequences whose validity is ambiguous, n_amb[i] their number; n_dec[i] the decisions taken for
+   the receiver (LOS, M elements, every allowed Rx-leg and environment sequence). */
 int or_rx_paths(const or_ctx* C, const float* rx_xyz, int64_t n_rx, int64_t* seq_out, int32_t cap,
                 int32_t* n_seq, int64_t* env_out, int32_t env_cap, int32_t* n_env, uint8_t* los,
-                uint32_t* vis_bits, int32_t* amb_out)
+                uint32_t* vis_bits, int32_t* amb_out, uint8_t* los_amb, uint32_t* vis_amb,
+                int64_t* amb_out_ids, int32_t amb_cap, int32_t* n_amb, int64_t* n_dec)
 {
     int F = C->F, hf = C->P.host_face, M = C->P.M;
     int W = (M + 31) / 32;
     int64_t n_ids = C->P.max_order_rx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_rx >= 1 ? F : 0);
+    const int64_t env_tag = (int64_t)1 << 62;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n_rx; ++i) {
         v3 r = vf(rx_xyz + 3 * i);
-        int amb = 0;
-        los[i] = !blocked_decision(C, C->tx, r, -1, -1, &amb);
-        for (int w = 0; w < W; ++w) vis_bits[i * W + w] = 0;
-        for (int m = 0; m < M; ++m)
-            if (!blocked_decision(C, C->e[m], r, hf, -1, &amb)) vis_bits[i * W + m / 32] |= 1u << (m % 32);
+        int amb = 0, a = 0, na = 0;
+        int64_t nd = 1 + M;
+        los[i] = !blocked_decision(C, C->tx, r, -1, -1, &a);
+        if (los_amb) los_amb[i] = (uint8_t)(a != 0);
+        amb |= a;
+        for (int w = 0; w < W; ++w) {
+            vis_bits[i * W + w] = 0;
+            if (vis_amb) vis_amb[i * W + w] = 0;
+        }
+        for (int m = 0; m < M; ++m) {
+            a = 0;
+            if (!blocked_decision(C, C->e[m], r, hf, -1, &a)) vis_bits[i * W + m / 32] |= 1u << (m % 32);
+            if (a && vis_amb) vis_amb[i * W + m / 32] |= 1u << (m % 32);
+            amb |= a;
+        }
         int n = 0, ne = 0;
         for (int64_t id = 0; id < n_ids; ++id) {
             int seq[2];
             int k = decode_seq(C, id, seq);
             v3 pts[4];
-            if (seq_allowed(C, seq, k, 1) && validate_seq(C, C->c, hf, r, -1, seq, k, &amb, pts)) {
-                if (n < cap) seq_out[i * cap + n] = id;
-                ++n;
+            if (seq_allowed(C, seq, k, 1)) {
+                a = 0;
+                ++nd;
+                if (validate_seq(C, C->c, hf, r, -1, seq, k, &a, pts)) {
+                    if (n < cap) seq_out[i * cap + n] = id;
+                    ++n;
+                }
+                if (a) {
+                    if (amb_out_ids && na < amb_cap) amb_out_ids[i * amb_cap + na] = id;
+                    ++na;
+                }
+                amb |= a;
             }
-            if (C->P.env_paths && seq_allowed(C, seq, k, 2) && validate_seq(C, C->tx, -1, r, -1, seq, k, &amb, pts)) {
-                if (ne < env_cap) env_out[i * env_cap + ne] = id;
-                ++ne;
+            if (C->P.env_paths && seq_allowed(C, seq, k, 2)) {
+                a = 0;
+                ++nd;
+                if (validate_seq(C, C->tx, -1, r, -1, seq, k, &a, pts)) {
+                    if (ne < env_cap) env_out[i * env_cap + ne] = id;
+                    ++ne;
+                }
+                if (a) {
+                    if (amb_out_ids && na < amb_cap) amb_out_ids[i * amb_cap + na] = id | env_tag;
+                    ++na;
+                }
+                amb |= a;
             }
         }
         n_seq[i] = n;
         n_env[i] = ne;
         amb_out[i] = amb;
+        if (n_amb) n_amb[i] = na;
+        if (n_dec) n_dec[i] = nd;
     }
     return 0;
 }
@@ -562,7 +635,7 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
     uint8_t* tx_vis = (uint8_t*)malloc(M > 0 ? M : 1);
     int64_t n_tx = 0;
     int32_t tx_amb = 0;
-    or_tx_leg(C, tx_ids, cap, &n_tx, tx_vis, &tx_amb);
+    or_tx_leg(C, tx_ids, cap, &n_tx, tx_vis, &tx_amb, NULL, NULL, 0, NULL, NULL);
     if (n_tx > cap) n_tx = cap;
     int64_t n_ids = C->P.max_order_rx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_rx >= 1 ? F : 0);
     (void)max_paths;

@@ -409,6 +409,31 @@ def paper_anechoic(grid_step: float = 0.01) -> Workload:
                     np.ones((1, 127), np.complex64) * 1.25, 0, 0, False)
 
 
+def plate_corridor(n_side: int = 20, grid: int = 8, spacing: float = 0.25, half: float = 60.0) -> Workload:
+    """37-element hex RIS (lambda/2, 28 GHz) at the origin facing +y between two stacks of ``n_side``
+    large parallel plates (planes x = +-(0.5 + i*spacing), eps_r 3): every receiver has about
+    2 n_side^2 + 2 n_side geometric order-2 candidates on each receiver leg (one per plate pair on
+    opposite sides), most of them occluded by the inner plates. Tx (0.2, 3, 0.4) isotropic;
+    grid x grid receivers over [-0.4, 0.4]^2 in x and z at y = 2; order <= 2 on both legs."""
+    rng = SplitMix64(SEED_BASE + 6)
+    f = 28e9
+    lam = C0 / f
+    mb = _MeshBuilder()
+    for i in range(n_side):
+        x = 0.5 + i * spacing
+        mb.quad((x, -half, -half), (x, half, -half), (x, half, half), (x, -half, half), 0)
+        mb.quad((-x, -half, -half), (-x, -half, half), (-x, half, half), (-x, half, -half), 0)
+    scene = mb.scene([(3.0, 0.0)])
+    ris = RIS(hex_layout(3, lam / 2), np.zeros(3, np.float32), np.array([0, 0, 1], np.float32),
+              np.array([1, 0, 0], np.float32), lam / 2, lam / 2, 0.0, -1)
+    tx = Antenna(np.array([0.2, 3.0, 0.4], np.float32), identity_orient(), 1.0, 1.0, PATTERN_ISO)
+    rx = Antenna(np.zeros(3, np.float32), identity_orient(), 1.0, 1.0, PATTERN_ISO)
+    g = linspace_grid(-0.4, 0.4, grid, -0.4, 0.4, grid, 2.0, jitter=True)
+    rx_xyz = np.stack([g[:, 0], g[:, 2], g[:, 1]], axis=1).astype(np.float32)
+    return Workload(f"plate_corridor_{2 * n_side}faces_{grid}x{grid}", f, scene, ris, tx, rx, rx_xyz,
+                    phase_configs(rng, 1, len(ris.elem_uv)), 2, 2, True)
+
+
 WORKLOADS = {
     "free_space": free_space,
     "room": room,

@@ -67,6 +67,16 @@ def test_grad_phases_against_oracle(prec):
     assert np.all(np.abs(Jg - J_ref) <= 1e-4 * np.abs(J_ref) + 1e-3)
     rel = np.linalg.norm(gg - g_ref, axis=1) / np.linalg.norm(g_ref, axis=1)
     assert rel.max() <= GRAD_TOL[prec], rel
+    # element by element, against each element's first-order error scale: a rounding error of about
+    # u S_r in E_r (S_r the incoherent sum of the receiver's terms) moves w = conj(E)/|E|^2 by about
+    # u S_r/|E_r|^2, so |dg_bm| <~ c u sum_r 2 |A_rm Gamma_bm| S_r / |E_r|^2 (>= |g_bm|)
+    G = amp[None, :].astype(np.float64) * np.exp(1j * ph.astype(np.float64))
+    E = f["E0"][None, :] + G @ f["A"].T
+    S_r = np.abs(f["E0"])[None, :] + np.abs(G) @ np.abs(f["A"]).T
+    scale = 2 * np.abs(G) * ((S_r / np.abs(E) ** 2) @ np.abs(f["A"]))
+    elem = np.abs(gg - g_ref) / scale
+    print(f"precision {prec}: gradient 2-norm error {rel.max():.2e}, element-wise {elem.max():.2e}")
+    assert elem.max() <= GRAD_TOL[prec], elem.max()
 
 
 @pytest.mark.gpu

@@ -547,3 +547,148 @@ def test_shell_faces_never_block_inside_the_scene_box():
         n_blocked += r_full[0]
         assert r_full[0] == r_in[0], (a, b)
     assert n_checked > 150 and 0 < n_blocked < n_checked
+
+
+# ------------------------------------------------------------------------------------------------
+# Directional antennas on reflected legs: pattern angles come from the real (un-mirrored) segments
+# ------------------------------------------------------------------------------------------------
+def _tilted_plane_scene(normal, height, half=40.0, eps=5.3):
+    """One large planar quad through (0, 0, height) with unit normal `normal` (a tilted ceiling)."""
+    n = np.asarray(normal, np.float64)
+    n /= np.linalg.norm(n)
+    a = np.cross(n, [1.0, 0.0, 0.0])
+    a /= np.linalg.norm(a)
+    b = np.cross(n, a)
+    c = np.array([0.0, 0.0, height])
+    corners = [c - half * a - half * b, c + half * a - half * b, c + half * a + half * b, c - half * a + half * b]
+    mb = S._MeshBuilder()
+    mb.quad(*[tuple(p) for p in corners], 0)
+    return mb.scene([(eps, 0.0)])
+
+
+def _tilted_ceiling_case():
+    w = _free(tx=(0.4, -1.5, 1.0), tx_pat=S.PATTERN_COS_POW, tx_gain=10.0, rx_pat=S.PATTERN_MONOPOLE_QW,
+              tx_orient=S.orient_towards((0.4, -1.5, 1.0), (0.4, 1.0, 1.25)),
+              rx_orient=S.orient_towards((0.0, 0.0, 0.0), (0.3, 0.4, 1.0)))
+    w.scene = _tilted_plane_scene((0.15, -0.25, -1.0), 2.4)
+    w.max_order_tx = w.max_order_rx = 1
+    w.env_paths = True
+    return w
+
+
+def _tilted_ceiling_expected(w, R, wrong=None):
+    """Closed form of the tilted-ceiling case built from explicit reflection points: the channel row
+    A[m] (four leg pairings per element) and E0 (LOS plus the ceiling path), with the Tx pattern,
+    both element patterns and the Rx pattern evaluated on the real segment next to each antenna or
+    element. Fresnel TE in its Snell form per bounce (Sec. II-B; Eqs. 4, 7, 8).
+    `wrong` names one angle to take from a plausible misreading instead, to show the pin detects it:
+    "ft" / "fout" - the departure direction at the Tx / at the element taken on the straight line from
+    the source's image to the destination; "fin" / "fr" - the arrival direction at the element / at
+    the Rx taken on the straight line between the leg's two ends, as if there were no bounce."""
+    V = w.scene.verts.astype(np.float64)
+    tri = V[w.scene.tris[0]]
+    nw = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+    nw /= np.linalg.norm(nw)
+    dw = nw @ tri[0]
+    mirror = lambda p: p - 2 * (p @ nw - dw) * nw
+    hit = lambda a, b: a + (dw - a @ nw) / ((b - a) @ nw) * (b - a)      # line a->b meets the plane
+    unit = lambda v: v / np.linalg.norm(v)
+    lam = S.C0 / w.freq_hz
+    k = 2 * math.pi / lam
+    n2 = math.sqrt(float(np.float32(5.3)))
+
+    def fres(cos_i):
+        sin_i = math.sqrt(max(0.0, 1 - cos_i ** 2))
+        cos_t = math.sqrt(1 - (sin_i / n2) ** 2)
+        return (cos_i - n2 * cos_t) / (cos_i + n2 * cos_t)
+
+    def leg(src, dst, reflected, wrong_dep=False, wrong_back=False):
+        """(length, unit direction leaving src, unit direction from dst back along the last segment,
+        Fresnel factor)"""
+        if not reflected:
+            return np.linalg.norm(dst - src), unit(dst - src), unit(src - dst), 1.0
+        img = mirror(src)
+        P = hit(img, dst)
+        L = np.linalg.norm(P - src) + np.linalg.norm(dst - P)
+        f = fres(abs(unit(P - src) @ nw))
+        dep = unit(dst - img) if wrong_dep else unit(P - src)
+        back = unit(src - dst) if wrong_back else unit(P - dst)
+        return L, dep, back, f
+
+    def monopole(c):
+        return (math.cos(math.pi / 2 * c) / math.sqrt(1 - c * c)) ** 2
+
+    T = w.tx.pos.astype(np.float64)
+    zt = w.tx.orient[2].astype(np.float64)
+    zt /= np.linalg.norm(zt)
+    zr = w.rx.orient[2].astype(np.float64)
+    zr /= np.linalg.norm(zr)
+    Gt = float(np.float32(w.tx.gain_lin))
+    Ft = lambda d: max(d @ zt, 0.0) ** (Gt / 2 - 1)
+    Fr = lambda d: monopole(d @ zr)
+    nr = np.array([0.0, 0.0, 1.0])                      # RIS normal t1 x t2
+    d = float(np.float32(w.ris.dy))
+    G = 4 * math.pi * d * d / lam ** 2
+    e = O.Oracle(w).element_positions()
+    A = np.zeros(len(e), complex)
+    for m in range(len(e)):
+        for tref in (False, True):
+            Lt, dep_t, back_t, ft = leg(T, e[m], tref, wrong == "ft", wrong == "fin")
+            for rref in (False, True):
+                Lr, dep_r, back_r, fr = leg(e[m], R, rref, wrong == "fout", wrong == "fr")
+                amp = math.sqrt(2 * ETA0 * Gt * Ft(dep_t)) \
+                    * math.sqrt(G * max(back_t @ nr, 0) * max(dep_r @ nr, 0) * d * d / (4 * math.pi)) / Lt \
+                    * math.sqrt(Fr(back_r)) * lam / (4 * math.pi * Lr)
+                A[m] += amp * ft * fr * np.exp(-1j * k * (Lt + Lr))
+    E0 = 0j
+    for ref in (False, True):
+        L, dep, back, f = leg(T, R, ref, wrong == "ft", wrong == "fr")
+        E0 += math.sqrt(2 * ETA0 * Gt * Ft(dep)) * math.sqrt(Fr(back)) * lam / (4 * math.pi * L) * f \
+            * np.exp(-1j * k * L)
+    return A, E0
+
+
+def test_reflected_legs_directional_patterns_tilted_ceiling():
+    """Horn Tx (cos^(Gt/2-1), Sec. III-B) and a tilted quarter-wave monopole Rx under one large tilted
+    ceiling: every element sees the Tx directly and through the ceiling and reaches the Rx directly and
+    through it. The oracle's channel row and E0 equal the closed form whose four pattern factors (Ft,
+    F_in, F_out, Fr) are evaluated on the explicit, un-mirrored segments (reading 7). Taking any one of
+    those angles from a misreading (the image line at a departure, the end-to-end line at an arrival)
+    changes the closed form far beyond the tolerance, so each factor is pinned."""
+    w = _tilted_ceiling_case()
+    o = O.Oracle(w)
+    for R in ([0.6, 0.8, 1.2], [-0.9, 0.3, 0.7], [0.2, -0.6, 1.6]):
+        R = np.asarray(R, np.float32).astype(np.float64)
+        f = o.field(R.astype(np.float32)[None])
+        assert not f["amb"][0]
+        A_exp, E0_exp = _tilted_ceiling_expected(w, R)
+        assert np.max(np.abs(f["A"][0] - A_exp)) < 1e-11 * np.max(np.abs(A_exp))
+        assert abs(f["E0"][0] - E0_exp) < 1e-11 * abs(E0_exp)
+        for wrong in ("ft", "fin", "fout", "fr"):
+            A_bad, E0_bad = _tilted_ceiling_expected(w, R, wrong)
+            dA = np.max(np.abs(A_bad - A_exp)) / np.max(np.abs(A_exp))
+            assert dA > 1e-3, (wrong, dA)
+
+
+def test_ambiguity_only_without_a_robust_failure():
+    """A validity decision is ambiguous only when some condition sits within the tolerance band of
+    flipping and no condition fails robustly (Sec. II-B conditions: reflection point in its face,
+    neighbours on the same side, segments unblocked)."""
+    mb = S._MeshBuilder()
+    mb.quad((0, -10, 0), (0, -10, 3), (0, 10, 3), (0, 10, 0), 0)          # wall x = 0, face 0
+    mb.quad((10, 1, 0), (11, 1, 0), (11, 1, 3), (10, 1, 3), 0)            # small plate y = 1, face 1
+    mb.quad((-5, 0, -2), (5, 0, -2), (5, 2, -2), (-5, 2, -2), 0)          # floor patch z = -2, y in [0, 2]
+    w = _free()
+    w.scene = mb.scene([(5.3, 0.0)])
+    o = O.Oracle(w)
+    # source on the wall, sequence (plate, wall): the second bounce lies on the source's own plane
+    # (a boundary case of the same-side test), but the first reflection point is 10 m outside the
+    # plate, so the sequence is rejected robustly
+    ok, amb, _ = o.validate((0, 3, 1.5), 0, (5, 5, 1.2), -1, o.seq_id(1, 0))
+    assert not ok and not amb
+    # a reflection point exactly on the edge y = 0 of the floor patch: marginal, nothing fails robustly
+    ok, amb, pts = o.validate((1, 0.5, 1), -1, (1, -0.5, 1), -1, 2)
+    assert amb and abs(pts[1][1]) < 1e-12
+    # well inside: robust
+    ok, amb, _ = o.validate((1, 1.5, 1), -1, (1, 0.5, 1), -1, 2)
+    assert ok and not amb

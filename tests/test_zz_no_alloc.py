@@ -62,3 +62,21 @@ def test_rejects_scene_beyond_static_scratch():
     with pytest.raises(R.RisrtError) as e:
         ctx.find_paths_noalloc(scene, w.tx.pos, -1, w.ris.center, w.ris.host_face, 2)
     assert e.value.code == 6 and "static scratch" in str(e.value)
+
+
+def test_trace_after_noalloc_retries_with_wide_slab():
+    """Kernel attributes are shared by every caller in the process: a path search without allocation,
+    then a trace whose receivers each have more geometric candidates than its first slab holds (two
+    stacks of parallel plates), which retries with a wider slab and sorts it with more shared memory.
+    The path search still matches, and the trace's path sets match the oracle."""
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    from tests.helpers import oracle_parity, run_gpu
+    w = S.plate_corridor()
+    ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
+    scene, ris, rx = R.upload_workload(ctx, w)
+    ids = ctx.find_paths_noalloc(scene, w.tx.pos, -1, w.ris.center, w.ris.host_face, w.max_order_tx)
+    g = run_gpu(w)
+    assert g["paths"]["stats"].n_candidates > 512 * w.n_rx
+    assert np.array_equal(ids, np.sort(g["paths"]["tx_seqs"]))
+    oracle_parity(w, g)
