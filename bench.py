@@ -43,6 +43,13 @@ def _peaks():
 # 2 sub + 3 FMA for L^2, rsqrt, L, cos, sqrt, 2 mul amplitude, 3 FMA + add + div for dL, FMA + round
 # + sub for the phase, sincos (2), complex scale (2 mul), complex c_m product (4) and accumulate (4).
 EVAL_OPS_PER_UNIT = 32
+# Per field unit, counted from the formula (not from the binary): FP32 lane operations and
+# special-function (MUFU) operations of an order-0 term, and what each bounce adds. MUFU: reciprocal
+# square root of L^2, square root of cos(theta_out), reciprocal of (L + D0), sine and cosine of the
+# phase; per bounce a square root and a reciprocal (Fresnel). FP32 per bounce: incidence cosine
+# (3 FMA, 1 mul), eps - sin^2 (2), a - s, a + s, the quotient (1 mul), the amplitude product (1 mul).
+EVAL_FP32_PER_UNIT, EVAL_FP32_PER_BOUNCE = 14, 9
+EVAL_MUFU_PER_UNIT, EVAL_MUFU_PER_BOUNCE = 5, 2
 # One image-method candidate test (Rx x face sequence): same-side test (3 FMA, sub, 2 compares),
 # and for the ~half that pass it the reflection point (sub, div, 3 sub, 3 FMA) and the in-face test
 # of a two-triangle face (6 x (3 FMA + sub) + 2 min + 2 compares): counted as 8 + 0.5 * 40.
@@ -86,6 +93,112 @@ def measured_traffic(kernel):
     if kernel_source_hash(t["sources"]) != t["sha256_16"]:
         return None, "kernel sources changed since the ncu capture"
     return t["bytes_per_step"], t["profile"]
+
+
+def measure_peaks(ctx, R):
+    """Issue rates of the FP32 FMA, special-function and FP64 FMA pipes (lane operations per second),
+    from the library's microbenchmarks (best of three launches, full occupancy)."""
+    kinds = {"ffma": R.MB_FFMA, "mufu_sin": R.MB_MUFU_SIN, "mufu_cos": R.MB_MUFU_COS, "mufu_rsq": R.MB_MUFU_RSQ,
+             "mufu_rcp": R.MB_MUFU_RCP, "mufu_sqrt": R.MB_MUFU_SQRT, "mufu_ex2": R.MB_MUFU_EX2, "dfma": R.MB_DFMA}
+    out = {}
+    for name, k in kinds.items():
+        ops, ms = ctx.microbench(k, 2048 if k != R.MB_DFMA else 256)
+        out[name] = ops
+    out["mufu"] = min(out[k] for k in out if k.startswith("mufu"))
+    return out
+
+
+def unit_bounce_counts(ps):
+    """Field units of a path set split by the bounce count of their Rx-leg path: (order 0, 1, 2)."""
+    ex = ps.export()
+    st = ex["stats"]
+    F, M = st.n_faces, st.M
+    n1 = sum(int(np.sum(s < F)) for s in ex["seqs"])
+    n2 = sum(len(s) for s in ex["seqs"]) - n1
+    return st.n_rx * M, n1 * M, n2 * M
+
+
+def bench_free_space(ctx, R, dev, steps=20):
+    """The free-space case (37-element hexagonal RIS, 32x32 receivers, LOS + order 0, 9 configurations):
+    trace + eval per step as device time, the launch-latency-bound end of the workload range."""
+    import torch
+    w = S.free_space()
+    scene, ris, rx = R.upload_workload(ctx, w)
+    g = torch.from_numpy(w.gammas).to(dev)
+    E = torch.empty((g.shape[0], w.n_rx), dtype=torch.complex64, device=dev)
+    P = torch.empty((g.shape[0], w.n_rx), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ps = None
+    for _ in range(3):
+        ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w), reuse=ps)
+        ctx.eval_field(ps, g, E, P)
+    torch.cuda.synchronize()
+    ts, te = [], []
+    for _ in range(steps):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w), reuse=ps)
+        b.record(stream)
+        ctx.eval_field(ps, g, E, P)
+        c.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(c))
+        te.append(b.elapsed_time(c))
+    units = ps.stats().units * g.shape[0]
+    ms = float(np.median(ts))
+    out = {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "n_cfg": int(g.shape[0]),
+           "units_per_step": units, "step_us": ms * 1e3, "eval_us": float(np.median(te)) * 1e3,
+           "evals_per_s": units / (ms / 1e3), "note": "median of %d steps; trace includes its host round trips" % steps}
+    for h in (ps, rx, ris, scene):
+        h.close()
+    return out
+
+
+def bench_plain_fp32(ctx, R, dev, w, ps, gam, E, P, flush, reps=5, oracle_rx=97):
+    """The field evaluation against its plain FP32 baseline (one thread per receiver, absolute FP32
+    phase with sincosf, IEEE square roots and divisions) on the same path set: device time of each and
+    their errors against the FP64 oracle on a deterministic receiver sample."""
+    import torch
+    from oracle import oracle as O
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    ctx.eval_field(ps, gam, E, P)
+    t_eval = timed(lambda: ctx.eval_field(ps, gam, E, P))
+    E_fast = E.cpu().numpy().T.copy()
+    ctx.eval_field_plain(ps, gam, E, P)
+    t_plain = timed(lambda: ctx.eval_field_plain(ps, gam, E, P))
+    E_plain = E.cpu().numpy().T.copy()
+    idx = np.unique(np.linspace(0, w.n_rx - 1, oracle_rx).astype(int))
+    rx = w.rx_xyz[idx]
+    o = O.Oracle(w)
+    fld = o.field(rx)
+    E_ref, _, S_ref = O.Oracle.evaluate(fld, w.gammas)
+    ok = ~fld["amb"][:, None] & (S_ref > 0)
+    strong = ok & (np.abs(E_ref) >= 0.05 * S_ref)
+    Sd = np.where(S_ref > 0, S_ref, 1.0)
+
+    def err(Eg):
+        Eg = Eg[idx]
+        return {"max_field_err_over_S": float((np.abs(Eg - E_ref) / Sd)[ok].max()),
+                "max_phase_err_rad": float(np.abs(np.angle(Eg * np.conj(E_ref)))[strong].max()),
+                "max_power_rel_err": float((np.abs(np.abs(Eg) ** 2 / np.abs(E_ref) ** 2 - 1))[strong].max())}
+
+    units = ps.stats().units * gam.shape[0]
+    return {"eval_ms": t_eval, "plain_fp32_eval_ms": t_plain, "eval_evals_per_s": units / (t_eval / 1e3),
+            "plain_fp32_evals_per_s": units / (t_plain / 1e3), "eval_speedup": t_plain / t_eval,
+            "error_eval": err(E_fast), "error_plain_fp32": err(E_plain), "oracle_receivers": int(len(idx))}
 
 
 def bench_gradient(ctx, R, dev, steps=200, reps=5):
@@ -554,6 +667,36 @@ def main():
             roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
                     "traffic": None}
 
+    # measured pipe peaks; the field kernel against the special-function and FP32 pipes (its op counts
+    # per unit from the formula, split by the bounce count of each unit's path)
+    mpeaks = measure_peaks(ctx, R)
+    if roof is not None and dom == "k_validate":
+        secs = ms_step / 1e3
+        roof["node_visits_per_s"] = st.node_visits / secs
+        roof["segments_per_s"] = st.n_segments / secs
+        roof["candidates_per_s"] = st.n_candidates / secs
+    u0, u1, u2 = unit_bounce_counts(ps)
+    roof_field = None
+    if "k_eval" in prof:
+        ev_ms = prof["k_eval"][0] / n_prof_steps
+        mufu_ops = n_cfg * (u0 * EVAL_MUFU_PER_UNIT + u1 * (EVAL_MUFU_PER_UNIT + EVAL_MUFU_PER_BOUNCE)
+                            + u2 * (EVAL_MUFU_PER_UNIT + 2 * EVAL_MUFU_PER_BOUNCE))
+        fp32_ops = n_cfg * (u0 * EVAL_FP32_PER_UNIT + u1 * (EVAL_FP32_PER_UNIT + EVAL_FP32_PER_BOUNCE)
+                            + u2 * (EVAL_FP32_PER_UNIT + 2 * EVAL_FP32_PER_BOUNCE))
+        units_eval = (u0 + u1 + u2) * n_cfg
+        t_mufu = mufu_ops / mpeaks["mufu"]
+        t_fp32 = fp32_ops / mpeaks["ffma"]
+        bound = "mufu" if t_mufu >= t_fp32 else "fp32"
+        roof_units = units_eval / max(t_mufu, t_fp32)
+        achieved = units_eval / (ev_ms / 1e3)
+        roof_field = {"kernel": "k_eval", "bound": "alu", "pipe": bound, "achieved": achieved,
+                      "peak": roof_units, "unit": "units/s", "frac": achieved / roof_units, "traffic": None,
+                      "ms_per_step": ev_ms, "units": units_eval, "units_by_bounces": [u0, u1, u2],
+                      "mufu_ops_per_step": mufu_ops, "fp32_ops_per_step": fp32_ops,
+                      "mufu_frac": (mufu_ops / (ev_ms / 1e3)) / mpeaks["mufu"],
+                      "fp32_frac": (fp32_ops / (ev_ms / 1e3)) / mpeaks["ffma"],
+                      "peak_note": "min over the measured MUFU and FP32 FMA issue rates of peak / ops per unit"}
+
     # end to end through the C ABI with host buffers (scene, RIS, receivers, configs up; P down)
     e2e = None
     if not args.no_e2e:
@@ -590,6 +733,17 @@ def main():
         e2e = {"value": u_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    plain = None
+    vs_baseline = None
+    free = None
+    if rank == 0:
+        plain = bench_plain_fp32(ctx, R, dev, w, ps, gam, E, P, flush)
+        # the same step with the plain FP32 field evaluation in place of eval_field
+        plain_step_ms = ms_per_step - plain["eval_ms"] + plain["plain_fp32_eval_ms"]
+        plain["step_ms_with_plain_eval"] = plain_step_ms
+        plain["step_evals_per_s_with_plain_eval"] = units / (plain_step_ms / 1e3)
+        vs_baseline = plain_step_ms / ms_per_step
+        free = bench_free_space(ctx, R, dev)
     sweep = None
     if rank == 0 and not args.no_sweep:
         sweep = bench_sweep(ctx, R, dev)
@@ -609,7 +763,11 @@ def main():
         clk = clocks_summary(clk_path, local)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": vs_baseline,
+                "vs_baseline_note": "against the same step with the plain FP32 field evaluation (one thread per "
+                                    "receiver, absolute FP32 phase, sincosf) measured in this run; the paper "
+                                    "prints no number",
+                "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "faces": st.n_faces,
                            "triangles": int(len(w.scene.tris)), "order_tx": w.max_order_tx,
                            "order_rx": w.max_order_rx, "env_paths": bool(w.env_paths), "n_cfg": n_cfg,
@@ -618,7 +776,9 @@ def main():
                            "candidates": st.n_candidates, "segments": st.n_segments,
                            "bvh_node_visits": st.node_visits, "tri_tests": st.tri_tests,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+                "roofline_field": roof_field, "measured_peaks": mpeaks, "cpu_baseline": cpu,
+                "vs_plain_fp32": plain, "free_space": free,
                 "stages": stages, "sweep": sweep, "gradient": grad, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:

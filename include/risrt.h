@@ -208,6 +208,14 @@ int risrt_pathset_export(const risrt_pathset* ps, int32_t* rx_count_host, int64_
 int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg,
                      float* E_out, float* P_out);
 
+/* Plain FP32 baseline of risrt_eval_field (same arguments, same outputs): one thread per receiver
+ * walks every (element, Rx-leg path) term with the phase computed in FP32 from the absolute unfolded
+ * length (sincosf of 2 pi L / lambda, with its full range reduction), IEEE square roots and
+ * divisions. It exists to measure what the FP64 per-path phase reference, the element-major warp
+ * layout and the single-instruction approximations of risrt_eval_field buy, in time and accuracy. */
+int risrt_eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg,
+                           float* E_out, float* P_out);
+
 /* Dense channel matrix: A [n_rx][M] complex64 with A[r][m] = c_m sum_q b_mq(r), so that
  * E = E0 + A . Gamma (Eq. 9 is linear in Gamma), and E0 [n_rx] complex64 (may be NULL). */
 int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out);
@@ -336,6 +344,25 @@ int risrt_profile_query(risrt_ctx* ctx, const char* name, double* total_ms, int6
 int risrt_profile_names(risrt_ctx* ctx, char* buf, size_t cap, size_t* needed);
 
 int risrt_profile_reset(risrt_ctx* ctx);
+
+/* Issue-rate microbenchmarks of the pipes the field kernels use (the measured denominators of their
+ * roofline). kind: RISRT_MB_FFMA (FP32 fused multiply-add), RISRT_MB_MUFU_* (the special-function
+ * unit's single-instruction sine, cosine, reciprocal square root, reciprocal, square root and base-2
+ * exponential), RISRT_MB_DFMA (FP64 fused multiply-add). Runs independent chains on every SM at full
+ * occupancy for `iters` iterations per chain; *ops_per_s receives the lane operations per second of
+ * the best of three timed launches (CUDA events on the context's stream), *ms (may be NULL) its
+ * duration. Synchronises the stream. */
+enum {
+    RISRT_MB_FFMA = 0,
+    RISRT_MB_MUFU_SIN = 1,
+    RISRT_MB_MUFU_COS = 2,
+    RISRT_MB_MUFU_RSQ = 3,
+    RISRT_MB_MUFU_RCP = 4,
+    RISRT_MB_MUFU_SQRT = 5,
+    RISRT_MB_MUFU_EX2 = 6,
+    RISRT_MB_DFMA = 7
+};
+int risrt_microbench(risrt_ctx* ctx, int kind, int32_t iters, double* ops_per_s, double* ms);
 
 /* Number of kernels the library has launched in this process (all contexts), for accounting. */
 int risrt_launch_count(int64_t* out);

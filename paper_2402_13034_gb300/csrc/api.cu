@@ -560,6 +560,24 @@ int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma
     return eval_field(ctx, ps, (const float2*)gamma, n_cfg, (float2*)E_out, P_out);
 }
 
+int risrt_eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg, float* E_out,
+                           float* P_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!ps || !gamma || !E_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (n_cfg < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_cfg must be >= 1");
+    if (((uintptr_t)gamma | (uintptr_t)E_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    return eval_field_plain(ctx, ps, (const float2*)gamma, n_cfg, (float2*)E_out, P_out);
+}
+
+int risrt_microbench(risrt_ctx* ctx, int kind, int32_t iters, double* ops_per_s, double* ms)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!ops_per_s || iters < 1 || kind < RISRT_MB_FFMA || kind > RISRT_MB_DFMA)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "bad microbenchmark arguments");
+    return microbench(ctx, kind, iters, ops_per_s, ms);
+}
+
 int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out)
 {
     RISRT_CHECK_CTX(ctx);

@@ -9,6 +9,31 @@ namespace risrt {
 struct cf { float re, im; };
 __device__ __forceinline__ cf cmulf(cf a, cf b) { return cf{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 
+// Single special-function-unit instructions (PTX .approx forms: square root to about 1 ulp,
+// reciprocal to 1 ulp; denormal inputs flush to zero), for the per-element terms whose FP32
+// tolerance is far above a few ulp. sqrt_approx(0) = 0.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Fresnel coefficient of a lossless dielectric (real eps_r >= sin^2, TE or TM) with one square root
+// and one reciprocal: R_TE = (c - s) / (c + s), R_TM = (eps c - s) / (eps c + s), s = sqrt(eps - sin^2).
+__device__ __forceinline__ float fresnel_real_fast(float c, float er, bool tm)
+{
+    const float s = sqrt_approx(fmaxf(er - fmaxf(1.f - c * c, 0.f), 0.f));
+    const float a = tm ? er * c : c;
+    return (a - s) * rcp_approx(a + s);
+}
+
 // principal complex square root in FP32
 __device__ __forceinline__ cf csqrtf_(float x, float y)
 {

@@ -24,7 +24,15 @@ __device__ __forceinline__ float rx_pattern(float c, float gain)
     return 1.f;
 }
 
-// b_mq for one (path record, element) pair; returns false if the term is zero by visibility.
+// Fresnel factor of one bounce at incidence cosine c: one square root and one reciprocal for a
+// lossless dielectric, the complex form otherwise.
+__device__ __forceinline__ cf bounce_factor(float c, float er, float ei, bool tm)
+{
+    if (ei == 0.f && er >= 1.f) return cf{fresnel_real_fast(c, er, tm), 0.f};
+    return fresnel_f(c, er, ei, tm);
+}
+
+// b_mq for one (path record, element) pair.
 template <int PAT>
 __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_lam, float gr, bool tm)
 {
@@ -33,29 +41,56 @@ __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_
     const float iL = rsqrtf(L2);
     const float L = L2 * iL;
     const float cos_out = dz * iL;
-    float amp = sqrtf(fmaxf(cos_out, 0.f)) * iL;
+    float amp = sqrt_approx(fmaxf(cos_out, 0.f)) * iL;
     if (PAT != RISRT_PATTERN_ISO) {
         float cr = -(dx * p.v.x + dy * p.v.y + dz * p.v.z) * iL;
-        amp *= sqrtf(gr * rx_pattern<PAT>(cr, gr));
+        amp *= sqrt_approx(gr * rx_pattern<PAT>(cr, gr));
+    } else {
+        amp *= sqrt_approx(gr);
+    }
+    cf R = cf{amp, 0.f};
+    const int k = __float_as_int(p.a.y);
+    if (k >= 1) {
+        float c1 = fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) * iL;
+        R = cmulf(R, bounce_factor(c1, p.a.z, p.a.w, tm));
+        if (k == 2) {
+            float c2 = fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) * iL;
+            R = cmulf(R, bounce_factor(c2, p.n1.w, p.n2.w, tm));
+        }
+    }
+    const float dL = (e.z - 2.f * (e.x * p.w.x + e.y * p.w.y)) * rcp_approx(L + p.w.w);
+    float x = p.a.x + dL * inv_lam;
+    x -= rintf(x);
+    float sn, cs;
+    __sincosf(6.28318530717958647f * x, &sn, &cs);
+    return cmulf(R, cf{cs, -sn});          // e^{-j 2 pi x}
+}
+
+// The same term as a plain FP32 program: unfolded length L = |w - u_m| from the RIS-frame image,
+// absolute phase 2 pi L / lambda reduced by sincosf itself, IEEE square roots and divisions, Fresnel in
+// its general complex form.
+template <int PAT>
+__device__ __forceinline__ cf rx_leg_term_plain(const PathRec& p, float4 e, float k0, float gr, bool tm)
+{
+    const float dx = p.w.x - e.x, dy = p.w.y - e.y, dz = p.w.z;
+    const float L = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float cos_out = dz / L;
+    float amp = sqrtf(fmaxf(cos_out, 0.f)) / L;
+    if (PAT != RISRT_PATTERN_ISO) {
+        float cr = -(dx * p.v.x + dy * p.v.y + dz * p.v.z) / L;
+        amp *= sqrtf(gr * pattern_f(PAT, gr, cr));
     } else {
         amp *= sqrtf(gr);
     }
     cf R = cf{amp, 0.f};
     const int k = __float_as_int(p.a.y);
     if (k >= 1) {
-        float c1 = fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) * iL;
-        R = cmulf(R, fresnel_f(c1, p.a.z, p.a.w, tm));
-        if (k == 2) {
-            float c2 = fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) * iL;
-            R = cmulf(R, fresnel_f(c2, p.n1.w, p.n2.w, tm));
-        }
+        R = cmulf(R, fresnel_f(fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) / L, p.a.z, p.a.w, tm));
+        if (k == 2) R = cmulf(R, fresnel_f(fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) / L, p.n1.w, p.n2.w, tm));
     }
-    const float dL = (e.z - 2.f * (e.x * p.w.x + e.y * p.w.y)) / (L + p.w.w);
-    float x = p.a.x + dL * inv_lam;
-    x -= rintf(x);
     float sn, cs;
-    __sincosf(6.28318530717958647f * x, &sn, &cs);
-    return cmulf(R, cf{cs, -sn});          // e^{-j 2 pi x}
+    sincosf(k0 * L, &sn, &cs);
+    return cmulf(R, cf{cs, -sn});
 }
 
 constexpr int kEvalWarps = 8;
@@ -194,6 +229,55 @@ k_eval(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const u
     }
 }
 
+// Plain FP32 baseline: one thread per receiver, every (element, path) term in turn.
+template <int PAT, int NC>
+__global__ void __launch_bounds__(128)
+k_eval_plain(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const uint32_t* __restrict__ vis, int W,
+             const float4* __restrict__ elem, const float2* __restrict__ cm, const float2* __restrict__ gamma,
+             int M, int64_t n_rx, int cfg0, int n_cfg, const float2* __restrict__ E0, float2* __restrict__ E,
+             float* __restrict__ P, float k0, float gr, int tm, float inv_2eta0)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_rx) return;
+    const int64_t o = off[r];
+    const int nq = (int)(off[r + 1] - o);
+    cf acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = cf{0.f, 0.f};
+    for (int m = 0; m < M; ++m) {
+        const float4 e = elem[m];
+        const bool direct = (vis[r * W + (m >> 5)] >> (m & 31)) & 1u;
+        cf sum = cf{0.f, 0.f};
+        for (int q = 0; q < nq; ++q) {
+            const PathRec p = rec[o + q];
+            if (__float_as_int(p.a.y) == 0 && !direct) continue;
+            const cf b = rx_leg_term_plain<PAT>(p, e, k0, gr, tm != 0);
+            sum.re += b.re;
+            sum.im += b.im;
+        }
+        const float2 c2 = cm[m];
+        const cf cb = cmulf(sum, cf{c2.x, c2.y});
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (c < n_cfg) {
+                const float2 g = gamma[(int64_t)(cfg0 + c) * M + m];
+                acc[c].re += g.x * cb.re - g.y * cb.im;
+                acc[c].im += g.x * cb.im + g.y * cb.re;
+            }
+        }
+    }
+    const float2 e0 = E0[r];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if (c < n_cfg) {
+            float er = e0.x + acc[c].re, ei = e0.y + acc[c].im;
+            int64_t oi = (int64_t)(cfg0 + c) * n_rx + r;
+            E[oi] = make_float2(er, ei);
+            if (P) P[oi] = (er * er + ei * ei) * inv_2eta0;
+        }
+    }
+}
+
 // A[r][m] = c_m sum_q b_mq: one warp per receiver, lanes own elements, paths broadcast.
 template <int PAT>
 __global__ void __launch_bounds__(32 * kEvalWarps)
@@ -261,6 +345,35 @@ int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int
         }
 #undef RISRT_EVAL_NC
 #undef RISRT_EVAL
+    }
+    return RISRT_OK;
+}
+
+int eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P)
+{
+    const float k0 = (float)(2.0 * kPi * ps->freq / kC0);
+    const float inv_2eta0 = (float)(1.0 / (2.0 * kEta0));
+    const int tm = (ps->flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
+    const unsigned grid = nblk(ps->n_rx, 128);
+    for (int c0 = 0; c0 < n_cfg; c0 += kMaxCfgPerPass) {
+        const int nc = std::min(kMaxCfgPerPass, n_cfg - c0);
+#define RISRT_PLAIN(PAT, NCV)                                                                                 \
+    RISRT_KERNEL(ctx, "k_eval_plain", (k_eval_plain<PAT, NCV><<<grid, 128, 0, ctx->stream>>>(                   \
+                                         ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, gamma, ps->M,   \
+                                         ps->n_rx, c0, nc, ps->E0, E, P, k0, ps->rx_gain, tm, inv_2eta0)))
+#define RISRT_PLAIN_NC(PAT)                  \
+    do {                                     \
+        if (nc == 1) RISRT_PLAIN(PAT, 1);    \
+        else if (nc == 2) RISRT_PLAIN(PAT, 2); \
+        else RISRT_PLAIN(PAT, 4);            \
+    } while (0)
+        switch (ps->rx_pattern) {
+            case RISRT_PATTERN_COS_POW: RISRT_PLAIN_NC(RISRT_PATTERN_COS_POW); break;
+            case RISRT_PATTERN_MONOPOLE_QW: RISRT_PLAIN_NC(RISRT_PATTERN_MONOPOLE_QW); break;
+            default: RISRT_PLAIN_NC(RISRT_PATTERN_ISO); break;
+        }
+#undef RISRT_PLAIN_NC
+#undef RISRT_PLAIN
     }
     return RISRT_OK;
 }

@@ -341,6 +341,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 double freq, int max_order_tx, int max_order_rx, uint32_t flags, risrt_pathset* ps);
 int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
 int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0);
+int eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
+int microbench(risrt_ctx* ctx, int kind, int iters, double* ops_per_s, double* ms);
 size_t grad_workspace_bytes(int n_t, int B, int M, int precision);
 int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes);
 int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,

@@ -23,6 +23,7 @@ PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP16 = 0, 1, 2, 3
 GRAD_KEEP_A = 0x100
 SWEEP_KEEP_A = 0x100
 SWEEP_DEFER_CHECK = 0x200
+MB_FFMA, MB_MUFU_SIN, MB_MUFU_COS, MB_MUFU_RSQ, MB_MUFU_RCP, MB_MUFU_SQRT, MB_MUFU_EX2, MB_DFMA = range(8)
 
 _lock = threading.Lock()
 _lib = None
@@ -44,6 +45,8 @@ _SIGS = {
     "risrt_pathset_stats_get": (C.c_int, [_P, _P]),
     "risrt_pathset_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
+    "risrt_eval_field_plain": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
+    "risrt_microbench": (C.c_int, [_P, C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
     "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_sweep_configs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int, _P, _P, C.c_size_t]),
@@ -299,6 +302,18 @@ class Context:
         n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
         self._check(load().risrt_eval_field(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"), n_cfg,
                                             _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def eval_field_plain(self, ps: PathSet, gamma, E_out, P_out=None):
+        """The plain FP32 baseline of eval_field (same arguments and outputs)."""
+        n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
+        self._check(load().risrt_eval_field_plain(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"), n_cfg,
+                                                  _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def microbench(self, kind: int, iters: int = 4096):
+        """Issue rate of one pipe (MB_* kinds): (lane operations per second, ms of the best launch)."""
+        ops, ms = C.c_double(), C.c_double()
+        self._check(load().risrt_microbench(self._ptr, int(kind), int(iters), C.byref(ops), C.byref(ms)))
+        return ops.value, ms.value
 
     def sweep_workspace(self, n_rx: int, M: int, n_cfg: int, precision: int):
         """A device workspace tensor for sweep_configs (None for FP32)."""

@@ -272,3 +272,37 @@ def test_endpoints_outside_scene_box(monkeypatch, maps):
     st, o, op, fld = oracle_parity(w, g)
     los = np.asarray(op["los"], bool)
     assert los.any() and (~los).any()             # the Tx sees over the walls into part of the room
+
+
+def test_plain_fp32_baseline_error():
+    """The plain FP32 baseline of the field evaluation (absolute FP32 phase 2 pi L / lambda with sincosf)
+    against the oracle on the room. Its phase error per term is bounded by the FP32 rounding of L and of
+    k L (L <= 12 m, k L <= 7.1e3 rad, so a few 1e-4 rad), i.e. a field error of at most about 1e-3 S;
+    the element-major kernel with the FP64 per-path phase reference stays within 5e-5 S."""
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    w = S.room(grid=16)
+    g = run_gpu(w, keep=True)
+    ctx, scene, ris, rx, ps = g["handles"]
+    gam = torch.from_numpy(w.gammas).cuda()
+    E = torch.empty((gam.shape[0], w.n_rx), dtype=torch.complex64, device="cuda")
+    ctx.eval_field_plain(ps, gam, E)
+    torch.cuda.synchronize()
+    Ep = E.cpu().numpy().T
+    _, fld, E_ref, P_ref, S_ref = _oracle_all(w)
+    ok = ~fld["amb"][:, None] & (S_ref > 0)
+    Sd = np.where(S_ref > 0, S_ref, 1.0)
+    err_plain = (np.abs(Ep - E_ref) / Sd)[ok].max()
+    err_fast = (np.abs(g["E"] - E_ref) / Sd)[ok].max()
+    print(f"max |dE|/S: plain FP32 {err_plain:.2e}, eval_field {err_fast:.2e}")
+    assert err_fast <= 5e-5
+    assert err_plain <= 1e-3
+
+
+def test_microbenchmarks_positive():
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
+    rates = {k: ctx.microbench(k, 64)[0] for k in range(8)}
+    assert all(v > 1e9 for v in rates.values()), rates
+    assert rates[R.MB_FFMA] > rates[R.MB_MUFU_SIN]
