@@ -37,6 +37,7 @@ typedef struct risrt_scene risrt_scene;
 typedef struct risrt_ris risrt_ris;
 typedef struct risrt_rxset risrt_rxset;
 typedef struct risrt_pathset risrt_pathset;
+typedef struct risrt_amat risrt_amat;
 
 enum {
     RISRT_OK = 0,
@@ -70,12 +71,15 @@ enum {
 
 /* Create a context on CUDA device `device`, enqueueing work on `stream` (a cudaStream_t; NULL means
  * the legacy default stream). Fails with RISRT_ERR_CUDA if the device cannot be used.
- * Scenes, RIS, receiver sets and path sets take their device memory from a block cache of the
- * context that creates them; destroying them with that context returns the blocks to it (up to
- * 2 GiB stay cached for reuse; an allocation that fails releases the cache and retries). Destroy
- * objects before their context: an object destroyed with another context or NULL frees its memory
- * with cudaFree. */
-int risrt_create(risrt_ctx** out, int device, void* stream);
+ * Scenes, RIS, receiver sets, path sets and resident channel matrices take their device memory from
+ * a block cache of the context that creates them; destroying them with that context returns the
+ * blocks to it (up to 2 GiB stay cached for reuse; an allocation that fails releases the cache and
+ * retries). Destroy objects before their context: an object destroyed with another context or NULL
+ * frees its memory with cudaFree.
+ * hbm_budget_bytes: upper bound on the device bytes the context holds at once (objects in use plus
+ * cached blocks; 0 = no bound). A request that would exceed it first releases the cache, then fails
+ * with RISRT_ERR_OOM, so a host can give each context a share of the GPU (serving admission). */
+int risrt_create(risrt_ctx** out, int device, void* stream, size_t hbm_budget_bytes);
 
 /* Change the stream later calls enqueue on (synchronises the previous stream first, since cached
  * blocks may still be in use by its work). */
@@ -216,9 +220,26 @@ int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma
 int risrt_eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg,
                            float* E_out, float* P_out);
 
-/* Dense channel matrix: A [n_rx][M] complex64 with A[r][m] = c_m sum_q b_mq(r), so that
- * E = E0 + A . Gamma (Eq. 9 is linear in Gamma), and E0 [n_rx] complex64 (may be NULL). */
-int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out);
+/* Dense channel matrix (Eq. 9 is linear in Gamma): A [n_rx][M] complex64 with A[r][m] = c_m sum_q b_mq(r),
+ * so that E = E0 + A . Gamma, and E0 [n_rx] complex64.
+ *  - A_out != NULL: written into caller memory (E0_out may be NULL). If resident_out != NULL,
+ *    *resident_out receives a handle viewing A_out and E0_out (the caller keeps them alive).
+ *  - A_out == NULL: resident_out must not be NULL; the library allocates A and E0 in blocks of this
+ *    context (16 n_rx (M + 1) bytes, counted against its budget), builds them there and returns a
+ *    handle that owns them (E0_out is ignored).
+ * The handle feeds risrt_sweep_configs and risrt_grad_phases; free it with risrt_amat_destroy. */
+int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out, risrt_amat** resident_out);
+
+/* A handle viewing caller memory A [n_rx][M] and E0 [n_rx] (complex64; E0 may be NULL, meaning 0) for
+ * risrt_sweep_configs and risrt_grad_phases; no copy, the caller keeps the memory alive and unchanged
+ * while the handle is used. 1 <= n_rx <= 2^26, 1 <= M <= 65536. */
+int risrt_amat_wrap(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M, risrt_amat** out);
+
+/* Device pointers and sizes of a channel matrix (any output may be NULL). */
+int risrt_amat_data(const risrt_amat* amat, const float** A, const float** E0, int64_t* n_rx, int32_t* M);
+
+/* Free a handle (synchronises the context; owned memory returns to the context's cache). */
+int risrt_amat_destroy(risrt_ctx* ctx, risrt_amat* amat);
 
 /* ------------------------------------------------------------------------------------------------
  * Configuration sweep (Eq. 9 is linear in Gamma; Eq. 10)
@@ -234,17 +255,23 @@ enum {
 /* Bytes of device workspace risrt_sweep_configs needs for these sizes and precision (0 for FP32). */
 int risrt_sweep_workspace_size(int64_t n_rx, int32_t M, int32_t n_cfg, int precision, size_t* bytes);
 
-/* For every receiver r and configuration c:
- *   P[r][c] = |E0[r] + sum_m A[r][m] Gamma[c][m]|^2 / (2 eta0)
- *   A      [n_rx][M] complex64 (risrt_build_A)      E0 [n_rx] complex64 or NULL
- *   gamma  [n_cfg][M] complex64                       P_out [n_rx][n_cfg] float
+/* For every receiver r and configuration c of the channel matrix `amat` (risrt_build_A or
+ * risrt_amat_wrap):
+ *   E[r][c] = E0[r] + sum_m A[r][m] Gamma[c][m],   P[r][c] = |E[r][c]|^2 / (2 eta0)   (Eqs. 9, 10)
+ * Configurations, exactly one of:
+ *   gamma      [n_cfg][M] complex64, or
+ *   gamma_2bit [n_cfg][ceil(M/4)] uint8: 2-bit phase codes q, element m in bits 2 (m % 4) of byte m / 4
+ *              (the bits of a row's last byte beyond M are ignored), Gamma = amp j^q (q = 0..3: amp,
+ *              j amp, -amp, -j amp: phases quantised to 2 bits with one common amplitude). Every
+ *              value is exact in BF16 when amp is.
+ * Outputs (at least one): P_out [n_rx][n_cfg] float, E_out [n_rx][n_cfg] complex64.
  * The tensor-core precisions run the complex product as one real GEMM ([Re A | Im A] against
  * interleaved [Re G, -Im G] / [Im G, Re G] rows) with the |E|^2 epilogue fused; they need a
  * workspace of risrt_sweep_workspace_size bytes (16-byte aligned) and synchronise the stream.
- * 1 <= M <= 65536, 1 <= n_cfg. Errors: RISRT_ERR_INVALID_ARG; RISRT_ERR_TIMEOUT if a pipeline wait
- * in the tensor-core kernel expired (the kernel then stops and the output is incomplete). */
-int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M,
-                        const float* gamma, int32_t n_cfg, int precision, float* P_out, void* workspace,
+ * 1 <= n_cfg <= 2^24. Errors: RISRT_ERR_INVALID_ARG; RISRT_ERR_TIMEOUT if a pipeline wait in the
+ * tensor-core kernel expired (the kernel then stops and the output is incomplete). */
+int risrt_sweep_configs(risrt_ctx* ctx, const risrt_amat* amat, const float* gamma, const uint8_t* gamma_2bit,
+                        float amp, int32_t n_cfg, int precision, float* P_out, float* E_out, void* workspace,
                         size_t workspace_bytes);
 
 /* OR-ed into the precision of risrt_sweep_configs with RISRT_PREC_BF16 or RISRT_PREC_BF16X2
@@ -278,13 +305,13 @@ int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precis
  * changed. Ignored for RISRT_PREC_FP32. */
 #define RISRT_GRAD_KEEP_A 0x100
 
-/* For B phase configurations Gamma_bm = amp_m e^{j phases[b][m]}:
+/* For B phase configurations Gamma_bm = amp_m e^{j phases[b][m]} on the channel matrix `amat`:
  *   J[b]       = sum_{t} log P_b(target[t]),  P = |E0 + A Gamma_b|^2 / (2 eta0)
  *   grad[b][m] = dJ[b]/dphases[b][m] = -2 Im(Gamma_bm sum_t A[target[t]][m] conj(E) / |E|^2)
  * with |E|^2 clamped below at 1e-30 of its maximum over the targets of configuration b.
- *   A [n_rx][M] complex64, E0 [n_rx] complex64 or NULL, target [n_target] int32 rows of A
- *   (NULL: rows 0..n_target-1), phases [B][M] float, amp [M] float or NULL (1), J_out [B] float,
- *   grad_out [B][M] float, workspace of risrt_grad_workspace_size bytes. All device memory.
+ *   target [n_target] int32 rows of A (NULL: rows 0..n_target-1), phases [B][M] float, amp [M] float or
+ *   NULL (1), J_out [B] float, grad_out [B][M] float, workspace of risrt_grad_workspace_size bytes. All
+ *   device memory.
  * precision RISRT_PREC_FP32: FP32 arithmetic on the CUDA cores, A read twice (forward and adjoint
  * GEMM, each split over its reduction axis with the partial sums added in a fixed order, so results
  * do not depend on scheduling). RISRT_PREC_BF16X2: both GEMMs on the tensor cores as real BF16 GEMMs
@@ -294,9 +321,9 @@ int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precis
  * the stream (the target rows are validated on the device). Errors: RISRT_ERR_INVALID_ARG (sizes,
  * precision, a target row outside [0, n_rx)); RISRT_ERR_NOT_READY (the paired tensor-core kernel
  * cannot run on this device); RISRT_ERR_TIMEOUT (a pipeline wait in the tensor-core kernel expired). */
-int risrt_grad_phases(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M,
-                      const int32_t* target, int32_t n_target, const float* phases, const float* amp,
-                      int32_t B, float* J_out, float* grad_out, void* workspace, size_t workspace_bytes, int precision);
+int risrt_grad_phases(risrt_ctx* ctx, const risrt_amat* amat, const int32_t* target, int32_t n_target,
+                      const float* phases, const float* amp, int32_t B, float* J_out, float* grad_out,
+                      void* workspace, size_t workspace_bytes, int precision);
 
 /* ------------------------------------------------------------------------------------------------
  * Allocation-free path search (this entry point has no counterpart in the paper; it exists for

@@ -34,18 +34,34 @@ cudaError_t ctx_malloc(risrt_ctx* ctx, void** p, size_t bytes)
             return cudaSuccess;
         }
     }
+    // cached blocks count against the context's budget and may be what the device is missing: they are
+    // released before a new block would exceed the budget, and before one more try after a failure
+    auto release_cache = [&]() {
+        std::lock_guard<std::mutex> lk(ctx->pool_mu);
+        for (auto& kv : ctx->pool_free) {
+            ctx->pool_size.erase(kv.second);
+            ctx->allocated -= kv.first;
+            cudaFree(kv.second);
+        }
+        ctx->pool_free.clear();
+        ctx->pool_cached = 0;
+    };
+    if (ctx && ctx->budget) {
+        bool over;
+        {
+            std::lock_guard<std::mutex> lk(ctx->pool_mu);
+            over = ctx->allocated + bytes > ctx->budget;
+        }
+        if (over) release_cache();
+        std::lock_guard<std::mutex> lk(ctx->pool_mu);
+        if (ctx->allocated + bytes > ctx->budget) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
-        // cached blocks may be what is missing: release them and try once more
-        if (ctx) {
-            std::lock_guard<std::mutex> lk(ctx->pool_mu);
-            for (auto& kv : ctx->pool_free) {
-                ctx->pool_size.erase(kv.second);
-                cudaFree(kv.second);
-            }
-            ctx->pool_free.clear();
-            ctx->pool_cached = 0;
-        }
+        if (ctx) release_cache();
         cudaGetLastError();
         e = cudaMalloc(p, bytes);
         if (e != cudaSuccess) {
@@ -56,6 +72,7 @@ cudaError_t ctx_malloc(risrt_ctx* ctx, void** p, size_t bytes)
     if (ctx) {
         std::lock_guard<std::mutex> lk(ctx->pool_mu);
         ctx->pool_size[*p] = bytes;
+        ctx->allocated += bytes;
     }
     return cudaSuccess;
 }
@@ -72,6 +89,7 @@ void ctx_free(risrt_ctx* ctx, void* p)
                 ctx->pool_cached += it->second;
                 return;
             }
+            ctx->allocated -= it->second;
             ctx->pool_size.erase(it);
         }
     }
@@ -156,7 +174,7 @@ int set_device(risrt_ctx* ctx)
 
 extern "C" {
 
-int risrt_create(risrt_ctx** out, int device, void* stream)
+int risrt_create(risrt_ctx** out, int device, void* stream, size_t hbm_budget_bytes)
 {
     if (!out) return fail(nullptr, RISRT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -170,6 +188,7 @@ int risrt_create(risrt_ctx** out, int device, void* stream)
     if (!c) return fail(nullptr, RISRT_ERR_OOM, "host allocation failed");
     c->device = device;
     c->stream = (cudaStream_t)stream;
+    c->budget = hbm_budget_bytes;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     *out = c;
     return RISRT_OK;
@@ -578,12 +597,92 @@ int risrt_microbench(risrt_ctx* ctx, int kind, int32_t iters, double* ops_per_s,
     return microbench(ctx, kind, iters, ops_per_s, ms);
 }
 
-int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out)
+int risrt_build_A(risrt_ctx* ctx, const risrt_pathset* ps, float* A_out, float* E0_out, risrt_amat** resident_out)
 {
     RISRT_CHECK_CTX(ctx);
-    if (!ps || !A_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (!ps || (!A_out && !resident_out)) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL path set, or neither A_out nor resident_out");
     if (((uintptr_t)A_out | (uintptr_t)E0_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
-    return build_A(ctx, ps, (float2*)A_out, (float2*)E0_out);
+    if (resident_out) *resident_out = nullptr;
+    risrt_amat* h = nullptr;
+    if (resident_out) {
+        h = new (std::nothrow) risrt_amat();
+        if (!h) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+        h->owner = ctx;
+        h->n_rx = ps->n_rx;
+        h->M = ps->M;
+    }
+    float2* A = (float2*)A_out;
+    float2* E0 = (float2*)E0_out;
+    if (!A_out) {               // resident: the library holds A and E0 in blocks of this context
+        void* a = nullptr;
+        void* e = nullptr;
+        cudaError_t err = ctx_malloc(ctx, &a, sizeof(float2) * (size_t)ps->n_rx * ps->M);
+        if (err == cudaSuccess) err = ctx_malloc(ctx, &e, sizeof(float2) * (size_t)ps->n_rx);
+        if (err != cudaSuccess) {
+            ctx_free(ctx, a);
+            delete h;
+            return cuda_fail(ctx, err, "channel matrix allocation");
+        }
+        A = (float2*)a;
+        E0 = (float2*)e;
+        h->owned = true;
+    }
+    int rc = build_A(ctx, ps, A, E0);
+    if (rc) {
+        if (h && h->owned) {
+            sync_ctx(ctx);
+            ctx_free(ctx, A);
+            ctx_free(ctx, E0);
+        }
+        delete h;
+        return rc;
+    }
+    if (h) {
+        h->A = A;
+        h->E0 = E0;
+        *resident_out = h;
+    }
+    return RISRT_OK;
+}
+
+int risrt_amat_wrap(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M, risrt_amat** out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!A || !out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || M < 1 || M > 65536) return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
+    if (((uintptr_t)A | (uintptr_t)E0) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    risrt_amat* h = new (std::nothrow) risrt_amat();
+    if (!h) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+    h->owner = ctx;
+    h->A = (const float2*)A;
+    h->E0 = (const float2*)E0;
+    h->n_rx = n_rx;
+    h->M = M;
+    *out = h;
+    return RISRT_OK;
+}
+
+int risrt_amat_data(const risrt_amat* amat, const float** A, const float** E0, int64_t* n_rx, int32_t* M)
+{
+    if (!amat) return RISRT_ERR_INVALID_ARG;
+    if (A) *A = (const float*)amat->A;
+    if (E0) *E0 = (const float*)amat->E0;
+    if (n_rx) *n_rx = amat->n_rx;
+    if (M) *M = amat->M;
+    return RISRT_OK;
+}
+
+int risrt_amat_destroy(risrt_ctx* ctx, risrt_amat* amat)
+{
+    if (!amat) return RISRT_OK;
+    if (amat->owned) {
+        if (ctx) sync_ctx(ctx);
+        risrt_ctx* pc = ctx && ctx == amat->owner ? ctx : nullptr;
+        ctx_free(pc, (void*)amat->A);
+        ctx_free(pc, (void*)amat->E0);
+    }
+    delete amat;
+    return RISRT_OK;
 }
 
 int risrt_sweep_workspace_size(int64_t n_rx, int32_t M, int32_t n_cfg, int precision, size_t* bytes)
@@ -594,23 +693,28 @@ int risrt_sweep_workspace_size(int64_t n_rx, int32_t M, int32_t n_cfg, int preci
     return RISRT_OK;
 }
 
-int risrt_sweep_configs(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M, const float* gamma,
-                        int32_t n_cfg, int precision, float* P_out, void* workspace, size_t workspace_bytes)
+int risrt_sweep_configs(risrt_ctx* ctx, const risrt_amat* amat, const float* gamma, const uint8_t* gamma_2bit, float amp,
+                        int32_t n_cfg, int precision, float* P_out, float* E_out, void* workspace, size_t workspace_bytes)
 {
     RISRT_CHECK_CTX(ctx);
-    if (!A || !gamma || !P_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
-    if (n_rx < 1 || n_rx > ((int64_t)1 << 26) || M < 1 || M > 65536 || n_cfg < 1 || n_cfg > (1 << 24))
-        return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
+    if (!amat || (!gamma == !gamma_2bit) || (!P_out && !E_out))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "need the channel matrix, exactly one of gamma / gamma_2bit, and P_out or E_out");
+    if (n_cfg < 1 || n_cfg > (1 << 24)) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_cfg out of range");
+    if (gamma_2bit && !std::isfinite(amp)) return fail(ctx, RISRT_ERR_INVALID_ARG, "amp must be finite");
     const int opts = precision & ~0xff;
     precision &= 0xff;
     if (precision < RISRT_PREC_FP32 || precision > RISRT_PREC_FP16 || (opts & ~(RISRT_SWEEP_KEEP_A | RISRT_SWEEP_DEFER_CHECK)))
         return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown precision or option");
     if (opts && precision == RISRT_PREC_FP16)
         return fail(ctx, RISRT_ERR_INVALID_ARG, "RISRT_SWEEP_KEEP_A / DEFER_CHECK need RISRT_PREC_BF16 or BF16X2");
-    if (((uintptr_t)A | (uintptr_t)gamma | (uintptr_t)E0) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    if (((uintptr_t)gamma | (uintptr_t)E_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
     if (precision != RISRT_PREC_FP32 && ((uintptr_t)workspace & 15u))
         return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
-    return sweep_configs(ctx, (const float2*)A, (const float2*)E0, n_rx, M, (const float2*)gamma, n_cfg, precision, P_out,
+    GammaSrc G;
+    G.G = (const float2*)gamma;
+    G.g2 = gamma_2bit;
+    G.amp = amp;
+    return sweep_configs(ctx, amat->A, amat->E0, amat->n_rx, amat->M, G, n_cfg, precision, P_out, (float2*)E_out,
                          workspace, workspace_bytes, (opts & RISRT_SWEEP_KEEP_A) != 0, (opts & RISRT_SWEEP_DEFER_CHECK) != 0);
 }
 
@@ -629,12 +733,16 @@ int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precis
     return RISRT_OK;
 }
 
-int risrt_grad_phases(risrt_ctx* ctx, const float* A, const float* E0, int64_t n_rx, int32_t M, const int32_t* target,
-                      int32_t n_target, const float* phases, const float* amp, int32_t B, float* J_out, float* grad_out,
-                      void* workspace, size_t workspace_bytes, int precision)
+int risrt_grad_phases(risrt_ctx* ctx, const risrt_amat* amat, const int32_t* target, int32_t n_target, const float* phases,
+                      const float* amp, int32_t B, float* J_out, float* grad_out, void* workspace, size_t workspace_bytes,
+                      int precision)
 {
     RISRT_CHECK_CTX(ctx);
-    if (!A || !phases || !J_out || !grad_out || !workspace) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (!amat || !phases || !J_out || !grad_out || !workspace) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    const float* A = (const float*)amat->A;
+    const float* E0 = (const float*)amat->E0;
+    const int64_t n_rx = amat->n_rx;
+    const int32_t M = amat->M;
     if (n_rx < 1 || M < 1 || M > 65536 || n_target < 1 || B < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
     const bool keep_a = (precision & RISRT_GRAD_KEEP_A) != 0;
     precision &= ~RISRT_GRAD_KEEP_A;

@@ -177,6 +177,8 @@ struct risrt_ctx {
     std::multimap<size_t, void*> pool_free;
     std::unordered_map<void*, size_t> pool_size;
     size_t pool_cached = 0;
+    size_t budget = 0;           // cap on the device bytes this context holds (0: none)
+    size_t allocated = 0;        // bytes of every block this context holds (in use or cached)
     std::string err;
     Antenna tx{}, rx{};
     // tracing
@@ -250,6 +252,17 @@ struct PathRec {
     float4 n1;       // bounce-1 normal in the RIS frame, eps2.re
     float4 n2;       // bounce-2 normal (unfolded) in the RIS frame, eps2.im
     float4 v;        // Rx pattern axis, unfolded into the RIS frame
+};
+
+// A dense channel matrix A [n_rx][M] and E0 [n_rx] (complex64) on the device: either owned (built by
+// the library into blocks of its context) or a view of caller memory.
+struct risrt_amat {
+    risrt_ctx* owner = nullptr;
+    const float2* A = nullptr;
+    const float2* E0 = nullptr;      // may be NULL (E0 = 0)
+    int64_t n_rx = 0;
+    int M = 0;
+    bool owned = false;
 };
 
 struct risrt_pathset {

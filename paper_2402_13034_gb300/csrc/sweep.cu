@@ -24,7 +24,7 @@ constexpr int kSB_R = 128, kSB_C = 64, kSB_K = 16;
 
 __global__ void __launch_bounds__(256)
 k_sweep_fp32(const float2* __restrict__ A, const float2* __restrict__ E0, int64_t n_rx, int M,
-             const float2* __restrict__ G, int C, float* __restrict__ P, float scale)
+             GammaSrc G, int C, float* __restrict__ P, float scale, float2* __restrict__ Eout)
 {
     __shared__ float2 sA[kSB_K][kSB_R + 1];
     __shared__ float2 sG[kSB_K][kSB_C + 1];
@@ -48,7 +48,7 @@ k_sweep_fp32(const float2* __restrict__ A, const float2* __restrict__ E0, int64_
         for (int i = tid; i < kSB_C * kSB_K; i += 256) {
             const int cc = i / kSB_K, kk = i % kSB_K;
             const int c = c0 + cc, k = k0 + kk;
-            sG[kk][cc] = (c < C && k < M) ? G[(int64_t)c * M + k] : make_float2(0.f, 0.f);
+            sG[kk][cc] = (c < C && k < M) ? G.at(c, k, M) : make_float2(0.f, 0.f);
         }
         __syncthreads();
 #pragma unroll
@@ -78,7 +78,8 @@ k_sweep_fp32(const float2* __restrict__ A, const float2* __restrict__ E0, int64_
             const int c = c0 + tc + 16 * j;
             if (c >= C) continue;
             const float er = acc[i][j].x + e0.x, ei = acc[i][j].y + e0.y;
-            P[r * C + c] = (er * er + ei * ei) * scale;
+            if (P) P[r * C + c] = (er * er + ei * ei) * scale;
+            if (Eout) Eout[r * C + c] = make_float2(er, ei);
         }
     }
 }
@@ -122,7 +123,7 @@ __global__ void k_pack_X(const float2* __restrict__ A, int64_t n_rx, int M, int 
 
 // Y rows (2C + padding up to Np) of length Kp; the split layout repeats the 2M block for the residual.
 template <typename T>
-__global__ void k_pack_Y(const float2* __restrict__ G, int C, int M, int Np, int Kp, bool split, T* __restrict__ Y)
+__global__ void k_pack_Y(GammaSrc G, int C, int M, int Np, int Kp, bool split, T* __restrict__ Y)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int n = (int)(i / Kp);
@@ -134,7 +135,7 @@ __global__ void k_pack_Y(const float2* __restrict__ G, int C, int M, int Np, int
         const int kk = k % (2 * M);
         const int m = kk % M;
         const bool second = kk >= M;              // multiplies Im A
-        const float2 g = G[(int64_t)c * M + m];
+        const float2 g = G.at(c, m, M);
         if (!(n & 1)) v = second ? -g.y : g.x;   // Re E = Re A Re G - Im A Im G
         else v = second ? g.x : g.y;             // Im E = Re A Im G + Im A Re G
     }
@@ -172,14 +173,14 @@ size_t sweep_workspace_bytes(int64_t n_rx, int M, int C, int precision)
     return s.x_bytes + s.y_bytes + 4096;
 }
 
-int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_rx, int M, const float2* G, int C,
-                  int precision, float* P, void* ws, size_t ws_bytes, bool keep_a, bool defer)
+int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_rx, int M, GammaSrc G, int C,
+                  int precision, float* P, float2* Eout, void* ws, size_t ws_bytes, bool keep_a, bool defer)
 {
     cudaStream_t s = ctx->stream;
     const float inv2eta = (float)(1.0 / (2.0 * kEta0));
     if (precision == RISRT_PREC_FP32) {
         dim3 grid(nblk(n_rx, kSB_R), nblk(C, kSB_C));
-        RISRT_KERNEL(ctx, "k_sweep_fp32", (k_sweep_fp32<<<grid, 256, 0, s>>>(A, E0, n_rx, M, G, C, P, inv2eta)));
+        RISRT_KERNEL(ctx, "k_sweep_fp32", (k_sweep_fp32<<<grid, 256, 0, s>>>(A, E0, n_rx, M, G, C, P, inv2eta, Eout)));
         return RISRT_OK;
     }
     SweepShape sh = sweep_shape(n_rx, M, C, precision);
@@ -213,7 +214,7 @@ int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_r
                                                                                             (__nv_bfloat16*)Y)));
     }
     return sweep_tc(ctx, X, Y, sh, precision == RISRT_PREC_FP16, E0, n_rx, C, P, inv2eta / (xscale * xscale), xscale,
-                    d_max + 1, defer);
+                    d_max + 1, defer, Eout);
 }
 
 int sweep_check(risrt_ctx* ctx, const void* ws, size_t ws_bytes)

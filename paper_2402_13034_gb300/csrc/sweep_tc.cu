@@ -101,7 +101,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
 __global__ void __launch_bounds__(192, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int num_kb, uint32_t idesc,
            const float2* __restrict__ E0, int64_t n_rx, int C, float* __restrict__ P, float pscale, float e0scale,
-           unsigned* __restrict__ err)
+           unsigned* __restrict__ err, float2* __restrict__ Eout, float escale)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -205,7 +205,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUte
                 const int c = (n0 >> 1) + j * 8 + q;
                 if (c < C) {
                     const float er = v[2 * q] + e0.x, ei = v[2 * q + 1] + e0.y;
-                    P[row * C + c] = (er * er + ei * ei) * pscale;
+                    if (P) P[row * C + c] = (er * er + ei * ei) * pscale;
+                    if (Eout) Eout[row * C + c] = make_float2(er * escale, ei * escale);
                 }
             }
         }
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(192, 1)
 k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int num_kb, int tiles_n,
                 int num_tiles, uint32_t idesc, const float2* __restrict__ E0, int64_t n_rx, int C,
                 float* __restrict__ P, float pscale, float e0scale, unsigned* __restrict__ err, int num_kb_total,
-                float2* __restrict__ Cout)
+                float2* __restrict__ Cout, float2* __restrict__ Eout, float escale)
 {
     // split-K (num_kb k-blocks per split, num_kb_total in all): tile t covers split z = t / tiles_mn;
     // with Cout the epilogue writes the complex partial sums D[row][2c] + j D[row][2c + 1] (+ E0 in
@@ -462,6 +463,13 @@ k_sweep_tc_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
                 }
                 if (!live) continue;
                 const int c0 = cbase + j * 8;
+                if (Eout) {                          // complex field, receiver-major like P
+                    float2* edst = Eout + row * C + c0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (c0 + q < C) edst[q] = make_float2((v[2 * q] + e0.x) * escale, (v[2 * q + 1] + e0.y) * escale);
+                }
+                if (!P) continue;
                 float* dst = P + row * C + c0;
                 if (vec && c0 + 8 <= C) {
                     reinterpret_cast<float4*>(dst)[0] = make_float4(p[0], p[1], p[2], p[3]);
@@ -564,8 +572,9 @@ uint32_t make_idesc(bool fp16, int m, int n)
 }  // namespace
 
 int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh, bool fp16, const float2* E0,
-             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev, bool defer)
+             int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev, bool defer, float2* Eout)
 {
+    const float escale = 1.f / e0scale;
     cudaStream_t s = ctx->stream;
     CUtensorMap mX, mY;
     if (((uintptr_t)X & 15) || ((uintptr_t)Y & 15)) return fail(ctx, RISRT_ERR_INVALID_ARG, "operands not 16-byte aligned");
@@ -594,14 +603,15 @@ int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh,
         cudaError_t le = cudaSuccess;
         RISRT_KERNEL(ctx, "k_sweep_tc_pair",
                      (le = cudaLaunchKernelEx(&cfg, k_sweep_tc_pair, mX, mY, sh.Kp / kTcBK, tiles_n, num_tiles, idesc, E0,
-                                              n_rx, C, P, pscale, e0scale, err_dev, sh.Kp / kTcBK, (float2*)nullptr)));
+                                              n_rx, C, P, pscale, e0scale, err_dev, sh.Kp / kTcBK, (float2*)nullptr,
+                                              Eout, escale)));
         if (le != cudaSuccess) return cuda_fail(ctx, le, "k_sweep_tc_pair");
     } else {
         RISRT_CUDA(ctx, cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
         dim3 grid((unsigned)(sh.Mp / kTcBM), (unsigned)(sh.Np / kTcBN));
         const uint32_t idesc = make_idesc(fp16, kTcBM, kTcBN);
         RISRT_KERNEL(ctx, "k_sweep_tc", (k_sweep_tc<<<grid, 192, kSmemBytes, s>>>(mX, mY, sh.Kp / kTcBK, idesc, E0, n_rx,
-                                                                                C, P, pscale, e0scale, err_dev)));
+                                                                                C, P, pscale, e0scale, err_dev, Eout, escale)));
     }
     if (defer) return RISRT_OK;          // the flag stays in the workspace (risrt_sweep_check)
     unsigned h = 0;
@@ -649,7 +659,7 @@ int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, 
     cudaError_t le = cudaSuccess;
     RISRT_KERNEL(ctx, "k_sweep_tc_pair",
                  (le = cudaLaunchKernelEx(&cfg, k_sweep_tc_pair, mX, mY, kb_per, tiles_n, num_tiles, idesc, E0rows, rows, C,
-                                          (float*)nullptr, 0.f, 1.f, err_dev, kb_total, out)));
+                                          (float*)nullptr, 0.f, 1.f, err_dev, kb_total, out, (float2*)nullptr, 1.f)));
     if (le != cudaSuccess) return cuda_fail(ctx, le, "k_sweep_tc_pair");
     unsigned h = 0;
     RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

@@ -31,7 +31,7 @@ _lib = None
 # Every symbol the header declares, with (restype, argtypes).
 _P = C.c_void_p
 _SIGS = {
-    "risrt_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "risrt_create": (C.c_int, [C.POINTER(_P), C.c_int, _P, C.c_size_t]),
     "risrt_set_stream": (C.c_int, [_P, _P]),
     "risrt_destroy": (C.c_int, [_P]),
     "risrt_last_error": (C.c_char_p, [_P]),
@@ -47,13 +47,15 @@ _SIGS = {
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_eval_field_plain": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_microbench": (C.c_int, [_P, C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
-    "risrt_build_A": (C.c_int, [_P, _P, _P, _P]),
+    "risrt_build_A": (C.c_int, [_P, _P, _P, _P, C.POINTER(_P)]),
+    "risrt_amat_wrap": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.POINTER(_P)]),
+    "risrt_amat_data": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "risrt_amat_destroy": (C.c_int, [_P, _P]),
     "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
-    "risrt_sweep_configs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int, _P, _P, C.c_size_t]),
+    "risrt_sweep_configs": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_int32, C.c_int, _P, _P, _P, C.c_size_t]),
     "risrt_sweep_check": (C.c_int, [_P, _P, C.c_size_t]),
     "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
-    "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P,
-                                    C.c_size_t, C.c_int]),
+    "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P, C.c_size_t, C.c_int]),
     "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
                                            C.POINTER(C.c_int32)]),
     "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
@@ -165,6 +167,38 @@ class RxSet(_Handle):
         self._keep = keep
 
 
+class AMat(_Handle):
+    """A channel matrix A [n_rx, M] and E0 [n_rx] on the device (owned by the library or a view)."""
+
+    def __init__(self, ctx, ptr, n_rx, M, keep=None):
+        super().__init__(ctx, ptr, "risrt_amat_destroy")
+        self.n_rx, self.M = n_rx, M
+        self._keep = keep
+
+    def tensors(self):
+        """(A, E0) as complex64 CUDA tensors sharing the device memory (E0 None if absent); valid while
+        the handle lives."""
+        import torch
+        a, e = C.c_void_p(), C.c_void_p()
+        rc = load().risrt_amat_data(self._ptr, C.byref(a), C.byref(e), None, None)
+        if rc:
+            raise RisrtError(rc, "amat data")
+
+        def view(ptr, n):
+            if not ptr.value:
+                return None
+            return torch.as_tensor(_DevBytes(ptr.value, n * 8), device=f"cuda:{self._ctx.device}").view(torch.complex64)
+        A = view(a, self.n_rx * self.M)
+        return A.view(self.n_rx, self.M), view(e, self.n_rx)
+
+
+class _DevBytes:
+    """A device byte range exposed through __cuda_array_interface__ (no copy, no ownership)."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3}
+
+
 class PathSet(_Handle):
     def stats(self) -> PathsetStats:
         st = PathsetStats()
@@ -200,11 +234,11 @@ class PathSet(_Handle):
 class Context:
     """One device + stream. Methods mirror the C ABI; see include/risrt.h for semantics."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, hbm_budget: int = 0):
         lib = load()
         self._ptr = C.c_void_p()
         s = None if stream is None else C.c_void_p(stream)
-        rc = lib.risrt_create(C.byref(self._ptr), device, s)
+        rc = lib.risrt_create(C.byref(self._ptr), device, s, int(hbm_budget))
         if rc:
             raise RisrtError(rc, lib.risrt_last_error(None).decode())
         self.device = device
@@ -326,19 +360,33 @@ class Context:
             return None
         return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
 
-    def sweep_configs(self, A, E0, gamma, P_out, precision: int, workspace=None, keep_a: bool = False,
-                      defer_check: bool = False):
-        """A: complex64 CUDA [n_rx, M]; E0: complex64 [n_rx] or None; gamma: complex64 [C, M];
-        P_out: float32 [n_rx, C]. keep_a: reuse A as packed into the workspace by an earlier call;
-        defer_check: enqueue only (capturable), check later with sweep_check."""
+    def amat(self, A, E0=None) -> "AMat":
+        """A channel-matrix handle viewing the complex64 CUDA tensors A [n_rx, M] and E0 [n_rx] (or None)."""
         n_rx, M = A.shape
-        n_cfg = gamma.shape[0]
+        out = C.c_void_p()
+        self._check(load().risrt_amat_wrap(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
+                                           int(n_rx), int(M), C.byref(out)))
+        return AMat(self, out, int(n_rx), int(M), keep=(A, E0))
+
+    def _as_amat(self, A, E0):
+        return A if isinstance(A, AMat) else self.amat(A, E0)
+
+    def sweep_configs(self, A, E0, gamma, P_out, precision: int, workspace=None, keep_a: bool = False,
+                      defer_check: bool = False, gamma_2bit=None, amp: float = 1.0, E_out=None):
+        """A: complex64 CUDA [n_rx, M] (with E0 complex64 [n_rx] or None) or an AMat handle (E0 ignored);
+        gamma: complex64 [C, M], or None with gamma_2bit: uint8 CUDA [C, ceil(M/4)] codes (Gamma = amp j^q);
+        P_out: float32 [n_rx, C] or None; E_out: complex64 [n_rx, C] or None. keep_a: reuse A as packed into
+        the workspace by an earlier call; defer_check: enqueue only (capturable), check later with
+        sweep_check."""
+        h = self._as_amat(A, E0)
+        n_cfg = gamma.shape[0] if gamma is not None else gamma_2bit.shape[0]
         ws_ptr = None if workspace is None else C.c_void_p(workspace.data_ptr())
         ws_n = 0 if workspace is None else workspace.numel()
         opts = (SWEEP_KEEP_A if keep_a else 0) | (SWEEP_DEFER_CHECK if defer_check else 0)
-        self._check(load().risrt_sweep_configs(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
-                                               int(n_rx), int(M), _dev_ptr(gamma, "torch.complex64"), int(n_cfg),
-                                               int(precision) | opts, _dev_ptr(P_out, "torch.float32"), ws_ptr, ws_n))
+        self._check(load().risrt_sweep_configs(self._ptr, h.ptr, _dev_ptr(gamma, "torch.complex64"),
+                                               _dev_ptr(gamma_2bit, "torch.uint8"), float(amp), int(n_cfg),
+                                               int(precision) | opts, _dev_ptr(P_out, "torch.float32"),
+                                               _dev_ptr(E_out, "torch.complex64"), ws_ptr, ws_n))
 
     def sweep_check(self, workspace):
         """Waits for the stream; raises RisrtError if a deferred-check sweep on this workspace timed out."""
@@ -354,16 +402,16 @@ class Context:
 
     def grad_phases(self, A, E0, target, phases, amp, J_out, grad_out, workspace=None, precision: int = PREC_FP32,
                     keep_a: bool = False):
-        """A: complex64 CUDA [n_rx, M]; target: int32 CUDA [n_t] or None (first n_t rows given by
+        """A: complex64 CUDA [n_rx, M] (with E0) or an AMat; target: int32 CUDA [n_t] or None (first n_t rows given by
         phases' companion J); phases: float32 [B, M]; amp: float32 [M] or None; J_out [B]; grad_out [B, M];
         precision PREC_FP32 (CUDA cores) or PREC_BF16X2 (tensor cores, split BF16); keep_a: A, E0 and target
         are those of the previous call with this workspace (its packed A is reused)."""
-        n_rx, M = A.shape
+        h = self._as_amat(A, E0)
+        n_rx, M = h.n_rx, h.M
         B = phases.shape[0]
         n_t = target.numel() if target is not None else n_rx
         ws = workspace if workspace is not None else self.grad_workspace(n_t, B, M, precision)
-        self._check(load().risrt_grad_phases(self._ptr, _dev_ptr(A, "torch.complex64"), _dev_ptr(E0, "torch.complex64"),
-                                             int(n_rx), int(M), _dev_ptr(target, "torch.int32"), int(n_t),
+        self._check(load().risrt_grad_phases(self._ptr, h.ptr, _dev_ptr(target, "torch.int32"), int(n_t),
                                              _dev_ptr(phases, "torch.float32"), _dev_ptr(amp, "torch.float32"), int(B),
                                              _dev_ptr(J_out, "torch.float32"), _dev_ptr(grad_out, "torch.float32"),
                                              C.c_void_p(ws.data_ptr()), ws.numel(),
@@ -379,9 +427,18 @@ class Context:
                                                      int(cap), C.byref(n)))
         return ids[: n.value].copy()
 
-    def build_A(self, ps: PathSet, A_out, E0_out=None):
+    def build_A(self, ps: PathSet, A_out=None, E0_out=None, resident: bool = False):
+        """Channel matrix into A_out [n_rx, M] / E0_out [n_rx] (complex64 CUDA). With A_out None the
+        library keeps A and E0 resident and an AMat owning them is returned; with resident=True and
+        A_out given, an AMat viewing A_out / E0_out is returned."""
+        out = C.c_void_p()
+        want = A_out is None or resident
         self._check(load().risrt_build_A(self._ptr, ps.ptr, _dev_ptr(A_out, "torch.complex64"),
-                                         _dev_ptr(E0_out, "torch.complex64")))
+                                         _dev_ptr(E0_out, "torch.complex64"), C.byref(out) if want else None))
+        if not want:
+            return None
+        st = ps.stats()
+        return AMat(self, out, st.n_rx, st.M, keep=(A_out, E0_out) if A_out is not None else None)
 
 
 def launch_count() -> int:
