@@ -220,6 +220,24 @@ int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma
 int risrt_eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg,
                            float* E_out, float* P_out);
 
+/* Channel impulse response of the RIS part of the field (Sec. II-B: every multipath component that
+ * goes through the RIS) for one configuration gamma [M] complex64. Let P = n_tx_paths + 1 (Tx-leg
+ * paths: p = 0 the direct leg, p >= 1 the valid reflected Tx-leg sequences in ascending id, as in
+ * risrt_pathset_export) and let the Rx-leg entries be those of the path set, receiver-major, each
+ * receiver's direct entry first, then its reflected sequences in ascending id (n_rx_paths in all).
+ *   taps_out     [n_rx_paths][P] complex64: tap (entry q, p) = sum_m Gamma_m K c_mp b_mq, the field of
+ *                the multipath components that take Tx-leg path p and Rx-leg path q (a direct leg
+ *                counts the elements it reaches unblocked); the taps of a receiver plus E0 add up to
+ *                the field of risrt_eval_field
+ *   rx_delay_out [n_rx_paths] double: |I_q - c| / c0, the Rx-leg travel time from the RIS centre c
+ *                (seconds; the receiver image I_q from FP64, stored in FP32, about 1e-7 relative)
+ *   tx_delay_out [P] double: |T_p - c| / c0 with T_p the Tx image of path p (FP64)
+ * A tap's delay is tx_delay[p] + rx_delay[q]: the travel time through the RIS centre; the offsets of
+ * the individual elements (at most the aperture over c0) stay in the tap's phase. LOS and environment
+ * paths are not taps here (they are summed in E0). Enqueued on the context's stream. */
+int risrt_eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, float* taps_out, double* rx_delay_out,
+                   double* tx_delay_out);
+
 /* Dense channel matrix (Eq. 9 is linear in Gamma): A [n_rx][M] complex64 with A[r][m] = c_m sum_q b_mq(r),
  * so that E = E0 + A . Gamma, and E0 [n_rx] complex64.
  *  - A_out != NULL: written into caller memory (E0_out may be NULL). If resident_out != NULL,

@@ -75,6 +75,8 @@ def _load():
                                         C.c_int32, C.c_void_p, C.c_void_p]
             lib.or_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+            lib.or_cir.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             lib.or_element_positions.argtypes = [C.c_void_p, C.c_void_p]
             lib.or_segment_blocked.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                                C.c_void_p]
@@ -248,6 +250,28 @@ class Oracle:
         _load().or_field(self._ctx, _ptr(rx), n, _ptr(E0), _ptr(S0), _ptr(A), _ptr(SA), _ptr(amb), 0)
         return dict(E0=E0[:, 0] + 1j * E0[:, 1], S0=S0, A=A[..., 0] + 1j * A[..., 1], SA=SA,
                     amb=amb.astype(bool))
+
+    def cir(self, rx_xyz: np.ndarray, gamma: np.ndarray, cap: int = 4096):
+        """RIS channel impulse response per receiver: a list of taps (Rx-leg id q, Tx-leg id p, delay in
+        seconds through the RIS centre, complex amplitude sum_m Gamma_m e_mpq and its incoherent
+        magnitude sabs), q-major in ascending ids (-1 = direct leg first)."""
+        rx = np.ascontiguousarray(rx_xyz, np.float32).reshape(-1, 3)
+        n = len(rx)
+        g = np.asarray(gamma, np.complex128).ravel()
+        gi = np.ascontiguousarray(np.stack([g.real, g.imag], 1))
+        amp = np.zeros((n, cap, 2))
+        sabs = np.zeros((n, cap))
+        delay = np.zeros((n, cap))
+        p_id = np.zeros((n, cap), np.int64)
+        q_id = np.zeros((n, cap), np.int64)
+        cnt = np.zeros(n, np.int32)
+        _load().or_cir(self._ctx, _ptr(rx), n, _ptr(gi), cap, _ptr(amp), _ptr(sabs), _ptr(delay), _ptr(p_id), _ptr(q_id),
+                       _ptr(cnt))
+        if (cnt > cap).any():
+            raise RuntimeError("oracle CIR capacity exceeded")
+        return [dict(q=q_id[i, : cnt[i]].copy(), p=p_id[i, : cnt[i]].copy(), delay=delay[i, : cnt[i]].copy(),
+                     amp=amp[i, : cnt[i], 0] + 1j * amp[i, : cnt[i], 1], sabs=sabs[i, : cnt[i]].copy())
+                for i in range(n)]
 
     @staticmethod
     def evaluate(fld: dict, gamma: np.ndarray):

@@ -708,6 +708,83 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
     return 0;
 }
 
+/* Channel impulse response of the RIS part (Sec. II-B: every multipath component through the RIS),
+   per receiver: one tap per pair (Rx-leg path q, Tx-leg path p) in the order q = direct, then the
+   valid Rx-leg sequences by ascending id; within q, p = direct, then the valid Tx-leg sequences by
+   ascending id. The tap's amplitude is sum_m Gamma_m e_mpq (the plain triple sum restricted to one
+   (p, q); a direct leg counts only the elements it reaches unblocked), its delay the travel time of
+   the path through the RIS centre, (|T_p - c| + |I_q - c|) / c0 with T_p, I_q the image-method end
+   points. gamma [M] interleaved (re, im); outputs [n_rx][cap]: amp (re, im), sabs (sum_m |Gamma_m e_mpq|,
+   the tap's incoherent magnitude), delay (s), p_id and q_id
+   (-1 for a direct leg); count[n_rx] (may exceed cap: then only cap taps are written). */
+int or_cir(const or_ctx* C, const float* rx_xyz, int64_t n_rx, const double* gamma, int32_t cap, double* amp,
+           double* sabs, double* delay, int64_t* p_id, int64_t* q_id, int32_t* count)
+{
+    int F = C->F, hf = C->P.host_face, M = C->P.M;
+    int64_t tcap = 1 << 20;
+    int64_t* tx_ids = (int64_t*)malloc(sizeof(int64_t) * tcap);
+    uint8_t* tx_vis = (uint8_t*)malloc(M > 0 ? M : 1);
+    int64_t n_tx = 0;
+    int32_t tx_amb = 0;
+    or_tx_leg(C, tx_ids, tcap, &n_tx, tx_vis, &tx_amb, NULL, NULL, 0, NULL, NULL);
+    if (n_tx > tcap) n_tx = tcap;
+    int64_t n_ids = C->P.max_order_rx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_rx >= 1 ? F : 0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n_rx; ++i) {
+        v3 r = vf(rx_xyz + 3 * i);
+        int amb = 0;
+        int64_t* rx_ids = (int64_t*)malloc(sizeof(int64_t) * (n_ids > 0 ? n_ids : 1));
+        int n_q = 0;
+        for (int64_t id = 0; id < n_ids; ++id) {
+            int seq[2];
+            int k = decode_seq(C, id, seq);
+            v3 pts[4];
+            if (seq_allowed(C, seq, k, 1) && validate_seq(C, C->c, hf, r, -1, seq, k, &amb, pts)) rx_ids[n_q++] = id;
+        }
+        uint8_t* rx_direct = (uint8_t*)malloc(M > 0 ? M : 1);
+        for (int m = 0; m < M; ++m) rx_direct[m] = !blocked_decision(C, C->e[m], r, hf, -1, &amb);
+        int nt = 0;
+        for (int q = -1; q < n_q; ++q) {
+            int rseq[2], rk = 0;
+            if (q >= 0) rk = decode_seq(C, rx_ids[q], rseq);
+            double Lq = leg_by_images(C, C->c, r, rseq, rk).L;
+            for (int64_t p = -1; p < n_tx; ++p) {
+                int tseq[2], tk = 0;
+                if (p >= 0) tk = decode_seq(C, tx_ids[p], tseq);
+                double Lp = leg_by_images(C, C->tx, C->c, tseq, tk).L;
+                double complex a = 0.0;
+                double sa = 0.0;
+                for (int m = 0; m < M; ++m) {
+                    if (p < 0 && !tx_vis[m]) continue;
+                    if (q < 0 && !rx_direct[m]) continue;
+                    leg_t gt = leg_by_images(C, C->tx, C->e[m], tseq, tk);
+                    leg_t gr = leg_by_images(C, C->e[m], r, rseq, rk);
+                    double complex g = gamma[2 * m] + I * gamma[2 * m + 1];
+                    double complex v = g * ris_term(C, &gt, &gr);
+                    a += v;
+                    sa += cabs(v);
+                }
+                if (nt < cap) {
+                    int64_t o = i * cap + nt;
+                    amp[2 * o] = creal(a);
+                    amp[2 * o + 1] = cimag(a);
+                    sabs[o] = sa;
+                    delay[o] = (Lp + Lq) / OR_C0;
+                    p_id[o] = p < 0 ? -1 : tx_ids[p];
+                    q_id[o] = q < 0 ? -1 : rx_ids[q];
+                }
+                ++nt;
+            }
+        }
+        count[i] = nt;
+        free(rx_direct);
+        free(rx_ids);
+    }
+    free(tx_ids);
+    free(tx_vis);
+    return 0;
+}
+
 /* Element positions as the oracle sees them (for tests of the frame convention). */
 void or_element_positions(const or_ctx* C, double* out)
 {

@@ -589,6 +589,16 @@ int risrt_eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float*
     return eval_field_plain(ctx, ps, (const float2*)gamma, n_cfg, (float2*)E_out, P_out);
 }
 
+int risrt_eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, float* taps_out, double* rx_delay_out,
+                   double* tx_delay_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!ps || !gamma || !taps_out || !rx_delay_out || !tx_delay_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (((uintptr_t)gamma | (uintptr_t)taps_out | (uintptr_t)rx_delay_out | (uintptr_t)tx_delay_out) & 7u)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "arrays must be 8-byte aligned");
+    return eval_cir(ctx, ps, (const float2*)gamma, (float2*)taps_out, rx_delay_out, tx_delay_out);
+}
+
 int risrt_microbench(risrt_ctx* ctx, int kind, int32_t iters, double* ops_per_s, double* ms)
 {
     RISRT_CHECK_CTX(ctx);

@@ -278,6 +278,46 @@ k_eval_plain(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, c
     }
 }
 
+// Channel impulse response of the RIS part: one warp per receiver, lanes own elements; for every Rx-leg
+// entry q and Tx-leg path p the tap sum_m g[m][p] b_mq (g = Gamma_m K c_mp), written at (entry, p),
+// and the entry's delay from the RIS centre D0 / c0.
+template <int PAT>
+__global__ void __launch_bounds__(32 * kEvalWarps)
+k_cir(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const uint32_t* __restrict__ vis, int W,
+      const float4* __restrict__ elem, const float2* __restrict__ g, int M, int P, int64_t n_rx,
+      float2* __restrict__ taps, double* __restrict__ rx_delay, float inv_lam, float gr, int tm)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)kEvalWarps + (threadIdx.x >> 5);
+    if (r >= n_rx) return;
+    const int64_t o = off[r];
+    const int nq = (int)(off[r + 1] - o);
+    for (int q = 0; q < nq; ++q) {
+        const PathRec pr = rec[o + q];
+        const bool reflected = __float_as_int(pr.a.y) > 0;
+        if (lane == 0) rx_delay[o + q] = (double)pr.w.w / kC0;
+        for (int p = 0; p < P; ++p) {
+            cf acc = cf{0.f, 0.f};
+            for (int m0 = 0; m0 < M; m0 += 32) {
+                const int m = m0 + lane;
+                if (m >= M) break;
+                if (!reflected && !((vis[r * W + (m >> 5)] >> (m & 31)) & 1u)) continue;
+                const cf b = rx_leg_term<PAT>(pr, elem[m], inv_lam, gr, tm != 0);
+                const float2 gg = g[(int64_t)m * P + p];
+                const cf v = cmulf(b, cf{gg.x, gg.y});
+                acc.re += v.re;
+                acc.im += v.im;
+            }
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                acc.re += __shfl_down_sync(0xffffffffu, acc.re, s);
+                acc.im += __shfl_down_sync(0xffffffffu, acc.im, s);
+            }
+            if (lane == 0) taps[(o + q) * P + p] = make_float2(acc.re, acc.im);
+        }
+    }
+}
+
 // A[r][m] = c_m sum_q b_mq: one warp per receiver, lanes own elements, paths broadcast.
 template <int PAT>
 __global__ void __launch_bounds__(32 * kEvalWarps)
@@ -376,6 +416,32 @@ int eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamm
 #undef RISRT_PLAIN
     }
     return RISRT_OK;
+}
+
+int eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, float2* taps, double* rx_delay, double* tx_delay)
+{
+    const int P = (int)ps->tx_seq_host.size() + 1;
+    void* g = nullptr;
+    RISRT_CUDA(ctx, ctx_malloc(ctx, &g, sizeof(float2) * (size_t)ps->M * P));
+    int rc = cir_tx_coef(ctx, ps, gamma, (float2*)g, tx_delay);
+    if (!rc) {
+        const float inv_lam = (float)(ps->freq / kC0);
+        const int tm = (ps->flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
+        const unsigned grid = nblk(ps->n_rx, kEvalWarps);
+        auto launch = [&](auto kern) -> int {
+            RISRT_KERNEL(ctx, "k_cir", (kern<<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
+                                           ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, (const float2*)g, ps->M, P,
+                                           ps->n_rx, taps, rx_delay, inv_lam, ps->rx_gain, tm)));
+            return RISRT_OK;
+        };
+        switch (ps->rx_pattern) {
+            case RISRT_PATTERN_COS_POW: rc = launch(k_cir<RISRT_PATTERN_COS_POW>); break;
+            case RISRT_PATTERN_MONOPOLE_QW: rc = launch(k_cir<RISRT_PATTERN_MONOPOLE_QW>); break;
+            default: rc = launch(k_cir<RISRT_PATTERN_ISO>); break;
+        }
+    }
+    ctx_free(ctx, g);    // later users of the block are ordered after this work on the context's stream
+    return rc;
 }
 
 int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0)

@@ -254,6 +254,33 @@ struct PathRec {
     float4 v;        // Rx pattern axis, unfolded into the RIS frame
 };
 
+namespace risrt {
+struct Frame {             // RIS frame, FP64
+    double c[3], t1[3], t2[3], n[3];
+};
+struct AntD {
+    double pos[3];
+    double z[3];           // unit boresight (local z axis)
+    double power, gain;
+    int pattern;
+};
+struct WaveD {
+    double lam, k, omega;
+    double inv_lam;        // 1 / lambda
+    float inv_we;          // 1 / (omega eps0): eps_c = eps_r - j sigma / (omega eps0)
+    int tm;
+};
+// One valid reflected Tx-leg path kept with its path set: the Tx image across its faces (FP64) and,
+// per face in propagation order, the FP32 unit normal and complex permittivity.
+struct TxPathD {
+    dv4 img;
+    float4 n[2];
+    float2 eps[2];
+    int k;                 // order
+    int id;                // sequence id
+};
+}  // namespace risrt
+
 // A dense channel matrix A [n_rx][M] and E0 [n_rx] (complex64) on the device: either owned (built by
 // the library into blocks of its context) or a view of caller memory.
 struct risrt_amat {
@@ -292,6 +319,15 @@ struct risrt_pathset {
     uint8_t* los = nullptr;          // [n_rx]
     std::vector<int64_t> tx_seq_host;
     std::vector<uint8_t> tx_vis_host;
+    // the Tx leg and the parameters of the trace, for per-path outputs (risrt_eval_cir)
+    risrt::TxPathD* tx_paths = nullptr;   // [n_tx] valid reflected Tx-leg paths by ascending id
+    int64_t cap_tx_paths = 0;
+    uint8_t* tx_vis_dev = nullptr;        // [M] Tx -> e_m unblocked
+    int64_t cap_tx_vis = 0;
+    risrt::Frame fr{};
+    risrt::AntD txa{};
+    risrt::WaveD wv{};
+    double K = 0.0;
     // statistics: counted on the device, fetched when first asked for (the trace does not wait)
     mutable int64_t units = 0;
     mutable int64_t fp64_refines = 0;
@@ -355,6 +391,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
 int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
 int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0);
 int eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
+int eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, float2* taps, double* rx_delay, double* tx_delay);
+int cir_tx_coef(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, float2* g, double* tx_delay);
 int microbench(risrt_ctx* ctx, int kind, int iters, double* ops_per_s, double* ms);
 size_t grad_workspace_bytes(int n_t, int B, int M, int precision);
 int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes);

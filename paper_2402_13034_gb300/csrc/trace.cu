@@ -16,16 +16,6 @@ namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-struct Frame {             // RIS frame, FP64
-    double c[3], t1[3], t2[3], n[3];
-};
-struct AntD {
-    double pos[3];
-    double z[3];           // unit boresight (local z axis)
-    double power, gain;
-    int pattern;
-};
-
 __device__ __forceinline__ d3 fr_c(const Frame& F) { return D3(F.c[0], F.c[1], F.c[2]); }
 __device__ __forceinline__ d3 fr_t1(const Frame& F) { return D3(F.t1[0], F.t1[1], F.t1[2]); }
 __device__ __forceinline__ d3 fr_t2(const Frame& F) { return D3(F.t2[0], F.t2[1], F.t2[2]); }
@@ -1166,16 +1156,9 @@ __global__ void k_tx_vis(DeviceScene S, const float4* __restrict__ elem, int M, 
 
 // ------------------------------------------------------------------------------------------------
 // Tx-leg element coefficients: K * c_m = K * sum_p sqrt(2 eta0 Pt Gt Ft) sqrt(F_in) R_p e^{-jkL}/L
-// (Eq. 4, Eq. 5, Eq. 7; K = sqrt(G dy dz / 4 pi) lambda / 4 pi), all in FP64.
+// (Eq. 4, Eq. 5, Eq. 7; K = sqrt(G dy dz / 4 pi) lambda / 4 pi): FP64 for the unfolded length L and
+// frac(L / lambda), FP32 for directions, Fresnel products and patterns (they enter amplitudes only).
 // ------------------------------------------------------------------------------------------------
-struct WaveD {
-    double lam, k, omega;
-    double inv_lam;        // 1 / lambda
-    float inv_we;          // 1 / (omega eps0): eps_c = eps_r - j sigma / (omega eps0)
-    int tm;
-};
-
-
 
 // FP32 face data for the per-path terms: unit normal and complex permittivity of the face's material.
 __device__ __forceinline__ float3 face_n32(const DeviceScene& S, int f)
@@ -1190,9 +1173,40 @@ __device__ __forceinline__ float2 face_eps32(const DeviceScene& S, int f, const 
 }
 __device__ __forceinline__ float3 mirror_dir_f(float3 v, float3 n) { return v - n * (2.f * dot(n, v)); }
 
-// One warp per element, lanes over its Tx-leg paths (LOS first): FP64 for the unfolded length L and
-// frac(L / lambda), FP32 for directions, Fresnel products and patterns (they enter amplitudes only);
-// fixed reduction order (lane-strided paths, shuffle tree).
+// One Tx-leg term of element e from the Tx image Ts across k faces (nf / ef: FP32 normals and complex
+// permittivities of the faces in propagation order): sqrt(2 eta0 Pt Gt Ft) sqrt(F_in) R_p e^{-jkL} / L
+// (Eq. 4, Eq. 5, Fresnel per bounce) with L and frac(L / lambda) in FP64, directions, Fresnel
+// products and patterns in FP32 (they enter amplitudes only).
+__device__ __forceinline__ cf tx_term(d3 e, d3 Ts, int k, const float3* nf, const float2* ef, float3 z, float3 nr,
+                                      float gt, float amp0, int pattern, const WaveD& wv)
+{
+    const d3 d = e - Ts;
+    const double L = sqrt(dot(d, d));
+    const double x = L * wv.inv_lam;
+    const float ph = (float)(x - floor(x));
+    float3 u = to_f(d);                       // arrival direction at the element: the last segment is real
+    u = u * rsqrtf(dot(u, u));
+    cf Rp = cf{1.f, 0.f};
+    if (k >= 1) {
+        const float3 nl = nf[k - 1];
+        Rp = fresnel_f(fabsf(dot(u, nl)), ef[k - 1].x, ef[k - 1].y, wv.tm);
+        if (k == 2) {
+            const float3 n1 = mirror_dir_f(nf[0], nl);
+            Rp = cmulf(Rp, fresnel_f(fabsf(dot(u, n1)), ef[0].x, ef[0].y, wv.tm));
+        }
+    }
+    float3 dep = u;
+    for (int j = k - 1; j >= 0; --j) dep = mirror_dir_f(dep, nf[j]);
+    const float Ft = pattern_f(pattern, gt, dot(dep, z));
+    const float Fin = fmaxf(-dot(u, nr), 0.f);  // element pattern max(cos, 0) toward the Tx side
+    const float amp = amp0 * sqrtf(Ft * Fin) / (float)L;
+    float sn, cs;
+    sincospif(2.f * ph, &sn, &cs);            // e^{-j 2 pi frac(L / lambda)}
+    return cmulf(Rp, cf{amp * cs, -amp * sn});
+}
+
+// Tx-leg element coefficients: K * c_m = K * sum_p (the terms of tx_term), one warp per element, lanes
+// over its Tx-leg paths (LOS first); fixed reduction order (lane-strided paths, shuffle tree).
 __global__ void k_cm(DeviceScene S, const float4* __restrict__ elem, int M, Frame fr, AntD tx, WaveD wv, double K,
                      const uint8_t* __restrict__ tx_vis, const int* __restrict__ tx_seq,
                      const int64_t* __restrict__ n_tx_dev, const SeqEntry* __restrict__ seqs,
@@ -1211,43 +1225,23 @@ __global__ void k_cm(DeviceScene S, const float4* __restrict__ elem, int M, Fram
     float are = 0.f, aim = 0.f;
     for (int p = lane - 1; p < n_tx; p += 32) {
         d3 Ts = T;
-        int fa[2] = {-1, -1};
         int k = 0;
+        float3 nf[2] = {f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f)};
+        float2 ef[2] = {make_float2(1.f, 0.f), make_float2(1.f, 0.f)};
         if (p < 0) {
             if (!tx_vis[m]) continue;
         } else {
             const int si = tx_seq[p];
             const int4 info = seqs[si].info;
             k = info.w;
-            fa[0] = info.x;
-            fa[1] = info.y;
+            for (int j = 0; j < k; ++j) {
+                const int f = j == 0 ? info.x : info.y;
+                nf[j] = face_n32(S, f);
+                ef[j] = face_eps32(S, f, wv);
+            }
             Ts = k == 2 ? ld3(seqd[si].S2) : ld3(seqd[si].S1);
         }
-        const d3 d = e - Ts;
-        const double L = sqrt(dot(d, d));
-        const double x = L * wv.inv_lam;
-        const float ph = (float)(x - floor(x));
-        float3 u = to_f(d);                       // arrival direction at the element: the last segment is real
-        u = u * rsqrtf(dot(u, u));
-        cf Rp = cf{1.f, 0.f};
-        if (k >= 1) {
-            const float3 nl = face_n32(S, fa[k - 1]);
-            const float2 el = face_eps32(S, fa[k - 1], wv);
-            Rp = fresnel_f(fabsf(dot(u, nl)), el.x, el.y, wv.tm);
-            if (k == 2) {
-                const float3 n1 = mirror_dir_f(face_n32(S, fa[0]), nl);
-                const float2 e1 = face_eps32(S, fa[0], wv);
-                Rp = cmulf(Rp, fresnel_f(fabsf(dot(u, n1)), e1.x, e1.y, wv.tm));
-            }
-        }
-        float3 dep = u;
-        for (int j = k - 1; j >= 0; --j) dep = mirror_dir_f(dep, face_n32(S, fa[j]));
-        const float Ft = pattern_f(tx.pattern, gt, dot(dep, z));
-        const float Fin = fmaxf(-dot(u, nr), 0.f);  // element pattern max(cos, 0) toward the Tx side
-        const float amp = amp0 * sqrtf(Ft * Fin) / (float)L;
-        float sn, cs;
-        sincospif(2.f * ph, &sn, &cs);            // e^{-j 2 pi frac(L / lambda)}
-        const cf t = cmulf(Rp, cf{amp * cs, -amp * sn});
+        const cf t = tx_term(e, Ts, k, nf, ef, z, nr, gt, amp0, tx.pattern, wv);
         are += t.re;
         aim += t.im;
     }
@@ -1258,12 +1252,72 @@ __global__ void k_cm(DeviceScene S, const float4* __restrict__ elem, int M, Fram
     if (lane == 0) cm[m] = make_float2((float)(K * are), (float)(K * aim));
 }
 
-// Sequence ids of the Tx-leg paths (for the host copy of the path set).
+// Sequence ids of the Tx-leg paths (for the host copy of the path set) and their table kept with the
+// path set (image, face normals and permittivities), in id order.
 __global__ void k_tx_ids(const int* __restrict__ cand, const int64_t* __restrict__ n_dev, int cap,
-                         const SeqEntry* __restrict__ seqs, int64_t* __restrict__ ids)
+                         const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, DeviceScene S, WaveD wv,
+                         int64_t* __restrict__ ids, TxPathD* __restrict__ paths)
 {
     const int n = (int)min(*n_dev, (int64_t)cap);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) ids[i] = seqs[cand[i]].info.z;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int si = cand[i];
+        const int4 info = seqs[si].info;
+        ids[i] = info.z;
+        TxPathD t;
+        t.k = info.w;
+        t.id = info.z;
+        t.img = info.w == 2 ? seqd[si].S2 : seqd[si].S1;
+        for (int j = 0; j < 2; ++j) {
+            const int f = j == 0 ? info.x : info.y;
+            const bool on = j < info.w;
+            const float3 nv = on ? face_n32(S, f) : f3(0.f, 0.f, 0.f);
+            t.n[j] = make_float4(nv.x, nv.y, nv.z, 0.f);
+            t.eps[j] = on ? face_eps32(S, f, wv) : make_float2(1.f, 0.f);
+        }
+        paths[i] = t;
+    }
+}
+
+// Per (element m, Tx-leg path p; p = 0 the direct leg, p >= 1 the kept reflected paths in id order):
+// g[m][p] = Gamma_m K c_mp, the element coefficient restricted to one Tx-leg path (the terms k_cm sums),
+// and the delay of each Tx-leg path at the RIS centre, |T_p - c| / c0 in FP64.
+__global__ void k_cir_coef(const float4* __restrict__ elem, int M, Frame fr, AntD tx, WaveD wv, double K,
+                           const uint8_t* __restrict__ tx_vis, const TxPathD* __restrict__ paths, int n_tx,
+                           const float2* __restrict__ gamma, float2* __restrict__ g, double* __restrict__ tx_delay)
+{
+    const int P = n_tx + 1;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * P) return;
+    const int m = (int)(i / P), p = (int)(i % P);
+    d3 Ts = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
+    int k = 0;
+    float3 nf[2] = {f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f)};
+    float2 ef[2] = {make_float2(1.f, 0.f), make_float2(1.f, 0.f)};
+    if (p > 0) {
+        const TxPathD t = paths[p - 1];
+        k = t.k;
+        Ts = ld3(t.img);
+        for (int j = 0; j < 2; ++j) {
+            nf[j] = f3(t.n[j].x, t.n[j].y, t.n[j].z);
+            ef[j] = t.eps[j];
+        }
+    }
+    if (m == 0) {
+        const d3 dc = fr_c(fr) - Ts;
+        tx_delay[p] = sqrt(dot(dc, dc)) / kC0;
+    }
+    float2 out = make_float2(0.f, 0.f);
+    if (p > 0 || tx_vis[m]) {
+        const float3 z = f3((float)tx.z[0], (float)tx.z[1], (float)tx.z[2]);
+        const float3 nr = f3((float)fr.n[0], (float)fr.n[1], (float)fr.n[2]);
+        const float amp0 = (float)sqrt(2.0 * kEta0 * tx.power * tx.gain);
+        const cf t = tx_term(elem_pos(fr, elem[m]), Ts, k, nf, ef, z, nr, (float)tx.gain, amp0, tx.pattern, wv);
+        const cf c = cf{(float)(K * t.re), (float)(K * t.im)};
+        const float2 gm = gamma[m];
+        const cf v = cmulf(c, cf{gm.x, gm.y});
+        out = make_float2(v.re, v.im);
+    }
+    g[i] = out;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1720,7 +1774,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         c = ps->elem ? ps->cap_m : 0;
         if ((rc = grow(ctx, pool, &ps->elem, &c, M))) return rc;
         ps->cap_m = std::max<int64_t>(ps->cap_m, M);
+        if ((rc = grow(ctx, pool, &ps->tx_vis_dev, &ps->cap_tx_vis, M))) return rc;
     }
+    ps->fr = fr;
+    ps->txa = tx;
+    ps->wv = wv;
+    ps->K = K;
     RISRT_CUDA(ctx, cudaMemcpyAsync(ps->elem, ris->elem, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s));
 
     // --- scratch: sequence tables, candidates, counters
@@ -1877,7 +1936,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         int64_t *flag = L.flag, *pos = L.pos, *tot = L.tot, *env_cnt_tot = L.env_cnt_tot;
         void* scan_tmp = L.scan_tmp;
         Candidates &crx = L.crx, &cenv = L.cenv, &ctx_leg = L.ctx_leg;
-        uint8_t* tx_vis = L.tx_vis;
+        uint8_t* tx_vis = ps->tx_vis_dev;       // kept with the path set (per-path outputs read it)
+        if ((rc = grow(ctx, pool, &ps->tx_paths, &ps->cap_tx_paths, cap))) return rc;
         unsigned long long* counters = L.counters;
         int* flags_dev = L.flags_dev;
         float* c_xyz = L.c_xyz;
@@ -2035,7 +2095,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                               flags_dev + 1)));
         RISRT_KERNEL_ON(ctx, sA, "k_cm", (k_cm<<<nblk((int64_t)M * 32, 128), 128, 0, sA>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand,
                                                                                   ctx_leg.cnt64, tab[0].e, tab[0].d, ps->cm)));
-        RISRT_KERNEL_ON(ctx, sA, "k_tx_ids", (k_tx_ids<<<1, 256, 0, sA>>>(ctx_leg.cand, ctx_leg.cnt64, cap, tab[0].e, L.tx_ids)));
+        RISRT_KERNEL_ON(ctx, sA, "k_tx_ids", (k_tx_ids<<<1, 256, 0, sA>>>(ctx_leg.cand, ctx_leg.cnt64, cap, tab[0].e, tab[0].d, S,
+                                                                         wv, L.tx_ids, ps->tx_paths)));
         // Rx leg (source: RIS centre) and environment paths (source: Tx); their validations use the maps
         const cudaEvent_t maps_ready = sB != s ? ctx->ev[1] : nullptr;
         fork(sC, ctx->ev[5]);
@@ -2103,6 +2164,18 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         return RISRT_OK;
     }
     return fail(ctx, RISRT_ERR_CAPACITY, "too many geometric path candidates per receiver");
+}
+
+// Per-Tx-path element coefficients of a traced path set for one configuration (risrt_eval_cir):
+// g [M][1 + n_tx] complex, tx_delay [1 + n_tx] seconds; on the context's stream.
+int cir_tx_coef(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, float2* g, double* tx_delay)
+{
+    const int n_tx = (int)ps->tx_seq_host.size();
+    const int64_t n = (int64_t)ps->M * (n_tx + 1);
+    RISRT_KERNEL(ctx, "k_cir_coef", (k_cir_coef<<<nblk(n, 128), 128, 0, ctx->stream>>>(
+                                         ps->elem, ps->M, ps->fr, ps->txa, ps->wv, ps->K, ps->tx_vis_dev, ps->tx_paths,
+                                         n_tx, gamma, g, tx_delay)));
+    return RISRT_OK;
 }
 
 }  // namespace risrt

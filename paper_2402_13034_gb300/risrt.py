@@ -46,6 +46,7 @@ _SIGS = {
     "risrt_pathset_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_eval_field_plain": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
+    "risrt_eval_cir": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "risrt_microbench": (C.c_int, [_P, C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P, C.POINTER(_P)]),
     "risrt_amat_wrap": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.POINTER(_P)]),
@@ -342,6 +343,22 @@ class Context:
         n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
         self._check(load().risrt_eval_field_plain(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"), n_cfg,
                                                   _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def eval_cir(self, ps: PathSet, gamma):
+        """RIS channel impulse response for one configuration gamma (complex64 CUDA [M]): returns
+        (taps complex64 [n_rx_paths, n_tx_paths + 1], rx_delay float64 [n_rx_paths], tx_delay float64
+        [n_tx_paths + 1]) as CUDA tensors (entries receiver-major as in PathSet.export)."""
+        import torch
+        st = ps.stats()
+        P = st.n_tx_paths + 1
+        dev = f"cuda:{self.device}"
+        taps = torch.empty((st.n_rx_paths, P), dtype=torch.complex64, device=dev)
+        rxd = torch.empty(st.n_rx_paths, dtype=torch.float64, device=dev)
+        txd = torch.empty(P, dtype=torch.float64, device=dev)
+        self._check(load().risrt_eval_cir(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"),
+                                          _dev_ptr(taps, "torch.complex64"), _dev_ptr(rxd, "torch.float64"),
+                                          _dev_ptr(txd, "torch.float64")))
+        return taps, rxd, txd
 
     def microbench(self, kind: int, iters: int = 4096):
         """Issue rate of one pipe (MB_* kinds): (lane operations per second, ms of the best launch)."""

@@ -409,6 +409,48 @@ def paper_anechoic(grid_step: float = 0.01) -> Workload:
                     np.ones((1, 127), np.complex64) * 1.25, 0, 0, False)
 
 
+def paper_reflective(grid_step: float = 0.01, closeup: bool = False, wall: float = 0.05) -> Workload:
+    """The reflective set-up of Sec. III (Table 2): three metal walls (eps_r 1, sigma 1e7 S/m) of a
+    2 x 2.4 x 1 m room (blocks ``wall`` thick: x = 2 opposite the RIS, y = +-1.2 at the sides; the
+    side x = 0 is the opening holding the RIS), a 0.9 x 0.05 x 1 m metal panel centred (1.55, -0.475,
+    0.5) that blocks the Tx -> Rx line, the 127-element hex RIS (12 cm / 13 pitch, 6.6 mm elements)
+    centred u = (0, 0, 0.5) with normal +x, 23.8 GHz, horn Tx (Gt 19 dB, 10 dBm) at
+    t = (1.86 m, -36 deg, 90 deg) about u aimed at u, vertical monopole Rx. Receivers on z = 11.4 cm
+    over 0.92 <= x <= 1.52, 0.02 <= y <= 0.92 at ``grid_step`` (Fig. 4 c), or with ``closeup`` over
+    1.1 <= x <= 1.3, 0.25 <= y <= 0.45 at 2 mm (Fig. 5). RIS -> Rx reflections up to order 2, no
+    Tx-leg reflections, no environment paths (every multipath component from the RIS, Sec. III).
+    Configuration: each element on (Gamma = 1.25) when its direct Tx -> element -> intended-Rx path
+    phase lies within a quarter turn of zero, else off (Eq. 11 alphabet; a geometric stand-in for the
+    configuration algorithm the paper cites), intended Rx r = (1.4 m, 10 deg, 106 deg) about u."""
+    f = 23.8e9
+    u = np.array([0.0, 0.0, 0.5])
+    mb = _MeshBuilder()
+    mats = [(1.0, 1e7)]
+    mb.box((2.0, -1.2, 0.0), (2.0 + wall, 1.2, 1.0), 0)                 # opposite the RIS
+    mb.box((0.0, -1.2 - wall, 0.0), (2.0 + wall, -1.2, 1.0), 0)         # side walls
+    mb.box((0.0, 1.2, 0.0), (2.0 + wall, 1.2 + wall, 1.0), 0)
+    mb.box((1.1, -0.5, 0.0), (2.0, -0.45, 1.0), 0)                      # blocking panel
+    scene = mb.scene(mats)
+    txp = spherical_to_cartesian(u, 1.86, -36.0, 90.0).astype(np.float32)
+    ris = RIS(hex_layout(6, 0.12 / 13), u.astype(np.float32), np.array([0, 1, 0], np.float32),
+              np.array([0, 0, 1], np.float32), 6.6e-3, 6.6e-3, 0.0, -1)
+    tx = Antenna(txp, orient_towards(txp, u), 0.01, 10 ** 1.9, PATTERN_COS_POW)
+    rx = Antenna(np.zeros(3, np.float32), identity_orient(), 1.0, 1.0, PATTERN_MONOPOLE_QW)
+    if closeup:
+        rx_xyz = linspace_grid(1.1, 1.3, 101, 0.25, 0.45, 101, 0.114)
+    else:
+        nx = int(round((1.52 - 0.92) / grid_step)) + 1
+        ny = int(round((0.92 - 0.02) / grid_step)) + 1
+        rx_xyz = linspace_grid(0.92, 1.52, nx, 0.02, 0.92, ny, 0.114)
+    target = spherical_to_cartesian(u, 1.4, 10.0, 106.0)
+    foc = focus_phase_config(ris, txp, target, f)
+    gam = np.where(np.real(foc) > 0, 1.25, 0.0).astype(np.complex64)
+    name = "paper_reflective_closeup" if closeup else "paper_reflective"
+    w = Workload(name, f, scene, ris, tx, rx, rx_xyz, gam[None], 0, 2, False)
+    w.extra["intended_rx"] = target
+    return w
+
+
 def plate_corridor(n_side: int = 20, grid: int = 8, spacing: float = 0.25, half: float = 60.0) -> Workload:
     """37-element hex RIS (lambda/2, 28 GHz) at the origin facing +y between two stacks of ``n_side``
     large parallel plates (planes x = +-(0.5 + i*spacing), eps_r 3): every receiver has about
@@ -440,4 +482,5 @@ WORKLOADS = {
     "sweep": sweep,
     "office": office,
     "paper_anechoic": paper_anechoic,
+    "paper_reflective": paper_reflective,
 }

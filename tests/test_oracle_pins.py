@@ -692,3 +692,76 @@ def test_ambiguity_only_without_a_robust_failure():
     # well inside: robust
     ok, amb, _ = o.validate((1, 1.5, 1), -1, (1, 0.5, 1), -1, 2)
     assert ok and not amb
+
+
+def test_cir_taps_one_wall_closed_form():
+    """Channel impulse response of the one-wall case: exactly four RIS taps (direct / wall on each
+    leg), each the closed-form sum of its leg pairing over the elements (with an arbitrary
+    configuration), delayed by the travel time through the RIS centre between the image-method end
+    points (|T_p - c| + |R_q - c|) / c0, and the taps plus E0 give E (Sec. II-B, Eq. 9)."""
+    mb = S._MeshBuilder()
+    h = 40.0
+    mb.quad((1.0, -h, -h), (1.0, h, -h), (1.0, h, h), (1.0, -h, h), 0)
+    w = _free()
+    w.scene = mb.scene([(5.3, 0.0)])
+    w.max_order_tx = w.max_order_rx = 1
+    o = O.Oracle(w)
+    R = np.array([0.3, 0.2, 1.5], np.float32).astype(np.float64)
+    rng = np.random.default_rng(12)
+    gam = 1.25 * np.exp(2j * np.pi * rng.random(w.n_elem))
+    taps = o.cir(R.astype(np.float32)[None], gam)[0]
+    assert list(taps["q"]) == [-1, -1, 0, 0] and list(taps["p"]) == [-1, 0, -1, 0]
+    lam = S.C0 / w.freq_hz
+    k = 2 * math.pi / lam
+    e = o.element_positions()
+    T = w.tx.pos.astype(np.float64)
+    c = w.ris.center.astype(np.float64)
+    mir = lambda p: np.array([2.0 - p[0], p[1], p[2]])
+    n2 = math.sqrt(float(np.float32(5.3)))
+
+    def fres(cos_i):
+        sin_i = math.sqrt(max(0.0, 1 - cos_i ** 2))
+        cos_t = math.sqrt(1 - (sin_i / n2) ** 2)
+        return (cos_i - n2 * cos_t) / (cos_i + n2 * cos_t)
+
+    d = float(np.float32(w.ris.dy))
+    G = 4 * math.pi * d * d / lam ** 2
+    for j, (rref, tref) in enumerate([(False, False), (False, True), (True, False), (True, True)]):
+        Ts = mir(T) if tref else T
+        Rs = mir(R) if rref else R
+        a = 0j
+        for m in range(len(e)):
+            rt = np.linalg.norm(e[m] - Ts)
+            rr = np.linalg.norm(Rs - e[m])
+            cin = (Ts - e[m])[2] / rt
+            cout = (Rs - e[m])[2] / rr
+            amp = math.sqrt(2 * ETA0) * math.sqrt(G * cin * cout * d * d / (4 * math.pi)) / rt * lam / (4 * math.pi * rr)
+            f = (fres(abs((e[m] - Ts)[0]) / rt) if tref else 1.0) * (fres(abs((Rs - e[m])[0]) / rr) if rref else 1.0)
+            a += gam[m] * amp * f * np.exp(-1j * k * (rt + rr))
+        assert abs(taps["amp"][j] - a) < 1e-12 * abs(a)
+        tau = (np.linalg.norm(Ts - c) + np.linalg.norm(Rs - c)) / S.C0
+        assert abs(taps["delay"][j] - tau) < 1e-15 * tau + 1e-21
+    f = o.field(R.astype(np.float32)[None])
+    E, _, _ = O.Oracle.evaluate(f, gam)
+    assert abs(taps["amp"].sum() + f["E0"][0] - E[0]) < 1e-13 * abs(E[0])
+
+
+def test_reflective_closeup_fading_period():
+    """The paper's reflective set-up (Sec. III, Table 2): along x through the close-up region of Fig. 5
+    the received power fades with a dominant period of about lambda/2 (Sec. IV-B)."""
+    g = json.load(open(os.path.join(GOLD, "paper_closeup_fading.json")))
+    w = S.paper_reflective(closeup=True)
+    o = O.Oracle(w)
+    lam = S.C0 / w.freq_hz
+    xs = np.arange(g["x_range_m"][0], g["x_range_m"][1] + 1e-9, g["step_m"])
+    yc = 0.5 * sum(g["y_range_m"])
+    line = np.stack([xs, np.full(len(xs), yc), np.full(len(xs), g["rx_height_m"])], 1).astype(np.float32)
+    f = o.field(line)
+    _, P, _ = O.Oracle.evaluate(f, w.gammas[0])
+    spec = np.abs(np.fft.rfft(P - P.mean()))
+    freqs = np.fft.rfftfreq(len(P), g["step_m"])
+    period = 1.0 / freqs[1 + np.argmax(spec[1:])]
+    lo, hi = g["accepted_period_over_lambda"]
+    assert lo * lam <= period <= hi * lam, period / lam
+    # the interference is deep: a range of well over 10 dB along the line
+    assert 10 * np.log10(P.max() / P.min()) > 10
