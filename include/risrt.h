@@ -220,6 +220,21 @@ int risrt_eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma
 int risrt_eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, int32_t n_cfg,
                            float* E_out, float* P_out);
 
+/* Field with strict per-element validation of reflected paths. The paper validates each face sequence
+ * once between the RIS centre and the Rx (and between the Tx and the RIS centre) and lets every element
+ * use the accepted sequences (Sec. II-B); here every element's reflected legs are validated between
+ * the element itself and each end, with the same conditions (reflection points in their faces,
+ * neighbours strictly on the same side of each plane, every segment unblocked; the bounce next to the
+ * element may not lie on a plane through it), and each element's field uses only its own valid legs:
+ *   E = E0 + sum_m Gamma_m K c_m^strict sum_{q valid for m} b_mq,  P = |E|^2 / (2 eta0)   (Eqs. 9, 10)
+ * Arguments as risrt_trace_paths followed by those of risrt_eval_field (gamma [n_cfg][M] complex64,
+ * E_out [n_cfg][n_rx] complex64, P_out [n_cfg][n_rx] float or NULL). Costs about M traces (a one-element
+ * trace per element plus one for E0) and synchronises the stream; it keeps no path set.
+ * Errors as risrt_trace_paths. */
+int risrt_eval_field_strict(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris, const risrt_rxset* rxset,
+                            double freq_hz, int32_t max_order_tx, int32_t max_order_rx, uint32_t flags,
+                            const float* gamma, int32_t n_cfg, float* E_out, float* P_out);
+
 /* Channel impulse response of the RIS part of the field (Sec. II-B: every multipath component that
  * goes through the RIS) for one configuration gamma [M] complex64. Let P = n_tx_paths + 1 (Tx-leg
  * paths: p = 0 the direct leg, p >= 1 the valid reflected Tx-leg sequences in ascending id, as in

@@ -48,7 +48,7 @@ class _Problem(C.Structure):
         ("rx_orient", C.c_float * 9), ("rx_gain", C.c_float), ("rx_pattern", C.c_int32),
         ("freq", C.c_double),
         ("max_order_tx", C.c_int32), ("max_order_rx", C.c_int32), ("env_paths", C.c_int32),
-        ("fresnel_tm", C.c_int32),
+        ("fresnel_tm", C.c_int32), ("strict_elements", C.c_int32),
     ]
 
 
@@ -78,6 +78,9 @@ def _load():
             lib.or_cir.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             lib.or_element_positions.argtypes = [C.c_void_p, C.c_void_p]
+            lib.or_element_paths.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                             C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
+                                             C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
             lib.or_segment_blocked.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                                C.c_void_p]
             lib.or_validate.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
@@ -107,7 +110,7 @@ def set_amb_tol(tol: float) -> None:
 class Oracle:
     """FP64 oracle bound to one workload (scene, RIS, antennas, frequency, orders, flags)."""
 
-    def __init__(self, w, fresnel_tm: bool = False):
+    def __init__(self, w, fresnel_tm: bool = False, strict: bool = False):
         lib = _load()
         self.w = w
         sc, ris = w.scene, w.ris
@@ -138,6 +141,7 @@ class Oracle:
         P.freq = w.freq_hz
         P.max_order_tx, P.max_order_rx = w.max_order_tx, w.max_order_rx
         P.env_paths, P.fresnel_tm = int(w.env_paths), int(fresnel_tm)
+        P.strict_elements = int(strict)
         self._P = P
         self._ctx = lib.or_create(C.byref(P))
         self.F = lib.or_n_faces(self._ctx)
@@ -236,6 +240,26 @@ class Oracle:
                     env=[env[i, : n_env[i]].copy() for i in range(n)],
                     los=los.astype(bool), vis=vis, amb=amb.astype(bool), los_amb=los_amb.astype(bool),
                     vis_amb=vis_amb, amb_seqs=amb_rx, amb_env=amb_env, n_dec=n_dec)
+
+    def element_paths(self, m: int, rx_xyz: np.ndarray, cap: int = 512, amb_cap: int = 256):
+        """Strict mode's path sets of element m (reflected legs validated at the element itself): the
+        valid Tx-leg ids, and per receiver the valid Rx-leg ids, each with the ambiguous decisions, and
+        the number of decisions."""
+        rx = np.ascontiguousarray(rx_xyz, np.float32).reshape(-1, 3)
+        n = len(rx)
+        tx = np.zeros(1 << 16, np.int64)
+        tx_amb = np.zeros(1 << 12, np.int64)
+        n_tx, n_tx_amb, n_dec = np.zeros(1, np.int64), np.zeros(1, np.int64), np.zeros(1, np.int64)
+        seq = np.full((n, cap), -1, np.int64)
+        amb = np.full((n, amb_cap), -1, np.int64)
+        n_seq, n_amb = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        _load().or_element_paths(self._ctx, int(m), _ptr(rx), n, _ptr(tx), len(tx), _ptr(n_tx), _ptr(tx_amb), len(tx_amb),
+                                 _ptr(n_tx_amb), _ptr(seq), cap, _ptr(n_seq), _ptr(amb), amb_cap, _ptr(n_amb), _ptr(n_dec))
+        if (n_seq > cap).any() or (n_amb > amb_cap).any() or n_tx[0] > len(tx) or n_tx_amb[0] > len(tx_amb):
+            raise RuntimeError("oracle path capacity exceeded")
+        return dict(tx_seqs=tx[: int(n_tx[0])].copy(), tx_amb=tx_amb[: int(n_tx_amb[0])].copy(),
+                    seqs=[seq[i, : n_seq[i]].copy() for i in range(n)],
+                    amb_seqs=[amb[i, : n_amb[i]].copy() for i in range(n)], n_dec=int(n_dec[0]))
 
     # --- field --------------------------------------------------------------------------------
     def field(self, rx_xyz: np.ndarray):

@@ -63,6 +63,7 @@ typedef struct {
     float rx_orient[9]; float rx_gain; int32_t rx_pattern;
     double freq;
     int32_t max_order_tx, max_order_rx, env_paths, fresnel_tm;
+    int32_t strict_elements;   /* 1: validate each element's reflected legs at the element itself */
 } or_problem;
 
 typedef struct { double x, y, z; } v3;
@@ -419,6 +420,7 @@ static int coplanar(const or_ctx* C, int a, int b)
 }
 
 static int contains_centre(const or_ctx* C, int f) { return fabs(sdist(C, C->c, f)) < 1e-6; }
+static int contains_pt(const or_ctx* C, int f, v3 p) { return fabs(sdist(C, p, f)) < 1e-6; }
 
 static int decode_seq(const or_ctx* C, int64_t id, int* seq)
 {
@@ -437,6 +439,15 @@ static int seq_allowed(const or_ctx* C, const int* seq, int k, int mode)
     if (mode == 0 && contains_centre(C, seq[k - 1])) return 0;
     if (mode == 1 && contains_centre(C, seq[0])) return 0;
     return 1;
+}
+
+/* The same rule for the legs of one element validated at the element itself (strict mode): the
+   bounce next to the element may not lie on a plane through the element. */
+static int seq_allowed_at(const or_ctx* C, const int* seq, int k, int tx_leg, v3 e)
+{
+    for (int j = 1; j < k; ++j)
+        if (seq[j] == seq[j - 1] || coplanar(C, seq[j], seq[j - 1])) return 0;
+    return !contains_pt(C, tx_leg ? seq[k - 1] : seq[0], e);
 }
 
 /* --------------------------------------------------------------------------------------------
@@ -639,6 +650,28 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
     if (n_tx > cap) n_tx = cap;
     int64_t n_ids = C->P.max_order_rx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_rx >= 1 ? F : 0);
     (void)max_paths;
+    /* strict mode: every element's own valid Tx-leg sequences */
+    const int strict = C->P.strict_elements != 0;
+    int64_t n_tx_ids = C->P.max_order_tx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_tx >= 1 ? F : 0);
+    int64_t* stx_ids = NULL;
+    int64_t* stx_n = NULL;
+    int* stx_amb = NULL;
+    if (strict) {
+        stx_ids = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1) * (size_t)(n_tx_ids > 0 ? n_tx_ids : 1));
+        stx_n = (int64_t*)calloc(M > 0 ? M : 1, sizeof(int64_t));
+        stx_amb = (int*)calloc(M > 0 ? M : 1, sizeof(int));
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int m = 0; m < M; ++m) {
+            for (int64_t id = 0; id < n_tx_ids; ++id) {
+                int seq[2];
+                int k = decode_seq(C, id, seq);
+                v3 pts[4];
+                if (seq_allowed_at(C, seq, k, 1, C->e[m]) &&
+                    validate_seq(C, C->tx, -1, C->e[m], hf, seq, k, &stx_amb[m], pts))
+                    stx_ids[(int64_t)m * n_tx_ids + stx_n[m]++] = id;
+            }
+        }
+    }
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n_rx; ++i) {
         v3 r = vf(rx_xyz + 3 * i);
@@ -668,24 +701,45 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
                 s0 += cabs(v);
             }
         }
+        int64_t* m_rx = strict ? (int64_t*)malloc(sizeof(int64_t) * (n_ids > 0 ? n_ids : 1)) : NULL;
         for (int m = 0; m < M; ++m) {
             double complex a = 0.0;
             double sa = 0.0;
             int rx_direct = !blocked_decision(C, C->e[m], r, hf, -1, &amb);
-            for (int64_t p = -1; p < n_tx; ++p) {           /* p = -1: direct Tx -> e_m */
+            /* the element's reflected legs: validated once at the RIS centre (Sec. II-B), or, in strict
+               mode, between the element itself and each end */
+            const int64_t* mt_ids = tx_ids;
+            int64_t mt_n = n_tx;
+            const int64_t* mr_ids = rx_ids;
+            int mr_n = n_q;
+            if (strict) {
+                mt_ids = stx_ids + (int64_t)m * n_tx_ids;
+                mt_n = stx_n[m];
+                amb |= stx_amb[m];
+                mr_n = 0;
+                for (int64_t id = 0; id < n_ids; ++id) {
+                    int seq[2];
+                    int k = decode_seq(C, id, seq);
+                    v3 pts[4];
+                    if (seq_allowed_at(C, seq, k, 0, C->e[m]) && validate_seq(C, C->e[m], hf, r, -1, seq, k, &amb, pts))
+                        m_rx[mr_n++] = id;
+                }
+                mr_ids = m_rx;
+            }
+            for (int64_t p = -1; p < mt_n; ++p) {           /* p = -1: direct Tx -> e_m */
                 int tseq[2], tk = 0;
                 if (p < 0) {
                     if (!tx_vis[m]) continue;
                 } else {
-                    tk = decode_seq(C, tx_ids[p], tseq);
+                    tk = decode_seq(C, mt_ids[p], tseq);
                 }
                 leg_t gt = leg_by_images(C, C->tx, C->e[m], tseq, tk);
-                for (int q = -1; q < n_q; ++q) {           /* q = -1: direct e_m -> Rx */
+                for (int q = -1; q < mr_n; ++q) {           /* q = -1: direct e_m -> Rx */
                     int rseq[2], rk = 0;
                     if (q < 0) {
                         if (!rx_direct) continue;
                     } else {
-                        rk = decode_seq(C, rx_ids[q], rseq);
+                        rk = decode_seq(C, mr_ids[q], rseq);
                     }
                     leg_t gr = leg_by_images(C, C->e[m], r, rseq, rk);
                     double complex v = ris_term(C, &gt, &gr);
@@ -697,6 +751,7 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
             A[(i * M + m) * 2 + 1] = cimag(a);
             SA[i * M + m] = sa;
         }
+        free(m_rx);
         free(rx_ids);
         E0[2 * i] = creal(e0);
         E0[2 * i + 1] = cimag(e0);
@@ -705,6 +760,67 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
     }
     free(tx_ids);
     free(tx_vis);
+    free(stx_ids);
+    free(stx_n);
+    free(stx_amb);
+    return 0;
+}
+
+/* Strict mode's path sets of element m (its reflected legs validated at the element itself):
+   valid Tx-leg ids (ascending) with per-decision ambiguity, and per receiver its valid Rx-leg ids with
+   the ambiguous ones; n_dec counts the decisions. Layout as or_tx_leg / or_rx_paths. */
+int or_element_paths(const or_ctx* C, int m, const float* rx_xyz, int64_t n_rx, int64_t* tx_out, int64_t tx_cap,
+                     int64_t* n_tx, int64_t* tx_amb_ids, int64_t tx_amb_cap, int64_t* n_tx_amb, int64_t* seq_out,
+                     int32_t cap, int32_t* n_seq, int64_t* amb_ids, int32_t amb_cap, int32_t* n_amb, int64_t* n_dec)
+{
+    int F = C->F, hf = C->P.host_face;
+    v3 e = C->e[m];
+    int64_t n_tx_ids = C->P.max_order_tx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_tx >= 1 ? F : 0);
+    int64_t n = 0, na = 0, nd = 0;
+    for (int64_t id = 0; id < n_tx_ids; ++id) {
+        int seq[2];
+        int k = decode_seq(C, id, seq);
+        if (!seq_allowed_at(C, seq, k, 1, e)) continue;
+        v3 pts[4];
+        int a = 0;
+        ++nd;
+        if (validate_seq(C, C->tx, -1, e, hf, seq, k, &a, pts)) {
+            if (n < tx_cap) tx_out[n] = id;
+            ++n;
+        }
+        if (a) {
+            if (na < tx_amb_cap) tx_amb_ids[na] = id;
+            ++na;
+        }
+    }
+    *n_tx = n;
+    *n_tx_amb = na;
+    int64_t n_ids = C->P.max_order_rx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_rx >= 1 ? F : 0);
+    int64_t nd_rx = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nd_rx)
+    for (int64_t i = 0; i < n_rx; ++i) {
+        v3 r = vf(rx_xyz + 3 * i);
+        int nq = 0, nqa = 0;
+        for (int64_t id = 0; id < n_ids; ++id) {
+            int seq[2];
+            int k = decode_seq(C, id, seq);
+            if (!seq_allowed_at(C, seq, k, 0, e)) continue;
+            v3 pts[4];
+            int a = 0;
+            ++nd_rx;
+            if (validate_seq(C, e, hf, r, -1, seq, k, &a, pts)) {
+                if (nq < cap) seq_out[i * cap + nq] = id;
+                ++nq;
+            }
+            if (a) {
+                if (nqa < amb_cap) amb_ids[i * amb_cap + nqa] = id;
+                ++nqa;
+            }
+        }
+        n_seq[i] = nq;
+        n_amb[i] = nqa;
+    }
+    *n_dec = nd + nd_rx;
     return 0;
 }
 

@@ -589,6 +589,21 @@ int risrt_eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float*
     return eval_field_plain(ctx, ps, (const float2*)gamma, n_cfg, (float2*)E_out, P_out);
 }
 
+int risrt_eval_field_strict(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris, const risrt_rxset* rxset,
+                            double freq_hz, int32_t max_order_tx, int32_t max_order_rx, uint32_t flags, const float* gamma,
+                            int32_t n_cfg, float* E_out, float* P_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!scene || !ris || !rxset || !gamma || !E_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->tx.set || !ctx->rx.set) return fail(ctx, RISRT_ERR_NOT_READY, "antennas not set");
+    if (!(freq_hz > 0) || max_order_tx < 0 || max_order_tx > 2 || max_order_rx < 0 || max_order_rx > 2 || n_cfg < 1 ||
+        (flags & ~(uint32_t)(RISRT_FLAG_ENV_PATHS | RISRT_FLAG_FRESNEL_TM)))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "bad frequency, order, configuration count or flags");
+    if (((uintptr_t)gamma | (uintptr_t)E_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    return eval_field_strict(ctx, scene, ris, rxset, freq_hz, max_order_tx, max_order_rx, flags, (const float2*)gamma,
+                             n_cfg, (float2*)E_out, P_out);
+}
+
 int risrt_eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, float* taps_out, double* rx_delay_out,
                    double* tx_delay_out)
 {

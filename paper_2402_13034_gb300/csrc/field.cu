@@ -166,13 +166,14 @@ k_eval_em(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, cons
 }
 
 // One warp per receiver; lanes walk the flattened (path, element) index space so small arrays keep
-// every lane busy. NC configurations share each b_mq.
+// every lane busy. NC configurations share each b_mq. Configuration c's Gamma_m is gamma[c gstride + m];
+// with accum the RIS sum is added to E (E0 and P untouched).
 template <int PAT, int NC>
 __global__ void __launch_bounds__(32 * kEvalWarps)
 k_eval(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const uint32_t* __restrict__ vis, int W,
        const float4* __restrict__ elem, const float2* __restrict__ cm, const float2* __restrict__ gamma,
        int M, int64_t n_rx, int cfg0, int n_cfg, const float2* __restrict__ E0, float2* __restrict__ E,
-       float* __restrict__ P, float inv_lam, float gr, int tm, float inv_2eta0)
+       float* __restrict__ P, float inv_lam, float gr, int tm, float inv_2eta0, int gstride, bool accum)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = blockIdx.x * (int64_t)kEvalWarps + (threadIdx.x >> 5);
@@ -195,7 +196,7 @@ k_eval(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const u
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 if (c < n_cfg) {
-                    const float2 g = gamma[(int64_t)(cfg0 + c) * M + m];
+                    const float2 g = gamma[(int64_t)(cfg0 + c) * gstride + m];
                     acc[c].re += g.x * cb.re - g.y * cb.im;
                     acc[c].im += g.x * cb.im + g.y * cb.re;
                 }
@@ -216,12 +217,17 @@ k_eval(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const u
         }
     }
     if (lane == 0) {
-        const float2 e0 = E0[r];
+        const float2 e0 = accum ? make_float2(0.f, 0.f) : E0[r];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             if (c < n_cfg) {
+                const int64_t oi = (int64_t)(cfg0 + c) * n_rx + r;
+                if (accum) {
+                    const float2 prev = E[oi];
+                    E[oi] = make_float2(prev.x + acc[c].re, prev.y + acc[c].im);
+                    continue;
+                }
                 float er = e0.x + acc[c].re, ei = e0.y + acc[c].im;
-                int64_t oi = (int64_t)(cfg0 + c) * n_rx + r;
                 E[oi] = make_float2(er, ei);
                 if (P) P[oi] = (er * er + ei * ei) * inv_2eta0;
             }
@@ -370,7 +376,8 @@ int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int
         else                                                                                                  \
             RISRT_KERNEL(ctx, "k_eval", (k_eval<PAT, NCV><<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(          \
                                             ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, gamma, ps->M, \
-                                            ps->n_rx, c0, nc, ps->E0, E, P, inv_lam, ps->rx_gain, tm, inv_2eta0))); \
+                                            ps->n_rx, c0, nc, ps->E0, E, P, inv_lam, ps->rx_gain, tm, inv_2eta0, \
+                                            ps->M, false)));                                                  \
     } while (0)
 #define RISRT_EVAL_NC(PAT)           \
     do {                             \
@@ -385,6 +392,32 @@ int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int
         }
 #undef RISRT_EVAL_NC
 #undef RISRT_EVAL
+    }
+    return RISRT_OK;
+}
+
+int eval_field_accum(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int gstride, int n_cfg, float2* E)
+{
+    const float inv_lam = (float)(ps->freq / kC0);
+    const int tm = (ps->flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
+    const unsigned grid = nblk(ps->n_rx, kEvalWarps);
+    for (int c0 = 0; c0 < n_cfg; c0 += kMaxCfgPerPass) {
+        const int nc = std::min(kMaxCfgPerPass, n_cfg - c0);
+        auto launch = [&](auto kern) -> int {
+            RISRT_KERNEL(ctx, "k_eval", (kern<<<grid, 32 * kEvalWarps, 0, ctx->stream>>>(
+                                            ps->rec, ps->rx_off, ps->vis, ps->W, ps->elem, ps->cm, gamma, ps->M, ps->n_rx,
+                                            c0, nc, ps->E0, E, nullptr, inv_lam, ps->rx_gain, tm, 0.f, gstride, true)));
+            return RISRT_OK;
+        };
+        int rc;
+#define RISRT_ACC_NC(PAT) (nc == 1 ? launch(k_eval<PAT, 1>) : nc == 2 ? launch(k_eval<PAT, 2>) : launch(k_eval<PAT, 4>))
+        switch (ps->rx_pattern) {
+            case RISRT_PATTERN_COS_POW: rc = RISRT_ACC_NC(RISRT_PATTERN_COS_POW); break;
+            case RISRT_PATTERN_MONOPOLE_QW: rc = RISRT_ACC_NC(RISRT_PATTERN_MONOPOLE_QW); break;
+            default: rc = RISRT_ACC_NC(RISRT_PATTERN_ISO); break;
+        }
+#undef RISRT_ACC_NC
+        if (rc) return rc;
     }
     return RISRT_OK;
 }

@@ -235,6 +235,9 @@ struct risrt_ris {
     int host_face = -1;
     float4* elem = nullptr;      // [M] (a_m, b_m, a^2 + b^2, 0)
     std::vector<float> uv_host;  // [M][2]
+    // a RIS the library makes for one element (strict mode) is centred exactly at the element
+    bool exact_center = false;
+    double center_d[3] = {0.0, 0.0, 0.0};
 };
 
 struct risrt_rxset {
@@ -393,6 +396,11 @@ int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0);
 int eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
 int eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, float2* taps, double* rx_delay, double* tx_delay);
 int cir_tx_coef(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, float2* g, double* tx_delay);
+int strict_tx_cm(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, double freq, int max_tx, uint32_t flags,
+                 float2* cm);
+int eval_field_accum(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int gstride, int n_cfg, float2* E);
+int eval_field_strict(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rxs, double freq,
+                      int max_tx, int max_rx, uint32_t flags, const float2* gamma, int n_cfg, float2* E, float* P);
 int microbench(risrt_ctx* ctx, int kind, int iters, double* ops_per_s, double* ms);
 size_t grad_workspace_bytes(int n_t, int B, int M, int precision);
 int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes);

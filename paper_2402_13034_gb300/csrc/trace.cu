@@ -1320,6 +1320,79 @@ __global__ void k_cir_coef(const float4* __restrict__ elem, int M, Frame fr, Ant
     g[i] = out;
 }
 
+// Strict mode, Tx leg: every (element m, allowed Tx-leg sequence si) decided in FP64 between the Tx and
+// the element itself (reflection points in their faces, back-trace parameters in (0, 1), neighbours on
+// the same side of each plane, every segment unblocked); the bounce next to the element may not lie on
+// a plane through it. Elements run fastest, so the threads of a warp share a sequence.
+__global__ void k_tx_strict(DeviceScene S, const float4* __restrict__ elem, int M, Frame fr, AntD tx, int host_face,
+                            float tol_base, const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd,
+                            int n_seq, int W, uint32_t* __restrict__ mask, unsigned long long* refines, int* err)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_seq * M) return;
+    const int m = (int)(i % M), si = (int)(i / M);
+    const int4 info = seqs[si].info;
+    const int k = info.w;
+    const int fa[2] = {info.x, info.y};
+    const d3 e = elem_pos(fr, elem[m]);
+    if (contains_point(S.faces[fa[k - 1]], e)) return;
+    const d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
+    d3 pts[4];
+    if (!seq_geom_fp64(S, T, e, info, seqd[si], pts)) return;
+    for (int j = 0; j <= k; ++j) {
+        const int ign0 = j == 0 ? -1 : fa[j - 1];
+        const int ign1 = j == k ? host_face : fa[j];
+        if (seg_blocked(S, pts[j], pts[j + 1], ign0, ign1, tol_base, refines, err)) return;
+    }
+    atomicOr(&mask[(int64_t)si * W + (m >> 5)], 1u << (m & 31));
+}
+
+// Strict mode's K c_m: the direct Tx leg if unblocked plus every Tx-leg sequence valid for element m
+// (mask bit m), one warp per element, lanes over the sequences, fixed reduction order.
+__global__ void k_cm_strict(DeviceScene S, const float4* __restrict__ elem, int M, Frame fr, AntD tx, WaveD wv, double K,
+                            int host_face, float tol_base, const SeqEntry* __restrict__ seqs,
+                            const SeqEntryD* __restrict__ seqd, int n_seq, int W, const uint32_t* __restrict__ mask,
+                            float2* __restrict__ cm, unsigned long long* refines, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (m >= M) return;
+    const d3 e = elem_pos(fr, elem[m]);
+    const d3 T = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
+    const float3 z = f3((float)tx.z[0], (float)tx.z[1], (float)tx.z[2]);
+    const float3 nr = f3((float)fr.n[0], (float)fr.n[1], (float)fr.n[2]);
+    const float gt = (float)tx.gain;
+    const float amp0 = (float)sqrt(2.0 * kEta0 * tx.power * tx.gain);
+    float are = 0.f, aim = 0.f;
+    for (int p = lane - 1; p < n_seq; p += 32) {
+        d3 Ts = T;
+        int k = 0;
+        float3 nf[2] = {f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f)};
+        float2 ef[2] = {make_float2(1.f, 0.f), make_float2(1.f, 0.f)};
+        if (p < 0) {
+            if (seg_blocked(S, T, e, -1, host_face, tol_base, refines, err)) continue;
+        } else {
+            if (!((mask[(int64_t)p * W + (m >> 5)] >> (m & 31)) & 1u)) continue;
+            const int4 info = seqs[p].info;
+            k = info.w;
+            for (int j = 0; j < k; ++j) {
+                const int f = j == 0 ? info.x : info.y;
+                nf[j] = face_n32(S, f);
+                ef[j] = face_eps32(S, f, wv);
+            }
+            Ts = k == 2 ? ld3(seqd[p].S2) : ld3(seqd[p].S1);
+        }
+        const cf t = tx_term(e, Ts, k, nf, ef, z, nr, gt, amp0, tx.pattern, wv);
+        are += t.re;
+        aim += t.im;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        are += __shfl_down_sync(0xffffffffu, are, o);
+        aim += __shfl_down_sync(0xffffffffu, aim, o);
+    }
+    if (lane == 0) cm[m] = make_float2((float)(K * are), (float)(K * aim));
+}
+
 // ------------------------------------------------------------------------------------------------
 // Path records (FP64 reference quantities per (Rx, path)) and E0 = LOS + environment paths.
 // ------------------------------------------------------------------------------------------------
@@ -1669,6 +1742,45 @@ static int side_streams(risrt_ctx* ctx)
     return RISRT_OK;
 }
 
+// Frame of the RIS (its exact FP64 centre when it has one), the antennas, the wave and the RIS
+// constant K = sqrt(G dy dz / 4 pi) lambda / 4 pi (G from the element size unless given).
+static void trace_params(const risrt_ctx* ctx, const risrt_ris* ris, double freq, uint32_t flags, Frame& fr, AntD& tx,
+                         AntD& rxa, WaveD& wv, double& K)
+{
+    d3 t1 = D3(ris->t1[0], ris->t1[1], ris->t1[2]), t2 = D3(ris->t2[0], ris->t2[1], ris->t2[2]);
+    d3 nn = cross(t1, t2);
+    nn = nn * (1.0 / norm(nn));
+    for (int k = 0; k < 3; ++k) {
+        fr.c[k] = ris->exact_center ? ris->center_d[k] : (double)ris->center[k];
+        fr.t1[k] = ris->t1[k];
+        fr.t2[k] = ris->t2[k];
+    }
+    fr.n[0] = nn.x; fr.n[1] = nn.y; fr.n[2] = nn.z;
+    auto mk_ant = [](const Antenna& a) {
+        AntD o;
+        double z[3] = {a.orient[6], a.orient[7], a.orient[8]};
+        double zn = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+        for (int k = 0; k < 3; ++k) {
+            o.pos[k] = a.pos[k];
+            o.z[k] = z[k] / zn;
+        }
+        o.power = a.power_w;
+        o.gain = a.gain_lin;
+        o.pattern = a.pattern;
+        return o;
+    };
+    tx = mk_ant(ctx->tx);
+    rxa = mk_ant(ctx->rx);
+    wv.lam = kC0 / freq;
+    wv.k = 2.0 * kPi / wv.lam;
+    wv.omega = 2.0 * kPi * freq;
+    wv.inv_lam = 1.0 / wv.lam;
+    wv.inv_we = (float)(1.0 / (wv.omega * kEps0));
+    wv.tm = (flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
+    double G = ris->elem_gain > 0 ? (double)ris->elem_gain : 4.0 * kPi * (double)ris->dy * (double)ris->dz / (wv.lam * wv.lam);
+    K = sqrt(G * (double)ris->dy * (double)ris->dz / (4.0 * kPi)) * wv.lam / (4.0 * kPi);
+}
+
 int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rxs, double freq,
                 int max_tx, int max_rx, uint32_t flags, risrt_pathset* ps)
 {
@@ -1687,39 +1799,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
 
     // frame, antennas, wave
     Frame fr;
-    d3 t1 = D3(ris->t1[0], ris->t1[1], ris->t1[2]), t2 = D3(ris->t2[0], ris->t2[1], ris->t2[2]);
-    d3 nn = cross(t1, t2);
-    nn = nn * (1.0 / norm(nn));
-    for (int k = 0; k < 3; ++k) {
-        fr.c[k] = ris->center[k];
-        fr.t1[k] = ris->t1[k];
-        fr.t2[k] = ris->t2[k];
-    }
-    fr.n[0] = nn.x; fr.n[1] = nn.y; fr.n[2] = nn.z;
-    auto mk_ant = [](const Antenna& a) {
-        AntD o;
-        double z[3] = {a.orient[6], a.orient[7], a.orient[8]};
-        double zn = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
-        for (int k = 0; k < 3; ++k) {
-            o.pos[k] = a.pos[k];
-            o.z[k] = z[k] / zn;
-        }
-        o.power = a.power_w;
-        o.gain = a.gain_lin;
-        o.pattern = a.pattern;
-        return o;
-    };
-    AntD tx = mk_ant(ctx->tx), rxa = mk_ant(ctx->rx);
+    AntD tx, rxa;
     WaveD wv;
-    wv.lam = kC0 / freq;
-    wv.k = 2.0 * kPi / wv.lam;
-    wv.omega = 2.0 * kPi * freq;
-    wv.inv_lam = 1.0 / wv.lam;
-    wv.inv_we = (float)(1.0 / (wv.omega * kEps0));
-    wv.tm = (flags & RISRT_FLAG_FRESNEL_TM) ? 1 : 0;
-    double G = ris->elem_gain > 0 ? (double)ris->elem_gain : 4.0 * kPi * (double)ris->dy * (double)ris->dz / (wv.lam * wv.lam);
-    double K = sqrt(G * (double)ris->dy * (double)ris->dz / (4.0 * kPi)) * wv.lam / (4.0 * kPi);
-
+    double K;
+    trace_params(ctx, ris, freq, flags, fr, tx, rxa, wv, K);
     float ext = sc->scene_extent;
     for (int k = 0; k < 3; ++k) {
         ext = std::max(ext, std::fabs(ctx->tx.pos[k]));
@@ -2175,6 +2258,104 @@ int cir_tx_coef(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, fl
     RISRT_KERNEL(ctx, "k_cir_coef", (k_cir_coef<<<nblk(n, 128), 128, 0, ctx->stream>>>(
                                          ps->elem, ps->M, ps->fr, ps->txa, ps->wv, ps->K, ps->tx_vis_dev, ps->tx_paths,
                                          n_tx, gamma, g, tx_delay)));
+    return RISRT_OK;
+}
+
+// Strict mode's K c_m of every element (risrt_eval_field_strict): the Tx-leg sequence table from the Tx
+// (no exclusion by the RIS centre; each element applies its own), every (element, sequence) decided in
+// FP64 at the element, the valid terms summed. Synchronises the stream (the table size sizes the work).
+int strict_tx_cm(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, double freq, int max_tx, uint32_t flags,
+                 float2* cm)
+{
+    cudaStream_t s = ctx->stream;
+    const DeviceScene S = sc->dev();
+    const int F = sc->n_faces, M = ris->M, W = (M + 31) / 32;
+    Frame fr;
+    AntD tx, rxa;
+    WaveD wv;
+    double K;
+    trace_params(ctx, ris, freq, flags, fr, tx, rxa, wv, K);
+    float ext = sc->scene_extent;
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, std::max(std::fabs(ctx->tx.pos[k]), std::fabs(ris->center[k])));
+    const float tol_base = 4e-6f * (1.f + 3.f * ext);
+    if (sc->n_tris == 0) max_tx = 0;
+    const int64_t n_ids = max_tx >= 2 ? (int64_t)F + (int64_t)F * F : (max_tx >= 1 ? F : 0);
+    void *flagb = nullptr, *posb = nullptr, *tmp = nullptr, *tab = nullptr, *tabd = nullptr, *maskb = nullptr, *small = nullptr;
+    auto release = [&]() {
+        cudaStreamSynchronize(s);
+        for (void* q : {flagb, posb, tmp, tab, tabd, maskb, small}) ctx_free(ctx, q);
+    };
+#define RISRT_STRICT_CUDA(call)                                   \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) {                                  \
+            release();                                            \
+            return cuda_fail(ctx, _e, #call);                     \
+        }                                                         \
+    } while (0)
+    RISRT_STRICT_CUDA(ctx_malloc(ctx, &small, 64));
+    unsigned long long* refines = (unsigned long long*)small;
+    int* err = (int*)((char*)small + 16);
+    RISRT_STRICT_CUDA(cudaMemsetAsync(small, 0, 64, s));
+    int64_t n_seq = 0;
+    if (n_ids > 0) {
+        RISRT_STRICT_CUDA(ctx_malloc(ctx, &flagb, sizeof(int64_t) * n_ids));
+        RISRT_STRICT_CUDA(ctx_malloc(ctx, &posb, sizeof(int64_t) * (n_ids + 1)));
+        RISRT_STRICT_CUDA(ctx_malloc(ctx, &tmp, scan_temp_bytes(std::max<int64_t>(n_ids, 2))));
+        int64_t* flag = (int64_t*)flagb;
+        int64_t* pos = (int64_t*)posb;
+        auto allowed = [&]() -> int {     // launch failures return here, so release() still runs
+            RISRT_KERNEL(ctx, "k_seq_allowed", (k_seq_allowed<<<nblk(n_ids, 256), 256, 0, s>>>(S, n_ids, 2, fr, D3(tx.pos[0], tx.pos[1], tx.pos[2]),
+                                                                                             1e-4f * (1.f + ext), flag)));
+            return RISRT_OK;
+        };
+        auto count = [&]() -> int {
+            RISRT_KERNEL(ctx, "k_seq_count", (k_seq_count<<<1, 32, 0, s>>>(flag, pos, n_ids, pos + n_ids)));
+            return RISRT_OK;
+        };
+        int lrc = allowed();
+        if (!lrc) RISRT_STRICT_CUDA(exclusive_scan_i64(flag, pos, n_ids, tmp, s));
+        if (!lrc) lrc = count();
+        if (lrc) {
+            release();
+            return lrc;
+        }
+        RISRT_STRICT_CUDA(cudaMemcpyAsync(&n_seq, pos + n_ids, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RISRT_STRICT_CUDA(cudaStreamSynchronize(s));
+        if (n_seq > 0) {
+            RISRT_STRICT_CUDA(ctx_malloc(ctx, &tab, sizeof(SeqEntry) * n_seq));
+            RISRT_STRICT_CUDA(ctx_malloc(ctx, &tabd, sizeof(SeqEntryD) * n_seq));
+            RISRT_STRICT_CUDA(ctx_malloc(ctx, &maskb, sizeof(uint32_t) * n_seq * W));
+            RISRT_STRICT_CUDA(cudaMemsetAsync(maskb, 0, sizeof(uint32_t) * n_seq * W, s));
+            auto build = [&]() -> int {
+                RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(n_ids, 256), 256, 0, s>>>(S, n_ids, flag, pos, D3(tx.pos[0], tx.pos[1], tx.pos[2]),
+                                                                                             (SeqEntry*)tab, (SeqEntryD*)tabd)));
+                RISRT_KERNEL(ctx, "k_tx_strict", (k_tx_strict<<<nblk(n_seq * M, 128), 128, 0, s>>>(
+                                                     S, ris->elem, M, fr, tx, ris->host_face, tol_base, (const SeqEntry*)tab,
+                                                     (const SeqEntryD*)tabd, (int)n_seq, W, (uint32_t*)maskb, refines, err)));
+                return RISRT_OK;
+            };
+            if ((lrc = build())) {
+                release();
+                return lrc;
+            }
+        }
+    }
+    auto coef = [&]() -> int {
+        RISRT_KERNEL(ctx, "k_cm_strict", (k_cm_strict<<<nblk((int64_t)M * 32, 128), 128, 0, s>>>(
+                                             S, ris->elem, M, fr, tx, wv, K, ris->host_face, tol_base, (const SeqEntry*)tab,
+                                             (const SeqEntryD*)tabd, (int)n_seq, W, (const uint32_t*)maskb, cm, refines, err)));
+        return RISRT_OK;
+    };
+    if (int crc = coef()) {
+        release();
+        return crc;
+    }
+    int h_err = 0;
+    RISRT_STRICT_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    release();
+#undef RISRT_STRICT_CUDA
+    if (h_err) return fail(ctx, RISRT_ERR_CAPACITY, "BVH traversal stack overflow");
     return RISRT_OK;
 }
 

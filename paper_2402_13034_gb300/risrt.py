@@ -47,6 +47,8 @@ _SIGS = {
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_eval_field_plain": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "risrt_eval_cir": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "risrt_eval_field_strict": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint32, _P, C.c_int32,
+                                          _P, _P]),
     "risrt_microbench": (C.c_int, [_P, C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P, C.POINTER(_P)]),
     "risrt_amat_wrap": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.POINTER(_P)]),
@@ -343,6 +345,16 @@ class Context:
         n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
         self._check(load().risrt_eval_field_plain(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"), n_cfg,
                                                   _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def eval_field_strict(self, scene: Scene, ris: RIS, rxset: RxSet, freq_hz: float, max_order_tx: int,
+                          max_order_rx: int, flags: int, gamma, E_out, P_out=None):
+        """The field with every element's reflected legs validated at the element itself (strict mode);
+        gamma complex64 CUDA [C, M], E_out complex64 [C, n_rx], P_out float32 [C, n_rx] or None."""
+        n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
+        self._check(load().risrt_eval_field_strict(self._ptr, scene.ptr, ris.ptr, rxset.ptr, float(freq_hz),
+                                                   int(max_order_tx), int(max_order_rx), int(flags),
+                                                   _dev_ptr(gamma, "torch.complex64"), n_cfg,
+                                                   _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
 
     def eval_cir(self, ps: PathSet, gamma):
         """RIS channel impulse response for one configuration gamma (complex64 CUDA [M]): returns

@@ -765,3 +765,82 @@ def test_reflective_closeup_fading_period():
     assert lo * lam <= period <= hi * lam, period / lam
     # the interference is deep: a range of well over 10 dB along the line
     assert 10 * np.log10(P.max() / P.min()) > 10
+
+
+@pytest.mark.parametrize("leg", ["rx", "tx"])
+def test_strict_element_validation_finite_wall(leg):
+    """Strict mode (each element's reflected legs validated at the element itself, instead of once at
+    the RIS centre as in Sec. II-B): a finite wall x = 1 whose top edge splits the elements' own
+    reflection points on one leg. Each element's validity comes from brute-force Fermat minimisation
+    over the wall plane; the strict channel row equals the closed form over the valid pairings per
+    element, the centre-validated row the closed form with the centre's validity for every element."""
+    lam = S.C0 / 28e9
+    k0 = 2 * math.pi / lam
+    T = np.array([0.0, -1.5, 2.0], np.float32).astype(np.float64)
+    R = np.array([0.3, 0.2, 1.5], np.float32).astype(np.float64)
+    base = _free()
+    e = O.Oracle(base).element_positions()
+    c = base.ris.center.astype(np.float64)
+
+    def fermat(a, b):
+        f = lambda p: np.linalg.norm(np.array([1.0, p[0], p[1]]) - a) + np.linalg.norm(b - np.array([1.0, p[0], p[1]]))
+        x0 = [0.5 * (a[1] + b[1]), 0.5 * (a[2] + b[2])]
+        res = minimize(f, x0=x0, method="Nelder-Mead", options=dict(xatol=1e-12, fatol=1e-14, maxiter=40000))
+        return res.x
+    end = R if leg == "rx" else T
+    zs = np.array([fermat(em, end)[1] for em in e])
+    zc = fermat(c, end)[1]
+    rows = np.unique(np.round(zs, 5))                   # elements of one hex row share a height
+    mid = len(rows) // 2
+    z1 = float(np.float32(0.5 * (rows[mid - 1] + rows[mid])))   # edge between two rows
+    assert np.min(np.abs(zs - z1)) > 1e-4
+    mb = S._MeshBuilder()
+    mb.quad((1.0, -40.0, -40.0), (1.0, 40.0, -40.0), (1.0, 40.0, z1), (1.0, -40.0, z1), 0)
+    w = _free()
+    w.scene = mb.scene([(5.3, 0.0)])
+    w.max_order_tx = w.max_order_rx = 1
+    other = T if leg == "rx" else R
+    other_in = [fermat(em, other)[1] <= z1 for em in e]      # the other leg's validity per element
+
+    mir = lambda p: np.array([2.0 - p[0], p[1], p[2]])
+    n2 = math.sqrt(float(np.float32(5.3)))
+
+    def fres(cos_i):
+        sin_i = math.sqrt(max(0.0, 1 - cos_i ** 2))
+        cos_t = math.sqrt(1 - (sin_i / n2) ** 2)
+        return (cos_i - n2 * cos_t) / (cos_i + n2 * cos_t)
+
+    d = float(np.float32(w.ris.dy))
+    G = 4 * math.pi * d * d / lam ** 2
+
+    def row(valid_leg, valid_other):
+        out = np.zeros(len(e), complex)
+        for m in range(len(e)):
+            tx_ok = valid_leg[m] if leg == "tx" else valid_other[m]
+            rx_ok = valid_leg[m] if leg == "rx" else valid_other[m]
+            for Ts, tref in ((T, False), (mir(T), True)):
+                if tref and not tx_ok:
+                    continue
+                for Rs, rref in ((R, False), (mir(R), True)):
+                    if rref and not rx_ok:
+                        continue
+                    rt = np.linalg.norm(e[m] - Ts)
+                    rr = np.linalg.norm(Rs - e[m])
+                    cin, cout = (Ts - e[m])[2] / rt, (Rs - e[m])[2] / rr
+                    amp = math.sqrt(2 * ETA0) * math.sqrt(G * cin * cout * d * d / (4 * math.pi)) / rt * lam / (4 * math.pi * rr)
+                    f = (fres(abs((e[m] - Ts)[0]) / rt) if tref else 1.0) * (fres(abs((Rs - e[m])[0]) / rr) if rref else 1.0)
+                    out[m] += amp * f * np.exp(-1j * k0 * (rt + rr))
+        return out
+
+    strict_valid = zs <= z1
+    A_strict = O.Oracle(w, strict=True).field(R.astype(np.float32)[None])
+    A_centre = O.Oracle(w).field(R.astype(np.float32)[None])
+    assert not A_strict["amb"][0] and not A_centre["amb"][0]
+    exp_s = row(strict_valid, other_in)
+    centre_other = [fermat(c, other)[1] <= z1] * len(e)
+    exp_c = row([zc <= z1] * len(e), centre_other)
+    scale = np.max(np.abs(exp_s))
+    assert np.max(np.abs(A_strict["A"][0] - exp_s)) < 1e-11 * scale
+    assert np.max(np.abs(A_centre["A"][0] - exp_c)) < 1e-11 * scale
+    assert 0 < strict_valid.sum() < len(e)
+    assert np.max(np.abs(exp_s - exp_c)) > 1e-3 * scale
