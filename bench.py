@@ -679,10 +679,12 @@ def main():
     roof_field = None
     if "k_eval" in prof:
         ev_ms = prof["k_eval"][0] / n_prof_steps
-        mufu_ops = n_cfg * (u0 * EVAL_MUFU_PER_UNIT + u1 * (EVAL_MUFU_PER_UNIT + EVAL_MUFU_PER_BOUNCE)
-                            + u2 * (EVAL_MUFU_PER_UNIT + 2 * EVAL_MUFU_PER_BOUNCE))
-        fp32_ops = n_cfg * (u0 * EVAL_FP32_PER_UNIT + u1 * (EVAL_FP32_PER_UNIT + EVAL_FP32_PER_BOUNCE)
-                            + u2 * (EVAL_FP32_PER_UNIT + 2 * EVAL_FP32_PER_BOUNCE))
+        # the term b_mq of a (receiver, element, path) is computed once and shared by every configuration;
+        # each configuration adds one complex multiply-accumulate per (receiver, element)
+        mufu_ops = (u0 * EVAL_MUFU_PER_UNIT + u1 * (EVAL_MUFU_PER_UNIT + EVAL_MUFU_PER_BOUNCE)
+                    + u2 * (EVAL_MUFU_PER_UNIT + 2 * EVAL_MUFU_PER_BOUNCE))
+        fp32_ops = (u0 * EVAL_FP32_PER_UNIT + u1 * (EVAL_FP32_PER_UNIT + EVAL_FP32_PER_BOUNCE)
+                    + u2 * (EVAL_FP32_PER_UNIT + 2 * EVAL_FP32_PER_BOUNCE)) + n_cfg * st.n_rx * st.M * 4
         units_eval = (u0 + u1 + u2) * n_cfg
         t_mufu = mufu_ops / mpeaks["mufu"]
         t_fp32 = fp32_ops / mpeaks["ffma"]

@@ -472,23 +472,33 @@ int or_tx_leg(const or_ctx* C, int64_t* seq_out, int64_t cap, int64_t* n_seq, ui
         ++nd;
     }
     int64_t n_ids = C->P.max_order_tx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_tx >= 1 ? F : 0);
+    /* every sequence decided independently (in parallel), then listed in ascending id order;
+       state: bit 0 allowed, bit 1 valid, bit 2 ambiguous */
+    uint8_t* state = (uint8_t*)calloc(n_ids > 0 ? (size_t)n_ids : 1, 1);
+#pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t id = 0; id < n_ids; ++id) {
         int seq[2];
         int k = decode_seq(C, id, seq);
         if (!seq_allowed(C, seq, k, 0)) continue;
         v3 pts[4];
         int a = 0;
+        int ok = validate_seq(C, C->tx, -1, C->c, hf, seq, k, &a, pts);
+        state[id] = (uint8_t)(1 | (ok ? 2 : 0) | (a ? 4 : 0));
+    }
+    for (int64_t id = 0; id < n_ids; ++id) {
+        if (!(state[id] & 1)) continue;
         ++nd;
-        if (validate_seq(C, C->tx, -1, C->c, hf, seq, k, &a, pts)) {
+        if (state[id] & 2) {
             if (n < cap) seq_out[n] = id;
             ++n;
         }
-        if (a) {
+        if (state[id] & 4) {
             if (amb_ids && na < amb_cap) amb_ids[na] = id;
             ++na;
+            amb = 1;
         }
-        amb |= a;
     }
+    free(state);
     *n_seq = n;
     *amb_out = amb;
     if (n_amb) *n_amb = na;

@@ -32,7 +32,10 @@ __device__ __forceinline__ cf bounce_factor(float c, float er, float ei, bool tm
     return fresnel_f(c, er, ei, tm);
 }
 
-// b_mq for one (path record, element) pair.
+// b_mq for one (path record, element) pair. Paths whose bounces are all lossless dielectrics under the
+// TE coefficient (kRecLosslessTE) keep R real: per bounce c = |(w - u).n'| / L, s = sqrt(eps_r - 1 + c^2),
+// R *= (c - s)^2 / (1 - eps_r), which equals (c - s) / (c + s) since c^2 - s^2 = 1 - eps_r; the branch is
+// uniform across a warp (its lanes share the path record).
 template <int PAT>
 __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_lam, float gr, bool tm)
 {
@@ -48,9 +51,19 @@ __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_
     } else {
         amp *= sqrt_approx(gr);
     }
+    const int kk = __float_as_int(p.a.y);
+    const int k = kk & 3;
     cf R = cf{amp, 0.f};
-    const int k = __float_as_int(p.a.y);
-    if (k >= 1) {
+    if (kk & kRecLosslessTE) {
+        const float c1 = fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) * iL;
+        const float d1 = c1 - sqrt_approx(fmaxf(fmaf(c1, c1, p.a.z), 0.f));
+        R.re *= d1 * d1 * p.a.w;
+        if (k == 2) {
+            const float c2 = fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) * iL;
+            const float d2 = c2 - sqrt_approx(fmaxf(fmaf(c2, c2, p.n1.w), 0.f));
+            R.re *= d2 * d2 * p.n2.w;
+        }
+    } else if (k >= 1) {
         float c1 = fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) * iL;
         R = cmulf(R, bounce_factor(c1, p.a.z, p.a.w, tm));
         if (k == 2) {
@@ -63,7 +76,8 @@ __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_
     x -= rintf(x);
     float sn, cs;
     __sincosf(6.28318530717958647f * x, &sn, &cs);
-    return cmulf(R, cf{cs, -sn});          // e^{-j 2 pi x}
+    if (kk & kRecLosslessTE || k == 0) return cf{R.re * cs, -R.re * sn};   // e^{-j 2 pi x}, R real
+    return cmulf(R, cf{cs, -sn});
 }
 
 // The same term as a plain FP32 program: unfolded length L = |w - u_m| from the RIS-frame image,
@@ -83,10 +97,16 @@ __device__ __forceinline__ cf rx_leg_term_plain(const PathRec& p, float4 e, floa
         amp *= sqrtf(gr);
     }
     cf R = cf{amp, 0.f};
-    const int k = __float_as_int(p.a.y);
-    if (k >= 1) {
-        R = cmulf(R, fresnel_f(fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) / L, p.a.z, p.a.w, tm));
-        if (k == 2) R = cmulf(R, fresnel_f(fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) / L, p.n1.w, p.n2.w, tm));
+    const int kk = __float_as_int(p.a.y);
+    const int k = kk & 3;
+    if (k >= 1) {          // a lossless-TE record holds eps_r - 1 in place of eps_r and no imaginary part
+        const bool lt = (kk & kRecLosslessTE) != 0;
+        const float er1 = lt ? p.a.z + 1.f : p.a.z, ei1 = lt ? 0.f : p.a.w;
+        R = cmulf(R, fresnel_f(fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) / L, er1, ei1, tm));
+        if (k == 2) {
+            const float er2 = lt ? p.n1.w + 1.f : p.n1.w, ei2 = lt ? 0.f : p.n2.w;
+            R = cmulf(R, fresnel_f(fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) / L, er2, ei2, tm));
+        }
     }
     float sn, cs;
     sincosf(k0 * L, &sn, &cs);
@@ -97,10 +117,11 @@ constexpr int kEvalWarps = 8;
 constexpr int kMaxCfgPerPass = 4;
 constexpr int kElemMajorMin = 64;   // arrays of at least this many elements: lanes own elements
 
-// One warp per receiver, lanes own elements (m = lane + 32 k): each lane keeps its element's data in
-// registers and sums b_mq over the receiver's paths, whose records every lane of the warp reads at
-// the same address (one broadcast load per path); then c_m and the NC configurations' Gamma_m
-// scale the sum. For arrays of kElemMajorMin elements or more.
+// One warp per receiver, lanes own elements, two per pass (m = m0 + lane and m0 + 32 + lane): each
+// lane keeps its elements' data in registers and sums b_mq over the receiver's paths, whose records
+// every lane of the warp reads at the same address (one broadcast load per path serves two elements);
+// then c_m and the NC configurations' Gamma_m scale the sums. For arrays of kElemMajorMin elements or
+// more.
 template <int PAT, int NC>
 __global__ void __launch_bounds__(32 * kEvalWarps)
 k_eval_em(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, const uint32_t* __restrict__ vis, int W,
@@ -116,27 +137,39 @@ k_eval_em(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, cons
     cf acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = cf{0.f, 0.f};
-    for (int m0 = 0; m0 < M; m0 += 32) {
-        const int m = m0 + lane;
-        const bool valid = m < M;
-        const float4 e = valid ? elem[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool direct = valid && ((vis[r * W + (m >> 5)] >> (m & 31)) & 1u);
-        cf sum = cf{0.f, 0.f};
+    for (int m0 = 0; m0 < M; m0 += 64) {
+        int mm[2];
+        bool valid[2], direct[2];
+        float4 e[2];
+        cf sum[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            mm[h] = m0 + 32 * h + lane;
+            valid[h] = mm[h] < M;
+            e[h] = valid[h] ? elem[mm[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            direct[h] = valid[h] && ((vis[r * W + (mm[h] >> 5)] >> (mm[h] & 31)) & 1u);
+            sum[h] = cf{0.f, 0.f};
+        }
         for (int q = 0; q < nq; ++q) {
             const PathRec p = rec[o + q];
-            const bool on = valid && (__float_as_int(p.a.y) > 0 || direct);   // order 0: the direct leg
-            if (!on) continue;
-            const cf b = rx_leg_term<PAT>(p, e, inv_lam, gr, tm != 0);
-            sum.re += b.re;
-            sum.im += b.im;
+            const bool reflected = __float_as_int(p.a.y) > 0;      // order 0: the direct leg
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!(valid[h] && (reflected || direct[h]))) continue;
+                const cf b = rx_leg_term<PAT>(p, e[h], inv_lam, gr, tm != 0);
+                sum[h].re += b.re;
+                sum[h].im += b.im;
+            }
         }
-        if (valid) {
-            const float2 c2 = cm[m];
-            const cf cb = cmulf(sum, cf{c2.x, c2.y});
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!valid[h]) continue;
+            const float2 c2 = cm[mm[h]];
+            const cf cb = cmulf(sum[h], cf{c2.x, c2.y});
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 if (c < n_cfg) {
-                    const float2 g = gamma[(int64_t)(cfg0 + c) * M + m];
+                    const float2 g = gamma[(int64_t)(cfg0 + c) * M + mm[h]];
                     acc[c].re += g.x * cb.re - g.y * cb.im;
                     acc[c].im += g.x * cb.im + g.y * cb.re;
                 }

@@ -249,9 +249,13 @@ struct risrt_rxset {
 };
 
 // Rx-leg path record (structure of arrays, one entry per (rx, path)); see field.cu for use.
+// With kRecLosslessTE set in the order field every bounce is a lossless dielectric under the TE
+// coefficient and the eps fields hold (eps_r - 1, 1 / (1 - eps_r)) per bounce: a.z, a.w for bounce 1,
+// n1.w, n2.w for bounce 2.
+constexpr int kRecLosslessTE = 4;
 struct PathRec {
     float4 w;        // w = I - c in the RIS frame (t1, t2, n), and D0 = |w|
-    float4 a;        // frac(D0/lambda), order (int bits), eps1 (re, im)
+    float4 a;        // frac(D0/lambda), order (int bits, low 2; kRecLosslessTE), eps1 (re, im)
     float4 n1;       // bounce-1 normal in the RIS frame, eps2.re
     float4 n2;       // bounce-2 normal (unfolded) in the RIS frame, eps2.im
     float4 v;        // Rx pattern axis, unfolded into the RIS frame

@@ -1463,11 +1463,24 @@ __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n
             n2 = mirror_dir_f(face_n32(S, fa[1]), n1);
             e2 = face_eps32(S, fa[1], wv);
         }
+        // every bounce a lossless dielectric with the TE coefficient: the record carries eps_r - 1 and
+        // 1 / (1 - eps_r) per bounce instead of the complex permittivities (bit 2 of the order field), so
+        // the field kernel evaluates R = (c - s)^2 / (1 - eps_r) with s = sqrt(eps_r - 1 + c^2), real
+        const bool fast = !wv.tm && k >= 1 && e1.y == 0.f && e1.x >= 1.f && (k < 2 || (e2.y == 0.f && e2.x >= 1.f));
+        float az = e1.x, aw = e1.y, n1w = e2.x, n2w = e2.y;
+        if (fast) {
+            az = e1.x - 1.f;
+            aw = e1.x == 1.f ? 0.f : (float)(1.0 / (1.0 - (double)e1.x));
+            if (k == 2) {
+                n1w = e2.x - 1.f;
+                n2w = e2.x == 1.f ? 0.f : (float)(1.0 / (1.0 - (double)e2.x));
+            }
+        }
         PathRec pr;
         pr.w = local4(fr, w, (float)D0);   // FP64 projection: |w_local| must match D0 for the phase
-        pr.a = make_float4(fr0, __int_as_float(k), e1.x, e1.y);
-        pr.n1 = local(n1, e2.x);
-        pr.n2 = local(n2, e2.y);
+        pr.a = make_float4(fr0, __int_as_float(k | (fast ? kRecLosslessTE : 0)), az, aw);
+        pr.n1 = local(n1, n1w);
+        pr.n2 = local(n2, n2w);
         pr.v = local(v, 0.f);
         rec[o + q] = pr;
         rec_seq[o + q] = id;

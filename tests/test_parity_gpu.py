@@ -12,7 +12,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2402_13034_gb300 import scenarios as S
-from tests.helpers import compare_fields, oracle_parity, run_gpu
+from tests.helpers import compare_fields, compare_pathsets, oracle_parity, run_gpu, subset_paths
 
 pytestmark = pytest.mark.gpu
 
@@ -306,3 +306,26 @@ def test_microbenchmarks_positive():
     rates = {k: ctx.microbench(k, 64)[0] for k in range(8)}
     assert all(v > 1e9 for v in rates.values()), rates
     assert rates[R.MB_FFMA] > rates[R.MB_MUFU_SIN]
+
+
+def test_order2_above_10k_faces_sampled():
+    """Order 2 on both legs and environment paths in an office of 10,008 faces: about 10^8 face
+    sequences per source, pruned on the GPU to those whose second face the beam through the first can
+    reach (per source, then per super-patch of receivers) before the per-receiver candidate search.
+    The whole 128x128 grid is traced; the oracle, which enumerates every sequence without pruning,
+    checks the path sets of 6 receivers spread over it decision by decision."""
+    w = S.office(n_boxes=1667)
+    w.max_order_tx = w.max_order_rx = 2
+    w.gammas = w.gammas[:1]
+    assert w.scene.n_faces >= 10000
+    g = run_gpu(w)
+    idx = np.unique(np.linspace(0, w.n_rx - 1, 6).astype(int))
+    o = O.Oracle(w)
+    op = o.rx_paths(w.rx_xyz[idx])
+    pc = compare_pathsets(subset_paths(g["paths"], idx), op, o.tx_leg())
+    assert not pc["bad"], pc["bad"][:10]
+    assert pc["amb_rate"] <= 1e-5
+    n2 = sum(int(np.sum(s >= w.scene.n_faces)) for s in op["seqs"])
+    print(f"order 2 at {w.scene.n_faces} faces: {pc['n_dec']} decisions, {pc['n_amb']} ambiguous, "
+          f"{sum(len(s) for s in op['seqs'])} Rx-leg paths ({n2} of order 2), {len(g['paths']['tx_seqs'])} Tx-leg paths")
+    assert n2 > 0
