@@ -365,7 +365,7 @@ def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
         dE = np.abs(np.sqrt(Pg * 2 * 120 * np.pi) - np.abs(E_ref)) / np.where(S_ref > 0, S_ref, 1)
         ent = {"ms": ms, "tflops": flop / (ms / 1e3) / 1e12,
                "db_err": {"median": float(np.median(db)), "p99": float(np.percentile(db, 99)),
-                          "max": float(db.max())},
+                          "max": float(db.max()), "frac_above_0.01dB": float(np.mean(db > 0.01))},
                "max_field_err_over_S": float(dE[ok].max())}
         kname = next((k for k in ("k_sweep_tc_pair", "k_sweep_tc") if k in prof), None)
         if kname:
