@@ -264,6 +264,44 @@ def bench_gradient(ctx, R, dev, steps=200, reps=5):
     return out
 
 
+def bench_serving_load(dev_index, rates=(5.0, 10.0, 20.0, 30.0), n_req=24, slots=4):
+    """Latency against offered load below saturation: the serving mix (same scenes and generator as
+    bench_serving) at each rate, requests submitted at their arrival times."""
+    from paper_2402_13034_gb300 import serve
+    scenes = {}
+    for w, name in ((S.room(grid=8), "room_492tri"), (S.office(), "office_20ktri"), (S.hall(target_grid=8), "hall_200ktri")):
+        w.name = name
+        scenes[name] = w
+    srv = serve.Server(device=dev_index, slots=slots)
+    for name, w in scenes.items():
+        srv.add_scene(name, w.scene)
+    table = []
+    try:
+        warm = [serve.Request("coverage", name, w.ris, w.tx, w.rx, w.rx_xyz[:64], w.gammas[:1], w.freq_hz, 1, 1, True)
+                for name, w in scenes.items() for _ in range(slots)]
+        srv.drain([srv.submit(r) for r in warm])
+        for k, rate in enumerate(rates):
+            reqs = serve.mixed_requests(S.SEED_BASE + 40 + k, n_req, rate, scenes)
+            t0 = time.perf_counter()
+            futs = []
+            for t_arr, r in reqs:
+                dt = t0 + t_arr - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                futs.append(srv.submit(r))
+            for f in futs:
+                f.exception(timeout=600)
+            wall = time.perf_counter() - t0
+            res = [f.result() for f in futs if f.exception() is None]
+            st = serve.latency_stats(res)
+            table.append({"offered_req_s": rate, "served_req_s": len(res) / wall, "p50_ms": st["p50_ms"],
+                          "p99_ms": st["p99_ms"], "service_p50_ms": st["service_p50_ms"],
+                          "service_p99_ms": st["service_p99_ms"], "requests": n_req, "rejected": n_req - len(res)})
+    finally:
+        srv.close()
+    return table
+
+
 def bench_serving(dev_index, n_req=64, rate_hz=2000.0, slots=4):
     """Seeded Poisson stream (mean rate_hz) of the serving mix: scenes of 492 (room), ~20k (office)
     and ~200k (hall) triangles, RIS of 37 / 127 / 1,024 / 4,096 elements, receiver grids of 1k-1M
@@ -755,6 +793,7 @@ def main():
     serving = None
     if rank == 0 and not args.no_serve:
         serving = bench_serving(local)
+        serving["latency_vs_load"] = bench_serving_load(local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

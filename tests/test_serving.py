@@ -212,3 +212,52 @@ def test_channel_cache_lru_and_locks():
     assert "big" not in srv._channels
     srv.close()
     assert srv.channel_bytes == 0 and not srv._channels
+
+
+@pytest.mark.gpu
+def test_served_results_match_oracle():
+    """A sample of served requests against the FP64 oracle: coverage (direct field evaluation) and
+    sweep (channel matrix on the tensor cores, split BF16, with 2-bit configurations, which BF16
+    carries exactly) on two scenes, the room (492 triangles, order 2) and the office (19,932
+    triangles, order 1), with a resident-channel repeat. The served power gives |E|; it must be within
+    5e-5 of the incoherent magnitude S(r) of the oracle's field on every receiver without an ambiguous
+    decision (Eqs. 9, 10)."""
+    from oracle import oracle as O
+    from paper_2402_13034_gb300 import build as B
+    B.build()
+    room = S.room(grid=6, n_boxes=12)
+    room.name = "room_o"
+    office = S.office()
+    office.name = "office_o"
+    office.rx_xyz = office.rx_xyz[::1024]                     # 16 receivers spread over the target area
+    reqs = []
+    for w, orders in ((room, (2, 2)), (office, (1, 1))):
+        codes, g2 = S.two_bit_configs(S.SplitMix64(7), 5, w.n_elem)
+        gph = S.phase_configs(S.SplitMix64(8), 3, w.n_elem)
+        for kind, g, key in (("coverage", gph, None), ("sweep", g2, "c_" + w.name), ("sweep", g2[:2], "c_" + w.name)):
+            reqs.append((w, serve.Request(kind, w.name, w.ris, w.tx, w.rx, w.rx_xyz, g, w.freq_hz, orders[0],
+                                          orders[1], True, channel_key=key)))
+    srv = serve.Server(slots=3)
+    for w in (room, office):
+        srv.add_scene(w.name, w.scene)
+    # the repeat sweeps go in after the first ones have stored their channels
+    first = [i for i in range(len(reqs)) if i % 3 != 2]
+    got = [None] * len(reqs)
+    for batch in (first, [i for i in range(len(reqs)) if i % 3 == 2]):
+        futs = {i: srv.submit(reqs[i][1]) for i in batch}
+        for i, f in futs.items():
+            got[i] = f.result(timeout=600).P
+    hits = srv.channel_hits
+    srv.close()
+    assert hits >= 2
+    checked = 0
+    for (w, r), P in zip(reqs, got):
+        wo = S.Workload(w.name, w.freq_hz, w.scene, w.ris, w.tx, w.rx, w.rx_xyz, r.gammas, r.max_order_tx,
+                        r.max_order_rx, True)
+        fld = O.Oracle(wo).field(wo.rx_xyz)
+        E_ref, P_ref, S_ref = O.Oracle.evaluate(fld, r.gammas)
+        ok = ~fld["amb"][:, None] & (S_ref > 0)
+        dE = np.abs(np.sqrt(P.astype(np.float64) * 2 * 120 * np.pi) - np.abs(E_ref)) / np.where(S_ref > 0, S_ref, 1.0)
+        assert dE[ok].max() <= 5e-5, (r.kind, w.name, dE[ok].max())
+        checked += int(ok.sum())
+    assert checked > 100
