@@ -45,7 +45,7 @@ enum {
     RISRT_ERR_OOM = 2,         /* device allocation failed */
     RISRT_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
     RISRT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
-    RISRT_ERR_NOT_READY = 5,   /* an input object is missing (e.g. antenna not set) */
+    RISRT_ERR_NOT_READY = 5,   /* an input object is missing (antenna not set) or an asynchronous trace is unchecked */
     RISRT_ERR_CAPACITY = 6     /* a fixed internal capacity would be exceeded */
 };
 
@@ -133,7 +133,8 @@ int risrt_antenna_set(risrt_ctx* ctx, int which, const float pos[3], const float
 int risrt_rx_upload(risrt_ctx* ctx, const float* rx_xyz_host, int64_t n_rx, risrt_rxset** out);
 
 /* Wrap caller-owned device memory [n_rx][3] float as an Rx set without copying. The caller keeps
- * the memory alive and unchanged until risrt_rxset_destroy. */
+ * the memory alive until risrt_rxset_destroy; its contents may change between traces only within the
+ * largest |coordinate| measured here (the traces' FP32 error bounds use it). Synchronises the stream. */
 int risrt_rx_bind(risrt_ctx* ctx, const float* rx_xyz, int64_t n_rx, risrt_rxset** out);
 
 /* ------------------------------------------------------------------------------------------------
@@ -166,6 +167,47 @@ int risrt_rx_bind(risrt_ctx* ctx, const float* rx_xyz, int64_t n_rx, risrt_rxset
 int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris,
                       const risrt_rxset* rxset, double freq_hz, int32_t max_order_tx,
                       int32_t max_order_rx, uint32_t flags, risrt_pathset** inout);
+
+/* Fixed capacities of an asynchronous trace. */
+typedef struct {
+    int32_t cand_cap;              /* geometric path candidates per destination and leg (1 .. 65536) */
+    int32_t max_paths_per_rx;      /* Rx-leg entries per receiver, the direct one included (>= 1) */
+    int32_t max_env_paths_per_rx;  /* environment (Tx -> Rx reflected) paths per receiver (>= 0) */
+} risrt_trace_limits;
+
+/* Bytes of device workspace risrt_trace_paths_async needs for these inputs, orders, flags and limits
+ * (host arithmetic over the sizes; launches nothing). Errors as risrt_trace_paths. */
+int risrt_trace_workspace_size(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris,
+                               const risrt_rxset* rxset, int32_t max_order_tx, int32_t max_order_rx,
+                               uint32_t flags, const risrt_trace_limits* limits, size_t* bytes);
+
+/* The path search of risrt_trace_paths (same paths, bit for bit, when the limits hold them) that neither
+ * synchronises nor allocates device memory: every array of the path set and all scratch live in
+ * `workspace` (256-byte aligned, at least risrt_trace_workspace_size bytes, owned by the caller, not to
+ * be reused until the path set is no longer needed), sequence-table sizes and path counts stay on the
+ * device, and the work is only enqueued, so the call can be captured into a CUDA graph and replayed
+ * (with new contents of the inputs: receiver coordinates must stay within the extent measured when the
+ * receiver set was uploaded or bound). The first trace of a context, of either kind, creates its
+ * side streams and sets kernel attributes: make it before any capture, and capture only after the
+ * context's earlier work has completed (a capturing stream cannot wait on work outside the capture). Candidates, entries or
+ * environment paths beyond the limits are dropped and flagged; risrt_trace_check reports them
+ * (RISRT_ERR_CAPACITY) and must run, after the work completes and before the workspace is reused,
+ * before risrt_pathset_stats_get, risrt_pathset_export or risrt_eval_cir; risrt_eval_field,
+ * risrt_build_A and the sweeps can be enqueued right after this call. Grids span every sequence id, so
+ * order 2 suits scenes of a few thousand faces. *inout: NULL, or a path set filled by this call before
+ * (one created by risrt_trace_paths is refused). */
+int risrt_trace_paths_async(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris, const risrt_rxset* rxset,
+                            double freq_hz, int32_t max_order_tx, int32_t max_order_rx, uint32_t flags,
+                            const risrt_trace_limits* limits, void* workspace, size_t workspace_bytes,
+                            risrt_pathset** inout);
+
+/* Waits for an asynchronous trace and reads its counts, flags and Tx-leg ids; RISRT_ERR_CAPACITY names
+ * the limit that was exceeded (the path set is then incomplete), RISRT_OK otherwise. Call it after every
+ * run of the trace, each replay of a CUDA graph that holds one included: every run advances a counter
+ * on the device, and risrt_pathset_stats_get, risrt_pathset_export and risrt_eval_cir return
+ * RISRT_ERR_NOT_READY while that counter is ahead of the one read here (the device-side consumers,
+ * risrt_eval_field, risrt_build_A and the sweeps, need no check). A no-op for other path sets. */
+int risrt_trace_check(risrt_ctx* ctx, risrt_pathset* ps);
 
 /* Counts of a path set (host struct). */
 typedef struct {

@@ -449,6 +449,9 @@ int risrt_rx_upload(risrt_ctx* ctx, const float* rx_xyz_host, int64_t n_rx, risr
         delete r;
         return cuda_fail(ctx, e, "cudaMemcpyAsync");
     }
+    float ext = 0.f;                  // largest |coordinate| (the traces' FP32 error bounds use it)
+    for (int64_t i = 0; i < 3 * n_rx; ++i) ext = std::max(ext, std::fabs(rx_xyz_host[i]));
+    r->ext = ext;
     *out = r;
     return RISRT_OK;
 }
@@ -465,6 +468,13 @@ int risrt_rx_bind(risrt_ctx* ctx, const float* rx_xyz, int64_t n_rx, risrt_rxset
     r->n = n_rx;
     r->xyz = const_cast<float*>(rx_xyz);
     r->owned = false;
+    float ext = 0.f;
+    int rc = rx_extent(ctx, rx_xyz, n_rx, &ext);
+    if (rc) {
+        delete r;
+        return rc;
+    }
+    r->ext = ext;
     *out = r;
     return RISRT_OK;
 }
@@ -484,6 +494,7 @@ int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris*
     if (flags & ~(uint32_t)(RISRT_FLAG_ENV_PATHS | RISRT_FLAG_FRESNEL_TM)) return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown flag");
     risrt_pathset* ps = *inout;
     bool created = false;
+    if (ps && ps->external) return fail(ctx, RISRT_ERR_INVALID_ARG, "the path set lives in a workspace: trace it with risrt_trace_paths_async");
     if (!ps) {
         ps = new (std::nothrow) risrt_pathset();
         if (ps) ps->owner = ctx;
@@ -499,10 +510,90 @@ int risrt_trace_paths(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris*
     return RISRT_OK;
 }
 
-// Waits for the trace that filled ps and brings its device-side statistics to the host (once).
+static int check_trace_args(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris, const risrt_rxset* rxset,
+                            int32_t max_order_tx, int32_t max_order_rx, uint32_t flags, const risrt_trace_limits* lim)
+{
+    if (!scene || !ris || !rxset || !lim) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->tx.set || !ctx->rx.set) return fail(ctx, RISRT_ERR_NOT_READY, "Tx and Rx antennas must be set");
+    if (max_order_tx < 0 || max_order_tx > 2 || max_order_rx < 0 || max_order_rx > 2)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "orders must be in [0, 2]");
+    if ((max_order_tx == 2 || max_order_rx == 2) && scene->n_faces > 40000)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "order 2 supports at most 40000 faces");
+    if (ris->host_face >= scene->n_faces) return fail(ctx, RISRT_ERR_INVALID_ARG, "host_face out of range");
+    if (flags & ~(uint32_t)(RISRT_FLAG_ENV_PATHS | RISRT_FLAG_FRESNEL_TM)) return fail(ctx, RISRT_ERR_INVALID_ARG, "unknown flag");
+    if (lim->cand_cap < 1 || lim->cand_cap > (1 << 16) || lim->max_paths_per_rx < 1 || lim->max_env_paths_per_rx < 0)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "limits out of range");
+    return RISRT_OK;
+}
+
+int risrt_trace_workspace_size(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris, const risrt_rxset* rxset,
+                               int32_t max_order_tx, int32_t max_order_rx, uint32_t flags, const risrt_trace_limits* lim,
+                               size_t* bytes)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!bytes) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (int rc = check_trace_args(ctx, scene, ris, rxset, max_order_tx, max_order_rx, flags, lim)) return rc;
+    risrt_pathset probe;
+    AsyncTrace at;
+    at.cand_cap = lim->cand_cap;
+    at.max_paths = lim->max_paths_per_rx;
+    at.max_env = lim->max_env_paths_per_rx;
+    at.need = bytes;
+    return trace_paths(ctx, scene, ris, rxset, 1e9, max_order_tx, max_order_rx, flags, &probe, &at);
+}
+
+int risrt_trace_paths_async(risrt_ctx* ctx, const risrt_scene* scene, const risrt_ris* ris, const risrt_rxset* rxset,
+                            double freq_hz, int32_t max_order_tx, int32_t max_order_rx, uint32_t flags,
+                            const risrt_trace_limits* lim, void* workspace, size_t workspace_bytes, risrt_pathset** inout)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!inout || !workspace) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (int rc = check_trace_args(ctx, scene, ris, rxset, max_order_tx, max_order_rx, flags, lim)) return rc;
+    if (!(freq_hz > 0) || !std::isfinite(freq_hz)) return fail(ctx, RISRT_ERR_INVALID_ARG, "frequency must be positive");
+    if ((uintptr_t)workspace & 255u) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    risrt_pathset* ps = *inout;
+    bool created = false;
+    if (ps && !ps->external) return fail(ctx, RISRT_ERR_INVALID_ARG, "the path set was filled by risrt_trace_paths");
+    if (!ps) {
+        ps = new (std::nothrow) risrt_pathset();
+        if (!ps) return fail(ctx, RISRT_ERR_OOM, "host allocation failed");
+        ps->owner = ctx;
+        created = true;
+    }
+    AsyncTrace at;
+    at.ws = workspace;
+    at.bytes = workspace_bytes;
+    at.cand_cap = lim->cand_cap;
+    at.max_paths = lim->max_paths_per_rx;
+    at.max_env = lim->max_env_paths_per_rx;
+    int rc = trace_paths(ctx, scene, ris, rxset, freq_hz, max_order_tx, max_order_rx, flags, ps, &at);
+    if (rc) {
+        if (created) delete ps;
+        return rc;
+    }
+    *inout = ps;
+    return RISRT_OK;
+}
+
+int risrt_trace_check(risrt_ctx* ctx, risrt_pathset* ps)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!ps) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL path set");
+    return trace_check(ctx, ps);
+}
+
+// Waits for the trace that filled ps and brings its device-side statistics to the host (once per
+// trace). An asynchronous trace's host copies are current only if no run of it (a graph replay
+// included) came after its last risrt_trace_check: RISRT_ERR_NOT_READY otherwise.
 static int pathset_sync(const risrt_pathset* ps)
 {
+    if (ps->check_pending) return RISRT_ERR_NOT_READY;       // an asynchronous trace not checked yet
     if (ps->stream && cudaStreamSynchronize(ps->stream) != cudaSuccess) return RISRT_ERR_CUDA;
+    if (ps->external) {
+        unsigned long long gen = 0;
+        if (cudaMemcpy(&gen, ps->gen_dev, sizeof(gen), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+        if (gen != ps->checked_gen) return RISRT_ERR_NOT_READY;
+    }
     if (ps->stats_pending) {
         unsigned long long c[6];
         if (cudaMemcpy(c, ps->ctr_dev, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
@@ -546,6 +637,8 @@ int risrt_pathset_export(const risrt_pathset* ps, int32_t* rx_count_host, int64_
     std::vector<int64_t> off(n + 1), eoff(n + 1);
     if (cudaMemcpy(off.data(), ps->rx_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
     if (cudaMemcpy(eoff.data(), ps->env_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess) return RISRT_ERR_CUDA;
+    // the caller sized its arrays from the counts on the host: the offsets must agree with them
+    if (off[n] != ps->n_paths || eoff[n] != ps->n_env) return RISRT_ERR_NOT_READY;
     if (rx_count_host)
         for (int64_t r = 0; r < n; ++r) rx_count_host[r] = (int32_t)(off[r + 1] - off[r] - 1);
     if (rx_seq_host && ps->n_paths > 0) {
@@ -611,6 +704,8 @@ int risrt_eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, 
     if (!ps || !gamma || !taps_out || !rx_delay_out || !tx_delay_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
     if (((uintptr_t)gamma | (uintptr_t)taps_out | (uintptr_t)rx_delay_out | (uintptr_t)tx_delay_out) & 7u)
         return fail(ctx, RISRT_ERR_INVALID_ARG, "arrays must be 8-byte aligned");
+    if (int rc = pathset_sync(ps))
+        return fail(ctx, rc, rc == RISRT_ERR_NOT_READY ? "call risrt_trace_check after an asynchronous trace" : "CUDA error");
     return eval_cir(ctx, ps, (const float2*)gamma, (float2*)taps_out, rx_delay_out, tx_delay_out);
 }
 
@@ -839,6 +934,10 @@ int risrt_pathset_destroy(risrt_ctx* ctx, risrt_pathset* ps)
 {
     if (!ps) return RISRT_OK;
     if (ctx) sync_ctx(ctx);
+    if (ps->external) {             // its device arrays belong to the caller's workspace
+        delete ps;
+        return RISRT_OK;
+    }
     risrt_ctx* pc = ctx && ctx == ps->owner ? ctx : nullptr;
     for (void* p : {(void*)ps->rec, (void*)ps->rx_off, (void*)ps->vis, (void*)ps->E0, (void*)ps->cm, (void*)ps->elem,
                     (void*)ps->rx_seq, (void*)ps->env_seq, (void*)ps->env_off, (void*)ps->los, ps->scratch,

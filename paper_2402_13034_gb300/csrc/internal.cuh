@@ -335,11 +335,23 @@ struct risrt_pathset {
     risrt::AntD txa{};
     risrt::WaveD wv{};
     double K = 0.0;
+    // asynchronous traces: every device array lives in the caller's workspace (external), and the
+    // counts, flags and Tx-leg ids stay on the device until risrt_trace_check reads them
+    bool external = false;
+    bool check_pending = false;
+    const int* chk_flags = nullptr;          // [0] candidate slab full, [1] traversal stack, [2] path arrays full
+    const int64_t* chk_ntx = nullptr;
+    const int64_t* chk_ids = nullptr;
+    int chk_cap = 0;
+    // generation of the asynchronous trace: advanced on the device by every run (a graph replay
+    // included), recorded on the host by risrt_trace_check; the host copies are current when they agree
+    const unsigned long long* gen_dev = nullptr;
+    unsigned long long checked_gen = 0;
     // statistics: counted on the device, fetched when first asked for (the trace does not wait)
     mutable int64_t units = 0;
     mutable int64_t fp64_refines = 0;
     mutable int64_t n_candidates = 0, n_segments = 0, node_visits = 0, tri_tests = 0;
-    unsigned long long* ctr_dev = nullptr;   // [6] copy of the trace's counters
+    unsigned long long* ctr_dev = nullptr;   // [6] copy of the trace's counters ([6] the generation, asynchronous)
     mutable bool stats_pending = false;
     cudaStream_t stream = nullptr;           // stream of the trace that filled this set
     int64_t cap_rx_seq = 0;
@@ -393,8 +405,24 @@ void prof_end(risrt_ctx* ctx);
 int build_scene(risrt_ctx* ctx, risrt_scene* sc, const float* verts_host, int64_t n_verts,
                 const int32_t* tris_host, const int32_t* face_host, const int32_t* mat_host,
                 const float* mats_host, int n_mat);
+// An asynchronous trace (risrt_trace_paths_async): all device memory from the workspace `ws` of `bytes`
+// (nullptr: only store the bytes needed in *need), fixed capacities, no host synchronisation.
+struct AsyncTrace {
+    void* ws = nullptr;
+    size_t bytes = 0;
+    int cand_cap = 512;          // geometric candidates per destination and leg
+    int max_paths = 64;          // Rx-leg entries per receiver (the direct one included)
+    int max_env = 64;            // environment paths per receiver
+    size_t* need = nullptr;
+};
 int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rx,
-                double freq, int max_order_tx, int max_order_rx, uint32_t flags, risrt_pathset* ps);
+                double freq, int max_order_tx, int max_order_rx, uint32_t flags, risrt_pathset* ps,
+                const AsyncTrace* at = nullptr);
+// Reads the device-side results of an asynchronous trace (synchronises); RISRT_ERR_CAPACITY if one of
+// its fixed capacities was exceeded.
+int trace_check(risrt_ctx* ctx, risrt_pathset* ps);
+// max |coordinate| of n points on the device (synchronises)
+int rx_extent(risrt_ctx* ctx, const float* xyz, int64_t n, float* out);
 int eval_field(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);
 int build_A(risrt_ctx* ctx, const risrt_pathset* ps, float2* A, float2* E0);
 int eval_field_plain(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamma, int n_cfg, float2* E, float* P);

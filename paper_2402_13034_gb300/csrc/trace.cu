@@ -316,9 +316,10 @@ __global__ void k_patch_boxes(const float* __restrict__ dst_xyz, const int* __re
 // One bit per (super-patch, sequence): can a destination of the super-patch make the sequence valid
 // (box_in_beam on the super-patch box)? Word w of super-patch p covers sequences 32w .. 32w + 31.
 __global__ void k_seq_cull(DeviceScene S, const SeqEntry* __restrict__ seqs, int n_seq, const float4* __restrict__ boxes,
-                           int64_t n_super, int words, unsigned* __restrict__ mask)
+                           int64_t n_super, int words, unsigned* __restrict__ mask, const int64_t* __restrict__ n_dev)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev) n_seq = (int)min((int64_t)n_seq, *n_dev);   // the table's size on the device (asynchronous traces)
     for (int64_t sp = blockIdx.y; sp < n_super; sp += gridDim.y) {
         bool k = false;
         if (i < n_seq) {
@@ -365,8 +366,10 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
              const SeqEntry* __restrict__ seqs, const SeqEntryD* __restrict__ seqd, int n_seq,
              float tol_base, int* __restrict__ cand, int* __restrict__ cand_cnt, int cap,
              int* __restrict__ overflow, unsigned long long* __restrict__ refines, const int* __restrict__ slist,
-             const int* __restrict__ slist_cnt, int64_t slist_stride, RefineQ rq, DenseOut dl)
+             const int* __restrict__ slist_cnt, int64_t slist_stride, RefineQ rq, DenseOut dl,
+             const int64_t* __restrict__ n_dev)
 {
+    if (n_dev) n_seq = (int)min((int64_t)n_seq, *n_dev);   // the table's size on the device (asynchronous traces)
     __shared__ int2 dbuf[kCandThreads / 32][kDenseBuf];
     __shared__ int dseq[kCandThreads / 32][kDenseBuf];
     __shared__ SeqEntry sh[kCandThreads];
@@ -1416,7 +1419,8 @@ constexpr int kRecGroup = 8;
 // frac(D0 / lambda); the normals, pattern axis and permittivities are FP32 (they enter amplitudes only).
 __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, Frame fr, WaveD wv,
                           AntD rxa, const int* __restrict__ cand, int cap, const int64_t* __restrict__ off,
-                          const SeqEntry* __restrict__ seqs, PathRec* __restrict__ rec, int64_t* __restrict__ rec_seq)
+                          const SeqEntry* __restrict__ seqs, PathRec* __restrict__ rec, int64_t* __restrict__ rec_seq,
+                          int64_t rec_cap, int* __restrict__ overflow)
 {
     const int lane = threadIdx.x & (kRecGroup - 1);   // kRecGroup lanes per receiver, over its paths
     int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kRecGroup;
@@ -1431,6 +1435,10 @@ __global__ void k_records(DeviceScene S, const float* __restrict__ rx, int64_t n
     const float3 zr = f3((float)rxa.z[0], (float)rxa.z[1], (float)rxa.z[2]);
     auto local = [&](float3 v, float wv_) { return make_float4(dot(v, t1), dot(v, t2), dot(v, nn), wv_); };
     for (int q = lane; q < n; q += kRecGroup) {
+        if (o + q >= rec_cap) {               // a workspace-bound path set is full
+            atomicExch(overflow, 1);
+            break;
+        }
         int k = 0;
         int fa[2] = {-1, -1};
         int64_t id = -1;
@@ -1568,11 +1576,26 @@ __global__ void k_los(DeviceScene S, const float* __restrict__ rx, int64_t n_rx,
 
 __global__ void k_env_ids(const int* __restrict__ cand, int cap, const int64_t* __restrict__ cnt,
                           const int64_t* __restrict__ off, int64_t n_rx, const SeqEntry* __restrict__ seqs,
-                          int64_t* __restrict__ out)
+                          int64_t* __restrict__ out, int64_t out_cap, int* __restrict__ overflow)
 {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_rx) return;
-    for (int q = 0; q < cnt[r]; ++q) out[off[r] + q] = seqs[cand[r * (int64_t)cap + q]].info.z;
+    for (int q = 0; q < cnt[r]; ++q) {
+        if (off[r] + q >= out_cap) {          // a workspace-bound path set is full
+            atomicExch(overflow, 1);
+            return;
+        }
+        out[off[r] + q] = seqs[cand[r * (int64_t)cap + q]].info.z;
+    }
+}
+
+__global__ void k_trace_init(float* __restrict__ c_xyz, float cx, float cy, float cz, unsigned* __restrict__ rx_bb,
+                             unsigned long long* __restrict__ gen)
+{
+    const int t = threadIdx.x;
+    if (t == 0 && gen) *gen += 1ull;
+    if (t < 3) c_xyz[t] = t == 0 ? cx : (t == 1 ? cy : cz);
+    if (t < 8) rx_bb[t] = t < 3 ? 0xffffffffu : 0u;
 }
 
 __global__ void k_abs_max(const float* __restrict__ v, int64_t n, unsigned* __restrict__ out)
@@ -1795,7 +1818,7 @@ static void trace_params(const risrt_ctx* ctx, const risrt_ris* ris, double freq
 }
 
 int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rxs, double freq,
-                int max_tx, int max_rx, uint32_t flags, risrt_pathset* ps)
+                int max_tx, int max_rx, uint32_t flags, risrt_pathset* ps, const AsyncTrace* at)
 {
     cudaStream_t s = ctx->stream;
     if (int arc = trace_func_attrs(ctx)) return arc;
@@ -1822,8 +1845,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         ext = std::max(ext, std::fabs(ris->center[k]));
     }
     {   // receivers' extent (max |coordinate|) enters the FP32 error bound; an uploaded set keeps it
-        float rx_ext = rxs->owned ? rxs->ext : -1.f;
+        float rx_ext = rxs->ext;
         if (rx_ext < 0.f) {
+            if (at) return fail(ctx, RISRT_ERR_INVALID_ARG, "receiver set without a known extent");
             if (!ctx->small) RISRT_CUDA(ctx, cudaMalloc(&ctx->small, 256));
             unsigned* d_ext = (unsigned*)ctx->small;
             RISRT_CUDA(ctx, cudaMemsetAsync(d_ext, 0, sizeof(unsigned), s));
@@ -1832,7 +1856,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_CUDA(ctx, cudaMemcpyAsync(&h_ext, d_ext, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
             RISRT_CUDA(ctx, cudaStreamSynchronize(s));
             memcpy(&rx_ext, &h_ext, sizeof(float));
-            if (rxs->owned) rxs->ext = rx_ext;
+            rxs->ext = rx_ext;
         }
         ext = std::max(ext, rx_ext);
     }
@@ -1851,9 +1875,36 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     // --- resident per-Rx arrays
     int rc;
     // the path set's device memory comes from its owner's block cache (reused buffers are only
-    // touched by work ordered after their earlier uses on this stream)
+    // touched by work ordered after their earlier uses on this stream), or, for an asynchronous trace,
+    // from the caller's workspace (WA), the scratch after the path set's arrays
     risrt_ctx* pool = ps->owner == ctx ? ctx : nullptr;
-    if (ps->cap_rx < n_rx || !ps->vis) {
+    Arena WA{at ? (char*)at->ws : nullptr, 0};
+    if (at) {
+        const int cap0 = at->cand_cap;
+        const int64_t np = n_rx * (int64_t)at->max_paths, ne = std::max<int64_t>(n_rx * (int64_t)at->max_env, 1);
+        ps->vis = WA.get<uint32_t>(n_rx * W);
+        ps->E0 = WA.get<float2>(n_rx);
+        ps->rx_off = WA.get<int64_t>(n_rx + 1);
+        ps->los = WA.get<uint8_t>(n_rx);
+        ps->env_off = WA.get<int64_t>(n_rx + 1);
+        ps->cm = WA.get<float2>(M);
+        ps->elem = WA.get<float4>(M);
+        ps->tx_vis_dev = WA.get<uint8_t>(M);
+        ps->tx_paths = WA.get<TxPathD>(cap0);
+        ps->rec = WA.get<PathRec>(np);
+        ps->rx_seq = WA.get<int64_t>(np);
+        ps->env_seq = WA.get<int64_t>(ne);
+        ps->ctr_dev = WA.get<unsigned long long>(7);
+        ps->gen_dev = ps->ctr_dev + 6;
+        ps->cap_rx = n_rx;
+        ps->cap_m = M;
+        ps->cap_tx_vis = M;
+        ps->cap_tx_paths = cap0;
+        ps->cap_paths = np;
+        ps->cap_rx_seq = np;
+        ps->cap_env = ne;
+        ps->external = true;
+    } else if (ps->cap_rx < n_rx || !ps->vis) {
         for (void* q : {(void*)ps->vis, (void*)ps->E0, (void*)ps->rx_off, (void*)ps->los, (void*)ps->env_off}) ctx_free(pool, q);
         ps->vis = nullptr; ps->E0 = nullptr; ps->rx_off = nullptr; ps->los = nullptr; ps->env_off = nullptr;
         int64_t c = 0;
@@ -1864,7 +1915,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         c = 0; if ((rc = grow(ctx, pool, &ps->env_off, &c, n_rx + 1))) return rc;
         ps->cap_rx = n_rx;
     }
-    {
+    if (!at) {
         int64_t c = ps->cm ? ps->cap_m : 0;
         if ((rc = grow(ctx, pool, &ps->cm, &c, M))) return rc;
         c = ps->elem ? ps->cap_m : 0;
@@ -1876,20 +1927,20 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     ps->txa = tx;
     ps->wv = wv;
     ps->K = K;
-    RISRT_CUDA(ctx, cudaMemcpyAsync(ps->elem, ris->elem, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s));
+    if (!at || at->ws) RISRT_CUDA(ctx, cudaMemcpyAsync(ps->elem, ris->elem, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s));
 
     // --- scratch: sequence tables, candidates, counters
     const int64_t n_ids_tx = max_tx >= 2 ? (int64_t)F + (int64_t)F * F : (max_tx >= 1 ? F : 0);
     const int64_t n_ids_rx = max_rx >= 2 ? (int64_t)F + (int64_t)F * F : (max_rx >= 1 ? F : 0);
     const int64_t n_ids_env = max_env >= 2 ? (int64_t)F + (int64_t)F * F : (max_env >= 1 ? F : 0);
     const int64_t n_ids_max = std::max(n_ids_tx, std::max(n_ids_rx, n_ids_env));
-    int cap = ps->cand_cap > 0 ? ps->cand_cap : 512;
+    int cap = at ? at->cand_cap : (ps->cand_cap > 0 ? ps->cand_cap : 512);
     const int rq_cap = (int)std::min<int64_t>(16 * n_rx + 4096, (int64_t)1 << 22);
 
     // Streams of the concurrent parts (the trace's own stream when profiling every kernel, so that
     // each kernel's events bracket it alone, or when RISRT_OVERLAP=0)
     cudaStream_t sA = s, sB = s, sC = s;
-    {
+    if (!at || at->ws) {
         const char* ov = getenv("RISRT_OVERLAP");
         const bool overlap = !(ov && ov[0] == '0') && !(ctx->profiling && ctx->prof_only.empty());
         if (overlap) {
@@ -1911,7 +1962,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     };
     // work an earlier trace left on the side streams (one that returned early with an error) comes
     // before this trace's use of the path set's buffers
-    if (ctx->side[0]) {
+    // (skipped while the stream is being captured into a graph: a captured stream may not wait on work
+    // outside the capture, and a trace captured after the context's earlier work has none pending)
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap_st);
+    if (ctx->side[0] && (!at || at->ws) && cap_st == cudaStreamCaptureStatusNone) {
         join(ctx->side[0], ctx->ev[3]);
         join(ctx->side[1], ctx->ev[4]);
         join(ctx->side[2], ctx->ev[6]);
@@ -2013,11 +2068,20 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.tx.scan_tmp = A.get<char>(scan_temp_bytes(2));
             L.tx.work = A.get<unsigned long long>(1);
         };
+        if (at) {              // the scratch follows the path set's arrays in the workspace
+            Arena probe = WA;
+            Layout Lp;
+            layout(probe, Lp);
+            const size_t need_ws = probe.used + 256;
+            if (at->need) *at->need = need_ws;
+            if (!at->ws) return RISRT_OK;
+            if (need_ws > at->bytes) return fail(ctx, RISRT_ERR_INVALID_ARG, "workspace smaller than risrt_trace_workspace_size");
+        }
         Arena measure;
         Layout Lm;
         layout(measure, Lm);
         const size_t need = measure.used + 256;
-        if (ps->scratch_bytes < need) {
+        if (!at && ps->scratch_bytes < need) {
             ctx_free(pool, ps->scratch);
             ps->scratch = nullptr;
             ps->scratch_bytes = 0;
@@ -2025,7 +2089,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             if (e != cudaSuccess) return fail(ctx, RISRT_ERR_OOM, "scratch allocation failed");
             ps->scratch_bytes = need;
         }
-        Arena A{(char*)ps->scratch, 0};
+        Arena A = at ? WA : Arena{(char*)ps->scratch, 0};
         Layout L;
         layout(A, L);
         SeqTable* tab = L.tab;
@@ -2033,14 +2097,16 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         void* scan_tmp = L.scan_tmp;
         Candidates &crx = L.crx, &cenv = L.cenv, &ctx_leg = L.ctx_leg;
         uint8_t* tx_vis = ps->tx_vis_dev;       // kept with the path set (per-path outputs read it)
-        if ((rc = grow(ctx, pool, &ps->tx_paths, &ps->cap_tx_paths, cap))) return rc;
+        if (!at && (rc = grow(ctx, pool, &ps->tx_paths, &ps->cap_tx_paths, cap))) return rc;
         unsigned long long* counters = L.counters;
         int* flags_dev = L.flags_dev;
         float* c_xyz = L.c_xyz;
         RISRT_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 8, s));
         RISRT_CUDA(ctx, cudaMemsetAsync(flags_dev, 0, sizeof(int) * 4, s));
-        float cxyz[3] = {ris->center[0], ris->center[1], ris->center[2]};
-        RISRT_CUDA(ctx, cudaMemcpyAsync(c_xyz, cxyz, sizeof(cxyz), cudaMemcpyHostToDevice, s));
+        // the RIS centre as the Tx leg's destination and the receivers' bounding-box seeds (a kernel, not a
+        // copy from host memory, so a captured trace keeps no host address)
+        RISRT_KERNEL(ctx, "k_trace_init", (k_trace_init<<<1, 32, 0, s>>>(c_xyz, ris->center[0], ris->center[1], ris->center[2],
+                                                                           L.rx_bb, at ? ps->ctr_dev + 6 : nullptr)));
         const float* rxp = rxs->xyz;
         const d3 Tpos = D3(tx.pos[0], tx.pos[1], tx.pos[2]);
         const d3 Cpos = D3(fr.c[0], fr.c[1], fr.c[2]);
@@ -2088,7 +2154,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_KERNEL(ctx, "k_seq_build", (k_seq_build<<<nblk(nid, 256), 256, 0, s>>>(S, nid, flag, pos, src_of[i], tab[i].e, tab[i].d)));
             RISRT_KERNEL(ctx, "k_seq_count", (k_seq_count<<<1, 32, 0, s>>>(flag, pos, nid, L.seq_n + i)));
         }
-        {   // the three table sizes in one read-back
+        if (at) {   // no read-back: grids cover every sequence id, the kernels read the sizes on the device
+            for (int i = 0; i < 3; ++i) tab[i].n = (int)n_ids_of[i];
+        } else {    // the three table sizes in one read-back
             int64_t n_allowed[3];
             RISRT_CUDA(ctx, cudaMemcpyAsync(n_allowed, L.seq_n, sizeof(n_allowed), cudaMemcpyDeviceToHost, s));
             RISRT_CUDA(ctx, cudaStreamSynchronize(s));
@@ -2097,8 +2165,6 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
 
         // receivers in Morton order for the candidate search
         {
-            const unsigned bb_init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
-            RISRT_CUDA(ctx, cudaMemcpyAsync(L.rx_bb, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
             RISRT_KERNEL(ctx, "k_rx_bounds", (k_rx_bounds<<<std::min<unsigned>(nblk(n_rx, 256), 1024u), 256, 0, s>>>(
                                                  rxs->xyz, n_rx, L.rx_bb)));
             RISRT_KERNEL(ctx, "k_rx_morton", (k_rx_morton<<<nblk(n_rx, 256), 256, 0, s>>>(rxs->xyz, n_rx, L.rx_bb, L.rx_keys,
@@ -2111,7 +2177,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         // many-destination leg first waits for maps_ready (the visibility maps, built on another stream).
         auto run_candidates = [&](const SeqTable& t, const float* dst, int64_t n_dst, d3 src, int src_face,
                                   int dst_face, Candidates& cs, int map_src, cudaStream_t st, const LegBufs& lb,
-                                  cudaEvent_t maps_ready) -> int {
+                                  cudaEvent_t maps_ready, const int64_t* n_dev) -> int {
             RISRT_CUDA(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * n_dst, st));
             if (t.n > 0) {
                 dim3 grid(nblk(n_dst, kCandThreads), std::min<unsigned>(nblk(t.n, kCandChunk), 32768u));
@@ -2131,7 +2197,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     RISRT_KERNEL_ON(ctx, st, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, st>>>(dst, L.rx_order, n_dst,
                                                                                                        lb.sp_box)));
                     RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
-                                                                  256, 0, st>>>(S, t.e, t.n, lb.sp_box, n_super, words, lb.sp_mask)));
+                                                                  256, 0, st>>>(S, t.e, t.n, lb.sp_box, n_super, words, lb.sp_mask, n_dev)));
                     RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
                                                             lb.sp_mask, words, n_super, (int64_t)words * 32, lb.sp_list, lb.sp_cnt)));
                     slist = lb.sp_list;
@@ -2143,11 +2209,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     const size_t shm = sizeof(FaceTest) * (size_t)F;
                     RISRT_KERNEL_ON(ctx, st, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, st>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
-                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl)));
+                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl, n_dev)));
                 } else {
                     RISRT_KERNEL_ON(ctx, st, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, st>>>(
                                                           S, dst, n_dst, ord, src, t.e, t.d, t.n, tol_base, cs.cand, cs.cnt,
-                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl)));
+                                                          cs.cap, flags_dev, counters, slist, slist_cnt, slist_stride, rq, dl, n_dev)));
                 }
                 RISRT_KERNEL_ON(ctx, st, "k_refine_cand", (k_refine_cand<<<ctx->sm_count * 2, 256, 0, st>>>(
                                                        S, dst, src, t.e, t.d, rq, cs.cand, cs.cnt, cs.cap, flags_dev, counters, dl)));
@@ -2186,7 +2252,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         // Tx leg (destination: RIS centre, mounted on host_face), its element visibility, c_m (its path
         // count stays on the device) and path ids, beside the receiver legs on stream sA
         fork(sA, ctx->ev[2]);
-        if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg, 0, sA, L.tx, nullptr))) return rc;
+        const int64_t* nd0 = at ? L.seq_n + 0 : nullptr;
+        const int64_t* nd1 = at ? L.seq_n + 1 : nullptr;
+        const int64_t* nd2 = at ? L.seq_n + 2 : nullptr;
+        if ((rc = run_candidates(tab[0], c_xyz, 1, Tpos, -1, ris->host_face, ctx_leg, 0, sA, L.tx, nullptr, nd0))) return rc;
         RISRT_KERNEL_ON(ctx, sA, "k_tx_vis", (k_tx_vis<<<nblk(M, 128), 128, 0, sA>>>(S, ris->elem, M, fr, tx, ris->host_face, tol_base, tx_vis, counters,
                                               flags_dev + 1)));
         RISRT_KERNEL_ON(ctx, sA, "k_cm", (k_cm<<<nblk((int64_t)M * 32, 128), 128, 0, sA>>>(S, ris->elem, M, fr, tx, wv, K, tx_vis, ctx_leg.cand,
@@ -2196,8 +2265,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         // Rx leg (source: RIS centre) and environment paths (source: Tx); their validations use the maps
         const cudaEvent_t maps_ready = sB != s ? ctx->ev[1] : nullptr;
         fork(sC, ctx->ev[5]);
-        if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx, 1, s, L.main, maps_ready))) return rc;
-        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv, 0, sC, L.env, maps_ready))) return rc;
+        if ((rc = run_candidates(tab[1], rxp, n_rx, Cpos, ris->host_face, -1, crx, 1, s, L.main, maps_ready, nd1))) return rc;
+        if (env && (rc = run_candidates(tab[2], rxp, n_rx, Tpos, -1, -1, cenv, 0, sC, L.env, maps_ready, nd2))) return rc;
         join(sA, ctx->ev[3]);
         join(sB, ctx->ev[4]);
         join(sC, ctx->ev[6]);
@@ -2211,6 +2280,34 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             RISRT_CUDA(ctx, exclusive_scan_i64(env_cnt_tot, ps->env_off, n_rx + 1, scan_tmp, s));
         } else {
             RISRT_CUDA(ctx, cudaMemsetAsync(ps->env_off, 0, sizeof(int64_t) * (n_rx + 1), s));
+        }
+        if (at) {
+            // no read-back: records and ids go to the workspace's fixed-size arrays (a full array sets
+            // flag 2), the counts and Tx-leg ids stay on the device for risrt_trace_check
+            ps->n_paths = -1;
+            ps->n_env = -1;
+            ps->chk_flags = flags_dev;
+            ps->chk_ntx = ctx_leg.cnt64;
+            ps->chk_ids = L.tx_ids;
+            ps->chk_cap = cap;
+            ps->check_pending = true;
+            fork(sB, ctx->ev[0]);
+            RISRT_KERNEL_ON(ctx, sB, "k_e0", (k_e0<<<nblk(n_rx * kRecGroup, 128), 128, 0, sB>>>(S, rxp, n_rx, tx, rxa, wv, ps->los, cenv.cand,
+                                                                                         cenv.cap, env ? cenv.cnt64 : nullptr,
+                                                                                         tab[2].e, tab[2].d, ps->E0)));
+            if (env)
+                RISRT_KERNEL_ON(ctx, sB, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, sB>>>(cenv.cand, cenv.cap, cenv.cnt64,
+                                                                                               ps->env_off, n_rx, tab[2].e,
+                                                                                               ps->env_seq, ps->cap_env,
+                                                                                               flags_dev + 2)));
+            RISRT_KERNEL(ctx, "k_records", (k_records<<<nblk(n_rx * kRecGroup, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
+                                                          tab[1].e, ps->rec, ps->rx_seq, ps->cap_paths, flags_dev + 2)));
+            RISRT_KERNEL(ctx, "k_units", (k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1)));
+            join(sB, ctx->ev[4]);
+            RISRT_CUDA(ctx, cudaMemcpyAsync(ps->ctr_dev, counters, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToDevice, s));
+            ps->stats_pending = true;
+            ps->stream = s;
+            return RISRT_OK;
         }
         // one read-back: error flags, path counts, Tx-leg ids and visibility
         int host_flags[2];
@@ -2246,10 +2343,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                                                                      tab[2].e, tab[2].d, ps->E0)));
         if (env && n_env > 0) {
             RISRT_KERNEL_ON(ctx, sB, "k_env_ids", (k_env_ids<<<nblk(n_rx, 128), 128, 0, sB>>>(cenv.cand, cenv.cap, cenv.cnt64, ps->env_off,
-                                                                                           n_rx, tab[2].e, ps->env_seq)));
+                                                                                           n_rx, tab[2].e, ps->env_seq, INT64_MAX,
+                                                                                           flags_dev + 2)));
         }
         RISRT_KERNEL(ctx, "k_records", (k_records<<<nblk(n_rx * kRecGroup, 128), 128, 0, s>>>(S, rxp, n_rx, fr, wv, rxa, crx.cand, crx.cap, ps->rx_off,
-                                                      tab[1].e, ps->rec, ps->rx_seq)));
+                                                      tab[1].e, ps->rec, ps->rx_seq, INT64_MAX, flags_dev + 2)));
         RISRT_KERNEL(ctx, "k_units", (k_units<<<nblk(n_rx, 256), 256, 0, s>>>(ps->rx_off, n_rx, M, counters + 1)));
         join(sB, ctx->ev[4]);
         // statistics stay on the device until asked for (risrt_pathset_stats_get waits for them)
@@ -2369,6 +2467,54 @@ int strict_tx_cm(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, do
     release();
 #undef RISRT_STRICT_CUDA
     if (h_err) return fail(ctx, RISRT_ERR_CAPACITY, "BVH traversal stack overflow");
+    return RISRT_OK;
+}
+
+int trace_check(risrt_ctx* ctx, risrt_pathset* ps)
+{
+    // a regular trace is checked before it returns; an asynchronous one is read again every time, since
+    // a replayed graph reruns its kernels without the host code that would mark it pending
+    if (!ps->external) return RISRT_OK;
+    cudaStream_t s = ctx->stream;
+    int fl[3] = {0, 0, 0};
+    int64_t n_tx64 = 0, n_paths = 0, n_env = 0;
+    unsigned long long gen = 0;
+    std::vector<int64_t> ids((size_t)std::max(ps->chk_cap, 1));
+    ps->tx_vis_host.resize(ps->M);
+    RISRT_CUDA(ctx, cudaMemcpyAsync(fl, ps->chk_flags, sizeof(fl), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&n_tx64, ps->chk_ntx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&n_paths, ps->rx_off + ps->n_rx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&n_env, ps->env_off + ps->n_rx, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(ids.data(), ps->chk_ids, sizeof(int64_t) * ps->chk_cap, cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(ps->tx_vis_host.data(), ps->tx_vis_dev, ps->M, cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&gen, ps->gen_dev, sizeof(gen), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    ps->stats_pending = true;
+    ps->check_pending = true;                  // until the checks below pass: no host copies of a failed trace
+    if (fl[1]) return fail(ctx, RISRT_ERR_CAPACITY, "BVH traversal stack overflow");
+    if (fl[0]) return fail(ctx, RISRT_ERR_CAPACITY, "a destination had more geometric candidates than cand_cap");
+    if (fl[2] || n_paths > ps->cap_paths || n_env > ps->cap_env)
+        return fail(ctx, RISRT_ERR_CAPACITY, "more paths than max_paths_per_rx / max_env_paths_per_rx hold");
+    const int n_tx = (int)std::min<int64_t>(n_tx64, ps->chk_cap);
+    ps->tx_seq_host.assign(ids.begin(), ids.begin() + n_tx);
+    ps->n_paths = n_paths;
+    ps->n_env = n_env;
+    ps->checked_gen = gen;
+    ps->check_pending = false;
+    return RISRT_OK;
+}
+
+int rx_extent(risrt_ctx* ctx, const float* xyz, int64_t n, float* out)
+{
+    cudaStream_t s = ctx->stream;
+    if (!ctx->small) RISRT_CUDA(ctx, cudaMalloc(&ctx->small, 256));
+    unsigned* d_ext = (unsigned*)ctx->small;
+    RISRT_CUDA(ctx, cudaMemsetAsync(d_ext, 0, sizeof(unsigned), s));
+    RISRT_KERNEL(ctx, "k_abs_max", (k_abs_max<<<std::min<unsigned>(nblk(3 * n, 256), 1024u), 256, 0, s>>>(xyz, 3 * n, d_ext)));
+    unsigned h = 0;
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, d_ext, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    memcpy(out, &h, sizeof(float));
     return RISRT_OK;
 }
 
@@ -2514,12 +2660,12 @@ int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src3[3
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<true><<<grid, kCandThreads, shm, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
                                                   L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr},
-                                                  DenseOut{nullptr, nullptr, nullptr, nullptr})));
+                                                  DenseOut{nullptr, nullptr, nullptr, nullptr}, nullptr)));
         } else {
             RISRT_KERNEL(ctx, "k_candidates", (k_candidates<false><<<grid, kCandThreads, 0, s>>>(
                                                   S, L.dst, 1, nullptr, src, L.e, L.d, n_seq, tol_base, L.cand, L.cnt, cap,
                                                   L.flags, L.counters, nullptr, nullptr, 0, RefineQ{nullptr, 0, nullptr},
-                                                  DenseOut{nullptr, nullptr, nullptr, nullptr})));
+                                                  DenseOut{nullptr, nullptr, nullptr, nullptr}, nullptr)));
         }
         RISRT_KERNEL(ctx, "k_cand_counts", (k_cand_counts<<<1, 32, 0, s>>>(L.cnt, 1, cap, L.cnt64_tmp)));
         RISRT_CUDA(ctx, exclusive_scan_i64(L.cnt64_tmp, L.dense_off, 2, L.scan_tmp, s));

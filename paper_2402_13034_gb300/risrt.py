@@ -42,6 +42,10 @@ _SIGS = {
     "risrt_rx_upload": (C.c_int, [_P, _P, C.c_int64, C.POINTER(_P)]),
     "risrt_rx_bind": (C.c_int, [_P, _P, C.c_int64, C.POINTER(_P)]),
     "risrt_trace_paths": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint32, C.POINTER(_P)]),
+    "risrt_trace_workspace_size": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_uint32, _P, C.POINTER(C.c_size_t)]),
+    "risrt_trace_paths_async": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint32, _P, _P,
+                                          C.c_size_t, C.POINTER(_P)]),
+    "risrt_trace_check": (C.c_int, [_P, _P]),
     "risrt_pathset_stats_get": (C.c_int, [_P, _P]),
     "risrt_pathset_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "risrt_eval_field": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
@@ -72,6 +76,10 @@ _SIGS = {
     "risrt_rxset_destroy": (C.c_int, [_P, _P]),
     "risrt_pathset_destroy": (C.c_int, [_P, _P]),
 }
+
+
+class TraceLimits(C.Structure):
+    _fields_ = [("cand_cap", C.c_int32), ("max_paths_per_rx", C.c_int32), ("max_env_paths_per_rx", C.c_int32)]
 
 
 class RisrtError(RuntimeError):
@@ -333,6 +341,35 @@ class Context:
         self._check(load().risrt_trace_paths(self._ptr, scene.ptr, ris.ptr, rxset.ptr, float(freq_hz),
                                              int(max_order_tx), int(max_order_rx), int(flags), C.byref(ptr)))
         return reuse if reuse is not None else PathSet(self, ptr, "risrt_pathset_destroy")
+
+    def trace_workspace(self, scene: Scene, ris: RIS, rxset: RxSet, max_order_tx: int, max_order_rx: int,
+                        flags: int = 0, cand_cap: int = 512, max_paths: int = 64, max_env: int = 64):
+        """(workspace tensor, limits) for trace_paths_async."""
+        import torch
+        lim = TraceLimits(cand_cap, max_paths, max_env)
+        nb = C.c_size_t()
+        self._check(load().risrt_trace_workspace_size(self._ptr, scene.ptr, ris.ptr, rxset.ptr, int(max_order_tx),
+                                                      int(max_order_rx), int(flags), C.byref(lim), C.byref(nb)))
+        return torch.empty(nb.value + 256, dtype=torch.uint8, device=f"cuda:{self.device}"), lim
+
+    def trace_paths_async(self, scene: Scene, ris: RIS, rxset: RxSet, freq_hz: float, max_order_tx: int,
+                          max_order_rx: int, flags: int, workspace, limits, reuse: PathSet | None = None) -> PathSet:
+        """Enqueue a trace into the workspace (no synchronisation, no allocation); trace_check before reading
+        counts or exporting."""
+        ptr = reuse.ptr if reuse is not None else C.c_void_p()
+        base = (workspace.data_ptr() + 255) // 256 * 256
+        nbytes = workspace.numel() - (base - workspace.data_ptr())
+        self._check(load().risrt_trace_paths_async(self._ptr, scene.ptr, ris.ptr, rxset.ptr, float(freq_hz),
+                                                   int(max_order_tx), int(max_order_rx), int(flags), C.byref(limits),
+                                                   C.c_void_p(base), nbytes, C.byref(ptr)))
+        if reuse is not None:
+            return reuse
+        ps = PathSet(self, ptr, "risrt_pathset_destroy")
+        ps._keep = workspace
+        return ps
+
+    def trace_check(self, ps: PathSet):
+        self._check(load().risrt_trace_check(self._ptr, ps.ptr))
 
     def eval_field(self, ps: PathSet, gamma, E_out, P_out=None):
         """gamma: complex64 CUDA [C, M]; E_out: complex64 CUDA [C, n_rx]; P_out: float32 CUDA [C, n_rx]."""
