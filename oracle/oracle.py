@@ -49,6 +49,7 @@ class _Problem(C.Structure):
         ("freq", C.c_double),
         ("max_order_tx", C.c_int32), ("max_order_rx", C.c_int32), ("env_paths", C.c_int32),
         ("fresnel_tm", C.c_int32), ("strict_elements", C.c_int32),
+        ("vector_pol", C.c_int32), ("tx_pol", C.c_float * 3), ("rx_pol", C.c_float * 3),
     ]
 
 
@@ -75,6 +76,8 @@ def _load():
                                         C.c_int32, C.c_void_p, C.c_void_p]
             lib.or_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+            lib.or_field_vec.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             lib.or_cir.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             lib.or_element_positions.argtypes = [C.c_void_p, C.c_void_p]
@@ -110,7 +113,7 @@ def set_amb_tol(tol: float) -> None:
 class Oracle:
     """FP64 oracle bound to one workload (scene, RIS, antennas, frequency, orders, flags)."""
 
-    def __init__(self, w, fresnel_tm: bool = False, strict: bool = False):
+    def __init__(self, w, fresnel_tm: bool = False, strict: bool = False, vector: bool = False):
         lib = _load()
         self.w = w
         sc, ris = w.scene, w.ris
@@ -142,6 +145,13 @@ class Oracle:
         P.max_order_tx, P.max_order_rx = w.max_order_tx, w.max_order_rx
         P.env_paths, P.fresnel_tm = int(w.env_paths), int(fresnel_tm)
         P.strict_elements = int(strict)
+        P.vector_pol = int(vector)
+        if vector:
+            if w.tx.pol is None or w.rx.pol is None:
+                raise ValueError("the vector field needs the Tx and Rx polarisation axes")
+            P.tx_pol[:] = [float(x) for x in np.asarray(w.tx.pol, np.float32)]
+            P.rx_pol[:] = [float(x) for x in np.asarray(w.rx.pol, np.float32)]
+        self.vector = bool(vector)
         self._P = P
         self._ctx = lib.or_create(C.byref(P))
         self.F = lib.or_n_faces(self._ctx)
@@ -274,6 +284,39 @@ class Oracle:
         _load().or_field(self._ctx, _ptr(rx), n, _ptr(E0), _ptr(S0), _ptr(A), _ptr(SA), _ptr(amb), 0)
         return dict(E0=E0[:, 0] + 1j * E0[:, 1], S0=S0, A=A[..., 0] + 1j * A[..., 1], SA=SA,
                     amb=amb.astype(bool))
+
+    def field_vec(self, rx_xyz: np.ndarray):
+        """Vector mode: ``field``'s entries for the received values (co-polarised with the Rx axis) plus
+        the field vectors E03 [n, 3], A3 [n, M, 3] and their incoherent magnitudes S03, SA3."""
+        if not self.vector:
+            raise ValueError("the oracle was built without vector=True")
+        rx = np.ascontiguousarray(rx_xyz, np.float32).reshape(-1, 3)
+        n = len(rx)
+        E0 = np.zeros((n, 2))
+        S0 = np.zeros(n)
+        A = np.zeros((n, self.M, 2))
+        SA = np.zeros((n, self.M))
+        amb = np.zeros(n, np.int32)
+        E03 = np.zeros((n, 3, 2))
+        S03 = np.zeros(n)
+        A3 = np.zeros((n, self.M, 3, 2))
+        SA3 = np.zeros((n, self.M))
+        rc = _load().or_field_vec(self._ctx, _ptr(rx), n, _ptr(E0), _ptr(S0), _ptr(A), _ptr(SA), _ptr(amb), _ptr(E03),
+                                  _ptr(S03), _ptr(A3), _ptr(SA3))
+        if rc:
+            raise RuntimeError("or_field_vec failed")
+        return dict(E0=E0[:, 0] + 1j * E0[:, 1], S0=S0, A=A[..., 0] + 1j * A[..., 1], SA=SA, amb=amb.astype(bool),
+                    E03=E03[..., 0] + 1j * E03[..., 1], S03=S03, A3=A3[..., 0] + 1j * A3[..., 1], SA3=SA3)
+
+    @staticmethod
+    def evaluate_vec(fld: dict, gamma: np.ndarray):
+        """Vector mode for configurations gamma [C, M]: received E, P = |E|^2 / (2 eta0), S (as
+        ``evaluate``), the field vectors E3 [n, C, 3] and their incoherent magnitudes S3 [n, C]."""
+        g = np.atleast_2d(np.asarray(gamma, np.complex128))
+        E, P, S = Oracle.evaluate(fld, g)
+        E3 = fld["E03"][:, None, :] + np.einsum("rmj,cm->rcj", fld["A3"], g)
+        S3 = fld["S03"][:, None] + fld["SA3"] @ np.abs(g).T
+        return E, P, S, E3, S3
 
     def cir(self, rx_xyz: np.ndarray, gamma: np.ndarray, cap: int = 4096):
         """RIS channel impulse response per receiver: a list of taps (Rx-leg id q, Tx-leg id p, delay in

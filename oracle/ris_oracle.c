@@ -31,6 +31,18 @@
  *
  * Every geometric decision also reports whether it lies within AMB_TOL of flipping ("ambiguous");
  * comparisons against another implementation exclude those decisions.
+ *
+ * Vector mode (the polarisation extension that Sec. II-A names for Eq. 6 without giving a model): each
+ * term keeps every scalar factor above except the Fresnel products and is multiplied by a polarisation
+ * factor built from the real segment directions of its path:
+ *   launch     e = unit(P(d0) a_t), P(k) = I - k k^T, a_t the Tx polarisation axis, d0 the departure
+ *   bounce     e <- R_TE (e.s) s + R_TM (e.p_in) p_out, s = unit(k_in x n), p = s x k  (both Fresnel
+ *              coefficients, complex permittivity as above; at normal incidence e <- R_TE e)
+ *   RIS        e <- P(k_out) (e - 2 (e.n) n): the incident field with its normal component reversed
+ *              (tangential components kept), restricted to the outgoing wavefront
+ *   reception  received = unit(P(k_arr) a_r) . e ; the field vector E3 = sum of the terms' e (Eq. 8's
+ *              amplitude included); zero where a projected axis vanishes.
+ * With every field TE and co-polarised the received value equals the scalar model's.
  */
 #include <complex.h>
 #include <math.h>
@@ -64,6 +76,8 @@ typedef struct {
     double freq;
     int32_t max_order_tx, max_order_rx, env_paths, fresnel_tm;
     int32_t strict_elements;   /* 1: validate each element's reflected legs at the element itself */
+    int32_t vector_pol;        /* 1: vector field with polarisation (TE and TM per bounce) */
+    float tx_pol[3], rx_pol[3];  /* polarisation axes of the Tx and Rx antennas (global) */
 } or_problem;
 
 typedef struct { double x, y, z; } v3;
@@ -90,6 +104,7 @@ typedef struct {
     v3 c, t1, t2, n;          /* RIS frame; n = unit(t1 x t2) */
     v3* e;                    /* element centres e_m = c + a t1 + b t2 */
     v3 tx, tx_z, rx_z;        /* Tx position, antenna boresights (unit local z axes) */
+    v3 tx_pol, rx_pol;        /* unit polarisation axes (vector mode) */
     double lam, k, G, omega;
 } or_ctx;
 
@@ -218,6 +233,8 @@ or_ctx* or_create(const or_problem* P)
     C->tx = vf(P->tx_pos);
     C->tx_z = unit(vf(P->tx_orient + 6));
     C->rx_z = unit(vf(P->rx_orient + 6));
+    C->tx_pol = norm(vf(P->tx_pol)) > 0 ? unit(vf(P->tx_pol)) : mk(0, 0, 0);
+    C->rx_pol = norm(vf(P->rx_pol)) > 0 ? unit(vf(P->rx_pol)) : mk(0, 0, 0);
     C->lam = OR_C0 / P->freq;
     C->k = 2.0 * OR_PI / C->lam;
     C->omega = 2.0 * OR_PI * P->freq;
@@ -588,6 +605,8 @@ typedef struct {
     v3 dep;              /* unit direction leaving the first point */
     v3 arr_back;         /* unit direction from the last point back towards the previous one */
     double complex R;    /* product of Fresnel coefficients */
+    v3 dir[3];           /* directions of the real segments, dir[0] = dep, dir[k] = -arr_back */
+    int k, seq[2];       /* bounce faces in propagation order */
 } leg_t;
 
 /* A leg by the image method (Sec. II-B): the source is mirrored across the faces of the sequence
@@ -612,6 +631,9 @@ static leg_t leg_by_images(const or_ctx* C, v3 src, v3 dst, const int* seq, int 
     }
     g.dep = dir[0];
     g.arr_back = scl(dir[k], -1.0);
+    g.k = k;
+    for (int j = 0; j <= k; ++j) g.dir[j] = dir[j];
+    for (int j = 0; j < k; ++j) g.seq[j] = seq[j];
     g.R = 1.0;
     for (int j = 1; j <= k; ++j)
         g.R *= fresnel_c(C, fabs(dot(dir[j - 1], C->fn[seq[j - 1]])), seq[j - 1]);
@@ -643,12 +665,95 @@ static double complex ris_term(const or_ctx* C, const leg_t* gt, const leg_t* gr
     return Et * ris * rx * gt->R * gr->R * cexp(-I * C->k * (gt->L + gr->L));
 }
 
+/* ---------------------------------------------------------------------------------------------
+ * Vector mode (polarisation factors as described in the file header)
+ * ------------------------------------------------------------------------------------------- */
+typedef struct { double complex x, y, z; } cv3;
+
+static cv3 cv_real(v3 a) { cv3 r = {a.x, a.y, a.z}; return r; }
+static cv3 cv_scale(cv3 a, double complex s) { cv3 r = {a.x * s, a.y * s, a.z * s}; return r; }
+static cv3 cv_add(cv3 a, cv3 b) { cv3 r = {a.x + b.x, a.y + b.y, a.z + b.z}; return r; }
+static double complex cv_dot(cv3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }   /* bilinear */
+static double cv_norm(cv3 a) { return sqrt(cabs(a.x) * cabs(a.x) + cabs(a.y) * cabs(a.y) + cabs(a.z) * cabs(a.z)); }
+
+/* unit(P(k) a): the field direction of an antenna with polarisation axis a for propagation direction k
+   (zero when a lies along k) */
+static v3 pol_dir(v3 a, v3 k)
+{
+    v3 p = sub(a, scl(k, dot(a, k)));
+    double l = norm(p);
+    return l > 1e-12 ? scl(p, 1.0 / l) : mk(0, 0, 0);
+}
+
+/* One bounce on face f of a field e travelling along kin, leaving along kout: TE part along
+   s = unit(kin x n) scaled by R_TE, TM part from p_in = s x kin to p_out = s x kout scaled by R_TM. */
+static cv3 bounce_vec(const or_ctx* C, cv3 e, v3 kin, v3 kout, int f)
+{
+    const v3 n = C->fn[f];
+    const double ci = fabs(dot(kin, n));
+    const int m = C->fmat[f];
+    double re, im;
+    or_fresnel(ci, C->P.mats[2 * m], C->P.mats[2 * m + 1], C->P.freq, 0, &re, &im);
+    const double complex rte = re + I * im;
+    or_fresnel(ci, C->P.mats[2 * m], C->P.mats[2 * m + 1], C->P.freq, 1, &re, &im);
+    const double complex rtm = re + I * im;
+    v3 s = cross(kin, n);
+    const double ls = norm(s);
+    if (ls < 1e-12) return cv_scale(e, rte);        /* normal incidence: R_TM = -R_TE, p_out = -p_in */
+    s = scl(s, 1.0 / ls);
+    const v3 pin = cross(s, kin), pout = cross(s, kout);
+    return cv_add(cv_scale(cv_real(s), rte * cv_dot(e, s)), cv_scale(cv_real(pout), rtm * cv_dot(e, pin)));
+}
+
+/* the bounces of a leg in propagation order */
+static cv3 leg_vec(const or_ctx* C, const leg_t* g, cv3 e)
+{
+    for (int j = 1; j <= g->k; ++j) e = bounce_vec(C, e, g->dir[j - 1], g->dir[j], g->seq[j - 1]);
+    return e;
+}
+
+/* Vector mode, Tx -> ... -> Rx without the RIS: the received value; *E3 the field vector. */
+static double complex direct_term_vec(const or_ctx* C, const leg_t* g, cv3* E3)
+{
+    const or_problem* P = &C->P;
+    double Ft = or_pattern(P->tx_pattern, P->tx_gain, dot(g->dep, C->tx_z));
+    double Fr = or_pattern(P->rx_pattern, P->rx_gain, dot(g->arr_back, C->rx_z));
+    double amp = sqrt(2.0 * OR_ETA0 * P->tx_power * P->tx_gain * Ft) * sqrt(P->rx_gain * Fr) *
+                 C->lam / (4.0 * OR_PI * g->L);
+    const double complex a = amp * cexp(-I * C->k * g->L);
+    const cv3 e = leg_vec(C, g, cv_real(pol_dir(C->tx_pol, g->dep)));
+    *E3 = cv_scale(e, a);
+    return a * cv_dot(e, pol_dir(C->rx_pol, g->dir[g->k]));
+}
+
+/* Vector mode, one RIS term e_mpq without Gamma_m: the received value; *E3 the field vector. */
+static double complex ris_term_vec(const or_ctx* C, const leg_t* gt, const leg_t* gr, cv3* E3)
+{
+    const or_problem* P = &C->P;
+    double Ft = or_pattern(P->tx_pattern, P->tx_gain, dot(gt->dep, C->tx_z));
+    double Fin = elem_pattern(dot(gt->arr_back, C->n));
+    double Fout = elem_pattern(dot(gr->dep, C->n));
+    double Fr = or_pattern(P->rx_pattern, P->rx_gain, dot(gr->arr_back, C->rx_z));
+    double Et = sqrt(2.0 * OR_ETA0 * P->tx_power * P->tx_gain * Ft);                    /* Eq. 4 */
+    double ris = sqrt(C->G * Fin * Fout * (double)P->dy * (double)P->dz / (4.0 * OR_PI)) / gt->L; /* Eq. 7 */
+    double rx = sqrt(P->rx_gain * Fr) * C->lam / (4.0 * OR_PI * gr->L);                 /* Eq. 8 */
+    const double complex a = Et * ris * rx * cexp(-I * C->k * (gt->L + gr->L));
+    cv3 e = leg_vec(C, gt, cv_real(pol_dir(C->tx_pol, gt->dep)));
+    e = cv_add(e, cv_scale(cv_real(C->n), -2.0 * cv_dot(e, C->n)));      /* normal component reversed */
+    const v3 ko = gr->dir[0];
+    e = cv_add(e, cv_scale(cv_real(ko), -cv_dot(e, ko)));                 /* outgoing wavefront */
+    e = leg_vec(C, gr, e);
+    *E3 = cv_scale(e, a);
+    return a * cv_dot(e, pol_dir(C->rx_pol, gr->dir[gr->k]));
+}
+
 /* For each receiver: E0 = E_LOS + E_env, S0 = |E_LOS| + sum |env terms|, the channel row
    A[m] = sum_p sum_q e_mpq (so E = E0 + sum_m Gamma_m A[m]), SA[m] = sum_p sum_q |e_mpq| and an
    ambiguity flag covering every decision this receiver depends on (Tx-leg ones included). */
-int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, double* S0, double* A,
-             double* SA, int32_t* amb_out, int32_t max_paths)
+static int field_impl(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, double* S0, double* A,
+                      double* SA, int32_t* amb_out, double* E03, double* S03, double* A3, double* SA3)
 {
+    const int vec = C->P.vector_pol != 0;
     int F = C->F, hf = C->P.host_face, M = C->P.M;
     /* Tx leg (shared by all receivers) */
     int64_t cap = 1 << 20;
@@ -659,7 +764,6 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
     or_tx_leg(C, tx_ids, cap, &n_tx, tx_vis, &tx_amb, NULL, NULL, 0, NULL, NULL);
     if (n_tx > cap) n_tx = cap;
     int64_t n_ids = C->P.max_order_rx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_rx >= 1 ? F : 0);
-    (void)max_paths;
     /* strict mode: every element's own valid Tx-leg sequences */
     const int strict = C->P.strict_elements != 0;
     int64_t n_tx_ids = C->P.max_order_tx >= 2 ? (int64_t)F + (int64_t)F * F : (C->P.max_order_tx >= 1 ? F : 0);
@@ -687,13 +791,18 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
         v3 r = vf(rx_xyz + 3 * i);
         int amb = tx_amb;
         double complex e0 = 0.0;
-        double s0 = 0.0;
+        double s0 = 0.0, s03 = 0.0;
+        cv3 e03 = {0.0, 0.0, 0.0}, t3;
         /* LOS (Friis form of Eq. 4 + Eq. 8) */
         if (!blocked_decision(C, C->tx, r, -1, -1, &amb)) {
             leg_t g = leg_by_images(C, C->tx, r, NULL, 0);
-            double complex v = direct_term(C, &g);
+            double complex v = vec ? direct_term_vec(C, &g, &t3) : direct_term(C, &g);
             e0 += v;
             s0 += cabs(v);
+            if (vec) {
+                e03 = cv_add(e03, t3);
+                s03 += cv_norm(t3);
+            }
         }
         /* valid Rx-leg sequences (validated once at the RIS centre) and environment paths */
         int64_t* rx_ids = (int64_t*)malloc(sizeof(int64_t) * (n_ids > 0 ? n_ids : 1));
@@ -706,15 +815,20 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
                 rx_ids[n_q++] = id;
             if (C->P.env_paths && seq_allowed(C, seq, k, 2) && validate_seq(C, C->tx, -1, r, -1, seq, k, &amb, pts)) {
                 leg_t g = leg_by_images(C, C->tx, r, seq, k);
-                double complex v = direct_term(C, &g);
+                double complex v = vec ? direct_term_vec(C, &g, &t3) : direct_term(C, &g);
                 e0 += v;
                 s0 += cabs(v);
+                if (vec) {
+                    e03 = cv_add(e03, t3);
+                    s03 += cv_norm(t3);
+                }
             }
         }
         int64_t* m_rx = strict ? (int64_t*)malloc(sizeof(int64_t) * (n_ids > 0 ? n_ids : 1)) : NULL;
         for (int m = 0; m < M; ++m) {
             double complex a = 0.0;
-            double sa = 0.0;
+            double sa = 0.0, sa3 = 0.0;
+            cv3 a3 = {0.0, 0.0, 0.0};
             int rx_direct = !blocked_decision(C, C->e[m], r, hf, -1, &amb);
             /* the element's reflected legs: validated once at the RIS centre (Sec. II-B), or, in strict
                mode, between the element itself and each end */
@@ -752,20 +866,40 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
                         rk = decode_seq(C, mr_ids[q], rseq);
                     }
                     leg_t gr = leg_by_images(C, C->e[m], r, rseq, rk);
-                    double complex v = ris_term(C, &gt, &gr);
+                    double complex v = vec ? ris_term_vec(C, &gt, &gr, &t3) : ris_term(C, &gt, &gr);
                     a += v;
                     sa += cabs(v);
+                    if (vec) {
+                        a3 = cv_add(a3, t3);
+                        sa3 += cv_norm(t3);
+                    }
                 }
             }
             A[(i * M + m) * 2] = creal(a);
             A[(i * M + m) * 2 + 1] = cimag(a);
             SA[i * M + m] = sa;
+            if (A3) {
+                double complex c3[3] = {a3.x, a3.y, a3.z};
+                for (int j = 0; j < 3; ++j) {
+                    A3[((i * M + m) * 3 + j) * 2] = creal(c3[j]);
+                    A3[((i * M + m) * 3 + j) * 2 + 1] = cimag(c3[j]);
+                }
+                SA3[i * M + m] = sa3;
+            }
         }
         free(m_rx);
         free(rx_ids);
         E0[2 * i] = creal(e0);
         E0[2 * i + 1] = cimag(e0);
         S0[i] = s0;
+        if (E03) {
+            double complex c3[3] = {e03.x, e03.y, e03.z};
+            for (int j = 0; j < 3; ++j) {
+                E03[(i * 3 + j) * 2] = creal(c3[j]);
+                E03[(i * 3 + j) * 2 + 1] = cimag(c3[j]);
+            }
+            S03[i] = s03;
+        }
         amb_out[i] = amb;
     }
     free(tx_ids);
@@ -774,6 +908,22 @@ int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, dou
     free(stx_n);
     free(stx_amb);
     return 0;
+}
+
+int or_field(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, double* S0, double* A,
+             double* SA, int32_t* amb_out, int32_t max_paths)
+{
+    (void)max_paths;
+    return field_impl(C, rx_xyz, n_rx, E0, S0, A, SA, amb_out, NULL, NULL, NULL, NULL);
+}
+
+/* Vector mode: or_field's outputs (the received values) and the field vectors E03 [n][3], A3 [n][M][3]
+   (complex, as interleaved pairs) with their incoherent magnitudes S03, SA3 (sums of term norms). */
+int or_field_vec(const or_ctx* C, const float* rx_xyz, int64_t n_rx, double* E0, double* S0, double* A, double* SA,
+                 int32_t* amb_out, double* E03, double* S03, double* A3, double* SA3)
+{
+    if (!C->P.vector_pol) return -1;
+    return field_impl(C, rx_xyz, n_rx, E0, S0, A, SA, amb_out, E03, S03, A3, SA3);
 }
 
 /* Strict mode's path sets of element m (its reflected legs validated at the element itself):
@@ -846,6 +996,7 @@ int or_element_paths(const or_ctx* C, int m, const float* rx_xyz, int64_t n_rx, 
 int or_cir(const or_ctx* C, const float* rx_xyz, int64_t n_rx, const double* gamma, int32_t cap, double* amp,
            double* sabs, double* delay, int64_t* p_id, int64_t* q_id, int32_t* count)
 {
+    if (C->P.vector_pol) return -1;           /* taps of the scalar model only */
     int F = C->F, hf = C->P.host_face, M = C->P.M;
     int64_t tcap = 1 << 20;
     int64_t* tx_ids = (int64_t*)malloc(sizeof(int64_t) * tcap);

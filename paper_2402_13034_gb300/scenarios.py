@@ -110,6 +110,7 @@ class Antenna:
     power_w: float = 1.0
     gain_lin: float = 1.0
     pattern: int = PATTERN_ISO
+    pol: np.ndarray | None = None   # float32 [3] polarisation axis (global), for the vector field; None: unset
 
 
 @dataclass
