@@ -295,6 +295,36 @@ int risrt_eval_field_strict(risrt_ctx* ctx, const risrt_scene* scene, const risr
 int risrt_eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, float* taps_out, double* rx_delay_out,
                    double* tx_delay_out);
 
+/* Polarisation axis (unit vector, global frame; normalised here) of the Tx or Rx antenna for the vector
+ * field. A dipole or monopole's axis is its own; a horn's is the direction of its aperture field. The
+ * axes in force when a vector-field call is made are used. Errors: RISRT_ERR_INVALID_ARG for a zero
+ * or non-finite axis. */
+int risrt_antenna_set_polarization(risrt_ctx* ctx, int which, const float axis[3]);
+
+/* Vector field with polarisation (the extension of Eq. 6 named in Sec. II-A) over the paths of ps,
+ * which must have been traced with `scene` and `rxset`. Every path keeps the scalar model's factors
+ * (Eqs. 4-8) but the Fresnel products and carries a field vector: launched along the Tx axis projected
+ * on the wavefront (unit length), split at every bounce into TE (along unit(k_in x n), R_TE) and TM
+ * (R_TM, from s x k_in to s x k_out) parts with complex permittivities (RISRT_FLAG_FRESNEL_TM has no
+ * effect here), re-radiated by the RIS as Gamma_m times the incident field with its normal component
+ * reversed and restricted to the outgoing wavefront, and received on the Rx axis projected on the
+ * arrival wavefront (unit length). Directions of every segment are those of each element's own path.
+ *   gamma  [n_cfg][M] complex64 (device)
+ *   E_out  [n_cfg][n_rx] complex64: received values (LOS and environment paths included); with every
+ *          field TE and co-polarised they equal risrt_eval_field's (TE) values
+ *   E3_out [n_cfg][n_rx][3] complex64 or NULL: the field vectors (global frame, Eq. 8 amplitudes)
+ *   P_out  [n_cfg][n_rx] float or NULL: |E|^2 / (2 eta0) of the received value (Eq. 10)
+ * Enqueued on the context's stream. Errors: RISRT_ERR_NOT_READY if an axis is unset or an asynchronous
+ * path set is unchecked; RISRT_ERR_INVALID_ARG for another scene or receiver set (by size). */
+int risrt_eval_field_vec(risrt_ctx* ctx, const risrt_scene* scene, const risrt_rxset* rxset, const risrt_pathset* ps,
+                         const float* gamma, int32_t n_cfg, float* E_out, float* E3_out, float* P_out);
+
+/* Channel matrix of the vector field's received values: A_out [n_rx][M] complex64 with the received
+ * E = E0 + A . Gamma, E0_out [n_rx] complex64 or NULL (LOS and environment paths). A_out can feed the
+ * sweeps through risrt_amat_wrap. Arguments and errors as risrt_eval_field_vec. */
+int risrt_build_A_vec(risrt_ctx* ctx, const risrt_scene* scene, const risrt_rxset* rxset, const risrt_pathset* ps,
+                      float* A_out, float* E0_out);
+
 /* Dense channel matrix (Eq. 9 is linear in Gamma): A [n_rx][M] complex64 with A[r][m] = c_m sum_q b_mq(r),
  * so that E = E0 + A . Gamma, and E0 [n_rx] complex64.
  *  - A_out != NULL: written into caller memory (E0_out may be NULL). If resident_out != NULL,

@@ -697,6 +697,54 @@ int risrt_eval_field_strict(risrt_ctx* ctx, const risrt_scene* scene, const risr
                              n_cfg, (float2*)E_out, P_out);
 }
 
+int risrt_antenna_set_polarization(risrt_ctx* ctx, int which, const float axis[3])
+{
+    RISRT_CHECK_CTX(ctx);
+    if (which != RISRT_TX && which != RISRT_RX) return fail(ctx, RISRT_ERR_INVALID_ARG, "which must be RISRT_TX or RISRT_RX");
+    if (!axis) return fail(ctx, RISRT_ERR_INVALID_ARG, "axis is NULL");
+    const double n = std::sqrt((double)axis[0] * axis[0] + (double)axis[1] * axis[1] + (double)axis[2] * axis[2]);
+    if (!(n > 0) || !std::isfinite(n)) return fail(ctx, RISRT_ERR_INVALID_ARG, "axis must be a finite non-zero vector");
+    for (int k = 0; k < 3; ++k) ctx->pol[which][k] = (float)(axis[k] / n);
+    ctx->pol_set[which] = true;
+    return RISRT_OK;
+}
+
+// Shared checks of the vector-field calls: the scene and receivers the path set was traced with, both
+// polarisation axes set, and an asynchronous path set checked since its last run.
+static int check_vec_args(risrt_ctx* ctx, const risrt_scene* scene, const risrt_rxset* rxset, const risrt_pathset* ps)
+{
+    if (!scene || !rxset || !ps) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->pol_set[RISRT_TX] || !ctx->pol_set[RISRT_RX])
+        return fail(ctx, RISRT_ERR_NOT_READY, "set both polarisation axes (risrt_antenna_set_polarization)");
+    if (rxset->n != ps->n_rx || scene->n_faces != ps->n_faces)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "scene and receivers must be those the path set was traced with");
+    if (ps->external)
+        if (int rc = pathset_sync(ps))
+            return fail(ctx, rc, rc == RISRT_ERR_NOT_READY ? "call risrt_trace_check after an asynchronous trace" : "CUDA error");
+    return RISRT_OK;
+}
+
+int risrt_eval_field_vec(risrt_ctx* ctx, const risrt_scene* scene, const risrt_rxset* rxset, const risrt_pathset* ps,
+                         const float* gamma, int32_t n_cfg, float* E_out, float* E3_out, float* P_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!gamma || !E_out || n_cfg < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "NULL argument or n_cfg < 1");
+    if (((uintptr_t)gamma | (uintptr_t)E_out | (uintptr_t)E3_out) & 7u)
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    if (int rc = check_vec_args(ctx, scene, rxset, ps)) return rc;
+    return eval_field_vec(ctx, scene, rxset, ps, (const float2*)gamma, n_cfg, (float2*)E_out, (float2*)E3_out, P_out);
+}
+
+int risrt_build_A_vec(risrt_ctx* ctx, const risrt_scene* scene, const risrt_rxset* rxset, const risrt_pathset* ps,
+                      float* A_out, float* E0_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!A_out) return fail(ctx, RISRT_ERR_INVALID_ARG, "A_out is NULL");
+    if (((uintptr_t)A_out | (uintptr_t)E0_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    if (int rc = check_vec_args(ctx, scene, rxset, ps)) return rc;
+    return build_A_vec(ctx, scene, rxset, ps, (float2*)A_out, (float2*)E0_out);
+}
+
 int risrt_eval_cir(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, float* taps_out, double* rx_delay_out,
                    double* tx_delay_out)
 {

@@ -3,12 +3,9 @@
 // does not decide them.
 #pragma once
 
-#include "internal.cuh"
+#include "frame.cuh"
 
 namespace risrt {
-
-__device__ __forceinline__ d3 ld3(const dv4& p) { return D3(p.x, p.y, p.z); }
-__device__ __forceinline__ d3 ldv(const float4& p) { return D3((double)p.x, (double)p.y, (double)p.z); }
 
 // ------------------------------------------------------------------------------------------------
 // triangle tests

@@ -181,6 +181,8 @@ struct risrt_ctx {
     size_t allocated = 0;        // bytes of every block this context holds (in use or cached)
     std::string err;
     Antenna tx{}, rx{};
+    float pol[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};   // unit polarisation axes (Tx, Rx) of the vector field
+    bool pol_set[2] = {false, false};
     // tracing
     bool profiling = false;
     std::string prof_only;       // non-empty: only kernels of this name are bracketed
@@ -333,6 +335,7 @@ struct risrt_pathset {
     int64_t cap_tx_vis = 0;
     risrt::Frame fr{};
     risrt::AntD txa{};
+    risrt::AntD rxa{};                    // the Rx antenna of the trace (gain, pattern, boresight)
     risrt::WaveD wv{};
     double K = 0.0;
     // asynchronous traces: every device array lives in the caller's workspace (external), and the
@@ -434,6 +437,10 @@ int eval_field_accum(risrt_ctx* ctx, const risrt_pathset* ps, const float2* gamm
 int eval_field_strict(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, const risrt_rxset* rxs, double freq,
                       int max_tx, int max_rx, uint32_t flags, const float2* gamma, int n_cfg, float2* E, float* P);
 int microbench(risrt_ctx* ctx, int kind, int iters, double* ops_per_s, double* ms);
+int eval_field_vec(risrt_ctx* ctx, const risrt_scene* sc, const risrt_rxset* rxs, const risrt_pathset* ps,
+                   const float2* gamma, int n_cfg, float2* E, float2* E3, float* P);
+int build_A_vec(risrt_ctx* ctx, const risrt_scene* sc, const risrt_rxset* rxs, const risrt_pathset* ps, float2* A,
+                float2* E0);
 size_t grad_workspace_bytes(int n_t, int B, int M, int precision);
 int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes);
 int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,

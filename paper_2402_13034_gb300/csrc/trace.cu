@@ -9,22 +9,13 @@
 #include <string>
 
 #include "cplx32.cuh"
+#include "frame.cuh"
 #include "geom.cuh"
 
 namespace risrt {
 namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
-__device__ __forceinline__ d3 fr_c(const Frame& F) { return D3(F.c[0], F.c[1], F.c[2]); }
-__device__ __forceinline__ d3 fr_t1(const Frame& F) { return D3(F.t1[0], F.t1[1], F.t1[2]); }
-__device__ __forceinline__ d3 fr_t2(const Frame& F) { return D3(F.t2[0], F.t2[1], F.t2[2]); }
-__device__ __forceinline__ d3 fr_n(const Frame& F) { return D3(F.n[0], F.n[1], F.n[2]); }
-
-__device__ __forceinline__ d3 elem_pos(const Frame& F, float4 e)
-{
-    return fr_c(F) + fr_t1(F) * (double)e.x + fr_t2(F) * (double)e.y;
-}
 
 // ------------------------------------------------------------------------------------------------
 // sequence tables
@@ -1163,18 +1154,6 @@ __global__ void k_tx_vis(DeviceScene S, const float4* __restrict__ elem, int M, 
 // frac(L / lambda), FP32 for directions, Fresnel products and patterns (they enter amplitudes only).
 // ------------------------------------------------------------------------------------------------
 
-// FP32 face data for the per-path terms: unit normal and complex permittivity of the face's material.
-__device__ __forceinline__ float3 face_n32(const DeviceScene& S, int f)
-{
-    const float4 p = S.faces[f].plane32;
-    return f3(p.x, p.y, p.z);
-}
-__device__ __forceinline__ float2 face_eps32(const DeviceScene& S, int f, const WaveD& wv)
-{
-    const float2 m = S.mats[S.faces[f].mat];
-    return make_float2(m.x, -m.y * wv.inv_we);
-}
-__device__ __forceinline__ float3 mirror_dir_f(float3 v, float3 n) { return v - n * (2.f * dot(n, v)); }
 
 // One Tx-leg term of element e from the Tx image Ts across k faces (nf / ef: FP32 normals and complex
 // permittivities of the faces in propagation order): sqrt(2 eta0 Pt Gt Ft) sqrt(F_in) R_p e^{-jkL} / L
@@ -1925,6 +1904,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     }
     ps->fr = fr;
     ps->txa = tx;
+    ps->rxa = rxa;
     ps->wv = wv;
     ps->K = K;
     if (!at || at->ws) RISRT_CUDA(ctx, cudaMemcpyAsync(ps->elem, ris->elem, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s));

@@ -53,6 +53,9 @@ _SIGS = {
     "risrt_eval_cir": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "risrt_eval_field_strict": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.c_int32, C.c_uint32, _P, C.c_int32,
                                           _P, _P]),
+    "risrt_antenna_set_polarization": (C.c_int, [_P, C.c_int, _P]),
+    "risrt_eval_field_vec": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, _P, _P, _P]),
+    "risrt_build_A_vec": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "risrt_microbench": (C.c_int, [_P, C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "risrt_build_A": (C.c_int, [_P, _P, _P, _P, C.POINTER(_P)]),
     "risrt_amat_wrap": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.POINTER(_P)]),
@@ -322,6 +325,11 @@ class Context:
         self._check(load().risrt_antenna_set(self._ptr, which, _ptr(p), _ptr(o), float(power_w), float(gain_lin),
                                              int(pattern)))
 
+    def antenna_set_polarization(self, which, axis):
+        """Polarisation axis (global frame) of the Tx or Rx antenna for the vector field."""
+        a = _f32(axis, 3)
+        self._check(load().risrt_antenna_set_polarization(self._ptr, which, _ptr(a)))
+
     def rx_upload(self, rx_xyz) -> RxSet:
         r = _f32(rx_xyz)
         out = C.c_void_p()
@@ -392,6 +400,22 @@ class Context:
                                                    int(max_order_tx), int(max_order_rx), int(flags),
                                                    _dev_ptr(gamma, "torch.complex64"), n_cfg,
                                                    _dev_ptr(E_out, "torch.complex64"), _dev_ptr(P_out, "torch.float32")))
+
+    def eval_field_vec(self, scene: Scene, rxset: RxSet, ps: PathSet, gamma, E_out, E3_out=None, P_out=None):
+        """Vector field with polarisation over the paths of ps (traced with scene and rxset): received
+        values E_out complex64 [C, n_rx], field vectors E3_out complex64 [C, n_rx, 3] or None, P_out
+        float32 [C, n_rx] or None; gamma complex64 CUDA [C, M]."""
+        n_cfg = gamma.shape[0] if gamma.dim() == 2 else 1
+        self._check(load().risrt_eval_field_vec(self._ptr, scene.ptr, rxset.ptr, ps.ptr,
+                                                _dev_ptr(gamma, "torch.complex64"), n_cfg,
+                                                _dev_ptr(E_out, "torch.complex64"), _dev_ptr(E3_out, "torch.complex64"),
+                                                _dev_ptr(P_out, "torch.float32")))
+
+    def build_A_vec(self, scene: Scene, rxset: RxSet, ps: PathSet, A_out, E0_out=None):
+        """Channel matrix of the vector field's received values into A_out [n_rx, M] and E0_out [n_rx]
+        (complex64 CUDA)."""
+        self._check(load().risrt_build_A_vec(self._ptr, scene.ptr, rxset.ptr, ps.ptr, _dev_ptr(A_out, "torch.complex64"),
+                                             _dev_ptr(E0_out, "torch.complex64")))
 
     def eval_cir(self, ps: PathSet, gamma):
         """RIS channel impulse response for one configuration gamma (complex64 CUDA [M]): returns
@@ -529,5 +553,9 @@ def upload_workload(ctx: Context, w, rx_device=None):
                          w.ris.host_face)
     ctx.antenna_set(TX, w.tx.pos, w.tx.orient, w.tx.power_w, w.tx.gain_lin, w.tx.pattern)
     ctx.antenna_set(RX, None, w.rx.orient, w.rx.power_w, w.rx.gain_lin, w.rx.pattern)
+    if getattr(w.tx, "pol", None) is not None:
+        ctx.antenna_set_polarization(TX, w.tx.pol)
+    if getattr(w.rx, "pol", None) is not None:
+        ctx.antenna_set_polarization(RX, w.rx.pol)
     rx = ctx.rx_bind(rx_device) if rx_device is not None else ctx.rx_upload(w.rx_xyz)
     return scene, ris, rx
