@@ -11,6 +11,7 @@ metric (bounded receiver samples per step) instead.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import os
 import subprocess
@@ -65,7 +66,7 @@ PRECISIONS = {0: "fp32_simt", 1: "bf16", 2: "bf16x2", 3: "fp16"}
 # with: a changed source reports null traffic until the capture is repeated.
 DOMINANT = "k_validate"      # the kernel whose launches the timed region brackets with events
 MEASURED_TRAFFIC = {
-    "k_validate": {"bytes_per_step": 196.0e6, "sha256_16": "9555eb150b5c8b4f",
+    "k_validate": {"bytes_per_step": 196.25e6, "sha256_16": "49a3a3636c401269",
                    "sources": [("trace.cu", "k_validate("), ("geom.cuh", None), ("scene.cu", None)],
                    "profile": "profiles/k_validate_room_256x256_dram.md"},
 }
@@ -199,6 +200,54 @@ def bench_plain_fp32(ctx, R, dev, w, ps, gam, E, P, flush, reps=5, oracle_rx=97)
     return {"eval_ms": t_eval, "plain_fp32_eval_ms": t_plain, "eval_evals_per_s": units / (t_eval / 1e3),
             "plain_fp32_evals_per_s": units / (t_plain / 1e3), "eval_speedup": t_plain / t_eval,
             "error_eval": err(E_fast), "error_plain_fp32": err(E_plain), "oracle_receivers": int(len(idx))}
+
+
+def bench_vector(ctx, R, dev, w, scene, rxs, ps, gam, flush, reps=5, oracle_rx=33):
+    """The vector field with polarisation (vertical Tx and Rx axes) on the same path set: device time
+    of one call (Tx-leg vectors, E0 and the field kernel) with received values only and with the field
+    vectors too, its units/s, and its errors against the oracle's vector mode on a receiver sample."""
+    import torch
+    from oracle import oracle as O
+    stream = torch.cuda.current_stream(dev)
+    axis = np.array([0.0, 0.0, 1.0], np.float32)
+    ctx.antenna_set_polarization(R.TX, axis)
+    ctx.antenna_set_polarization(R.RX, axis)
+    C = gam.shape[0]
+    Ev = torch.empty((C, w.n_rx), dtype=torch.complex64, device=dev)
+    E3 = torch.empty((C, w.n_rx, 3), dtype=torch.complex64, device=dev)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    t_rx = timed(lambda: ctx.eval_field_vec(scene, rxs, ps, gam, Ev))
+    t_3 = timed(lambda: ctx.eval_field_vec(scene, rxs, ps, gam, Ev, E3))
+    Eg, E3g = Ev.cpu().numpy().T, E3.cpu().numpy().transpose(1, 0, 2)
+    idx = np.unique(np.linspace(0, w.n_rx - 1, oracle_rx).astype(int))
+    wv = copy.copy(w)
+    wv.tx = copy.copy(w.tx)
+    wv.rx = copy.copy(w.rx)
+    wv.tx.pol, wv.rx.pol = axis, axis
+    fld = O.Oracle(wv, vector=True).field_vec(w.rx_xyz[idx])
+    E_ref, _, S_ref, E3_ref, S3_ref = O.Oracle.evaluate_vec(fld, w.gammas)
+    ok = ~fld["amb"]
+    Sd = np.where(S_ref > 0, S_ref, 1.0)
+    S3d = np.where(S3_ref > 0, S3_ref, 1.0)[..., None]
+    units = ps.stats().units * C
+    return {"ms_received": t_rx, "ms_with_vectors": t_3, "evals_per_s_received": units / (t_rx / 1e3),
+            "evals_per_s_with_vectors": units / (t_3 / 1e3), "axes": "Tx z, Rx z",
+            "max_err_received_over_S": float((np.abs(Eg[idx] - E_ref) / Sd)[ok].max()),
+            "max_err_vectors_over_S3": float((np.abs(E3g[idx] - E3_ref) / S3d)[ok].max()),
+            "oracle_receivers": int(ok.sum())}
 
 
 def bench_gradient(ctx, R, dev, steps=200, reps=5):
@@ -516,25 +565,33 @@ def run_reference(args, w, n_cfg):
 
 
 def run_case(args):
-    """Small fixed cases for profilers: 'trace' (room workload at --grid, two traces and an eval) and
-    'sweep' (16,384 receivers x 1,024 elements x 1,024 configurations, --precision)."""
+    """Small fixed cases for profilers: 'trace' (room workload at --grid, two traces and an eval),
+    'vector' (the same with the vector field, vertical Tx and Rx axes, field vectors on) and 'sweep'
+    (16,384 receivers x 1,024 elements x 1,024 configurations, --precision)."""
     import torch
     from paper_2402_13034_gb300 import build as B
     from paper_2402_13034_gb300 import risrt as R
     B.build()
     ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
-    if args.case == "trace":
+    if args.case in ("trace", "vector"):
         w = S.room(grid=args.grid)
         scene, ris, rx = R.upload_workload(ctx, w)
         g = torch.from_numpy(w.gammas).cuda()
         E = torch.empty((g.shape[0], w.n_rx), dtype=torch.complex64, device="cuda")
         P = torch.empty((g.shape[0], w.n_rx), dtype=torch.float32, device="cuda")
+        E3 = torch.empty((g.shape[0], w.n_rx, 3), dtype=torch.complex64, device="cuda")
+        axis = np.array([0.0, 0.0, 1.0], np.float32)
+        ctx.antenna_set_polarization(R.TX, axis)
+        ctx.antenna_set_polarization(R.RX, axis)
         ps = None
         for _ in range(2):
             ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w), reuse=ps)
-            ctx.eval_field(ps, g, E, P)
+            if args.case == "trace":
+                ctx.eval_field(ps, g, E, P)
+            else:
+                ctx.eval_field_vec(scene, rx, ps, g, E, E3, P)
         torch.cuda.synchronize()
-        print(json.dumps({"case": "trace", "grid": args.grid, "units": ps.stats().units}))
+        print(json.dumps({"case": args.case, "grid": args.grid, "units": ps.stats().units}))
     else:
         n, M, C = 16384, 1024, 1024
         rng = np.random.default_rng(0)
@@ -563,7 +620,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--case", choices=["trace", "sweep"], default=None,
+    ap.add_argument("--case", choices=["trace", "vector", "sweep"], default=None,
                     help="run a small fixed case for a profiler instead of the benchmark")
     ap.add_argument("--precision", type=int, default=1)
     args = ap.parse_args()
@@ -776,6 +833,7 @@ def main():
     plain = None
     vs_baseline = None
     free = None
+    vector = None
     if rank == 0:
         plain = bench_plain_fp32(ctx, R, dev, w, ps, gam, E, P, flush)
         # the same step with the plain FP32 field evaluation in place of eval_field
@@ -784,6 +842,8 @@ def main():
         plain["step_evals_per_s_with_plain_eval"] = units / (plain_step_ms / 1e3)
         vs_baseline = plain_step_ms / ms_per_step
         free = bench_free_space(ctx, R, dev)
+        vector = bench_vector(ctx, R, dev, w, scene, rxs, ps, gam, flush)
+        vector["vs_scalar_eval_ms"] = vector["ms_received"] / plain["eval_ms"]
     sweep = None
     if rank == 0 and not args.no_sweep:
         sweep = bench_sweep(ctx, R, dev)
@@ -819,7 +879,7 @@ def main():
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "roofline_field": roof_field, "measured_peaks": mpeaks, "cpu_baseline": cpu,
-                "vs_plain_fp32": plain, "free_space": free,
+                "vs_plain_fp32": plain, "free_space": free, "vector_field": vector,
                 "stages": stages, "sweep": sweep, "gradient": grad, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
