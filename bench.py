@@ -150,8 +150,65 @@ def bench_free_space(ctx, R, dev, steps=20):
     out = {"workload": w.name, "n_rx": w.n_rx, "elements": w.n_elem, "n_cfg": int(g.shape[0]),
            "units_per_step": units, "step_us": ms * 1e3, "eval_us": float(np.median(te)) * 1e3,
            "evals_per_s": units / (ms / 1e3), "note": "median of %d steps; trace includes its host round trips" % steps}
+    E_ref = E.clone()
     for h in (ps, rx, ris, scene):
         h.close()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    gr = bench_graph(R, dev, w, E_ref, flush, steps=steps)
+    out["graph"] = gr
+    out["graph_step_us"] = gr["ms_per_step"] * 1e3
+    return out
+
+
+def bench_graph(R, dev, w, E_ref, flush, steps=20):
+    """Trace + field evaluation as one CUDA graph: the asynchronous trace (no host round trip, every
+    array in a workspace) and eval_field captured on a stream of their own, replayed `steps` times
+    with the L2 flushed before each; device time per replay (events on the graph's stream), the
+    regular step's result compared bitwise, and the workspace size."""
+    import torch
+    gs = torch.cuda.Stream(dev)
+    ctx = R.Context(dev.index, gs.cuda_stream)
+    out = {}
+    with torch.cuda.stream(gs):
+        scene, ris, rx = R.upload_workload(ctx, w)
+        flags = R.flags_of(w)
+        ws, lim = ctx.trace_workspace(scene, ris, rx, w.max_order_tx, w.max_order_rx, flags, cand_cap=512,
+                                      max_paths=64, max_env=64)
+        g = torch.from_numpy(np.ascontiguousarray(w.gammas, np.complex64)).to(dev)
+        E = torch.empty((g.shape[0], w.n_rx), dtype=torch.complex64, device=dev)
+        P = torch.empty((g.shape[0], w.n_rx), dtype=torch.float32, device=dev)
+        ps = ctx.trace_paths_async(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, flags, ws, lim)
+        ctx.trace_check(ps)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        graph.capture_begin(capture_error_mode="thread_local")
+        try:
+            ctx.trace_paths_async(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, flags, ws, lim, reuse=ps)
+            ctx.eval_field(ps, g, E, P)
+        finally:
+            graph.capture_end()
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(gs)
+            graph.replay()
+            b.record(gs)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ctx.trace_check(ps)
+        units = ps.stats().units * g.shape[0]
+        ms = float(np.median(ts))
+        out = {"ms_per_step": ms, "evals_per_s": units / (ms / 1e3), "units_per_step": units,
+               "workspace_bytes": int(ws.numel()), "equals_regular_step": bool(torch.equal(E, E_ref)),
+               "note": "median of %d replays of one graph holding the asynchronous trace and eval_field" % steps}
+        del graph
+        for h in (ps, rx, ris, scene):
+            h.close()
+    torch.cuda.synchronize()
     return out
 
 
@@ -834,6 +891,7 @@ def main():
     vs_baseline = None
     free = None
     vector = None
+    graph = None
     if rank == 0:
         plain = bench_plain_fp32(ctx, R, dev, w, ps, gam, E, P, flush)
         # the same step with the plain FP32 field evaluation in place of eval_field
@@ -841,6 +899,11 @@ def main():
         plain["step_ms_with_plain_eval"] = plain_step_ms
         plain["step_evals_per_s_with_plain_eval"] = units / (plain_step_ms / 1e3)
         vs_baseline = plain_step_ms / ms_per_step
+        # the timed step's field (its path set carries the room's antennas; the free-space case below
+        # sets the context's own)
+        E_step = torch.empty_like(E)
+        ctx.eval_field(ps, gam, E_step, P)
+        graph = bench_graph(R, dev, w.__class__(**{**w.__dict__, "rx_xyz": rx_host}), E_step, flush, steps=10)
         free = bench_free_space(ctx, R, dev)
         vector = bench_vector(ctx, R, dev, w, scene, rxs, ps, gam, flush)
         vector["vs_scalar_eval_ms"] = vector["ms_received"] / plain["eval_ms"]
@@ -879,7 +942,7 @@ def main():
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "roofline_field": roof_field, "measured_peaks": mpeaks, "cpu_baseline": cpu,
-                "vs_plain_fp32": plain, "free_space": free, "vector_field": vector,
+                "vs_plain_fp32": plain, "free_space": free, "vector_field": vector, "graph_step": graph,
                 "stages": stages, "sweep": sweep, "gradient": grad, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
