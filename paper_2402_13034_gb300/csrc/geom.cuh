@@ -86,10 +86,30 @@ __device__ __forceinline__ float box_entry(float4 lo, float4 hi, float3 a, float
     return tmin <= tmax ? tmin : __int_as_float(0x7f800000);
 }
 
-__device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d)); }
+// Entry parameter with the segment's a * inv precomputed: one FMA per slab plane, t = lo inv - a inv.
+__device__ __forceinline__ float box_entry_fma(float4 lo, float4 hi, float3 inv, float3 ainv)
+{
+    float tx0 = fmaf(lo.x, inv.x, -ainv.x), tx1 = fmaf(hi.x, inv.x, -ainv.x);
+    float ty0 = fmaf(lo.y, inv.y, -ainv.y), ty1 = fmaf(hi.y, inv.y, -ainv.y);
+    float tz0 = fmaf(lo.z, inv.z, -ainv.z), tz1 = fmaf(hi.z, inv.z, -ainv.z);
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), 1.f));
+    return tmin <= tmax ? tmin : __int_as_float(0x7f800000);
+}
 
-struct TraceCounters {
-    unsigned long long cand, segs, nodes, tris;
+// Reciprocal by one special-function instruction (about 1 ulp, denormal inputs flushed). Slab tests
+// take it: every BVH box is padded by 1e-4 (1 + scene extent), many orders of magnitude above the
+// position error an ulp of the inverse direction (or of a * inv) makes at the slab planes.
+__device__ __forceinline__ float rcp_slab(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float safe_inv(float d) { return rcp_slab(fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d)); }
+
+struct TraceCounters {           // per thread (32 bits each; widened when flushed)
+    unsigned cand, segs, nodes, tris;
 };
 
 // Warp-aggregated add of the per-thread counters (all lanes of the warp must call it).
@@ -104,11 +124,11 @@ __device__ __forceinline__ void flush_counters(const TraceCounters& t, unsigned 
     }
 }
 
-// One step of a four-wide walk along the segment a + t dir, t in [0, 1] (inv = 1 / dir): the children
-// the segment enters, except subtrees made only of the faces g0 / g1, nearest entry first. Returns
-// the nearest (kNoChild if none) and pushes the others farthest first; the caller keeps 3 free
-// stack entries.
-__device__ __forceinline__ int bvh4_step(const Bvh4Node& nd, float3 a, float3 inv, int g0, int g1, int* stack, int& sp)
+// One step of a four-wide walk along the segment a + t dir, t in [0, 1] (inv = 1 / dir, ainv = a * inv):
+// the children the segment enters, except subtrees made only of the faces g0 / g1, nearest entry
+// first. Returns the nearest (kNoChild if none) and pushes the others farthest first; the caller keeps
+// 3 free stack entries.
+__device__ __forceinline__ int bvh4_step(const Bvh4Node& nd, float3 inv, float3 ainv, int g0, int g1, int* stack, int& sp)
 {
     float t[4];
     int c[4];
@@ -116,7 +136,7 @@ __device__ __forceinline__ int bvh4_step(const Bvh4Node& nd, float3 a, float3 in
     for (int k = 0; k < 4; ++k) {
         c[k] = __float_as_int(nd.lo[k].w);
         const int f = __float_as_int(nd.hi[k].w);
-        t[k] = (c[k] != kNoChild && f != g0 && f != g1) ? box_entry(nd.lo[k], nd.hi[k], a, inv) : 3e38f;
+        t[k] = (c[k] != kNoChild && f != g0 && f != g1) ? box_entry_fma(nd.lo[k], nd.hi[k], inv, ainv) : 3e38f;
     }
     auto cs = [&](int i, int j) {
         if (t[j] < t[i]) {
@@ -170,6 +190,7 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
     float3 dir = b - a;
     float len = sqrtf(dot(dir, dir));
     float3 inv = f3(safe_inv(dir.x), safe_inv(dir.y), safe_inv(dir.z));
+    const float3 ainv = f3(a.x * inv.x, a.y * inv.y, a.z * inv.z);
     float tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
     const int g0 = ign0 >= 0 ? ign0 : -3, g1 = ign1 >= 0 ? ign1 : -3;   // subtrees of one ignored face are skipped
     while (true) {
@@ -197,7 +218,7 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
         const Bvh4Node nd = S.nodes4[c];
         if (tc) ++tc->nodes;
         // any hit ends the query, so the children entered first along the segment are visited first
-        c = bvh4_step(nd, a, inv, g0, g1, stack, sp);
+        c = bvh4_step(nd, inv, ainv, g0, g1, stack, sp);
         if (c == kNoChild) {
             if (sp == 0) break;
             c = stack[--sp];

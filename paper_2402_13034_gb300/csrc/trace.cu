@@ -873,8 +873,9 @@ __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float*
 // first block); blocked candidates are set to -1. Persistent while-while traversal: each lane pulls
 // the next work-list entry (receiver, slot, sequence) from a warp-aggregated atomic counter as soon
 // as its current one is finished, computes the candidate's FP32 path points and their error bounds
-// (path_points), and every loop iteration advances each busy lane by at most kSteps BVH visits, so
-// lanes stay busy while traversal lengths differ. A first segment whose point lies in a decided cell
+// (path_points), and every loop iteration advances each busy lane by at most kSteps BVH visits,
+// moving on to the candidate's next segment within them, so lanes stay busy while traversal lengths
+// differ. A first segment whose point lies in a decided cell
 // of the source's visibility map takes the map's answer; a segment with both ends in the scene box
 // does not walk the shell subtree. Triangles too close to call in FP32 are queued for an FP64
 // settlement after the kernel. ctr[0..3]: candidates, segments, nodes, triangle tests.
@@ -907,7 +908,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     int r = 0, slot = 0, si = 0, j = 0;
     int4 info = make_int4(0, 0, 0, 0);
     float3 p[4] = {f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f)};
-    float3 a = f3(0.f, 0.f, 0.f), dir = a, inv = a;
+    float3 a = f3(0.f, 0.f, 0.f), dir = a, inv = a, ainv = a;
     float len = 0.f, tb = 0.f;
     int ign0 = -1, ign1 = -1, g0 = -3, g1 = -3;
     int stack[64];
@@ -921,6 +922,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         dir = p[j + 1] - a;
         len = sqrtf(dot(dir, dir));
         inv = f3(safe_inv(dir.x), safe_inv(dir.y), safe_inv(dir.z));
+        ainv = f3(a.x * inv.x, a.y * inv.y, a.z * inv.z);
         tb = tol_base + 2e-7f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + len);
         ign0 = j == 0 ? src_face : (j == 1 ? info.x : info.y);
         ign1 = j == info.w ? dst_face : (j == 0 ? info.x : info.y);
@@ -934,8 +936,9 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                 if (p1err <= 0.5f * kMapDelta) {
                     const FaceGrid g = S.face_grid[info.x];
                     const float3 dq = p[1] - xyz(g.o);
-                    const float fa = floorf((dot(dq, xyz(g.u)) - g.u.w) / g.o.w);
-                    const float fb = floorf((dot(dq, xyz(g.v)) - g.v.w) / g.dv);
+                    // (a cell's entry holds up to kMapDelta outside it, far beyond the reciprocal's ulp)
+                    const float fa = floorf((dot(dq, xyz(g.u)) - g.u.w) * rcp_slab(g.o.w));
+                    const float fb = floorf((dot(dq, xyz(g.v)) - g.v.w) * rcp_slab(g.dv));
                     if (fa >= 0.f && fa < (float)g.nu && fb >= 0.f && fb < (float)g.nv) {
                         const uint8_t st = smap[g.off + (int)fa * g.nv + (int)fb];
                         if (st != 0) {
@@ -1017,7 +1020,13 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         if (!__any_sync(FULL, active)) break;
         if (!active) continue;
         {
-            for (int it = 0; it < kSteps && cur != kNone; ++it) {
+            for (int it = 0; it < kSteps; ++it) {
+                if (cur == kNone) {          // segment done: the candidate's next segment right away
+                    if (blocked || j >= info.w) break;
+                    ++j;
+                    start_segment();
+                    continue;
+                }
                 if (cur < 0) {
                     if (test_leaf(~cur)) {
                         blocked = true;
@@ -1037,7 +1046,7 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                 }
                 const Bvh4Node nd = S.nodes4[cur];
                 ++tc.nodes;
-                cur = bvh4_step(nd, a, inv, g0, g1, stack, sp);   // nearest entered child next
+                cur = bvh4_step(nd, inv, ainv, g0, g1, stack, sp);   // nearest entered child next
                 if (cur == kNoChild) cur = sp > 0 ? stack[--sp] : kNone;
             }
         }
