@@ -47,7 +47,8 @@ int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh,
              int64_t n_rx, int C, float* P, float pscale, float e0scale, unsigned* err_dev, bool defer = false,
              float2* Eout = nullptr);
 
-// D = X . Y^T on SM pairs with split-K, complex partial sums out (see sweep_tc.cu).
+// D = X . Y^T on SM pairs with split-K, complex partial sums out; enqueued only, the caller clears
+// and reads err_dev (see sweep_tc.cu).
 int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, int Np, int Kp, const float2* E0rows, int C,
                     float2* out, int splits, int* parts, unsigned* err_dev);
 

@@ -624,7 +624,8 @@ int sweep_tc(risrt_ctx* ctx, const void* X, const void* Y, const SweepShape& sh,
 // D = X . Y^T on SM pairs (BF16, both K-major: X [rows][Kp], Y [Np][Kp]) with the reduction split
 // into about `splits` parts; writes the complex partial sums D[row][2c] + j D[row][2c + 1] (+ E0rows[row]
 // in part 0) to out[(z C + c) rows + row] and the number of parts to *parts. RISRT_ERR_NOT_READY when
-// the pair kernel cannot be placed on this device.
+// the pair kernel cannot be placed on this device. Enqueued only: the caller clears *err_dev before
+// and reads it after its last GEMM (an expired pipeline wait sets it).
 int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, int Np, int Kp, const float2* E0rows, int C,
                     float2* out, int splits, int* parts, unsigned* err_dev)
 {
@@ -642,7 +643,6 @@ int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, 
     const int tiles_m = (int)((rows + 2 * kTcBM - 1) / (2 * kTcBM)), tiles_n = Np / kTcBN;
     const int num_tiles = tiles_m * tiles_n * z;
     const int nc = num_tiles < ncl ? num_tiles : ncl;
-    RISRT_CUDA(ctx, cudaMemsetAsync(err_dev, 0, sizeof(unsigned), s));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -661,10 +661,6 @@ int gemm_tc_complex(risrt_ctx* ctx, const void* X, int64_t rows, const void* Y, 
                  (le = cudaLaunchKernelEx(&cfg, k_sweep_tc_pair, mX, mY, kb_per, tiles_n, num_tiles, idesc, E0rows, rows, C,
                                           (float*)nullptr, 0.f, 1.f, err_dev, kb_total, out, (float2*)nullptr, 1.f)));
     if (le != cudaSuccess) return cuda_fail(ctx, le, "k_sweep_tc_pair");
-    unsigned h = 0;
-    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
-    if (h) return fail(ctx, RISRT_ERR_TIMEOUT, "tensor-core GEMM: a pipeline wait expired");
     *parts = z;
     return RISRT_OK;
 }
