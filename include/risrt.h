@@ -391,6 +391,19 @@ int risrt_sweep_configs(risrt_ctx* ctx, const risrt_amat* amat, const float* gam
 #define RISRT_SWEEP_KEEP_A 0x100
 #define RISRT_SWEEP_DEFER_CHECK 0x200
 
+/* Fused channel tile -> tensor-core sweep over a path set (Eq. 9 linear in Gamma, Eq. 10): the channel
+ * matrix A[r][m] = c_m sum_q b_mq(r) of risrt_build_A is computed, 128 receivers x 32 elements at a
+ * time, straight into shared memory and consumed there by the tensor cores in BF16 (FP32
+ * accumulation); A is never written to memory. At most 128 configurations per call (one tensor-memory
+ * accumulator). Configurations as in risrt_sweep_configs: gamma [n_cfg][M] complex64 or gamma_2bit
+ * [n_cfg][ceil(M/4)] codes with amp. P_out [n_rx][n_cfg] float (|E|^2 / (2 eta0)) and/or E_out
+ * [n_rx][n_cfg] complex64, receiver-major. Arithmetic and accuracy as risrt_sweep_configs with
+ * RISRT_PREC_BF16 on the same path set's channel matrix. Synchronises the stream. Errors:
+ * RISRT_ERR_INVALID_ARG (n_cfg outside [1, 128], both or neither of gamma / gamma_2bit, no output),
+ * RISRT_ERR_TIMEOUT (a pipeline wait expired; the call's outputs are then undefined). */
+int risrt_sweep_fused(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, const uint8_t* gamma_2bit, float amp,
+                      int32_t n_cfg, float* P_out, float* E_out);
+
 /* After sweeps with RISRT_SWEEP_DEFER_CHECK on this workspace: waits for the context's stream and
  * returns RISRT_ERR_TIMEOUT if a pipeline wait of the last such sweep expired (its output is then
  * incomplete), else RISRT_OK. The flag is cleared by every sweep. */

@@ -886,6 +886,22 @@ int risrt_sweep_configs(risrt_ctx* ctx, const risrt_amat* amat, const float* gam
                          workspace, workspace_bytes, (opts & RISRT_SWEEP_KEEP_A) != 0, (opts & RISRT_SWEEP_DEFER_CHECK) != 0);
 }
 
+int risrt_sweep_fused(risrt_ctx* ctx, const risrt_pathset* ps, const float* gamma, const uint8_t* gamma_2bit, float amp,
+                      int32_t n_cfg, float* P_out, float* E_out)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!ps || (!gamma == !gamma_2bit) || (!P_out && !E_out))
+        return fail(ctx, RISRT_ERR_INVALID_ARG, "need the path set, exactly one of gamma / gamma_2bit, and P_out or E_out");
+    if (n_cfg < 1 || n_cfg > sweep_fused_max_configs()) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_cfg must be in [1, 128]");
+    if (gamma_2bit && !std::isfinite(amp)) return fail(ctx, RISRT_ERR_INVALID_ARG, "amp must be finite");
+    if (((uintptr_t)gamma | (uintptr_t)E_out) & 7u) return fail(ctx, RISRT_ERR_INVALID_ARG, "complex arrays must be 8-byte aligned");
+    GammaSrc G;
+    G.G = (const float2*)gamma;
+    G.g2 = gamma_2bit;
+    G.amp = amp;
+    return sweep_fused(ctx, ps, G, n_cfg, P_out, (float2*)E_out);
+}
+
 int risrt_sweep_check(risrt_ctx* ctx, const void* workspace, size_t workspace_bytes)
 {
     RISRT_CHECK_CTX(ctx);

@@ -38,6 +38,10 @@ struct GammaSrc {
 int sweep_configs(risrt_ctx* ctx, const float2* A, const float2* E0, int64_t n_rx, int M, GammaSrc G, int C,
                   int precision, float* P, float2* Eout, void* ws, size_t ws_bytes, bool keep_a = false,
                   bool defer = false);
+// Fused channel tile -> tensor-core sweep over a path set (A computed in shared memory, BF16): at most
+// sweep_fused_max_configs() configurations; P and/or Eout receiver-major [n_rx][C]. Synchronises.
+int sweep_fused(risrt_ctx* ctx, const risrt_pathset* ps, GammaSrc G, int C, float* P, float2* Eout);
+int sweep_fused_max_configs();
 // The deferred wait-timeout flag of the last sweep on this workspace (waits for the stream).
 int sweep_check(risrt_ctx* ctx, const void* ws, size_t ws_bytes);
 // D = X . Y^T on tcgen05 (X: [n_rx][Kp], Y: [Np][Kp], 16-bit, K-major), then

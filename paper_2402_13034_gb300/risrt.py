@@ -63,6 +63,7 @@ _SIGS = {
     "risrt_amat_destroy": (C.c_int, [_P, _P]),
     "risrt_sweep_workspace_size": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_sweep_configs": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_int32, C.c_int, _P, _P, _P, C.c_size_t]),
+    "risrt_sweep_fused": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_int32, _P, _P]),
     "risrt_sweep_check": (C.c_int, [_P, _P, C.c_size_t]),
     "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P, C.c_size_t, C.c_int]),
@@ -460,6 +461,15 @@ class Context:
 
     def _as_amat(self, A, E0):
         return A if isinstance(A, AMat) else self.amat(A, E0)
+
+    def sweep_fused(self, ps: PathSet, gamma, P_out=None, gamma_2bit=None, amp: float = 1.0, E_out=None):
+        """Fused channel tile -> tensor-core sweep over a path set (A never materialised), at most 128
+        configurations: gamma complex64 CUDA [C, M] (or gamma_2bit uint8 [C, ceil(M/4)] with amp);
+        P_out float32 [n_rx, C] and/or E_out complex64 [n_rx, C]."""
+        n_cfg = gamma.shape[0] if gamma is not None else gamma_2bit.shape[0]
+        self._check(load().risrt_sweep_fused(self._ptr, ps.ptr, _dev_ptr(gamma, "torch.complex64"),
+                                             _dev_ptr(gamma_2bit, "torch.uint8"), float(amp), int(n_cfg),
+                                             _dev_ptr(P_out, "torch.float32"), _dev_ptr(E_out, "torch.complex64")))
 
     def sweep_configs(self, A, E0, gamma, P_out, precision: int, workspace=None, keep_a: bool = False,
                       defer_check: bool = False, gamma_2bit=None, amp: float = 1.0, E_out=None):
