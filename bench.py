@@ -457,6 +457,10 @@ def bench_serving(dev_index, n_req=64, rate_hz=2000.0, slots=4):
     return out
 
 
+def st_units(ps):
+    return ps.stats().units
+
+
 def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
     """E = E0 + A Gamma for every receiver and configuration on the sweep workload (room with a
     32x32 RIS, 65,536 receivers, 4,096 two-bit configurations), per precision."""
@@ -524,6 +528,28 @@ def bench_sweep(ctx, R, dev, n_cfg=4096, reps=3, oracle_rows=48):
             ent["kernel_tflops_executed"] = 2.0 * Mp * Np * Kp / (kms / 1e3) / 1e12
         out[name] = ent
     ctx.profile_enable(False)
+    # the fused channel tile -> tensor-core sweep (A never materialised) against build_A + the BF16 sweep,
+    # at the 128 configurations one fused call takes
+    C1 = 128
+    G1 = G[:C1].contiguous()
+    P1 = torch.empty((n, C1), dtype=torch.float32, device=dev)
+    P2 = torch.empty((n, C1), dtype=torch.float32, device=dev)
+    ws1 = ctx.sweep_workspace(n, M, C1, R.PREC_BF16)
+
+    def unfused():
+        ctx.build_A(ps, A, E0)
+        ctx.sweep_configs(A, E0, G1, P2, R.PREC_BF16, ws1)
+
+    unfused()
+    ctx.sweep_fused(ps, G1, P1)
+    t_unf = timed(unfused, reps)
+    t_fus = timed(lambda: ctx.sweep_fused(ps, G1, P1), reps)
+    Pf, Pu = P1.cpu().numpy().astype(np.float64), P2.cpu().numpy().astype(np.float64)
+    sel = Pu > 1e-3 * Pu.max()
+    out["fused_128cfg"] = {"ms_fused": t_fus, "ms_build_A_plus_bf16_sweep": t_unf, "speedup": t_unf / t_fus,
+                           "evals_per_s_fused": st_units(ps) * C1 / (t_fus / 1e3),
+                           "max_db_fused_vs_unfused": float(np.max(np.abs(10 * np.log10(Pf[sel] / Pu[sel])))),
+                           "A_bytes_not_written": n * M * 8}
     out["speedup_bf16_vs_fp32"] = out["fp32_simt"]["ms"] / out["bf16"]["ms"]
     out["speedup_bf16x2_vs_fp32"] = out["fp32_simt"]["ms"] / out["bf16x2"]["ms"]
     peaks = _peaks()
@@ -623,8 +649,10 @@ def run_reference(args, w, n_cfg):
 
 def run_case(args):
     """Small fixed cases for profilers: 'trace' (room workload at --grid, two traces and an eval),
-    'vector' (the same with the vector field, vertical Tx and Rx axes, field vectors on) and 'sweep'
-    (16,384 receivers x 1,024 elements x 1,024 configurations, --precision)."""
+    'vector' (the same with the vector field, vertical Tx and Rx axes, field vectors on), 'grad' (the
+    office's 16,384 targets x 4,096 elements x 64 configurations, split-BF16 adjoint: one call packing
+    A, three keeping it) and 'sweep' (16,384 receivers x 1,024 elements x 1,024 configurations,
+    --precision)."""
     import torch
     from paper_2402_13034_gb300 import build as B
     from paper_2402_13034_gb300 import risrt as R
@@ -649,6 +677,22 @@ def run_case(args):
                 ctx.eval_field_vec(scene, rx, ps, g, E, E3, P)
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "grid": args.grid, "units": ps.stats().units}))
+    elif args.case == "grad":
+        w = S.office()
+        scene, ris, rx = R.upload_workload(ctx, w)
+        ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w))
+        A = torch.empty((w.n_rx, w.n_elem), dtype=torch.complex64, device="cuda")
+        E0 = torch.empty(w.n_rx, dtype=torch.complex64, device="cuda")
+        ctx.build_A(ps, A, E0)
+        phases = torch.from_numpy(w.extra["phases"]).cuda()
+        J = torch.empty(phases.shape[0], device="cuda")
+        g = torch.empty_like(phases)
+        ws = ctx.grad_workspace(w.n_rx, phases.shape[0], w.n_elem, R.PREC_BF16X2)
+        ctx.grad_phases(A, E0, None, phases, None, J, g, ws, R.PREC_BF16X2)
+        for _ in range(3):
+            ctx.grad_phases(A, E0, None, phases, None, J, g, ws, R.PREC_BF16X2, keep_a=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "grad", "targets": w.n_rx, "elements": w.n_elem, "configs": int(phases.shape[0])}))
     else:
         n, M, C = 16384, 1024, 1024
         rng = np.random.default_rng(0)
@@ -677,7 +721,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--case", choices=["trace", "vector", "sweep"], default=None,
+    ap.add_argument("--case", choices=["trace", "vector", "grad", "sweep"], default=None,
                     help="run a small fixed case for a profiler instead of the benchmark")
     ap.add_argument("--precision", type=int, default=1)
     args = ap.parse_args()

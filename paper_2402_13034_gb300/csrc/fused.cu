@@ -4,10 +4,11 @@
 // accumulator in tensor memory (128 configurations, Re/Im interleaved):
 //   warp 0      TMA producer of the configuration operand Y (128B-swizzled, 64 K columns per stage)
 //   warp 1      allocates the accumulator; one thread issues tcgen05.mma (M = 128, N = 256, K = 16)
-//   warps 2-5   epilogue: E = D + E0, P = |E|^2 / (2 eta0)
-//   warps 6-21  A producers: per stage 32 elements of 128 receivers, one element per lane, a warp per
-//               receiver row at a time (the row's path records broadcast to the warp), BF16 values
-//               written in the MMA's swizzled K-major layout
+//   warps 2-31  A producers: per stage 32 elements of 128 receivers, one element per lane, a warp per
+//               receiver row at a time (the row's path records broadcast to the warp; rows claimed
+//               from a per-stage counter, so warps with short rows take more), BF16 values written in
+//               the MMA's swizzled K-major layout; then warps 2-5 run the epilogue
+//               (E = D + E0, P = |E|^2 / (2 eta0))
 // K is ordered by blocks of 32 elements, [Re A | Im A] within a block, and Y's rows follow the same
 // order: D[r][2c] = sum Re A Re G - Im A Im G = Re E_c, D[r][2c + 1] = sum Re A Im G + Im A Re G.
 // Every mbarrier wait has a clock deadline; on expiry the kernel records an error and returns after
@@ -22,8 +23,11 @@ namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-constexpr int kFuseProd = 16;                          // producer warps
-constexpr int kFuseThreads = 192 + 32 * kFuseProd;
+#ifndef RISRT_FUSE_PROD
+#define RISRT_FUSE_PROD 30
+#endif
+constexpr int kFuseProd = RISRT_FUSE_PROD;             // producer warps
+constexpr int kFuseThreads = 64 + 32 * kFuseProd;
 constexpr int kFuseStages = 4;
 constexpr int kFStageA = kTcBM * kTcBK * 2;            // 16 KB: 128 rows x 64 BF16
 constexpr int kFStageB = kTcBN * kTcBK * 2;            // 32 KB: 256 rows x 64 BF16
@@ -60,12 +64,14 @@ k_sweep_fused(const __grid_constant__ CUtensorMap tmY, int nkb, uint32_t idesc, 
     uint64_t* tfull = empty + kFuseStages;
     uint32_t* tmem_slot = (uint32_t*)(tfull + 1);
     __shared__ int abort_flag;
+    __shared__ unsigned row_ctr[kFuseStages];   // rows claimed from each stage over all its uses
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m0 = (int64_t)blockIdx.x * kTcBM;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kFuseStages; ++s) {
+            row_ctr[s] = 0;
             mbar_init(smem_u32(&full[s]), 1 + kFuseProd);   // the TMA's arrive.expect_tx + one per producer warp
             mbar_init(smem_u32(&empty[s]), 1);
         }
@@ -124,33 +130,7 @@ k_sweep_fused(const __grid_constant__ CUtensorMap tmY, int nkb, uint32_t idesc, 
             }
             mma_commit(smem_u32(tfull));           // accumulator complete (or issued work drained)
         }
-    } else if (warp < 6) {   // epilogue warps 2..5: TMEM lanes 32*(warp%4) .. +31
-        const bool ok = mbar_wait(smem_u32(tfull), 0, deadline + kFuseWait);
-        if (!ok) {
-            atomicExch(err, 1u);
-            *(volatile int*)&abort_flag = 1;
-        }
-        fence_after();
-        const int lane_base = 32 * (warp & 3);
-        const int64_t row = m0 + lane_base + lane;
-        const bool live = ok && !*(volatile int*)&abort_flag && row < n_rx;
-        const float2 e0 = live ? E0[row] : make_float2(0.f, 0.f);
-        for (int j = 0; j < kTcBN / 16; ++j) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(j * 16), v);
-            if (!live) continue;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int c = j * 8 + q;
-                if (c < C) {
-                    const float er = v[2 * q] + e0.x, ei = v[2 * q + 1] + e0.y;
-                    if (P) P[row * C + c] = (er * er + ei * ei) * pscale;
-                    if (Eout) Eout[row * C + c] = make_float2(er, ei);
-                }
-            }
-        }
-    } else {   // A producers
-        const int pw = warp - 6;
+    } else {   // A producers (warps 2 and up), then the epilogue (warps 2..5)
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % kFuseStages;
             bool ok = true;
@@ -170,7 +150,13 @@ k_sweep_fused(const __grid_constant__ CUtensorMap tmY, int nkb, uint32_t idesc, 
             const float4 e = valid ? elem[m] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float2 c2 = valid ? cm[m] : make_float2(0.f, 0.f);
             uint8_t* stage = sA + s * kFStageA;
-            for (int rr = pw; rr < kTcBM; rr += kFuseProd) {
+            // every warp claims rows until one past the last: kTcBM + kFuseProd claims per use of a stage
+            const unsigned base = (unsigned)(kb / kFuseStages) * (kTcBM + kFuseProd);
+            while (true) {
+                unsigned claim = 0;
+                if (lane == 0) claim = atomicAdd(&row_ctr[s], 1u);
+                const int rr = (int)(__shfl_sync(0xffffffffu, claim, 0) - base);
+                if (rr >= kTcBM) break;
                 const int64_t row = m0 + rr;
                 cf a = cf{0.f, 0.f};
                 if (row < n_rx) {
@@ -194,6 +180,32 @@ k_sweep_fused(const __grid_constant__ CUtensorMap tmY, int nkb, uint32_t idesc, 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+        }
+        if (warp < 6) {   // then the epilogue, warps 2..5: TMEM lanes 32*(warp%4) .. +31
+            const bool ok = mbar_wait(smem_u32(tfull), 0, deadline + kFuseWait);
+            if (!ok) {
+                atomicExch(err, 1u);
+                *(volatile int*)&abort_flag = 1;
+            }
+            fence_after();
+            const int lane_base = 32 * (warp & 3);
+            const int64_t row = m0 + lane_base + lane;
+            const bool live = ok && !*(volatile int*)&abort_flag && row < n_rx;
+            const float2 e0 = live ? E0[row] : make_float2(0.f, 0.f);
+            for (int j = 0; j < kTcBN / 16; ++j) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(j * 16), v);
+                if (!live) continue;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int c = j * 8 + q;
+                    if (c < C) {
+                        const float er = v[2 * q] + e0.x, ei = v[2 * q + 1] + e0.y;
+                        if (P) P[row * C + c] = (er * er + ei * ei) * pscale;
+                        if (Eout) Eout[row * C + c] = make_float2(er, ei);
+                    }
+                }
+            }
         }
     }
     fence_before();
