@@ -66,7 +66,7 @@ PRECISIONS = {0: "fp32_simt", 1: "bf16", 2: "bf16x2", 3: "fp16"}
 # with: a changed source reports null traffic until the capture is repeated.
 DOMINANT = "k_validate"      # the kernel whose launches the timed region brackets with events
 MEASURED_TRAFFIC = {
-    "k_validate": {"bytes_per_step": 196.25e6, "sha256_16": "49a3a3636c401269",
+    "k_validate": {"bytes_per_step": 193.06e6, "sha256_16": "e830eec905a149b9",
                    "sources": [("trace.cu", "k_validate("), ("geom.cuh", None), ("scene.cu", None)],
                    "profile": "profiles/k_validate_room_256x256_dram.md"},
 }
