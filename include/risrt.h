@@ -422,6 +422,12 @@ int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precis
  * are then reused (only the phase-dependent operands are rebuilt). Results are undefined if they
  * changed. Ignored for RISRT_PREC_FP32. */
 #define RISRT_GRAD_KEEP_A 0x100
+/* OR-ed into the precision of risrt_grad_phases: the call only enqueues work on the stream and does not
+ * synchronise, so successive steps overlap and a step can be captured into a CUDA graph; with
+ * RISRT_GRAD_KEEP_A the target rows are not validated again (they are those of the earlier call). The
+ * tensor-core GEMMs' wait-timeout flag is left in the workspace for risrt_grad_check (cleared by every
+ * call); J_out and grad_out are ready in stream order. */
+#define RISRT_GRAD_DEFER_CHECK 0x200
 
 /* For B phase configurations Gamma_bm = amp_m e^{j phases[b][m]} on the channel matrix `amat`:
  *   J[b]       = sum_{t} log P_b(target[t]),  P = |E0 + A Gamma_b|^2 / (2 eta0)
@@ -436,12 +442,17 @@ int risrt_grad_workspace_size(int32_t n_target, int32_t B, int32_t M, int precis
  * in which every factor is split into a high and a low BF16 part (three products per pair, about
  * 1e-5 relative), FP32 accumulation, partial sums again added in a fixed order; A's target rows are
  * packed into the two operands on every call. The workspace must be 256-byte aligned. Synchronises
- * the stream (the target rows are validated on the device). Errors: RISRT_ERR_INVALID_ARG (sizes,
+ * the stream (the target rows are validated on the device) unless RISRT_GRAD_DEFER_CHECK. Errors: RISRT_ERR_INVALID_ARG (sizes,
  * precision, a target row outside [0, n_rx)); RISRT_ERR_NOT_READY (the paired tensor-core kernel
  * cannot run on this device); RISRT_ERR_TIMEOUT (a pipeline wait in the tensor-core kernel expired). */
 int risrt_grad_phases(risrt_ctx* ctx, const risrt_amat* amat, const int32_t* target, int32_t n_target,
                       const float* phases, const float* amp, int32_t B, float* J_out, float* grad_out,
                       void* workspace, size_t workspace_bytes, int precision);
+
+/* After calls with RISRT_GRAD_DEFER_CHECK on this workspace: waits for the context's stream and returns
+ * RISRT_ERR_TIMEOUT if a pipeline wait of the last such call's tensor-core GEMMs expired (its J and
+ * gradient are then incomplete), else RISRT_OK. */
+int risrt_grad_check(risrt_ctx* ctx, const void* workspace, size_t workspace_bytes);
 
 /* ------------------------------------------------------------------------------------------------
  * Allocation-free path search (this entry point has no counterpart in the paper; it exists for

@@ -17,8 +17,12 @@ class RISLogPower(torch.autograd.Function):
         grad = torch.empty((B, M), dtype=torch.float32, device=phases.device)
         ws = objective.workspace(B)
         keep = objective.precision == 2 and objective._packed.get(B, False)   # A was packed by an earlier call
+        # steps that reuse the packed A only enqueue (no synchronisation) when the library runs on torch's
+        # current stream, which orders J and the gradient before torch reads them; check() reads the
+        # tensor cores' timeout flag afterwards
+        defer = keep and objective.lib.stream == torch.cuda.current_stream(phases.device).cuda_stream
         objective.lib.grad_phases(objective.A, objective.E0, objective.target, phases, objective.amp, J, grad,
-                                  ws, objective.precision, keep_a=keep)
+                                  ws, objective.precision, keep_a=keep, defer_check=defer)
         objective._packed[B] = True
         ctx.save_for_backward(grad)
         return J
@@ -49,6 +53,12 @@ class PhaseObjective:
     def __call__(self, phases):
         return RISLogPower.apply(phases, self)
 
+    def check(self):
+        """Raises RisrtError if a deferred tensor-core step of this objective timed out (waits for the stream)."""
+        if self.precision == 2:
+            for ws in self._ws.values():
+                self.lib.grad_check(ws)
+
 
 def ascend(objective: PhaseObjective, phases0, steps: int = 200, lr: float = 0.05):
     """Adam ascent on every configuration's phases at once; returns (phases, J per step [steps+1, B])."""
@@ -63,4 +73,5 @@ def ascend(objective: PhaseObjective, phases0, steps: int = 200, lr: float = 0.0
         opt.step()
     with torch.no_grad():
         hist.append(objective(phases).detach())
+    objective.check()
     return phases.detach(), torch.stack(hist)

@@ -929,7 +929,8 @@ int risrt_grad_phases(risrt_ctx* ctx, const risrt_amat* amat, const int32_t* tar
     const int32_t M = amat->M;
     if (n_rx < 1 || M < 1 || M > 65536 || n_target < 1 || B < 1) return fail(ctx, RISRT_ERR_INVALID_ARG, "sizes out of range");
     const bool keep_a = (precision & RISRT_GRAD_KEEP_A) != 0;
-    precision &= ~RISRT_GRAD_KEEP_A;
+    const bool defer = (precision & RISRT_GRAD_DEFER_CHECK) != 0;
+    precision &= ~(RISRT_GRAD_KEEP_A | RISRT_GRAD_DEFER_CHECK);
     if (precision != RISRT_PREC_FP32 && precision != RISRT_PREC_BF16X2)
         return fail(ctx, RISRT_ERR_INVALID_ARG, "precision must be RISRT_PREC_FP32 or RISRT_PREC_BF16X2");
     if (!target && n_target > n_rx) return fail(ctx, RISRT_ERR_INVALID_ARG, "n_target > n_rx without a target list");
@@ -941,10 +942,17 @@ int risrt_grad_phases(risrt_ctx* ctx, const risrt_amat* amat, const int32_t* tar
         if (rc) return rc;
     }
     int rc = grad_phases(ctx, (const float2*)A, (const float2*)E0, M, target, n_target, phases, amp, B, J_out, grad_out,
-                         workspace, workspace_bytes, precision, keep_a);
+                         workspace, workspace_bytes, precision, keep_a, defer);
     if (rc) return rc;
-    RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!defer) RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return RISRT_OK;
+}
+
+int risrt_grad_check(risrt_ctx* ctx, const void* workspace, size_t workspace_bytes)
+{
+    RISRT_CHECK_CTX(ctx);
+    if (!workspace || workspace_bytes < 64) return fail(ctx, RISRT_ERR_INVALID_ARG, "no workspace");
+    return grad_check(ctx, workspace, workspace_bytes);
 }
 
 int risrt_find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* scene, const float src[3], int32_t src_face,

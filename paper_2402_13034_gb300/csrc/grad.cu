@@ -524,10 +524,10 @@ int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void
 
 // Tensor-core adjoint: both GEMMs on SM pairs (split-K), the packing of A into its forward and
 // transposed operands done per call unless keep_a (A and the targets may change between calls). The
-// GEMMs' pipeline-timeout flag is read once, after the last kernel.
+// GEMMs' pipeline-timeout flag is read once, after the last kernel, or left for grad_check (defer).
 static int grad_phases_tc(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
                           const float* phases, const float* amp, int B, float* J, float* grad, void* ws, size_t ws_bytes,
-                          bool keep_a)
+                          bool keep_a, bool defer)
 {
     cudaStream_t s = ctx->stream;
     const GradTcLayout L = grad_tc_layout(n_t, B, M);
@@ -569,21 +569,29 @@ static int grad_phases_tc(risrt_ctx* ctx, const float2* A, const float2* E0, int
     RISRT_KERNEL(ctx, "k_gpack_yb", (k_gpack_yb<<<dim3(nblk(n_t, 256), gy_b), 256, 0, s>>>(W, n_t, B, L.Kb, Yb)));
     if ((rc = gemm_tc_complex(ctx, Xb, M, Yb, L.Np, L.Kb, nullptr, 2 * B, Gp, L.sb, &pb, err))) return rc;
     RISRT_KERNEL(ctx, "k_adj_grad", (k_adj_grad_tc<<<nblk((int64_t)B * M, 256), 256, 0, s>>>(Gp, pb, phases, amp, B, M, grad)));
+    if (defer) return RISRT_OK;
+    return grad_check(ctx, ws, ws_bytes);
+}
+
+int grad_check(risrt_ctx* ctx, const void* ws, size_t ws_bytes)
+{
+    const unsigned* err = (const unsigned*)((const char*)ws + ws_bytes - 32);   // as in grad_phases_tc
     unsigned h = 0;
-    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    RISRT_CUDA(ctx, cudaStreamSynchronize(s));
+    RISRT_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    RISRT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (h) return fail(ctx, RISRT_ERR_TIMEOUT, "tensor-core GEMM: a pipeline wait expired");
     return RISRT_OK;
 }
 
 int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
                 const float* phases, const float* amp, int B, float* J, float* grad, void* ws, size_t ws_bytes,
-                int precision, bool keep_a)
+                int precision, bool keep_a, bool defer)
 {
     if (precision == RISRT_PREC_BF16X2)
-        return grad_phases_tc(ctx, A, E0, M, target, n_t, phases, amp, B, J, grad, ws, ws_bytes, keep_a);
+        return grad_phases_tc(ctx, A, E0, M, target, n_t, phases, amp, B, J, grad, ws, ws_bytes, keep_a, defer);
     cudaStream_t s = ctx->stream;
     const GradSplits g = grad_splits(n_t, B, M);
+    RISRT_CUDA(ctx, cudaMemsetAsync((char*)ws + ws_bytes - 32, 0, sizeof(unsigned), s));   // no timeout flag here
     float2* E = (float2*)ws;                               // [fwd][B][n_t] partials, then w in split 0
     float2* Gp = E + (size_t)g.fwd * n_t * B;              // [bwd][B][M]
     RISRT_KERNEL(ctx, "k_adj_forward", (k_adj_forward<<<dim3(nblk(n_t, kFR), nblk(B, kFB), g.fwd), 256, 0, s>>>(

@@ -445,7 +445,9 @@ size_t grad_workspace_bytes(int n_t, int B, int M, int precision);
 int check_targets(risrt_ctx* ctx, const int* target, int n_t, int64_t n_rx, void* ws, size_t ws_bytes);
 int grad_phases(risrt_ctx* ctx, const float2* A, const float2* E0, int M, const int* target, int n_t,
                 const float* phases, const float* amp, int B, float* J, float* grad, void* ws, size_t ws_bytes,
-                int precision, bool keep_a);
+                int precision, bool keep_a, bool defer = false);
+// The deferred tensor-core timeout flag of the last grad_phases on this workspace (waits for the stream).
+int grad_check(risrt_ctx* ctx, const void* ws, size_t ws_bytes);
 int find_paths_noalloc(risrt_ctx* ctx, const risrt_scene* sc, const float src[3], int src_face, const float dst[3],
                        int dst_face, int max_order, int64_t* ids_host, int cap_host, int* n_host);
 

@@ -21,6 +21,7 @@ PATTERN_ISO, PATTERN_COS_POW, PATTERN_MONOPOLE_QW = 0, 1, 2
 FLAG_ENV_PATHS, FLAG_FRESNEL_TM = 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP16 = 0, 1, 2, 3
 GRAD_KEEP_A = 0x100
+GRAD_DEFER_CHECK = 0x200
 SWEEP_KEEP_A = 0x100
 SWEEP_DEFER_CHECK = 0x200
 MB_FFMA, MB_MUFU_SIN, MB_MUFU_COS, MB_MUFU_RSQ, MB_MUFU_RCP, MB_MUFU_SQRT, MB_MUFU_EX2, MB_DFMA = range(8)
@@ -67,6 +68,7 @@ _SIGS = {
     "risrt_sweep_check": (C.c_int, [_P, _P, C.c_size_t]),
     "risrt_grad_workspace_size": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int, C.POINTER(C.c_size_t)]),
     "risrt_grad_phases": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P, C.c_size_t, C.c_int]),
+    "risrt_grad_check": (C.c_int, [_P, _P, C.c_size_t]),
     "risrt_find_paths_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.c_int32,
                                            C.POINTER(C.c_int32)]),
     "risrt_profile_enable": (C.c_int, [_P, C.c_int]),
@@ -257,6 +259,7 @@ class Context:
         if rc:
             raise RisrtError(rc, lib.risrt_last_error(None).decode())
         self.device = device
+        self.stream = stream
 
     def _check(self, rc: int):
         if rc:
@@ -275,6 +278,7 @@ class Context:
 
     def set_stream(self, stream_handle: int | None):
         self._check(load().risrt_set_stream(self._ptr, None if stream_handle is None else C.c_void_p(stream_handle)))
+        self.stream = stream_handle
 
     # --- tracing -------------------------------------------------------------------------------
     def profile_enable(self, on: bool = True):
@@ -501,11 +505,12 @@ class Context:
         return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
 
     def grad_phases(self, A, E0, target, phases, amp, J_out, grad_out, workspace=None, precision: int = PREC_FP32,
-                    keep_a: bool = False):
+                    keep_a: bool = False, defer_check: bool = False):
         """A: complex64 CUDA [n_rx, M] (with E0) or an AMat; target: int32 CUDA [n_t] or None (first n_t rows given by
         phases' companion J); phases: float32 [B, M]; amp: float32 [M] or None; J_out [B]; grad_out [B, M];
         precision PREC_FP32 (CUDA cores) or PREC_BF16X2 (tensor cores, split BF16); keep_a: A, E0 and target
-        are those of the previous call with this workspace (its packed A is reused)."""
+        are those of the previous call with this workspace (its packed A is reused); defer_check: enqueue only (no
+        synchronisation), check later with grad_check."""
         h = self._as_amat(A, E0)
         n_rx, M = h.n_rx, h.M
         B = phases.shape[0]
@@ -515,7 +520,12 @@ class Context:
                                              _dev_ptr(phases, "torch.float32"), _dev_ptr(amp, "torch.float32"), int(B),
                                              _dev_ptr(J_out, "torch.float32"), _dev_ptr(grad_out, "torch.float32"),
                                              C.c_void_p(ws.data_ptr()), ws.numel(),
-                                             int(precision) | (GRAD_KEEP_A if keep_a else 0)))
+                                             int(precision) | (GRAD_KEEP_A if keep_a else 0)
+                                             | (GRAD_DEFER_CHECK if defer_check else 0)))
+
+    def grad_check(self, workspace):
+        """Timeout flag of the last deferred grad_phases on this workspace (waits for the stream)."""
+        self._check(load().risrt_grad_check(self._ptr, C.c_void_p(workspace.data_ptr()), workspace.numel()))
 
     def find_paths_noalloc(self, scene: Scene, src, src_face: int, dst, dst_face: int, max_order: int,
                            cap: int = 4096) -> np.ndarray:

@@ -123,6 +123,12 @@ def test_grad_tensor_core_many_tiles(n_rx, n_t, M, Bn):
             assert np.all(np.abs(Jg - J_ref) <= 1e-4 * np.abs(J_ref) + 1e-3), (prec, keep, np.abs(Jg - J_ref).max())
             rel = np.linalg.norm(gg - g_ref, axis=1) / np.linalg.norm(g_ref, axis=1)
             assert rel.max() <= GRAD_TOL[prec], (prec, keep, rel.max())
+        # the same step enqueued only (no synchronisation, timeout flag checked afterwards): same results
+        J2, g2 = torch.empty_like(J), torch.empty_like(g)
+        ctx.grad_phases(Ad, E0d, td, torch.from_numpy(ph2).cuda(), torch.from_numpy(amp).cuda(), J2, g2, ws, prec,
+                        keep_a=True, defer_check=True)
+        ctx.grad_check(ws)
+        assert torch.equal(J, J2) and torch.equal(g, g2)
 
 
 @pytest.mark.gpu
