@@ -16,6 +16,7 @@ import json
 import os
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -422,6 +423,92 @@ def bench_serving_load(dev_index, rates=(5.0, 10.0, 20.0, 30.0), n_req=24, slots
     return table
 
 
+def bench_serving_sustained(dev_index, rate_hz: float, seconds: float, slots=4):
+    """A sustained run of the serving mix: requests arriving as a seeded Poisson stream at rate_hz for
+    `seconds`, generated as they are submitted; per request only its latency and queueing time are
+    kept (outputs are dropped on completion); GPU utilisation sampled by nvidia-smi during the run."""
+    from paper_2402_13034_gb300 import serve
+    scenes = {}
+    for w, name in ((S.room(grid=8), "room_492tri"), (S.office(), "office_20ktri"), (S.hall(target_grid=8), "hall_200ktri")):
+        w.name = name
+        scenes[name] = w
+    srv = serve.Server(device=dev_index, slots=slots)
+    for name, w in scenes.items():
+        srv.add_scene(name, w.scene)
+    lock = threading.Lock()
+    lat, que = [], []
+    state = {"pending": 0, "failed": 0}
+    failures = {}                                  # exception type -> [count, first message]
+    all_done = threading.Event()
+
+    def on_done(f):
+        with lock:
+            e = f.exception()
+            if e is None:
+                r = f.result()
+                lat.append(r.latency_s)
+                que.append(r.queue_s)
+            else:
+                state["failed"] += 1
+                rec = failures.setdefault(type(e).__name__, [0, str(e)[:160]])
+                rec[0] += 1
+            state["pending"] -= 1
+            if state["pending"] == 0 and state.get("submitted_all"):
+                all_done.set()
+
+    util_path = os.path.join(os.environ.get("RISRT_CLOCKS_DIR", "/tmp"), ".util.csv")
+    sampler = None
+    n_sub = 0
+    try:
+        warm = [serve.Request("coverage", name, w.ris, w.tx, w.rx, w.rx_xyz[:64], w.gammas[:1], w.freq_hz, 1, 1, True)
+                for name, w in scenes.items() for _ in range(slots)]
+        srv.drain([srv.submit(r) for r in warm])
+        try:
+            sampler = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), "--query-gpu=utilization.gpu",
+                                        "--format=csv,noheader,nounits", "-lms", "500"],
+                                       stdout=open(util_path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            sampler = None
+        t0 = time.perf_counter()
+        for t_arr, r in serve.iter_mixed_requests(S.SEED_BASE + 60, rate_hz, scenes):
+            if t_arr > seconds:
+                break
+            dt = t0 + t_arr - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            with lock:
+                state["pending"] += 1
+            srv.submit(r).add_done_callback(on_done)
+            n_sub += 1
+        with lock:
+            state["submitted_all"] = True
+            if state["pending"] == 0:
+                all_done.set()
+        all_done.wait(timeout=1800)
+        wall = time.perf_counter() - t0
+    finally:
+        if sampler:
+            sampler.terminate()
+        srv.close()
+    util = []
+    try:
+        util = [float(x) for x in open(util_path).read().split() if x.strip()]
+    except Exception:
+        pass
+    l_ms, q_ms = np.array(lat) * 1e3, np.array(que) * 1e3
+    return {"offered_req_s": rate_hz, "seconds_of_arrivals": seconds, "requests": n_sub, "served": len(lat),
+            "rejected_or_failed": state["failed"],
+            "failures": {k: {"count": v[0], "first": v[1]} for k, v in failures.items()},
+            "served_req_s": len(lat) / wall, "wall_s": wall,
+            "p50_ms": float(np.percentile(l_ms, 50)) if len(l_ms) else None,
+            "p99_ms": float(np.percentile(l_ms, 99)) if len(l_ms) else None,
+            "service_p50_ms": float(np.percentile(l_ms - q_ms, 50)) if len(l_ms) else None,
+            "service_p99_ms": float(np.percentile(l_ms - q_ms, 99)) if len(l_ms) else None,
+            "gpu_util_mean_pct": float(np.mean(util)) if util else None, "gpu_util_samples": len(util),
+            "channel_hits": srv.channel_hits, "graph_replays": srv.graph_replays,
+            "phase_s": {k: round(v, 3) for k, v in srv.phase_s.items()}}
+
+
 def bench_serving(dev_index, n_req=64, rate_hz=2000.0, slots=4):
     """Seeded Poisson stream (mean rate_hz) of the serving mix: scenes of 492 (room), ~20k (office)
     and ~200k (hall) triangles, RIS of 37 / 127 / 1,024 / 4,096 elements, receiver grids of 1k-1M
@@ -735,6 +822,12 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="also run the serving mix for this many seconds of arrivals at --serve-rate")
+    ap.add_argument("--serve-slots", type=str, default="4",
+                    help="stream slots of the sustained run, comma-separated for one run per count and rate")
+    ap.add_argument("--serve-rate", type=str, default="40",
+                    help="offered rate(s) in requests/s of the sustained run, comma-separated for one run each")
     ap.add_argument("--case", choices=["trace", "vector", "grad", "sweep"], default=None,
                     help="run a small fixed case for a profiler instead of the benchmark")
     ap.add_argument("--precision", type=int, default=1)
@@ -975,6 +1068,10 @@ def main():
     if rank == 0 and not args.no_serve:
         serving = bench_serving(local)
         serving["latency_vs_load"] = bench_serving_load(local)
+        if args.serve_seconds > 0:
+            serving["sustained"] = [dict(bench_serving_sustained(local, float(r), args.serve_seconds, int(k)),
+                                         slots=int(k))
+                                    for k in args.serve_slots.split(",") for r in args.serve_rate.split(",")]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

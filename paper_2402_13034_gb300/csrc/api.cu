@@ -65,6 +65,7 @@ cudaError_t ctx_malloc(risrt_ctx* ctx, void** p, size_t bytes)
         cudaGetLastError();
         e = cudaMalloc(p, bytes);
         if (e != cudaSuccess) {
+            cudaGetLastError();                  // returned to the caller, not left for a launch check
             *p = nullptr;
             return e;
         }
@@ -146,6 +147,9 @@ static void prof_collect(risrt_ctx* ctx)
 
 int cuda_fail(risrt_ctx* ctx, cudaError_t e, const char* where)
 {
+    // the failure is returned here; clearing the thread's last-error state keeps a later launch
+    // check from reporting it again (an error that breaks the context persists regardless)
+    cudaGetLastError();
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     return fail(ctx, e == cudaErrorMemoryAllocation ? RISRT_ERR_OOM : RISRT_ERR_CUDA, m);
 }
@@ -158,6 +162,10 @@ namespace {
 
 int set_device(risrt_ctx* ctx)
 {
+    // A non-sticky error that an earlier failed runtime call on this thread left behind (an
+    // allocation another library retried, say) was returned to that call; discard it so the launch
+    // checks of this call report only their own failures. A sticky error persists and shows again.
+    cudaGetLastError();
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     return RISRT_OK;

@@ -15,6 +15,7 @@ The admission policy (AdmissionController) is plain host logic and is tested wit
 """
 from __future__ import annotations
 
+import itertools
 import math
 import queue
 import threading
@@ -158,7 +159,9 @@ class Server:
         if budget_bytes is None:
             import torch
             free, _ = torch.cuda.mem_get_info(device)
-            budget_bytes = int(free * 0.8)
+            # blocks torch's caching allocator holds but no tensor uses are available to requests too
+            idle = torch.cuda.memory_reserved(device) - torch.cuda.memory_allocated(device)
+            budget_bytes = int((free + idle) * 0.8)
         self.channel_budget = int(budget_bytes * cache_fraction)
         self.admission = AdmissionController(budget_bytes - self.channel_budget, slots)
         self._channels = {}          # channel_key -> _Channel (insertion order = least recently used first)
@@ -166,6 +169,11 @@ class Server:
         self.channel_bytes = 0
         self.channel_hits = 0
         self.graph_replays = 0
+        # host wall time of the request phases summed over requests (slot threads overlap): inputs
+        # uploaded, trace (synchronous), field or channel + sweep until the stream is idle, read-back
+        self.phase_s = {"upload": 0.0, "trace": 0.0, "compute": 0.0, "readback": 0.0}
+        self.oom_retries = 0
+        self._phase_lock = threading.Lock()
         self._pending: "queue.Queue[tuple]" = queue.Queue()
         self._next_id = 0
         self._id_lock = threading.Lock()
@@ -237,7 +245,8 @@ class Server:
             except queue.Empty:
                 pass
             i = 0
-            while i < len(waiting):                    # FIFO, skipping requests that do not fit yet
+            while i < len(waiting):                    # FIFO: the oldest request that does not fit yet
+                                                       # holds back the later ones (no starvation)
                 req, fut, fp = waiting[i]
                 if fut.cancelled():
                     waiting.pop(i)
@@ -256,10 +265,18 @@ class Server:
         try:
             if not fut.set_running_or_notify_cancel():
                 return
-            if self._executor is not None:
-                P = self._executor(slot, req)
-            else:
-                P = self._gpu_execute(slot, req)
+            run = self._executor if self._executor is not None else self._gpu_execute
+            try:
+                P = run(slot, req)
+            except Exception as e:                # noqa: BLE001 - retried once, else reported
+                if not _is_oom(e):
+                    raise
+                # device memory is shared by torch's caching allocator and the library's own
+                # blocks; what one side caches the other cannot get, so release torch's idle blocks
+                # and run the request once more
+                self._release_idle_memory()
+                self.oom_retries += 1
+                P = run(slot, req)
             t_end = time.perf_counter()
             fut.set_result(Result(req.rid, P, t_end - req.arrival, t_start - req.arrival, fp))
         except BaseException as e:                    # noqa: BLE001 - reported through the future
@@ -269,6 +286,14 @@ class Server:
             self.admission.release(fp)
             self._slot_free.put(slot)
 
+    def _release_idle_memory(self):
+        if self._executor is not None:
+            return
+        import torch
+        with self._phase_lock:
+            torch.cuda.synchronize(self.device)
+            torch.cuda.empty_cache()
+
     def _context(self, slot: int):
         if self._contexts[slot] is None:
             import torch
@@ -277,11 +302,17 @@ class Server:
             self._contexts[slot] = (R.Context(self.device, stream.cuda_stream), stream)
         return self._contexts[slot]
 
+    def _phase_done(self, name: str, t0: float) -> float:
+        t = time.perf_counter()
+        with self._phase_lock:
+            self.phase_s[name] += t - t0
+        return t
+
     def _gpu_execute(self, slot: int, req: Request) -> np.ndarray:
         import torch
-        from . import risrt as R
         ctx, stream = self._context(slot)
         with torch.cuda.stream(stream):
+            t = time.perf_counter()
             n, C, M = len(req.rx_xyz), req.gammas.shape[0], req.gammas.shape[1]
             dev = f"cuda:{self.device}"
             G = torch.from_numpy(np.ascontiguousarray(req.gammas, np.complex64)).to(dev, non_blocking=False)
@@ -289,40 +320,60 @@ class Server:
                 ch = self._channel_acquire(req.channel_key, n, M, C, req.precision)
                 if ch is not None:
                     try:
-                        return self._sweep_resident(ctx, stream, ch, G)
+                        t = self._phase_done("upload", t)
+                        return self._sweep_resident(ctx, stream, ch, G, t)
                     finally:
                         ch.lock.release()
             scene = self._scene_handle(slot, ctx, req.scene_id)
-            ris = ctx.ris_upload(req.ris.elem_uv, req.ris.center, req.ris.t1, req.ris.t2, req.ris.dy, req.ris.dz,
-                                 req.ris.elem_gain, req.ris.host_face)
-            ctx.antenna_set(R.TX, req.tx.pos, req.tx.orient, req.tx.power_w, req.tx.gain_lin, req.tx.pattern)
-            ctx.antenna_set(R.RX, None, req.rx.orient, req.rx.power_w, req.rx.gain_lin, req.rx.pattern)
-            rx = ctx.rx_upload(req.rx_xyz)
-            flags = R.FLAG_ENV_PATHS if req.env_paths else 0
-            ps = ctx.trace_paths(scene, ris, rx, req.freq_hz, req.max_order_tx, req.max_order_rx, flags)
-            keep = None
-            if not uses_channel(req):
-                E = torch.empty((C, n), dtype=torch.complex64, device=dev)
-                P = torch.empty((C, n), dtype=torch.float32, device=dev)
-                ctx.eval_field(ps, G, E, P)
-                out = P.t().contiguous()
-            else:
-                A = torch.empty((n, M), dtype=torch.complex64, device=dev)
-                E0 = torch.empty(n, dtype=torch.complex64, device=dev)
-                ctx.build_A(ps, A, E0)
-                out = torch.empty((n, C), dtype=torch.float32, device=dev)
-                prec = req.precision if req.kind == "sweep" else R.PREC_BF16X2
-                ws = ctx.sweep_workspace(n, M, max(C, CHANNEL_CFG_CAP), prec)
-                ctx.sweep_configs(A, E0, G, out, prec, ws)
-                if req.kind == "sweep" and req.channel_key is not None and prec in (R.PREC_BF16, R.PREC_BF16X2):
-                    keep = (A, E0, ws, prec, max(C, CHANNEL_CFG_CAP))
-            host = out.cpu().numpy()
-            stream.synchronize()
-            for h in (ps, rx, ris):
-                h.close()
-            if keep is not None:
-                self._channel_store(req.channel_key, n, M, *keep)
-            return host
+            handles = []
+            try:
+                return self._trace_and_evaluate(ctx, stream, scene, req, G, handles, t)
+            finally:
+                for h in reversed(handles):
+                    h.close()
+
+    def _trace_and_evaluate(self, ctx, stream, scene, req, G, handles, t):
+        """Upload, trace and evaluate one request on its slot's stream; the handles it creates go to
+        `handles` so the caller closes them whatever happens."""
+        import torch
+        from . import risrt as R
+        n, C, M = len(req.rx_xyz), req.gammas.shape[0], req.gammas.shape[1]
+        dev = G.device
+        ris = ctx.ris_upload(req.ris.elem_uv, req.ris.center, req.ris.t1, req.ris.t2, req.ris.dy, req.ris.dz,
+                             req.ris.elem_gain, req.ris.host_face)
+        handles.append(ris)
+        ctx.antenna_set(R.TX, req.tx.pos, req.tx.orient, req.tx.power_w, req.tx.gain_lin, req.tx.pattern)
+        ctx.antenna_set(R.RX, None, req.rx.orient, req.rx.power_w, req.rx.gain_lin, req.rx.pattern)
+        rx = ctx.rx_upload(req.rx_xyz)
+        handles.append(rx)
+        t = self._phase_done("upload", t)
+        flags = R.FLAG_ENV_PATHS if req.env_paths else 0
+        ps = ctx.trace_paths(scene, ris, rx, req.freq_hz, req.max_order_tx, req.max_order_rx, flags)
+        handles.append(ps)
+        t = self._phase_done("trace", t)
+        keep = None
+        if not uses_channel(req):
+            E = torch.empty((C, n), dtype=torch.complex64, device=dev)
+            P = torch.empty((C, n), dtype=torch.float32, device=dev)
+            ctx.eval_field(ps, G, E, P)
+            out = P.t().contiguous()
+        else:
+            A = torch.empty((n, M), dtype=torch.complex64, device=dev)
+            E0 = torch.empty(n, dtype=torch.complex64, device=dev)
+            ctx.build_A(ps, A, E0)
+            out = torch.empty((n, C), dtype=torch.float32, device=dev)
+            prec = req.precision if req.kind == "sweep" else R.PREC_BF16X2
+            ws = ctx.sweep_workspace(n, M, max(C, CHANNEL_CFG_CAP), prec)
+            ctx.sweep_configs(A, E0, G, out, prec, ws)
+            if req.kind == "sweep" and req.channel_key is not None and prec in (R.PREC_BF16, R.PREC_BF16X2):
+                keep = (A, E0, ws, prec, max(C, CHANNEL_CFG_CAP))
+        stream.synchronize()
+        t = self._phase_done("compute", t)
+        host = _read_back(out, stream)
+        if keep is not None:
+            self._channel_store(req.channel_key, n, M, *keep)
+        self._phase_done("readback", t)
+        return host
 
     # -- resident channels --------------------------------------------------------------------------
     def _channel_acquire(self, key, n, M, C, precision):
@@ -340,7 +391,7 @@ class Server:
         self.channel_hits += 1
         return ch
 
-    def _sweep_resident(self, ctx, stream, ch, G):
+    def _sweep_resident(self, ctx, stream, ch, G, t):
         """Sweep on a resident channel: A stays packed in its workspace; a CUDA graph of the sweep is
         captured once per configuration count and replayed with the new configurations."""
         import torch
@@ -369,11 +420,16 @@ class Server:
             g.replay()
             ctx.sweep_check(ch.ws)
             self.graph_replays += 1
-            return P_static.cpu().numpy()
+            t = self._phase_done("compute", t)
+            host = _read_back(P_static, stream)
+            self._phase_done("readback", t)
+            return host
         out = torch.empty((n, C), dtype=torch.float32, device=G.device)
         ctx.sweep_configs(ch.A, ch.E0, G, out, ch.precision, ch.ws, keep_a=True)
-        host = out.cpu().numpy()
         stream.synchronize()
+        t = self._phase_done("compute", t)
+        host = _read_back(out, stream)
+        self._phase_done("readback", t)
         return host
 
     def _channel_store(self, key, n, M, A, E0, ws, precision, cfg_cap):
@@ -424,6 +480,24 @@ class Server:
                 c[0].close()
 
 
+def _read_back(out, stream) -> np.ndarray:
+    """The result copied into page-locked host memory from torch's caching host allocator: the copy
+    runs at the link's rate instead of through a staging buffer, and the block goes back to the
+    cache for a later result once the caller drops the array (the array keeps its tensor alive)."""
+    import torch
+    host = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+    host.copy_(out, non_blocking=True)
+    stream.synchronize()
+    return host.numpy()
+
+
+def _is_oom(e: BaseException) -> bool:
+    """A device allocation failure of the library (RISRT_ERR_OOM) or of torch."""
+    if getattr(e, "code", None) == 2 and type(e).__name__ == "RisrtError":
+        return True
+    return type(e).__name__ == "OutOfMemoryError"
+
+
 def latency_stats(results) -> dict:
     """Latency (arrival to result), queueing (arrival to start) and service (start to result), ms."""
     lat = np.array([r.latency_s for r in results]) * 1e3
@@ -465,13 +539,19 @@ def _ris_of_size(w, n_elem: int):
     return S.RIS(layouts[n_elem](), r.center, r.t1, r.t2, lam / 2, lam / 2, 0.0, r.host_face)
 
 
-def mixed_requests(seed: int, n: int, rate_hz: float, scenes: dict, rx_range=(1e3, 1e6), cfg_range=(1, 512),
-                   ris_sizes=(37, 127, 1024, 4096), n_channels: int = 4, reuse: float = 0.5):
-    """Seeded Poisson stream of the serving mix: per request a scene (name -> scenarios.Workload), a
-    RIS of one of ris_sizes elements on that scene's RIS wall, a receiver grid of log-uniform size in
-    rx_range over the scene's floor (margin 0.15 m) at 1.2 m, a log-uniform configuration count in
-    cfg_range, and coverage or sweep with equal odds; a fraction `reuse` of the sweeps query one of
-    n_channels fixed channels (same scene, RIS, Tx and receivers, new configurations)."""
+def mixed_requests(seed: int, n: int, rate_hz: float, scenes: dict, **kw):
+    """The first n requests of iter_mixed_requests (a list of (arrival time, Request))."""
+    return list(itertools.islice(iter_mixed_requests(seed, rate_hz, scenes, **kw), n))
+
+
+def iter_mixed_requests(seed: int, rate_hz: float, scenes: dict, rx_range=(1e3, 1e6), cfg_range=(1, 512),
+                        ris_sizes=(37, 127, 1024, 4096), n_channels: int = 4, reuse: float = 0.5):
+    """Seeded Poisson stream of the serving mix, generated as it is consumed: per request a scene
+    (name -> scenarios.Workload), a RIS of one of ris_sizes elements on that scene's RIS wall, a
+    receiver grid of log-uniform size in rx_range over the scene's floor (margin 0.15 m) at 1.2 m, a
+    log-uniform configuration count in cfg_range, and coverage or sweep with equal odds; a fraction
+    `reuse` of the sweeps query one of n_channels fixed channels (same scene, RIS, Tx and receivers,
+    new configurations)."""
     from . import scenarios as S
     rng = S.SplitMix64(seed)
     names = sorted(scenes)
@@ -490,8 +570,7 @@ def mixed_requests(seed: int, n: int, rate_hz: float, scenes: dict, rx_range=(1e
 
     channels = [setup() for _ in range(n_channels)]
     t = 0.0
-    out = []
-    for _ in range(n):
+    while True:
         t += -math.log(max(rng.uniform(), 1e-300)) / rate_hz
         kind = "sweep" if rng.uniform() < 0.5 else "coverage"
         key = None
@@ -503,6 +582,5 @@ def mixed_requests(seed: int, n: int, rate_hz: float, scenes: dict, rx_range=(1e
             w, ris, rx = setup()
         C = max(1, min(int(cfg_range[1]), int(log_uniform(cfg_range[0], cfg_range[1] + 1))))
         g = S.phase_configs(rng, C, ris.elem_uv.shape[0])
-        out.append((t, Request(kind, w.name, ris, w.tx, w.rx, rx, g, w.freq_hz, 1, 1, True, channel_key=key)))
-    return out
+        yield t, Request(kind, w.name, ris, w.tx, w.rx, rx, g, w.freq_hz, 1, 1, True, channel_key=key)
 

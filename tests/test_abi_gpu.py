@@ -47,6 +47,37 @@ def test_hbm_budget_bounds_context_memory():
     _traced(S.room(grid=256), ctx2)
 
 
+def test_device_allocation_failure_leaves_context_usable():
+    """A trace whose device allocation really fails (the GPU's memory held by torch's allocator)
+    returns RISRT_ERR_OOM; once the memory is back, the same context on the same thread traces
+    normally: the failed allocation's error is not reported again by a later launch check."""
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    ctx = _ctx()
+    w32 = S.room(grid=32)
+    handles, ps = _traced(w32, ctx)                 # kernels loaded, context warm
+    ref = ps.export()
+    for h in (ps, *handles):
+        h.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    hog = torch.empty(free - (256 << 20), dtype=torch.uint8, device="cuda")
+    try:
+        with pytest.raises(R.RisrtError) as e:
+            _traced(S.room(grid=256), ctx)          # two candidate slabs alone take 256 MiB
+        assert e.value.code == 2
+    finally:
+        del hog
+        torch.cuda.empty_cache()
+    handles, ps = _traced(w32, ctx)
+    got = ps.export()
+    for k in ("los", "vis", "tx_seqs", "tx_vis"):
+        assert np.array_equal(ref[k], got[k]), k
+    for k in ("seqs", "env"):
+        assert all(np.array_equal(a, b) for a, b in zip(ref[k], got[k], strict=True)), k
+
+
 def test_resident_channel_matrix_matches_caller_memory():
     """build_A without an output array keeps A and E0 in the library; its contents, and sweeps and
     gradients through the handle, are bitwise those of the caller-memory path."""

@@ -107,6 +107,45 @@ def test_executor_failure_is_isolated():
     srv.close()
 
 
+class RisrtError(RuntimeError):
+    """Stands in for the binding's error class (same name and code attribute)."""
+    def __init__(self, code):
+        super().__init__(f"risrt error {code}")
+        self.code = code
+
+
+def test_allocation_failure_retried_once():
+    """A request whose first run fails to allocate (library code 2) runs once more; a second
+    allocation failure, or any other error, reaches the caller; nothing else is retried."""
+    ws = _room_workloads()
+    reqs = _requests(ws, 4)
+    calls = {}
+
+    def executor(slot, req):
+        calls[req.rid] = calls.get(req.rid, 0) + 1
+        if req.rid == 0 and calls[0] == 1:
+            raise RisrtError(2)
+        if req.rid == 1:
+            raise RisrtError(2)
+        if req.rid == 2:
+            raise RisrtError(3)
+        return np.zeros((len(req.rx_xyz), req.gammas.shape[0]), np.float32)
+
+    srv = serve.Server(slots=1, budget_bytes=1 << 40, executor=executor)
+    for name, w in ws.items():
+        srv.add_scene(name, w.scene)
+    futs = [srv.submit(r) for r in reqs]
+    assert futs[0].result(timeout=10).P.shape[0] == len(reqs[0].rx_xyz)
+    for i in (1, 2):
+        with pytest.raises(RisrtError):
+            futs[i].result(timeout=10)
+    assert futs[3].result(timeout=10) is not None
+    srv.close()
+    assert calls == {0: 2, 1: 2, 2: 1, 3: 1}
+    assert srv.oom_retries == 2
+    assert srv.admission.running == 0
+
+
 @pytest.mark.gpu
 def test_results_identical_alone_and_in_mix():
     from paper_2402_13034_gb300 import build as B
