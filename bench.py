@@ -423,16 +423,18 @@ def bench_serving_load(dev_index, rates=(5.0, 10.0, 20.0, 30.0), n_req=24, slots
     return table
 
 
-def bench_serving_sustained(dev_index, rate_hz: float, seconds: float, slots=4):
+def bench_serving_sustained(dev_index, rate_hz: float, seconds: float, slots=4, max_wait_s=None):
     """A sustained run of the serving mix: requests arriving as a seeded Poisson stream at rate_hz for
-    `seconds`, generated as they are submitted; per request only its latency and queueing time are
-    kept (outputs are dropped on completion); GPU utilisation sampled by nvidia-smi during the run."""
+    `seconds`, generated as they are submitted (shared-input mode: grids and configuration pools
+    reused so that generation keeps up with thousands of requests per second); per request only its
+    latency and queueing time are kept (outputs are dropped on completion); GPU utilisation sampled
+    by nvidia-smi during the run. max_wait_s: requests not admitted within it are shed."""
     from paper_2402_13034_gb300 import serve
     scenes = {}
     for w, name in ((S.room(grid=8), "room_492tri"), (S.office(), "office_20ktri"), (S.hall(target_grid=8), "hall_200ktri")):
         w.name = name
         scenes[name] = w
-    srv = serve.Server(device=dev_index, slots=slots)
+    srv = serve.Server(device=dev_index, slots=slots, max_wait_s=max_wait_s)
     for name, w in scenes.items():
         srv.add_scene(name, w.scene)
     lock = threading.Lock()
@@ -470,12 +472,15 @@ def bench_serving_sustained(dev_index, rate_hz: float, seconds: float, slots=4):
         except Exception:
             sampler = None
         t0 = time.perf_counter()
-        for t_arr, r in serve.iter_mixed_requests(S.SEED_BASE + 60, rate_hz, scenes):
+        late_max = 0.0
+        for t_arr, r in serve.iter_mixed_requests(S.SEED_BASE + 60, rate_hz, scenes, shared_inputs=True):
             if t_arr > seconds:
                 break
             dt = t0 + t_arr - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
+            else:
+                late_max = max(late_max, -dt)
             with lock:
                 state["pending"] += 1
             srv.submit(r).add_done_callback(on_done)
@@ -484,6 +489,7 @@ def bench_serving_sustained(dev_index, rate_hz: float, seconds: float, slots=4):
             state["submitted_all"] = True
             if state["pending"] == 0:
                 all_done.set()
+        t_sub = time.perf_counter() - t0
         all_done.wait(timeout=1800)
         wall = time.perf_counter() - t0
     finally:
@@ -497,6 +503,8 @@ def bench_serving_sustained(dev_index, rate_hz: float, seconds: float, slots=4):
         pass
     l_ms, q_ms = np.array(lat) * 1e3, np.array(que) * 1e3
     return {"offered_req_s": rate_hz, "seconds_of_arrivals": seconds, "requests": n_sub, "served": len(lat),
+            "submitted_req_s": n_sub / t_sub, "submission_late_max_s": late_max, "max_wait_s": max_wait_s,
+            "shed_queue_full": srv.shed_full, "shed_not_admitted_in_time": srv.shed_late,
             "rejected_or_failed": state["failed"],
             "failures": {k: {"count": v[0], "first": v[1]} for k, v in failures.items()},
             "served_req_s": len(lat) / wall, "wall_s": wall,
@@ -826,6 +834,8 @@ def main():
                     help="also run the serving mix for this many seconds of arrivals at --serve-rate")
     ap.add_argument("--serve-slots", type=str, default="4",
                     help="stream slots of the sustained run, comma-separated for one run per count and rate")
+    ap.add_argument("--serve-max-wait", type=float, default=0.0,
+                    help="sustained run: shed requests not admitted within this many seconds (0: never)")
     ap.add_argument("--serve-rate", type=str, default="40",
                     help="offered rate(s) in requests/s of the sustained run, comma-separated for one run each")
     ap.add_argument("--case", choices=["trace", "vector", "grad", "sweep"], default=None,
@@ -1069,7 +1079,8 @@ def main():
         serving = bench_serving(local)
         serving["latency_vs_load"] = bench_serving_load(local)
         if args.serve_seconds > 0:
-            serving["sustained"] = [dict(bench_serving_sustained(local, float(r), args.serve_seconds, int(k)),
+            mw = args.serve_max_wait if args.serve_max_wait > 0 else None
+            serving["sustained"] = [dict(bench_serving_sustained(local, float(r), args.serve_seconds, int(k), mw),
                                          slots=int(k))
                                     for k in args.serve_slots.split(",") for r in args.serve_rate.split(",")]
 

@@ -15,6 +15,7 @@ The admission policy (AdmissionController) is plain host logic and is tested wit
 """
 from __future__ import annotations
 
+import collections
 import itertools
 import math
 import queue
@@ -50,6 +51,10 @@ class Request:
     arrival: float = 0.0
     rid: int = -1
     meta: dict = field(default_factory=dict)
+
+
+class Overloaded(RuntimeError):
+    """A request shed by the server's load limits (queue full, or not admitted in time)."""
 
 
 @dataclass
@@ -151,10 +156,19 @@ class _Channel:
 
 class Server:
     def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int | None = None, executor=None,
-                 cache_fraction: float = 0.25):
+                 cache_fraction: float = 0.25, max_queue: int | None = None, max_wait_s: float | None = None):
         """executor(slot_index, request) -> np.ndarray replaces the GPU path (used by host tests).
-        cache_fraction of the budget holds resident channels; the rest is for running requests."""
+        cache_fraction of the budget holds resident channels; the rest is for running requests.
+        Load shedding (off by default): with max_queue, a request submitted while that many wait for
+        admission fails at once with Overloaded; with max_wait_s, a request still waiting that long
+        after its arrival fails with Overloaded instead of being admitted later."""
         self.device = device
+        self.max_queue = max_queue
+        self.max_wait_s = max_wait_s
+        self.shed_full = 0           # rejected at submission, queue full
+        self.shed_late = 0           # rejected while waiting, past max_wait_s
+        self._n_waiting = 0
+        self._wait_lock = threading.Lock()
         self._executor = executor
         if budget_bytes is None:
             import torch
@@ -180,11 +194,14 @@ class Server:
         self._scenes = {}            # scene_id -> (host Scene, {slot: risrt scene handle})
         self._scene_lock = threading.Lock()
         self._slot_free = queue.Queue()
-        self._threads = []
+        self._slot_work = [queue.Queue() for _ in range(slots)]
         self._stop = threading.Event()
         self._contexts = [None] * slots
         for s in range(slots):
             self._slot_free.put(s)
+        self._threads = [threading.Thread(target=self._worker, args=(s,), daemon=True) for s in range(slots)]
+        for t in self._threads:
+            t.start()
         self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self._dispatcher.start()
 
@@ -219,8 +236,21 @@ class Server:
         if not self.admission.fits_ever(fp):
             fut.set_exception(MemoryError(f"request needs ~{fp} bytes, above the budget {self.admission.budget}"))
             return fut
+        with self._wait_lock:
+            full = self.max_queue is not None and self._n_waiting >= self.max_queue
+            if full:
+                self.shed_full += 1
+            else:
+                self._n_waiting += 1
+        if full:
+            fut.set_exception(Overloaded(f"{self.max_queue} requests already wait for admission"))
+            return fut
         self._pending.put((req, fut, fp))
         return fut
+
+    def _left_queue(self):
+        with self._wait_lock:
+            self._n_waiting -= 1
 
     def _validate(self, req: Request) -> str | None:
         if req.kind not in ("coverage", "sweep"):
@@ -237,28 +267,41 @@ class Server:
 
     # -- dispatch ---------------------------------------------------------------------------------
     def _dispatch(self):
-        waiting = []
+        waiting = collections.deque()                  # FIFO by arrival
         while not self._stop.is_set():
             try:
                 while True:
                     waiting.append(self._pending.get(timeout=0.0005 if waiting else 0.05))
             except queue.Empty:
                 pass
-            i = 0
-            while i < len(waiting):                    # FIFO: the oldest request that does not fit yet
-                                                       # holds back the later ones (no starvation)
-                req, fut, fp = waiting[i]
+            if self.max_wait_s is not None:            # the oldest are at the front
+                now = time.perf_counter()
+                while waiting and now - waiting[0][0].arrival > self.max_wait_s:
+                    req, fut, fp = waiting.popleft()
+                    self._left_queue()
+                    self.shed_late += 1
+                    if not fut.done():                 # done only if cancelled
+                        fut.set_exception(Overloaded(f"not admitted within {self.max_wait_s} s"))
+            # FIFO: the oldest request that does not fit yet holds back the later ones (no starvation)
+            while waiting:
+                req, fut, fp = waiting[0]
                 if fut.cancelled():
-                    waiting.pop(i)
+                    waiting.popleft()
+                    self._left_queue()
                     continue
-                if self.admission.try_admit(fp):
-                    waiting.pop(i)
-                    slot = self._slot_free.get()
-                    t = threading.Thread(target=self._run, args=(slot, req, fut, fp), daemon=True)
-                    t.start()
-                    self._threads.append(t)
-                else:
+                if not self.admission.try_admit(fp):
                     break
+                waiting.popleft()
+                self._left_queue()
+                self._slot_work[self._slot_free.get()].put((req, fut, fp))
+
+    def _worker(self, slot: int):
+        """The slot's thread: runs the requests the dispatcher hands to this slot, one at a time."""
+        while True:
+            item = self._slot_work[slot].get()
+            if item is None:
+                return
+            self._run(slot, *item)
 
     def _run(self, slot: int, req: Request, fut: Future, fp: int):
         t_start = time.perf_counter()
@@ -463,6 +506,8 @@ class Server:
     def close(self):
         self._stop.set()
         self._dispatcher.join(timeout=5)
+        for q in self._slot_work:
+            q.put(None)
         for t in self._threads:
             t.join(timeout=60)
         with self._scene_lock:
@@ -539,34 +584,71 @@ def _ris_of_size(w, n_elem: int):
     return S.RIS(layouts[n_elem](), r.center, r.t1, r.t2, lam / 2, lam / 2, 0.0, r.host_face)
 
 
+POOL_CFGS = 1024
+
+
 def mixed_requests(seed: int, n: int, rate_hz: float, scenes: dict, **kw):
     """The first n requests of iter_mixed_requests (a list of (arrival time, Request))."""
     return list(itertools.islice(iter_mixed_requests(seed, rate_hz, scenes, **kw), n))
 
 
 def iter_mixed_requests(seed: int, rate_hz: float, scenes: dict, rx_range=(1e3, 1e6), cfg_range=(1, 512),
-                        ris_sizes=(37, 127, 1024, 4096), n_channels: int = 4, reuse: float = 0.5):
+                        ris_sizes=(37, 127, 1024, 4096), n_channels: int = 4, reuse: float = 0.5,
+                        shared_inputs: bool = False):
     """Seeded Poisson stream of the serving mix, generated as it is consumed: per request a scene
     (name -> scenarios.Workload), a RIS of one of ris_sizes elements on that scene's RIS wall, a
     receiver grid of log-uniform size in rx_range over the scene's floor (margin 0.15 m) at 1.2 m, a
     log-uniform configuration count in cfg_range, and coverage or sweep with equal odds; a fraction
     `reuse` of the sweeps query one of n_channels fixed channels (same scene, RIS, Tx and receivers,
-    new configurations)."""
+    new configurations).
+
+    shared_inputs: generate at thousands of requests per second. Receiver counts are rounded to
+    1/16 of a decade and each (scene, count) grid is built once; each request's configurations are
+    C consecutive rows, from a random row, of one seeded pool of POOL_CFGS configurations per RIS
+    size (arrays shared between requests, never written). The sizes and the work per request keep
+    the mix's distributions."""
     from . import scenarios as S
     rng = S.SplitMix64(seed)
     names = sorted(scenes)
+    grids, rises, pools = {}, {}, {}
 
     def log_uniform(lo, hi):
         return math.exp(math.log(lo) + rng.uniform() * (math.log(hi) - math.log(lo)))
 
-    def setup():
-        w = scenes[names[int(rng.uniform() * len(names)) % len(names)]]
-        ris = _ris_of_size(w, ris_sizes[int(rng.uniform() * len(ris_sizes)) % len(ris_sizes)])
-        side = max(1, int(round(math.sqrt(log_uniform(*rx_range)))))
+    def grid(w, n):
+        if shared_inputs:
+            n = 10.0 ** (round(16 * math.log10(n)) / 16)
+        side = max(1, int(round(math.sqrt(n))))
+        key = (w.name, side)
+        if key in grids:
+            return grids[key]
         v = w.scene.verts
         x0, y0 = float(v[:, 0].min()) + 0.15, float(v[:, 1].min()) + 0.15
         x1, y1 = float(v[:, 0].max()) - 0.15, float(v[:, 1].max()) - 0.15
-        return w, ris, S.linspace_grid(x0, x1, side, y0, y1, side, 1.2, jitter=True)
+        g = S.linspace_grid(x0, x1, side, y0, y1, side, 1.2, jitter=True)
+        if shared_inputs:
+            grids[key] = g
+        return g
+
+    def ris_of(w, size):
+        key = (w.name, size)
+        if key not in rises:
+            rises[key] = _ris_of_size(w, size)
+        return rises[key]
+
+    def setup():
+        w = scenes[names[int(rng.uniform() * len(names)) % len(names)]]
+        ris = ris_of(w, ris_sizes[int(rng.uniform() * len(ris_sizes)) % len(ris_sizes)])
+        return w, ris, grid(w, log_uniform(*rx_range))
+
+    def configs(C, M):
+        if not shared_inputs:
+            return S.phase_configs(rng, C, M)
+        if M not in pools:
+            pools[M] = S.phase_configs(S.SplitMix64(seed * 1000003 + M), max(POOL_CFGS, int(cfg_range[1])), M)
+        p = pools[M]
+        r0 = int(rng.uniform() * (p.shape[0] - C + 1)) % (p.shape[0] - C + 1)
+        return p[r0:r0 + C]
 
     channels = [setup() for _ in range(n_channels)]
     t = 0.0
@@ -581,6 +663,6 @@ def iter_mixed_requests(seed: int, rate_hz: float, scenes: dict, rx_range=(1e3, 
         else:
             w, ris, rx = setup()
         C = max(1, min(int(cfg_range[1]), int(log_uniform(cfg_range[0], cfg_range[1] + 1))))
-        g = S.phase_configs(rng, C, ris.elem_uv.shape[0])
+        g = configs(C, ris.elem_uv.shape[0])
         yield t, Request(kind, w.name, ris, w.tx, w.rx, rx, g, w.freq_hz, 1, 1, True, channel_key=key)
 

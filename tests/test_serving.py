@@ -300,3 +300,87 @@ def test_served_results_match_oracle():
         assert dE[ok].max() <= 5e-5, (r.kind, w.name, dE[ok].max())
         checked += int(ok.sum())
     assert checked > 100
+
+
+def _blocking_executor():
+    """An executor whose requests run until `release` is set; `started` is set when one starts."""
+    started, release = threading.Event(), threading.Event()
+
+    def run(slot, req):
+        started.set()
+        assert release.wait(timeout=10)
+        return np.zeros((len(req.rx_xyz), req.gammas.shape[0]), np.float32)
+    return run, started, release
+
+
+def test_load_shedding_queue_bound():
+    """With max_queue = 2 and the only slot busy, two requests wait and later ones fail at once with
+    Overloaded; the waiting ones are served once the slot frees."""
+    ws = _room_workloads()
+    reqs = _requests(ws, 6)
+    run, started, release = _blocking_executor()
+    srv = serve.Server(slots=1, budget_bytes=1 << 40, executor=run, max_queue=2)
+    for name, w in ws.items():
+        srv.add_scene(name, w.scene)
+    first = srv.submit(reqs[0])
+    assert started.wait(timeout=10)
+    futs = [srv.submit(r) for r in reqs[1:]]
+    for f in futs[2:]:
+        with pytest.raises(serve.Overloaded):
+            f.result(timeout=1)
+    release.set()
+    for f in [first] + futs[:2]:
+        assert f.result(timeout=10) is not None
+    assert srv.shed_full == 3 and srv.shed_late == 0
+    srv.close()
+    assert srv.admission.running == 0
+
+
+def test_load_shedding_wait_limit():
+    """With max_wait_s, a request that cannot be admitted within the limit fails with Overloaded
+    and never runs; the running one completes."""
+    ws = _room_workloads()
+    reqs = _requests(ws, 3)
+    run, started, release = _blocking_executor()
+    ran = []
+
+    def executor(slot, req):
+        ran.append(req.rid)
+        return run(slot, req)
+
+    srv = serve.Server(slots=1, budget_bytes=1 << 40, executor=executor, max_wait_s=0.1)
+    for name, w in ws.items():
+        srv.add_scene(name, w.scene)
+    first = srv.submit(reqs[0])
+    assert started.wait(timeout=10)
+    late = [srv.submit(r) for r in reqs[1:]]
+    for f in late:
+        with pytest.raises(serve.Overloaded):
+            f.result(timeout=5)
+    release.set()
+    assert first.result(timeout=10) is not None
+    srv.close()
+    assert ran == [0] and srv.shed_late == 2 and srv.shed_full == 0
+
+
+def test_shared_input_mix_keeps_distributions():
+    """The shared-input mix draws sizes from the same distributions (receiver counts within 1/32 of
+    a decade of a log-uniform draw, C in range, configurations rows of one pool per RIS size) and
+    reuses grid arrays."""
+    ws = _room_workloads()
+    scenes = {}
+    for name, w in ws.items():
+        w.name = name
+        scenes[name] = w
+    reqs = serve.mixed_requests(5, 300, 2000.0, scenes, rx_range=(100, 4000), shared_inputs=True)
+    n = np.array([len(r.rx_xyz) for _, r in reqs])
+    assert n.min() >= 0.8 * 100 and n.max() <= 1.2 * 4000
+    logs = np.log10(n)
+    assert abs(np.median(logs) - 0.5 * (2 + np.log10(4000))) < 0.2
+    ids = {id(r.rx_xyz) for _, r in reqs}
+    assert len(ids) < len(reqs) // 2
+    for _, r in reqs:
+        assert 1 <= r.gammas.shape[0] <= 512 and r.gammas.flags.c_contiguous
+        assert np.allclose(np.abs(r.gammas), 1.0, atol=1e-6)
+    t = np.array([a for a, _ in reqs])
+    assert np.all(np.diff(t) > 0) and abs(len(t) / t[-1] - 2000.0) < 400
