@@ -160,6 +160,84 @@ using namespace risrt;
 
 namespace {
 
+uint32_t spread16(uint32_t x)          // bits 0..15 of x to the even bits 0..30
+{
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+struct TileLayout {
+    size_t bb = 0, pairs = 0, elem = 0, ofs = 0, bytes = 0;
+};
+
+// Spatial tiles of a RIS for the direct legs: the elements in the Morton order of their (a, b)
+// coordinates (quantised to 16 bits over the array's extent; ties by index), 32 consecutive ones per
+// tile; per tile the bounds of its element centres; per visibility word (elements 32 w .. 32 w + 31)
+// the tiles that hold its elements with the bits of those elements. One host buffer, laid out as
+// tile bounds, word pairs, tile elements, word offsets.
+TileLayout build_tiles(const float* uv, int M, std::vector<char>& buf, int& n_tiles)
+{
+    float amin = uv[0], amax = uv[0], bmin = uv[1], bmax = uv[1];
+    for (int m = 1; m < M; ++m) {
+        amin = std::min(amin, uv[2 * m]);
+        amax = std::max(amax, uv[2 * m]);
+        bmin = std::min(bmin, uv[2 * m + 1]);
+        bmax = std::max(bmax, uv[2 * m + 1]);
+    }
+    const double sa = amax > amin ? 65535.0 / ((double)amax - amin) : 0.0;
+    const double sb = bmax > bmin ? 65535.0 / ((double)bmax - bmin) : 0.0;
+    std::vector<std::pair<uint32_t, int>> key(M);
+    for (int m = 0; m < M; ++m) {
+        const uint32_t qa = (uint32_t)std::llround(((double)uv[2 * m] - amin) * sa);
+        const uint32_t qb = (uint32_t)std::llround(((double)uv[2 * m + 1] - bmin) * sb);
+        key[m] = {spread16(qa) | (spread16(qb) << 1), m};
+    }
+    std::sort(key.begin(), key.end());
+    const int T = (M + 31) / 32, W = (M + 31) / 32;
+    n_tiles = T;
+    std::vector<float4> bb(T, make_float4(3e38f, -3e38f, 3e38f, -3e38f));
+    std::vector<int> elem((size_t)T * 32, -1);
+    std::vector<std::vector<std::pair<int, unsigned>>> per_word(W);
+    for (int i = 0; i < M; ++i) {
+        const int t = i / 32, m = key[i].second;
+        elem[(size_t)i] = m;
+        float4& b = bb[t];
+        b = make_float4(std::min(b.x, uv[2 * m]), std::max(b.y, uv[2 * m]), std::min(b.z, uv[2 * m + 1]),
+                        std::max(b.w, uv[2 * m + 1]));
+        auto& pw = per_word[m >> 5];
+        if (pw.empty() || pw.back().first != t) pw.push_back({t, 0u});
+        pw.back().second |= 1u << (m & 31);
+    }
+    std::vector<int> ofs(W + 1, 0);
+    std::vector<int2> pairs;
+    for (int w = 0; w < W; ++w) {
+        std::sort(per_word[w].begin(), per_word[w].end());       // one pair per tile, tiles ascending
+        std::vector<std::pair<int, unsigned>> merged;
+        for (const auto& q : per_word[w]) {
+            if (!merged.empty() && merged.back().first == q.first) merged.back().second |= q.second;
+            else merged.push_back(q);
+        }
+        for (const auto& q : merged) pairs.push_back(make_int2(q.first, (int)q.second));
+        ofs[w + 1] = (int)pairs.size();
+    }
+    TileLayout L;
+    L.bb = 0;
+    L.pairs = L.bb + sizeof(float4) * (size_t)T;
+    L.elem = L.pairs + sizeof(int2) * pairs.size();
+    L.ofs = L.elem + sizeof(int) * elem.size();
+    L.bytes = L.ofs + sizeof(int) * ofs.size();
+    buf.assign(L.bytes, 0);
+    memcpy(buf.data() + L.bb, bb.data(), sizeof(float4) * bb.size());
+    memcpy(buf.data() + L.pairs, pairs.data(), sizeof(int2) * pairs.size());
+    memcpy(buf.data() + L.elem, elem.data(), sizeof(int) * elem.size());
+    memcpy(buf.data() + L.ofs, ofs.data(), sizeof(int) * ofs.size());
+    return L;
+}
+
 int set_device(risrt_ctx* ctx)
 {
     // A non-sticky error that an earlier failed runtime call on this thread left behind (an
@@ -398,9 +476,23 @@ int risrt_ris_upload(risrt_ctx* ctx, const float* elem_uv_host, int32_t M, const
         return cuda_fail(ctx, err, "cudaMalloc");
     }
     err = cudaMemcpyAsync(r->elem, e.data(), sizeof(float4) * M, cudaMemcpyHostToDevice, ctx->stream);
+    std::vector<char> tiles;
+    if (err == cudaSuccess && M > kTileMinElems) {
+        const TileLayout tl = build_tiles(elem_uv_host, M, tiles, r->n_tiles);
+        err = ctx_malloc(ctx, &r->tile_buf, tiles.size());
+        if (err == cudaSuccess) {
+            char* b = (char*)r->tile_buf;
+            r->tile_bb = (float4*)(b + tl.bb);
+            r->word_tile = (int2*)(b + tl.pairs);
+            r->tile_elem = (int*)(b + tl.elem);
+            r->word_ofs = (int*)(b + tl.ofs);
+            err = cudaMemcpyAsync(r->tile_buf, tiles.data(), tiles.size(), cudaMemcpyHostToDevice, ctx->stream);
+        }
+    }
     if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
     if (err != cudaSuccess) {
         ctx_free(ctx, r->elem);
+        ctx_free(ctx, r->tile_buf);
         delete r;
         return cuda_fail(ctx, err, "element upload");
     }
@@ -997,6 +1089,7 @@ int risrt_ris_destroy(risrt_ctx* ctx, risrt_ris* r)
     if (!r) return RISRT_OK;
     if (ctx) sync_ctx(ctx);
     ctx_free(ctx && ctx == r->owner ? ctx : nullptr, r->elem);
+    ctx_free(ctx && ctx == r->owner ? ctx : nullptr, r->tile_buf);
     delete r;
     return RISRT_OK;
 }

@@ -118,6 +118,7 @@ struct FaceGrid {
     float dv;
 };
 constexpr float kMapDelta = 1e-3f;   // a cell's map entry holds for points up to this far outside it
+constexpr int kTileMinElems = 64;    // RIS with more elements get spatial tiles for the direct legs
 
 struct DeviceScene {
     int64_t n_tris;
@@ -237,6 +238,14 @@ struct risrt_ris {
     int host_face = -1;
     float4* elem = nullptr;      // [M] (a_m, b_m, a^2 + b^2, 0)
     std::vector<float> uv_host;  // [M][2]
+    // Spatial tiles of up to 32 elements (consecutive in the Morton order of (a, b)) for the direct
+    // legs' visibility, built at upload for M > kTileMinElems; one device block holds all four arrays.
+    int n_tiles = 0;
+    void* tile_buf = nullptr;
+    float4* tile_bb = nullptr;   // [n_tiles] (a_min, a_max, b_min, b_max) of the tile's element centres
+    int2* word_tile = nullptr;   // [n_pairs] (tile, bits of a visibility word's elements in that tile)
+    int* tile_elem = nullptr;    // [n_tiles * 32] element indices, -1 past the tile's end
+    int* word_ofs = nullptr;     // [W + 1] word w's pairs are word_tile[word_ofs[w] .. word_ofs[w + 1])
     // a RIS the library makes for one element (strict mode) is centred exactly at the element
     bool exact_center = false;
     double center_d[3] = {0.0, 0.0, 0.0};

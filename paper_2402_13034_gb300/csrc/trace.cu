@@ -705,20 +705,27 @@ __device__ uint8_t classify_pyramid(const DeviceScene& S, bool in_box, float3 A,
     int sp = 0;
     int cur = occ_start(S, in_box, stack, sp);
     if (cur == kNoRoot) return 1;
-    // the pyramid's planes, outside = positive side: four through A, the fifth the base plane
-    float3 pn[5];
+    // the pyramid's planes, outside = positive side: four through A, the fifth the base plane, the
+    // sixth across the axis at A (or behind A by as much as a base corner lies behind it), which
+    // culls what lies behind the apex: boxes there straddle the side planes one by one
+    const float3 cdir = (C[0] + C[2]) * 0.5f - A;
+    const float3 ax = cdir * rsqrtf(fmaxf(dot(cdir, cdir), 1e-30f));
+    float3 pn[6];
+    float pmin = 0.f;
     for (int k = 0; k < 4; ++k) {
         float3 n = cross(C[k] - A, C[(k + 1) % 4] - A);
         n = n * rsqrtf(fmaxf(dot(n, n), 1e-30f));
         if (dot(n, C[(k + 2) % 4] - A) > 0.f) n = n * -1.f;
         pn[k] = n;
+        pmin = fminf(pmin, dot(ax, C[k] - A));
     }
     pn[4] = nb;
-    auto pq = [&](int k) { return k < 4 ? A : C[0]; };
+    pn[5] = ax * -1.f;
+    const float3 Acap = A + ax * pmin;
+    auto pq = [&](int k) { return k < 4 ? A : (k == 4 ? C[0] : Acap); };
     const int g0 = ig0 >= 0 ? ig0 : -3, g1 = ig1 >= 0 ? ig1 : -3;
     bool mixed = false, covered = false;
     int budget = 0, visits = 0;
-    const float3 cdir = (C[0] + C[2]) * 0.5f - A;
     const float3 cinv = f3(safe_inv(cdir.x), safe_inv(cdir.y), safe_inv(cdir.z));
     while (true) {
         if (cur < 0) {
@@ -728,7 +735,7 @@ __device__ uint8_t classify_pyramid(const DeviceScene& S, bool in_box, float3 A,
                 const TriVerts tv = S.tri_verts[L];
                 const float3 V[3] = {xyz(tv.v0), xyz(tv.v1), xyz(tv.v2)};
                 bool sep = false;
-                for (int k = 0; k < 5 && !sep; ++k) {
+                for (int k = 0; k < 6 && !sep; ++k) {
                     const float3 q = pq(k);
                     sep = dot(pn[k], V[0] - q) > margin && dot(pn[k], V[1] - q) > margin && dot(pn[k], V[2] - q) > margin;
                 }
@@ -772,7 +779,7 @@ __device__ uint8_t classify_pyramid(const DeviceScene& S, bool in_box, float3 A,
             ch[q] = __float_as_int(nd.lo[q].w);
             const int fq = __float_as_int(nd.hi[q].w);
             bool in = ch[q] != kNoChild && fq != g0 && fq != g1;
-            for (int k = 0; k < 5 && in; ++k) in = !box_outside(nd.lo[q], nd.hi[q], pn[k], pq(k), margin);
+            for (int k = 0; k < 6 && in; ++k) in = !box_outside(nd.lo[q], nd.hi[q], pn[k], pq(k), margin);
             // entered children in the order the centre ray meets them (boxes it misses last)
             t[q] = in ? fminf(box_entry(nd.lo[q], nd.hi[q], A, cinv), 1e30f) : 3e38f;
         }
@@ -843,30 +850,141 @@ __global__ void k_elem_bounds(const float4* __restrict__ elem, int M, float4* __
 
 // Per receiver: the pyramid from R through the RIS aperture (the element centres' bounding rectangle
 // in the RIS plane, enlarged by kMapDelta) contains every element -> R segment, so its class decides
-// all of them at once (1 all visible, 2 all blocked, 0 trace each element).
-__global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, Frame fr,
-                                                     const float4* __restrict__ eb, int host_face, float margin,
-                                                     uint8_t* __restrict__ state)
+// all of them at once (1 all visible, 2 all blocked, 0 trace each element). With und set, the
+// undecided receivers are appended to und (order unspecified; *und_n counts them).
+__device__ __forceinline__ uint8_t aperture_class(const DeviceScene& S, d3 R, const Frame& fr, float4 b,
+                                                  int host_face, float margin)
 {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n_rx) return;
-    const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
     const d3 c = fr_c(fr), n = fr_n(fr), t1 = fr_t1(fr), t2 = fr_t2(fr);
     const double sd = dot(n, R - c);
+    if (!(fabs(sd) > 1e-2)) return 0;
+    const double a0 = b.x - kMapDelta, a1 = b.y + kMapDelta, b0 = b.z - kMapDelta, b1 = b.w + kMapDelta;
+    const d3 Cd[4] = {c + t1 * a0 + t2 * b0, c + t1 * a1 + t2 * b0, c + t1 * a1 + t2 * b1, c + t1 * a0 + t2 * b1};
+    const float3 C[4] = {to_f(Cd[0]), to_f(Cd[1]), to_f(Cd[2]), to_f(Cd[3])};
+    const float3 nb = to_f(sd > 0.0 ? n * -1.0 : n);
+    // the elements lie in the rectangle: with its corners and R in the scene box, every element -> R
+    // segment does too
+    const bool in_box = in_scene_box(S, R) && in_scene_box(S, Cd[0]) && in_scene_box(S, Cd[1]) &&
+                        in_scene_box(S, Cd[2]) && in_scene_box(S, Cd[3]);
+    return classify_pyramid(S, in_box, to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
+}
+
+// Append the lanes whose `add` is set to list (one atomic per warp); every lane of the warp calls it.
+__device__ __forceinline__ void warp_append(bool add, uint32_t value, uint32_t* list, unsigned* count)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(FULL, add);
+    if (bal == 0u) return;
+    unsigned base = 0;
+    if (lane == __ffs(bal) - 1) base = atomicAdd(count, (unsigned)__popc(bal));
+    base = __shfl_sync(FULL, base, __ffs(bal) - 1);
+    if (add) list[base + __popc(bal & ((1u << lane) - 1u))] = value;
+}
+
+__global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, Frame fr,
+                                                     const float4* __restrict__ eb, int host_face, float margin,
+                                                     uint8_t* __restrict__ state, uint32_t* __restrict__ und,
+                                                     unsigned* __restrict__ und_n)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     uint8_t st = 0;
-    if (fabs(sd) > 1e-2) {
-        const float4 b = *eb;
-        const double a0 = b.x - kMapDelta, a1 = b.y + kMapDelta, b0 = b.z - kMapDelta, b1 = b.w + kMapDelta;
-        const d3 Cd[4] = {c + t1 * a0 + t2 * b0, c + t1 * a1 + t2 * b0, c + t1 * a1 + t2 * b1, c + t1 * a0 + t2 * b1};
-        const float3 C[4] = {to_f(Cd[0]), to_f(Cd[1]), to_f(Cd[2]), to_f(Cd[3])};
-        const float3 nb = to_f(sd > 0.0 ? n * -1.0 : n);
-        // the elements lie in the aperture rectangle: with its corners and R in the scene box, every
-        // element -> R segment does too
-        const bool in_box = in_scene_box(S, R) && in_scene_box(S, Cd[0]) && in_scene_box(S, Cd[1]) &&
-                            in_scene_box(S, Cd[2]) && in_scene_box(S, Cd[3]);
-        st = classify_pyramid(S, in_box, to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
+    if (r < n_rx) {
+        const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+        st = aperture_class(S, R, fr, *eb, host_face, margin);
+        state[r] = st;
     }
-    state[r] = st;
+    if (und) warp_append(r < n_rx && st == 0, (uint32_t)r, und, und_n);
+}
+
+// Visibility words of the receivers whose aperture pyramid is decided; the undecided receivers'
+// words come from k_vis_tiles and k_direct_tiles.
+__global__ void k_vis_decided(int64_t n_rx, int W, int M, const uint8_t* __restrict__ state, uint32_t* __restrict__ vis)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_rx * W) return;
+    const uint8_t st = state[i / W];
+    if (st == 0) return;
+    const int left = M - 32 * (int)(i % W);
+    vis[i] = st == 2 ? 0u : (left >= 32 ? 0xffffffffu : ((1u << left) - 1u));
+}
+
+// Per (undecided receiver u, tile t): the class of the pyramid from the receiver through the tile's
+// rectangle (its element centres' bounds, enlarged by kMapDelta) -> tstate[u * T + t]; undecided
+// tiles are appended to work as u * T + t. Grid-stride over the device count of undecided receivers.
+__global__ void __launch_bounds__(128) k_tile_aperture(DeviceScene S, const float* __restrict__ rx, Frame fr,
+                                                       const float4* __restrict__ tile_bb, int T, int host_face,
+                                                       float margin, const uint32_t* __restrict__ und,
+                                                       const unsigned* __restrict__ und_n, uint8_t* __restrict__ tstate,
+                                                       uint32_t* __restrict__ work, unsigned* __restrict__ work_n)
+{
+    const int64_t total = (int64_t)*und_n * T;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += stride) {   // uniform per block
+        const int64_t i = base + threadIdx.x;
+        uint8_t st = 0;
+        if (i < total) {
+            const int64_t r = und[i / T];
+            const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+            st = aperture_class(S, R, fr, tile_bb[i % T], host_face, margin);
+            tstate[i] = st;
+        }
+        warp_append(i < total && st == 0, (uint32_t)i, work, work_n);
+    }
+}
+
+// Visibility words of the undecided receivers from their tiles' classes: bits of the elements whose
+// tile is all visible (elements of undecided tiles are added by k_direct_tiles).
+__global__ void k_vis_tiles(int W, int T, const uint32_t* __restrict__ und, const unsigned* __restrict__ und_n,
+                            const int* __restrict__ word_ofs, const int2* __restrict__ word_tile,
+                            const uint8_t* __restrict__ tstate, uint32_t* __restrict__ vis)
+{
+    const int64_t total = (int64_t)*und_n * W;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int64_t u = i / W;
+        const int w = (int)(i % W);
+        uint32_t v = 0u;
+        for (int p = word_ofs[w]; p < word_ofs[w + 1]; ++p) {
+            const int2 q = word_tile[p];
+            if (tstate[u * T + q.x] == 1) v |= (uint32_t)q.y;
+        }
+        vis[(int64_t)und[u] * W + w] = v;
+    }
+}
+
+// Element -> receiver rays for the undecided tiles, one warp per work entry (lanes over the tile's
+// elements); the visible elements' bits are OR-ed into their words (one atomic per word touched).
+__global__ void __launch_bounds__(128) k_direct_tiles(DeviceScene S, const float* __restrict__ rx, const float4* __restrict__ elem,
+                                                      int W, int T, Frame fr, int host_face, float tol_base,
+                                                      const uint32_t* __restrict__ und, const int* __restrict__ tile_elem,
+                                                      const uint32_t* __restrict__ work, const unsigned* __restrict__ work_n,
+                                                      uint32_t* __restrict__ vis, unsigned long long* refines, int* err)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = *work_n;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {   // uniform per warp
+        const uint32_t i = work[k];
+        const int64_t r = und[i / T];
+        const int m = tile_elem[(int64_t)(i % T) * 32 + lane];
+        bool visible = false;
+        if (m >= 0) {
+            const d3 e = elem_pos(fr, elem[m]);
+            const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
+            visible = !seg_blocked(S, e, R, host_face, -1, tol_base, refines, err);
+        }
+        unsigned todo = __ballot_sync(FULL, visible);
+        while (todo) {
+            const int leader = __ffs(todo) - 1;
+            const int word = __shfl_sync(FULL, m >> 5, leader);
+            const bool mine = visible && (m >> 5) == word;
+            const unsigned bits = __reduce_or_sync(FULL, mine ? 1u << (m & 31) : 0u);
+            todo &= ~__ballot_sync(FULL, mine);
+            if (lane == leader) atomicOr(&vis[r * W + word], bits);
+        }
+    }
 }
 
 // Occlusion of every segment of every candidate (segments in propagation order, early exit on the
@@ -1858,6 +1976,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     ps->rx_pattern = ctx->rx.pattern;
     ps->rx_gain = ctx->rx.gain_lin;
     const int W = (M + 31) / 32;
+    // tiled direct legs ((receiver, tile) entries numbered in 32 bits); RISRT_TILES=0 forces one ray
+    // per element for every receiver whose aperture pyramid is undecided (both give the same bits)
+    const int T_tiles = ris->n_tiles;
+    const char* tiles_env = getenv("RISRT_TILES");
+    const bool tiled = T_tiles > 0 && (uint64_t)n_rx * (uint64_t)T_tiles < (1ull << 32) &&
+                       !(tiles_env && tiles_env[0] == '0');
     ps->W = W;
 
     // --- resident per-Rx arrays
@@ -1985,6 +2109,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             uint8_t* smap[2];        // visibility maps of the face cells from the Tx and from the RIS centre
             float4* elem_bb;         // element centre bounds in the RIS frame
             uint8_t* rx_state;       // per receiver: class of its RIS-aperture pyramid
+            uint32_t* und;           // tiled direct legs: receivers with an undecided aperture pyramid,
+            unsigned* tile_n;        // their count and the count of undecided (receiver, tile) entries,
+            uint8_t* tstate;         // the class of each (undecided receiver, tile) pyramid
+            uint32_t* twork;         // and the undecided (receiver, tile) entries
             LegBufs main, env, tx;   // work lists, settlement queues and scan space of the Rx leg, of the
                                      // environment paths and of the Tx leg (they run on separate streams)
         };
@@ -2025,6 +2153,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             for (int q = 0; q < 2; ++q) L.smap[q] = A.get<uint8_t>((size_t)std::max<int64_t>(sc->n_cells, 1));
             L.elem_bb = A.get<float4>(1);
             L.rx_state = A.get<uint8_t>((size_t)n_rx);
+            L.und = A.get<uint32_t>(tiled ? (size_t)n_rx : 1);
+            L.tile_n = A.get<unsigned>(2);
+            L.tstate = A.get<uint8_t>(tiled ? (size_t)n_rx * T_tiles : 1);
+            L.twork = A.get<uint32_t>(tiled ? (size_t)n_rx * T_tiles : 1);
             L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_seq, L.dense_off, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
                              L.scan_tmp, L.counters + 6};
             // the environment paths run beside the Rx leg: their own work list, queue and scan space
@@ -2122,13 +2254,32 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         if (sB != s) RISRT_CUDA(ctx, cudaEventRecord(ctx->ev[1], sB));
         // direct legs: element -> receiver visibility (aperture pyramids, then rays where undecided), LOS
         {
-            int64_t nthreads = n_rx * W * 32;
+            const float mg = 1e-4f * (1.f + ext);
             RISRT_KERNEL_ON(ctx, sB, "k_elem_bounds", (k_elem_bounds<<<1, 256, 0, sB>>>(ris->elem, M, L.elem_bb)));
-            RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.elem_bb,
-                                                                                            ris->host_face, 1e-4f * (1.f + ext),
-                                                                                            L.rx_state)));
-            RISRT_KERNEL_ON(ctx, sB, "k_direct_vis", (k_direct_vis<<<nblk(nthreads, 128), 128, 0, sB>>>(S, rxp, n_rx, ris->elem, M, W, fr, ris->host_face,
-                                                             tol_base, ps->vis, counters, flags_dev + 1, L.rx_state)));
+            if (tiled) {
+                // receivers, then spatial tiles of 32 elements, decided by pyramids; rays for the rest
+                const unsigned grid = (unsigned)ctx->sm_count * 8;
+                RISRT_CUDA(ctx, cudaMemsetAsync(L.tile_n, 0, sizeof(unsigned) * 2, sB));
+                RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.elem_bb,
+                                                                  ris->host_face, mg, L.rx_state, L.und, L.tile_n)));
+                RISRT_KERNEL_ON(ctx, sB, "k_vis_decided", (k_vis_decided<<<nblk(n_rx * W, 256), 256, 0, sB>>>(n_rx, W, M, L.rx_state,
+                                                                                                        ps->vis)));
+                RISRT_KERNEL_ON(ctx, sB, "k_tile_aperture", (k_tile_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, ris->tile_bb, T_tiles,
+                                                                  ris->host_face, mg, L.und, L.tile_n, L.tstate, L.twork,
+                                                                  L.tile_n + 1)));
+                RISRT_KERNEL_ON(ctx, sB, "k_vis_tiles", (k_vis_tiles<<<grid, 256, 0, sB>>>(W, T_tiles, L.und, L.tile_n, ris->word_ofs,
+                                                                  ris->word_tile, L.tstate, ps->vis)));
+                RISRT_KERNEL_ON(ctx, sB, "k_direct_tiles", (k_direct_tiles<<<grid, 128, 0, sB>>>(S, rxp, ris->elem, W, T_tiles, fr,
+                                                                  ris->host_face, tol_base, L.und, ris->tile_elem, L.twork,
+                                                                  L.tile_n + 1, ps->vis, counters, flags_dev + 1)));
+            } else {
+                const int64_t nthreads = n_rx * W * 32;
+                RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.elem_bb,
+                                                                  ris->host_face, mg, L.rx_state, nullptr, nullptr)));
+                RISRT_KERNEL_ON(ctx, sB, "k_direct_vis", (k_direct_vis<<<nblk(nthreads, 128), 128, 0, sB>>>(S, rxp, n_rx, ris->elem, M, W, fr,
+                                                                  ris->host_face, tol_base, ps->vis, counters, flags_dev + 1,
+                                                                  L.rx_state)));
+            }
             RISRT_KERNEL_ON(ctx, sB, "k_los", (k_los<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, tx, tol_base, ps->los, counters, flags_dev + 1)));
         }
 

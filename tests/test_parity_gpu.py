@@ -84,6 +84,24 @@ def test_room_pathsets_bit_exact(grid):
     assert n_ref.max() > 5
 
 
+@pytest.mark.parametrize("side", [32, 64])
+def test_tiled_direct_legs(side, monkeypatch):
+    """Square RIS of 1,024 and 4,096 elements in the room with its boxes, so that many receivers see
+    part of the aperture: element -> receiver visibility decided through pyramids over spatial tiles
+    of 32 elements (rays only for undecided tiles) equals one ray per element (RISRT_TILES=0) bit for
+    bit, and the path sets and fields match the oracle."""
+    w = S.room(grid=12, square_side=side)
+    g = run_gpu(w)
+    monkeypatch.setenv("RISRT_TILES", "0")
+    g0 = run_gpu(w)
+    monkeypatch.delenv("RISRT_TILES")
+    assert np.array_equal(g["paths"]["vis"], g0["paths"]["vis"])
+    assert np.array_equal(g["P"], g0["P"])
+    seen = np.array([sum(bin(int(x)).count("1") for x in row) for row in g["paths"]["vis"]])
+    assert np.any((seen > 0) & (seen < side * side))     # partly shadowed receivers exist
+    oracle_parity(w, g)
+
+
 def test_room_field_parity():
     w = S.room(grid=16)
     g = run_gpu(w, want_A=True)
