@@ -514,7 +514,8 @@ def bench_serving_sustained(dev_index, rate_hz: float, seconds: float, slots=4, 
             "service_p99_ms": float(np.percentile(l_ms - q_ms, 99)) if len(l_ms) else None,
             "gpu_util_mean_pct": float(np.mean(util)) if util else None, "gpu_util_samples": len(util),
             "channel_hits": srv.channel_hits, "graph_replays": srv.graph_replays,
-            "phase_s": {k: round(v, 3) for k, v in srv.phase_s.items()}}
+            "phase_s": {k: round(v, 3) for k, v in srv.phase_s.items()},
+            "oom_retries": srv.oom_retries, "idle_trims": srv.idle_trims}
 
 
 def bench_serving(dev_index, n_req=64, rate_hz=2000.0, slots=4):

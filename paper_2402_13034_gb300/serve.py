@@ -187,6 +187,8 @@ class Server:
         # uploaded, trace (synchronous), field or channel + sweep until the stream is idle, read-back
         self.phase_s = {"upload": 0.0, "trace": 0.0, "compute": 0.0, "readback": 0.0}
         self.oom_retries = 0
+        self.idle_trims = 0
+        self._device_lock = threading.Lock()     # graph captures; releases of cached device memory
         self._phase_lock = threading.Lock()
         self._pending: "queue.Queue[tuple]" = queue.Queue()
         self._next_id = 0
@@ -309,6 +311,7 @@ class Server:
             if not fut.set_running_or_notify_cancel():
                 return
             run = self._executor if self._executor is not None else self._gpu_execute
+            self._trim_idle_memory(fp)
             try:
                 P = run(slot, req)
             except Exception as e:                # noqa: BLE001 - retried once, else reported
@@ -330,12 +333,25 @@ class Server:
             self._slot_free.put(slot)
 
     def _release_idle_memory(self):
+        """Return torch's idle cached blocks to the driver. Held under the device lock, which graph
+        captures also hold: freeing memory waits on the device, and a wait on a stream that is
+        capturing would invalidate that capture."""
         if self._executor is not None:
             return
         import torch
-        with self._phase_lock:
-            torch.cuda.synchronize(self.device)
+        with self._device_lock:
             torch.cuda.empty_cache()
+
+    def _trim_idle_memory(self, fp: int):
+        """Before a request of at least a GiB: if torch's idle cached blocks exceed half of the
+        running-request budget, release them (the library allocates outside torch's cache)."""
+        if self._executor is not None or fp < (1 << 30):
+            return
+        import torch
+        idle = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        if idle > self.admission.budget // 2:
+            self._release_idle_memory()
+            self.idle_trims += 1
 
     def _context(self, slot: int):
         if self._contexts[slot] is None:
@@ -447,12 +463,13 @@ class Server:
                 # capture on this slot's stream without torch.cuda.graph's device-wide synchronize and
                 # allocator cache release, which would stall every other slot
                 g = torch.cuda.CUDAGraph()
-                g.capture_begin(capture_error_mode="thread_local")
-                try:
-                    ctx.sweep_configs(ch.A, ch.E0, G_static, P_static, ch.precision, ch.ws, keep_a=True,
-                                      defer_check=True)
-                finally:
-                    g.capture_end()
+                with self._device_lock:
+                    g.capture_begin(capture_error_mode="thread_local")
+                    try:
+                        ctx.sweep_configs(ch.A, ch.E0, G_static, P_static, ch.precision, ch.ws, keep_a=True,
+                                          defer_check=True)
+                    finally:
+                        g.capture_end()
                 gr = ch.graphs[C] = (g, G_static, P_static)
                 with self._chan_lock:
                     extra = G_static.numel() * 8 + P_static.numel() * 4
