@@ -260,6 +260,51 @@ def bench_plain_fp32(ctx, R, dev, w, ps, gam, E, P, flush, reps=5, oracle_rx=97)
             "error_eval": err(E_fast), "error_plain_fp32": err(E_plain), "oracle_receivers": int(len(idx))}
 
 
+def bench_direct_legs(R, dev, grid=1000, side=64, reps=3):
+    """Element -> receiver visibility of a 4,096-element square RIS (64 x 64, lambda/2) in the room,
+    1M receivers: the trace with the direct legs over spatial tiles (pyramids per tile of 32
+    elements, rays for undecided tiles) against one ray per element of every undecided receiver
+    (RISRT_TILES=0); median trace time, kernel times of the direct legs from a profiled trace, and
+    equality of the visibility bits."""
+    import torch
+    w = S.room(grid=grid, square_side=side)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = R.Context(dev.index or 0, stream.cuda_stream)
+    scene, ris, rx = R.upload_workload(ctx, w)
+    out, bits = {"workload": f"room_{side * side}el_{grid}x{grid}_order2", "n_rx": w.n_rx, "elements": w.n_elem}, {}
+    kern = ("k_rx_aperture", "k_vis_decided", "k_tile_aperture", "k_vis_tiles", "k_direct_tiles", "k_direct_vis")
+    for mode in ("tiled", "per_element"):
+        if mode == "per_element":
+            os.environ["RISRT_TILES"] = "0"
+        try:
+            ts = []
+            for _ in range(reps + 1):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w))
+                stream.synchronize()
+                ts.append((time.perf_counter() - t) * 1e3)
+                ps.close()
+            ctx.profile_enable(True)
+            ctx.profile_reset()
+            ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w))
+            prof = ctx.profile()
+            ctx.profile_enable(False)
+            bits[mode] = ps.export()["vis"]
+            ps.close()
+        finally:
+            os.environ.pop("RISRT_TILES", None)
+        out[mode] = {"trace_ms": float(np.median(ts[1:])),
+                     "direct_legs_ms": float(sum(prof[k][0] for k in kern if k in prof)),
+                     "kernels_ms": {k: round(prof[k][0], 3) for k in kern if k in prof}}
+    out["vis_equal"] = bool(np.array_equal(bits["tiled"], bits["per_element"]))
+    out["speedup_direct_legs"] = out["per_element"]["direct_legs_ms"] / max(out["tiled"]["direct_legs_ms"], 1e-9)
+    for h in (rx, ris, scene):
+        h.close()
+    ctx.close()
+    return out
+
+
 def bench_vector(ctx, R, dev, w, scene, rxs, ps, gam, flush, reps=5, oracle_rx=33):
     """The vector field with polarisation (vertical Tx and Rx axes) on the same path set: device time
     of one call (Tx-leg vectors, E0 and the field kernel) with received values only and with the field
@@ -769,7 +814,7 @@ def run_case(args):
     B.build()
     ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
     if args.case in ("trace", "vector"):
-        w = S.room(grid=args.grid)
+        w = S.room(grid=args.grid, square_side=args.side)
         scene, ris, rx = R.upload_workload(ctx, w)
         g = torch.from_numpy(w.gammas).cuda()
         E = torch.empty((g.shape[0], w.n_rx), dtype=torch.complex64, device="cuda")
@@ -824,6 +869,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="risrt", choices=["risrt", "reference"])
     ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--side", type=int, default=0,
+                    help="--case trace/vector: a square RIS of side x side elements instead of the 127-element hex")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=20.0)
@@ -1068,6 +1115,7 @@ def main():
         graph = bench_graph(R, dev, w.__class__(**{**w.__dict__, "rx_xyz": rx_host}), E_step, flush, steps=10)
         free = bench_free_space(ctx, R, dev)
         vector = bench_vector(ctx, R, dev, w, scene, rxs, ps, gam, flush)
+        direct = bench_direct_legs(R, dev)
         vector["vs_scalar_eval_ms"] = vector["ms_received"] / plain["eval_ms"]
     sweep = None
     if rank == 0 and not args.no_sweep:
@@ -1110,6 +1158,7 @@ def main():
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "roofline_field": roof_field, "measured_peaks": mpeaks, "cpu_baseline": cpu,
                 "vs_plain_fp32": plain, "free_space": free, "vector_field": vector, "graph_step": graph,
+                "direct_legs_4096el": direct,
                 "stages": stages, "sweep": sweep, "gradient": grad, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -177,16 +177,20 @@ __device__ __forceinline__ int occ_start(const DeviceScene& S, bool ends_in_box,
     return first;
 }
 
-// Is segment A->B blocked (faces ign0 / ign1 skipped)? `refines` counts FP64 settlements,
-// `err` is set if the traversal stack would overflow (never expected; treated as blocked).
-__device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
-                           unsigned long long* refines, int* err, TraceCounters* tc = nullptr)
+// Is segment a->b blocked (faces ign0 / ign1 skipped)? a, b: FP32 end points within a few ulps of
+// the exact ones (the filter's tolerance covers that); in_box: both exact ends lie in the scene box
+// (the shell subtree is then skipped); exact(A, B) gives the FP64 ends for the settlement of a
+// triangle too close to call. `refines` counts FP64 settlements, `err` is set if the traversal stack
+// would overflow (never expected; treated as blocked).
+template <class Exact>
+__device__ bool seg_blocked_f(const DeviceScene& S, float3 a, float3 b, bool in_box, int ign0, int ign1,
+                              float tol_base, unsigned long long* refines, int* err, Exact exact,
+                              TraceCounters* tc = nullptr)
 {
     int stack[64];
     int sp = 0;
-    int c = occ_start(S, in_scene_box(S, A) && in_scene_box(S, B), stack, sp);   // current node in a register;
-    if (c == kNoRoot) return false;                                               // entered children go on the stack
-    float3 a = to_f(A), b = to_f(B);
+    int c = occ_start(S, in_box, stack, sp);     // current node in a register;
+    if (c == kNoRoot) return false;             // entered children go on the stack
     float3 dir = b - a;
     float len = sqrtf(dot(dir, dir));
     float3 inv = f3(safe_inv(dir.x), safe_inv(dir.y), safe_inv(dir.z));
@@ -203,6 +207,8 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
                 if (r == 1) return true;
                 if (r == 2) {
                     if (refines) atomicAdd(refines, 1ull);
+                    d3 A, B;
+                    exact(A, B);
                     const d3 dirD = B - A;
                     if (tri_hit_fp64(S.tri_verts[i], A, dirD, norm(dirD))) return true;
                 }
@@ -225,6 +231,14 @@ __device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1
         }
     }
     return false;
+}
+
+// The same for FP64 end points A, B (rounded to FP32 for the filter).
+__device__ bool seg_blocked(const DeviceScene& S, d3 A, d3 B, int ign0, int ign1, float tol_base,
+                           unsigned long long* refines, int* err, TraceCounters* tc = nullptr)
+{
+    return seg_blocked_f(S, to_f(A), to_f(B), in_scene_box(S, A) && in_scene_box(S, B), ign0, ign1, tol_base,
+                         refines, err, [&](d3& x, d3& y) { x = A; y = B; }, tc);
 }
 
 // ------------------------------------------------------------------------------------------------

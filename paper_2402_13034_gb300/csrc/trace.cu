@@ -848,25 +848,42 @@ __global__ void k_elem_bounds(const float4* __restrict__ elem, int M, float4* __
     if (threadIdx.x == 0) *out = red[0];
 }
 
-// Per receiver: the pyramid from R through the RIS aperture (the element centres' bounding rectangle
-// in the RIS plane, enlarged by kMapDelta) contains every element -> R segment, so its class decides
-// all of them at once (1 all visible, 2 all blocked, 0 trace each element). With und set, the
-// undecided receivers are appended to und (order unspecified; *und_n counts them).
-__device__ __forceinline__ uint8_t aperture_class(const DeviceScene& S, d3 R, const Frame& fr, float4 b,
-                                                  int host_face, float margin)
+// Per tile: the corners of its rectangle (element-centre bounds enlarged by kMapDelta) computed in
+// FP64 and rounded to FP32, and in c[0].w whether all four lie in the scene box (1) or not (0).
+struct TileGeom {
+    float4 c[4];
+};
+__global__ void k_tile_geom(DeviceScene S, Frame fr, const float4* __restrict__ tile_bb, int T, TileGeom* __restrict__ out)
 {
-    const d3 c = fr_c(fr), n = fr_n(fr), t1 = fr_t1(fr), t2 = fr_t2(fr);
-    const double sd = dot(n, R - c);
-    if (!(fabs(sd) > 1e-2)) return 0;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const d3 c = fr_c(fr), t1 = fr_t1(fr), t2 = fr_t2(fr);
+    const float4 b = tile_bb[t];
     const double a0 = b.x - kMapDelta, a1 = b.y + kMapDelta, b0 = b.z - kMapDelta, b1 = b.w + kMapDelta;
     const d3 Cd[4] = {c + t1 * a0 + t2 * b0, c + t1 * a1 + t2 * b0, c + t1 * a1 + t2 * b1, c + t1 * a0 + t2 * b1};
-    const float3 C[4] = {to_f(Cd[0]), to_f(Cd[1]), to_f(Cd[2]), to_f(Cd[3])};
-    const float3 nb = to_f(sd > 0.0 ? n * -1.0 : n);
-    // the elements lie in the rectangle: with its corners and R in the scene box, every element -> R
-    // segment does too
-    const bool in_box = in_scene_box(S, R) && in_scene_box(S, Cd[0]) && in_scene_box(S, Cd[1]) &&
-                        in_scene_box(S, Cd[2]) && in_scene_box(S, Cd[3]);
-    return classify_pyramid(S, in_box, to_f(R), C, nb, (float)fabs(sd), host_face, -1, margin);
+    bool in_box = true;
+    TileGeom g;
+    for (int k = 0; k < 4; ++k) {
+        const float3 q = to_f(Cd[k]);
+        g.c[k] = make_float4(q.x, q.y, q.z, 0.f);
+        in_box = in_box && in_scene_box(S, Cd[k]);
+    }
+    g.c[0].w = in_box ? 1.f : 0.f;
+    out[t] = g;
+}
+
+// The class of the pyramid from receiver R through a rectangle of the RIS plane (g: its FP32 corners
+// and in-box flag): 1 all visible, 2 all blocked, 0 undecided; in_box: R and the rectangle lie in the
+// scene box, so every segment from R to the rectangle does too. The distance to the RIS plane is
+// taken in FP32: the classification works with margins, so its decisions are sound either way.
+__device__ __forceinline__ uint8_t rect_class(const DeviceScene& S, float3 R, float3 c32, float3 n32, const TileGeom& g,
+                                              int host_face, float margin, bool& in_box)
+{
+    in_box = g.c[0].w != 0.f && in_scene_box(S, R);
+    const float sd = dot(n32, R - c32);
+    if (!(fabsf(sd) > 1e-2f)) return 0;
+    const float3 C[4] = {xyz(g.c[0]), xyz(g.c[1]), xyz(g.c[2]), xyz(g.c[3])};
+    return classify_pyramid(S, in_box, R, C, sd > 0.f ? n32 * -1.f : n32, fabsf(sd), host_face, -1, margin);
 }
 
 // Append the lanes whose `add` is set to list (one atomic per warp); every lane of the warp calls it.
@@ -882,16 +899,21 @@ __device__ __forceinline__ void warp_append(bool add, uint32_t value, uint32_t* 
     if (add) list[base + __popc(bal & ((1u << lane) - 1u))] = value;
 }
 
+// Per receiver: the pyramid from R through the RIS aperture (ag: the element centres' bounding
+// rectangle in the RIS plane, enlarged by kMapDelta) contains every element -> R segment, so its class
+// decides all of them at once (1 all visible, 2 all blocked, 0 trace each element or tile). With und
+// set, the undecided receivers are appended to und (order unspecified; *und_n counts them).
 __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float* __restrict__ rx, int64_t n_rx, Frame fr,
-                                                     const float4* __restrict__ eb, int host_face, float margin,
+                                                     const TileGeom* __restrict__ ag, int host_face, float margin,
                                                      uint8_t* __restrict__ state, uint32_t* __restrict__ und,
                                                      unsigned* __restrict__ und_n)
 {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     uint8_t st = 0;
     if (r < n_rx) {
-        const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
-        st = aperture_class(S, R, fr, *eb, host_face, margin);
+        bool in_box;
+        st = rect_class(S, f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]), to_f(fr_c(fr)), to_f(fr_n(fr)), *ag, host_face,
+                        margin, in_box);
         state[r] = st;
     }
     if (und) warp_append(r < n_rx && st == 0, (uint32_t)r, und, und_n);
@@ -910,24 +932,25 @@ __global__ void k_vis_decided(int64_t n_rx, int W, int M, const uint8_t* __restr
 }
 
 // Per (undecided receiver u, tile t): the class of the pyramid from the receiver through the tile's
-// rectangle (its element centres' bounds, enlarged by kMapDelta) -> tstate[u * T + t]; undecided
+// rectangle -> tstate[u * T + t] (bits 0-1: the class of rect_class; bit 2: its in_box); undecided
 // tiles are appended to work as u * T + t. Grid-stride over the device count of undecided receivers.
 __global__ void __launch_bounds__(128) k_tile_aperture(DeviceScene S, const float* __restrict__ rx, Frame fr,
-                                                       const float4* __restrict__ tile_bb, int T, int host_face,
+                                                       const TileGeom* __restrict__ tg, int T, int host_face,
                                                        float margin, const uint32_t* __restrict__ und,
                                                        const unsigned* __restrict__ und_n, uint8_t* __restrict__ tstate,
                                                        uint32_t* __restrict__ work, unsigned* __restrict__ work_n)
 {
     const int64_t total = (int64_t)*und_n * T;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float3 c32 = to_f(fr_c(fr)), n32 = to_f(fr_n(fr));
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += stride) {   // uniform per block
         const int64_t i = base + threadIdx.x;
         uint8_t st = 0;
         if (i < total) {
             const int64_t r = und[i / T];
-            const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
-            st = aperture_class(S, R, fr, tile_bb[i % T], host_face, margin);
-            tstate[i] = st;
+            bool in_box;
+            st = rect_class(S, f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]), c32, n32, tg[i % T], host_face, margin, in_box);
+            tstate[i] = st | (in_box ? 4 : 0);
         }
         warp_append(i < total && st == 0, (uint32_t)i, work, work_n);
     }
@@ -947,7 +970,7 @@ __global__ void k_vis_tiles(int W, int T, const uint32_t* __restrict__ und, cons
         uint32_t v = 0u;
         for (int p = word_ofs[w]; p < word_ofs[w + 1]; ++p) {
             const int2 q = word_tile[p];
-            if (tstate[u * T + q.x] == 1) v |= (uint32_t)q.y;
+            if ((tstate[u * T + q.x] & 3) == 1) v |= (uint32_t)q.y;
         }
         vis[(int64_t)und[u] * W + w] = v;
     }
@@ -955,9 +978,12 @@ __global__ void k_vis_tiles(int W, int T, const uint32_t* __restrict__ und, cons
 
 // Element -> receiver rays for the undecided tiles, one warp per work entry (lanes over the tile's
 // elements); the visible elements' bits are OR-ed into their words (one atomic per word touched).
+// End points in FP32 (the element from the FP32 frame, within a few ulps of the exact point); the
+// FP64 ends are formed only for a triangle too close to call.
 __global__ void __launch_bounds__(128) k_direct_tiles(DeviceScene S, const float* __restrict__ rx, const float4* __restrict__ elem,
                                                       int W, int T, Frame fr, int host_face, float tol_base,
                                                       const uint32_t* __restrict__ und, const int* __restrict__ tile_elem,
+                                                      const uint8_t* __restrict__ tstate,
                                                       const uint32_t* __restrict__ work, const unsigned* __restrict__ work_n,
                                                       uint32_t* __restrict__ vis, unsigned long long* refines, int* err)
 {
@@ -965,15 +991,21 @@ __global__ void __launch_bounds__(128) k_direct_tiles(DeviceScene S, const float
     const int lane = threadIdx.x & 31;
     const int64_t n = *work_n;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float3 c32 = to_f(fr_c(fr)), t1 = to_f(fr_t1(fr)), t2 = to_f(fr_t2(fr));
     for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {   // uniform per warp
         const uint32_t i = work[k];
         const int64_t r = und[i / T];
         const int m = tile_elem[(int64_t)(i % T) * 32 + lane];
         bool visible = false;
         if (m >= 0) {
-            const d3 e = elem_pos(fr, elem[m]);
-            const d3 R = D3((double)rx[3 * r], (double)rx[3 * r + 1], (double)rx[3 * r + 2]);
-            visible = !seg_blocked(S, e, R, host_face, -1, tol_base, refines, err);
+            const float4 el = elem[m];
+            const float3 a = f3(fmaf(t2.x, el.y, fmaf(t1.x, el.x, c32.x)), fmaf(t2.y, el.y, fmaf(t1.y, el.x, c32.y)),
+                                fmaf(t2.z, el.y, fmaf(t1.z, el.x, c32.z)));
+            const float3 b = f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+            bool in_box = (tstate[i] & 4) != 0;
+            if (!in_box) in_box = in_scene_box(S, elem_pos(fr, el)) && in_scene_box(S, b);
+            visible = !seg_blocked_f(S, a, b, in_box, host_face, -1, tol_base, refines, err,
+                                     [&](d3& x, d3& y) { x = elem_pos(fr, el); y = D3(b.x, b.y, b.z); });
         }
         unsigned todo = __ballot_sync(FULL, visible);
         while (todo) {
@@ -2113,6 +2145,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             unsigned* tile_n;        // their count and the count of undecided (receiver, tile) entries,
             uint8_t* tstate;         // the class of each (undecided receiver, tile) pyramid
             uint32_t* twork;         // and the undecided (receiver, tile) entries
+            TileGeom* tgeom;         // per tile: FP32 corners of its rectangle, in-box flag
+            TileGeom* ageom;         // the same for the whole aperture
             LegBufs main, env, tx;   // work lists, settlement queues and scan space of the Rx leg, of the
                                      // environment paths and of the Tx leg (they run on separate streams)
         };
@@ -2157,6 +2191,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.tile_n = A.get<unsigned>(2);
             L.tstate = A.get<uint8_t>(tiled ? (size_t)n_rx * T_tiles : 1);
             L.twork = A.get<uint32_t>(tiled ? (size_t)n_rx * T_tiles : 1);
+            L.tgeom = A.get<TileGeom>(tiled ? (size_t)T_tiles : 1);
+            L.ageom = A.get<TileGeom>(1);
             L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_seq, L.dense_off, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
                              L.scan_tmp, L.counters + 6};
             // the environment paths run beside the Rx leg: their own work list, queue and scan space
@@ -2256,25 +2292,28 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
         {
             const float mg = 1e-4f * (1.f + ext);
             RISRT_KERNEL_ON(ctx, sB, "k_elem_bounds", (k_elem_bounds<<<1, 256, 0, sB>>>(ris->elem, M, L.elem_bb)));
+            RISRT_KERNEL_ON(ctx, sB, "k_tile_geom", (k_tile_geom<<<1, 32, 0, sB>>>(S, fr, L.elem_bb, 1, L.ageom)));
             if (tiled) {
                 // receivers, then spatial tiles of 32 elements, decided by pyramids; rays for the rest
                 const unsigned grid = (unsigned)ctx->sm_count * 8;
                 RISRT_CUDA(ctx, cudaMemsetAsync(L.tile_n, 0, sizeof(unsigned) * 2, sB));
-                RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.elem_bb,
+                RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.ageom,
                                                                   ris->host_face, mg, L.rx_state, L.und, L.tile_n)));
                 RISRT_KERNEL_ON(ctx, sB, "k_vis_decided", (k_vis_decided<<<nblk(n_rx * W, 256), 256, 0, sB>>>(n_rx, W, M, L.rx_state,
                                                                                                         ps->vis)));
-                RISRT_KERNEL_ON(ctx, sB, "k_tile_aperture", (k_tile_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, ris->tile_bb, T_tiles,
+                RISRT_KERNEL_ON(ctx, sB, "k_tile_geom", (k_tile_geom<<<nblk(T_tiles, 128), 128, 0, sB>>>(S, fr, ris->tile_bb, T_tiles,
+                                                                                               L.tgeom)));
+                RISRT_KERNEL_ON(ctx, sB, "k_tile_aperture", (k_tile_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, L.tgeom, T_tiles,
                                                                   ris->host_face, mg, L.und, L.tile_n, L.tstate, L.twork,
                                                                   L.tile_n + 1)));
                 RISRT_KERNEL_ON(ctx, sB, "k_vis_tiles", (k_vis_tiles<<<grid, 256, 0, sB>>>(W, T_tiles, L.und, L.tile_n, ris->word_ofs,
                                                                   ris->word_tile, L.tstate, ps->vis)));
                 RISRT_KERNEL_ON(ctx, sB, "k_direct_tiles", (k_direct_tiles<<<grid, 128, 0, sB>>>(S, rxp, ris->elem, W, T_tiles, fr,
-                                                                  ris->host_face, tol_base, L.und, ris->tile_elem, L.twork,
-                                                                  L.tile_n + 1, ps->vis, counters, flags_dev + 1)));
+                                                                  ris->host_face, tol_base, L.und, ris->tile_elem, L.tstate,
+                                                                  L.twork, L.tile_n + 1, ps->vis, counters, flags_dev + 1)));
             } else {
                 const int64_t nthreads = n_rx * W * 32;
-                RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.elem_bb,
+                RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.ageom,
                                                                   ris->host_face, mg, L.rx_state, nullptr, nullptr)));
                 RISRT_KERNEL_ON(ctx, sB, "k_direct_vis", (k_direct_vis<<<nblk(nthreads, 128), 128, 0, sB>>>(S, rxp, n_rx, ris->elem, M, W, fr,
                                                                   ris->host_face, tol_base, ps->vis, counters, flags_dev + 1,
