@@ -304,18 +304,65 @@ __global__ void k_patch_boxes(const float* __restrict__ dst_xyz, const int* __re
     }
 }
 
-// One bit per (super-patch, sequence): can a destination of the super-patch make the sequence valid
-// (box_in_beam on the super-patch box)? Word w of super-patch p covers sequences 32w .. 32w + 31.
+// Groups of kGroupSuper consecutive super-patches: the union of their boxes, and in lo.w a margin
+// above every member's (plus a slack far beyond FP32 error), so that a sequence culled for the group
+// is culled for each member: box_in_beam only rejects a box wholly separated by more than the margin,
+// and a separation of the group's box by a larger margin separates every member box too.
+constexpr int kGroupSuper = 16;
+__global__ void k_group_boxes(const float4* __restrict__ sp_box, int64_t n_super, int64_t n_groups, float4* __restrict__ g_box)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_groups) return;
+    const float inf = __int_as_float(0x7f800000);
+    float3 lo = f3(inf, inf, inf), hi = f3(-inf, -inf, -inf);
+    float m = 0.f;
+    for (int64_t sp = g * kGroupSuper; sp < min(n_super, (g + 1) * kGroupSuper); ++sp) {
+        const float3 a = xyz(sp_box[2 * sp]), b = xyz(sp_box[2 * sp + 1]);
+        lo = f3(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z));
+        hi = f3(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z));
+        m = fmaxf(m, cull_margin(a, b));
+    }
+    g_box[2 * g] = make_float4(lo.x, lo.y, lo.z, m + 1e-4f);
+    g_box[2 * g + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+}
+
+// One bit per (box, sequence): can a destination in the box make the sequence valid (box_in_beam)?
+// Word w of box p covers sequences 32w .. 32w + 31. margin_in_w: the boxes carry their margin in
+// lo.w (group boxes), else cull_margin of the box.
 __global__ void k_seq_cull(DeviceScene S, const SeqEntry* __restrict__ seqs, int n_seq, const float4* __restrict__ boxes,
-                           int64_t n_super, int words, unsigned* __restrict__ mask, const int64_t* __restrict__ n_dev)
+                           int64_t n_super, int words, unsigned* __restrict__ mask, const int64_t* __restrict__ n_dev,
+                           bool margin_in_w)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (n_dev) n_seq = (int)min((int64_t)n_seq, *n_dev);   // the table's size on the device (asynchronous traces)
     for (int64_t sp = blockIdx.y; sp < n_super; sp += gridDim.y) {
         bool k = false;
         if (i < n_seq) {
+            const float4 l4 = boxes[2 * sp];
+            const float3 lo = xyz(l4), hi = xyz(boxes[2 * sp + 1]);
+            k = box_in_beam(S, seqs[i], lo, hi, margin_in_w ? l4.w : cull_margin(lo, hi));
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, k);
+        if ((threadIdx.x & 31) == 0 && (i >> 5) < words) mask[sp * words + (i >> 5)] = b;
+    }
+}
+
+// Second level: one bit per (super-patch, position in its group's survivor list): box_in_beam of the
+// survivor on the super-patch box. Blocks past the group's count exit at once (k_mask_compact reads
+// only the words its count covers).
+__global__ void k_seq_cull2(DeviceScene S, const SeqEntry* __restrict__ seqs, const float4* __restrict__ boxes,
+                            int64_t n_super, const int* __restrict__ g_list, const int* __restrict__ g_cnt,
+                            int64_t stride, int words, unsigned* __restrict__ mask)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t sp = blockIdx.y; sp < n_super; sp += gridDim.y) {
+        const int64_t g = sp / kGroupSuper;
+        const int n = g_cnt[g];
+        if ((int)(blockIdx.x * blockDim.x) >= n) continue;        // uniform per block
+        bool k = false;
+        if (i < n) {
             const float3 lo = xyz(boxes[2 * sp]), hi = xyz(boxes[2 * sp + 1]);
-            k = box_in_beam(S, seqs[i], lo, hi, cull_margin(lo, hi));
+            k = box_in_beam(S, seqs[g_list[g * stride + i]], lo, hi, cull_margin(lo, hi));
         }
         const unsigned b = __ballot_sync(0xffffffffu, k);
         if ((threadIdx.x & 31) == 0 && (i >> 5) < words) mask[sp * words + (i >> 5)] = b;
@@ -325,13 +372,17 @@ __global__ void k_seq_cull(DeviceScene S, const SeqEntry* __restrict__ seqs, int
 // Indices of the set bits of each super-patch's sequence mask, in increasing order (one block of 256
 // threads per super-patch): list[p * stride + i] for i < cnt[p].
 __global__ void k_mask_compact(const unsigned* __restrict__ mask, int words, int64_t n_super, int64_t stride,
-                               int* __restrict__ list, int* __restrict__ cnt)
+                               int* __restrict__ list, int* __restrict__ cnt, const int* __restrict__ g_list,
+                               const int* __restrict__ g_cnt)
 {
     __shared__ int part[256];
     for (int64_t sp = blockIdx.x; sp < n_super; sp += gridDim.x) {
         const unsigned* m = mask + sp * words;
-        const int per = (words + (int)blockDim.x - 1) / (int)blockDim.x;
-        const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+        // second level: bits are positions in the group's survivor list, valid up to its count
+        const int nw = g_list ? min(words, (g_cnt[sp / kGroupSuper] + 31) / 32) : words;
+        const int* remap = g_list ? g_list + (sp / kGroupSuper) * stride : nullptr;
+        const int per = (nw + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
         int c = 0;
         for (int w = w0; w < w1; ++w) c += __popc(m[w]);
         part[threadIdx.x] = c;
@@ -345,7 +396,10 @@ __global__ void k_mask_compact(const unsigned* __restrict__ mask, int words, int
         int pos = part[threadIdx.x] - c;
         int* out = list + sp * stride;
         for (int w = w0; w < w1; ++w)
-            for (unsigned b = m[w]; b; b &= b - 1) out[pos++] = w * 32 + __ffs(b) - 1;
+            for (unsigned b = m[w]; b; b &= b - 1) {
+                const int idx = w * 32 + __ffs(b) - 1;
+                out[pos++] = remap ? remap[idx] : idx;
+            }
         if (threadIdx.x == blockDim.x - 1) cnt[sp] = part[threadIdx.x];
         __syncthreads();
     }
@@ -400,6 +454,18 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
     const int* lst = slist ? slist + spi * slist_stride : nullptr;
     const int lcnt = slist ? slist_cnt[spi] : n_seq;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this warp's box over its active destinations
+    const float inf = __int_as_float(0x7f800000);
+    float3 wlo = active ? R : f3(inf, inf, inf), whi = active ? R : f3(-inf, -inf, -inf);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wlo = f3(fminf(wlo.x, __shfl_xor_sync(0xffffffffu, wlo.x, o)), fminf(wlo.y, __shfl_xor_sync(0xffffffffu, wlo.y, o)),
+                 fminf(wlo.z, __shfl_xor_sync(0xffffffffu, wlo.z, o)));
+        whi = f3(fmaxf(whi.x, __shfl_xor_sync(0xffffffffu, whi.x, o)), fmaxf(whi.y, __shfl_xor_sync(0xffffffffu, whi.y, o)),
+                 fmaxf(whi.z, __shfl_xor_sync(0xffffffffu, whi.z, o)));
+    }
+    const bool warp_any = __any_sync(0xffffffffu, active);
+    const float wmargin = warp_any ? cull_margin(wlo, whi) : 0.f;
     int wn = 0;                                      // staged work-list entries of this warp (uniform)
     auto flush = [&]() {
         __syncwarp();
@@ -437,87 +503,98 @@ k_candidates(DeviceScene S, const float* __restrict__ dst_xyz, int64_t n_dst, co
         }
         if (k) kept[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)threadIdx.x;
         __syncthreads();
-        for (int q = 0; q < n_kept; ++q) {
-            const int j = kept[q];
-            const int sidx = sh_idx[j];
-            const SeqEntry& e = sh[j];
-            // the geometric tests (A)-(D); false when they reject, or when the decision is queued
-            auto passes = [&]() -> bool {
-                // (A)
-                const float sR = dot(xyz(e.pL), R) - e.pL.w;
-                const float sp = e.sL.w;
-                const bool clearA = fabsf(sR) > tol_base && fabsf(sp) > tol_base;
-                if (clearA && sp * sR < 0.f) return false;
-                bool unsure = !clearA;
-                // (B) last reflection point P = R + t (S_L - R), t = sR / (sR + sp)
-                const float den = sR + sp;
-                const float3 d = xyz(e.sL) - R;
-                const float iden = __frcp_rn(den);
-                const float t = sR * iden;
-                const float3 P = R + d * t;
-                const float d2 = dot(d, d);
-                const float cond = d2 * rsqrtf(d2) * fabsf(iden);   // |d| / |den| (a few ulps suffice: tol has margin)
-                const float tol = tol_base * fminf(cond, 1e6f);
-                const int k = e.info.w;
-                const int cB = face_class<SMEM_FACES>(S, sh_faces, k == 2 ? e.info.y : e.info.x, P, tol);
-                if (cB == 0) return false;
-                unsure |= cB == 2;
-                if (k == 2) {
-                    // (C)
-                    const float s1P = dot(xyz(e.p1), P) - e.p1.w;
-                    const float ssrc = e.s1.w;
-                    const bool clearC = fabsf(s1P) > tol && fabsf(ssrc) > tol_base;
-                    if (clearC && s1P * ssrc < 0.f) return false;
-                    unsure |= !clearC;
-                    // (D) P1 = P + t1 (S1 - P), t1 = s1P / (s1P + ssrc)
-                    const float den1 = s1P + ssrc;
-                    const float3 d1 = xyz(e.s1) - P;
-                    const float iden1 = __frcp_rn(den1);
-                    const float3 P1 = P + d1 * (s1P * iden1);
-                    const float d12 = dot(d1, d1);
-                    const float cond1 = d12 * rsqrtf(d12) * fabsf(iden1);
-                    const float tol1 = tol * fminf(cond1, 1e6f) + tol_base;
-                    const int cD = face_class<SMEM_FACES>(S, sh_faces, e.info.x, P1, tol1);
-                    if (cD == 0) return false;
-                    unsure |= cD == 2;
-                }
-                if (unsure) {
-                    if (rq.q) {
-                        const unsigned pos = atomicAdd(rq.cnt, 1u);
-                        if (pos < (unsigned)rq.cap) {
-                            rq.q[pos] = make_int4((int)r, sidx, 0, 0);
-                            return false;
-                        }
-                    }
-                    atomicAdd(refines, 1ull);
-                    d3 pts[4];
-                    const d3 Rd = D3((double)R.x, (double)R.y, (double)R.z);
-                    if (!seq_geom_fp64(S, src, Rd, e.info, seqd[sidx], pts)) return false;
-                }
-                return true;
-            };
-            bool pass = active && passes();
-            int slot = -1;
-            if (pass) {
-                slot = atomicAdd(&cand_cnt[r], 1);
-                if (slot < cap) {
-                    cand[r * (int64_t)cap + slot] = sidx;
-                } else {
-                    atomicExch(overflow, 1);
-                    pass = false;
-                }
+        // a third level for first-order sequences: each warp's own box (32 Morton-adjacent
+        // destinations) against the kept ones, 32 at a time; the warp's destinations then test only the
+        // sequences that pass (second-order sequences, whose beam test costs two pyramids and whose
+        // beams are wide against a block in the scenes measured, are not culled again)
+        for (int c0 = 0; c0 < n_kept && warp_any; c0 += 32) {
+            bool wk = c0 + lane < n_kept;
+            if (wk) {
+                const SeqEntry& q = sh[kept[c0 + lane]];
+                wk = q.info.w != 1 || box_in_beam(S, q, wlo, whi, wmargin);
             }
-            if (dl.r) {                              // this warp's run of sequence sidx
-                const unsigned b = __ballot_sync(0xffffffffu, pass);
-                const int nb = __popc(b);
-                if (nb) {
-                    if (wn + nb > kDenseBuf) flush();
-                    if (pass) {
-                        const int k = wn + __popc(b & ((1u << lane) - 1u));
-                        dbuf[warp][k] = make_int2((int)r, slot);
-                        dseq[warp][k] = sidx;
+            for (unsigned bits = __ballot_sync(0xffffffffu, wk); bits; bits &= bits - 1) {
+                const int j = kept[c0 + __ffs(bits) - 1];
+                const int sidx = sh_idx[j];
+                const SeqEntry& e = sh[j];
+                // the geometric tests (A)-(D); false when they reject, or when the decision is queued
+                auto passes = [&]() -> bool {
+                    // (A)
+                    const float sR = dot(xyz(e.pL), R) - e.pL.w;
+                    const float sp = e.sL.w;
+                    const bool clearA = fabsf(sR) > tol_base && fabsf(sp) > tol_base;
+                    if (clearA && sp * sR < 0.f) return false;
+                    bool unsure = !clearA;
+                    // (B) last reflection point P = R + t (S_L - R), t = sR / (sR + sp)
+                    const float den = sR + sp;
+                    const float3 d = xyz(e.sL) - R;
+                    const float iden = __frcp_rn(den);
+                    const float t = sR * iden;
+                    const float3 P = R + d * t;
+                    const float d2 = dot(d, d);
+                    const float cond = d2 * rsqrtf(d2) * fabsf(iden);   // |d| / |den| (a few ulps suffice: tol has margin)
+                    const float tol = tol_base * fminf(cond, 1e6f);
+                    const int k = e.info.w;
+                    const int cB = face_class<SMEM_FACES>(S, sh_faces, k == 2 ? e.info.y : e.info.x, P, tol);
+                    if (cB == 0) return false;
+                    unsure |= cB == 2;
+                    if (k == 2) {
+                        // (C)
+                        const float s1P = dot(xyz(e.p1), P) - e.p1.w;
+                        const float ssrc = e.s1.w;
+                        const bool clearC = fabsf(s1P) > tol && fabsf(ssrc) > tol_base;
+                        if (clearC && s1P * ssrc < 0.f) return false;
+                        unsure |= !clearC;
+                        // (D) P1 = P + t1 (S1 - P), t1 = s1P / (s1P + ssrc)
+                        const float den1 = s1P + ssrc;
+                        const float3 d1 = xyz(e.s1) - P;
+                        const float iden1 = __frcp_rn(den1);
+                        const float3 P1 = P + d1 * (s1P * iden1);
+                        const float d12 = dot(d1, d1);
+                        const float cond1 = d12 * rsqrtf(d12) * fabsf(iden1);
+                        const float tol1 = tol * fminf(cond1, 1e6f) + tol_base;
+                        const int cD = face_class<SMEM_FACES>(S, sh_faces, e.info.x, P1, tol1);
+                        if (cD == 0) return false;
+                        unsure |= cD == 2;
                     }
-                    wn += nb;
+                    if (unsure) {
+                        if (rq.q) {
+                            const unsigned pos = atomicAdd(rq.cnt, 1u);
+                            if (pos < (unsigned)rq.cap) {
+                                rq.q[pos] = make_int4((int)r, sidx, 0, 0);
+                                return false;
+                            }
+                        }
+                        atomicAdd(refines, 1ull);
+                        d3 pts[4];
+                        const d3 Rd = D3((double)R.x, (double)R.y, (double)R.z);
+                        if (!seq_geom_fp64(S, src, Rd, e.info, seqd[sidx], pts)) return false;
+                    }
+                    return true;
+                };
+                bool pass = active && passes();
+                int slot = -1;
+                if (pass) {
+                    slot = atomicAdd(&cand_cnt[r], 1);
+                    if (slot < cap) {
+                        cand[r * (int64_t)cap + slot] = sidx;
+                    } else {
+                        atomicExch(overflow, 1);
+                        pass = false;
+                    }
+                }
+                if (dl.r) {                              // this warp's run of sequence sidx
+                    const unsigned b = __ballot_sync(0xffffffffu, pass);
+                    const int nb = __popc(b);
+                    if (nb) {
+                        if (wn + nb > kDenseBuf) flush();
+                        if (pass) {
+                            const int k = wn + __popc(b & ((1u << lane) - 1u));
+                            dbuf[warp][k] = make_int2((int)r, slot);
+                            dseq[warp][k] = sidx;
+                        }
+                        wn += nb;
+                    }
                 }
             }
         }
@@ -1865,6 +1942,10 @@ struct LegBufs {
     unsigned* sp_mask = nullptr;     // [n_super][ceil(n_seq / 32)] sequence survivors per super-patch
     int* sp_list = nullptr;          // [n_super][32 ceil(n_seq / 32)] the same as index lists
     int* sp_cnt = nullptr;           // [n_super]
+    float4* g_box = nullptr;         // the same for groups of kGroupSuper super-patches
+    unsigned* g_mask = nullptr;
+    int* g_list = nullptr;
+    int* g_cnt = nullptr;
 };
 constexpr int kTxLegQueue = 4096;   // settlements queued by the Tx leg (more are settled in place)
 
@@ -2012,6 +2093,10 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     // per element for every receiver whose aperture pyramid is undecided (both give the same bits)
     const int T_tiles = ris->n_tiles;
     const char* tiles_env = getenv("RISRT_TILES");
+    // sequence culling over groups of super-patches first; RISRT_CULL_LEVELS=1 culls each super-patch
+    // against every sequence (both give the same candidates)
+    const char* cull_env = getenv("RISRT_CULL_LEVELS");
+    const bool two_level_cull = !(cull_env && cull_env[0] == '1');
     const bool tiled = T_tiles > 0 && (uint64_t)n_rx * (uint64_t)T_tiles < (1ull << 32) &&
                        !(tiles_env && tiles_env[0] == '0');
     ps->W = W;
@@ -2213,6 +2298,11 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 lb->sp_mask = A.get<unsigned>(ns * ((n_ids_max + 31) / 32 + 1));
                 lb->sp_list = A.get<int>(ns * ((n_ids_max + 31) / 32 + 1) * 32);
                 lb->sp_cnt = A.get<int>(ns);
+                const size_t ng = ns / kGroupSuper + 1;
+                lb->g_box = A.get<float4>(ng * 2);
+                lb->g_mask = A.get<unsigned>(ng * ((n_ids_max + 31) / 32 + 1));
+                lb->g_list = A.get<int>(ng * ((n_ids_max + 31) / 32 + 1) * 32);
+                lb->g_cnt = A.get<int>(ng);
             }
             L.tx.dense_r = A.get<int>((size_t)cap);
             L.tx.dense_slot = A.get<int>((size_t)cap);
@@ -2375,10 +2465,32 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     const int64_t n_super = (n_dst + kSuperRx - 1) / kSuperRx;
                     RISRT_KERNEL_ON(ctx, st, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, st>>>(dst, L.rx_order, n_dst,
                                                                                                        lb.sp_box)));
-                    RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
-                                                                  256, 0, st>>>(S, t.e, t.n, lb.sp_box, n_super, words, lb.sp_mask, n_dev)));
-                    RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
-                                                            lb.sp_mask, words, n_super, (int64_t)words * 32, lb.sp_list, lb.sp_cnt)));
+                    if (n_super > 2 * kGroupSuper && two_level_cull) {
+                        // two levels: groups of super-patches against every sequence, then each
+                        // super-patch against its group's survivors
+                        const int64_t n_groups = (n_super + kGroupSuper - 1) / kGroupSuper;
+                        RISRT_KERNEL_ON(ctx, st, "k_group_boxes", (k_group_boxes<<<nblk(n_groups, 128), 128, 0, st>>>(
+                                                                  lb.sp_box, n_super, n_groups, lb.g_box)));
+                        RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_groups, 65535)),
+                                                                      256, 0, st>>>(S, t.e, t.n, lb.g_box, n_groups, words, lb.g_mask,
+                                                                                    n_dev, true)));
+                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_groups, 4096), 256, 0, st>>>(
+                                                                lb.g_mask, words, n_groups, (int64_t)words * 32, lb.g_list, lb.g_cnt,
+                                                                nullptr, nullptr)));
+                        RISRT_KERNEL_ON(ctx, st, "k_seq_cull2", (k_seq_cull2<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
+                                                                 256, 0, st>>>(S, t.e, lb.sp_box, n_super, lb.g_list, lb.g_cnt,
+                                                                               (int64_t)words * 32, words, lb.sp_mask)));
+                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
+                                                                lb.sp_mask, words, n_super, (int64_t)words * 32, lb.sp_list, lb.sp_cnt,
+                                                                lb.g_list, lb.g_cnt)));
+                    } else {
+                        RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
+                                                                      256, 0, st>>>(S, t.e, t.n, lb.sp_box, n_super, words, lb.sp_mask,
+                                                                                    n_dev, false)));
+                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
+                                                                lb.sp_mask, words, n_super, (int64_t)words * 32, lb.sp_list, lb.sp_cnt,
+                                                                nullptr, nullptr)));
+                    }
                     slist = lb.sp_list;
                     slist_cnt = lb.sp_cnt;
                     slist_stride = (int64_t)words * 32;

@@ -102,6 +102,22 @@ def test_tiled_direct_legs(side, monkeypatch):
     oracle_parity(w, g)
 
 
+def test_two_level_culling_same_paths(monkeypatch):
+    """The full 256x256 room (64 super-patches of 1,024 receivers, so the sequences are culled for
+    groups of 16 super-patches first): path sets and fields equal those of culling every super-patch
+    against every sequence (RISRT_CULL_LEVELS=1)."""
+    w = S.room()
+    g = run_gpu(w)
+    monkeypatch.setenv("RISRT_CULL_LEVELS", "1")
+    g1 = run_gpu(w)
+    monkeypatch.delenv("RISRT_CULL_LEVELS")
+    for k in ("los", "vis", "tx_seqs", "tx_vis"):
+        assert np.array_equal(g["paths"][k], g1["paths"][k]), k
+    for k in ("seqs", "env"):
+        assert all(np.array_equal(a, b) for a, b in zip(g["paths"][k], g1["paths"][k], strict=True)), k
+    assert np.array_equal(g["P"], g1["P"])
+
+
 def test_room_field_parity():
     w = S.room(grid=16)
     g = run_gpu(w, want_A=True)
