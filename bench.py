@@ -272,7 +272,8 @@ def bench_direct_legs(R, dev, grid=1000, side=64, reps=3):
     ctx = R.Context(dev.index or 0, stream.cuda_stream)
     scene, ris, rx = R.upload_workload(ctx, w)
     out, bits = {"workload": f"room_{side * side}el_{grid}x{grid}_order2", "n_rx": w.n_rx, "elements": w.n_elem}, {}
-    kern = ("k_rx_aperture", "k_vis_decided", "k_tile_aperture", "k_vis_tiles", "k_direct_tiles", "k_direct_vis")
+    kern = ("k_tile_geom", "k_rx_aperture", "k_vis_decided", "k_tile_aperture", "k_vis_tiles", "k_direct_tiles",
+            "k_direct_settle", "k_direct_vis")
     for mode in ("tiled", "per_element"):
         if mode == "per_element":
             os.environ["RISRT_TILES"] = "0"

@@ -181,11 +181,14 @@ __device__ __forceinline__ int occ_start(const DeviceScene& S, bool ends_in_box,
 // the exact ones (the filter's tolerance covers that); in_box: both exact ends lie in the scene box
 // (the shell subtree is then skipped); exact(A, B) gives the FP64 ends for the settlement of a
 // triangle too close to call. `refines` counts FP64 settlements, `err` is set if the traversal stack
-// would overflow (never expected; treated as blocked).
+// would overflow (never expected; treated as blocked). With `unsure` set (int[3], zeroed by the
+// caller), a triangle too close to call is not settled: unsure[0] counts them and unsure[1..2] keep
+// the first two, and the walk goes on; a false return with unsure[0] > 0 means "unblocked unless one
+// of those triangles is hit", for the caller to settle later (densely).
 template <class Exact>
 __device__ bool seg_blocked_f(const DeviceScene& S, float3 a, float3 b, bool in_box, int ign0, int ign1,
                               float tol_base, unsigned long long* refines, int* err, Exact exact,
-                              TraceCounters* tc = nullptr)
+                              TraceCounters* tc = nullptr, int* unsure = nullptr)
 {
     int stack[64];
     int sp = 0;
@@ -206,11 +209,16 @@ __device__ bool seg_blocked_f(const DeviceScene& S, float3 a, float3 b, bool in_
                 int r = tri_hit_fp32(S.tri_geom[i], a, dir, len, tb);
                 if (r == 1) return true;
                 if (r == 2) {
-                    if (refines) atomicAdd(refines, 1ull);
-                    d3 A, B;
-                    exact(A, B);
-                    const d3 dirD = B - A;
-                    if (tri_hit_fp64(S.tri_verts[i], A, dirD, norm(dirD))) return true;
+                    if (unsure) {
+                        if (unsure[0] < 2) unsure[1 + unsure[0]] = i;
+                        ++unsure[0];
+                    } else {
+                        if (refines) atomicAdd(refines, 1ull);
+                        d3 A, B;
+                        exact(A, B);
+                        const d3 dirD = B - A;
+                        if (tri_hit_fp64(S.tri_verts[i], A, dirD, norm(dirD))) return true;
+                    }
                 }
             }
             if (sp == 0) break;

@@ -930,6 +930,7 @@ __global__ void k_elem_bounds(const float4* __restrict__ elem, int M, float4* __
 struct TileGeom {
     float4 c[4];
 };
+constexpr int kTileDeferCap = 1 << 20;   // tile rays queued for the FP64 settlement (more settle in place)
 __global__ void k_tile_geom(DeviceScene S, Frame fr, const float4* __restrict__ tile_bb, int T, TileGeom* __restrict__ out)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1053,18 +1054,52 @@ __global__ void k_vis_tiles(int W, int T, const uint32_t* __restrict__ und, cons
     }
 }
 
+// One element -> receiver ray of an undecided tile: its FP32 end points (the element from the FP32
+// frame, within a few ulps of the exact point) and whether both exact ends lie in the scene box.
+struct TileRay {
+    float3 a, b;
+    bool in_box;
+};
+__device__ __forceinline__ TileRay tile_ray(const DeviceScene& S, const float* rx, int64_t r, float4 el, const Frame& fr,
+                                            float3 c32, float3 t1, float3 t2, bool tile_in_box)
+{
+    TileRay q;
+    q.a = f3(fmaf(t2.x, el.y, fmaf(t1.x, el.x, c32.x)), fmaf(t2.y, el.y, fmaf(t1.y, el.x, c32.y)),
+             fmaf(t2.z, el.y, fmaf(t1.z, el.x, c32.z)));
+    q.b = f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    q.in_box = tile_in_box || (in_scene_box(S, elem_pos(fr, el)) && in_scene_box(S, q.b));
+    return q;
+}
+
+// OR the bits of the lanes whose `visible` is set into their visibility words of receiver r (one
+// atomic per word touched); every lane of the warp calls it.
+__device__ __forceinline__ void or_visible_bits(bool visible, int m, uint32_t* vis, int64_t row)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned todo = __ballot_sync(FULL, visible);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int word = __shfl_sync(FULL, m >> 5, leader);
+        const bool mine = visible && (m >> 5) == word;
+        const unsigned bits = __reduce_or_sync(FULL, mine ? 1u << (m & 31) : 0u);
+        todo &= ~__ballot_sync(FULL, mine);
+        if (lane == leader) atomicOr(&vis[row + word], bits);
+    }
+}
+
 // Element -> receiver rays for the undecided tiles, one warp per work entry (lanes over the tile's
-// elements); the visible elements' bits are OR-ed into their words (one atomic per word touched).
-// End points in FP32 (the element from the FP32 frame, within a few ulps of the exact point); the
-// FP64 ends are formed only for a triangle too close to call.
+// elements); the visible elements' bits are OR-ed into their words. A ray with a triangle too close
+// to call in FP32 and no certain hit is queued (work entry, lane) for k_direct_settle, which settles
+// such rays 32 to a warp in FP64 (a full queue settles in place).
 __global__ void __launch_bounds__(128) k_direct_tiles(DeviceScene S, const float* __restrict__ rx, const float4* __restrict__ elem,
                                                       int W, int T, Frame fr, int host_face, float tol_base,
                                                       const uint32_t* __restrict__ und, const int* __restrict__ tile_elem,
                                                       const uint8_t* __restrict__ tstate,
                                                       const uint32_t* __restrict__ work, const unsigned* __restrict__ work_n,
-                                                      uint32_t* __restrict__ vis, unsigned long long* refines, int* err)
+                                                      uint32_t* __restrict__ vis, int4* __restrict__ dq, int dq_cap,
+                                                      unsigned* __restrict__ dq_n, unsigned long long* refines, int* err)
 {
-    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t n = *work_n;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1076,23 +1111,53 @@ __global__ void __launch_bounds__(128) k_direct_tiles(DeviceScene S, const float
         bool visible = false;
         if (m >= 0) {
             const float4 el = elem[m];
-            const float3 a = f3(fmaf(t2.x, el.y, fmaf(t1.x, el.x, c32.x)), fmaf(t2.y, el.y, fmaf(t1.y, el.x, c32.y)),
-                                fmaf(t2.z, el.y, fmaf(t1.z, el.x, c32.z)));
-            const float3 b = f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
-            bool in_box = (tstate[i] & 4) != 0;
-            if (!in_box) in_box = in_scene_box(S, elem_pos(fr, el)) && in_scene_box(S, b);
-            visible = !seg_blocked_f(S, a, b, in_box, host_face, -1, tol_base, refines, err,
-                                     [&](d3& x, d3& y) { x = elem_pos(fr, el); y = D3(b.x, b.y, b.z); });
+            const TileRay q = tile_ray(S, rx, r, el, fr, c32, t1, t2, (tstate[i] & 4) != 0);
+            auto exact = [&](d3& x, d3& y) { x = elem_pos(fr, el); y = D3(q.b.x, q.b.y, q.b.z); };
+            int un[3] = {0, -1, -1};
+            const bool blocked = seg_blocked_f(S, q.a, q.b, q.in_box, host_face, -1, tol_base, nullptr, err, exact,
+                                               nullptr, un);
+            visible = !blocked && un[0] == 0;
+            if (!blocked && un[0] > 0) {
+                const unsigned pos = atomicAdd(dq_n, 1u);
+                if (pos < (unsigned)dq_cap)     // up to two triangles to settle, else the whole ray (-1)
+                    dq[pos] = make_int4((int)i, lane, un[0] <= 2 ? un[1] : -1, un[0] <= 2 ? un[2] : -1);
+                else
+                    visible = !seg_blocked_f(S, q.a, q.b, q.in_box, host_face, -1, tol_base, refines, err, exact);
+            }
         }
-        unsigned todo = __ballot_sync(FULL, visible);
-        while (todo) {
-            const int leader = __ffs(todo) - 1;
-            const int word = __shfl_sync(FULL, m >> 5, leader);
-            const bool mine = visible && (m >> 5) == word;
-            const unsigned bits = __reduce_or_sync(FULL, mine ? 1u << (m & 31) : 0u);
-            todo &= ~__ballot_sync(FULL, mine);
-            if (lane == leader) atomicOr(&vis[r * W + word], bits);
+        or_visible_bits(visible, m, vis, r * W);
+    }
+}
+
+// The queued rays of k_direct_tiles, one per thread: the (at most two) triangles left too close to
+// call tested in FP64, or, for a ray that met more of them, the ray walked again with each settled in
+// FP64; visible bits OR-ed into their words.
+__global__ void k_direct_settle(DeviceScene S, const float* __restrict__ rx, const float4* __restrict__ elem, int W, int T,
+                                Frame fr, int host_face, float tol_base, const uint32_t* __restrict__ und,
+                                const int* __restrict__ tile_elem, const uint8_t* __restrict__ tstate,
+                                const int4* __restrict__ dq, int dq_cap, const unsigned* __restrict__ dq_n,
+                                uint32_t* __restrict__ vis, unsigned long long* refines, int* err)
+{
+    const unsigned n = min(*dq_n, (unsigned)dq_cap);
+    const float3 c32 = to_f(fr_c(fr)), t1 = to_f(fr_t1(fr)), t2 = to_f(fr_t2(fr));
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int4 e = dq[j];
+        const uint32_t i = (uint32_t)e.x;
+        const int64_t r = und[i / T];
+        const int m = tile_elem[(int64_t)(i % T) * 32 + e.y];
+        const float4 el = elem[m];
+        const TileRay q = tile_ray(S, rx, r, el, fr, c32, t1, t2, (tstate[i] & 4) != 0);
+        bool blocked;
+        if (e.z >= 0) {
+            atomicAdd(refines, e.w >= 0 ? 2ull : 1ull);
+            const d3 A = elem_pos(fr, el), B = D3(q.b.x, q.b.y, q.b.z), dD = B - A;
+            const double L = norm(dD);
+            blocked = tri_hit_fp64(S.tri_verts[e.z], A, dD, L) || (e.w >= 0 && tri_hit_fp64(S.tri_verts[e.w], A, dD, L));
+        } else {
+            blocked = seg_blocked_f(S, q.a, q.b, q.in_box, host_face, -1, tol_base, refines, err,
+                                    [&](d3& x, d3& y) { x = elem_pos(fr, el); y = D3(q.b.x, q.b.y, q.b.z); });
         }
+        if (!blocked) atomicOr(&vis[r * W + (m >> 5)], 1u << (m & 31));
     }
 }
 
@@ -2231,6 +2296,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             uint8_t* tstate;         // the class of each (undecided receiver, tile) pyramid
             uint32_t* twork;         // and the undecided (receiver, tile) entries
             TileGeom* tgeom;         // per tile: FP32 corners of its rectangle, in-box flag
+            int4* tdq;               // tile rays left for the FP64 settlement (work entry, lane, triangles)
             TileGeom* ageom;         // the same for the whole aperture
             LegBufs main, env, tx;   // work lists, settlement queues and scan space of the Rx leg, of the
                                      // environment paths and of the Tx leg (they run on separate streams)
@@ -2273,7 +2339,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.elem_bb = A.get<float4>(1);
             L.rx_state = A.get<uint8_t>((size_t)n_rx);
             L.und = A.get<uint32_t>(tiled ? (size_t)n_rx : 1);
-            L.tile_n = A.get<unsigned>(2);
+            L.tile_n = A.get<unsigned>(3);
+            L.tdq = A.get<int4>(tiled ? (size_t)kTileDeferCap : 1);
             L.tstate = A.get<uint8_t>(tiled ? (size_t)n_rx * T_tiles : 1);
             L.twork = A.get<uint32_t>(tiled ? (size_t)n_rx * T_tiles : 1);
             L.tgeom = A.get<TileGeom>(tiled ? (size_t)T_tiles : 1);
@@ -2386,7 +2453,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             if (tiled) {
                 // receivers, then spatial tiles of 32 elements, decided by pyramids; rays for the rest
                 const unsigned grid = (unsigned)ctx->sm_count * 8;
-                RISRT_CUDA(ctx, cudaMemsetAsync(L.tile_n, 0, sizeof(unsigned) * 2, sB));
+                RISRT_CUDA(ctx, cudaMemsetAsync(L.tile_n, 0, sizeof(unsigned) * 3, sB));
                 RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.ageom,
                                                                   ris->host_face, mg, L.rx_state, L.und, L.tile_n)));
                 RISRT_KERNEL_ON(ctx, sB, "k_vis_decided", (k_vis_decided<<<nblk(n_rx * W, 256), 256, 0, sB>>>(n_rx, W, M, L.rx_state,
@@ -2400,7 +2467,12 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                                                                   ris->word_tile, L.tstate, ps->vis)));
                 RISRT_KERNEL_ON(ctx, sB, "k_direct_tiles", (k_direct_tiles<<<grid, 128, 0, sB>>>(S, rxp, ris->elem, W, T_tiles, fr,
                                                                   ris->host_face, tol_base, L.und, ris->tile_elem, L.tstate,
-                                                                  L.twork, L.tile_n + 1, ps->vis, counters, flags_dev + 1)));
+                                                                  L.twork, L.tile_n + 1, ps->vis, L.tdq, kTileDeferCap,
+                                                                  L.tile_n + 2, counters, flags_dev + 1)));
+                RISRT_KERNEL_ON(ctx, sB, "k_direct_settle", (k_direct_settle<<<grid, 128, 0, sB>>>(S, rxp, ris->elem, W, T_tiles, fr,
+                                                                  ris->host_face, tol_base, L.und, ris->tile_elem, L.tstate,
+                                                                  L.tdq, kTileDeferCap, L.tile_n + 2, ps->vis, counters,
+                                                                  flags_dev + 1)));
             } else {
                 const int64_t nthreads = n_rx * W * 32;
                 RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.ageom,
