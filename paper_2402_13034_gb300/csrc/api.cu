@@ -176,7 +176,8 @@ struct TileLayout {
 
 // Spatial tiles of a RIS for the direct legs: the elements in the Morton order of their (a, b)
 // coordinates (quantised to 16 bits over the array's extent; ties by index), 32 consecutive ones per
-// tile; per tile the bounds of its element centres; per visibility word (elements 32 w .. 32 w + 31)
+// tile; per tile the bounds of its element centres, then per super-tile (four consecutive tiles) the
+// bounds of its tiles; per visibility word (elements 32 w .. 32 w + 31)
 // the tiles that hold its elements with the bits of those elements. One host buffer, laid out as
 // tile bounds, word pairs, tile elements, word offsets.
 TileLayout build_tiles(const float* uv, int M, std::vector<char>& buf, int& n_tiles)
@@ -212,6 +213,14 @@ TileLayout build_tiles(const float* uv, int M, std::vector<char>& buf, int& n_ti
         if (pw.empty() || pw.back().first != t) pw.push_back({t, 0u});
         pw.back().second |= 1u << (m & 31);
     }
+    // super-tiles: four consecutive tiles (128 elements consecutive in Morton order); their bounds
+    // follow the tiles' in the same array
+    for (int t = 0; t < T; t += 4) {
+        float4 b = bb[t];
+        for (int q = t + 1; q < std::min(T, t + 4); ++q)
+            b = make_float4(std::min(b.x, bb[q].x), std::max(b.y, bb[q].y), std::min(b.z, bb[q].z), std::max(b.w, bb[q].w));
+        bb.push_back(b);
+    }
     std::vector<int> ofs(W + 1, 0);
     std::vector<int2> pairs;
     for (int w = 0; w < W; ++w) {
@@ -226,7 +235,7 @@ TileLayout build_tiles(const float* uv, int M, std::vector<char>& buf, int& n_ti
     }
     TileLayout L;
     L.bb = 0;
-    L.pairs = L.bb + sizeof(float4) * (size_t)T;
+    L.pairs = L.bb + sizeof(float4) * bb.size();
     L.elem = L.pairs + sizeof(int2) * pairs.size();
     L.ofs = L.elem + sizeof(int) * elem.size();
     L.bytes = L.ofs + sizeof(int) * ofs.size();

@@ -242,7 +242,8 @@ struct risrt_ris {
     // legs' visibility, built at upload for M > kTileMinElems; one device block holds all four arrays.
     int n_tiles = 0;
     void* tile_buf = nullptr;
-    float4* tile_bb = nullptr;   // [n_tiles] (a_min, a_max, b_min, b_max) of the tile's element centres
+    float4* tile_bb = nullptr;   // [n_tiles + ceil(n_tiles / 4)] (a_min, a_max, b_min, b_max) of the tile's
+                                 // element centres, then of each super-tile (four consecutive tiles)
     int2* word_tile = nullptr;   // [n_pairs] (tile, bits of a visibility word's elements in that tile)
     int* tile_elem = nullptr;    // [n_tiles * 32] element indices, -1 past the tile's end
     int* word_ofs = nullptr;     // [W + 1] word w's pairs are word_tile[word_ofs[w] .. word_ofs[w + 1])

@@ -1009,36 +1009,74 @@ __global__ void k_vis_decided(int64_t n_rx, int W, int M, const uint8_t* __restr
     vis[i] = st == 2 ? 0u : (left >= 32 ? 0xffffffffu : ((1u << left) - 1u));
 }
 
-// Per (undecided receiver u, tile t): the class of the pyramid from the receiver through the tile's
-// rectangle -> tstate[u * T + t] (bits 0-1: the class of rect_class; bit 2: its in_box); undecided
-// tiles are appended to work as u * T + t. Grid-stride over the device count of undecided receivers.
-__global__ void __launch_bounds__(128) k_tile_aperture(DeviceScene S, const float* __restrict__ rx, Frame fr,
-                                                       const TileGeom* __restrict__ tg, int T, int host_face,
-                                                       float margin, const uint32_t* __restrict__ und,
-                                                       const unsigned* __restrict__ und_n, uint8_t* __restrict__ tstate,
-                                                       uint32_t* __restrict__ work, unsigned* __restrict__ work_n)
+// Per (undecided receiver u, super-tile s of four consecutive tiles): the class of the pyramid from
+// the receiver through the super-tile's rectangle -> sstate[u * ST + s] (bits 0-1: the class of
+// rect_class; bit 2: its in_box); undecided super-tiles are appended to swork as u * ST + s.
+// Grid-stride over the device count of undecided receivers.
+__global__ void __launch_bounds__(128) k_super_aperture(DeviceScene S, const float* __restrict__ rx, Frame fr,
+                                                        const TileGeom* __restrict__ sg, int ST, int host_face,
+                                                        float margin, const uint32_t* __restrict__ und,
+                                                        const unsigned* __restrict__ und_n, uint8_t* __restrict__ sstate,
+                                                        uint32_t* __restrict__ swork, unsigned* __restrict__ swork_n)
 {
-    const int64_t total = (int64_t)*und_n * T;
+    const int64_t total = (int64_t)*und_n * ST;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float3 c32 = to_f(fr_c(fr)), n32 = to_f(fr_n(fr));
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += stride) {   // uniform per block
         const int64_t i = base + threadIdx.x;
         uint8_t st = 0;
         if (i < total) {
-            const int64_t r = und[i / T];
+            const int64_t r = und[i / ST];
             bool in_box;
-            st = rect_class(S, f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]), c32, n32, tg[i % T], host_face, margin, in_box);
-            tstate[i] = st | (in_box ? 4 : 0);
+            st = rect_class(S, f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]), c32, n32, sg[i % ST], host_face, margin, in_box);
+            sstate[i] = st | (in_box ? 4 : 0);
         }
-        warp_append(i < total && st == 0, (uint32_t)i, work, work_n);
+        warp_append(i < total && st == 0, (uint32_t)i, swork, swork_n);
     }
 }
 
-// Visibility words of the undecided receivers from their tiles' classes: bits of the elements whose
-// tile is all visible (elements of undecided tiles are added by k_direct_tiles).
-__global__ void k_vis_tiles(int W, int T, const uint32_t* __restrict__ und, const unsigned* __restrict__ und_n,
+// Per tile of an undecided super-tile (four threads per swork entry): the class of the pyramid from
+// the receiver through the tile's rectangle -> tstate[u * T + t] (as sstate); undecided tiles are
+// appended to work as u * T + t. Tiles of decided super-tiles are never classified (their state is
+// the super-tile's).
+__global__ void __launch_bounds__(128) k_tile_aperture(DeviceScene S, const float* __restrict__ rx, Frame fr,
+                                                       const TileGeom* __restrict__ tg, int T, int ST, int host_face,
+                                                       float margin, const uint32_t* __restrict__ und,
+                                                       const uint32_t* __restrict__ swork, const unsigned* __restrict__ swork_n,
+                                                       uint8_t* __restrict__ tstate, uint32_t* __restrict__ work,
+                                                       unsigned* __restrict__ work_n)
+{
+    const int64_t total = (int64_t)*swork_n * 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float3 c32 = to_f(fr_c(fr)), n32 = to_f(fr_n(fr));
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += stride) {   // uniform per block
+        const int64_t k = base + threadIdx.x;
+        uint8_t st = 0;
+        bool live = false;
+        int64_t i = 0;
+        if (k < total) {
+            const uint32_t e = swork[k >> 2];
+            const int64_t u = e / ST;
+            const int t = (int)(e % ST) * 4 + (int)(k & 3);
+            if (t < T) {
+                live = true;
+                i = u * T + t;
+                const int64_t r = und[u];
+                bool in_box;
+                st = rect_class(S, f3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]), c32, n32, tg[t], host_face, margin, in_box);
+                tstate[i] = st | (in_box ? 4 : 0);
+            }
+        }
+        warp_append(live && st == 0, (uint32_t)i, work, work_n);
+    }
+}
+
+// Visibility words of the undecided receivers from their tiles' classes (a decided super-tile's class,
+// else the tile's own): bits of the elements whose tile is all visible (elements of undecided tiles
+// are added by k_direct_tiles).
+__global__ void k_vis_tiles(int W, int T, int ST, const uint32_t* __restrict__ und, const unsigned* __restrict__ und_n,
                             const int* __restrict__ word_ofs, const int2* __restrict__ word_tile,
-                            const uint8_t* __restrict__ tstate, uint32_t* __restrict__ vis)
+                            const uint8_t* __restrict__ sstate, const uint8_t* __restrict__ tstate, uint32_t* __restrict__ vis)
 {
     const int64_t total = (int64_t)*und_n * W;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1048,7 +1086,9 @@ __global__ void k_vis_tiles(int W, int T, const uint32_t* __restrict__ und, cons
         uint32_t v = 0u;
         for (int p = word_ofs[w]; p < word_ofs[w + 1]; ++p) {
             const int2 q = word_tile[p];
-            if ((tstate[u * T + q.x] & 3) == 1) v |= (uint32_t)q.y;
+            int st = sstate[u * ST + (q.x >> 2)] & 3;
+            if (st == 0) st = tstate[u * T + q.x] & 3;
+            if (st == 1) v |= (uint32_t)q.y;
         }
         vis[(int64_t)und[u] * W + w] = v;
     }
@@ -2156,7 +2196,7 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
     const int W = (M + 31) / 32;
     // tiled direct legs ((receiver, tile) entries numbered in 32 bits); RISRT_TILES=0 forces one ray
     // per element for every receiver whose aperture pyramid is undecided (both give the same bits)
-    const int T_tiles = ris->n_tiles;
+    const int T_tiles = ris->n_tiles, ST_tiles = (T_tiles + 3) / 4;
     const char* tiles_env = getenv("RISRT_TILES");
     // sequence culling over groups of super-patches first; RISRT_CULL_LEVELS=1 culls each super-patch
     // against every sequence (both give the same candidates)
@@ -2295,7 +2335,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             unsigned* tile_n;        // their count and the count of undecided (receiver, tile) entries,
             uint8_t* tstate;         // the class of each (undecided receiver, tile) pyramid
             uint32_t* twork;         // and the undecided (receiver, tile) entries
-            TileGeom* tgeom;         // per tile: FP32 corners of its rectangle, in-box flag
+            TileGeom* tgeom;         // per tile, then per super-tile: FP32 corners of its rectangle, in-box flag
+            uint8_t* sstate;         // per (undecided receiver, super-tile): class and in-box flag
+            uint32_t* swork;         // the undecided (receiver, super-tile) entries
             int4* tdq;               // tile rays left for the FP64 settlement (work entry, lane, triangles)
             TileGeom* ageom;         // the same for the whole aperture
             LegBufs main, env, tx;   // work lists, settlement queues and scan space of the Rx leg, of the
@@ -2339,11 +2381,13 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             L.elem_bb = A.get<float4>(1);
             L.rx_state = A.get<uint8_t>((size_t)n_rx);
             L.und = A.get<uint32_t>(tiled ? (size_t)n_rx : 1);
-            L.tile_n = A.get<unsigned>(3);
+            L.tile_n = A.get<unsigned>(4);
             L.tdq = A.get<int4>(tiled ? (size_t)kTileDeferCap : 1);
             L.tstate = A.get<uint8_t>(tiled ? (size_t)n_rx * T_tiles : 1);
             L.twork = A.get<uint32_t>(tiled ? (size_t)n_rx * T_tiles : 1);
-            L.tgeom = A.get<TileGeom>(tiled ? (size_t)T_tiles : 1);
+            L.tgeom = A.get<TileGeom>(tiled ? (size_t)(T_tiles + ST_tiles) : 1);
+            L.sstate = A.get<uint8_t>(tiled ? (size_t)n_rx * ST_tiles : 1);
+            L.swork = A.get<uint32_t>(tiled ? (size_t)n_rx * ST_tiles : 1);
             L.ageom = A.get<TileGeom>(1);
             L.main = LegBufs{L.dense_r, L.dense_slot, L.dense_seq, L.dense_off, L.dense_cnt, L.rq, rq_cap, L.rq_cnt,
                              L.scan_tmp, L.counters + 6};
@@ -2453,18 +2497,22 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
             if (tiled) {
                 // receivers, then spatial tiles of 32 elements, decided by pyramids; rays for the rest
                 const unsigned grid = (unsigned)ctx->sm_count * 8;
-                RISRT_CUDA(ctx, cudaMemsetAsync(L.tile_n, 0, sizeof(unsigned) * 3, sB));
+                RISRT_CUDA(ctx, cudaMemsetAsync(L.tile_n, 0, sizeof(unsigned) * 4, sB));
                 RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.ageom,
                                                                   ris->host_face, mg, L.rx_state, L.und, L.tile_n)));
                 RISRT_KERNEL_ON(ctx, sB, "k_vis_decided", (k_vis_decided<<<nblk(n_rx * W, 256), 256, 0, sB>>>(n_rx, W, M, L.rx_state,
                                                                                                         ps->vis)));
-                RISRT_KERNEL_ON(ctx, sB, "k_tile_geom", (k_tile_geom<<<nblk(T_tiles, 128), 128, 0, sB>>>(S, fr, ris->tile_bb, T_tiles,
-                                                                                               L.tgeom)));
+                // (receiver, super-tile) pyramids, then (receiver, tile) pyramids of undecided super-tiles
+                RISRT_KERNEL_ON(ctx, sB, "k_tile_geom", (k_tile_geom<<<nblk(T_tiles + ST_tiles, 128), 128, 0, sB>>>(
+                                                                  S, fr, ris->tile_bb, T_tiles + ST_tiles, L.tgeom)));
+                RISRT_KERNEL_ON(ctx, sB, "k_super_aperture", (k_super_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, L.tgeom + T_tiles,
+                                                                  ST_tiles, ris->host_face, mg, L.und, L.tile_n, L.sstate,
+                                                                  L.swork, L.tile_n + 3)));
                 RISRT_KERNEL_ON(ctx, sB, "k_tile_aperture", (k_tile_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, L.tgeom, T_tiles,
-                                                                  ris->host_face, mg, L.und, L.tile_n, L.tstate, L.twork,
-                                                                  L.tile_n + 1)));
-                RISRT_KERNEL_ON(ctx, sB, "k_vis_tiles", (k_vis_tiles<<<grid, 256, 0, sB>>>(W, T_tiles, L.und, L.tile_n, ris->word_ofs,
-                                                                  ris->word_tile, L.tstate, ps->vis)));
+                                                                  ST_tiles, ris->host_face, mg, L.und, L.swork, L.tile_n + 3,
+                                                                  L.tstate, L.twork, L.tile_n + 1)));
+                RISRT_KERNEL_ON(ctx, sB, "k_vis_tiles", (k_vis_tiles<<<grid, 256, 0, sB>>>(W, T_tiles, ST_tiles, L.und, L.tile_n,
+                                                                  ris->word_ofs, ris->word_tile, L.sstate, L.tstate, ps->vis)));
                 RISRT_KERNEL_ON(ctx, sB, "k_direct_tiles", (k_direct_tiles<<<grid, 128, 0, sB>>>(S, rxp, ris->elem, W, T_tiles, fr,
                                                                   ris->host_face, tol_base, L.und, ris->tile_elem, L.tstate,
                                                                   L.twork, L.tile_n + 1, ps->vis, L.tdq, kTileDeferCap,
