@@ -1238,6 +1238,8 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
     TraceCounters tc{};
     long long item = -1;
     int r = 0, slot = 0, si = 0, j = 0;
+    int js = 0;                  // segments walked so far; j = the segment walked now
+    bool swap12 = false;         // order 2: the last segment walked before the middle one (it is longer)
     int4 info = make_int4(0, 0, 0, 0);
     float3 p[4] = {f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f), f3(0.f, 0.f, 0.f)};
     float3 a = f3(0.f, 0.f, 0.f), dir = a, inv = a, ainv = a;
@@ -1342,6 +1344,10 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
                         p[3] = R;
                     }
                     j = 0;
+                    js = 0;
+                    // most candidates are blocked: after the first segment (often decided by the map),
+                    // the longer of the other two first
+                    swap12 = info.w == 2 && dot(p[3] - p[2], p[3] - p[2]) > dot(p[2] - p[1], p[2] - p[1]);
                     blocked = false;
                     ++tc.cand;
                     start_segment();
@@ -1354,8 +1360,9 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
         {
             for (int it = 0; it < kSteps; ++it) {
                 if (cur == kNone) {          // segment done: the candidate's next segment right away
-                    if (blocked || j >= info.w) break;
-                    ++j;
+                    if (blocked || js >= info.w) break;
+                    ++js;
+                    j = swap12 && js > 0 ? 3 - js : js;
                     start_segment();
                     continue;
                 }
@@ -1386,8 +1393,9 @@ k_validate(DeviceScene S, const float* __restrict__ dst_xyz, d3 src, int src_fac
             if (blocked) {
                 cand[(int64_t)r * cap + slot] = -1;
                 item = -1;
-            } else if (j < info.w) {
-                ++j;
+            } else if (js < info.w) {
+                ++js;
+                j = swap12 && js > 0 ? 3 - js : js;
                 start_segment();
             } else {
                 item = -1;
