@@ -48,6 +48,20 @@ constexpr int kEvalWarps = 8;
 constexpr int kMaxCfgPerPass = 4;
 constexpr int kElemMajorMin = 64;   // arrays of at least this many elements: lanes own elements
 
+// b_mq of one record for the lane's two elements (those with `on` set), added to their sums.
+template <int PAT, int K, bool LT>
+__device__ __forceinline__ void add_terms(const PathRec& p, const float4 (&e)[2], const bool (&on)[2], cf (&sum)[2],
+                                          float inv_lam, float gr, bool tm)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!on[h]) continue;
+        const cf b = rx_leg_term_k<PAT, K, LT>(p, e[h], inv_lam, gr, tm);
+        sum[h].re += b.re;
+        sum[h].im += b.im;
+    }
+}
+
 // One warp per receiver, lanes own elements, two per pass (m = m0 + lane and m0 + 32 + lane): each
 // lane keeps its elements' data in registers and sums b_mq over the receiver's paths, whose records
 // every lane of the warp reads at the same address (one broadcast load per path serves two elements);
@@ -83,13 +97,17 @@ k_eval_em(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, cons
         }
         for (int q = 0; q < nq; ++q) {
             const PathRec p = rec[o + q];
-            const bool reflected = __float_as_int(p.a.y) > 0;      // order 0: the direct leg
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (!(valid[h] && (reflected || direct[h]))) continue;
-                const cf b = rx_leg_term<PAT>(p, e[h], inv_lam, gr, tm != 0);
-                sum[h].re += b.re;
-                sum[h].im += b.im;
+            // one branch per record (uniform across the warp) into straight-line code for both elements
+            const int kk = __float_as_int(p.a.y), k = kk & 3;
+            if (kk & kRecLosslessTE) {
+                if (k == 2) add_terms<PAT, 2, true>(p, e, valid, sum, inv_lam, gr, tm != 0);
+                else add_terms<PAT, 1, true>(p, e, valid, sum, inv_lam, gr, tm != 0);
+            } else if (k == 0) {
+                add_terms<PAT, 0, false>(p, e, direct, sum, inv_lam, gr, tm != 0);   // the direct leg
+            } else if (k == 1) {
+                add_terms<PAT, 1, false>(p, e, valid, sum, inv_lam, gr, tm != 0);
+            } else {
+                add_terms<PAT, 2, false>(p, e, valid, sum, inv_lam, gr, tm != 0);
             }
         }
 #pragma unroll

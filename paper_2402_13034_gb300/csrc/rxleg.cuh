@@ -30,12 +30,13 @@ __device__ __forceinline__ cf bounce_factor(float c, float er, float ei, bool tm
     return fresnel_f(c, er, ei, tm);
 }
 
-// b_mq for one (path record, element) pair. Paths whose bounces are all lossless dielectrics under the
-// TE coefficient (kRecLosslessTE) keep R real: per bounce c = |(w - u).n'| / L, s = sqrt(eps_r - 1 + c^2),
-// R *= (c - s)^2 / (1 - eps_r), which equals (c - s) / (c + s) since c^2 - s^2 = 1 - eps_r; the branch is
-// uniform across a warp (its lanes share the path record).
-template <int PAT>
-__device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_lam, float gr, bool tm)
+// b_mq for one (path record, element) pair, with the record's bounce count K and its lossless-TE flag
+// LT fixed at compile time (straight-line code). Paths whose bounces are all lossless dielectrics
+// under the TE coefficient (kRecLosslessTE) keep R real: per bounce c = |(w - u).n'| / L,
+// s = sqrt(eps_r - 1 + c^2), R *= (c - s)^2 / (1 - eps_r), which equals (c - s) / (c + s) since
+// c^2 - s^2 = 1 - eps_r.
+template <int PAT, int K, bool LT>
+__device__ __forceinline__ cf rx_leg_term_k(const PathRec& p, float4 e, float inv_lam, float gr, bool tm)
 {
     const float dx = p.w.x - e.x, dy = p.w.y - e.y, dz = p.w.z;
     const float L2 = dx * dx + dy * dy + dz * dz;
@@ -49,22 +50,20 @@ __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_
     } else {
         amp *= sqrt_approx(gr);
     }
-    const int kk = __float_as_int(p.a.y);
-    const int k = kk & 3;
     cf R = cf{amp, 0.f};
-    if (kk & kRecLosslessTE) {
+    if (LT) {
         const float c1 = fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) * iL;
         const float d1 = c1 - sqrt_approx(fmaxf(fmaf(c1, c1, p.a.z), 0.f));
         R.re *= d1 * d1 * p.a.w;
-        if (k == 2) {
+        if (K == 2) {
             const float c2 = fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) * iL;
             const float d2 = c2 - sqrt_approx(fmaxf(fmaf(c2, c2, p.n1.w), 0.f));
             R.re *= d2 * d2 * p.n2.w;
         }
-    } else if (k >= 1) {
+    } else if (K >= 1) {
         float c1 = fabsf(dx * p.n1.x + dy * p.n1.y + dz * p.n1.z) * iL;
         R = cmulf(R, bounce_factor(c1, p.a.z, p.a.w, tm));
-        if (k == 2) {
+        if (K == 2) {
             float c2 = fabsf(dx * p.n2.x + dy * p.n2.y + dz * p.n2.z) * iL;
             R = cmulf(R, bounce_factor(c2, p.n1.w, p.n2.w, tm));
         }
@@ -74,8 +73,21 @@ __device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_
     x -= rintf(x);
     float sn, cs;
     __sincosf(6.28318530717958647f * x, &sn, &cs);
-    if (kk & kRecLosslessTE || k == 0) return cf{R.re * cs, -R.re * sn};   // e^{-j 2 pi x}, R real
+    if (LT || K == 0) return cf{R.re * cs, -R.re * sn};   // e^{-j 2 pi x}, R real
     return cmulf(R, cf{cs, -sn});
+}
+
+// b_mq for one (path record, element) pair: the specialised term for the record's bounce count and
+// lossless-TE flag (the branch is uniform across a warp whose lanes share the record).
+template <int PAT>
+__device__ __forceinline__ cf rx_leg_term(const PathRec& p, float4 e, float inv_lam, float gr, bool tm)
+{
+    const int kk = __float_as_int(p.a.y);
+    const int k = kk & 3;
+    if (kk & kRecLosslessTE)
+        return k == 2 ? rx_leg_term_k<PAT, 2, true>(p, e, inv_lam, gr, tm) : rx_leg_term_k<PAT, 1, true>(p, e, inv_lam, gr, tm);
+    if (k == 0) return rx_leg_term_k<PAT, 0, false>(p, e, inv_lam, gr, tm);
+    return k == 1 ? rx_leg_term_k<PAT, 1, false>(p, e, inv_lam, gr, tm) : rx_leg_term_k<PAT, 2, false>(p, e, inv_lam, gr, tm);
 }
 
 }  // namespace risrt
