@@ -67,7 +67,7 @@ PRECISIONS = {0: "fp32_simt", 1: "bf16", 2: "bf16x2", 3: "fp16"}
 # with: a changed source reports null traffic until the capture is repeated.
 DOMINANT = "k_validate"      # the kernel whose launches the timed region brackets with events
 MEASURED_TRAFFIC = {
-    "k_validate": {"bytes_per_step": 193.06e6, "sha256_16": "e830eec905a149b9",
+    "k_validate": {"bytes_per_step": 194.19e6, "sha256_16": "a5748581a548a124",
                    "sources": [("trace.cu", "k_validate("), ("geom.cuh", None), ("scene.cu", None)],
                    "profile": "profiles/k_validate_room_256x256_dram.md"},
 }
@@ -272,8 +272,8 @@ def bench_direct_legs(R, dev, grid=1000, side=64, reps=3):
     ctx = R.Context(dev.index or 0, stream.cuda_stream)
     scene, ris, rx = R.upload_workload(ctx, w)
     out, bits = {"workload": f"room_{side * side}el_{grid}x{grid}_order2", "n_rx": w.n_rx, "elements": w.n_elem}, {}
-    kern = ("k_tile_geom", "k_rx_aperture", "k_vis_decided", "k_tile_aperture", "k_vis_tiles", "k_direct_tiles",
-            "k_direct_settle", "k_direct_vis")
+    kern = ("k_tile_geom", "k_rx_aperture", "k_vis_decided", "k_super_aperture", "k_tile_aperture", "k_vis_tiles",
+            "k_direct_tiles", "k_direct_settle", "k_direct_vis")
     for mode in ("tiled", "per_element"):
         if mode == "per_element":
             os.environ["RISRT_TILES"] = "0"

@@ -1038,7 +1038,8 @@ __global__ void __launch_bounds__(128) k_super_aperture(DeviceScene S, const flo
 // Per tile of an undecided super-tile (four threads per swork entry): the class of the pyramid from
 // the receiver through the tile's rectangle -> tstate[u * T + t] (as sstate); undecided tiles are
 // appended to work as u * T + t. Tiles of decided super-tiles are never classified (their state is
-// the super-tile's).
+// the super-tile's). swork == nullptr: one super-tile (at most four tiles), not classified on its own
+// (its rectangle is the aperture's): entry u of the undecided receivers stands for (u, 0).
 __global__ void __launch_bounds__(128) k_tile_aperture(DeviceScene S, const float* __restrict__ rx, Frame fr,
                                                        const TileGeom* __restrict__ tg, int T, int ST, int host_face,
                                                        float margin, const uint32_t* __restrict__ und,
@@ -1055,7 +1056,7 @@ __global__ void __launch_bounds__(128) k_tile_aperture(DeviceScene S, const floa
         bool live = false;
         int64_t i = 0;
         if (k < total) {
-            const uint32_t e = swork[k >> 2];
+            const uint32_t e = swork ? swork[k >> 2] : (uint32_t)(k >> 2);
             const int64_t u = e / ST;
             const int t = (int)(e % ST) * 4 + (int)(k & 3);
             if (t < T) {
@@ -1086,7 +1087,7 @@ __global__ void k_vis_tiles(int W, int T, int ST, const uint32_t* __restrict__ u
         uint32_t v = 0u;
         for (int p = word_ofs[w]; p < word_ofs[w + 1]; ++p) {
             const int2 q = word_tile[p];
-            int st = sstate[u * ST + (q.x >> 2)] & 3;
+            int st = sstate ? sstate[u * ST + (q.x >> 2)] & 3 : 0;
             if (st == 0) st = tstate[u * T + q.x] & 3;
             if (st == 1) v |= (uint32_t)q.y;
         }
@@ -2513,14 +2514,18 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 // (receiver, super-tile) pyramids, then (receiver, tile) pyramids of undecided super-tiles
                 RISRT_KERNEL_ON(ctx, sB, "k_tile_geom", (k_tile_geom<<<nblk(T_tiles + ST_tiles, 128), 128, 0, sB>>>(
                                                                   S, fr, ris->tile_bb, T_tiles + ST_tiles, L.tgeom)));
-                RISRT_KERNEL_ON(ctx, sB, "k_super_aperture", (k_super_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, L.tgeom + T_tiles,
-                                                                  ST_tiles, ris->host_face, mg, L.und, L.tile_n, L.sstate,
-                                                                  L.swork, L.tile_n + 3)));
+                // (one super-tile is the aperture itself: its tiles are classified directly)
+                const bool supers = ST_tiles > 1;
+                if (supers)
+                    RISRT_KERNEL_ON(ctx, sB, "k_super_aperture", (k_super_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, L.tgeom + T_tiles,
+                                                                      ST_tiles, ris->host_face, mg, L.und, L.tile_n, L.sstate,
+                                                                      L.swork, L.tile_n + 3)));
                 RISRT_KERNEL_ON(ctx, sB, "k_tile_aperture", (k_tile_aperture<<<grid, 128, 0, sB>>>(S, rxp, fr, L.tgeom, T_tiles,
-                                                                  ST_tiles, ris->host_face, mg, L.und, L.swork, L.tile_n + 3,
-                                                                  L.tstate, L.twork, L.tile_n + 1)));
+                                                                  ST_tiles, ris->host_face, mg, L.und, supers ? L.swork : nullptr,
+                                                                  supers ? L.tile_n + 3 : L.tile_n, L.tstate, L.twork, L.tile_n + 1)));
                 RISRT_KERNEL_ON(ctx, sB, "k_vis_tiles", (k_vis_tiles<<<grid, 256, 0, sB>>>(W, T_tiles, ST_tiles, L.und, L.tile_n,
-                                                                  ris->word_ofs, ris->word_tile, L.sstate, L.tstate, ps->vis)));
+                                                                  ris->word_ofs, ris->word_tile, supers ? L.sstate : nullptr,
+                                                                  L.tstate, ps->vis)));
                 RISRT_KERNEL_ON(ctx, sB, "k_direct_tiles", (k_direct_tiles<<<grid, 128, 0, sB>>>(S, rxp, ris->elem, W, T_tiles, fr,
                                                                   ris->host_face, tol_base, L.und, ris->tile_elem, L.tstate,
                                                                   L.twork, L.tile_n + 1, ps->vis, L.tdq, kTileDeferCap,
@@ -2593,8 +2598,9 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                     const int64_t n_super = (n_dst + kSuperRx - 1) / kSuperRx;
                     RISRT_KERNEL_ON(ctx, st, "k_patch_boxes", (k_patch_boxes<<<(unsigned)n_super, 256, 0, st>>>(dst, L.rx_order, n_dst,
                                                                                                        lb.sp_box)));
-                    if (n_super > 2 * kGroupSuper && two_level_cull) {
-                        // two levels: groups of super-patches against every sequence, then each
+                    if (n_super > 16 * kGroupSuper && two_level_cull) {
+                        // two levels (above 256 super-patches, where they pay: measured on the room
+                        // and the hall): groups of super-patches against every sequence, then each
                         // super-patch against its group's survivors
                         const int64_t n_groups = (n_super + kGroupSuper - 1) / kGroupSuper;
                         RISRT_KERNEL_ON(ctx, st, "k_group_boxes", (k_group_boxes<<<nblk(n_groups, 128), 128, 0, st>>>(

@@ -103,10 +103,10 @@ def test_tiled_direct_legs(side, monkeypatch):
 
 
 def test_two_level_culling_same_paths(monkeypatch):
-    """The full 256x256 room (64 super-patches of 1,024 receivers, so the sequences are culled for
-    groups of 16 super-patches first): path sets and fields equal those of culling every super-patch
-    against every sequence (RISRT_CULL_LEVELS=1)."""
-    w = S.room()
+    """The room at 600x600 receivers (352 super-patches of 1,024 receivers, so the sequences are culled
+    for groups of 16 super-patches first): path sets and fields equal those of culling every
+    super-patch against every sequence (RISRT_CULL_LEVELS=1)."""
+    w = S.room(grid=600)
     g = run_gpu(w)
     monkeypatch.setenv("RISRT_CULL_LEVELS", "1")
     g1 = run_gpu(w)
