@@ -117,7 +117,12 @@ int risrt_scene_upload(risrt_ctx* ctx, const float* verts_host, int64_t n_verts,
  * Tang22), element pattern F(theta) = max(cos theta, 0) about n (Sec. III-C).
  *   elem_uv_host [M][2] float (a_m, b_m).  1 <= M <= 65536.
  *   host_face: face of the scene the RIS is mounted on (ignored for occlusion of rays leaving or
- *   reaching an element), or -1. */
+ *   reaching an element), or -1.
+ * For M > 64 the call also stores spatial tiles of 32 elements (consecutive in the Morton order of
+ * (a_m, b_m)) with which a trace decides element -> receiver visibility tile by tile; a trace over
+ * such a RIS takes about 5 n_rx M / 32 bytes more scratch (included in risrt_trace_workspace_size).
+ * The environment variable RISRT_TILES=0, read by each trace, makes it trace every element instead
+ * (the same visibility bits). */
 int risrt_ris_upload(risrt_ctx* ctx, const float* elem_uv_host, int32_t M, const float center[3],
                      const float t1[3], const float t2[3], float dy, float dz, float elem_gain,
                      int32_t host_face, risrt_ris** out);
