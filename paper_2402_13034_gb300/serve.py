@@ -296,6 +296,16 @@ class Server:
                 waiting.popleft()
                 self._left_queue()
                 self._slot_work[self._slot_free.get()].put((req, fut, fp))
+        # closed: requests still waiting for admission fail instead of never completing
+        while True:
+            try:
+                waiting.append(self._pending.get_nowait())
+            except queue.Empty:
+                break
+        for req, fut, fp in waiting:
+            self._left_queue()
+            if not fut.done():
+                fut.set_exception(RuntimeError("server closed before the request was admitted"))
 
     def _worker(self, slot: int):
         """The slot's thread: runs the requests the dispatcher hands to this slot, one at a time."""

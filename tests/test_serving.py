@@ -363,6 +363,28 @@ def test_load_shedding_wait_limit():
     assert ran == [0] and srv.shed_late == 2 and srv.shed_full == 0
 
 
+def test_close_fails_waiting_requests():
+    """No request is left pending by close: requests still waiting for admission when the server
+    closes fail with an error (those admitted meanwhile complete), and the running one completes."""
+    ws = _room_workloads()
+    reqs = _requests(ws, 4)
+    run, started, release = _blocking_executor()
+    srv = serve.Server(slots=1, budget_bytes=1 << 40, executor=run)
+    for name, w in ws.items():
+        srv.add_scene(name, w.scene)
+    first = srv.submit(reqs[0])
+    assert started.wait(timeout=10)
+    waiting = [srv.submit(r) for r in reqs[1:]]
+    time.sleep(0.1)
+    release.set()
+    srv.close()
+    assert first.result(timeout=10) is not None
+    for f in waiting:
+        assert f.done()
+        if f.exception() is not None:               # else admitted before the close took effect
+            assert "closed" in str(f.exception())
+
+
 def test_shared_input_mix_keeps_distributions():
     """The shared-input mix draws sizes from the same distributions (receiver counts within 1/32 of
     a decade of a log-uniform draw, C in range, configurations rows of one pool per RIS size) and
