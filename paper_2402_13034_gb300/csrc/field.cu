@@ -45,16 +45,22 @@ __device__ __forceinline__ cf rx_leg_term_plain(const PathRec& p, float4 e, floa
 }
 
 constexpr int kEvalWarps = 8;
+#ifndef RISRT_EVAL_EPL
+#define RISRT_EVAL_EPL 2
+#endif
+// elements per lane per pass of the element-major kernel (measured on the room: 3 and 4 take 6% and 2%
+// longer than 2)
+constexpr int kEvalEpl = RISRT_EVAL_EPL;
 constexpr int kMaxCfgPerPass = 4;
 constexpr int kElemMajorMin = 64;   // arrays of at least this many elements: lanes own elements
 
 // b_mq of one record for the lane's two elements (those with `on` set), added to their sums.
 template <int PAT, int K, bool LT>
-__device__ __forceinline__ void add_terms(const PathRec& p, const float4 (&e)[2], const bool (&on)[2], cf (&sum)[2],
-                                          float inv_lam, float gr, bool tm)
+__device__ __forceinline__ void add_terms(const PathRec& p, const float4 (&e)[kEvalEpl], const bool (&on)[kEvalEpl],
+                                          cf (&sum)[kEvalEpl], float inv_lam, float gr, bool tm)
 {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kEvalEpl; ++h) {
         if (!on[h]) continue;
         const cf b = rx_leg_term_k<PAT, K, LT>(p, e[h], inv_lam, gr, tm);
         sum[h].re += b.re;
@@ -62,9 +68,9 @@ __device__ __forceinline__ void add_terms(const PathRec& p, const float4 (&e)[2]
     }
 }
 
-// One warp per receiver, lanes own elements, two per pass (m = m0 + lane and m0 + 32 + lane): each
+// One warp per receiver, lanes own elements, kEvalEpl per pass (m = m0 + 32 h + lane): each
 // lane keeps its elements' data in registers and sums b_mq over the receiver's paths, whose records
-// every lane of the warp reads at the same address (one broadcast load per path serves two elements);
+// every lane of the warp reads at the same address (one broadcast load per path serves kEvalEpl elements);
 // then c_m and the NC configurations' Gamma_m scale the sums. For arrays of kElemMajorMin elements or
 // more.
 template <int PAT, int NC>
@@ -82,13 +88,13 @@ k_eval_em(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, cons
     cf acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = cf{0.f, 0.f};
-    for (int m0 = 0; m0 < M; m0 += 64) {
-        int mm[2];
-        bool valid[2], direct[2];
-        float4 e[2];
-        cf sum[2];
+    for (int m0 = 0; m0 < M; m0 += 32 * kEvalEpl) {
+        int mm[kEvalEpl];
+        bool valid[kEvalEpl], direct[kEvalEpl];
+        float4 e[kEvalEpl];
+        cf sum[kEvalEpl];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kEvalEpl; ++h) {
             mm[h] = m0 + 32 * h + lane;
             valid[h] = mm[h] < M;
             e[h] = valid[h] ? elem[mm[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -111,7 +117,7 @@ k_eval_em(const PathRec* __restrict__ rec, const int64_t* __restrict__ off, cons
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kEvalEpl; ++h) {
             if (!valid[h]) continue;
             const float2 c2 = cm[mm[h]];
             const cf cb = cmulf(sum[h], cf{c2.x, c2.y});
