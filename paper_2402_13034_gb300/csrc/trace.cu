@@ -997,16 +997,32 @@ __global__ void __launch_bounds__(128) k_rx_aperture(DeviceScene S, const float*
     if (und) warp_append(r < n_rx && st == 0, (uint32_t)r, und, und_n);
 }
 
-// Visibility words of the receivers whose aperture pyramid is decided; the undecided receivers'
-// words come from k_vis_tiles and k_direct_tiles.
+// Visibility words of the receivers whose aperture pyramid is decided, four words per thread (one
+// 16-byte store when rows are multiples of four words and the array is 16-byte aligned); the
+// undecided receivers' words come from k_vis_tiles and k_direct_tiles.
 __global__ void k_vis_decided(int64_t n_rx, int W, int M, const uint8_t* __restrict__ state, uint32_t* __restrict__ vis)
 {
+    const int W4 = (W + 3) >> 2;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_rx * W) return;
-    const uint8_t st = state[i / W];
+    if (i >= n_rx * W4) return;
+    const int64_t r = i / W4;
+    const uint8_t st = state[r];
     if (st == 0) return;
-    const int left = M - 32 * (int)(i % W);
-    vis[i] = st == 2 ? 0u : (left >= 32 ? 0xffffffffu : ((1u << left) - 1u));
+    const int w0 = (int)(i % W4) * 4;
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int left = M - 32 * (w0 + k);
+        v[k] = st == 2 || left <= 0 ? 0u : (left >= 32 ? 0xffffffffu : ((1u << left) - 1u));
+    }
+    uint32_t* row = vis + r * W;
+    if ((W & 3) == 0 && ((uintptr_t)vis & 15) == 0) {
+        *reinterpret_cast<uint4*>(row + w0) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (w0 + k < W) row[w0 + k] = v[k];
+    }
 }
 
 // Per (undecided receiver u, super-tile s of four consecutive tiles): the class of the pyramid from
@@ -2509,8 +2525,8 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                 RISRT_CUDA(ctx, cudaMemsetAsync(L.tile_n, 0, sizeof(unsigned) * 4, sB));
                 RISRT_KERNEL_ON(ctx, sB, "k_rx_aperture", (k_rx_aperture<<<nblk(n_rx, 128), 128, 0, sB>>>(S, rxp, n_rx, fr, L.ageom,
                                                                   ris->host_face, mg, L.rx_state, L.und, L.tile_n)));
-                RISRT_KERNEL_ON(ctx, sB, "k_vis_decided", (k_vis_decided<<<nblk(n_rx * W, 256), 256, 0, sB>>>(n_rx, W, M, L.rx_state,
-                                                                                                        ps->vis)));
+                RISRT_KERNEL_ON(ctx, sB, "k_vis_decided", (k_vis_decided<<<nblk(n_rx * ((W + 3) / 4), 256), 256, 0, sB>>>(
+                                                                  n_rx, W, M, L.rx_state, ps->vis)));
                 // (receiver, super-tile) pyramids, then (receiver, tile) pyramids of undecided super-tiles
                 RISRT_KERNEL_ON(ctx, sB, "k_tile_geom", (k_tile_geom<<<nblk(T_tiles + ST_tiles, 128), 128, 0, sB>>>(
                                                                   S, fr, ris->tile_bb, T_tiles + ST_tiles, L.tgeom)));
