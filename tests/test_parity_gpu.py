@@ -102,6 +102,27 @@ def test_tiled_direct_legs(side, monkeypatch):
     oracle_parity(w, g)
 
 
+def test_tiled_direct_legs_at_scale(monkeypatch):
+    """200x200 receivers against a 4,096-element RIS: many undecided tiles, rays whose FP32 walk meets
+    triangles too close to call (settled in FP64 after the walk) — the visibility bits equal one ray
+    per element (RISRT_TILES=0), whose settlements run in the walk."""
+    import torch
+    from paper_2402_13034_gb300 import risrt as R
+    w = S.room(grid=200, square_side=64)
+    ctx = R.Context(0, torch.cuda.current_stream().cuda_stream)
+    scene, ris, rx = R.upload_workload(ctx, w)
+    bits = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("RISRT_TILES", mode)
+        ps = ctx.trace_paths(scene, ris, rx, w.freq_hz, w.max_order_tx, w.max_order_rx, R.flags_of(w))
+        bits[mode] = ps.export()["vis"]
+        ps.close()
+    monkeypatch.delenv("RISRT_TILES")
+    assert np.array_equal(bits["1"], bits["0"])
+    seen = np.unpackbits(bits["1"].view(np.uint8), axis=1).sum(axis=1)
+    assert np.any((seen > 0) & (seen < 4096))
+
+
 def test_two_level_culling_same_paths(monkeypatch):
     """The room at 600x600 receivers (352 super-patches of 1,024 receivers, so the sequences are culled
     for groups of 16 super-patches first): path sets and fields equal those of culling every
