@@ -371,37 +371,58 @@ __global__ void k_seq_cull2(DeviceScene S, const SeqEntry* __restrict__ seqs, co
 
 // Indices of the set bits of each super-patch's sequence mask, in increasing order (one block of 256
 // threads per super-patch): list[p * stride + i] for i < cnt[p].
-__global__ void k_mask_compact(const unsigned* __restrict__ mask, int words, int64_t n_super, int64_t stride,
-                               int* __restrict__ list, int* __restrict__ cnt, const int* __restrict__ g_list,
-                               const int* __restrict__ g_cnt)
+constexpr int kCompactThreads = 1024;
+__global__ void __launch_bounds__(kCompactThreads) k_mask_compact(const unsigned* __restrict__ mask, int words, int64_t n_super,
+                                                                  int64_t stride, int* __restrict__ list,
+                                                                  int* __restrict__ cnt, const int* __restrict__ g_list,
+                                                                  const int* __restrict__ g_cnt)
 {
-    __shared__ int part[256];
+    __shared__ int wsum[kCompactThreads / 32];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t sp = blockIdx.x; sp < n_super; sp += gridDim.x) {
         const unsigned* m = mask + sp * words;
         // second level: bits are positions in the group's survivor list, valid up to its count
         const int nw = g_list ? min(words, (g_cnt[sp / kGroupSuper] + 31) / 32) : words;
         const int* remap = g_list ? g_list + (sp / kGroupSuper) * stride : nullptr;
-        const int per = (nw + (int)blockDim.x - 1) / (int)blockDim.x;
-        const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
-        int c = 0;
-        for (int w = w0; w < w1; ++w) c += __popc(m[w]);
-        part[threadIdx.x] = c;
-        __syncthreads();
-        for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scan of the per-thread counts
-            const int v = (int)threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        int* out = list + sp * stride;
+        int total = 0;
+        for (int r0 = 0; r0 < nw; r0 += kCompactThreads) {   // rounds of one word per thread
+            const int wi = r0 + (int)threadIdx.x;
+            const unsigned mw = wi < nw ? m[wi] : 0u;
+            const int c = __popc(mw);
+            int x = c;                                        // inclusive scan over the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
             __syncthreads();
-            part[threadIdx.x] += v;
+            if (warp == 0) {                                  // inclusive scan of the warp totals
+                int v = wsum[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, v, o);
+                    if (lane >= o) v += y;
+                }
+                wsum[lane] = v;
+            }
+            __syncthreads();
+            const int wbase = total + (warp > 0 ? wsum[warp - 1] : 0);
+            // the warp's 32 words in order, each word's set bits written by the lanes they name
+            for (int j = 0; j < 32; ++j) {
+                const unsigned wj = __shfl_sync(FULL, mw, j);
+                const int oj = __shfl_sync(FULL, x - c, j);
+                if ((wj >> lane) & 1u) {
+                    const int idx = (r0 + warp * 32 + j) * 32 + lane;
+                    out[wbase + oj + __popc(wj & ((1u << lane) - 1u))] = remap ? remap[idx] : idx;
+                }
+            }
+            total += wsum[kCompactThreads / 32 - 1];
             __syncthreads();
         }
-        int pos = part[threadIdx.x] - c;
-        int* out = list + sp * stride;
-        for (int w = w0; w < w1; ++w)
-            for (unsigned b = m[w]; b; b &= b - 1) {
-                const int idx = w * 32 + __ffs(b) - 1;
-                out[pos++] = remap ? remap[idx] : idx;
-            }
-        if (threadIdx.x == blockDim.x - 1) cnt[sp] = part[threadIdx.x];
-        __syncthreads();
+        if (threadIdx.x == 0) cnt[sp] = total;
     }
 }
 
@@ -2624,20 +2645,20 @@ int trace_paths(risrt_ctx* ctx, const risrt_scene* sc, const risrt_ris* ris, con
                         RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_groups, 65535)),
                                                                       256, 0, st>>>(S, t.e, t.n, lb.g_box, n_groups, words, lb.g_mask,
                                                                                     n_dev, true)));
-                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_groups, 4096), 256, 0, st>>>(
+                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_groups, 4096), kCompactThreads, 0, st>>>(
                                                                 lb.g_mask, words, n_groups, (int64_t)words * 32, lb.g_list, lb.g_cnt,
                                                                 nullptr, nullptr)));
                         RISRT_KERNEL_ON(ctx, st, "k_seq_cull2", (k_seq_cull2<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
                                                                  256, 0, st>>>(S, t.e, lb.sp_box, n_super, lb.g_list, lb.g_cnt,
                                                                                (int64_t)words * 32, words, lb.sp_mask)));
-                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
+                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), kCompactThreads, 0, st>>>(
                                                                 lb.sp_mask, words, n_super, (int64_t)words * 32, lb.sp_list, lb.sp_cnt,
                                                                 lb.g_list, lb.g_cnt)));
                     } else {
                         RISRT_KERNEL_ON(ctx, st, "k_seq_cull", (k_seq_cull<<<dim3(nblk(t.n, 256), (unsigned)std::min<int64_t>(n_super, 65535)),
                                                                       256, 0, st>>>(S, t.e, t.n, lb.sp_box, n_super, words, lb.sp_mask,
                                                                                     n_dev, false)));
-                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), 256, 0, st>>>(
+                        RISRT_KERNEL_ON(ctx, st, "k_mask_compact", (k_mask_compact<<<(unsigned)std::min<int64_t>(n_super, 4096), kCompactThreads, 0, st>>>(
                                                                 lb.sp_mask, words, n_super, (int64_t)words * 32, lb.sp_list, lb.sp_cnt,
                                                                 nullptr, nullptr)));
                     }
